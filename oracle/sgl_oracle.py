@@ -1,0 +1,404 @@
+"""Plain FP64 CPU oracle for the spherical Gauss-Laguerre (SGL) Fourier transform.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this module:
+it is called by ``tests/``, by ``__graft_entry__.smoke()`` and by the CPU
+baseline leg of ``bench.py``.  It shares no code with the CUDA library.
+
+What it computes (Prestin & Wuelker, "Fast Fourier Transforms for Spherical
+Gauss-Laguerre Basis Functions"):
+
+* the SGL basis ``H_nlm = N_nl R_nl(r) Y_lm(theta, phi)`` (Def 1.2, Def 2.1),
+  index set ``|m| <= l < n <= B`` (Cor 1.3);
+* the quadrature of the SGL sampling theorem (Thm 3.4), i.e. the forward
+  transform ``fhat_nlm = sum_{i,j,k} w_ijk f(x_ijk) conj(H_nlm(x_ijk))``, and
+  the reconstruction (inverse) ``f(x) = sum fhat_nlm H_nlm(x)`` (Algorithm 2);
+* the adjoints of both, from the matrix form of Sect. 3.4.
+
+Readings taken where the paper is silent or differs from the grid used here
+(each is listed in the design notes with its reason):
+
+R1  radial rule: B generalized Gauss-Laguerre nodes in ``t = r^2`` with
+    alpha = 1/2 (weight ``t^{1/2} e^{-t}``), so that
+    ``int_0^inf p(r) r^2 e^{-r^2} dr = 1/2 sum_i w_i p(sqrt(t_i))``; exact for
+    the bandlimit-B integrands of Eq. (zwischenstufe) because, after the exact
+    angular projection, the radial integrand for fixed l is a polynomial of
+    degree ``<= 2B-2-l`` in t.
+R2  sphere weights: Thm 3.1's ``b_j`` sums to 2; the azimuthal factor
+    ``pi/B`` is applied, ``beta_j = (pi/B) b_j``.
+R3  Lemma 3.7 recurs the *normalized* radial functions ``N_nl R_nl``.
+R4  the Legendre functions are carried fully normalized (``Lambda_lm =
+    Y_lm e^{-i m phi}``) with the Condon-Shortley phase of Def 2.1 and
+    ``Y_{l,-m} = (-1)^m conj(Y_lm)``.
+R5  samples are Gaussian-weighted: ``ftil(x) = exp(-r^2/2) f(x)``; the radial
+    table is ``T_nl(i) = N_nl R_nl(r_i) exp(-t_i/2)`` and the radial weight
+    ``what_i = (w_i/2) exp(t_i)`` (the symmetric form of the paper's
+    ``a_i exp(r_i^2)`` modification, Sect. 3.2 and Sect. 5).
+R6  phi-DFT sign ``e^{-i m phi}`` forward, ``e^{+i m phi}`` inverse, no 1/N;
+    the Nyquist bin ``m = B`` is not a coefficient (dropped forward, zero
+    inverse).
+
+Layouts (Sect. 3.4 index maps with ``i < B``):
+  samples ``[batch][i][j][k]``: psi = 4B^2 i + 2B j + k, complex128;
+  coefficients ``[batch][omega]``: omega = n(n-1)(2n-1)/6 + l(l+1) + m.
+"""
+from __future__ import annotations
+
+from functools import lru_cache
+from math import lgamma, log, pi, sqrt
+
+import numpy as np
+
+__all__ = [
+    "coeff_count", "omega", "nlm_list",
+    "sphere_rule", "laguerre_rule", "radial_weights", "grid",
+    "legendre_table", "radial_table",
+    "laguerre_explicit", "legendre_rodrigues", "basis_explicit",
+    "forward", "inverse", "forward_direct", "inverse_direct", "sgl_matrix",
+    "adjoint_forward", "adjoint_inverse", "sample_weights",
+    "physical_to_weighted", "weighted_to_physical",
+]
+
+
+# ---------------------------------------------------------------------------
+# index maps (Sect. 3.4)
+# ---------------------------------------------------------------------------
+
+def coeff_count(B: int) -> int:
+    """Omega = B(B+1)(2B+1)/6, the number of SGL coefficients (Sect. 3.4)."""
+    return B * (B + 1) * (2 * B + 1) // 6
+
+
+def omega(n: int, l: int, m: int) -> int:
+    """Linear coefficient index omega(n,l,m) of Sect. 3.4."""
+    return n * (n - 1) * (2 * n - 1) // 6 + l * (l + 1) + m
+
+
+def nlm_list(B: int):
+    """All (n, l, m) with |m| <= l < n <= B, in omega order."""
+    out = []
+    for n in range(1, B + 1):
+        for l in range(n):
+            for m in range(-l, l + 1):
+                out.append((n, l, m))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# quadrature rules (Thm 3.1, Lemma 3.2; Thm 3.3 restated for t = r^2)
+# ---------------------------------------------------------------------------
+
+def sphere_rule(B: int):
+    """Equiangular rule of order L = B (Thm 3.1).
+
+    Returns theta_j = (2j+1) pi / 4B, phi_k = k pi / B (j, k < 2B) and the
+    weights beta_j = (pi/B) b_j with b_j the closed form of Thm 3.1 (R2).
+    """
+    j = np.arange(2 * B)
+    theta = (2 * j + 1) * pi / (4 * B)
+    phi = np.arange(2 * B) * pi / B
+    l = np.arange(B)
+    inner = np.sin(np.outer(2 * j + 1, 2 * l + 1) * pi / (4 * B)) / (2 * l + 1)
+    b = np.sin(theta) * (2.0 / B) * inner.sum(axis=1)
+    beta = (pi / B) * b
+    return theta, phi, beta
+
+
+def _laguerre_pair(n: int, alpha: float, t: np.ndarray):
+    """(L_n^(alpha)(t), L_{n-1}^(alpha)(t)) by the three-term recurrence
+    Eq. (laguerre_recursion)."""
+    prev = np.zeros_like(t)
+    cur = np.ones_like(t)
+    for k in range(n):
+        nxt = ((2 * k + alpha + 1 - t) * cur - (k + alpha) * prev) / (k + 1)
+        prev, cur = cur, nxt
+    return cur, prev
+
+
+@lru_cache(maxsize=None)
+def laguerre_rule(B: int, alpha: float = 0.5):
+    """Generalized Gauss-Laguerre rule with B nodes for t^alpha e^{-t} (R1).
+
+    Nodes: eigenvalues of the Jacobi matrix of the recurrence
+    Eq. (laguerre_recursion) (a library eigensolver), polished by Newton steps
+    on L_B^(alpha) evaluated by that recurrence.  Weights: the Christoffel
+    form w_i = Gamma(B+alpha+1) t_i / (B! (B+alpha)^2 L_{B-1}(t_i)^2),
+    evaluated in logarithms.
+    """
+    k = np.arange(B, dtype=np.float64)
+    off = np.sqrt(np.arange(1, B) * (np.arange(1, B) + alpha))
+    jac = np.diag(2 * k + alpha + 1) + np.diag(off, 1) + np.diag(off, -1)
+    t = np.sort(np.linalg.eigvalsh(jac))
+    for _ in range(4):
+        ln, ln1 = _laguerre_pair(B, alpha, t)
+        dln = (B * ln - (B + alpha) * ln1) / t
+        t = t - ln / dln
+    _, ln1 = _laguerre_pair(B, alpha, t)
+    logw = (lgamma(B + alpha + 1) - lgamma(B + 1) + np.log(t)
+            - 2 * log(B + alpha) - 2 * np.log(np.abs(ln1)))
+    return t, logw
+
+
+def radial_weights(B: int):
+    """r_i, t_i = r_i^2 and the modified radial weights
+    what_i = (w_i / 2) exp(t_i) (R1, R5)."""
+    t, logw = laguerre_rule(B)
+    what = np.exp(logw - log(2.0) + t)
+    return np.sqrt(t), t, what
+
+
+def grid(B: int):
+    """(r_i, theta_j, phi_k, what_i, beta_j) of the sampling grid."""
+    r, _, what = radial_weights(B)
+    theta, phi, beta = sphere_rule(B)
+    return r, theta, phi, what, beta
+
+
+def sample_weights(B: int) -> np.ndarray:
+    """w_psi = what_i * beta_j as a (B, 2B, 2B) array (Sect. 3.4)."""
+    _, _, what = radial_weights(B)
+    _, _, beta = sphere_rule(B)
+    return np.broadcast_to(what[:, None, None] * beta[None, :, None], (B, 2 * B, 2 * B))
+
+
+# ---------------------------------------------------------------------------
+# basis tables (Def 2.1 + Eq. legendre_recurrence; Lemma 3.7)
+# ---------------------------------------------------------------------------
+
+@lru_cache(maxsize=None)
+def legendre_table(B: int) -> np.ndarray:
+    """Lam[m, l, j] = Y_lm(theta_j, phi) e^{-i m phi} for 0 <= m <= l < B.
+
+    The normalized form of Eq. (legendre_recurrence) (R4).  Seed:
+    Lam_mm = (-1)^m sqrt((2m+1)/4pi * prod_{k<=m} (2k-1)/(2k)) sin^m theta,
+    formed in logarithms; Lam_{m+1,m} = sqrt(2m+3) cos theta Lam_mm.
+    Entries with l < m are zero.  Negative orders follow from
+    Lam_{l,-m} = (-1)^m Lam_{l,m}.
+    """
+    theta, _, _ = sphere_rule(B)
+    x = np.cos(theta)
+    logsin = np.log(np.sin(theta))
+    lam = np.zeros((B, B, 2 * B))
+    logprod = 0.0
+    for m in range(B):
+        if m > 0:
+            logprod += log((2 * m - 1) / (2 * m))
+        seed = np.exp(0.5 * log((2 * m + 1) / (4 * pi)) + 0.5 * logprod + m * logsin)
+        lam[m, m] = -seed if (m % 2) else seed
+        if m + 1 < B:
+            lam[m, m + 1] = sqrt(2 * m + 3) * x * lam[m, m]
+        for l in range(m + 1, B - 1):
+            # Lam_{l+1,m} from Lam_{l,m} and Lam_{l-1,m}
+            a = sqrt((2 * l + 1) * (2 * l + 3) / ((l + 1 - m) * (l + 1 + m)))
+            c = sqrt((2 * l + 3) * (l + m) * (l - m) / ((2 * l - 1) * (l + 1 - m) * (l + 1 + m)))
+            lam[m, l + 1] = a * x * lam[m, l] - c * lam[m, l - 1]
+    return lam
+
+
+@lru_cache(maxsize=None)
+def radial_table(B: int) -> np.ndarray:
+    """T[l, n-1, i] = N_nl R_nl(r_i) exp(-t_i/2) for 0 <= l < n <= B.
+
+    Lemma 3.7 read for the normalized functions (R3), seed
+    sqrt(2/Gamma(l+3/2)) r^l formed in logarithms together with exp(-t/2).
+    Entries with n <= l are zero.
+    """
+    _, t, _ = radial_weights(B)
+    logt = np.log(t)
+    T = np.zeros((B, B, B))
+    for l in range(B):
+        seed = np.exp(0.5 * log(2.0) - 0.5 * lgamma(l + 1.5) + 0.5 * l * logt - 0.5 * t)
+        prev = np.zeros(B)
+        cur = seed
+        T[l, l] = cur  # n = l + 1
+        for n in range(l + 1, B):
+            # R_{n+1,l} from R_{n,l} and R_{n-1,l}
+            a = (2 * n - l - 0.5 - t) / sqrt((n + 0.5) * (n - l))
+            c = sqrt((n - 0.5) / (n + 0.5) * (n - l - 1) / (n - l))
+            nxt = a * cur - c * prev
+            prev, cur = cur, nxt
+            T[l, n] = cur
+    return T
+
+
+# ---------------------------------------------------------------------------
+# independent closed-form evaluators (used only at small B)
+# ---------------------------------------------------------------------------
+
+def laguerre_explicit(k: int, alpha: float, t) -> np.ndarray:
+    """L_k^(alpha)(t) by the explicit sum Eq. (associated_laguerre_explicit)."""
+    t = np.asarray(t, dtype=np.float64)
+    total = np.zeros_like(t)
+    for j in range(k + 1):
+        logbin = lgamma(k + alpha + 1) - lgamma(k - j + 1) - lgamma(alpha + j + 1)
+        total = total + ((-1) ** j) * np.exp(logbin - lgamma(j + 1)) * t ** j
+    return total
+
+
+def legendre_rodrigues(l: int, m: int, x) -> np.ndarray:
+    """P_lm(x) by the Rodrigues form of Def 2.1, 0 <= m <= l, with exact
+    integer polynomial coefficients (small l only)."""
+    from math import comb
+    # (x^2 - 1)^l = sum_q C(l,q) (-1)^(l-q) x^(2q)
+    coef = {2 * q: comb(l, q) * (-1) ** (l - q) for q in range(l + 1)}
+    for _ in range(l + m):  # differentiate l+m times
+        coef = {p - 1: c * p for p, c in coef.items() if p > 0}
+    x = np.asarray(x, dtype=np.float64)
+    poly = np.zeros_like(x)
+    for p, c in coef.items():
+        poly = poly + float(c) * x ** p
+    from math import factorial
+    pref = (-1) ** m / (2.0 ** l * factorial(l))
+    return pref * (1 - x * x) ** (m / 2.0) * poly
+
+
+def basis_explicit(n: int, l: int, m: int, r, theta, phi) -> np.ndarray:
+    """H_nlm(r, theta, phi) of Def 1.2 from the closed forms (small B only)."""
+    from math import factorial
+    r = np.asarray(r, dtype=np.float64)
+    am = abs(m)
+    norm_nl = sqrt(2.0 * factorial(n - l - 1) / np.exp(lgamma(n + 0.5)))
+    radial = norm_nl * laguerre_explicit(n - l - 1, l + 0.5, r * r) * r ** l
+    cy = sqrt((2 * l + 1) / (4 * pi) * factorial(l - am) / factorial(l + am))
+    lam = cy * legendre_rodrigues(l, am, np.cos(theta))
+    if m < 0:
+        lam = lam * (-1) ** am
+    return radial * lam * np.exp(1j * m * np.asarray(phi))
+
+
+# ---------------------------------------------------------------------------
+# sample conventions (R5)
+# ---------------------------------------------------------------------------
+
+def physical_to_weighted(f: np.ndarray, B: int) -> np.ndarray:
+    _, t, _ = radial_weights(B)
+    return f * np.exp(-0.5 * t)[:, None, None]
+
+
+def weighted_to_physical(g: np.ndarray, B: int) -> np.ndarray:
+    _, t, _ = radial_weights(B)
+    return g * np.exp(0.5 * t)[:, None, None]
+
+
+# ---------------------------------------------------------------------------
+# transforms
+# ---------------------------------------------------------------------------
+
+def _as_batch_samples(samples: np.ndarray, B: int) -> np.ndarray:
+    s = np.asarray(samples, dtype=np.complex128)
+    return s.reshape(-1, B, 2 * B, 2 * B)
+
+
+def _as_batch_coeffs(coeffs: np.ndarray, B: int) -> np.ndarray:
+    c = np.asarray(coeffs, dtype=np.complex128)
+    return c.reshape(-1, coeff_count(B))
+
+
+def _sphere_coeffs_to_sgl(S: np.ndarray, B: int, what) -> np.ndarray:
+    """Radial stage (DRT of Eq. DRT_matrix), all l:  fhat_nlm =
+    sum_i T_nl(i) what_i S[b, i, l, m].  S is [b, i, l, m+B-1]."""
+    T = radial_table(B)
+    nb = S.shape[0]
+    out = np.zeros((nb, coeff_count(B)), dtype=np.complex128)
+    for l in range(B):
+        Tl = T[l, l:, :] * what[None, :]                 # (B-l, i)
+        X = S[:, :, l, B - 1 - l:B + l]                  # (b, i, 2l+1)
+        Y = np.einsum("ni,bim->bnm", Tl, X)              # (b, B-l, 2l+1)
+        for n in range(l + 1, B + 1):
+            o = omega(n, l, -l)
+            out[:, o:o + 2 * l + 1] = Y[:, n - l - 1, :]
+    return out
+
+
+def forward(samples: np.ndarray, B: int, weights: bool = True) -> np.ndarray:
+    """Forward SGL transform of weighted samples (Thm 3.4), separated form.
+
+    Steps of Eq. (SGL-Sampling-Theorem_rearranged) with the inner spherical
+    sum split as in Eq. (SFFT_rearranged): a phi-DFT of every ring (library
+    FFT), the Legendre sum over j per order m (Eq. DLT), then the radial sum
+    over i per (l, m) (Eq. DRT).  ``weights=False`` drops what_i and beta_j,
+    which is the adjoint of the inverse (Sect. 3.4).
+    """
+    f = _as_batch_samples(samples, B)
+    nb = f.shape[0]
+    _, _, what = radial_weights(B)
+    _, _, beta = sphere_rule(B)
+    if not weights:
+        what = np.ones_like(what)
+        beta = np.ones_like(beta)
+    lam = legendre_table(B)
+    G = np.fft.fft(f, axis=-1)                           # G[b,i,j,(m mod 2B)]
+    S = np.zeros((nb, B, B, 2 * B - 1), dtype=np.complex128)
+    for m in range(-(B - 1), B):
+        am = abs(m)
+        sign = (-1.0) ** am if m < 0 else 1.0
+        A = sign * lam[am, am:, :] * beta[None, :]       # (B-|m|, j)
+        Gm = G[:, :, :, m % (2 * B)]                     # (b, i, j)
+        S[:, :, am:, m + B - 1] = np.einsum("lj,bij->bil", A, Gm)
+    return _sphere_coeffs_to_sgl(S, B, what)
+
+
+def inverse(coeffs: np.ndarray, B: int) -> np.ndarray:
+    """Inverse SGL transform (Algorithm 4 steps): weighted samples
+    ftil(x_psi) = sum fhat_nlm T_nl(i) Lam_lm(theta_j) e^{i m phi_k}."""
+    c = _as_batch_coeffs(coeffs, B)
+    nb = c.shape[0]
+    T = radial_table(B)
+    lam = legendre_table(B)
+    S = np.zeros((nb, B, B, 2 * B - 1), dtype=np.complex128)  # [b,i,l,m]
+    for l in range(B):
+        Tl = T[l, l:, :]                                  # (B-l, i)
+        X = np.zeros((nb, B - l, 2 * l + 1), dtype=np.complex128)
+        for n in range(l + 1, B + 1):
+            o = omega(n, l, -l)
+            X[:, n - l - 1, :] = c[:, o:o + 2 * l + 1]
+        S[:, :, l, B - 1 - l:B + l] = np.einsum("ni,bnm->bim", Tl, X)
+    G = np.zeros((nb, B, 2 * B, 2 * B), dtype=np.complex128)  # [b,i,j,m mod 2B]
+    for m in range(-(B - 1), B):
+        am = abs(m)
+        sign = (-1.0) ** am if m < 0 else 1.0
+        A = sign * lam[am, am:, :]                       # (B-|m|, j)
+        G[:, :, :, m % (2 * B)] = np.einsum("lj,bil->bij", A, S[:, :, am:, m + B - 1])
+    # sum_m G e^{+i m phi_k}; the Nyquist bin stays zero (R6)
+    return np.fft.ifft(G, axis=-1) * (2 * B)
+
+
+def sgl_matrix(B: int) -> np.ndarray:
+    """Htil[omega, psi] = T_nl(i) Lam_lm(theta_j) e^{i m phi_k}, the weighted
+    basis samples (matrix form of Sect. 3.4), from the recurrence tables."""
+    T = radial_table(B)
+    lam = legendre_table(B)
+    _, phi, _ = sphere_rule(B)
+    rows = []
+    for (n, l, m) in nlm_list(B):
+        am = abs(m)
+        lm = lam[am, l, :] * ((-1.0) ** am if m < 0 else 1.0)
+        h = T[l, n - 1, :][:, None, None] * lm[None, :, None] * np.exp(1j * m * phi)[None, None, :]
+        rows.append(h.reshape(-1))
+    return np.array(rows)
+
+
+def forward_direct(samples: np.ndarray, B: int) -> np.ndarray:
+    """Naive forward transform, Algorithm 1: for every coefficient the full
+    triple sum over the grid, O(B^7).  Small B only."""
+    f = _as_batch_samples(samples, B).reshape(-1, 4 * B ** 3)
+    H = sgl_matrix(B)
+    w = sample_weights(B).reshape(-1)
+    return (f * w[None, :]) @ np.conj(H).T
+
+
+def inverse_direct(coeffs: np.ndarray, B: int) -> np.ndarray:
+    """Naive inverse transform, Algorithm 2: every sample summed over all
+    coefficients, O(B^7).  Small B only."""
+    c = _as_batch_coeffs(coeffs, B)
+    H = sgl_matrix(B)
+    return (c @ H).reshape(-1, B, 2 * B, 2 * B)
+
+
+def adjoint_forward(y: np.ndarray, B: int) -> np.ndarray:
+    """Adjoint of the forward map: F_fwd^H y = diag(w_psi) F_inv y (Sect. 3.4)."""
+    return inverse(y, B) * sample_weights(B)[None]
+
+
+def adjoint_inverse(g: np.ndarray, B: int) -> np.ndarray:
+    """Adjoint of the inverse map: F_inv^H g = the forward without weights."""
+    return forward(g, B, weights=False)
