@@ -1,0 +1,195 @@
+/*
+ * sgl.h - C ABI of the GB300 spherical Gauss-Laguerre (SGL) transform library.
+ *
+ * The library computes, for bandlimit B, the forward SGL transform of samples
+ * on the SGL grid (the quadrature of the SGL sampling theorem, Thm 3.4), its
+ * inverse (reconstruction of the samples from the coefficients, Algorithm 2 /
+ * Algorithm 4) and the adjoints of both (matrix form, Sect. 3.4), batched over
+ * many functions.  Every step runs in the library's own CUDA kernels for
+ * sm_103a; nothing falls back to the CPU.
+ *
+ * Grid (the sampling theorem with B radial nodes):
+ *   r_i      i < B    r_i^2 = t_i, the zeros of the generalized Laguerre
+ *                     polynomial L_B^(1/2) (Gauss-Laguerre rule for
+ *                     t^(1/2) e^(-t), Thm 3.3 restated in t = r^2);
+ *   theta_j  j < 2B   (2j+1) pi / (4B)            (Thm 3.1);
+ *   phi_k    k < 2B   k pi / B                    (Thm 3.1).
+ * Weights: what_i = (w_i / 2) exp(t_i) (the exp(r^2)-modified radial weight of
+ * Sect. 3.2, in the symmetric form), beta_j = (pi/B) b_j with b_j of Thm 3.1.
+ *
+ * Sample convention: samples are Gaussian-weighted, ftil(x) = exp(-r^2/2) f(x),
+ * unless the plan was made with SGL_SAMPLES_PHYSICAL (FP64 plans only), in
+ * which case they are the plain values f(x).
+ *
+ * Layouts (index maps of Sect. 3.4, with i < B):
+ *   samples      [batch][i][j][k], complex interleaved (re, im),
+ *                psi = 4B^2 i + 2B j + k within one function;
+ *   coefficients [batch][omega], complex interleaved,
+ *                omega(n,l,m) = n(n-1)(2n-1)/6 + l(l+1) + m, |m| <= l < n <= B,
+ *                Omega = B(B+1)(2B+1)/6 per function.
+ * Element type: double (complex128) for SGL_FP64 plans, float (complex64)
+ * for every other precision.
+ *
+ * Buffers: every data pointer may point to device memory or to host memory
+ * (pinned or pageable); the library asks the CUDA driver which it is.  Host
+ * buffers are staged through plan-owned device memory with copies on the
+ * call's stream, and the call then synchronizes that stream before it
+ * returns.  Device buffers are used in place and the call is asynchronous
+ * (stream-ordered).  Inputs are never modified.  The caller owns all data
+ * buffers; the plan owns its tables and workspace.
+ *
+ * Errors: argument errors are found before any work is queued and returned
+ * as SGL_ERR_ARG.  CUDA launch errors are returned as SGL_ERR_CUDA.  A
+ * device-side error flag (a bounded wait that gave up) is latched in the plan
+ * and returned as SGL_ERR_TIMEOUT by the next call that synchronizes or by
+ * sgl_check().  No call aborts the process.  sgl_last_error() returns a
+ * message for the most recent failure on a plan (or on a failed creation when
+ * passed NULL).
+ *
+ * Concurrency: a plan's workspace is shared by its calls, so calls on one
+ * plan must be ordered (one stream, or synchronized); distinct plans are
+ * independent.
+ */
+#ifndef SGL_H_
+#define SGL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgl_plan_s* sgl_plan_t;   /* opaque; freed by sgl_destroy */
+typedef struct CUstream_st* sgl_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  SGL_OK = 0,
+  SGL_ERR_ARG = 1,          /* invalid argument (size, pointer, enum) */
+  SGL_ERR_ALLOC = 2,        /* device or host allocation failed */
+  SGL_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+  SGL_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+  SGL_ERR_UNSUPPORTED = 5   /* valid but unsupported request (e.g. B too large) */
+} sgl_status;
+
+typedef enum {
+  SGL_FP64 = 0,    /* every stage in double precision on the CUDA cores */
+  SGL_FP32 = 1,    /* every stage in single precision on the CUDA cores */
+  SGL_TF32X3 = 2   /* FP32 FFT; Legendre and radial stages on tcgen05 tensor
+                      cores as three TF32 products (hi*hi + hi*lo + lo*hi)
+                      with FP32 accumulation */
+} sgl_precision;
+
+typedef enum {
+  SGL_SAMPLES_WEIGHTED = 0, /* samples are exp(-r^2/2) f(x) */
+  SGL_SAMPLES_PHYSICAL = 1  /* samples are f(x); SGL_FP64 plans only */
+} sgl_samples;
+
+/* Largest supported bandlimit.  2B must factor as 2^a * q with 2^a <= 16
+ * (the power of two capped at 16) and q <= 16; every B <= 16 and every
+ * multiple of 8 up to 128 qualifies. */
+#define SGL_MAX_B 128
+
+/*
+ * sgl_plan - create a plan for `batch` functions of bandlimit B.
+ *   out      receives the plan (set to NULL on failure).
+ *   B        bandlimit, 1 <= B <= SGL_MAX_B (see above for the factor rule).
+ *   batch    number of functions per call, >= 1.
+ *   prec     an sgl_precision.
+ *   samples  an sgl_samples; SGL_SAMPLES_PHYSICAL requires SGL_FP64.
+ * Builds the FP64 tables on the host (nodes and weights of Thm 3.1 and of the
+ * radial Gauss-Laguerre rule; Legendre functions, Def 2.1 and Eq.
+ * legendre_recurrence; radial functions, Lemma 3.7), uploads them and
+ * allocates the workspace on the current CUDA device.
+ */
+sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples);
+
+/*
+ * sgl_plan_many - one plan for nfn functions with their own bandlimits
+ * B_per_fn[f] (each obeying the rules of sgl_plan), weighted samples.
+ * Samples of function f start at element offset sgl_sample_offset(plan, f)
+ * of the samples buffer and its coefficients at sgl_coeff_offset(plan, f)
+ * (complex elements); functions are packed in order, each in its own
+ * single-function layout.  All functions run in the same kernel launches.
+ */
+sgl_status sgl_plan_many(sgl_plan_t* out, const int* B_per_fn, int nfn, int prec);
+
+/*
+ * sgl_forward - SGL coefficients of the samples (Thm 3.4 quadrature, computed
+ * as Algorithm 3: phi-FFT of every ring (Eq. SFFT_rearranged), a Legendre sum
+ * per order m (Eq. DLT), a radial sum per degree l (Eq. DRT)).
+ *   samples  batch sample arrays (layout above), device or host.
+ *   coeffs   batch coefficient arrays, device or host; fully overwritten.
+ */
+sgl_status sgl_forward(sgl_plan_t plan, const void* samples, void* coeffs, sgl_stream_t stream);
+
+/*
+ * sgl_inverse - samples on the grid of the function with the given
+ * coefficients (Algorithm 4: iDRT per l, Legendre synthesis per m, inverse
+ * phi-FFT; no weights).  The phi-frequency m = B (Nyquist) is zero.
+ */
+sgl_status sgl_inverse(sgl_plan_t plan, const void* coeffs, void* samples, sgl_stream_t stream);
+
+/*
+ * sgl_adjoint - the Hermitian adjoint of one of the two maps (Sect. 3.4):
+ *   of_inverse == 0: adjoint of sgl_forward, coefficients -> samples,
+ *                    out = diag(what_i beta_j) * inverse(in);
+ *   of_inverse != 0: adjoint of sgl_inverse, samples -> coefficients,
+ *                    out = the forward sum with what_i and beta_j dropped.
+ * For SGL_SAMPLES_PHYSICAL plans the adjoint is taken of the physical maps.
+ */
+sgl_status sgl_adjoint(sgl_plan_t plan, int of_inverse, const void* in, void* out, sgl_stream_t stream);
+
+/*
+ * sgl_grid - copy the grid of function `fn` (0 for single-B plans) to host
+ * arrays: r[B], theta[2B], phi[2B], w_r[B] (= what_i), w_theta[2B] (= beta_j).
+ * Any pointer may be NULL to skip that array.
+ */
+sgl_status sgl_grid(sgl_plan_t plan, int fn, double* r, double* theta, double* phi,
+                    double* w_r, double* w_theta);
+
+/* Element counts and offsets (complex elements). */
+int64_t sgl_sample_count(sgl_plan_t plan);           /* whole batch */
+int64_t sgl_coeff_count(sgl_plan_t plan);            /* whole batch */
+int64_t sgl_sample_offset(sgl_plan_t plan, int fn);  /* -1 if fn out of range */
+int64_t sgl_coeff_offset(sgl_plan_t plan, int fn);
+int     sgl_num_functions(sgl_plan_t plan);
+int     sgl_bandlimit(sgl_plan_t plan, int fn);      /* -1 if fn out of range */
+int64_t sgl_workspace_bytes(sgl_plan_t plan);        /* device bytes the plan holds */
+
+/* Number of kernel launches one sgl_forward / sgl_inverse call makes. */
+int sgl_launches_per_call(sgl_plan_t plan);
+
+/* Read the plan's device error flag with a copy on `stream`, synchronize that
+ * stream, and return the latched state: SGL_OK, or SGL_ERR_TIMEOUT once any
+ * bounded device-side wait of the plan has given up. */
+sgl_status sgl_check(sgl_plan_t plan, sgl_stream_t stream);
+
+/*
+ * Stage timing (profiling aid).  While enabled, every stage launch of the
+ * plan is bracketed by CUDA events recorded on the call's stream; sgl_stage_times
+ * synchronizes on the last event and returns, for each of the SGL_NUM_STAGES
+ * stages, the summed device milliseconds and the number of launches since
+ * profiling was enabled (arrays of SGL_NUM_STAGES entries, either may be NULL).
+ * Stage names: sgl_stage_name(i).  Disabling clears the sums.
+ */
+#define SGL_NUM_STAGES 6
+sgl_status  sgl_set_profiling(sgl_plan_t plan, int enable);
+sgl_status  sgl_stage_times(sgl_plan_t plan, double* ms, int64_t* launches);
+const char* sgl_stage_name(int stage);
+
+/* Message for the last failure on `plan` (or of plan creation when NULL).
+ * The string stays valid until the next call on the same plan. */
+const char* sgl_last_error(sgl_plan_t plan);
+
+/* Release the plan, its tables and its workspace.  NULL is ignored. */
+void sgl_destroy(sgl_plan_t plan);
+
+/* Library version string. */
+const char* sgl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGL_H_ */

@@ -1,0 +1,511 @@
+// C ABI of the SGL transform library: plans, dispatch, host-buffer staging.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sgl_internal.h"
+
+namespace sgl {
+size_t fft_smem_for(int prec, int n1, int n2, int B);
+int fft_pairs_per_cta(int prec, int B);
+void gemm_tile_dims(int& tm, int& tn, int& tk);
+cudaError_t tc_prepare(Plan& P);   // tensor-core tables and schedules (tc_gemm.cu)
+void tc_release(Plan& P);
+int tc_launches(const Plan& P);
+}  // namespace sgl
+
+using namespace sgl;
+
+static std::string g_create_error;
+
+static sgl_status fail(Plan* P, sgl_status st, const std::string& msg) {
+  if (P) P->err = msg; else g_create_error = msg;
+  return st;
+}
+
+static sgl_status cuda_fail(Plan* P, cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(P, SGL_ERR_CUDA, msg);
+}
+
+template <typename T>
+static cudaError_t dev_upload(Plan& P, T** dst, const std::vector<T>& src) {
+  if (src.empty()) { *dst = nullptr; return cudaSuccess; }
+  cudaError_t e = cudaMalloc((void**)dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  P.bytes += src.size() * sizeof(T);
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+static void clear_profile(Plan& P) {
+  for (int st = 0; st < SGL_NUM_STAGES; ++st) {
+    for (auto& pr : P.prof_ev[st]) {
+      P.ev_pool.push_back(pr.first);
+      P.ev_pool.push_back(pr.second);
+    }
+    P.prof_ev[st].clear();
+  }
+}
+
+static void release(Plan* P) {
+  if (!P) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(P->device);
+  clear_profile(*P);
+  for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
+  tc_release(*P);
+  void* ptrs[] = {P->d_tab, P->d_tab_lo, P->d_w1, P->d_w2, P->d_stage_in, P->d_stage_out, P->d_segs,
+                  P->d_fn_samp, P->d_fn_coef, P->d_si_rows, P->d_err, P->leg_fwd.d_tiles, P->rad_fwd.d_tiles,
+                  P->rad_inv.d_tiles, P->leg_inv.d_tiles, P->d_fft_fwd, P->d_fft_inv};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  cudaSetDevice(cur);
+  delete P;
+}
+
+template <typename real>
+static void pack_tables(const Plan& P, std::vector<real>& tab) {
+  tab.assign(P.tab_elems, real(0));
+  for (size_t s = 0; s < P.segs.size(); ++s) {
+    const SegDesc& sg = P.segs[s];
+    const HostTables& H = P.tables[s];
+    const int B = sg.B;
+    real* misc = tab.data() + sg.tab_misc;
+    for (int i = 0; i < B; ++i) {
+      misc[i] = (real)H.what[i];
+      misc[B + i] = (real)exp(-0.5 * H.t[i]);
+      misc[2 * B + i] = (real)exp(0.5 * H.t[i]);
+    }
+    for (int j = 0; j < 2 * B; ++j) misc[3 * B + j] = (real)H.beta[j];
+    for (int k = 0; k < 2 * B; ++k) {
+      // e^{-2 pi i k / 2B}
+      long double ang = 3.141592653589793238462643383279502884L * (long double)k / (long double)B;
+      misc[5 * B + 2 * k] = (real)cosl(ang);
+      misc[5 * B + 2 * k + 1] = (real)(-sinl(ang));
+    }
+    for (int m = 0; m < B; ++m)
+      for (int p = 0; p < 2; ++p) {
+        const int64_t r0 = leg_rows_before(B, m, p);
+        for (int q = 0; q < n_par(B, m, p); ++q) {
+          const int l = m + p + 2 * q;
+          for (int j = 0; j < B; ++j) {
+            const double v = H.lam[((size_t)m * B + l) * B + j];
+            tab[sg.tab_leg_f + (r0 + q) * B + j] = (real)(H.beta[j] * v);
+            tab[sg.tab_leg_i + (r0 + q) * B + j] = (real)v;
+          }
+        }
+      }
+    for (int l = 0; l < B; ++l) {
+      const int64_t r0 = rad_rows_before(B, l);
+      for (int q = 0; q < B - l; ++q) {
+        const int n = l + 1 + q;
+        for (int i = 0; i < B; ++i) {
+          const double v = H.T[((size_t)l * B + (n - 1)) * B + i];
+          tab[sg.tab_rad_f + (r0 + q) * B + i] = (real)(H.what[i] * v);
+          tab[sg.tab_rad_i + (r0 + q) * B + i] = (real)v;
+        }
+      }
+    }
+  }
+}
+
+static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) {
+  cudaGetDevice(&P->device);
+  P->nfn = (int)Bs.size();
+  P->uniform = uniform;
+  P->fn_B = Bs;
+  // offsets in user order
+  int64_t so = 0, co = 0;
+  for (int B : Bs) {
+    P->fn_samp_off.push_back(so);
+    P->fn_coef_off.push_back(co);
+    so += sample_count(B);
+    co += coeff_count(B);
+    P->maxB = std::max(P->maxB, B);
+  }
+  P->n_samples = so;
+  P->n_coeffs = co;
+  // segments: group by bandlimit, largest first
+  std::map<int, std::vector<int>, std::greater<int>> by_B;
+  for (int f = 0; f < P->nfn; ++f) by_B[Bs[f]].push_back(f);
+  std::vector<int64_t> fn_samp, fn_coef, si_rows;
+  int64_t w1 = 0, w2 = 0, tab = 0;
+  for (auto& kv : by_B) {
+    SegDesc sg;
+    memset(&sg, 0, sizeof(sg));
+    sg.B = kv.first;
+    sg.NB = (int)kv.second.size();
+    sg.n1 = fft_n1(2 * sg.B);
+    sg.n2 = 2 * sg.B / sg.n1;
+    sg.fn0 = (int)fn_samp.size();
+    for (int f : kv.second) {
+      fn_samp.push_back(P->fn_samp_off[f]);
+      fn_coef.push_back(P->fn_coef_off[f]);
+      P->seg_fn.push_back(f);
+    }
+    sg.w1_off = w1;
+    sg.w2_off = w2;
+    w1 += w1_size(sg.B, sg.NB);
+    w2 += w2_size(sg.B, sg.NB);
+    sg.tab_misc = tab;
+    tab += misc_size(sg.B);
+    sg.tab_leg_f = tab;
+    tab += leg_table_size(sg.B);
+    sg.tab_leg_i = tab;
+    tab += leg_table_size(sg.B);
+    sg.tab_rad_f = tab;
+    tab += rad_table_size(sg.B);
+    sg.tab_rad_i = tab;
+    tab += rad_table_size(sg.B);
+    tab = (tab + 31) / 32 * 32;
+    sg.si_rows = (int64_t)si_rows.size();
+    for (int mi = 0; mi < 2 * sg.B - 1; ++mi)
+      for (int p = 0; p < 2; ++p) si_rows.push_back(si_rows_before(sg.B, mi, p));
+    HostTables H;
+    std::string msg;
+    if (!build_tables(sg.B, H, msg)) return fail(P, SGL_ERR_ARG, "table generation: " + msg);
+    P->tables.push_back(std::move(H));
+    P->segs.push_back(sg);
+  }
+  P->w1_elems = w1;
+  P->w2_elems = w2;
+  P->tab_elems = tab;
+
+  const size_t rsz = (P->prec == SGL_FP64) ? sizeof(double) : sizeof(float);
+  cudaError_t e;
+  // tables
+  if (P->prec == SGL_FP64) {
+    std::vector<double> t;
+    pack_tables<double>(*P, t);
+    e = dev_upload(*P, (double**)&P->d_tab, t);
+  } else {
+    std::vector<float> t;
+    pack_tables<float>(*P, t);
+    e = dev_upload(*P, (float**)&P->d_tab, t);
+  }
+  if (e != cudaSuccess) return cuda_fail(P, e, "table upload");
+  e = dev_upload(*P, &P->d_segs, P->segs);
+  if (e != cudaSuccess) return cuda_fail(P, e, "segment upload");
+  e = dev_upload(*P, &P->d_fn_samp, fn_samp);
+  if (e != cudaSuccess) return cuda_fail(P, e, "offset upload");
+  e = dev_upload(*P, &P->d_fn_coef, fn_coef);
+  if (e != cudaSuccess) return cuda_fail(P, e, "offset upload");
+  e = dev_upload(*P, &P->d_si_rows, si_rows);
+  if (e != cudaSuccess) return cuda_fail(P, e, "offset upload");
+  // workspaces
+  e = cudaMalloc(&P->d_w1, w1 * rsz);
+  if (e != cudaSuccess) return fail(P, SGL_ERR_ALLOC, "workspace allocation failed");
+  P->bytes += w1 * rsz;
+  e = cudaMalloc(&P->d_w2, w2 * rsz);
+  if (e != cudaSuccess) return fail(P, SGL_ERR_ALLOC, "workspace allocation failed");
+  P->bytes += w2 * rsz;
+  e = cudaMalloc((void**)&P->d_err, sizeof(int));
+  if (e != cudaSuccess) return fail(P, SGL_ERR_ALLOC, "allocation failed");
+  cudaMemset(P->d_err, 0, sizeof(int));
+
+  // SIMT GEMM schedules
+  int TM, TN, TK;
+  gemm_tile_dims(TM, TN, TK);
+  std::vector<int4> lf, rf, ri, li;
+  for (size_t s = 0; s < P->segs.size(); ++s) {
+    const SegDesc& sg = P->segs[s];
+    const int B = sg.B, NB = sg.NB;
+    for (int g = 0; g < 2 * (2 * B - 1); ++g) {
+      const int m = (g >> 1) - (B - 1);
+      const int N = n_par(B, m < 0 ? -m : m, g & 1);
+      const int rows = NB * 2 * B;
+      for (int r0 = 0; r0 < rows; r0 += TM)
+        for (int c0 = 0; c0 < N; c0 += TN) lf.push_back(make_int4((int)s, g, r0, c0));
+    }
+    for (int l = 0; l < B; ++l) {
+      const int rows = NB * (2 * l + 1) * 2;
+      for (int r0 = 0; r0 < rows; r0 += TM) {
+        for (int c0 = 0; c0 < B - l; c0 += TN) rf.push_back(make_int4((int)s, l, r0, c0));
+        for (int c0 = 0; c0 < B; c0 += TN) ri.push_back(make_int4((int)s, l, r0, c0));
+      }
+    }
+    for (int mi = 0; mi < 2 * B - 1; ++mi) {
+      const int rows = NB * 2 * B;
+      for (int r0 = 0; r0 < rows; r0 += TM)
+        for (int c0 = 0; c0 < B; c0 += TN) li.push_back(make_int4((int)s, mi, r0, c0));
+    }
+  }
+  struct {
+    GemmSched* s;
+    std::vector<int4>* v;
+  } scheds[] = {{&P->leg_fwd, &lf}, {&P->rad_fwd, &rf}, {&P->rad_inv, &ri}, {&P->leg_inv, &li}};
+  for (auto& x : scheds) {
+    x.s->ntiles = (int)x.v->size();
+    e = dev_upload(*P, &x.s->d_tiles, *x.v);
+    if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
+  }
+  // FFT CTA lists (segment order)
+  std::vector<int4> ff;
+  for (size_t s = 0; s < P->segs.size(); ++s) {
+    const SegDesc& sg = P->segs[s];
+    const int JP = fft_pairs_per_cta(P->prec, sg.B);
+    for (int sh = 0; sh < sg.NB * sg.B; ++sh)
+      for (int j0 = 0; j0 < sg.B; j0 += JP) ff.push_back(make_int4((int)s, sh, j0, 0));
+  }
+  P->n_fft_fwd = P->n_fft_inv = (int)ff.size();
+  e = dev_upload(*P, &P->d_fft_fwd, ff);
+  if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
+  P->d_fft_inv = nullptr;
+  e = dev_upload(*P, &P->d_fft_inv, ff);
+  if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
+  for (const SegDesc& sg : P->segs) {
+    size_t smem = fft_smem_for(P->prec, sg.n1, sg.n2, sg.B);
+    if (smem > 227 * 1024) return fail(P, SGL_ERR_UNSUPPORTED, "FFT tile exceeds shared memory");
+  }
+  if (P->prec == SGL_TF32X3) {
+    e = tc_prepare(*P);
+    if (e != cudaSuccess) return cuda_fail(P, e, "tensor-core preparation");
+  }
+  P->launches_per_call = (int)P->segs.size() + 2;
+  if (P->prec == SGL_TF32X3) P->launches_per_call = (int)P->segs.size() + tc_launches(*P);
+  return SGL_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static size_t complex_bytes(const Plan& P) { return P.prec == SGL_FP64 ? 16 : 8; }
+
+static sgl_status ensure_stage(Plan& P, void** buf, size_t* have, size_t need) {
+  if (*have >= need) return SGL_OK;
+  if (*buf) {
+    cudaFree(*buf);
+    P.bytes -= *have;
+  }
+  *buf = nullptr;
+  *have = 0;
+  if (cudaMalloc(buf, need) != cudaSuccess) return fail(&P, SGL_ERR_ALLOC, "staging allocation failed");
+  *have = need;
+  P.bytes += need;
+  return SGL_OK;
+}
+
+// Runs fwd (is_fwd) or inv with in/out that may be host or device memory.
+static sgl_status execute(Plan* P, bool is_fwd, bool weights, const void* in, void* out, sgl_stream_t stream) {
+  if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
+  if (!in || !out) return fail(P, SGL_ERR_ARG, "null data pointer");
+  if (P->latched != SGL_OK) return (sgl_status)P->latched;
+  cudaStream_t s = (cudaStream_t)stream;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != P->device) cudaSetDevice(P->device);
+  const size_t cb = complex_bytes(*P);
+  const size_t in_bytes = (is_fwd ? P->n_samples : P->n_coeffs) * cb;
+  const size_t out_bytes = (is_fwd ? P->n_coeffs : P->n_samples) * cb;
+  const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
+  const void* din = in;
+  void* dout = out;
+  sgl_status st = SGL_OK;
+  cudaError_t e = cudaSuccess;
+  if (!in_dev) {
+    st = ensure_stage(*P, &P->d_stage_in, &P->stage_in_bytes, in_bytes);
+    if (st != SGL_OK) goto done;
+    e = cudaMemcpyAsync(P->d_stage_in, in, in_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { st = cuda_fail(P, e, "host-to-device copy"); goto done; }
+    din = P->d_stage_in;
+  }
+  if (!out_dev) {
+    st = ensure_stage(*P, &P->d_stage_out, &P->stage_out_bytes, out_bytes);
+    if (st != SGL_OK) goto done;
+    dout = P->d_stage_out;
+  }
+  e = is_fwd ? run_forward(*P, din, dout, s, weights) : run_inverse(*P, din, dout, s, weights);
+  if (e != cudaSuccess) { st = cuda_fail(P, e, is_fwd ? "forward launch" : "inverse launch"); goto done; }
+  if (!out_dev) {
+    e = cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) { st = cuda_fail(P, e, "device-to-host copy"); goto done; }
+  }
+  if (!in_dev || !out_dev) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { st = cuda_fail(P, e, "stream synchronize"); goto done; }
+  }
+done:
+  if (cur != P->device) cudaSetDevice(cur);
+  return st;
+}
+
+extern "C" {
+
+sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples) {
+  if (!out) return fail(nullptr, SGL_ERR_ARG, "null output pointer");
+  *out = nullptr;
+  if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
+  if (batch < 1) return fail(nullptr, SGL_ERR_ARG, "batch must be >= 1");
+  if (prec < SGL_FP64 || prec > SGL_TF32X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
+  if (samples != SGL_SAMPLES_WEIGHTED && samples != SGL_SAMPLES_PHYSICAL)
+    return fail(nullptr, SGL_ERR_ARG, "unknown sample convention");
+  if (samples == SGL_SAMPLES_PHYSICAL && prec != SGL_FP64)
+    return fail(nullptr, SGL_ERR_ARG, "physical samples need an FP64 plan");
+  if (!bandlimit_supported(B)) return fail(nullptr, SGL_ERR_UNSUPPORTED, "unsupported bandlimit");
+  Plan* P = new Plan();
+  P->prec = prec;
+  P->samples = samples;
+  std::vector<int> Bs(batch, B);
+  sgl_status st = build_plan(P, Bs, true);
+  if (st != SGL_OK) {
+    g_create_error = P->err;
+    release(P);
+    return st;
+  }
+  *out = (sgl_plan_t)P;
+  return SGL_OK;
+}
+
+sgl_status sgl_plan_many(sgl_plan_t* out, const int* B_per_fn, int nfn, int prec) {
+  if (!out) return fail(nullptr, SGL_ERR_ARG, "null output pointer");
+  *out = nullptr;
+  if (!B_per_fn || nfn < 1) return fail(nullptr, SGL_ERR_ARG, "need at least one function");
+  if (prec < SGL_FP64 || prec > SGL_TF32X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
+  std::vector<int> Bs(B_per_fn, B_per_fn + nfn);
+  for (int B : Bs) {
+    if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
+    if (!bandlimit_supported(B)) return fail(nullptr, SGL_ERR_UNSUPPORTED, "unsupported bandlimit");
+  }
+  Plan* P = new Plan();
+  P->prec = prec;
+  P->samples = SGL_SAMPLES_WEIGHTED;
+  bool uni = true;
+  for (int B : Bs) uni = uni && (B == Bs[0]);
+  sgl_status st = build_plan(P, Bs, uni);
+  if (st != SGL_OK) {
+    g_create_error = P->err;
+    release(P);
+    return st;
+  }
+  *out = (sgl_plan_t)P;
+  return SGL_OK;
+}
+
+sgl_status sgl_forward(sgl_plan_t plan, const void* samples, void* coeffs, sgl_stream_t stream) {
+  return execute((Plan*)plan, true, true, samples, coeffs, stream);
+}
+
+sgl_status sgl_inverse(sgl_plan_t plan, const void* coeffs, void* samples, sgl_stream_t stream) {
+  return execute((Plan*)plan, false, false, coeffs, samples, stream);
+}
+
+sgl_status sgl_adjoint(sgl_plan_t plan, int of_inverse, const void* in, void* out, sgl_stream_t stream) {
+  // adjoint of the forward map: weighted inverse pipeline; adjoint of the
+  // inverse map: forward pipeline without weights
+  if (of_inverse) return execute((Plan*)plan, true, false, in, out, stream);
+  return execute((Plan*)plan, false, true, in, out, stream);
+}
+
+sgl_status sgl_grid(sgl_plan_t plan, int fn, double* r, double* theta, double* phi, double* w_r,
+                    double* w_theta) {
+  Plan* P = (Plan*)plan;
+  if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
+  if (fn < 0 || fn >= P->nfn) return fail(P, SGL_ERR_ARG, "function index out of range");
+  const int B = P->fn_B[fn];
+  size_t seg = 0;
+  while (P->segs[seg].B != B) ++seg;
+  const HostTables& H = P->tables[seg];
+  if (r) memcpy(r, H.r.data(), B * sizeof(double));
+  if (theta) memcpy(theta, H.theta.data(), 2 * B * sizeof(double));
+  if (phi) memcpy(phi, H.phi.data(), 2 * B * sizeof(double));
+  if (w_r) memcpy(w_r, H.what.data(), B * sizeof(double));
+  if (w_theta) memcpy(w_theta, H.beta.data(), 2 * B * sizeof(double));
+  return SGL_OK;
+}
+
+int64_t sgl_sample_count(sgl_plan_t plan) { return plan ? ((Plan*)plan)->n_samples : -1; }
+int64_t sgl_coeff_count(sgl_plan_t plan) { return plan ? ((Plan*)plan)->n_coeffs : -1; }
+
+int64_t sgl_sample_offset(sgl_plan_t plan, int fn) {
+  Plan* P = (Plan*)plan;
+  if (!P || fn < 0 || fn >= P->nfn) return -1;
+  return P->fn_samp_off[fn];
+}
+
+int64_t sgl_coeff_offset(sgl_plan_t plan, int fn) {
+  Plan* P = (Plan*)plan;
+  if (!P || fn < 0 || fn >= P->nfn) return -1;
+  return P->fn_coef_off[fn];
+}
+
+int sgl_num_functions(sgl_plan_t plan) { return plan ? ((Plan*)plan)->nfn : -1; }
+
+int sgl_bandlimit(sgl_plan_t plan, int fn) {
+  Plan* P = (Plan*)plan;
+  if (!P || fn < 0 || fn >= P->nfn) return -1;
+  return P->fn_B[fn];
+}
+
+int64_t sgl_workspace_bytes(sgl_plan_t plan) { return plan ? ((Plan*)plan)->bytes : -1; }
+
+int sgl_launches_per_call(sgl_plan_t plan) { return plan ? ((Plan*)plan)->launches_per_call : -1; }
+
+sgl_status sgl_check(sgl_plan_t plan, sgl_stream_t stream) {
+  Plan* P = (Plan*)plan;
+  if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(P, e, "error flag read");
+  if (flag != 0) {
+    P->latched = SGL_ERR_TIMEOUT;
+    P->err = "a bounded device-side wait gave up";
+  }
+  return (sgl_status)P->latched;
+}
+
+sgl_status sgl_set_profiling(sgl_plan_t plan, int enable) {
+  Plan* P = (Plan*)plan;
+  if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
+  if (!enable) clear_profile(*P);
+  P->profiling = enable != 0;
+  return SGL_OK;
+}
+
+sgl_status sgl_stage_times(sgl_plan_t plan, double* ms, int64_t* launches) {
+  Plan* P = (Plan*)plan;
+  if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
+  for (int st = 0; st < SGL_NUM_STAGES; ++st) {
+    double sum = 0.0;
+    for (auto& pr : P->prof_ev[st]) {
+      cudaError_t e = cudaEventSynchronize(pr.second);
+      if (e != cudaSuccess) return cuda_fail(P, e, "profiling event");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, pr.first, pr.second);
+      sum += t;
+    }
+    if (ms) ms[st] = sum;
+    if (launches) launches[st] = (int64_t)P->prof_ev[st].size();
+  }
+  return SGL_OK;
+}
+
+const char* sgl_stage_name(int stage) {
+  static const char* names[SGL_NUM_STAGES] = {"fft_forward", "legendre_forward", "radial_forward",
+                                              "radial_inverse", "legendre_inverse", "fft_inverse"};
+  if (stage < 0 || stage >= SGL_NUM_STAGES) return "";
+  return names[stage];
+}
+
+const char* sgl_last_error(sgl_plan_t plan) {
+  if (!plan) return g_create_error.c_str();
+  return ((Plan*)plan)->err.c_str();
+}
+
+void sgl_destroy(sgl_plan_t plan) { release((Plan*)plan); }
+
+const char* sgl_version(void) { return "sgl-gb300 0.1"; }
+
+}  // extern "C"

@@ -1,0 +1,689 @@
+// CUDA kernels of the SGL transform for sm_103a: the phi-FFT of every ring
+// and the Legendre / radial contractions on the CUDA cores (FP64 and FP32).
+//
+// Forward (Algorithm 3):
+//   fft_fwd   G[i][j][m] = sum_k ftil[i][j][k] e^{-i m phi_k}     (Eq. SFFT_rearranged, inner sum)
+//             written as E = G_j + G_{2B-1-j}, O = G_j - G_{2B-1-j}, j < B,
+//             using Lambda_lm(pi - theta) = (-1)^{l+m} Lambda_lm(theta)
+//   gemm<LEG_F> S[l][m][i] = sum_j' beta_j' Lambda_lm(theta_j') {E|O}[m][j'][i]  (Eq. DLT)
+//   gemm<RAD_F> fhat[n,l,m] = sum_i what_i T_nl(i) S[l][m][i]                  (Eq. DRT_matrix)
+// Inverse (Algorithm 4): gemm<RAD_I> (iDRT, R_l^T), gemm<LEG_I> (Legendre
+// synthesis, Eq. iSFFT_rearranged inner sum), fft_inv (inverse phi-FFT).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sgl_internal.h"
+
+namespace sgl {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+template <typename real>
+struct cx {
+  real x, y;
+};
+
+template <typename real>
+__device__ __forceinline__ cx<real> cadd(cx<real> a, cx<real> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename real>
+__device__ __forceinline__ cx<real> csub(cx<real> a, cx<real> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename real>
+__device__ __forceinline__ cx<real> cmul(cx<real> a, cx<real> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// twiddle e^{-2 pi i k/N} (INV: conjugate) from a table of N entries
+template <typename real, bool INV>
+__device__ __forceinline__ cx<real> tw(const real* __restrict__ wre, const real* __restrict__ wim, int k) {
+  return {wre[k], INV ? -wim[k] : wim[k]};
+}
+
+// In-register radix-2 DIT FFT of compile-time size N (power of two <= 16);
+// input and output in natural order.  Twiddle of size-len stage index q:
+// W_N_total^{q * (N_total/len)} = table[q * wstep * (N/len)].
+template <typename real, int N, bool INV>
+__device__ __forceinline__ void fft_reg(cx<real>* v, const real* wre, const real* wim, int wstep) {
+  if constexpr (N > 1) {
+    constexpr int LOG = (N == 2) ? 1 : (N == 4) ? 2 : (N == 8) ? 3 : 4;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      int j = 0;
+#pragma unroll
+      for (int b = 0; b < LOG; ++b) j |= ((i >> b) & 1) << (LOG - 1 - b);
+      if (i < j) {
+        cx<real> t = v[i];
+        v[i] = v[j];
+        v[j] = t;
+      }
+    }
+#pragma unroll
+    for (int len = 2; len <= N; len <<= 1) {
+      const int half = len >> 1;
+#pragma unroll
+      for (int start = 0; start < N; start += len) {
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+          cx<real> w = tw<real, INV>(wre, wim, q * (N / len) * wstep);
+          cx<real> a = v[start + q];
+          cx<real> b = cmul(v[start + q + half], w);
+          v[start + q] = cadd(a, b);
+          v[start + q + half] = csub(a, b);
+        }
+      }
+    }
+  }
+}
+
+// Direct DFT of runtime size n <= 16 (any n), input u, output v.
+template <typename real, bool INV>
+__device__ __forceinline__ void dft_reg(const cx<real>* u, cx<real>* v, int n, const real* wre,
+                                        const real* wim, int wstep) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    if (k < n) {
+      cx<real> acc = {0, 0};
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (q < n) {
+          int idx = (q * k) % n;
+          cx<real> w = tw<real, INV>(wre, wim, idx * wstep);
+          cx<real> p = cmul(u[q], w);
+          acc = cadd(acc, p);
+        }
+      }
+      v[k] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// phi-FFT kernels
+// ---------------------------------------------------------------------------
+// Shared memory per CTA: R = 2*JP rings, each stored as separate real and
+// imaginary planes of n1 rows x (n2+1) columns (padded), ring pitch odd.
+struct FftArgs {
+  const SegDesc* segs;
+  const int64_t* fn_samp;
+  const int4* ctas;      // (seg, shell, j0, 0)
+  const void* tab;       // misc tables in the real type
+  const void* in;
+  void* out;
+  void* w1;
+  int JP;                // ring pairs per CTA
+  int mode;              // fwd: 0 none, 1 *exp(-t/2), 2 *exp(+t/2);
+                         // inv: 0 none, 1 *exp(+t/2), 2 *what*beta, 3 *what*beta*exp(-t/2)
+};
+
+__host__ __device__ inline int ring_pitch(int n1, int n2) {
+  int p = n1 * (n2 + 1);
+  return (p % 2 == 0) ? p + 1 : p;
+}
+
+template <typename real, int N1, int N2C, bool INV>
+__device__ __forceinline__ void fft_rings(real* sre, real* sim, const real* wre, const real* wim, int R, int n2,
+                                          int N, int pitch) {
+  const int n1 = N1;
+  const int n2p = n2 + 1;
+  // step A: N1-point DFT over n1 for every (ring, n2), then twiddle W_N^{n2 k1}
+  for (int w = threadIdx.x; w < R * n2; w += blockDim.x) {
+    const int r = w / n2, c2 = w - r * n2;
+    real* pr = sre + r * pitch + c2;
+    real* pi = sim + r * pitch + c2;
+    cx<real> v[N1];
+#pragma unroll
+    for (int a = 0; a < N1; ++a) v[a] = {pr[a * n2p], pi[a * n2p]};
+    fft_reg<real, N1, INV>(v, wre, wim, N / N1);
+#pragma unroll
+    for (int a = 1; a < N1; ++a) v[a] = cmul(v[a], tw<real, INV>(wre, wim, c2 * a));
+#pragma unroll
+    for (int a = 0; a < N1; ++a) {
+      pr[a * n2p] = v[a].x;
+      pi[a * n2p] = v[a].y;
+    }
+  }
+  __syncthreads();
+  // step B: n2-point DFT over n2 for every (ring, k1)
+  for (int w = threadIdx.x; w < R * n1; w += blockDim.x) {
+    const int r = w / n1, k1 = w - r * n1;
+    real* pr = sre + r * pitch + k1 * n2p;
+    real* pi = sim + r * pitch + k1 * n2p;
+    if constexpr (N2C > 0) {
+      cx<real> v[N2C];
+#pragma unroll
+      for (int a = 0; a < N2C; ++a) v[a] = {pr[a], pi[a]};
+      fft_reg<real, N2C, INV>(v, wre, wim, N / N2C);
+#pragma unroll
+      for (int a = 0; a < N2C; ++a) {
+        pr[a] = v[a].x;
+        pi[a] = v[a].y;
+      }
+    } else {
+      cx<real> u[16], v[16];
+#pragma unroll
+      for (int a = 0; a < 16; ++a)
+        if (a < n2) u[a] = {pr[a], pi[a]};
+      dft_reg<real, INV>(u, v, n2, wre, wim, N / n2);
+#pragma unroll
+      for (int a = 0; a < 16; ++a)
+        if (a < n2) {
+          pr[a] = v[a].x;
+          pi[a] = v[a].y;
+        }
+    }
+  }
+  __syncthreads();
+}
+
+// Forward: rings j0+q and 2B-1-(j0+q) of shell (b, i) -> E/O spectra.
+template <typename real, int N1, int N2C>
+__global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int4 cta = a.ctas[blockIdx.x];
+  const SegDesc sg = a.segs[cta.x];
+  const int B = sg.B, N = 2 * B, NB = sg.NB;
+  const int n2 = sg.n2;
+  const int shell = cta.y, j0 = cta.z;
+  const int b = shell / B, i = shell - b * B;
+  const int JP = min(a.JP, B - j0);
+  const int R = 2 * JP;
+  const int pitch = ring_pitch(N1, n2);
+  real* wre = reinterpret_cast<real*>(smem_raw);
+  real* wim = wre + N;
+  real* sre = wim + N;
+  real* sim = sre + 2 * a.JP * pitch;
+  const real* misc = reinterpret_cast<const real*>(a.tab) + sg.tab_misc;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    wre[k] = misc[5 * B + 2 * k];
+    wim[k] = misc[5 * B + 2 * k + 1];
+  }
+  real scale = 1;
+  if (a.mode == 1) scale = misc[B + i];
+  if (a.mode == 2) scale = misc[2 * B + i];
+  const cx<real>* in = reinterpret_cast<const cx<real>*>(a.in) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
+  for (int e = threadIdx.x; e < R * N; e += blockDim.x) {
+    const int r = e / N, k = e - r * N;
+    const int q = r >> 1;
+    const int j = (r & 1) ? (N - 1 - (j0 + q)) : (j0 + q);
+    cx<real> v = in[(int64_t)j * N + k];
+    const int c1 = k / n2, c2 = k - c1 * n2;
+    sre[r * pitch + c1 * (n2 + 1) + c2] = v.x * scale;
+    sim[r * pitch + c1 * (n2 + 1) + c2] = v.y * scale;
+  }
+  __syncthreads();
+  fft_rings<real, N1, N2C, false>(sre, sim, wre, wim, R, n2, N, pitch);
+  // E/O spectra for m in (-B, B): spectral index k = m mod N at slot (k % n1, k / n1)
+  real* w1 = reinterpret_cast<real*>(a.w1) + sg.w1_off;
+  const int total = (2 * B - 1) * 4 * JP;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int q = e % JP;
+    const int rest = e / JP;
+    const int c = rest & 1, p = (rest >> 1) & 1, m_idx = rest >> 2;
+    const int m = m_idx - (B - 1);
+    const int k = m >= 0 ? m : N + m;
+    const int slot = (k % N1) * (n2 + 1) + k / N1;
+    const real* plane = c ? sim : sre;
+    const real g0 = plane[(2 * q) * pitch + slot];
+    const real g1 = plane[(2 * q + 1) * pitch + slot];
+    const real v = p ? (g0 - g1) : (g0 + g1);
+    w1[(((((int64_t)m_idx * 2 + p) * NB + b) * 2 + c) * B + i) * B + j0 + q] = v;
+  }
+}
+
+// Inverse: G[m][b][c][i][j] of rings j0..j0+JP-1 and their mirrors -> samples.
+template <typename real, int N1, int N2C>
+__global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int4 cta = a.ctas[blockIdx.x];
+  const SegDesc sg = a.segs[cta.x];
+  const int B = sg.B, N = 2 * B, NB = sg.NB;
+  const int n2 = sg.n2;
+  const int shell = cta.y, j0 = cta.z;
+  const int b = shell / B, i = shell - b * B;
+  const int JP = min(a.JP, B - j0);
+  const int R = 2 * JP;
+  const int pitch = ring_pitch(N1, n2);
+  real* wre = reinterpret_cast<real*>(smem_raw);
+  real* wim = wre + N;
+  real* sre = wim + N;
+  real* sim = sre + 2 * a.JP * pitch;
+  const real* misc = reinterpret_cast<const real*>(a.tab) + sg.tab_misc;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    wre[k] = misc[5 * B + 2 * k];
+    wim[k] = misc[5 * B + 2 * k + 1];
+  }
+  // ring r: r < JP -> j = j0 + r; r >= JP -> j = N - j0 - 2*JP + r (mirror run)
+  const real* g = reinterpret_cast<const real*>(a.w1) + sg.w1_off;
+  // Nyquist bin (k = B) is zero
+  for (int e = threadIdx.x; e < 2 * R; e += blockDim.x) {
+    const int r = e >> 1;
+    const int slot = (B / n2) * (n2 + 1) + (B % n2);
+    ((e & 1) ? sim : sre)[r * pitch + slot] = 0;
+  }
+  const int total = (2 * B - 1) * 2 * R;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int r = e % R;
+    const int rest = e / R;
+    const int c = rest & 1, m_idx = rest >> 1;
+    const int m = m_idx - (B - 1);
+    const int k = m >= 0 ? m : N + m;
+    const int j = r < JP ? j0 + r : N - j0 - 2 * JP + r;
+    const real v = g[((((int64_t)m_idx * NB + b) * 2 + c) * B + i) * N + j];
+    const int c1 = k / n2, c2 = k - c1 * n2;
+    (c ? sim : sre)[r * pitch + c1 * (n2 + 1) + c2] = v;
+  }
+  __syncthreads();
+  fft_rings<real, N1, N2C, true>(sre, sim, wre, wim, R, n2, N, pitch);
+  cx<real>* out = reinterpret_cast<cx<real>*>(a.out) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
+  real si = 1;
+  if (a.mode == 1) si = misc[2 * B + i];
+  if (a.mode == 2) si = misc[i];
+  if (a.mode == 3) si = misc[i] * misc[B + i];
+  for (int e = threadIdx.x; e < R * N; e += blockDim.x) {
+    const int r = e / N, k = e - r * N;
+    const int j = r < JP ? j0 + r : N - j0 - 2 * JP + r;
+    const int slot = (k % N1) * (n2 + 1) + k / N1;
+    real s = si;
+    if (a.mode >= 2) s *= misc[3 * B + j];
+    cx<real> v = {sre[r * pitch + slot] * s, sim[r * pitch + slot] * s};
+    out[(int64_t)j * N + k] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SIMT GEMM stages (FP64 / FP32 on the CUDA cores)
+// ---------------------------------------------------------------------------
+enum Prob { LEG_F = 0, RAD_F = 1, RAD_I = 2, LEG_I = 3 };
+
+struct GemmArgs {
+  const SegDesc* segs;
+  const int64_t* fn_coef;
+  const int64_t* si_rows;
+  const int4* tiles;
+  const void* tab;
+  const void* x;     // stage input (W1, W2 or coefficients)
+  void* y;           // stage output
+  int weighted;      // forward stages: use the weighted tables
+};
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+__device__ __forceinline__ int64_t omega_idx(int n, int l, int m) {
+  return (int64_t)n * (n - 1) * (2 * n - 1) / 6 + (int64_t)l * (l + 1) + m;
+}
+__device__ __forceinline__ int64_t leg_rows_before_d(int B, int m, int p) {
+  int64_t rows = (int64_t)m * B - (int64_t)m * (m - 1) / 2;
+  if (p == 1) rows += (m >= B) ? 0 : (B - 1 - m) / 2 + 1;
+  return rows;
+}
+__device__ __forceinline__ int n_par_d(int B, int m, int p) {
+  int first = m + p;
+  return first >= B ? 0 : (B - 1 - first) / 2 + 1;
+}
+
+struct GroupCtx {
+  int B, NB, rows, N, K, KP, KPpad;
+  int g;       // group id within the stage
+  int m, am, p, l, m_idx;
+  int64_t xbase, xbase2, abase, abase2;
+};
+
+template <int PROB>
+__device__ __forceinline__ void group_setup(const GemmArgs& a, const SegDesc& sg, int g, GroupCtx& c) {
+  c.B = sg.B;
+  c.NB = sg.NB;
+  c.g = g;
+  const int B = sg.B, NB = sg.NB;
+  if (PROB == LEG_F) {
+    c.m_idx = g >> 1;
+    c.p = g & 1;
+    c.m = c.m_idx - (B - 1);
+    c.am = c.m < 0 ? -c.m : c.m;
+    c.rows = NB * 2 * B;
+    c.N = n_par_d(B, c.am, c.p);
+    c.K = B;
+    c.xbase = sg.w1_off + ((int64_t)c.m_idx * 2 + c.p) * NB * 2 * B * B;
+    c.abase = (a.weighted ? sg.tab_leg_f : sg.tab_leg_i) + leg_rows_before_d(B, c.am, c.p) * B;
+  } else if (PROB == RAD_F) {
+    c.l = g;
+    c.rows = NB * (2 * c.l + 1) * 2;
+    c.N = B - c.l;
+    c.K = B;
+    c.xbase = sg.w2_off + (int64_t)NB * 2 * B * c.l * c.l;
+    c.abase = (a.weighted ? sg.tab_rad_f : sg.tab_rad_i) + ((int64_t)c.l * B - (int64_t)c.l * (c.l - 1) / 2) * B;
+  } else if (PROB == RAD_I) {
+    c.l = g;
+    c.rows = NB * (2 * c.l + 1) * 2;
+    c.N = B;
+    c.K = B - c.l;
+    c.abase = sg.tab_rad_i + ((int64_t)c.l * B - (int64_t)c.l * (c.l - 1) / 2) * B;
+  } else {  // LEG_I
+    c.m_idx = g;
+    c.m = g - (B - 1);
+    c.am = c.m < 0 ? -c.m : c.m;
+    c.rows = NB * 2 * B;
+    c.N = B;
+    c.KP = n_par_d(B, c.am, 0);
+    c.KPpad = (c.KP + TK - 1) / TK * TK;
+    c.K = c.KPpad + n_par_d(B, c.am, 1);
+    const int64_t* sr = a.si_rows + sg.si_rows;
+    c.xbase = sg.w2_off + sr[2 * c.m_idx] * (int64_t)NB * 2 * B;
+    c.xbase2 = sg.w2_off + sr[2 * c.m_idx + 1] * (int64_t)NB * 2 * B;
+    c.abase = sg.tab_leg_i + leg_rows_before_d(B, c.am, 0) * B;
+    c.abase2 = sg.tab_leg_i + leg_rows_before_d(B, c.am, 1) * B;
+  }
+}
+
+template <int PROB, typename real>
+__device__ __forceinline__ real load_x(const GemmArgs& a, const SegDesc& sg, const GroupCtx& c, int row, int k) {
+  const real* X = reinterpret_cast<const real*>(a.x);
+  if (row >= c.rows || k >= c.K) return 0;
+  if (PROB == LEG_F || PROB == RAD_F) {
+    return X[c.xbase + (int64_t)row * c.B + k];
+  } else if (PROB == RAD_I) {
+    const int per_b = (2 * c.l + 1) * 2;
+    const int b = row / per_b;
+    const int rem = row - b * per_b;
+    const int mm = rem >> 1, cc = rem & 1;
+    const int64_t off = a.fn_coef[sg.fn0 + b] + omega_idx(c.l + 1 + k, c.l, mm - c.l);
+    return X[2 * off + cc];
+  } else {
+    const int64_t NB2B = (int64_t)c.NB * 2 * c.B;
+    if (k < c.KPpad) {
+      if (k >= c.KP) return 0;
+      return X[c.xbase + k * NB2B + row];
+    }
+    return X[c.xbase2 + (k - c.KPpad) * NB2B + row];
+  }
+}
+
+template <int PROB, typename real>
+__device__ __forceinline__ real load_a(const GemmArgs& a, const GroupCtx& c, int col, int k) {
+  const real* A = reinterpret_cast<const real*>(a.tab);
+  if (col >= c.N || k >= c.K) return 0;
+  if (PROB == LEG_F || PROB == RAD_F) {
+    return A[c.abase + (int64_t)col * c.B + k];
+  } else if (PROB == RAD_I) {
+    return A[c.abase + (int64_t)k * c.B + col];
+  } else {
+    if (k < c.KPpad) {
+      if (k >= c.KP) return 0;
+      return A[c.abase + (int64_t)k * c.B + col];
+    }
+    return A[c.abase2 + (int64_t)(k - c.KPpad) * c.B + col];
+  }
+}
+
+template <int PROB, typename real>
+__device__ __forceinline__ void store_y(const GemmArgs& a, const SegDesc& sg, const GroupCtx& c, int row, int col,
+                                        real v, real v2) {
+  if (row >= c.rows || col >= c.N) return;
+  real* Y = reinterpret_cast<real*>(a.y);
+  const int B = c.B, NB = c.NB;
+  if (PROB == LEG_F) {
+    const int b = row / (2 * B);
+    const int cc = (row / B) & 1;
+    const int i = row % B;
+    const int l = c.am + c.p + 2 * col;
+    const real s = (c.m < 0 && (c.am & 1)) ? real(-1) : real(1);
+    Y[sg.w2_off + (int64_t)NB * 2 * B * l * l + (((int64_t)b * (2 * l + 1) + (c.m + l)) * 2 + cc) * B + i] = s * v;
+  } else if (PROB == RAD_F) {
+    const int per_b = (2 * c.l + 1) * 2;
+    const int b = row / per_b;
+    const int rem = row - b * per_b;
+    const int mm = rem >> 1, cc = rem & 1;
+    const int64_t off = a.fn_coef[sg.fn0 + b] + omega_idx(c.l + 1 + col, c.l, mm - c.l);
+    Y[2 * off + cc] = v;
+  } else if (PROB == RAD_I) {
+    const int per_b = (2 * c.l + 1) * 2;
+    const int b = row / per_b;
+    const int rem = row - b * per_b;
+    const int mm = rem >> 1, cc = rem & 1;
+    const int m = mm - c.l;
+    const int am = m < 0 ? -m : m;
+    const int p = (c.l - am) & 1;
+    const int lp = (c.l - am - p) >> 1;
+    const int m_idx = m + B - 1;
+    const int64_t srow = a.si_rows[sg.si_rows + 2 * m_idx + p] + lp;
+    Y[sg.w2_off + srow * NB * 2 * B + ((int64_t)b * 2 + cc) * B + col] = v;
+  } else {
+    const real s = (c.m < 0 && (c.am & 1)) ? real(-1) : real(1);
+    const int64_t base = sg.w1_off + (int64_t)c.m_idx * NB * 2 * B * 2 * B + (int64_t)row * 2 * B;
+    Y[base + col] = s * (v + v2);
+    Y[base + 2 * B - 1 - col] = s * (v - v2);
+  }
+}
+
+template <int PROB, typename real>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
+  __shared__ real Xs[TK][TM + 1];
+  __shared__ real As[TK][TN + 1];
+  const int4 t = a.tiles[blockIdx.x];
+  const SegDesc sg = a.segs[t.x];
+  GroupCtx c;
+  group_setup<PROB>(a, sg, t.y, c);
+  const int row0 = t.z, col0 = t.w;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  real acc[4][4], acc2[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = acc2[r][q] = 0;
+  for (int k0 = 0; k0 < c.K; k0 += TK) {
+    // X tile: TM rows x TK (k fastest across threads for coalesced row reads)
+    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+      const int rr = e / TK, kk = e % TK;
+      Xs[kk][rr] = load_x<PROB, real>(a, sg, c, row0 + rr, k0 + kk);
+    }
+    for (int e = threadIdx.x; e < TN * TK; e += 256) {
+      int cc, kk;
+      if (PROB == RAD_I || PROB == LEG_I) {  // tables stored [k][col]: col fastest
+        kk = e / TN;
+        cc = e % TN;
+      } else {
+        cc = e / TK;
+        kk = e % TK;
+      }
+      As[kk][cc] = load_a<PROB, real>(a, c, col0 + cc, k0 + kk);
+    }
+    __syncthreads();
+    const bool second = (PROB == LEG_I) && (k0 >= c.KPpad);
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      real xv[4], av[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) xv[r] = Xs[kk][ty + 16 * r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) av[q] = As[kk][tx + 16 * q];
+      if (second) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc2[r][q] = fma(xv[r], av[q], acc2[r][q]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[r][q] = fma(xv[r], av[q], acc[r][q]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      store_y<PROB, real>(a, sg, c, row0 + ty + 16 * r, col0 + tx + 16 * q, acc[r][q], acc2[r][q]);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename real>
+size_t fft_smem_bytes(int n1, int n2, int B, int JP) {
+  return sizeof(real) * (2 * 2 * B + 2 * 2 * (size_t)JP * ring_pitch(n1, n2));
+}
+
+int fft_pairs_per_cta(int prec, int B) {
+  int jp = (prec == SGL_FP64) ? 8 : 16;
+  return jp < B ? jp : B;
+}
+
+template <typename real, bool INV>
+static cudaError_t launch_fft_t(const Plan& P, const FftArgs& a, int n1, int n2, int nctas, size_t smem,
+                                cudaStream_t s) {
+  void (*fn)(FftArgs) = nullptr;
+#define SGL_PICK(N1, N2C)                                                                   \
+  fn = INV ? (void (*)(FftArgs))fft_inv_kernel<real, N1, N2C> : (void (*)(FftArgs))fft_fwd_kernel<real, N1, N2C>;
+  if (n1 == 16 && n2 == 16) { SGL_PICK(16, 16) }
+  else if (n1 == 16 && n2 == 8) { SGL_PICK(16, 8) }
+  else if (n1 == 16) { SGL_PICK(16, 0) }
+  else if (n1 == 8) { SGL_PICK(8, 0) }
+  else if (n1 == 4) { SGL_PICK(4, 0) }
+  else if (n1 == 2) { SGL_PICK(2, 0) }
+  else { SGL_PICK(1, 0) }
+#undef SGL_PICK
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<nctas, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real>
+static cudaError_t launch_gemm_t(int prob, const GemmArgs& a, int ntiles, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  switch (prob) {
+    case LEG_F: gemm_simt_kernel<LEG_F, real><<<ntiles, 256, 0, s>>>(a); break;
+    case RAD_F: gemm_simt_kernel<RAD_F, real><<<ntiles, 256, 0, s>>>(a); break;
+    case RAD_I: gemm_simt_kernel<RAD_I, real><<<ntiles, 256, 0, s>>>(a); break;
+    default: gemm_simt_kernel<LEG_I, real><<<ntiles, 256, 0, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+// The FFT launches use one kernel instantiation per (n1, n2) class, so plans
+// whose segments differ in those factors launch one FFT kernel per segment
+// (the CTA list is sorted by segment; each launch gets its slice).
+struct FftSlice {
+  int first, count, n1, n2, B;
+};
+
+static void fft_slices(const Plan& P, std::vector<FftSlice>& out, bool inv) {
+  out.clear();
+  int first = 0;
+  for (size_t s = 0; s < P.segs.size(); ++s) {
+    const SegDesc& sg = P.segs[s];
+    const int JP = fft_pairs_per_cta(P.prec, sg.B);
+    const int per_shell = (sg.B + JP - 1) / JP;
+    const int count = sg.NB * sg.B * per_shell;
+    out.push_back({first, count, sg.n1, sg.n2, sg.B});
+    first += count;
+  }
+  (void)inv;
+}
+
+template <typename real>
+static cudaError_t run_fft(Plan& P, bool inv, const void* in, void* out, int mode, cudaStream_t s) {
+  StageTimer timer(P, inv ? ST_FFT_I : ST_FFT_F, s);
+  std::vector<FftSlice> sl;
+  fft_slices(P, sl, inv);
+  for (const FftSlice& f : sl) {
+    FftArgs a;
+    a.segs = P.d_segs;
+    a.fn_samp = P.d_fn_samp;
+    a.ctas = (inv ? P.d_fft_inv : P.d_fft_fwd) + f.first;
+    a.tab = P.d_tab;
+    a.in = in;
+    a.out = out;
+    a.w1 = P.d_w1;
+    a.JP = fft_pairs_per_cta(P.prec, f.B);
+    a.mode = mode;
+    size_t smem = fft_smem_bytes<real>(f.n1, f.n2, f.B, a.JP);
+    cudaError_t e = inv ? launch_fft_t<real, true>(P, a, f.n1, f.n2, f.count, smem, s)
+                        : launch_fft_t<real, false>(P, a, f.n1, f.n2, f.count, smem, s);
+    if (e != cudaSuccess) return e;
+  }
+  timer.finish();
+  return cudaSuccess;
+}
+
+// TF32x3 tensor-core stages (tc_gemm.cu)
+cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted, cudaStream_t s);
+
+template <typename real>
+static cudaError_t run_gemm(Plan& P, int prob, const GemmSched& sch, const void* x, void* y, int weighted,
+                            cudaStream_t s) {
+  GemmArgs a;
+  a.segs = P.d_segs;
+  a.fn_coef = P.d_fn_coef;
+  a.si_rows = P.d_si_rows;
+  a.tiles = sch.d_tiles;
+  a.tab = P.d_tab;
+  a.x = x;
+  a.y = y;
+  a.weighted = weighted;
+  static const int stage_of[4] = {ST_LEG_F, ST_RAD_F, ST_RAD_I, ST_LEG_I};
+  StageTimer timer(P, stage_of[prob], s);
+  cudaError_t e = launch_gemm_t<real>(prob, a, sch.ntiles, s);
+  timer.finish();
+  return e;
+}
+
+template <typename real>
+static cudaError_t forward_t(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights) {
+  int mode = 0;
+  if (P.samples == SGL_SAMPLES_PHYSICAL) mode = weights ? 1 : 2;
+  cudaError_t e = run_fft<real>(P, false, samples, nullptr, mode, s);
+  if (e != cudaSuccess) return e;
+  if (P.prec == SGL_TF32X3) {
+    e = run_tc_stage(P, LEG_F, P.d_w1, P.d_w2, weights, s);
+    if (e != cudaSuccess) return e;
+    return run_tc_stage(P, RAD_F, P.d_w2, coeffs, weights, s);
+  }
+  e = run_gemm<real>(P, LEG_F, P.leg_fwd, P.d_w1, P.d_w2, weights, s);
+  if (e != cudaSuccess) return e;
+  return run_gemm<real>(P, RAD_F, P.rad_fwd, P.d_w2, coeffs, weights, s);
+}
+
+template <typename real>
+static cudaError_t inverse_t(Plan& P, const void* coeffs, void* samples, cudaStream_t s, bool weights) {
+  cudaError_t e;
+  if (P.prec == SGL_TF32X3) {
+    e = run_tc_stage(P, RAD_I, coeffs, P.d_w2, 0, s);
+    if (e != cudaSuccess) return e;
+    e = run_tc_stage(P, LEG_I, P.d_w2, P.d_w1, 0, s);
+  } else {
+    e = run_gemm<real>(P, RAD_I, P.rad_inv, coeffs, P.d_w2, 0, s);
+    if (e != cudaSuccess) return e;
+    e = run_gemm<real>(P, LEG_I, P.leg_inv, P.d_w2, P.d_w1, 0, s);
+  }
+  if (e != cudaSuccess) return e;
+  int mode = 0;
+  if (weights) mode = (P.samples == SGL_SAMPLES_PHYSICAL) ? 3 : 2;
+  else if (P.samples == SGL_SAMPLES_PHYSICAL) mode = 1;
+  return run_fft<real>(P, true, nullptr, samples, mode, s);
+}
+
+cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights) {
+  if (P.prec == SGL_FP64) return forward_t<double>(P, samples, coeffs, s, weights);
+  return forward_t<float>(P, samples, coeffs, s, weights);
+}
+
+cudaError_t run_inverse(Plan& P, const void* coeffs, void* samples, cudaStream_t s, bool weights) {
+  if (P.prec == SGL_FP64) return inverse_t<double>(P, coeffs, samples, s, weights);
+  return inverse_t<float>(P, coeffs, samples, s, weights);
+}
+
+// Host-side helpers used by the plan builder
+size_t fft_smem_for(int prec, int n1, int n2, int B) {
+  int JP = fft_pairs_per_cta(prec, B);
+  return prec == SGL_FP64 ? fft_smem_bytes<double>(n1, n2, B, JP) : fft_smem_bytes<float>(n1, n2, B, JP);
+}
+
+void gemm_tile_dims(int& tm, int& tn, int& tk) {
+  tm = TM;
+  tn = TN;
+  tk = TK;
+}
+
+}  // namespace sgl

@@ -1,0 +1,201 @@
+// Internal declarations of the SGL transform library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sgl.h"
+
+namespace sgl {
+
+// ---------------------------------------------------------------------------
+// Host FP64 tables of one bandlimit (tables.cpp)
+// ---------------------------------------------------------------------------
+struct HostTables {
+  int B = 0;
+  std::vector<double> t, r, what;          // [B]   radial nodes t_i = r_i^2, weights what_i
+  std::vector<double> theta, phi, beta;    // [2B]  sphere rule (Thm 3.1, beta = pi/B b_j)
+  std::vector<double> lam;                 // [m][l][j'] m,l < B, j' < B: Lambda_lm(theta_j')
+  std::vector<double> T;                   // [l][n-1][i]: N_nl R_nl(r_i) exp(-t_i/2)
+};
+
+// Builds every table for bandlimit B (1 <= B <= SGL_MAX_B).  Returns false and
+// sets msg on failure.
+bool build_tables(int B, HostTables& out, std::string& msg);
+
+// Number of degrees l >= m with (l - m) % 2 == p, l < B.
+inline int n_par(int B, int m, int p) {
+  int first = m + p;
+  return first >= B ? 0 : (B - 1 - first) / 2 + 1;
+}
+
+// Largest power of two dividing n, capped at 16.
+inline int fft_n1(int n) {
+  int p = 1;
+  while (p < 16 && n % (2 * p) == 0) p *= 2;
+  return p;
+}
+
+inline bool bandlimit_supported(int B) {
+  if (B < 1 || B > SGL_MAX_B) return false;
+  int n = 2 * B;
+  return n / fft_n1(n) <= 16;
+}
+
+inline int64_t coeff_count(int B) { return (int64_t)B * (B + 1) * (2 * B + 1) / 6; }
+inline int64_t sample_count(int B) { return 4LL * B * B * B; }
+
+// ---------------------------------------------------------------------------
+// Table and workspace layouts (reals)
+// ---------------------------------------------------------------------------
+// Misc block of one bandlimit:
+//   [0, B)      what_i
+//   [B, 2B)     exp(-t_i/2)
+//   [2B, 3B)    exp(+t_i/2)
+//   [3B, 5B)    beta_j, j < 2B
+//   [5B, 9B)    twiddles e^{-2 pi i k/(2B)} as (re, im), k < 2B
+inline int64_t misc_size(int B) { return 9LL * B; }
+
+// Legendre block: for m = 0..B-1, p = 0,1: n_par(B,m,p) rows of B reals over
+// the half grid j' < B; row q of (m,p) is degree l = m + p + 2q.
+inline int64_t leg_rows_before(int B, int m, int p) {
+  int64_t rows = (int64_t)m * B - (int64_t)m * (m - 1) / 2;
+  if (p == 1) rows += n_par(B, m, 0);
+  return rows;
+}
+inline int64_t leg_table_size(int B) { return (int64_t)B * (B + 1) / 2 * B; }
+// Radial block: [l][n' < B-l][i < B], row n' is degree n = l + 1 + n'.
+inline int64_t rad_rows_before(int B, int l) { return (int64_t)l * B - (int64_t)l * (l - 1) / 2; }
+inline int64_t rad_table_size(int B) { return (int64_t)B * (B + 1) / 2 * B; }
+
+// Workspaces of a segment of NB functions with one bandlimit B:
+//   W1 forward "EO":  [m_idx < 2B-1][p<2][b<NB][c<2][i<B][j'<B]      (E = G_j'+G_mirror, O = G_j'-G_mirror)
+//   W1 inverse "G":   [m_idx < 2B-1][b<NB][c<2][i<B][j<2B]
+//   W2 forward "S_f": block l at NB*2*B*l^2: [b][m+l < 2l+1][c][i<B]
+//   W2 inverse "S_i": block (m_idx,p) at NB*2*B*si_rows_before: [l'<n_par][b][c][i<B]
+inline int64_t w1_size(int B, int NB) { return 4LL * NB * B * B * (2 * B - 1); }
+inline int64_t w2_size(int B, int NB) { return 2LL * NB * B * B * B; }
+inline int64_t si_rows_before(int B, int m_idx, int p) {
+  int64_t rows = 0;
+  for (int mi = 0; mi < m_idx; ++mi) {
+    int am = mi - (B - 1);
+    rows += B - (am < 0 ? -am : am);
+  }
+  if (p == 1) {
+    int am = m_idx - (B - 1);
+    rows += n_par(B, am < 0 ? -am : am, 0);
+  }
+  return rows;
+}
+
+// ---------------------------------------------------------------------------
+// Segments: functions of one bandlimit processed together
+// ---------------------------------------------------------------------------
+struct SegDesc {
+  int B, NB;          // bandlimit, functions in the segment
+  int n1, n2;         // 2B = n1 * n2 (phi-FFT factors)
+  int fn0;            // first entry of the segment in the per-function offset arrays
+  int pad;
+  int64_t w1_off, w2_off;               // reals
+  int64_t tab_leg_f, tab_leg_i;         // reals: Legendre tables (fwd: * beta, inv: plain)
+  int64_t tab_rad_f, tab_rad_i;         // reals: radial tables (fwd: * what, inv: plain)
+  int64_t tab_misc;                     // reals
+  int64_t si_rows;                      // offset of the segment's S_i row table in d_si_rows
+};
+
+// Tile of a GEMM stage: (segment, group, row0, col0)
+// FFT CTA:            (segment, shell = b*B + i, j'0, 0)
+
+struct GemmSched {
+  int4* d_tiles = nullptr;
+  int ntiles = 0;
+};
+
+struct Plan {
+  int prec = SGL_FP64;
+  int samples = SGL_SAMPLES_WEIGHTED;
+  int nfn = 0;
+  bool uniform = true;
+  int maxB = 0;
+  int64_t n_samples = 0, n_coeffs = 0;           // complex elements, whole plan
+  std::vector<int> fn_B;                         // user order
+  std::vector<int64_t> fn_samp_off, fn_coef_off; // user order, complex elements
+  std::vector<SegDesc> segs;
+  std::vector<int> seg_fn;                       // per segment order: user function index
+  std::vector<HostTables> tables;                // one per segment
+  int device = 0;
+
+  // device memory
+  void* d_tab = nullptr;        // tables in the plan's real type (hi parts for TF32x3)
+  void* d_tab_lo = nullptr;     // TF32x3 lo parts of the Legendre / radial tables
+  void* d_w1 = nullptr;
+  void* d_w2 = nullptr;
+  void* d_stage_in = nullptr;
+  void* d_stage_out = nullptr;
+  size_t stage_in_bytes = 0, stage_out_bytes = 0;
+  SegDesc* d_segs = nullptr;
+  int64_t* d_fn_samp = nullptr; // per segment order
+  int64_t* d_fn_coef = nullptr;
+  int64_t* d_si_rows = nullptr; // per segment: [(2B-1)*2] rows-before of S_i blocks
+  int* d_err = nullptr;
+  int64_t bytes = 0;
+  int64_t w1_elems = 0, w2_elems = 0, tab_elems = 0;
+
+  GemmSched leg_fwd, rad_fwd, rad_inv, leg_inv;
+  int4* d_fft_fwd = nullptr;
+  int4* d_fft_inv = nullptr;
+  int n_fft_fwd = 0, n_fft_inv = 0;
+  int launches_per_call = 0;
+
+  // stage timing (sgl_set_profiling): event pairs per stage, and a free pool
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[SGL_NUM_STAGES];
+  std::vector<cudaEvent_t> ev_pool;
+
+  std::string err;
+  int latched = SGL_OK;
+};
+
+enum Stage { ST_FFT_F = 0, ST_LEG_F = 1, ST_RAD_F = 2, ST_RAD_I = 3, ST_LEG_I = 4, ST_FFT_I = 5 };
+
+// Records a start event on construction and a stop event on finish() when the
+// plan is profiling; otherwise does nothing.
+struct StageTimer {
+  Plan& P;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  StageTimer(Plan& p, int st, cudaStream_t str) : P(p), stage(st), s(str) {
+    if (P.profiling) {
+      a = take();
+      cudaEventRecord(a, s);
+    }
+  }
+  cudaEvent_t take() {
+    if (!P.ev_pool.empty()) {
+      cudaEvent_t e = P.ev_pool.back();
+      P.ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void finish() {
+    if (P.profiling && a) {
+      cudaEvent_t b = take();
+      cudaEventRecord(b, s);
+      P.prof_ev[stage].push_back({a, b});
+      a = nullptr;
+    }
+  }
+};
+
+// Stage launchers (kernels.cu)
+cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights);
+cudaError_t run_inverse(Plan& P, const void* coeffs, void* samples, cudaStream_t s, bool weights);
+
+}  // namespace sgl

@@ -1,0 +1,344 @@
+"""Python binding of libsgl (include/sgl.h): argument marshalling only.
+
+Every function named ``sgl_*`` here calls the C function of the same name.
+The ``Plan`` class wraps a plan for torch tensors (device memory and streams
+come from PyTorch; every step of the transform runs in libsgl's kernels), and
+``SGLForward`` / ``SGLInverse`` make the transforms differentiable with the
+library's adjoint transforms as backward passes.
+
+The library must have been built (``paper_1604_05140_gb300.build.build()``);
+importing the binding without it raises immediately: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsgl.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "sgl.h")
+
+SGL_OK, SGL_ERR_ARG, SGL_ERR_ALLOC, SGL_ERR_CUDA, SGL_ERR_TIMEOUT, SGL_ERR_UNSUPPORTED = range(6)
+SGL_FP64, SGL_FP32, SGL_TF32X3 = 0, 1, 2
+SGL_SAMPLES_WEIGHTED, SGL_SAMPLES_PHYSICAL = 0, 1
+SGL_MAX_B = 128
+
+PRECISIONS = {"fp64": SGL_FP64, "fp32": SGL_FP32, "tf32x3": SGL_TF32X3}
+STATUS_NAMES = {0: "SGL_OK", 1: "SGL_ERR_ARG", 2: "SGL_ERR_ALLOC", 3: "SGL_ERR_CUDA",
+                4: "SGL_ERR_TIMEOUT", 5: "SGL_ERR_UNSUPPORTED"}
+
+
+class SGLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library():
+    """Load libsgl.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"libsgl.so not found at {LIB_PATH}: build it first with "
+            "`python -m paper_1604_05140_gb300.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    dp = ctypes.POINTER(ctypes.c_double)
+    sigs = {
+        "sgl_plan": (i32, [ctypes.POINTER(vp), i32, i32, i32, i32]),
+        "sgl_plan_many": (i32, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), i32, i32]),
+        "sgl_forward": (i32, [vp, vp, vp, vp]),
+        "sgl_inverse": (i32, [vp, vp, vp, vp]),
+        "sgl_adjoint": (i32, [vp, i32, vp, vp, vp]),
+        "sgl_grid": (i32, [vp, i32, dp, dp, dp, dp, dp]),
+        "sgl_sample_count": (i64, [vp]),
+        "sgl_coeff_count": (i64, [vp]),
+        "sgl_sample_offset": (i64, [vp, i32]),
+        "sgl_coeff_offset": (i64, [vp, i32]),
+        "sgl_num_functions": (i32, [vp]),
+        "sgl_bandlimit": (i32, [vp, i32]),
+        "sgl_workspace_bytes": (i64, [vp]),
+        "sgl_launches_per_call": (i32, [vp]),
+        "sgl_check": (i32, [vp, vp]),
+        "sgl_last_error": (ctypes.c_char_p, [vp]),
+        "sgl_destroy": (None, [vp]),
+        "sgl_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in include/sgl.h."""
+    with open(path) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(sgl_\w+)\s*\(", text, re.M)))
+
+
+def _check(st: int, plan=None):
+    if st != SGL_OK:
+        lib = load_library()
+        msg = lib.sgl_last_error(plan)
+        raise SGLError(st, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# C ABI, same names
+# ---------------------------------------------------------------------------
+
+def sgl_plan(B: int, batch: int = 1, prec: int = SGL_FP64, samples: int = SGL_SAMPLES_WEIGHTED):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.sgl_plan(ctypes.byref(h), int(B), int(batch), int(prec), int(samples)))
+    return h
+
+
+def sgl_plan_many(Bs: Sequence[int], prec: int = SGL_TF32X3):
+    lib = load_library()
+    arr = (ctypes.c_int * len(Bs))(*[int(b) for b in Bs])
+    h = ctypes.c_void_p()
+    _check(lib.sgl_plan_many(ctypes.byref(h), arr, len(Bs), int(prec)))
+    return h
+
+
+def sgl_forward(plan, samples_ptr: int, coeffs_ptr: int, stream: int = 0):
+    _check(load_library().sgl_forward(plan, samples_ptr, coeffs_ptr, stream), plan)
+
+
+def sgl_inverse(plan, coeffs_ptr: int, samples_ptr: int, stream: int = 0):
+    _check(load_library().sgl_inverse(plan, coeffs_ptr, samples_ptr, stream), plan)
+
+
+def sgl_adjoint(plan, of_inverse: int, in_ptr: int, out_ptr: int, stream: int = 0):
+    _check(load_library().sgl_adjoint(plan, int(of_inverse), in_ptr, out_ptr, stream), plan)
+
+
+def sgl_grid(plan, fn: int = 0):
+    lib = load_library()
+    B = lib.sgl_bandlimit(plan, fn)
+    if B < 1:
+        raise SGLError(SGL_ERR_ARG, "function index out of range")
+    r, th, ph, wr, wt = (np.zeros(n) for n in (B, 2 * B, 2 * B, B, 2 * B))
+    P = ctypes.POINTER(ctypes.c_double)
+    _check(lib.sgl_grid(plan, fn, *(a.ctypes.data_as(P) for a in (r, th, ph, wr, wt))), plan)
+    return r, th, ph, wr, wt
+
+
+def sgl_destroy(plan):
+    load_library().sgl_destroy(plan)
+
+
+def sgl_check(plan, stream: int = 0):
+    _check(load_library().sgl_check(plan, stream), plan)
+
+
+# ---------------------------------------------------------------------------
+# torch-facing plan
+# ---------------------------------------------------------------------------
+
+class Plan:
+    """A libsgl plan operating on torch tensors.
+
+    Single-bandlimit plans take samples of shape (batch, B, 2B, 2B) and
+    coefficients of shape (batch, Omega); plans over uneven bandlimits
+    (``Plan.many``) take flat 1-D tensors packed at ``sample_offset(f)`` /
+    ``coeff_offset(f)``.  Tensors may live on the GPU (used in place, launch
+    on the current torch stream) or in host memory (staged by the library).
+    """
+
+    def __init__(self, B: Optional[int] = None, batch: int = 1, precision: str = "fp64",
+                 samples: str = "weighted", _handle=None, _Bs=None):
+        import torch  # noqa: F401  (device memory and streams)
+        self.lib = load_library()
+        self.prec = PRECISIONS[precision]
+        self.precision = precision
+        if _handle is not None:
+            self.handle = _handle
+            self.Bs = list(_Bs)
+            self.B = None
+            self.batch = len(self.Bs)
+        else:
+            conv = {"weighted": SGL_SAMPLES_WEIGHTED, "physical": SGL_SAMPLES_PHYSICAL}[samples]
+            self.handle = sgl_plan(B, batch, self.prec, conv)
+            self.B = int(B)
+            self.batch = int(batch)
+            self.Bs = [self.B] * self.batch
+        self.n_samples = self.lib.sgl_sample_count(self.handle)
+        self.n_coeffs = self.lib.sgl_coeff_count(self.handle)
+
+    @classmethod
+    def many(cls, Bs: Sequence[int], precision: str = "tf32x3") -> "Plan":
+        h = sgl_plan_many(Bs, PRECISIONS[precision])
+        return cls(precision=precision, _handle=h, _Bs=Bs)
+
+    # shapes and types ----------------------------------------------------
+    @property
+    def dtype(self):
+        import torch
+        return torch.complex128 if self.prec == SGL_FP64 else torch.complex64
+
+    @property
+    def sample_shape(self):
+        if self.B is None:
+            return (self.n_samples,)
+        return (self.batch, self.B, 2 * self.B, 2 * self.B)
+
+    @property
+    def coeff_shape(self):
+        if self.B is None:
+            return (self.n_coeffs,)
+        return (self.batch, self.n_coeffs // self.batch)
+
+    def sample_offset(self, f: int) -> int:
+        return self.lib.sgl_sample_offset(self.handle, f)
+
+    def coeff_offset(self, f: int) -> int:
+        return self.lib.sgl_coeff_offset(self.handle, f)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return self.lib.sgl_workspace_bytes(self.handle)
+
+    @property
+    def launches_per_call(self) -> int:
+        return self.lib.sgl_launches_per_call(self.handle)
+
+    def grid(self, fn: int = 0):
+        return sgl_grid(self.handle, fn)
+
+    # execution ------------------------------------------------------------
+    def _prep(self, t, numel: int, name: str):
+        import torch
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.dtype != self.dtype:
+            raise TypeError(f"{name} must be {self.dtype}, got {t.dtype}")
+        if t.numel() != numel:
+            raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+    def _stream(self, *tensors) -> int:
+        import torch
+        for t in tensors:
+            if t.is_cuda:
+                return torch.cuda.current_stream(t.device).cuda_stream
+        return 0
+
+    def _out(self, like, shape, out):
+        import torch
+        if out is None:
+            out = torch.empty(shape, dtype=self.dtype, device=like.device,
+                              pin_memory=(not like.is_cuda and torch.cuda.is_available()))
+        return out
+
+    def forward(self, samples, out=None):
+        """Coefficients of the samples (sgl_forward)."""
+        self._prep(samples, self.n_samples, "samples")
+        out = self._out(samples, self.coeff_shape, out)
+        self._prep(out, self.n_coeffs, "out")
+        sgl_forward(self.handle, samples.data_ptr(), out.data_ptr(), self._stream(samples, out))
+        return out
+
+    def inverse(self, coeffs, out=None):
+        """Samples of the function with these coefficients (sgl_inverse)."""
+        self._prep(coeffs, self.n_coeffs, "coeffs")
+        out = self._out(coeffs, self.sample_shape, out)
+        self._prep(out, self.n_samples, "out")
+        sgl_inverse(self.handle, coeffs.data_ptr(), out.data_ptr(), self._stream(coeffs, out))
+        return out
+
+    def adjoint(self, x, of_inverse: bool, out=None):
+        """Hermitian adjoint of the forward map (of_inverse=False, coefficients
+        -> samples) or of the inverse map (of_inverse=True, samples ->
+        coefficients), sgl_adjoint."""
+        if of_inverse:
+            self._prep(x, self.n_samples, "x")
+            out = self._out(x, self.coeff_shape, out)
+            self._prep(out, self.n_coeffs, "out")
+        else:
+            self._prep(x, self.n_coeffs, "x")
+            out = self._out(x, self.sample_shape, out)
+            self._prep(out, self.n_samples, "out")
+        sgl_adjoint(self.handle, int(bool(of_inverse)), x.data_ptr(), out.data_ptr(), self._stream(x, out))
+        return out
+
+    def check(self):
+        import torch
+        sgl_check(self.handle, torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            sgl_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+
+_AUTOGRAD = None
+
+
+def _autograd_classes():
+    global _AUTOGRAD
+    if _AUTOGRAD is not None:
+        return _AUTOGRAD
+    import torch
+
+    class SGLForward(torch.autograd.Function):
+        """coeffs = forward(samples); backward: the adjoint of the forward map.
+        PyTorch's complex gradients are conjugate-Wirtinger, so the
+        vector-Jacobian product of a linear map is its Hermitian adjoint."""
+
+        @staticmethod
+        def forward(ctx, samples, plan):
+            ctx.plan = plan
+            return plan.forward(samples.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad):
+            return ctx.plan.adjoint(grad.contiguous(), of_inverse=False), None
+
+    class SGLInverse(torch.autograd.Function):
+        """samples = inverse(coeffs); backward: the adjoint of the inverse map."""
+
+        @staticmethod
+        def forward(ctx, coeffs, plan):
+            ctx.plan = plan
+            return plan.inverse(coeffs.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad):
+            return ctx.plan.adjoint(grad.contiguous(), of_inverse=True), None
+
+    _AUTOGRAD = (SGLForward, SGLInverse)
+    return _AUTOGRAD
+
+
+def sgl_forward_autograd(samples, plan):
+    return _autograd_classes()[0].apply(samples, plan)
+
+
+def sgl_inverse_autograd(coeffs, plan):
+    return _autograd_classes()[1].apply(coeffs, plan)

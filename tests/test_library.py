@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI: the library builds, loads, exports every
+function include/sgl.h declares, and rejects bad arguments before touching the
+GPU (no compute calls: this file runs without a GPU)."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+from paper_1604_05140_gb300 import sgl
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1604_05140_gb300 import build
+    if build.stale():
+        build.build()
+    return sgl.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = sgl.header_functions()
+    for must in ["sgl_plan", "sgl_plan_many", "sgl_forward", "sgl_inverse", "sgl_adjoint",
+                 "sgl_grid", "sgl_destroy", "sgl_last_error", "sgl_check"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", sgl.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in sgl.header_functions() if n not in exported]
+    assert not missing, missing
+    for n in sgl.header_functions():
+        assert hasattr(lib, n)
+
+
+def test_version(lib):
+    assert lib.sgl_version().decode().startswith("sgl-gb300")
+
+
+@pytest.mark.parametrize("args,status", [
+    ((0, 1, 0, 0), sgl.SGL_ERR_ARG),        # B < 1
+    ((8, 0, 0, 0), sgl.SGL_ERR_ARG),        # batch < 1
+    ((8, 1, 9, 0), sgl.SGL_ERR_ARG),        # unknown precision
+    ((8, 1, 0, 5), sgl.SGL_ERR_ARG),        # unknown sample convention
+    ((8, 1, 1, 1), sgl.SGL_ERR_ARG),        # physical samples need FP64
+    ((17, 1, 0, 0), sgl.SGL_ERR_UNSUPPORTED),   # 2B = 2 * 17: odd factor > 16
+    ((129, 1, 0, 0), sgl.SGL_ERR_UNSUPPORTED),  # above SGL_MAX_B
+])
+def test_plan_argument_errors(lib, args, status):
+    h = ctypes.c_void_p(1234)
+    st = lib.sgl_plan(ctypes.byref(h), *args)
+    assert st == status
+    assert h.value is None
+    assert lib.sgl_last_error(None)
+
+
+def test_plan_many_argument_errors(lib):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int * 3)(8, 0, 16)
+    assert lib.sgl_plan_many(ctypes.byref(h), arr, 3, 2) == sgl.SGL_ERR_ARG
+    assert lib.sgl_plan_many(ctypes.byref(h), arr, 0, 2) == sgl.SGL_ERR_ARG
+    assert lib.sgl_plan_many(None, arr, 3, 2) == sgl.SGL_ERR_ARG
+
+
+def test_null_plan_queries(lib):
+    assert lib.sgl_sample_count(None) == -1
+    assert lib.sgl_coeff_offset(None, 0) == -1
+    assert lib.sgl_forward(None, None, None, None) == sgl.SGL_ERR_ARG
+    lib.sgl_destroy(None)
+
+
+def test_supported_bandlimits_match_header_rule():
+    # every B <= 16 and every multiple of 8 up to 128 (the header's rule)
+    from paper_1604_05140_gb300.inputs import uneven_bandlimits
+    for B in list(range(1, 17)) + list(range(8, 129, 8)):
+        n = 2 * B
+        p = 1
+        while p < 16 and n % (2 * p) == 0:
+            p *= 2
+        assert n // p <= 16, B
+    assert set(uneven_bandlimits()) <= set(range(16, 129, 8))
