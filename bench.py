@@ -1,0 +1,411 @@
+"""Benchmark: SGL inverse + forward transform throughput at B=128, batch 64.
+
+One step = one sgl_inverse followed by one sgl_forward over a batch of 64
+functions of bandlimit B=128 (coefficients complex normal with 1/n decay,
+seeded; the paper's experiment of Sect. 4 run as a batch).  The headline
+line is the split-precision path (TF32x3 tensor-core stages); the plain FP64
+GPU path is timed on the same workload and reported alongside.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs an independent replica of the batch (the
+transform of one function never needs another function's data), so the job
+scales weakly with no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SGL fwd+inv transforms/sec and coeffs/sec at B=128, FP64 vs split-precision"
+B_BENCH = 128
+BATCH = 64
+L2_BYTES = 129 * 1024 * 1024
+
+
+def omega_count(B):
+    return B * (B + 1) * (2 * B + 1) // 6
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes / flops per launch of each stage (whole batch)
+# ---------------------------------------------------------------------------
+
+def stage_model(B, NB, cbytes):
+    """Bytes each stage must move (its inputs and outputs, once) and flops.
+
+    cbytes: bytes of one complex element (16 FP64, 8 FP32).  Real element
+    rb = cbytes/2.  Per function: samples 4B^3 complex, coefficients Omega
+    complex, E/O (or G) spectra 4B^2(2B-1) reals, S spectra 2B^3 reals.
+    """
+    rb = cbytes // 2
+    samp = 4 * B ** 3 * cbytes
+    coef = omega_count(B) * cbytes
+    w1 = 4 * B * B * (2 * B - 1) * rb
+    w2 = 2 * B ** 3 * rb
+    n = 2 * B
+    fft_flops = B * (2 * B) * 5 * n * np.log2(n)  # B*2B rings, 5 N log2 N each
+    leg_flops = 0
+    for m in range(-(B - 1), B):
+        am = abs(m)
+        leg_flops += 2 * (B - am) * B * (2 * B)  # (B-|m|) rows, K=B (folded), 2B real columns (re,im of B shells)
+    rad_flops = 2 * 2 * B * omega_count(B)       # per coefficient: B-term complex x real sum
+    return {
+        "fft_forward": (NB * (samp + w1), NB * fft_flops),
+        "legendre_forward": (NB * (w1 + w2), NB * leg_flops),
+        "radial_forward": (NB * (w2 + coef), NB * rad_flops),
+        "radial_inverse": (NB * (coef + w2), NB * rad_flops),
+        "legendre_inverse": (NB * (w2 + w1), NB * leg_flops),
+        "fft_inverse": (NB * (w1 + samp), NB * fft_flops),
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smmax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smmax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smmax) if smmax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas)
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_sample(B=B_BENCH, budget_s=12.0, seed=1604051403):
+    """Times the FP64 oracle (inverse then forward) on whole functions of the
+    benchmark workload until about budget_s seconds have passed."""
+    import oracle as O
+    from paper_1604_05140_gb300 import inputs
+    O.legendre_table(B)
+    O.radial_table(B)  # tables are set-up, not part of a transform
+    n, t0 = 0, time.perf_counter()
+    while True:
+        c = inputs.random_coeffs(B, 1, seed=seed + n, decay=True)
+        O.forward(O.inverse(c, B), B)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        if info:
+            cores = max(i.get("num_threads", 1) for i in info)
+    except Exception:
+        pass
+    return {"value": n / dt, "unit": "transforms/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} whole functions of B={B} (inverse + forward each) out of the batch of {BATCH}, "
+                      f"{dt:.1f} s, FP64 NumPy separated form"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def time_path(precision, steps, warmup, ws, rank, profile=True):
+    import torch
+    from paper_1604_05140_gb300 import Plan, inputs, sgl
+
+    plan = Plan(B_BENCH, BATCH, precision)
+    lib = sgl.load_library()
+    c_np = inputs.random_coeffs(B_BENCH, BATCH, seed=inputs.BASE_SEED + 3 + 1000 * rank, decay=True)
+    c = torch.from_numpy(c_np).to(plan.dtype).cuda()
+    s = torch.empty(plan.sample_shape, dtype=plan.dtype, device="cuda")
+    c2 = torch.empty(plan.coeff_shape, dtype=plan.dtype, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.inverse(c, out=s)
+        plan.forward(s, out=c2)
+    torch.cuda.synchronize()
+    err = float((c2 - c).abs().max().item() / c.abs().max().item())
+    if profile:
+        lib.sgl_set_profiling(plan.handle, 1)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        plan.inverse(c, out=s)
+        plan.forward(s, out=c2)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / steps
+    stage = {}
+    if profile:
+        import ctypes
+        n = 6
+        tms = (ctypes.c_double * n)()
+        tl = (ctypes.c_int64 * n)()
+        lib.sgl_stage_times(plan.handle, tms, tl)
+        for k in range(n):
+            if tl[k]:
+                stage[lib.sgl_stage_name(k).decode()] = (tms[k] / tl[k], int(tl[k]))
+        lib.sgl_set_profiling(plan.handle, 0)
+    launches = plan.launches_per_call * 2 * steps
+    return plan, ms, stage, clocks, err, launches, (c_np, c, s, c2)
+
+
+def e2e_path(plan, c_np, steps, warmup):
+    """Same step through the C ABI with host buffers: pinned host coefficients
+    in, pinned host coefficients out; the library stages the copies."""
+    import torch
+    c_host = torch.from_numpy(c_np).to(plan.dtype).pin_memory()
+    out_host = torch.empty(plan.coeff_shape, dtype=plan.dtype).pin_memory()
+    s = torch.empty(plan.sample_shape, dtype=plan.dtype, device="cuda")
+    for _ in range(max(1, warmup)):
+        plan.inverse(c_host, out=s)
+        plan.forward(s, out=out_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        plan.inverse(c_host, out=s)
+        plan.forward(s, out=out_host)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    nbytes = c_host.numel() * c_host.element_size()
+    return dt, nbytes
+
+
+def roofline(stage, cbytes, prec):
+    hbm, src = peaks()
+    model = stage_model(B_BENCH, BATCH, cbytes)
+    dom = max(stage, key=lambda k: stage[k][0] * stage[k][1])
+    ms, nl = stage[dom]
+    nbytes, flops = model[dom]
+    out = {"kernel": dom, "bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+           "traffic": None, "peak_source": src, "launch_ms": ms,
+           "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
+           "stage_ms": {k: v[0] for k, v in stage.items()}}
+    out["frac"] = out["achieved"] / out["peak"]
+    return out
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    precs = [args.precision] + ([] if args.no_fp64 or args.precision == "fp64" else ["fp64"])
+    results = {}
+    for prec in precs:
+        steps = args.steps if prec != "fp64" else max(1, min(args.steps, args.fp64_steps))
+        plan, ms, stage, clocks, err, launches, bufs = time_path(prec, steps, args.warmup, ws, rank)
+        ms_max = allmax(ws, ms)
+        results[prec] = dict(plan=plan, ms=ms_max, stage=stage, clocks=clocks, err=err, launches=launches,
+                             steps=steps, bufs=bufs)
+    head = results[args.precision]
+    plan = head["plan"]
+    cbytes = 16 if args.precision == "fp64" else 8
+    value = ws * BATCH / (head["ms"] * 1e-3)
+    rl = roofline(head["stage"], cbytes, args.precision)
+    e2e_dt, nbytes = e2e_path(plan, head["bufs"][0], max(2, min(args.steps, 5)), 1)
+    e2e_dt = allmax(ws, e2e_dt)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "transforms/s",
+        "n_gpus": ws,
+        "steps": head["steps"],
+        "warmup": args.warmup,
+        "ms_per_step": head["ms"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3+f32acc"}[args.precision],
+        "data": "synthetic: seeded complex-normal SGL coefficients with 1/n decay, synthesized to samples by the inverse",
+        "config": {"workload": f"SGL inverse+forward, B={B_BENCH}, batch {BATCH} functions per GPU",
+                   "B": B_BENCH, "batch": BATCH, "precision": args.precision,
+                   "samples_bytes_per_function": 4 * B_BENCH ** 3 * cbytes,
+                   "l2": "inputs larger than L2 (samples 4.3 GB per batch in FP32, 8.6 GB in FP64)",
+                   "parallelism": f"replicas x{ws}"},
+        "coeffs_per_s": value * omega_count(B_BENCH),
+        "round_trip_max_rel_err": head["err"],
+        "roofline": rl,
+        "e2e": {"value": ws * BATCH / e2e_dt, "unit": "transforms/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": head["launches"],
+        "clocks": head["clocks"],
+    }
+    if "fp64" in results and args.precision != "fp64":
+        r = results["fp64"]
+        line["fp64_path"] = {"value": ws * BATCH / (r["ms"] * 1e-3), "unit": "transforms/s", "ms_per_step": r["ms"],
+                             "steps": r["steps"], "round_trip_max_rel_err": r["err"],
+                             "stage_ms": {k: v[0] for k, v in r["stage"].items()}, "clocks": r["clocks"]}
+        line["split_vs_fp64"] = line["value"] / line["fp64_path"]["value"]
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample(budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # each step: one whole function of the workload (inverse + forward) in the oracle
+    import oracle as O
+    from paper_1604_05140_gb300 import inputs
+    O.legendre_table(B_BENCH)
+    O.radial_table(B_BENCH)
+    for w in range(args.warmup):
+        c = inputs.random_coeffs(B_BENCH, 1, seed=7 + w, decay=True)
+        O.forward(O.inverse(c, B_BENCH), B_BENCH)
+    times = []
+    for k in range(args.steps):
+        c = inputs.random_coeffs(B_BENCH, 1, seed=inputs.BASE_SEED + 3 + k, decay=True)
+        t0 = time.perf_counter()
+        O.forward(O.inverse(c, B_BENCH), B_BENCH)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = 1.0 / (ms * 1e-3)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"SGL inverse+forward, B={B_BENCH}, batch {BATCH} functions per GPU",
+                   "B": B_BENCH, "batch": BATCH, "precision": "fp64 (oracle)",
+                   "step_sample": "one function of the batch per step"},
+        "cpu_baseline": {"value": value, "unit": "transforms/s", "cores": cores, "kind": "oracle",
+                         "sample": "one whole function of B=128 per step (inverse + forward), FP64 NumPy"},
+        "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

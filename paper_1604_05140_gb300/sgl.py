@@ -72,6 +72,9 @@ def load_library():
         "sgl_last_error": (ctypes.c_char_p, [vp]),
         "sgl_destroy": (None, [vp]),
         "sgl_version": (ctypes.c_char_p, []),
+        "sgl_set_profiling": (i32, [vp, i32]),
+        "sgl_stage_times": (i32, [vp, vp, vp]),
+        "sgl_stage_name": (ctypes.c_char_p, [i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
