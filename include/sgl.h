@@ -185,6 +185,48 @@ const char* sgl_last_error(sgl_plan_t plan);
 /* Release the plan, its tables and its workspace.  NULL is ignored. */
 void sgl_destroy(sgl_plan_t plan);
 
+/*
+ * sgl_forward_noalloc - the FP64 forward transform (same result as
+ * sgl_forward on an FP64, weighted-samples plan of the same B and batch),
+ * for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this entry point exists for deployment.
+ *
+ * Who needs it: code that must not call cudaMalloc once it is running, e.g.
+ * a host application whose device memory is owned by its own allocator or a
+ * fixed budget, a plugin running inside such an application, or a real-time
+ * loop where an allocation could block on the device.  Creating a plan
+ * allocates tables and workspace; this call does not: its scratch lives in a
+ * static device array compiled into the library (16 MiB of doubles), and its
+ * tables and launch schedules in a second static array (8 MiB).  Every GPU
+ * that loads the library holds both arrays until the process exits.
+ *
+ *   B        bandlimit, 1 <= B <= 32 (and the factor rule of SGL_MAX_B).
+ *   batch    functions, >= 1, with 4 B^2 (2B-1) + 2 B^3 doubles of scratch per
+ *            function fitting the 2^21-double scratch: B = 32 allows 6
+ *            functions, B = 16 allows 52, B = 8 allows 431.  Larger requests
+ *            return SGL_ERR_UNSUPPORTED with a message saying how much
+ *            scratch they need.
+ *   samples  device pointer, batch x 4B^3 complex doubles (weighted samples).
+ *   coeffs   device pointer, batch x Omega complex doubles; overwritten.
+ *            Host pointers are rejected (SGL_ERR_ARG): staging them would
+ *            need device memory.
+ *   stream   stream the kernels are launched on.
+ *
+ * Set-up: the first call on a device looks up the device addresses of the
+ * two static arrays (cudaGetSymbolAddress, with that device current), and a
+ * call whose (B, batch) differs from the previous call on that device copies
+ * the new tables into the static array and synchronizes `stream`.  Make such
+ * calls before any stream capture.
+ *
+ * Sharing: every call on a device uses the same scratch and table arrays,
+ * which keep the last call's contents.  Calls whose kernels overlap on the GPU
+ * (different streams, or different (B, batch) while earlier work still runs)
+ * race on them.  Nothing in the scratch has to start at zero: each stage
+ * writes every element the next stage reads.  On failure the message is
+ * available from sgl_last_error(NULL).
+ */
+sgl_status sgl_forward_noalloc(int B, int batch, const void* samples, void* coeffs, sgl_stream_t stream);
+
 /* Library version string. */
 const char* sgl_version(void);
 

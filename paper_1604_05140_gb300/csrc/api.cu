@@ -23,6 +23,11 @@ using namespace sgl;
 
 static std::string g_create_error;
 
+namespace sgl {
+// Message returned by sgl_last_error(NULL).
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace sgl
+
 static sgl_status fail(Plan* P, sgl_status st, const std::string& msg) {
   if (P) P->err = msg; else g_create_error = msg;
   return st;
@@ -70,7 +75,7 @@ static void release(Plan* P) {
 }
 
 template <typename real>
-static void pack_tables(const Plan& P, std::vector<real>& tab) {
+void sgl::pack_tables(const Plan& P, std::vector<real>& tab) {
   tab.assign(P.tab_elems, real(0));
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
@@ -114,6 +119,9 @@ static void pack_tables(const Plan& P, std::vector<real>& tab) {
     }
   }
 }
+
+template void sgl::pack_tables<double>(const Plan& P, std::vector<double>& tab);
+template void sgl::pack_tables<float>(const Plan& P, std::vector<float>& tab);
 
 static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) {
   cudaGetDevice(&P->device);

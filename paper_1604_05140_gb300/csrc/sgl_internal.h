@@ -194,6 +194,11 @@ struct StageTimer {
   }
 };
 
+// Packs the host tables of every segment of P into one array of the plan's
+// real type, at the offsets recorded in the segment descriptors (api.cu).
+template <typename real>
+void pack_tables(const Plan& P, std::vector<real>& tab);
+
 // Stage launchers (kernels.cu)
 cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights);
 cudaError_t run_inverse(Plan& P, const void* coeffs, void* samples, cudaStream_t s, bool weights);

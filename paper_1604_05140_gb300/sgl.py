@@ -75,6 +75,7 @@ def load_library():
         "sgl_set_profiling": (i32, [vp, i32]),
         "sgl_stage_times": (i32, [vp, vp, vp]),
         "sgl_stage_name": (ctypes.c_char_p, [i32]),
+        "sgl_forward_noalloc": (i32, [i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
