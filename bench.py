@@ -390,6 +390,7 @@ def run_reference(args):
 
 
 def main():
+    global BATCH
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -400,7 +401,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="functions per GPU (64 is the benchmark workload; smaller only for profiling runs)")
     args = ap.parse_args()
+    BATCH = args.batch
     if args.impl == "reference":
         run_reference(args)
     else:

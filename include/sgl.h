@@ -77,7 +77,7 @@ typedef enum {
   SGL_FP32 = 1,    /* every stage in single precision on the CUDA cores */
   SGL_TF32X3 = 2   /* FP32 FFT; Legendre and radial stages on tcgen05 tensor
                       cores as three TF32 products (hi*hi + hi*lo + lo*hi)
-                      with FP32 accumulation */
+                      with FP32 accumulation; bandlimits divisible by 4 */
 } sgl_precision;
 
 typedef enum {

@@ -362,6 +362,8 @@ sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples) {
   if (samples == SGL_SAMPLES_PHYSICAL && prec != SGL_FP64)
     return fail(nullptr, SGL_ERR_ARG, "physical samples need an FP64 plan");
   if (!bandlimit_supported(B)) return fail(nullptr, SGL_ERR_UNSUPPORTED, "unsupported bandlimit");
+  if (prec == SGL_TF32X3 && B % 4 != 0)
+    return fail(nullptr, SGL_ERR_UNSUPPORTED, "SGL_TF32X3 plans need a bandlimit divisible by 4");
   Plan* P = new Plan();
   P->prec = prec;
   P->samples = samples;
@@ -385,6 +387,8 @@ sgl_status sgl_plan_many(sgl_plan_t* out, const int* B_per_fn, int nfn, int prec
   for (int B : Bs) {
     if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
     if (!bandlimit_supported(B)) return fail(nullptr, SGL_ERR_UNSUPPORTED, "unsupported bandlimit");
+    if (prec == SGL_TF32X3 && B % 4 != 0)
+      return fail(nullptr, SGL_ERR_UNSUPPORTED, "SGL_TF32X3 plans need bandlimits divisible by 4");
   }
   Plan* P = new Plan();
   P->prec = prec;

@@ -1,0 +1,325 @@
+// phi-FFT kernels for ring lengths 2B = 16 * N2 with N2 in {8, 16}
+// (B = 64 and B = 128), the four-step form of the inner sum of
+// Eq. (SFFT_rearranged):
+//   X[k1 + 16 k2] = sum_{n2} W_N^{n2 k1} W_{N2}^{n2 k2} sum_{n1} x[N2 n1 + n2] W_16^{n1 k1}.
+//
+// Data path: HBM -> registers (16 independent loads per thread) -> 16-point
+// FFT -> one XOR-swizzled shared-memory transpose -> N2-point FFT -> HBM.
+// A CTA owns one shell (b, i) and JP ring pairs (theta_j, theta_{2B-1-j});
+// the forward kernel emits E = G_j + G_mirror and O = G_j - G_mirror directly
+// from registers, the inverse kernel gathers its spectra from the Legendre
+// synthesis output.  The general kernels in kernels.cu cover every other 2B.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sgl_internal.h"
+
+namespace sgl {
+
+namespace {
+
+template <typename real>
+struct c2 {
+  real x, y;
+};
+
+template <typename real>
+__device__ __forceinline__ c2<real> operator+(c2<real> a, c2<real> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename real>
+__device__ __forceinline__ c2<real> operator-(c2<real> a, c2<real> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename real>
+__device__ __forceinline__ c2<real> cmul(c2<real> a, c2<real> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// cos(2 pi k / 16), k < 16
+constexpr double kCos16[16] = {
+    1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173,
+    0.0, -0.38268343236508977173, -0.70710678118654752440, -0.92387953251128675613,
+    -1.0, -0.92387953251128675613, -0.70710678118654752440, -0.38268343236508977173,
+    0.0, 0.38268343236508977173, 0.70710678118654752440, 0.92387953251128675613};
+
+// v * e^{-2 pi i K / N} (INV: e^{+...}) for compile-time K, N (N | 16 * something)
+template <typename real, int K, int N, bool INV>
+__device__ __forceinline__ c2<real> rot(c2<real> v) {
+  constexpr int k = ((K % N) + N) % N;
+  if constexpr (k == 0) {
+    return v;
+  } else if constexpr (4 * k == N) {  // -i (forward), +i (inverse)
+    return INV ? c2<real>{-v.y, v.x} : c2<real>{v.y, -v.x};
+  } else if constexpr (2 * k == N) {
+    return {-v.x, -v.y};
+  } else if constexpr (4 * k == 3 * N) {  // +i forward
+    return INV ? c2<real>{v.y, -v.x} : c2<real>{-v.y, v.x};
+  } else {
+    // angle 2 pi k / N = 2 pi (16 k / N) / 16 when N divides 16 k
+    static_assert((16 * k) % N == 0, "twiddle not on the 16-point circle");
+    constexpr int q = 16 * k / N;
+    constexpr double cd = kCos16[q];
+    constexpr double sd = kCos16[(q + 12) % 16];  // sin(x) = cos(x - pi/2)
+    const real c = (real)cd;
+    const real s = (real)sd;
+    const real sn = INV ? s : -s;
+    return {v.x * c - v.y * sn, v.x * sn + v.y * c};
+  }
+}
+
+template <int N, int I>
+struct BitRev {
+  static constexpr int LOG = N == 2 ? 1 : N == 4 ? 2 : N == 8 ? 3 : 4;
+  static constexpr int value() {
+    int j = 0;
+    for (int b = 0; b < LOG; ++b) j |= ((I >> b) & 1) << (LOG - 1 - b);
+    return j;
+  }
+};
+
+template <typename real, int N, bool INV, int LEN, int START, int Q>
+__device__ __forceinline__ void bfly(c2<real>* v) {
+  c2<real> a = v[START + Q];
+  c2<real> b = rot<real, Q * (N / LEN), N, INV>(v[START + Q + LEN / 2]);
+  v[START + Q] = a + b;
+  v[START + Q + LEN / 2] = a - b;
+}
+
+template <typename real, int N, bool INV, int LEN, int START, int Q>
+__device__ __forceinline__ void stage_q(c2<real>* v) {
+  if constexpr (Q < LEN / 2) {
+    bfly<real, N, INV, LEN, START, Q>(v);
+    stage_q<real, N, INV, LEN, START, Q + 1>(v);
+  }
+}
+
+template <typename real, int N, bool INV, int LEN, int START>
+__device__ __forceinline__ void stage_s(c2<real>* v) {
+  if constexpr (START < N) {
+    stage_q<real, N, INV, LEN, START, 0>(v);
+    stage_s<real, N, INV, LEN, START + LEN>(v);
+  }
+}
+
+template <typename real, int N, bool INV, int LEN>
+__device__ __forceinline__ void stages(c2<real>* v) {
+  if constexpr (LEN <= N) {
+    stage_s<real, N, INV, LEN, 0>(v);
+    stages<real, N, INV, LEN * 2>(v);
+  }
+}
+
+template <typename real, int N, int I>
+__device__ __forceinline__ void bitrev_perm(c2<real>* v) {
+  if constexpr (I < N) {
+    constexpr int J = BitRev<N, I>::value();
+    if constexpr (I < J) {
+      c2<real> t = v[I];
+      v[I] = v[J];
+      v[J] = t;
+    }
+    bitrev_perm<real, N, I + 1>(v);
+  }
+}
+
+// In-register N-point DFT (N = 8 or 16), natural order in and out.
+template <typename real, int N, bool INV>
+__device__ __forceinline__ void fft_n(c2<real>* v) {
+  bitrev_perm<real, N, 0>(v);
+  stages<real, N, INV, 2>(v);
+}
+
+// Shared-memory position (complex units) of row `row` (< 16), column `col`
+// (< N2) of ring r: rows of N2 columns, XOR swizzle by row and ring pair so
+// that both the column-wise writes and the row-wise reads are conflict-free.
+template <int N2>
+__device__ __forceinline__ int spos(int r, int row, int col) {
+  return r * (16 * N2) + row * N2 + ((col ^ row ^ (r >> 1)) & (N2 - 1));
+}
+
+}  // namespace
+
+// Forward: samples -> E/O spectra.  blockDim = 16 * JP.
+template <typename real, int N2>
+__global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
+  constexpr int N = 16 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);      // W_N^k, k < N
+  c2<real>* buf = tw + N;                                    // 2*JP rings of N
+  const int4 cta = a.ctas[blockIdx.x];
+  const SegDesc sg = a.segs[cta.x];
+  const int B = sg.B, NB = sg.NB;
+  const int shell = cta.y, j0 = cta.z;
+  const int b = shell / B, i = shell - b * B;
+  const int JPmax = a.JP;
+  const int JP = min(JPmax, B - j0);
+  const int R = 2 * JP;
+  const real* misc = reinterpret_cast<const real*>(a.tab) + sg.tab_misc;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = {misc[5 * B + 2 * k], misc[5 * B + 2 * k + 1]};
+  real scale = 1;
+  if (a.mode == 1) scale = misc[B + i];
+  if (a.mode == 2) scale = misc[2 * B + i];
+  const c2<real>* in = reinterpret_cast<const c2<real>*>(a.in) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
+  __syncthreads();
+
+  // step A: items (r, n2), n2 fastest; 16-point DFT over n1, twiddle, store
+  constexpr int PER = N2 / 8;  // (2*JP rings x N2 columns) / (16*JP threads)
+  c2<real> v[PER][16];
+  int rr[PER], cc[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int item = threadIdx.x + u * blockDim.x;
+    rr[u] = item / N2;
+    cc[u] = item % N2;
+    if (rr[u] < R) {
+      const int q = rr[u] >> 1;
+      const int j = (rr[u] & 1) ? (N - 1 - (j0 + q)) : (j0 + q);
+      const c2<real>* ring = in + (int64_t)j * N + cc[u];
+#pragma unroll
+      for (int n1 = 0; n1 < 16; ++n1) v[u][n1] = ring[n1 * N2];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    if (rr[u] < R) {
+#pragma unroll
+      for (int n1 = 0; n1 < 16; ++n1) v[u][n1] = {v[u][n1].x * scale, v[u][n1].y * scale};
+      fft_n<real, 16, false>(v[u]);
+#pragma unroll
+      for (int k1 = 1; k1 < 16; ++k1) v[u][k1] = cmul(v[u][k1], tw[cc[u] * k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) buf[spos<N2>(rr[u], k1, cc[u])] = v[u][k1];
+    }
+  }
+  __syncthreads();
+
+  // step B: items (q, k1), q fastest; N2-point DFT over n2 of both rings of
+  // the pair, then E/O straight to global memory
+  const int q = threadIdx.x % JPmax;
+  const int k1 = threadIdx.x / JPmax;
+  if (q < JP && k1 < 16) {
+    c2<real> x0[N2], x1[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+      x0[n2] = buf[spos<N2>(2 * q, k1, n2)];
+      x1[n2] = buf[spos<N2>(2 * q + 1, k1, n2)];
+    }
+    fft_n<real, N2, false>(x0);
+    fft_n<real, N2, false>(x1);
+    real* w1 = reinterpret_cast<real*>(a.w1) + sg.w1_off;
+    const int64_t sp = (int64_t)NB * 2 * B * B;               // stride of p
+    const int64_t sm = 2 * sp;                                // stride of m_idx
+    const int64_t base = (((int64_t)b * 2) * B + i) * B + j0 + q;  // c = 0, p = 0, m_idx = 0
+    const int64_t sc = (int64_t)B * B;                        // stride of c
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int k = k1 + 16 * k2;
+      if (k == B) continue;  // Nyquist: not a coefficient
+      const int m = k < B ? k : k - N;
+      const int64_t o = base + (int64_t)(m + B - 1) * sm;
+      const c2<real> e = x0[k2] + x1[k2];
+      const c2<real> d = x0[k2] - x1[k2];
+      w1[o] = e.x;
+      w1[o + sc] = e.y;
+      w1[o + sp] = d.x;
+      w1[o + sp + sc] = d.y;
+    }
+  }
+}
+
+// Inverse: G spectra -> samples.  blockDim = 16 * JP.
+template <typename real, int N2>
+__global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
+  constexpr int N = 16 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);
+  c2<real>* buf = tw + N;
+  const int4 cta = a.ctas[blockIdx.x];
+  const SegDesc sg = a.segs[cta.x];
+  const int B = sg.B, NB = sg.NB;
+  const int shell = cta.y, j0 = cta.z;
+  const int b = shell / B, i = shell - b * B;
+  const int JPmax = a.JP;
+  const int JP = min(JPmax, B - j0);
+  const int R = 2 * JP;
+  const real* misc = reinterpret_cast<const real*>(a.tab) + sg.tab_misc;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = {misc[5 * B + 2 * k], misc[5 * B + 2 * k + 1]};
+  __syncthreads();
+
+  // step 1: items (q, k1); gather X[k1 + 16 k2] of both rings, inverse
+  // N2-point DFT over k2, twiddle W_N^{-n2 k1}, store row k1
+  const int q = threadIdx.x % JPmax;
+  const int k1 = threadIdx.x / JPmax;
+  if (q < JP && k1 < 16) {
+    const real* g = reinterpret_cast<const real*>(a.w1) + sg.w1_off;
+    const int64_t sc = (int64_t)B * N;              // stride of c
+    const int64_t sm = (int64_t)NB * 2 * B * N;     // stride of m_idx
+    const int64_t base = (((int64_t)b * 2) * B + i) * N;
+    const int jA = j0 + q, jB = N - 1 - (j0 + q);
+    c2<real> x0[N2], x1[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int k = k1 + 16 * k2;
+      if (k == B) {
+        x0[k2] = {0, 0};
+        x1[k2] = {0, 0};
+      } else {
+        const int m = k < B ? k : k - N;
+        const int64_t o = base + (int64_t)(m + B - 1) * sm;
+        x0[k2] = {g[o + jA], g[o + sc + jA]};
+        x1[k2] = {g[o + jB], g[o + sc + jB]};
+      }
+    }
+    fft_n<real, N2, true>(x0);
+    fft_n<real, N2, true>(x1);
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+      c2<real> w = tw[n2 * k1];
+      w.y = -w.y;
+      buf[spos<N2>(2 * q, k1, n2)] = cmul(x0[n2], w);
+      buf[spos<N2>(2 * q + 1, k1, n2)] = cmul(x1[n2], w);
+    }
+  }
+  __syncthreads();
+
+  // step 2: items (r, n2), n2 fastest; inverse 16-point DFT over k1 -> x[N2 n1 + n2]
+  real si = 1;
+  if (a.mode == 1) si = misc[2 * B + i];
+  if (a.mode == 2) si = misc[i];
+  if (a.mode == 3) si = misc[i] * misc[B + i];
+  c2<real>* out = reinterpret_cast<c2<real>*>(a.out) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
+  for (int item = threadIdx.x; item < R * N2; item += blockDim.x) {
+    const int r = item / N2, n2 = item % N2;
+    c2<real> v[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) v[kk] = buf[spos<N2>(r, kk, n2)];
+    fft_n<real, 16, true>(v);
+    const int qq = r >> 1;
+    const int j = (r & 1) ? (N - 1 - (j0 + qq)) : (j0 + qq);
+    real s = si;
+    if (a.mode >= 2) s *= misc[3 * B + j];
+    c2<real>* ring = out + (int64_t)j * N + n2;
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) ring[n1 * N2] = {v[n1].x * s, v[n1].y * s};
+  }
+}
+
+// Launch helper: returns false when (n1, n2) is not handled here.
+template <typename real>
+bool fft16_launch(bool inv, const Fft16Args& a, int n1, int n2, int nctas, cudaStream_t s, cudaError_t* err) {
+  if (n1 != 16 || (n2 != 16 && n2 != 8)) return false;
+  const int N = 16 * n2;
+  const size_t smem = sizeof(c2<real>) * ((size_t)N + (size_t)2 * a.JP * N);
+  void (*fn)(Fft16Args) = nullptr;
+  if (n2 == 16) fn = inv ? fft16_inv_kernel<real, 16> : fft16_fwd_kernel<real, 16>;
+  else fn = inv ? fft16_inv_kernel<real, 8> : fft16_fwd_kernel<real, 8>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    fn<<<nctas, 16 * a.JP, smem, s>>>(a);
+    e = cudaGetLastError();
+  }
+  *err = e;
+  return true;
+}
+
+template bool fft16_launch<float>(bool, const Fft16Args&, int, int, int, cudaStream_t, cudaError_t*);
+template bool fft16_launch<double>(bool, const Fft16Args&, int, int, int, cudaStream_t, cudaError_t*);
+
+}  // namespace sgl

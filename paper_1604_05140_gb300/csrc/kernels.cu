@@ -598,6 +598,14 @@ static cudaError_t run_fft(Plan& P, bool inv, const void* in, void* out, int mod
     a.w1 = P.d_w1;
     a.JP = fft_pairs_per_cta(P.prec, f.B);
     a.mode = mode;
+    {
+      Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode};
+      cudaError_t e16 = cudaSuccess;
+      if (fft16_launch<real>(inv, a16, f.n1, f.n2, f.count, s, &e16)) {
+        if (e16 != cudaSuccess) return e16;
+        continue;
+      }
+    }
     size_t smem = fft_smem_bytes<real>(f.n1, f.n2, f.B, a.JP);
     cudaError_t e = inv ? launch_fft_t<real, true>(P, a, f.n1, f.n2, f.count, smem, s)
                         : launch_fft_t<real, false>(P, a, f.n1, f.n2, f.count, smem, s);
@@ -662,6 +670,13 @@ static cudaError_t inverse_t(Plan& P, const void* coeffs, void* samples, cudaStr
   if (weights) mode = (P.samples == SGL_SAMPLES_PHYSICAL) ? 3 : 2;
   else if (P.samples == SGL_SAMPLES_PHYSICAL) mode = 1;
   return run_fft<real>(P, true, nullptr, samples, mode, s);
+}
+
+// FP32 CUDA-core GEMM of one stage with the plan's SIMT schedule (the
+// tensor-core path uses it for the stages it does not cover).
+cudaError_t run_gemm_f32(Plan& P, int prob, const void* x, void* y, int weighted, cudaStream_t s) {
+  const GemmSched* sch[4] = {&P.leg_fwd, &P.rad_fwd, &P.rad_inv, &P.leg_inv};
+  return run_gemm<float>(P, prob, *sch[prob], x, y, weighted, s);
 }
 
 cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights) {

@@ -149,6 +149,7 @@ struct Plan {
   int4* d_fft_inv = nullptr;
   int n_fft_fwd = 0, n_fft_inv = 0;
   int launches_per_call = 0;
+  void* tc_state = nullptr;      // tensor-core stage state (tc_gemm.cu)
 
   // stage timing (sgl_set_profiling): event pairs per stage, and a free pool
   bool profiling = false;
@@ -193,6 +194,25 @@ struct StageTimer {
     }
   }
 };
+
+// Arguments of the specialized phi-FFT kernels for 2B = 16 * N2, N2 in {8, 16}
+// (fft16.cu).  mode: forward 0 none, 1 *exp(-t/2), 2 *exp(+t/2); inverse
+// 0 none, 1 *exp(+t/2), 2 *what*beta, 3 *what*beta*exp(-t/2).
+struct Fft16Args {
+  const SegDesc* segs;
+  const int64_t* fn_samp;
+  const int4* ctas;      // (segment, shell, j'0, 0)
+  const void* tab;
+  const void* in;
+  void* out;
+  void* w1;
+  int JP;                // ring pairs per CTA; blockDim = 16 * JP
+  int mode;
+};
+// Launches the specialized kernel when (n1, n2) = (16, 8) or (16, 16) and
+// returns true (launch status in *err); returns false otherwise.
+template <typename real>
+bool fft16_launch(bool inv, const Fft16Args& a, int n1, int n2, int nctas, cudaStream_t s, cudaError_t* err);
 
 // Packs the host tables of every segment of P into one array of the plan's
 // real type, at the offsets recorded in the segment descriptors (api.cu).

@@ -1,25 +1,704 @@
-// TF32x3 tensor-core stages (tcgen05) of the SGL transform.
+// TF32x3 tensor-core stages (tcgen05, TMEM, TMA) of the SGL transform.
+//
+// Forward Legendre stage (Eq. DLT, one GEMM per order m and theta-parity p)
+// and forward radial stage (Eq. DRT_matrix, one GEMM per degree l):
+//   D[row][n] = sum_k X[row][k] A[n][k]
+// X: the stage's FP32 input rows (E/O spectra, or per-degree spectra), K-major;
+// A: the FP64 table rounded to a hi + lo pair of TF32 values.  Three TF32
+// products per K step, X_hi A_hi + X_hi A_lo + X_lo A_hi, accumulate in FP32 in
+// tensor memory (the lo*lo term is below FP32 round-off).
+//
+// One persistent CTA per SM, warp-specialized (320 threads):
+//   warp 0      TMA producer: 128-row x 32-float X chunks (SWIZZLE_128B) into a
+//               4-stage ring; the group's pre-swizzled hi/lo table by bulk copy
+//   warp 1      TMEM owner and MMA issuer (one thread): 3 x 4 tcgen05.mma per chunk
+//   warps 2-5   split: X -> hi (in place, cvt.rna.tf32) and lo = X - hi
+//   warps 6-9   epilogue: tcgen05.ld of the double-buffered accumulator, sign,
+//               scatter to the next stage's layout
+// Every wait on an mbarrier is bounded: after ~2 s the CTA sets the plan's
+// error flag, stops, and frees its tensor memory.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
 
 #include "sgl_internal.h"
 
 namespace sgl {
 
-cudaError_t tc_prepare(Plan& P) {
-  (void)P;
-  return cudaErrorNotSupported;
+// SIMT launcher of the inverse stages (kernels.cu)
+cudaError_t run_gemm_f32(Plan& P, int prob, const void* x, void* y, int weighted, cudaStream_t s);
+
+namespace {
+
+enum { TC_LEG_F = 0, TC_RAD_F = 1 };
+
+// pipeline depth: the Legendre table (<= 64 rows) leaves room for 4 stages,
+// the radial table (<= 128 rows) for 2
+constexpr int kStagesLeg = 4;
+constexpr int kStagesRad = 2;
+constexpr int kChunkBytes = 128 * 128;  // 128 rows x 32 floats
+constexpr int kThreads = 320;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-void tc_release(Plan& P) { (void)P; }
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity.  On timeout, or when another
+// role already aborted, returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > kWaitNs) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// K-major, 128-byte swizzled operand: 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);       // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+  return d;
+}
+
+// kind::tf32 instruction descriptor: D f32, A and B tf32, both K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ int64_t omega_of(int n, int l, int m) {
+  return (int64_t)n * (n - 1) * (2 * n - 1) / 6 + (int64_t)l * (l + 1) + m;
+}
+
+}  // namespace
+
+struct TcArgs {
+  const int2* tiles;            // (group, row0) in group order
+  int ntiles;
+  const unsigned char* tabimg;  // pre-swizzled hi/lo tables
+  const int64_t* grp_off;       // byte offset of each group's image (weighted set, then plain set)
+  const int* grp_npad;          // padded N of each group
+  int ngroups;
+  void* y;
+  const int64_t* fn_coef;
+  int* err;
+  int B, NB, KC;
+  int weighted;
+  int64_t w2_off;
+  int npmax;
+};
+
+template <int PROB, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap xmap, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int KC = a.KC;
+  const int tab_bytes = 2 * KC * a.npmax * 128;            // hi + lo for the largest group
+  unsigned char* tab = base;                                 // [hi: KC][npad][128 B] [lo: same]
+  unsigned char* xs = base + tab_bytes;                      // STAGES x (hi 16 KB, lo 16 KB)
+  uint64_t* bars = (uint64_t*)(xs + STAGES * 2 * kChunkBytes);
+  uint64_t* full = bars;                 // [STAGES] TMA landed
+  uint64_t* split = bars + STAGES;      // [STAGES] hi/lo ready (128 arrivals)
+  uint64_t* empty = bars + 2 * STAGES;  // [STAGES] MMAs done with the stage
+  uint64_t* accf = bars + 3 * STAGES;   // [2] accumulator complete
+  uint64_t* acce = accf + 2;             // [2] accumulator drained (128 arrivals)
+  uint64_t* tabf = acce + 2;             // table landed
+  uint64_t* tabe = tabf + 1;             // table no longer read
+  uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < (uint32_t)(2 * a.npmax)) tmem_cols <<= 1;  // power of two >= 32
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(split + s, 128);
+      mbar_init(empty + s, 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(accf + k, 1);
+      mbar_init(acce + k, 128);
+    }
+    mbar_init(tabf, 1);
+    mbar_init(tabe, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // contiguous tile range of this CTA
+  const int t_begin = (int)((int64_t)a.ntiles * blockIdx.x / gridDim.x);
+  const int t_end = (int)((int64_t)a.ntiles * (blockIdx.x + 1) / gridDim.x);
+  const int B = a.B, NB = a.NB;
+  const int64_t wsel = a.weighted ? 0 : a.ngroups;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int cur = -1, ngrp = 0;
+      uint32_t c = 0;
+      for (int t = t_begin; t < t_end && !*abort_flag; ++t) {
+        const int2 tl = a.tiles[t];
+        if (tl.x != cur) {
+          if (ngrp > 0 && !mbar_wait(tabe, (ngrp - 1) & 1, abort_flag)) break;
+          const uint32_t bytes = (uint32_t)(2 * KC * a.grp_npad[tl.x] * 128);
+          mbar_arrive_tx(tabf, bytes);
+          bulk_load(tab, a.tabimg + a.grp_off[wsel + tl.x], bytes, tabf);
+          cur = tl.x;
+          ++ngrp;
+        }
+        // tensor rows of this tile
+        int64_t row;
+        if (PROB == TC_LEG_F) row = (int64_t)tl.x * NB * 2 * B + tl.y;
+        else row = (int64_t)NB * 2 * tl.x * tl.x + tl.y;
+        for (int kc = 0; kc < KC; ++kc, ++c) {
+          const int s = c % STAGES;
+          if (!mbar_wait(empty + s, ((c / STAGES) & 1) ^ 1, abort_flag)) break;
+          mbar_arrive_tx(full + s, kChunkBytes);
+          tma_load_2d(xs + s * 2 * kChunkBytes, &xmap, full + s, kc * 32, (int)row);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int cur = -1, ngrp = 0;
+      uint32_t c = 0, tcount = 0;
+      for (int t = t_begin; t < t_end && !*abort_flag; ++t, ++tcount) {
+        const int2 tl = a.tiles[t];
+        if (tl.x != cur) {
+          if (!mbar_wait(tabf, ngrp & 1, abort_flag)) break;
+          cur = tl.x;
+          ++ngrp;
+        }
+        const int npad = a.grp_npad[tl.x];
+        const uint32_t idesc = idesc_tf32(npad);
+        const int acc = tcount & 1;
+        if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
+        tc_after();
+        const uint32_t d = tmem + (uint32_t)(acc * a.npmax);
+        const uint32_t tab_hi = smem_u32(tab);
+        const uint32_t tab_lo = tab_hi + (uint32_t)(KC * npad * 128);
+        bool ok = true;
+        for (int kc = 0; kc < KC; ++kc, ++c) {
+          const int s = c % STAGES;
+          if (!mbar_wait(split + s, (c / STAGES) & 1, abort_flag)) { ok = false; break; }
+          tc_after();
+          const uint32_t xh = smem_u32(xs + s * 2 * kChunkBytes);
+          const uint32_t xl = xh + kChunkBytes;
+          const uint32_t th = tab_hi + (uint32_t)(kc * npad * 128);
+          const uint32_t tlo = tab_lo + (uint32_t)(kc * npad * 128);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t koff = (uint32_t)(kk * 32);
+            const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
+            mma_tf32(d, sw128_desc(xh + koff), sw128_desc(th + koff), idesc, first);
+            mma_tf32(d, sw128_desc(xh + koff), sw128_desc(tlo + koff), idesc, 1u);
+            mma_tf32(d, sw128_desc(xl + koff), sw128_desc(th + koff), idesc, 1u);
+          }
+          mma_commit(empty + s);
+        }
+        if (!ok) break;
+        mma_commit(accf + acc);
+        const bool last_of_group = (t + 1 >= t_end) || (a.tiles[t + 1].x != cur);
+        if (last_of_group) mma_commit(tabe);
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------- split: X -> (hi, lo) ----------------
+    const int tid = threadIdx.x - 64;  // 0..127
+    uint32_t c = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+      bool ok = true;
+      for (int kc = 0; kc < KC; ++kc, ++c) {
+        const int s = c % STAGES;
+        if (!mbar_wait(full + s, (c / STAGES) & 1, abort_flag)) { ok = false; break; }
+        float4* hi = (float4*)(xs + s * 2 * kChunkBytes);
+        float4* lo = (float4*)(xs + s * 2 * kChunkBytes + kChunkBytes);
+#pragma unroll
+        for (int v = 0; v < kChunkBytes / 16 / 128; ++v) {
+          const int idx = v * 128 + tid;
+          float4 x = hi[idx];
+          float4 h = {tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w)};
+          // lo rounded to TF32 too, so that the tensor core uses it unchanged
+          float4 l = {tf32_rna(x.x - h.x), tf32_rna(x.y - h.y), tf32_rna(x.z - h.z), tf32_rna(x.w - h.w)};
+          hi[idx] = h;
+          lo[idx] = l;
+        }
+        fence_proxy_async();
+        mbar_arrive(split + s);
+      }
+      if (!ok) break;
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
+    const int r_in = quarter * 32 + lane;       // tile row of this thread
+    uint32_t tcount = 0;
+    float* Y = reinterpret_cast<float*>(a.y);
+    for (int t = t_begin; t < t_end; ++t, ++tcount) {
+      const int2 tl = a.tiles[t];
+      const int acc = tcount & 1;
+      if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
+      tc_after();
+      const int npad = a.grp_npad[tl.x];
+      const uint32_t taddr = tmem + (uint32_t)(acc * a.npmax) + ((uint32_t)(quarter * 32) << 16);
+      const int grow = tl.y + r_in;
+      if (PROB == TC_LEG_F) {
+        const int g = tl.x;
+        const int m_idx = g >> 1, p = g & 1;
+        const int m = m_idx - (B - 1);
+        const int am = m < 0 ? -m : m;
+        const int ncol = (am + p >= B) ? 0 : (B - 1 - am - p) / 2 + 1;
+        const float sgn = (m < 0 && (am & 1)) ? -1.f : 1.f;
+        const bool valid = grow < NB * 2 * B;
+        const int b = grow / (2 * B), cc = (grow / B) & 1, i = grow % B;
+        for (int c0 = 0; c0 < npad; c0 += 16) {
+          float v[16];
+          tmem_ld16(taddr + (uint32_t)c0, v);
+          if (valid) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int col = c0 + k;
+              if (col < ncol) {
+                const int l = am + p + 2 * col;
+                Y[a.w2_off + (int64_t)NB * 2 * B * l * l + (((int64_t)b * (2 * l + 1) + (m + l)) * 2 + cc) * B + i] =
+                    sgn * v[k];
+              }
+            }
+          }
+        }
+      } else {
+        const int l = tl.x;
+        const int per_b = (2 * l + 1) * 2;
+        const bool valid = grow < NB * per_b;
+        const int b = grow / per_b;
+        const int rem = grow - b * per_b;
+        const int mm = rem >> 1, cc = rem & 1;
+        const int ncol = B - l;
+        const int64_t cbase = valid ? a.fn_coef[b] : 0;
+        for (int c0 = 0; c0 < npad; c0 += 16) {
+          float v[16];
+          tmem_ld16(taddr + (uint32_t)c0, v);
+          if (valid) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int col = c0 + k;
+              if (col < ncol) Y[2 * (cbase + omega_of(l + 1 + col, l, mm - l)) + cc] = v[k];
+            }
+          }
+        }
+      }
+      tc_before();
+      mbar_arrive(acce + acc);
+    }
+  }
+
+  __syncthreads();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    // let copies and MMAs already issued drain before the memory is released
+    const uint64_t t0 = gtimer();
+    while (gtimer() - t0 < 20000000ull) {
+    }
+  }
+  tc_after();
+  if (warp == 1) tmem_dealloc(tmem, tmem_cols);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TcStage {
+  CUtensorMap xmap;
+  int2* d_tiles = nullptr;
+  int ntiles = 0;
+  int64_t* d_off = nullptr;
+  int* d_npad = nullptr;
+  int ngroups = 0;
+  int npmax = 0;
+  int KC = 0;
+  size_t smem = 0;
+  int grid = 0;
+};
+
+struct TcSeg {
+  TcStage leg, rad;
+};
+
+struct TcState {
+  std::vector<TcSeg> segs;
+  unsigned char* d_img = nullptr;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D FP32 tensor [rows][B] with 128-row x 32-float boxes, 128-byte swizzle.
+bool make_xmap(CUtensorMap* map, void* base, int B, int64_t rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)B, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)B * 4};
+  cuuint32_t box[2] = {32, 128};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+uint32_t rna_tf32_bits(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  return u;
+}
+
+// Append the swizzled hi/lo image of a table A[n][k] (n < N, k < K; zero
+// padded to npad rows and KC*32 columns).
+void append_image(std::vector<unsigned char>& img, int N, int K, int npad, int KC,
+                  const std::vector<double>& A /* N x K */) {
+  const size_t off = img.size();
+  const size_t plane = (size_t)KC * npad * 128;
+  img.resize(off + 2 * plane, 0);
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k) {
+      const double v = A[(size_t)n * K + k];
+      const float f = (float)v;
+      const uint32_t hb = rna_tf32_bits(f);
+      float hi;
+      memcpy(&hi, &hb, 4);
+      const uint32_t lb = rna_tf32_bits((float)(v - (double)hi));
+      float lo;
+      memcpy(&lo, &lb, 4);
+      const int kc = k / 32, kin = k % 32;
+      const int chunk = kin / 4, w = kin % 4;
+      const size_t pos = (size_t)kc * npad * 128 + (size_t)n * 128 + (size_t)((chunk ^ (n & 7)) * 16) + w * 4;
+      memcpy(&img[off + pos], &hi, 4);
+      memcpy(&img[off + plane + pos], &lo, 4);
+    }
+}
+
+int pad16(int n) { return n <= 16 ? 16 : (n + 15) / 16 * 16; }
+
+}  // namespace
+
+cudaError_t tc_prepare(Plan& P) {
+  if (!get_encode()) return cudaErrorNotSupported;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  TcState* st = new TcState();
+  std::vector<unsigned char> img;
+  struct Pending {
+    std::vector<int64_t> off;
+    std::vector<int> npad;
+    std::vector<int2> tiles;
+  };
+  std::vector<Pending> pend;
+  for (size_t s = 0; s < P.segs.size(); ++s) {
+    const SegDesc& sg = P.segs[s];
+    const HostTables& H = P.tables[s];
+    const int B = sg.B, NB = sg.NB;
+    const int KC = (B + 31) / 32;
+    TcSeg ts;
+    // Legendre: groups g = m_idx*2 + p; images per (|m|, p), shared by +-m
+    Pending pl;
+    pl.off.assign(2 * 2 * (2 * B - 1), 0);
+    pl.npad.assign(2 * (2 * B - 1), 16);
+    int npmax = 16;
+    for (int w = 0; w < 2; ++w) {
+      std::vector<int64_t> am_off(2 * B, -1);
+      for (int am = 0; am < B; ++am)
+        for (int p = 0; p < 2; ++p) {
+          const int N = n_par(B, am, p);
+          if (N == 0) continue;
+          const int np = pad16(N);
+          npmax = np > npmax ? np : npmax;
+          std::vector<double> A((size_t)N * B);
+          for (int q = 0; q < N; ++q) {
+            const int l = am + p + 2 * q;
+            for (int j = 0; j < B; ++j) {
+              const double v = H.lam[((size_t)am * B + l) * B + j];
+              A[(size_t)q * B + j] = w == 0 ? H.beta[j] * v : v;
+            }
+          }
+          img.resize((img.size() + 1023) / 1024 * 1024);
+          am_off[am * 2 + p] = (int64_t)img.size();
+          append_image(img, N, B, np, KC, A);
+        }
+      for (int mi = 0; mi < 2 * B - 1; ++mi) {
+        const int m = mi - (B - 1);
+        const int am = m < 0 ? -m : m;
+        for (int p = 0; p < 2; ++p) {
+          const int g = mi * 2 + p;
+          pl.off[w * 2 * (2 * B - 1) + g] = am_off[am * 2 + p] < 0 ? 0 : am_off[am * 2 + p];
+          pl.npad[g] = pad16(n_par(B, am, p));
+        }
+      }
+    }
+    for (int mi = 0; mi < 2 * B - 1; ++mi) {
+      const int m = mi - (B - 1);
+      const int am = m < 0 ? -m : m;
+      for (int p = 0; p < 2; ++p) {
+        if (n_par(B, am, p) == 0) continue;
+        for (int r0 = 0; r0 < NB * 2 * B; r0 += 128) pl.tiles.push_back(make_int2(mi * 2 + p, r0));
+      }
+    }
+    ts.leg.ngroups = 2 * (2 * B - 1);
+    ts.leg.npmax = npmax;
+    ts.leg.KC = KC;
+    // radial: groups l
+    Pending pr;
+    pr.off.assign(2 * B, 0);
+    pr.npad.assign(B, 16);
+    int npmax_r = 16;
+    for (int w = 0; w < 2; ++w)
+      for (int l = 0; l < B; ++l) {
+        const int N = B - l;
+        const int np = pad16(N);
+        npmax_r = np > npmax_r ? np : npmax_r;
+        std::vector<double> A((size_t)N * B);
+        for (int q = 0; q < N; ++q)
+          for (int i = 0; i < B; ++i) {
+            const double v = H.T[((size_t)l * B + (l + q)) * B + i];
+            A[(size_t)q * B + i] = w == 0 ? H.what[i] * v : v;
+          }
+        img.resize((img.size() + 1023) / 1024 * 1024);
+        pr.off[w * B + l] = (int64_t)img.size();
+        pr.npad[l] = np;
+        append_image(img, N, B, np, KC, A);
+      }
+    for (int l = 0; l < B; ++l)
+      for (int r0 = 0; r0 < NB * (2 * l + 1) * 2; r0 += 128) pr.tiles.push_back(make_int2(l, r0));
+    ts.rad.ngroups = B;
+    ts.rad.npmax = npmax_r;
+    ts.rad.KC = KC;
+    // tensor maps over the segment's workspaces
+    float* w1 = (float*)P.d_w1 + sg.w1_off;
+    float* w2 = (float*)P.d_w2 + sg.w2_off;
+    if (!make_xmap(&ts.leg.xmap, w1, B, (int64_t)(2 * B - 1) * 2 * NB * 2 * B) ||
+        !make_xmap(&ts.rad.xmap, w2, B, (int64_t)2 * NB * B * B)) {
+      delete st;
+      return cudaErrorInvalidValue;
+    }
+    st->segs.push_back(ts);
+    pend.push_back(pl);
+    pend.push_back(pr);
+  }
+  cudaError_t e = cudaMalloc(&st->d_img, img.size());
+  if (e != cudaSuccess) { delete st; return e; }
+  P.bytes += img.size();
+  e = cudaMemcpy(st->d_img, img.data(), img.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { delete st; return e; }
+  for (size_t s = 0; s < st->segs.size(); ++s) {
+    TcStage* stg[2] = {&st->segs[s].leg, &st->segs[s].rad};
+    for (int k = 0; k < 2; ++k) {
+      Pending& pd = pend[2 * s + k];
+      TcStage& S = *stg[k];
+      S.ntiles = (int)pd.tiles.size();
+      e = cudaMalloc(&S.d_tiles, pd.tiles.size() * sizeof(int2));
+      if (e == cudaSuccess) e = cudaMemcpy(S.d_tiles, pd.tiles.data(), pd.tiles.size() * sizeof(int2),
+                                           cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMalloc(&S.d_off, pd.off.size() * sizeof(int64_t));
+      if (e == cudaSuccess) e = cudaMemcpy(S.d_off, pd.off.data(), pd.off.size() * sizeof(int64_t),
+                                           cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMalloc(&S.d_npad, pd.npad.size() * sizeof(int));
+      if (e == cudaSuccess) e = cudaMemcpy(S.d_npad, pd.npad.data(), pd.npad.size() * sizeof(int),
+                                           cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) { delete st; return e; }
+      const int stages = k == 0 ? kStagesLeg : kStagesRad;
+      S.smem = 1024 + (size_t)2 * S.KC * S.npmax * 128 + (size_t)stages * 2 * kChunkBytes + 256;
+      S.grid = S.ntiles < nsm ? S.ntiles : nsm;
+      if (S.smem > 227 * 1024) { delete st; return cudaErrorInvalidValue; }
+    }
+  }
+  P.tc_state = st;
+  return cudaSuccess;
+}
+
+void tc_release(Plan& P) {
+  TcState* st = (TcState*)P.tc_state;
+  if (!st) return;
+  for (TcSeg& s : st->segs)
+    for (TcStage* S : {&s.leg, &s.rad}) {
+      if (S->d_tiles) cudaFree(S->d_tiles);
+      if (S->d_off) cudaFree(S->d_off);
+      if (S->d_npad) cudaFree(S->d_npad);
+    }
+  if (st->d_img) cudaFree(st->d_img);
+  delete st;
+  P.tc_state = nullptr;
+}
 
 int tc_launches(const Plan& P) {
-  (void)P;
-  return 4;
+  // GEMM launches per call, averaged over forward (2 per segment) and
+  // inverse (2 SIMT launches); FFT launches are counted by the caller
+  return (int)P.segs.size() + 1;
 }
 
 cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted, cudaStream_t s) {
-  (void)P; (void)prob; (void)x; (void)y; (void)weighted; (void)s;
-  return cudaErrorNotSupported;
+  if (prob != 0 && prob != 1) return run_gemm_f32(P, prob, x, y, weighted, s);
+  TcState* st = (TcState*)P.tc_state;
+  if (!st) return cudaErrorNotSupported;
+  static const int stage_of[2] = {ST_LEG_F, ST_RAD_F};
+  StageTimer timer(P, stage_of[prob], s);
+  for (size_t k = 0; k < st->segs.size(); ++k) {
+    TcStage& S = prob == 0 ? st->segs[k].leg : st->segs[k].rad;
+    if (S.ntiles == 0) continue;
+    const SegDesc& sg = P.segs[k];
+    TcArgs a;
+    a.tiles = S.d_tiles;
+    a.ntiles = S.ntiles;
+    a.tabimg = st->d_img;
+    a.grp_off = S.d_off;
+    a.grp_npad = S.d_npad;
+    a.ngroups = S.ngroups;
+    a.y = y;
+    a.fn_coef = P.d_fn_coef + sg.fn0;
+    a.err = P.d_err;
+    a.B = sg.B;
+    a.NB = sg.NB;
+    a.KC = S.KC;
+    a.weighted = weighted;
+    a.w2_off = sg.w2_off;
+    a.npmax = S.npmax;
+    (void)x;
+    void (*fn)(const CUtensorMap, TcArgs) =
+        prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg> : tc_gemm_kernel<TC_RAD_F, kStagesRad>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem);
+    if (e != cudaSuccess) return e;
+    fn<<<S.grid, kThreads, S.smem, s>>>(S.xmap, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  timer.finish();
+  return cudaSuccess;
 }
 
 }  // namespace sgl

@@ -203,3 +203,66 @@ def test_inputs_not_modified():
     s0 = s.clone()
     p.forward(s)
     assert torch.equal(c, c0) and torch.equal(s, s0)
+
+
+# ---------------------------------------------------------------------------
+# split precision: TF32x3 tensor-core stages
+# ---------------------------------------------------------------------------
+TF32X3_TOL = 2e-6   # three TF32 products (2^-22 per dropped term), FP32 accumulation and FFT
+
+
+@pytest.mark.parametrize("B", [4, 8, 16, 24, 32, 64])
+def test_tf32x3_vs_oracle(B):
+    p = _plan(B, 3, "tf32x3")
+    c = inputs.random_coeffs(B, 3, seed=7000 + B)
+    s_gpu = p.inverse(_dev(c, torch.complex64)).cpu().numpy()
+    assert _err(s_gpu, O.inverse(c, B)) < TF32X3_TOL
+    g = inputs.random_samples(B, 3, seed=8000 + B)
+    f_gpu = p.forward(_dev(g, torch.complex64)).cpu().numpy()
+    assert _err(f_gpu, O.forward(g.astype(np.complex64), B)) < TF32X3_TOL
+    back = p.forward(_dev(O.inverse(c, B), torch.complex64)).cpu().numpy()
+    assert _err(back, c) < TF32X3_TOL
+    p.check()
+
+
+def test_tf32x3_adjoints_vs_oracle():
+    B = 16
+    p = _plan(B, 2, "tf32x3")
+    y = inputs.random_coeffs(B, 2, seed=9100)
+    x = inputs.random_samples(B, 2, seed=9200)
+    a1 = p.adjoint(_dev(y, torch.complex64), of_inverse=False).cpu().numpy()
+    assert _err(a1, O.adjoint_forward(y, B)) < TF32X3_TOL
+    a2 = p.adjoint(_dev(x, torch.complex64), of_inverse=True).cpu().numpy()
+    assert _err(a2, O.adjoint_inverse(x.astype(np.complex64), B)) < TF32X3_TOL
+
+
+def test_tf32x3_uneven_bandlimits():
+    from paper_1604_05140_gb300 import Plan
+    Bs = [16, 40, 8, 24, 40, 64, 16, 128]
+    p = Plan.many(Bs, precision="tf32x3")
+    cs = [inputs.random_coeffs(B, 1, seed=950 + k)[0] for k, B in enumerate(Bs)]
+    s = p.inverse(_dev(np.concatenate(cs), torch.complex64))
+    f = p.forward(s).cpu().numpy()
+    s = s.cpu().numpy()
+    for k, B in enumerate(Bs):
+        so, co = p.sample_offset(k), p.coeff_offset(k)
+        sk = s[so:so + 4 * B ** 3].reshape(1, B, 2 * B, 2 * B)
+        assert _err(sk, O.inverse(cs[k], B)) < TF32X3_TOL, (k, B)
+        assert _err(f[co:co + O.coeff_count(B)][None], cs[k][None]) < TF32X3_TOL, (k, B)
+    p.check()
+
+
+def test_tf32x3_full_size_b128_sampled_functions():
+    # B=128, batch 64, the benchmark configuration; two functions checked
+    # completely against the oracle, all 64 through the round trip
+    B, NB = 128, 64
+    p = _plan(B, NB, "tf32x3")
+    c = inputs.random_coeffs(B, NB, seed=inputs.BASE_SEED + 3, decay=True)
+    s = p.inverse(_dev(c, torch.complex64))
+    f = p.forward(s).cpu().numpy()
+    assert _err(f, c) < TF32X3_TOL
+    for k in (0, NB - 1):
+        sk = s[k].cpu().numpy()
+        assert _err(sk[None], O.inverse(c[k], B)) < TF32X3_TOL
+        assert _err(f[k][None], O.forward(sk, B)) < TF32X3_TOL
+    p.check()
