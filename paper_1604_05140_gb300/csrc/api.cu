@@ -264,7 +264,18 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
   P->n_fft_fwd = P->n_fft_inv = (int)ff.size();
   e = dev_upload(*P, &P->d_fft_fwd, ff);
   if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
-  P->d_fft_inv = nullptr;
+  if (P->prec == SGL_TF32X3) {
+    // the tensor-core Legendre synthesis stores spectra [m][b][c][j][i]: each
+    // inverse-FFT CTA takes JP consecutive shells of one ring pair (layout 1)
+    ff.clear();
+    for (size_t s = 0; s < P->segs.size(); ++s) {
+      const SegDesc& sg = P->segs[s];
+      const int JP = fft_pairs_per_cta(P->prec, sg.B);
+      for (int b = 0; b < sg.NB; ++b)
+        for (int i0 = 0; i0 < sg.B; i0 += JP)
+          for (int jp = 0; jp < sg.B; ++jp) ff.push_back(make_int4((int)s, b * sg.B + i0, jp, 1));
+    }
+  }
   e = dev_upload(*P, &P->d_fft_inv, ff);
   if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
   for (const SegDesc& sg : P->segs) {

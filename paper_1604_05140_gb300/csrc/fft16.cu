@@ -234,10 +234,14 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
   const int4 cta = a.ctas[blockIdx.x];
   const SegDesc sg = a.segs[cta.x];
   const int B = sg.B, NB = sg.NB;
-  const int shell = cta.y, j0 = cta.z;
-  const int b = shell / B, i = shell - b * B;
+  // cta.w = 0: spectra stored [m][b][c][i][j]; the CTA owns shell i and ring
+  //            pairs j0 .. j0+JP-1 (cta.y = b*B + i, cta.z = j0);
+  // cta.w = 1: spectra stored [m][b][c][j][i]; the CTA owns shells
+  //            i0 .. i0+JP-1 and the single ring pair jp (cta.y = b*B + i0, cta.z = jp)
+  const int lay = cta.w;
+  const int b = cta.y / B, i_or_i0 = cta.y - b * B, j_or_jp = cta.z;
   const int JPmax = a.JP;
-  const int JP = min(JPmax, B - j0);
+  const int JP = min(JPmax, B - (lay ? i_or_i0 : j_or_jp));
   const int R = 2 * JP;
   const real* misc = reinterpret_cast<const real*>(a.tab) + sg.tab_misc;
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = {misc[5 * B + 2 * k], misc[5 * B + 2 * k + 1]};
@@ -249,10 +253,15 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
   const int k1 = threadIdx.x / JPmax;
   if (q < JP && k1 < 16) {
     const real* g = reinterpret_cast<const real*>(a.w1) + sg.w1_off;
-    const int64_t sc = (int64_t)B * N;              // stride of c
-    const int64_t sm = (int64_t)NB * 2 * B * N;     // stride of m_idx
-    const int64_t base = (((int64_t)b * 2) * B + i) * N;
-    const int jA = j0 + q, jB = N - 1 - (j0 + q);
+    const int iq = lay ? i_or_i0 + q : i_or_i0;
+    const int jA = lay ? j_or_jp : j_or_jp + q;
+    const int jB = N - 1 - jA;
+    // element (m_idx, c, j) of ring (b, iq): m_idx*sm + c*sc + base + j*sj
+    const int64_t sm = (int64_t)NB * 2 * B * N;
+    const int64_t sc = (int64_t)B * N;
+    const int64_t sj = lay ? B : 1;
+    const int64_t base = lay ? ((int64_t)b * 2 * B * N + iq) : ((((int64_t)b * 2) * B + iq) * N);
+    const int64_t oA = base + jA * sj, oB = base + jB * sj;
     c2<real> x0[N2], x1[N2];
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) {
@@ -262,9 +271,9 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
         x1[k2] = {0, 0};
       } else {
         const int m = k < B ? k : k - N;
-        const int64_t o = base + (int64_t)(m + B - 1) * sm;
-        x0[k2] = {g[o + jA], g[o + sc + jA]};
-        x1[k2] = {g[o + jB], g[o + sc + jB]};
+        const int64_t o = (int64_t)(m + B - 1) * sm;
+        x0[k2] = {g[o + oA], g[o + sc + oA]};
+        x1[k2] = {g[o + oB], g[o + sc + oB]};
       }
     }
     fft_n<real, N2, true>(x0);
@@ -280,11 +289,7 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
   __syncthreads();
 
   // step 2: items (r, n2), n2 fastest; inverse 16-point DFT over k1 -> x[N2 n1 + n2]
-  real si = 1;
-  if (a.mode == 1) si = misc[2 * B + i];
-  if (a.mode == 2) si = misc[i];
-  if (a.mode == 3) si = misc[i] * misc[B + i];
-  c2<real>* out = reinterpret_cast<c2<real>*>(a.out) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
+  c2<real>* out = reinterpret_cast<c2<real>*>(a.out) + a.fn_samp[sg.fn0 + b];
   for (int item = threadIdx.x; item < R * N2; item += blockDim.x) {
     const int r = item / N2, n2 = item % N2;
     c2<real> v[16];
@@ -292,10 +297,15 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
     for (int kk = 0; kk < 16; ++kk) v[kk] = buf[spos<N2>(r, kk, n2)];
     fft_n<real, 16, true>(v);
     const int qq = r >> 1;
-    const int j = (r & 1) ? (N - 1 - (j0 + qq)) : (j0 + qq);
-    real s = si;
+    const int i = lay ? i_or_i0 + qq : i_or_i0;
+    const int jq = lay ? j_or_jp : j_or_jp + qq;
+    const int j = (r & 1) ? (N - 1 - jq) : jq;
+    real s = 1;
+    if (a.mode == 1) s = misc[2 * B + i];
+    if (a.mode == 2) s = misc[i];
+    if (a.mode == 3) s = misc[i] * misc[B + i];
     if (a.mode >= 2) s *= misc[3 * B + j];
-    c2<real>* ring = out + (int64_t)j * N + n2;
+    c2<real>* ring = out + ((int64_t)i * N + j) * N + n2;
 #pragma unroll
     for (int n1 = 0; n1 < 16; ++n1) ring[n1 * N2] = {v[n1].x * s, v[n1].y * s};
   }

@@ -238,9 +238,12 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
   const SegDesc sg = a.segs[cta.x];
   const int B = sg.B, N = 2 * B, NB = sg.NB;
   const int n2 = sg.n2;
-  const int shell = cta.y, j0 = cta.z;
-  const int b = shell / B, i = shell - b * B;
-  const int JP = min(a.JP, B - j0);
+  // cta.w selects the spectra layout (see fft16_inv_kernel): 0 -> one shell
+  // i = cta.y % B and ring pairs j0 = cta.z ...; 1 -> shells i0 = cta.y % B ...
+  // and one ring pair jp = cta.z
+  const int lay = cta.w;
+  const int b = cta.y / B, i_or_i0 = cta.y - b * B, j0 = cta.z;
+  const int JP = min(a.JP, B - (lay ? i_or_i0 : j0));
   const int R = 2 * JP;
   const int pitch = ring_pitch(N1, n2);
   real* wre = reinterpret_cast<real*>(smem_raw);
@@ -252,7 +255,10 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
     wre[k] = misc[5 * B + 2 * k];
     wim[k] = misc[5 * B + 2 * k + 1];
   }
-  // ring r: r < JP -> j = j0 + r; r >= JP -> j = N - j0 - 2*JP + r (mirror run)
+  // ring r (layout 0): r < JP -> j = j0 + r; r >= JP -> j = N - j0 - 2*JP + r (mirror run)
+  // ring r (layout 1): shell i0 + (r mod JP), j = jp (r < JP) or N - 1 - jp
+  auto ring_i = [&](int r) { return lay ? i_or_i0 + (r < JP ? r : r - JP) : i_or_i0; };
+  auto ring_j = [&](int r) { return lay ? (r < JP ? j0 : N - 1 - j0) : (r < JP ? j0 + r : N - j0 - 2 * JP + r); };
   const real* g = reinterpret_cast<const real*>(a.w1) + sg.w1_off;
   // Nyquist bin (k = B) is zero
   for (int e = threadIdx.x; e < 2 * R; e += blockDim.x) {
@@ -267,26 +273,26 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
     const int c = rest & 1, m_idx = rest >> 1;
     const int m = m_idx - (B - 1);
     const int k = m >= 0 ? m : N + m;
-    const int j = r < JP ? j0 + r : N - j0 - 2 * JP + r;
-    const real v = g[((((int64_t)m_idx * NB + b) * 2 + c) * B + i) * N + j];
+    const int i = ring_i(r), j = ring_j(r);
+    const int64_t fc = (((int64_t)m_idx * NB + b) * 2 + c) * B * N;  // start of (m_idx, b, c)
+    const real v = g[fc + (lay ? (int64_t)j * B + i : (int64_t)i * N + j)];
     const int c1 = k / n2, c2 = k - c1 * n2;
     (c ? sim : sre)[r * pitch + c1 * (n2 + 1) + c2] = v;
   }
   __syncthreads();
   fft_rings<real, N1, N2C, true>(sre, sim, wre, wim, R, n2, N, pitch);
-  cx<real>* out = reinterpret_cast<cx<real>*>(a.out) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
-  real si = 1;
-  if (a.mode == 1) si = misc[2 * B + i];
-  if (a.mode == 2) si = misc[i];
-  if (a.mode == 3) si = misc[i] * misc[B + i];
+  cx<real>* out = reinterpret_cast<cx<real>*>(a.out) + a.fn_samp[sg.fn0 + b];
   for (int e = threadIdx.x; e < R * N; e += blockDim.x) {
     const int r = e / N, k = e - r * N;
-    const int j = r < JP ? j0 + r : N - j0 - 2 * JP + r;
+    const int i = ring_i(r), j = ring_j(r);
     const int slot = (k % N1) * (n2 + 1) + k / N1;
-    real s = si;
+    real s = 1;
+    if (a.mode == 1) s = misc[2 * B + i];
+    if (a.mode == 2) s = misc[i];
+    if (a.mode == 3) s = misc[i] * misc[B + i];
     if (a.mode >= 2) s *= misc[3 * B + j];
     cx<real> v = {sre[r * pitch + slot] * s, sim[r * pitch + slot] * s};
-    out[(int64_t)j * N + k] = v;
+    out[((int64_t)i * N + j) * N + k] = v;
   }
 }
 
@@ -670,13 +676,6 @@ static cudaError_t inverse_t(Plan& P, const void* coeffs, void* samples, cudaStr
   if (weights) mode = (P.samples == SGL_SAMPLES_PHYSICAL) ? 3 : 2;
   else if (P.samples == SGL_SAMPLES_PHYSICAL) mode = 1;
   return run_fft<real>(P, true, nullptr, samples, mode, s);
-}
-
-// FP32 CUDA-core GEMM of one stage with the plan's SIMT schedule (the
-// tensor-core path uses it for the stages it does not cover).
-cudaError_t run_gemm_f32(Plan& P, int prob, const void* x, void* y, int weighted, cudaStream_t s) {
-  const GemmSched* sch[4] = {&P.leg_fwd, &P.rad_fwd, &P.rad_inv, &P.leg_inv};
-  return run_gemm<float>(P, prob, *sch[prob], x, y, weighted, s);
 }
 
 cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights) {

@@ -149,7 +149,8 @@ struct Plan {
   int4* d_fft_inv = nullptr;
   int n_fft_fwd = 0, n_fft_inv = 0;
   int launches_per_call = 0;
-  void* tc_state = nullptr;      // tensor-core stage state (tc_gemm.cu)
+  void* tc_state = nullptr;      // tensor-core forward stage state (tc_gemm.cu)
+  void* tc_inv_state = nullptr;  // tensor-core inverse stage state (tc_inv.cu)
 
   // stage timing (sgl_set_profiling): event pairs per stage, and a free pool
   bool profiling = false;

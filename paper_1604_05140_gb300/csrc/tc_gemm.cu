@@ -26,11 +26,43 @@
 #include <vector>
 
 #include "sgl_internal.h"
+#include "tc_ptx.cuh"
 
 namespace sgl {
 
-// SIMT launcher of the inverse stages (kernels.cu)
-cudaError_t run_gemm_f32(Plan& P, int prob, const void* x, void* y, int weighted, cudaStream_t s);
+// inverse tensor-core stages (tc_inv.cu)
+cudaError_t tc_inv_prepare(Plan& P);
+void tc_inv_release(Plan& P);
+cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream_t s);
+
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D FP32 tensor map: `rows` rows of `inner` floats (row pitch inner*4 bytes),
+// boxes of box_inner x box_rows, zero fill outside the tensor.
+bool make_map_2d(CUtensorMap* map, void* base, uint64_t inner, uint64_t rows, uint32_t box_inner, uint32_t box_rows,
+                 CUtensorMapSwizzle sw) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)inner * 4};
+  cuuint32_t box[2] = {box_inner, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
 
 namespace {
 
@@ -42,140 +74,8 @@ constexpr int kStagesLeg = 4;
 constexpr int kStagesRad = 2;
 constexpr int kChunkBytes = 128 * 128;  // 128 rows x 32 floats
 constexpr int kThreads = 320;
-constexpr uint64_t kWaitNs = 2000000000ull;
 
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase of the given parity.  On timeout, or when another
-// role already aborted, returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = gtimer();
-  while (true) {
-    if (mbar_try(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtimer() - t0 > kWaitNs) {
-      *abort_flag = 1;
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// K-major, 128-byte swizzled operand: 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);       // start address
-  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
-  d |= (uint64_t)1 << 46;                        // descriptor version
-  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
-  return d;
-}
-
-// kind::tf32 instruction descriptor: D f32, A and B tf32, both K-major, M = 128.
-__device__ __forceinline__ uint32_t idesc_tf32(int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ int64_t omega_of(int n, int l, int m) {
-  return (int64_t)n * (n - 1) * (2 * n - 1) / 6 + (int64_t)l * (l + 1) + m;
-}
-
+using namespace tcx;
 }  // namespace
 
 struct TcArgs {
@@ -212,10 +112,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   uint64_t* tabe = tabf + 1;             // table no longer read
   uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  // per-CTA copies of the tile slice and of the group metadata, so that no
+  // role waits on a global load per tile
+  int64_t* s_off = (int64_t*)(bars + 64);                 // [ngroups] table image offsets
+  int* s_npad = (int*)(s_off + a.ngroups);                 // [ngroups] padded N
+  int2* s_tiles = (int2*)(((uintptr_t)(s_npad + a.ngroups) + 7) & ~(uintptr_t)7);  // [max_tiles]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per tile: a main accumulator (hi*hi) and a correction accumulator
+  // (hi*lo + lo*hi), double-buffered.  The tensor cores round partial sums
+  // toward zero; keeping the small corrections apart cuts the number of
+  // truncating additions into the large accumulator by three, and the two are
+  // added with round-to-nearest in the epilogue.
+  // With NMAIN = 2 the hi*hi products of even and odd K steps go to two main
+  // accumulators, halving the truncating additions again (Legendre stage,
+  // whose accumulators are at most 64 columns wide).
+  constexpr int NMAIN = (PROB == TC_LEG_F) ? 2 : 1;
+  constexpr int NACC = NMAIN + 1;
   uint32_t tmem_cols = 32;
-  while (tmem_cols < (uint32_t)(2 * a.npmax)) tmem_cols <<= 1;  // power of two >= 32
+  while (tmem_cols < (uint32_t)(2 * NACC * a.npmax)) tmem_cols <<= 1;  // power of two >= 32
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -233,16 +148,21 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
+  // contiguous tile range of this CTA (re-based to 0 in shared memory)
+  const int g_begin = (int)((int64_t)a.ntiles * blockIdx.x / gridDim.x);
+  const int g_end = (int)((int64_t)a.ntiles * (blockIdx.x + 1) / gridDim.x);
+  const int t_begin = 0, t_end = g_end - g_begin;
+  const int64_t wsel = a.weighted ? 0 : a.ngroups;
+  for (int k = threadIdx.x; k < t_end; k += blockDim.x) s_tiles[k] = a.tiles[g_begin + k];
+  for (int k = threadIdx.x; k < a.ngroups; k += blockDim.x) {
+    s_off[k] = a.grp_off[wsel + k];
+    s_npad[k] = a.grp_npad[k];
+  }
   tc_before();
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
-
-  // contiguous tile range of this CTA
-  const int t_begin = (int)((int64_t)a.ntiles * blockIdx.x / gridDim.x);
-  const int t_end = (int)((int64_t)a.ntiles * (blockIdx.x + 1) / gridDim.x);
   const int B = a.B, NB = a.NB;
-  const int64_t wsel = a.weighted ? 0 : a.ngroups;
 
   if (warp == 0) {
     // ---------------- producer ----------------
@@ -250,12 +170,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       int cur = -1, ngrp = 0;
       uint32_t c = 0;
       for (int t = t_begin; t < t_end && !*abort_flag; ++t) {
-        const int2 tl = a.tiles[t];
+        const int2 tl = s_tiles[t];
         if (tl.x != cur) {
           if (ngrp > 0 && !mbar_wait(tabe, (ngrp - 1) & 1, abort_flag)) break;
-          const uint32_t bytes = (uint32_t)(2 * KC * a.grp_npad[tl.x] * 128);
+          const uint32_t bytes = (uint32_t)(2 * KC * s_npad[tl.x] * 128);
           mbar_arrive_tx(tabf, bytes);
-          bulk_load(tab, a.tabimg + a.grp_off[wsel + tl.x], bytes, tabf);
+          bulk_load(tab, a.tabimg + s_off[tl.x], bytes, tabf);
           cur = tl.x;
           ++ngrp;
         }
@@ -277,18 +197,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       int cur = -1, ngrp = 0;
       uint32_t c = 0, tcount = 0;
       for (int t = t_begin; t < t_end && !*abort_flag; ++t, ++tcount) {
-        const int2 tl = a.tiles[t];
+        const int2 tl = s_tiles[t];
         if (tl.x != cur) {
           if (!mbar_wait(tabf, ngrp & 1, abort_flag)) break;
           cur = tl.x;
           ++ngrp;
         }
-        const int npad = a.grp_npad[tl.x];
+        const int npad = s_npad[tl.x];
         const uint32_t idesc = idesc_tf32(npad);
         const int acc = tcount & 1;
         if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
         tc_after();
-        const uint32_t d = tmem + (uint32_t)(acc * a.npmax);
+        // buffer acc: [main 0][main 1 (NMAIN = 2)][correction], npmax columns each
+        const uint32_t d = tmem + (uint32_t)(NACC * acc * a.npmax);
+        const uint32_t dc = d + (uint32_t)(NMAIN * a.npmax);
         const uint32_t tab_hi = smem_u32(tab);
         const uint32_t tab_lo = tab_hi + (uint32_t)(KC * npad * 128);
         bool ok = true;
@@ -304,15 +226,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t koff = (uint32_t)(kk * 32);
             const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
-            mma_tf32(d, sw128_desc(xh + koff), sw128_desc(th + koff), idesc, first);
-            mma_tf32(d, sw128_desc(xh + koff), sw128_desc(tlo + koff), idesc, 1u);
-            mma_tf32(d, sw128_desc(xl + koff), sw128_desc(th + koff), idesc, 1u);
+            const uint32_t dm = d + (uint32_t)((kk % NMAIN) * a.npmax);
+            const uint32_t first_m = (kc > 0 || kk >= NMAIN) ? 1u : 0u;
+            mma_tf32(dm, sw128_desc(xh + koff), sw128_desc(th + koff), idesc, first_m);
+            mma_tf32(dc, sw128_desc(xh + koff), sw128_desc(tlo + koff), idesc, first);
+            mma_tf32(dc, sw128_desc(xl + koff), sw128_desc(th + koff), idesc, 1u);
           }
           mma_commit(empty + s);
         }
         if (!ok) break;
         mma_commit(accf + acc);
-        const bool last_of_group = (t + 1 >= t_end) || (a.tiles[t + 1].x != cur);
+        const bool last_of_group = (t + 1 >= t_end) || (s_tiles[t + 1].x != cur);
         if (last_of_group) mma_commit(tabe);
       }
     }
@@ -349,12 +273,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     uint32_t tcount = 0;
     float* Y = reinterpret_cast<float*>(a.y);
     for (int t = t_begin; t < t_end; ++t, ++tcount) {
-      const int2 tl = a.tiles[t];
+      const int2 tl = s_tiles[t];
       const int acc = tcount & 1;
       if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
       tc_after();
-      const int npad = a.grp_npad[tl.x];
-      const uint32_t taddr = tmem + (uint32_t)(acc * a.npmax) + ((uint32_t)(quarter * 32) << 16);
+      const int npad = s_npad[tl.x];
+      const uint32_t taddr = tmem + (uint32_t)(NACC * acc * a.npmax) + ((uint32_t)(quarter * 32) << 16);
+      const uint32_t tcorr = taddr + (uint32_t)(NMAIN * a.npmax);
+      const uint32_t tmain1 = taddr + (uint32_t)a.npmax;  // second main (NMAIN = 2)
       const int grow = tl.y + r_in;
       if (PROB == TC_LEG_F) {
         const int g = tl.x;
@@ -367,7 +293,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int b = grow / (2 * B), cc = (grow / B) & 1, i = grow % B;
         for (int c0 = 0; c0 < npad; c0 += 16) {
           float v[16];
-          tmem_ld16(taddr + (uint32_t)c0, v);
+          tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
+          if (NMAIN == 2) {
+            float w[16];
+            tmem_ld16(tmain1 + (uint32_t)c0, w);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] += w[k];
+          }
           if (valid) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -391,7 +323,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int64_t cbase = valid ? a.fn_coef[b] : 0;
         for (int c0 = 0; c0 < npad; c0 += 16) {
           float v[16];
-          tmem_ld16(taddr + (uint32_t)c0, v);
+          tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
+          if (NMAIN == 2) {
+            float w[16];
+            tmem_ld16(tmain1 + (uint32_t)c0, w);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] += w[k];
+          }
           if (valid) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -445,31 +383,9 @@ struct TcState {
   unsigned char* d_img = nullptr;
 };
 
-PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
-}
-
 // 2-D FP32 tensor [rows][B] with 128-row x 32-float boxes, 128-byte swizzle.
 bool make_xmap(CUtensorMap* map, void* base, int B, int64_t rows) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
-  if (!enc) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)B, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)B * 4};
-  cuuint32_t box[2] = {32, 128};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
+  return make_map_2d(map, base, (uint64_t)B, (uint64_t)rows, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 uint32_t rna_tf32_bits(float x) {
@@ -633,16 +549,20 @@ cudaError_t tc_prepare(Plan& P) {
                                            cudaMemcpyHostToDevice);
       if (e != cudaSuccess) { delete st; return e; }
       const int stages = k == 0 ? kStagesLeg : kStagesRad;
-      S.smem = 1024 + (size_t)2 * S.KC * S.npmax * 128 + (size_t)stages * 2 * kChunkBytes + 256;
       S.grid = S.ntiles < nsm ? S.ntiles : nsm;
+      const int max_tiles = (S.ntiles + S.grid - 1) / S.grid + 1;
+      // tables, X ring, 64 barrier/flag slots, group metadata, tile slice
+      S.smem = 1024 + (size_t)2 * S.KC * S.npmax * 128 + (size_t)stages * 2 * kChunkBytes + 64 * 8 +
+               (size_t)S.ngroups * 12 + 8 + (size_t)max_tiles * 8;
       if (S.smem > 227 * 1024) { delete st; return cudaErrorInvalidValue; }
     }
   }
   P.tc_state = st;
-  return cudaSuccess;
+  return tc_inv_prepare(P);
 }
 
 void tc_release(Plan& P) {
+  tc_inv_release(P);
   TcState* st = (TcState*)P.tc_state;
   if (!st) return;
   for (TcSeg& s : st->segs)
@@ -657,13 +577,13 @@ void tc_release(Plan& P) {
 }
 
 int tc_launches(const Plan& P) {
-  // GEMM launches per call, averaged over forward (2 per segment) and
-  // inverse (2 SIMT launches); FFT launches are counted by the caller
-  return (int)P.segs.size() + 1;
+  // GEMM launches per call (forward or inverse): two stages, one launch per
+  // segment each; FFT launches are counted by the caller
+  return 2 * (int)P.segs.size();
 }
 
 cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted, cudaStream_t s) {
-  if (prob != 0 && prob != 1) return run_gemm_f32(P, prob, x, y, weighted, s);
+  if (prob != 0 && prob != 1) return run_tc_inverse(P, prob, x, y, s);
   TcState* st = (TcState*)P.tc_state;
   if (!st) return cudaErrorNotSupported;
   static const int stage_of[2] = {ST_LEG_F, ST_RAD_F};

@@ -1,0 +1,741 @@
+// TF32x3 tensor-core inverse stages (tcgen05, TMEM, TMA) of the SGL transform.
+//
+// Inverse radial stage (iDRT, R_l^T of Sect. 3.3.2), one GEMM per degree l:
+//   S[i][col] = sum_{n'} T_{l+1+n',l}(i) fhat[col][n'],  col = (b, m, c)
+//   A operand: the table, M = 128 rows i, streamed per K chunk by bulk copy;
+//   B operand: coefficients gathered by the split warps (N = 128 columns).
+//   Output rows i are contiguous in the Legendre stage's input layout.
+// Inverse Legendre stage (the inner sum of Eq. iSFFT_rearranged), one tile
+// per (m, 128 rows (b, c, i)) with both theta-parities:
+//   P[row][j'] = sum_{l' even} S[row][l'] Lambda(theta_j'),  Q likewise for odd,
+//   G_j' = P + Q,  G_{2B-1-j'} = P - Q   (Lambda(pi - theta) = (-1)^{l+m} Lambda(theta)).
+//   A operand: S rows, loaded l'-major by TMA into a staging buffer and
+//   transposed to K-major hi/lo by the split warps; B operand: the table.
+// Same role layout as the forward kernels: warp 0 producer, warp 1 TMEM owner
+// and MMA issuer, warps 2-5 split, warps 6-9 epilogue; bounded waits.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "sgl_internal.h"
+#include "tc_ptx.cuh"
+
+namespace sgl {
+
+using namespace tcx;
+
+namespace {
+constexpr int kThreadsInv = 320;
+constexpr int kChunk = 128 * 128;   // 128 rows x 32 floats
+constexpr int kStagesLegI = 2;
+constexpr int kStagesRadI = 3;
+
+// 128-byte swizzled K-major position of (row, 16-byte chunk q) in a tile
+__device__ __forceinline__ int sw_pos(int row, int q) { return row * 128 + ((q ^ (row & 7)) << 4); }
+
+__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, int row, const float* v) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float4 h, l;
+    h.x = tf32_rna(v[4 * q + 0]);
+    h.y = tf32_rna(v[4 * q + 1]);
+    h.z = tf32_rna(v[4 * q + 2]);
+    h.w = tf32_rna(v[4 * q + 3]);
+    l.x = tf32_rna(v[4 * q + 0] - h.x);
+    l.y = tf32_rna(v[4 * q + 1] - h.y);
+    l.z = tf32_rna(v[4 * q + 2] - h.z);
+    l.w = tf32_rna(v[4 * q + 3] - h.w);
+    *(float4*)(hi + sw_pos(row, q)) = h;
+    *(float4*)(lo + sw_pos(row, q)) = l;
+  }
+}
+}  // namespace
+
+// ===========================================================================
+// inverse Legendre
+// ===========================================================================
+// Accumulators: the tensor cores round partial sums toward zero, so each
+// result keeps a main accumulator (hi*hi) and a correction accumulator
+// (hi*lo + lo*hi), added with round-to-nearest in the epilogue.  For the
+// Legendre synthesis (P and Q, main and correction) the j' range is cut in
+// halves of 64 columns so that two tiles' accumulators fit tensor memory; the
+// second half re-reads its rows from L2.
+struct LegIArgs {
+  const int2* tiles;          // (m_idx, row0 | j'-half), grouped by m_idx
+  int ntiles;
+  const unsigned char* tabimg;
+  const int64_t* am_off;      // image offset per |m|
+  const int* am_kc;           // KC_P | KC_Q << 8 per |m|
+  const int64_t* si_rows;     // S row offset per (m_idx, p)
+  float* g;                   // output, layout [m_idx][b][c][j < 2B][i]
+  int* err;
+  int B, NB, npad, kcmax;
+};
+
+__global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid_constant__ CUtensorMap smap,
+                                                                    LegIArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int B = a.B, NB = a.NB, npad = a.npad;
+  const int chunk_tab = npad * 128;                        // one table chunk (hi or lo)
+  unsigned char* tab = base;                               // [P hi][P lo][Q hi][Q lo]
+  unsigned char* stg = tab + (size_t)a.kcmax * 2 * chunk_tab;   // staging: 32 l' x 128 rows
+  unsigned char* xs = stg + kChunk;                        // stages x (hi, lo)
+  uint64_t* bars = (uint64_t*)(xs + kStagesLegI * 2 * kChunk);
+  uint64_t* stgf = bars;                  // staging landed
+  uint64_t* stge = bars + 1;              // staging read (128)
+  uint64_t* split = bars + 2;             // [S] hi/lo ready (128)
+  uint64_t* empty = split + kStagesLegI;  // [S] MMAs done
+  uint64_t* accf = empty + kStagesLegI;   // [2]
+  uint64_t* acce = accf + 2;              // [2] (128)
+  uint64_t* tabf = acce + 2;
+  uint64_t* tabe = tabf + 1;
+  uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  // per-group metadata and the tile slice, copied once to shared memory
+  int64_t* s_si = (int64_t*)(bars + 64);          // [(2B-1)*2] S row offsets
+  int64_t* s_off = s_si + 2 * (2 * B - 1);         // [B] table image offsets
+  int* s_kc = (int*)(s_off + B);                   // [B] KC_P | KC_Q << 8
+  int2* s_tiles = (int2*)(((uintptr_t)(s_kc + B) + 7) & ~(uintptr_t)7);
+  for (int k = threadIdx.x; k < 2 * (2 * B - 1); k += blockDim.x) s_si[k] = a.si_rows[k];
+  for (int k = threadIdx.x; k < B; k += blockDim.x) {
+    s_off[k] = a.am_off[k];
+    s_kc[k] = a.am_kc[k];
+  }
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nh = npad > 64 ? 64 : npad;  // accumulator width (columns of one j'-half)
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < (uint32_t)(8 * nh)) tmem_cols <<= 1;  // 2 buffers x {P, Q} x {main, corr}
+  if (threadIdx.x == 0) {
+    mbar_init(stgf, 1);
+    mbar_init(stge, 128);
+    for (int s = 0; s < kStagesLegI; ++s) {
+      mbar_init(split + s, 128);
+      mbar_init(empty + s, 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(accf + k, 1);
+      mbar_init(acce + k, 128);
+    }
+    mbar_init(tabf, 1);
+    mbar_init(tabe, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
+  const int g_begin = (int)((int64_t)a.ntiles * blockIdx.x / gridDim.x);
+  const int g_end = (int)((int64_t)a.ntiles * (blockIdx.x + 1) / gridDim.x);
+  const int nt = g_end - g_begin;
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) s_tiles[k] = a.tiles[g_begin + k];
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int cur = -1, ngrp = 0;
+      uint32_t c = 0;
+      for (int t = 0; t < nt && !*abort_flag; ++t) {
+        const int2 tl = s_tiles[t];
+        const int m_idx = tl.x;
+        const int am = m_idx >= B - 1 ? m_idx - (B - 1) : (B - 1) - m_idx;
+        const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
+        if (m_idx != cur) {
+          if (ngrp > 0 && !mbar_wait(tabe, (ngrp - 1) & 1, abort_flag)) break;
+          const uint32_t bytes = (uint32_t)((kcp + kcq) * 2 * chunk_tab);
+          mbar_arrive_tx(tabf, bytes);
+          bulk_load(tab, a.tabimg + s_off[am], bytes, tabf);
+          cur = m_idx;
+          ++ngrp;
+        }
+        bool ok = true;
+        for (int p = 0; p < 2 && ok; ++p) {
+          const int kcn = p ? kcq : kcp;
+          const int64_t r0 = s_si[2 * m_idx + p];
+          for (int kc = 0; kc < kcn; ++kc, ++c) {
+            if (!mbar_wait(stge, (c & 1) ^ 1, abort_flag)) { ok = false; break; }
+            mbar_arrive_tx(stgf, kChunk);
+            tma_load_2d(stg, &smap, stgf, tl.y & ~1, (int)(r0 + kc * 32));
+          }
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int cur = -1, ngrp = 0;
+      uint32_t c = 0, tcount = 0;
+      for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
+        const int2 tl = s_tiles[t];
+        const int m_idx = tl.x;
+        const int jh = tl.y & 1;
+        const uint32_t idesc = idesc_tf32(jh ? npad - 64 : nh);
+        const int am = m_idx >= B - 1 ? m_idx - (B - 1) : (B - 1) - m_idx;
+        const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
+        if (m_idx != cur) {
+          if (!mbar_wait(tabf, ngrp & 1, abort_flag)) break;
+          cur = m_idx;
+          ++ngrp;
+        }
+        const int acc = tcount & 1;
+        if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
+        tc_after();
+        bool ok = true;
+        for (int p = 0; p < 2 && ok; ++p) {
+          const int kcn = p ? kcq : kcp;
+          // accumulators of this buffer: [P main][P corr][Q main][Q corr], nh columns each
+          const uint32_t d = tmem + (uint32_t)((4 * acc + 2 * p) * nh);
+          const uint32_t dc = d + (uint32_t)nh;
+          const uint32_t th0 = smem_u32(tab) + (uint32_t)((p ? 2 * kcp : 0) * chunk_tab + jh * 64 * 128);
+          const uint32_t tl0 = th0 + (uint32_t)(kcn * chunk_tab);
+          for (int kc = 0; kc < kcn; ++kc, ++c) {
+            const int s = c % kStagesLegI;
+            if (!mbar_wait(split + s, (c / kStagesLegI) & 1, abort_flag)) { ok = false; break; }
+            tc_after();
+            const uint32_t xh = smem_u32(xs + s * 2 * kChunk);
+            const uint32_t xl = xh + kChunk;
+            const uint32_t th = th0 + (uint32_t)(kc * chunk_tab);
+            const uint32_t tlo = tl0 + (uint32_t)(kc * chunk_tab);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t ko = (uint32_t)(kk * 32);
+              const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
+              mma_tf32(d, sw128_desc(xh + ko), sw128_desc(th + ko), idesc, first);
+              mma_tf32(dc, sw128_desc(xh + ko), sw128_desc(tlo + ko), idesc, first);
+              mma_tf32(dc, sw128_desc(xl + ko), sw128_desc(th + ko), idesc, 1u);
+            }
+            mma_commit(empty + s);
+          }
+        }
+        if (!ok) break;
+        mma_commit(accf + acc);
+        if (t + 1 >= nt || s_tiles[t + 1].x != cur) mma_commit(tabe);
+      }
+    }
+  } else if (warp < 6) {
+    // staging [32 l'][128 rows] -> K-major hi/lo rows
+    const int r = threadIdx.x - 64;
+    uint32_t c = 0;
+    for (int t = 0; t < nt; ++t) {
+      const int2 tl = s_tiles[t];
+      const int m_idx = tl.x;
+      const int am = m_idx >= B - 1 ? m_idx - (B - 1) : (B - 1) - m_idx;
+      const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
+      bool ok = true;
+      for (int ch = 0; ch < kcp + kcq; ++ch, ++c) {
+        if (!mbar_wait(stgf, c & 1, abort_flag)) { ok = false; break; }
+        float v[32];
+        const float* sp = (const float*)stg;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = sp[k * 128 + r];
+        mbar_arrive(stge);
+        const int s = c % kStagesLegI;
+        if (!mbar_wait(empty + s, ((c / kStagesLegI) & 1) ^ 1, abort_flag)) { ok = false; break; }
+        split_store(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v);
+        fence_proxy_async();
+        mbar_arrive(split + s);
+      }
+      if (!ok) break;
+    }
+  } else {
+    const int quarter = warp & 3;
+    const int r_in = quarter * 32 + lane;
+    uint32_t tcount = 0;
+    for (int t = 0; t < nt; ++t, ++tcount) {
+      const int2 tl = s_tiles[t];
+      const int acc = tcount & 1;
+      if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
+      tc_after();
+      const int m_idx = tl.x;
+      const int m = m_idx - (B - 1);
+      const int am = m < 0 ? -m : m;
+      const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
+      const float sgn = (m < 0 && (am & 1)) ? -1.f : 1.f;
+      const int jh = tl.y & 1;
+      const int ncols = jh ? npad - 64 : nh;
+      const int grow = (tl.y & ~1) + r_in;
+      const bool valid = grow < NB * 2 * B;
+      const int b = grow / (2 * B), cc = (grow / B) & 1, i = grow % B;
+      float* out = a.g + (((int64_t)m_idx * NB + b) * 2 + cc) * (2 * B) * B + i;
+      const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
+      const uint32_t dP = tmem + (uint32_t)(4 * acc * nh) + lanes;
+      const uint32_t dQ = dP + (uint32_t)(2 * nh);
+      for (int c0 = 0; c0 < ncols; c0 += 16) {
+        float P[16], Q[16];
+        if (kcp) tmem_ld16_sum(dP + (uint32_t)c0, dP + (uint32_t)(nh + c0), P);
+        else
+#pragma unroll
+          for (int k = 0; k < 16; ++k) P[k] = 0.f;
+        if (kcq) tmem_ld16_sum(dQ + (uint32_t)c0, dQ + (uint32_t)(nh + c0), Q);
+        else
+#pragma unroll
+          for (int k = 0; k < 16; ++k) Q[k] = 0.f;
+        if (valid) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int j = jh * 64 + c0 + k;
+            if (j < B) {
+              out[(int64_t)j * B] = sgn * (P[k] + Q[k]);
+              out[(int64_t)(2 * B - 1 - j) * B] = sgn * (P[k] - Q[k]);
+            }
+          }
+        }
+      }
+      tc_before();
+      mbar_arrive(acce + acc);
+    }
+  }
+  __syncthreads();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    const uint64_t t0 = gtimer();
+    while (gtimer() - t0 < 20000000ull) {
+    }
+  }
+  tc_after();
+  if (warp == 1) tmem_dealloc(tmem, tmem_cols);
+}
+
+// ===========================================================================
+// inverse radial
+// ===========================================================================
+struct RadIArgs {
+  const int2* tiles;          // (l, col0), grouped by l
+  int ntiles;
+  const unsigned char* tabimg;
+  const int64_t* l_off;       // image offset per l (KC_l chunk pairs of 32 KB)
+  const int64_t* si_rows;     // S row offset per (m_idx, p)
+  const float* coef;          // complex interleaved coefficients
+  const int64_t* fn_coef;     // coefficient offset per function of the segment
+  float* s;                   // output S, layout [m_idx][p][l'][b][c][i]
+  int* err;
+  int B, NB;
+};
+
+__global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int B = a.B, NB = a.NB;
+  // stage s: [table hi][table lo][data hi][data lo], 16 KB each
+  unsigned char* st = base;
+  uint64_t* bars = (uint64_t*)(st + kStagesRadI * 4 * kChunk);
+  uint64_t* tfull = bars;                   // [S] table chunk landed
+  uint64_t* split = tfull + kStagesRadI;    // [S] data ready (128)
+  uint64_t* empty = split + kStagesRadI;    // [S] MMAs done
+  uint64_t* accf = empty + kStagesRadI;     // [2]
+  uint64_t* acce = accf + 2;                // [2] (128)
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  int64_t* s_si = (int64_t*)(bars + 64);          // [(2B-1)*2] S row offsets
+  int64_t* s_loff = s_si + 2 * (2 * B - 1);        // [B] table image offsets
+  int2* s_tiles = (int2*)(s_loff + B);
+  for (int k = threadIdx.x; k < 2 * (2 * B - 1); k += blockDim.x) s_si[k] = a.si_rows[k];
+  for (int k = threadIdx.x; k < B; k += blockDim.x) s_loff[k] = a.l_off[k];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tmem_cols = 512;  // 2 buffers x {main, corr} x 128 columns
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStagesRadI; ++s) {
+      mbar_init(tfull + s, 1);
+      mbar_init(split + s, 128);
+      mbar_init(empty + s, 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(accf + k, 1);
+      mbar_init(acce + k, 128);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
+  const int g_begin = (int)((int64_t)a.ntiles * blockIdx.x / gridDim.x);
+  const int g_end = (int)((int64_t)a.ntiles * (blockIdx.x + 1) / gridDim.x);
+  const int nt = g_end - g_begin;
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) s_tiles[k] = a.tiles[g_begin + k];
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t c = 0;
+      for (int t = 0; t < nt && !*abort_flag; ++t) {
+        const int l = s_tiles[t].x;
+        const int kcn = (B - l + 31) / 32;
+        bool ok = true;
+        for (int kc = 0; kc < kcn; ++kc, ++c) {
+          const int s = c % kStagesRadI;
+          if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) { ok = false; break; }
+          mbar_arrive_tx(tfull + s, 2 * kChunk);
+          bulk_load(st + s * 4 * kChunk, a.tabimg + s_loff[l] + (int64_t)kc * 2 * kChunk, 2 * kChunk, tfull + s);
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t c = 0, tcount = 0;
+      const uint32_t idesc = idesc_tf32(128);
+      for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
+        const int l = s_tiles[t].x;
+        const int kcn = (B - l + 31) / 32;
+        const int acc = tcount & 1;
+        if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
+        tc_after();
+        const uint32_t d = tmem + (uint32_t)(acc * 256);  // main
+        const uint32_t dc = d + 128u;                     // correction
+        bool ok = true;
+        for (int kc = 0; kc < kcn; ++kc, ++c) {
+          const int s = c % kStagesRadI;
+          const uint32_t ph = (c / kStagesRadI) & 1;
+          if (!mbar_wait(tfull + s, ph, abort_flag) || !mbar_wait(split + s, ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_after();
+          const uint32_t ah = smem_u32(st + s * 4 * kChunk);
+          const uint32_t al = ah + kChunk;
+          const uint32_t bh = al + kChunk;
+          const uint32_t bl = bh + kChunk;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t ko = (uint32_t)(kk * 32);
+            const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
+            mma_tf32(d, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, first);
+            mma_tf32(dc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, first);
+            mma_tf32(dc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
+          }
+          mma_commit(empty + s);
+        }
+        if (!ok) break;
+        mma_commit(accf + acc);
+      }
+    }
+  } else if (warp < 6) {
+    // gather: column (b, m, c) of the tile, 32 degrees n' per chunk
+    const int col_in = threadIdx.x - 64;
+    uint32_t c = 0;
+    for (int t = 0; t < nt; ++t) {
+      const int2 tl = s_tiles[t];
+      const int l = tl.x;
+      const int kcn = (B - l + 31) / 32;
+      const int per_b = (2 * l + 1) * 2;
+      const int col = tl.y + col_in;
+      const bool valid = col < NB * per_b;
+      const int b = valid ? col / per_b : 0;
+      const int rem = col - b * per_b;
+      const int m = (rem >> 1) - l, cc = rem & 1;
+      const float* cf = a.coef + 2 * a.fn_coef[b] + cc;
+      bool ok = true;
+      for (int kc = 0; kc < kcn; ++kc, ++c) {
+        const int s = c % kStagesRadI;
+        if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) { ok = false; break; }
+        float v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int np = kc * 32 + k;   // n = l + 1 + np
+          const int n = l + 1 + np;
+          v[k] = (valid && np < B - l)
+                     ? cf[2 * ((int64_t)n * (n - 1) * (2 * n - 1) / 6 + (int64_t)l * (l + 1) + m)]
+                     : 0.f;
+        }
+        unsigned char* sb = st + s * 4 * kChunk + 2 * kChunk;
+        split_store(sb, sb + kChunk, col_in, v);
+        fence_proxy_async();
+        mbar_arrive(split + s);
+      }
+      if (!ok) break;
+    }
+  } else {
+    const int quarter = warp & 3;
+    const int i = quarter * 32 + lane;   // TMEM lane = radius index
+    uint32_t tcount = 0;
+    for (int t = 0; t < nt; ++t, ++tcount) {
+      const int2 tl = s_tiles[t];
+      const int acc = tcount & 1;
+      if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
+      tc_after();
+      const int l = tl.x;
+      const int per_b = (2 * l + 1) * 2;
+      const int ncol = NB * per_b;
+      const int64_t L = (int64_t)NB * 2 * B;
+      const uint32_t dq = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quarter * 32) << 16);
+      // column (b, rem = 2(m+l) + c) decoded once per tile, then stepped
+      int b = tl.y / per_b;
+      int rem = tl.y - b * per_b;
+      for (int c0 = 0; c0 < 128; c0 += 16) {
+        float v[16];
+        tmem_ld16_sum(dq + (uint32_t)c0, dq + (uint32_t)(128 + c0), v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          if (i < B && tl.y + c0 + k < ncol) {
+            const int m = (rem >> 1) - l, cc = rem & 1;
+            const int am = m < 0 ? -m : m;
+            const int p = (l - am) & 1;
+            const int64_t srow = s_si[2 * (m + B - 1) + p] + ((l - am - p) >> 1);
+            a.s[srow * L + ((int64_t)b * 2 + cc) * B + i] = v[k];
+          }
+          if (++rem == per_b) {
+            rem = 0;
+            ++b;
+          }
+        }
+      }
+      tc_before();
+      mbar_arrive(acce + acc);
+    }
+  }
+  __syncthreads();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    const uint64_t t0 = gtimer();
+    while (gtimer() - t0 < 20000000ull) {
+    }
+  }
+  tc_after();
+  if (warp == 1) tmem_dealloc(tmem, tmem_cols);
+}
+
+// ===========================================================================
+// host side
+// ===========================================================================
+namespace {
+
+uint32_t rna_bits(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  return (u + 0x1000u) & 0xFFFFE000u;
+}
+
+// Append a hi and a lo plane of KC chunks, each `rows` x 32 floats, 128-byte
+// swizzled: value(row, k) for k < K.
+template <typename F>
+void append_planes(std::vector<unsigned char>& img, int rows, int K, int KC, F value) {
+  const size_t off = img.size();
+  const size_t plane = (size_t)KC * rows * 128;
+  img.resize(off + 2 * plane, 0);
+  for (int r = 0; r < rows; ++r)
+    for (int k = 0; k < K; ++k) {
+      const double v = value(r, k);
+      if (v == 0.0) continue;
+      const float f = (float)v;
+      const uint32_t hb = rna_bits(f);
+      float hi;
+      memcpy(&hi, &hb, 4);
+      const uint32_t lb = rna_bits((float)(v - (double)hi));
+      const int kc = k / 32, kin = k % 32;
+      const size_t pos = (size_t)kc * rows * 128 + (size_t)r * 128 + (size_t)((((kin >> 2) ^ (r & 7)) << 4) + (kin & 3) * 4);
+      memcpy(&img[off + pos], &hb, 4);
+      memcpy(&img[off + plane + pos], &lb, 4);
+    }
+}
+
+int pad16i(int n) { return n <= 16 ? 16 : (n + 15) / 16 * 16; }
+
+}  // namespace
+
+struct TcInvSeg {
+  // Legendre
+  CUtensorMap smap;
+  int2* leg_tiles = nullptr;
+  int leg_ntiles = 0, leg_grid = 0;
+  size_t leg_smem = 0;
+  int64_t* am_off = nullptr;
+  int* am_kc = nullptr;
+  int npad = 0, kcmax = 0;
+  // radial
+  int2* rad_tiles = nullptr;
+  int rad_ntiles = 0, rad_grid = 0;
+  size_t rad_smem = 0;
+  int64_t* l_off = nullptr;
+};
+
+struct TcInvState {
+  std::vector<TcInvSeg> segs;
+  unsigned char* d_img = nullptr;
+};
+
+bool make_map_2d(CUtensorMap* map, void* base, uint64_t inner, uint64_t rows, uint32_t box_inner, uint32_t box_rows,
+                 CUtensorMapSwizzle sw);
+
+template <typename T>
+static cudaError_t upload(T** dst, const std::vector<T>& v, int64_t& bytes) {
+  cudaError_t e = cudaMalloc((void**)dst, v.size() * sizeof(T) + 16);
+  if (e != cudaSuccess) return e;
+  bytes += v.size() * sizeof(T);
+  return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+cudaError_t tc_inv_prepare(Plan& P) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  TcInvState* st = new TcInvState();
+  std::vector<unsigned char> img;
+  std::vector<std::vector<int64_t>> am_offs, l_offs;
+  std::vector<std::vector<int>> am_kcs;
+  std::vector<std::vector<int2>> lt, rt;
+  for (size_t s = 0; s < P.segs.size(); ++s) {
+    const SegDesc& sg = P.segs[s];
+    const HostTables& H = P.tables[s];
+    const int B = sg.B, NB = sg.NB;
+    TcInvSeg ts;
+    ts.npad = pad16i(B);
+    // Legendre synthesis tables, per |m|: [P hi][P lo][Q hi][Q lo], rows j', K = l'
+    std::vector<int64_t> aoff(B, 0);
+    std::vector<int> akc(B, 0);
+    int kcmax = 1;
+    for (int am = 0; am < B; ++am) {
+      img.resize((img.size() + 1023) / 1024 * 1024);
+      aoff[am] = (int64_t)img.size();
+      int kcs[2];
+      for (int p = 0; p < 2; ++p) {
+        const int K = n_par(B, am, p);
+        kcs[p] = (K + 31) / 32;
+        if (kcs[p] == 0) continue;
+        append_planes(img, ts.npad, K, kcs[p], [&](int j, int q) -> double {
+          if (j >= B) return 0.0;
+          const int l = am + p + 2 * q;
+          return H.lam[((size_t)am * B + l) * B + j];
+        });
+      }
+      akc[am] = kcs[0] | (kcs[1] << 8);
+      kcmax = std::max(kcmax, kcs[0] + kcs[1]);
+    }
+    ts.kcmax = kcmax;
+    std::vector<int2> ltiles;
+    for (int mi = 0; mi < 2 * B - 1; ++mi)
+      for (int r0 = 0; r0 < NB * 2 * B; r0 += 128)
+        for (int jh = 0; jh * 64 < ts.npad; ++jh) ltiles.push_back(make_int2(mi, r0 | jh));
+    // radial inverse tables, per l: KC_l x [hi chunk][lo chunk], rows i (128), K = n'
+    std::vector<int64_t> loff(B, 0);
+    for (int l = 0; l < B; ++l) {
+      img.resize((img.size() + 1023) / 1024 * 1024);
+      loff[l] = (int64_t)img.size();
+      const int K = B - l, KC = (K + 31) / 32;
+      for (int kc = 0; kc < KC; ++kc)
+        append_planes(img, 128, 32, 1, [&](int i, int k) -> double {
+          const int np = kc * 32 + k;
+          if (i >= B || np >= K) return 0.0;
+          return H.T[((size_t)l * B + (l + np)) * B + i];
+        });
+    }
+    std::vector<int2> rtiles;
+    for (int l = 0; l < B; ++l)
+      for (int c0 = 0; c0 < NB * (2 * l + 1) * 2; c0 += 128) rtiles.push_back(make_int2(l, c0));
+    // tensor map over S: [B^2 rows of l'][NB*2*B]
+    float* w2 = (float*)P.d_w2 + sg.w2_off;
+    if (!make_map_2d(&ts.smap, w2, (uint64_t)NB * 2 * B, (uint64_t)B * B, 128, 32, CU_TENSOR_MAP_SWIZZLE_NONE)) {
+      delete st;
+      return cudaErrorInvalidValue;
+    }
+    st->segs.push_back(ts);
+    am_offs.push_back(aoff);
+    am_kcs.push_back(akc);
+    l_offs.push_back(loff);
+    lt.push_back(ltiles);
+    rt.push_back(rtiles);
+  }
+  int64_t bytes = 0;
+  cudaError_t e = upload(&st->d_img, img, bytes);
+  for (size_t s = 0; s < st->segs.size() && e == cudaSuccess; ++s) {
+    TcInvSeg& ts = st->segs[s];
+    const int B = P.segs[s].B;
+    e = upload(&ts.am_off, am_offs[s], bytes);
+    if (e == cudaSuccess) e = upload(&ts.am_kc, am_kcs[s], bytes);
+    if (e == cudaSuccess) e = upload(&ts.l_off, l_offs[s], bytes);
+    if (e == cudaSuccess) e = upload(&ts.leg_tiles, lt[s], bytes);
+    if (e == cudaSuccess) e = upload(&ts.rad_tiles, rt[s], bytes);
+    ts.leg_ntiles = (int)lt[s].size();
+    ts.rad_ntiles = (int)rt[s].size();
+    ts.leg_grid = std::min(ts.leg_ntiles, nsm);
+    ts.rad_grid = std::min(ts.rad_ntiles, nsm);
+    const int lmax = (ts.leg_ntiles + ts.leg_grid - 1) / std::max(ts.leg_grid, 1) + 1;
+    const int rmax = (ts.rad_ntiles + ts.rad_grid - 1) / std::max(ts.rad_grid, 1) + 1;
+    // tables, staging, operand ring, barrier slots, metadata (S row offsets,
+    // image offsets, chunk counts), tile slice
+    const size_t meta = (size_t)2 * (2 * B - 1) * 8 + (size_t)B * 12 + 8;
+    ts.leg_smem = 1024 + (size_t)ts.kcmax * 2 * ts.npad * 128 + kChunk + (size_t)kStagesLegI * 2 * kChunk + 64 * 8 +
+                  meta + (size_t)lmax * 8;
+    ts.rad_smem = 1024 + (size_t)kStagesRadI * 4 * kChunk + 64 * 8 + meta + (size_t)rmax * 8;
+    if (ts.leg_smem > 227 * 1024 || ts.rad_smem > 227 * 1024) e = cudaErrorInvalidValue;
+  }
+  P.bytes += bytes;
+  if (e != cudaSuccess) {
+    P.tc_inv_state = st;
+    return e;
+  }
+  P.tc_inv_state = st;
+  return cudaSuccess;
+}
+
+void tc_inv_release(Plan& P) {
+  TcInvState* st = (TcInvState*)P.tc_inv_state;
+  if (!st) return;
+  for (TcInvSeg& s : st->segs) {
+    void* ptrs[] = {s.leg_tiles, s.am_off, s.am_kc, s.rad_tiles, s.l_off};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+  if (st->d_img) cudaFree(st->d_img);
+  delete st;
+  P.tc_inv_state = nullptr;
+}
+
+// prob 2: inverse radial (x = coefficients, y = S); prob 3: inverse Legendre (x = S, y = G)
+cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream_t s) {
+  TcInvState* st = (TcInvState*)P.tc_inv_state;
+  if (!st) return cudaErrorNotSupported;
+  StageTimer timer(P, prob == 2 ? ST_RAD_I : ST_LEG_I, s);
+  for (size_t k = 0; k < st->segs.size(); ++k) {
+    TcInvSeg& ts = st->segs[k];
+    const SegDesc& sg = P.segs[k];
+    cudaError_t e;
+    if (prob == 2) {
+      RadIArgs a;
+      a.tiles = ts.rad_tiles;
+      a.ntiles = ts.rad_ntiles;
+      a.tabimg = st->d_img;
+      a.l_off = ts.l_off;
+      a.si_rows = P.d_si_rows + sg.si_rows;
+      a.coef = (const float*)x;
+      a.fn_coef = P.d_fn_coef + sg.fn0;
+      a.s = (float*)y + sg.w2_off;
+      a.err = P.d_err;
+      a.B = sg.B;
+      a.NB = sg.NB;
+      e = cudaFuncSetAttribute(tc_rad_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.rad_smem);
+      if (e != cudaSuccess) return e;
+      tc_rad_inv_kernel<<<ts.rad_grid, kThreadsInv, ts.rad_smem, s>>>(a);
+    } else {
+      LegIArgs a;
+      a.tiles = ts.leg_tiles;
+      a.ntiles = ts.leg_ntiles;
+      a.tabimg = st->d_img;
+      a.am_off = ts.am_off;
+      a.am_kc = ts.am_kc;
+      a.si_rows = P.d_si_rows + sg.si_rows;
+      a.g = (float*)y + sg.w1_off;
+      a.err = P.d_err;
+      a.B = sg.B;
+      a.NB = sg.NB;
+      a.npad = ts.npad;
+      a.kcmax = ts.kcmax;
+      e = cudaFuncSetAttribute(tc_leg_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.leg_smem);
+      if (e != cudaSuccess) return e;
+      tc_leg_inv_kernel<<<ts.leg_grid, kThreadsInv, ts.leg_smem, s>>>(ts.smap, a);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  timer.finish();
+  return cudaSuccess;
+}
+
+}  // namespace sgl
