@@ -73,7 +73,7 @@ enum { TC_LEG_F = 0, TC_RAD_F = 1 };
 constexpr int kStagesLeg = 4;
 constexpr int kStagesRad = 2;
 constexpr int kChunkBytes = 128 * 128;  // 128 rows x 32 floats
-constexpr int kThreads = 320;
+constexpr int kThreads = tcx::kRoleThreads;
 
 using namespace tcx;
 }  // namespace
@@ -135,12 +135,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(split + s, 128);
+      mbar_init(split + s, kSplitThreads);
       mbar_init(empty + s, 1);
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(accf + k, 1);
-      mbar_init(acce + k, 128);
+      mbar_init(acce + k, kEpiThreads);
     }
     mbar_init(tabf, 1);
     mbar_init(tabe, 1);
@@ -240,9 +240,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         if (last_of_group) mma_commit(tabe);
       }
     }
-  } else if (warp < 6) {
+  } else if (warp < kFirstEpiWarp) {
     // ---------------- split: X -> (hi, lo) ----------------
-    const int tid = threadIdx.x - 64;  // 0..127
+    const int tid = threadIdx.x - 32 * kFirstSplitWarp;  // 0 .. kSplitThreads-1
     uint32_t c = 0;
     for (int t = t_begin; t < t_end; ++t) {
       bool ok = true;
@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         float4* hi = (float4*)(xs + s * 2 * kChunkBytes);
         float4* lo = (float4*)(xs + s * 2 * kChunkBytes + kChunkBytes);
 #pragma unroll
-        for (int v = 0; v < kChunkBytes / 16 / 128; ++v) {
-          const int idx = v * 128 + tid;
+        for (int v = 0; v < kChunkBytes / 16 / kSplitThreads; ++v) {
+          const int idx = v * kSplitThreads + tid;
           float4 x = hi[idx];
           float4 h = {tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w)};
           // lo rounded to TF32 too, so that the tensor core uses it unchanged
@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   } else {
     // ---------------- epilogue ----------------
     const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
+    const int ehalf = (warp - kFirstEpiWarp) >> 2;  // which 16-column blocks
     const int r_in = quarter * 32 + lane;       // tile row of this thread
     uint32_t tcount = 0;
     float* Y = reinterpret_cast<float*>(a.y);
@@ -291,7 +292,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const float sgn = (m < 0 && (am & 1)) ? -1.f : 1.f;
         const bool valid = grow < NB * 2 * B;
         const int b = grow / (2 * B), cc = (grow / B) & 1, i = grow % B;
-        for (int c0 = 0; c0 < npad; c0 += 16) {
+        const int64_t rbase = a.w2_off + (int64_t)cc * B + i;
+        for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
           tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
           if (NMAIN == 2) {
@@ -305,9 +307,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             for (int k = 0; k < 16; ++k) {
               const int col = c0 + k;
               if (col < ncol) {
+                // S_f[l][b][m+l][c][i] = 2B (NB l^2 + b(2l+1) + m + l) + c B + i
                 const int l = am + p + 2 * col;
-                Y[a.w2_off + (int64_t)NB * 2 * B * l * l + (((int64_t)b * (2 * l + 1) + (m + l)) * 2 + cc) * B + i] =
-                    sgn * v[k];
+                const int64_t t = (int64_t)NB * l * l + (int64_t)(2 * b + 1) * l + b + m;
+                Y[rbase + 2 * (int64_t)B * t] = sgn * v[k];
               }
             }
           }
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int mm = rem >> 1, cc = rem & 1;
         const int ncol = B - l;
         const int64_t cbase = valid ? a.fn_coef[b] : 0;
-        for (int c0 = 0; c0 < npad; c0 += 16) {
+        for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
           tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
           if (NMAIN == 2) {

@@ -28,7 +28,7 @@ namespace sgl {
 using namespace tcx;
 
 namespace {
-constexpr int kThreadsInv = 320;
+constexpr int kThreadsInv = kRoleThreads;
 constexpr int kChunk = 128 * 128;   // 128 rows x 32 floats
 constexpr int kStagesLegI = 2;
 constexpr int kStagesRadI = 3;
@@ -36,18 +36,22 @@ constexpr int kStagesRadI = 3;
 // 128-byte swizzled K-major position of (row, 16-byte chunk q) in a tile
 __device__ __forceinline__ int sw_pos(int row, int q) { return row * 128 + ((q ^ (row & 7)) << 4); }
 
-__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, int row, const float* v) {
+// Split 4*NQ consecutive K values v of one row into TF32 hi/lo and store them
+// at 16-byte chunks q0 .. q0+NQ-1 of the row.
+template <int NQ>
+__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, int row, const float* v, int q0) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int qq = 0; qq < NQ; ++qq) {
+    const int q = q0 + qq;
     float4 h, l;
-    h.x = tf32_rna(v[4 * q + 0]);
-    h.y = tf32_rna(v[4 * q + 1]);
-    h.z = tf32_rna(v[4 * q + 2]);
-    h.w = tf32_rna(v[4 * q + 3]);
-    l.x = tf32_rna(v[4 * q + 0] - h.x);
-    l.y = tf32_rna(v[4 * q + 1] - h.y);
-    l.z = tf32_rna(v[4 * q + 2] - h.z);
-    l.w = tf32_rna(v[4 * q + 3] - h.w);
+    h.x = tf32_rna(v[4 * qq +0]);
+    h.y = tf32_rna(v[4 * qq +1]);
+    h.z = tf32_rna(v[4 * qq +2]);
+    h.w = tf32_rna(v[4 * qq +3]);
+    l.x = tf32_rna(v[4 * qq +0] - h.x);
+    l.y = tf32_rna(v[4 * qq +1] - h.y);
+    l.z = tf32_rna(v[4 * qq +2] - h.z);
+    l.w = tf32_rna(v[4 * qq +3] - h.w);
     *(float4*)(hi + sw_pos(row, q)) = h;
     *(float4*)(lo + sw_pos(row, q)) = l;
   }
@@ -112,14 +116,14 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
   while (tmem_cols < (uint32_t)(8 * nh)) tmem_cols <<= 1;  // 2 buffers x {P, Q} x {main, corr}
   if (threadIdx.x == 0) {
     mbar_init(stgf, 1);
-    mbar_init(stge, 128);
+    mbar_init(stge, kSplitThreads);
     for (int s = 0; s < kStagesLegI; ++s) {
-      mbar_init(split + s, 128);
+      mbar_init(split + s, kSplitThreads);
       mbar_init(empty + s, 1);
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(accf + k, 1);
-      mbar_init(acce + k, 128);
+      mbar_init(acce + k, kEpiThreads);
     }
     mbar_init(tabf, 1);
     mbar_init(tabe, 1);
@@ -217,9 +221,11 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
         if (t + 1 >= nt || s_tiles[t + 1].x != cur) mma_commit(tabe);
       }
     }
-  } else if (warp < 6) {
-    // staging [32 l'][128 rows] -> K-major hi/lo rows
-    const int r = threadIdx.x - 64;
+  } else if (warp < kFirstEpiWarp) {
+    // staging [32 l'][128 rows] -> K-major hi/lo rows; thread (r, h) converts
+    // the 16 values l' = 16h .. 16h+15 of row r
+    const int tid = threadIdx.x - 32 * kFirstSplitWarp;
+    const int r = tid & 127, h = tid >> 7;
     uint32_t c = 0;
     for (int t = 0; t < nt; ++t) {
       const int2 tl = s_tiles[t];
@@ -229,14 +235,14 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
       bool ok = true;
       for (int ch = 0; ch < kcp + kcq; ++ch, ++c) {
         if (!mbar_wait(stgf, c & 1, abort_flag)) { ok = false; break; }
-        float v[32];
-        const float* sp = (const float*)stg;
+        float v[16];
+        const float* sp = (const float*)stg + 16 * h * 128;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = sp[k * 128 + r];
+        for (int k = 0; k < 16; ++k) v[k] = sp[k * 128 + r];
         mbar_arrive(stge);
         const int s = c % kStagesLegI;
         if (!mbar_wait(empty + s, ((c / kStagesLegI) & 1) ^ 1, abort_flag)) { ok = false; break; }
-        split_store(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v);
+        split_store<4>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h);
         fence_proxy_async();
         mbar_arrive(split + s);
       }
@@ -244,6 +250,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
     }
   } else {
     const int quarter = warp & 3;
+    const int ehalf = (warp - kFirstEpiWarp) >> 2;  // alternate 16-column blocks
     const int r_in = quarter * 32 + lane;
     uint32_t tcount = 0;
     for (int t = 0; t < nt; ++t, ++tcount) {
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
       const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
       const uint32_t dP = tmem + (uint32_t)(4 * acc * nh) + lanes;
       const uint32_t dQ = dP + (uint32_t)(2 * nh);
-      for (int c0 = 0; c0 < ncols; c0 += 16) {
+      for (int c0 = 16 * ehalf; c0 < ncols; c0 += 32) {
         float P[16], Q[16];
         if (kcp) tmem_ld16_sum(dP + (uint32_t)c0, dP + (uint32_t)(nh + c0), P);
         else
@@ -342,12 +349,12 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesRadI; ++s) {
       mbar_init(tfull + s, 1);
-      mbar_init(split + s, 128);
+      mbar_init(split + s, kSplitThreads);
       mbar_init(empty + s, 1);
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(accf + k, 1);
-      mbar_init(acce + k, 128);
+      mbar_init(acce + k, kEpiThreads);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -417,9 +424,11 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
         mma_commit(accf + acc);
       }
     }
-  } else if (warp < 6) {
-    // gather: column (b, m, c) of the tile, 32 degrees n' per chunk
-    const int col_in = threadIdx.x - 64;
+  } else if (warp < kFirstEpiWarp) {
+    // gather: column (b, m, c) of the tile; thread (col, h) loads the degrees
+    // n' = 32 kc + 16h .. +15 of the chunk
+    const int tid = threadIdx.x - 32 * kFirstSplitWarp;
+    const int col_in = tid & 127, h = tid >> 7;
     uint32_t c = 0;
     for (int t = 0; t < nt; ++t) {
       const int2 tl = s_tiles[t];
@@ -436,17 +445,17 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       for (int kc = 0; kc < kcn; ++kc, ++c) {
         const int s = c % kStagesRadI;
         if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) { ok = false; break; }
-        float v[32];
+        float v[16];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int np = kc * 32 + k;   // n = l + 1 + np
+        for (int k = 0; k < 16; ++k) {
+          const int np = kc * 32 + 16 * h + k;   // n = l + 1 + np
           const int n = l + 1 + np;
           v[k] = (valid && np < B - l)
                      ? cf[2 * ((int64_t)n * (n - 1) * (2 * n - 1) / 6 + (int64_t)l * (l + 1) + m)]
                      : 0.f;
         }
         unsigned char* sb = st + s * 4 * kChunk + 2 * kChunk;
-        split_store(sb, sb + kChunk, col_in, v);
+        split_store<4>(sb, sb + kChunk, col_in, v, 4 * h);
         fence_proxy_async();
         mbar_arrive(split + s);
       }
@@ -454,6 +463,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     }
   } else {
     const int quarter = warp & 3;
+    const int ehalf = (warp - kFirstEpiWarp) >> 2;  // alternate 16-column blocks
     const int i = quarter * 32 + lane;   // TMEM lane = radius index
     uint32_t tcount = 0;
     for (int t = 0; t < nt; ++t, ++tcount) {
@@ -466,12 +476,13 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       const int ncol = NB * per_b;
       const int64_t L = (int64_t)NB * 2 * B;
       const uint32_t dq = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quarter * 32) << 16);
-      // column (b, rem = 2(m+l) + c) decoded once per tile, then stepped
-      int b = tl.y / per_b;
-      int rem = tl.y - b * per_b;
-      for (int c0 = 0; c0 < 128; c0 += 16) {
+      // column (b, rem = 2(m+l) + c) decoded at the start of each 16-column
+      // block, then stepped
+      for (int c0 = 16 * ehalf; c0 < 128; c0 += 32) {
         float v[16];
         tmem_ld16_sum(dq + (uint32_t)c0, dq + (uint32_t)(128 + c0), v);
+        int b = (tl.y + c0) / per_b;
+        int rem = tl.y + c0 - b * per_b;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           if (i < B && tl.y + c0 + k < ncol) {

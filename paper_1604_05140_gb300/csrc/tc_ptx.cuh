@@ -10,6 +10,18 @@ namespace tcx {
 
 constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every mbarrier wait
 
+// Warp roles of the tensor-core kernels: warp 0 producer, warp 1 TMEM owner
+// and MMA issuer, then kSplitWarps operand-split warps and kEpiWarps epilogue
+// warps.  Epilogue warp w reads TMEM lanes 32*(w%4) .. +31; the two warps of
+// one lane quarter take alternate 16-column blocks.
+constexpr int kSplitWarps = 8;
+constexpr int kEpiWarps = 8;
+constexpr int kFirstSplitWarp = 2;
+constexpr int kFirstEpiWarp = kFirstSplitWarp + kSplitWarps;
+constexpr int kSplitThreads = 32 * kSplitWarps;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kRoleThreads = 32 * (kFirstEpiWarp + kEpiWarps);
+
 static __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
