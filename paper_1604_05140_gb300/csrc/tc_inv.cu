@@ -9,10 +9,10 @@
 // per (m, 128 rows (b, c, i)) with both theta-parities:
 //   P[row][j'] = sum_{l' even} S[row][l'] Lambda(theta_j'),  Q likewise for odd,
 //   G_j' = P + Q,  G_{2B-1-j'} = P - Q   (Lambda(pi - theta) = (-1)^{l+m} Lambda(theta)).
-//   A operand: S rows, loaded l'-major by TMA into a staging buffer and
+//   A operand: S rows, loaded l'-major by TMA into a staging ring and
 //   transposed to K-major hi/lo by the split warps; B operand: the table.
-// Same role layout as the forward kernels: warp 0 producer, warp 1 TMEM owner
-// and MMA issuer, warps 2-5 split, warps 6-9 epilogue; bounded waits.
+// Same role layout as the forward kernels (tc_ptx.cuh): producer warp, TMEM
+// owner and MMA issuer warp, split warps, epilogue warps; bounded waits.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -30,7 +30,8 @@ using namespace tcx;
 namespace {
 constexpr int kThreadsInv = kRoleThreads;
 constexpr int kChunk = 128 * 128;   // 128 rows x 32 floats
-constexpr int kStagesLegI = 2;
+constexpr int kStagesLegI = 2;    // operand ring of the Legendre synthesis
+constexpr int kStagingLegI = 4;   // TMA staging ring of the Legendre synthesis
 constexpr int kStagesRadI = 3;
 
 // 128-byte swizzled K-major position of (row, 16-byte chunk q) in a tile
@@ -63,15 +64,17 @@ __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo
 // ===========================================================================
 // Accumulators: the tensor cores round partial sums toward zero, so each
 // result keeps a main accumulator (hi*hi) and a correction accumulator
-// (hi*lo + lo*hi), added with round-to-nearest in the epilogue.  For the
-// Legendre synthesis (P and Q, main and correction) the j' range is cut in
-// halves of 64 columns so that two tiles' accumulators fit tensor memory; the
-// second half re-reads its rows from L2.
+// (hi*lo + lo*hi), added with round-to-nearest in the epilogue.  With P and Q
+// that is four accumulators per tile, so the j' range is cut in halves of 64
+// columns to let two tiles' accumulators fit tensor memory.  Tiles run in the
+// order (m, j'-half, rows): only the current half of the table is resident,
+// which leaves shared memory for a 4-deep staging ring; each row block is
+// read once per half.
 struct LegIArgs {
-  const int2* tiles;          // (m_idx, row0 | j'-half), grouped by m_idx
+  const int2* tiles;          // (m_idx, row0 | j'-half), ordered by (m_idx, half, row0)
   int ntiles;
   const unsigned char* tabimg;
-  const int64_t* am_off;      // image offset per |m|
+  const int64_t* am_off;      // image offset per (|m|, half)
   const int* am_kc;           // KC_P | KC_Q << 8 per |m|
   const int64_t* si_rows;     // S row offset per (m_idx, p)
   float* g;                   // output, layout [m_idx][b][c][j < 2B][i]
@@ -84,39 +87,39 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int B = a.B, NB = a.NB, npad = a.npad;
-  const int chunk_tab = npad * 128;                        // one table chunk (hi or lo)
-  unsigned char* tab = base;                               // [P hi][P lo][Q hi][Q lo]
-  unsigned char* stg = tab + (size_t)a.kcmax * 2 * chunk_tab;   // staging: 32 l' x 128 rows
-  unsigned char* xs = stg + kChunk;                        // stages x (hi, lo)
+  const int nh = npad > 64 ? 64 : npad;                    // rows (j') of one table half
+  const int chunk_tab = nh * 128;                          // one table chunk (hi or lo)
+  unsigned char* tab = base;                               // [P hi][P lo][Q hi][Q lo] of one half
+  unsigned char* stg = tab + (size_t)a.kcmax * 2 * chunk_tab;   // staging ring: 32 l' x 128 rows each
+  unsigned char* xs = stg + kStagingLegI * kChunk;         // operand ring: (hi, lo)
   uint64_t* bars = (uint64_t*)(xs + kStagesLegI * 2 * kChunk);
-  uint64_t* stgf = bars;                  // staging landed
-  uint64_t* stge = bars + 1;              // staging read (128)
-  uint64_t* split = bars + 2;             // [S] hi/lo ready (128)
-  uint64_t* empty = split + kStagesLegI;  // [S] MMAs done
-  uint64_t* accf = empty + kStagesLegI;   // [2]
-  uint64_t* acce = accf + 2;              // [2] (128)
+  uint64_t* stgf = bars;                        // [T] staging landed
+  uint64_t* stge = stgf + kStagingLegI;         // [T] staging read
+  uint64_t* split = stge + kStagingLegI;        // [S] hi/lo ready
+  uint64_t* empty = split + kStagesLegI;        // [S] MMAs done
+  uint64_t* accf = empty + kStagesLegI;         // [2]
+  uint64_t* acce = accf + 2;                    // [2]
   uint64_t* tabf = acce + 2;
   uint64_t* tabe = tabf + 1;
   uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   // per-group metadata and the tile slice, copied once to shared memory
   int64_t* s_si = (int64_t*)(bars + 64);          // [(2B-1)*2] S row offsets
-  int64_t* s_off = s_si + 2 * (2 * B - 1);         // [B] table image offsets
-  int* s_kc = (int*)(s_off + B);                   // [B] KC_P | KC_Q << 8
+  int64_t* s_off = s_si + 2 * (2 * B - 1);         // [2B] table image offsets per (|m|, half)
+  int* s_kc = (int*)(s_off + 2 * B);               // [B] KC_P | KC_Q << 8
   int2* s_tiles = (int2*)(((uintptr_t)(s_kc + B) + 7) & ~(uintptr_t)7);
   for (int k = threadIdx.x; k < 2 * (2 * B - 1); k += blockDim.x) s_si[k] = a.si_rows[k];
-  for (int k = threadIdx.x; k < B; k += blockDim.x) {
-    s_off[k] = a.am_off[k];
-    s_kc[k] = a.am_kc[k];
-  }
+  for (int k = threadIdx.x; k < 2 * B; k += blockDim.x) s_off[k] = a.am_off[k];
+  for (int k = threadIdx.x; k < B; k += blockDim.x) s_kc[k] = a.am_kc[k];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nh = npad > 64 ? 64 : npad;  // accumulator width (columns of one j'-half)
   uint32_t tmem_cols = 32;
   while (tmem_cols < (uint32_t)(8 * nh)) tmem_cols <<= 1;  // 2 buffers x {P, Q} x {main, corr}
   if (threadIdx.x == 0) {
-    mbar_init(stgf, 1);
-    mbar_init(stge, kSplitThreads);
+    for (int s = 0; s < kStagingLegI; ++s) {
+      mbar_init(stgf + s, 1);
+      mbar_init(stge + s, kSplitThreads);
+    }
     for (int s = 0; s < kStagesLegI; ++s) {
       mbar_init(split + s, kSplitThreads);
       mbar_init(empty + s, 1);
@@ -139,6 +142,9 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
+  // the resident table changes with (m_idx, half)
+  auto table_key = [&](int2 tl) { return 2 * tl.x + (tl.y & 1); };
+  auto abs_m = [&](int m_idx) { return m_idx >= B - 1 ? m_idx - (B - 1) : (B - 1) - m_idx; };
 
   if (warp == 0) {
     if (lane == 0) {
@@ -146,15 +152,15 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
       uint32_t c = 0;
       for (int t = 0; t < nt && !*abort_flag; ++t) {
         const int2 tl = s_tiles[t];
-        const int m_idx = tl.x;
-        const int am = m_idx >= B - 1 ? m_idx - (B - 1) : (B - 1) - m_idx;
+        const int m_idx = tl.x, jh = tl.y & 1;
+        const int am = abs_m(m_idx);
         const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
-        if (m_idx != cur) {
+        if (table_key(tl) != cur) {
           if (ngrp > 0 && !mbar_wait(tabe, (ngrp - 1) & 1, abort_flag)) break;
           const uint32_t bytes = (uint32_t)((kcp + kcq) * 2 * chunk_tab);
           mbar_arrive_tx(tabf, bytes);
-          bulk_load(tab, a.tabimg + s_off[am], bytes, tabf);
-          cur = m_idx;
+          bulk_load(tab, a.tabimg + s_off[2 * am + jh], bytes, tabf);
+          cur = table_key(tl);
           ++ngrp;
         }
         bool ok = true;
@@ -162,9 +168,10 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
           const int kcn = p ? kcq : kcp;
           const int64_t r0 = s_si[2 * m_idx + p];
           for (int kc = 0; kc < kcn; ++kc, ++c) {
-            if (!mbar_wait(stge, (c & 1) ^ 1, abort_flag)) { ok = false; break; }
-            mbar_arrive_tx(stgf, kChunk);
-            tma_load_2d(stg, &smap, stgf, tl.y & ~1, (int)(r0 + kc * 32));
+            const int s = c % kStagingLegI;
+            if (!mbar_wait(stge + s, ((c / kStagingLegI) & 1) ^ 1, abort_flag)) { ok = false; break; }
+            mbar_arrive_tx(stgf + s, kChunk);
+            tma_load_2d(stg + s * kChunk, &smap, stgf + s, tl.y & ~1, (int)(r0 + kc * 32));
           }
         }
         if (!ok) break;
@@ -176,14 +183,13 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
       uint32_t c = 0, tcount = 0;
       for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
         const int2 tl = s_tiles[t];
-        const int m_idx = tl.x;
         const int jh = tl.y & 1;
         const uint32_t idesc = idesc_tf32(jh ? npad - 64 : nh);
-        const int am = m_idx >= B - 1 ? m_idx - (B - 1) : (B - 1) - m_idx;
+        const int am = abs_m(tl.x);
         const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
-        if (m_idx != cur) {
+        if (table_key(tl) != cur) {
           if (!mbar_wait(tabf, ngrp & 1, abort_flag)) break;
-          cur = m_idx;
+          cur = table_key(tl);
           ++ngrp;
         }
         const int acc = tcount & 1;
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
           // accumulators of this buffer: [P main][P corr][Q main][Q corr], nh columns each
           const uint32_t d = tmem + (uint32_t)((4 * acc + 2 * p) * nh);
           const uint32_t dc = d + (uint32_t)nh;
-          const uint32_t th0 = smem_u32(tab) + (uint32_t)((p ? 2 * kcp : 0) * chunk_tab + jh * 64 * 128);
+          const uint32_t th0 = smem_u32(tab) + (uint32_t)((p ? 2 * kcp : 0) * chunk_tab);
           const uint32_t tl0 = th0 + (uint32_t)(kcn * chunk_tab);
           for (int kc = 0; kc < kcn; ++kc, ++c) {
             const int s = c % kStagesLegI;
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
         }
         if (!ok) break;
         mma_commit(accf + acc);
-        if (t + 1 >= nt || s_tiles[t + 1].x != cur) mma_commit(tabe);
+        if (t + 1 >= nt || table_key(s_tiles[t + 1]) != cur) mma_commit(tabe);
       }
     }
   } else if (warp < kFirstEpiWarp) {
@@ -228,18 +234,17 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
     const int r = tid & 127, h = tid >> 7;
     uint32_t c = 0;
     for (int t = 0; t < nt; ++t) {
-      const int2 tl = s_tiles[t];
-      const int m_idx = tl.x;
-      const int am = m_idx >= B - 1 ? m_idx - (B - 1) : (B - 1) - m_idx;
+      const int am = abs_m(s_tiles[t].x);
       const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
       bool ok = true;
       for (int ch = 0; ch < kcp + kcq; ++ch, ++c) {
-        if (!mbar_wait(stgf, c & 1, abort_flag)) { ok = false; break; }
+        const int st = c % kStagingLegI;
+        if (!mbar_wait(stgf + st, (c / kStagingLegI) & 1, abort_flag)) { ok = false; break; }
         float v[16];
-        const float* sp = (const float*)stg + 16 * h * 128;
+        const float* sp = (const float*)(stg + st * kChunk) + 16 * h * 128;
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = sp[k * 128 + r];
-        mbar_arrive(stge);
+        mbar_arrive(stge + st);
         const int s = c % kStagesLegI;
         if (!mbar_wait(empty + s, ((c / kStagesLegI) & 1) ^ 1, abort_flag)) { ok = false; break; }
         split_store<4>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h);
@@ -598,23 +603,28 @@ cudaError_t tc_inv_prepare(Plan& P) {
     const int B = sg.B, NB = sg.NB;
     TcInvSeg ts;
     ts.npad = pad16i(B);
-    // Legendre synthesis tables, per |m|: [P hi][P lo][Q hi][Q lo], rows j', K = l'
-    std::vector<int64_t> aoff(B, 0);
+    // Legendre synthesis tables, per (|m|, j'-half of 64 rows):
+    // [P hi][P lo][Q hi][Q lo], rows j', K = l'
+    const int nh = ts.npad > 64 ? 64 : ts.npad;
+    const int halves = (ts.npad + 63) / 64;
+    std::vector<int64_t> aoff(2 * B, 0);
     std::vector<int> akc(B, 0);
     int kcmax = 1;
     for (int am = 0; am < B; ++am) {
-      img.resize((img.size() + 1023) / 1024 * 1024);
-      aoff[am] = (int64_t)img.size();
       int kcs[2];
-      for (int p = 0; p < 2; ++p) {
-        const int K = n_par(B, am, p);
-        kcs[p] = (K + 31) / 32;
-        if (kcs[p] == 0) continue;
-        append_planes(img, ts.npad, K, kcs[p], [&](int j, int q) -> double {
-          if (j >= B) return 0.0;
-          const int l = am + p + 2 * q;
-          return H.lam[((size_t)am * B + l) * B + j];
-        });
+      for (int p = 0; p < 2; ++p) kcs[p] = (n_par(B, am, p) + 31) / 32;
+      for (int jh = 0; jh < halves; ++jh) {
+        img.resize((img.size() + 1023) / 1024 * 1024);
+        aoff[2 * am + jh] = (int64_t)img.size();
+        for (int p = 0; p < 2; ++p) {
+          if (kcs[p] == 0) continue;
+          append_planes(img, nh, n_par(B, am, p), kcs[p], [&](int jr, int q) -> double {
+            const int j = 64 * jh + jr;
+            if (j >= B) return 0.0;
+            const int l = am + p + 2 * q;
+            return H.lam[((size_t)am * B + l) * B + j];
+          });
+        }
       }
       akc[am] = kcs[0] | (kcs[1] << 8);
       kcmax = std::max(kcmax, kcs[0] + kcs[1]);
@@ -622,8 +632,8 @@ cudaError_t tc_inv_prepare(Plan& P) {
     ts.kcmax = kcmax;
     std::vector<int2> ltiles;
     for (int mi = 0; mi < 2 * B - 1; ++mi)
-      for (int r0 = 0; r0 < NB * 2 * B; r0 += 128)
-        for (int jh = 0; jh * 64 < ts.npad; ++jh) ltiles.push_back(make_int2(mi, r0 | jh));
+      for (int jh = 0; jh < halves; ++jh)
+        for (int r0 = 0; r0 < NB * 2 * B; r0 += 128) ltiles.push_back(make_int2(mi, r0 | jh));
     // radial inverse tables, per l: KC_l x [hi chunk][lo chunk], rows i (128), K = n'
     std::vector<int64_t> loff(B, 0);
     for (int l = 0; l < B; ++l) {
@@ -672,8 +682,9 @@ cudaError_t tc_inv_prepare(Plan& P) {
     // tables, staging, operand ring, barrier slots, metadata (S row offsets,
     // image offsets, chunk counts), tile slice
     const size_t meta = (size_t)2 * (2 * B - 1) * 8 + (size_t)B * 12 + 8;
-    ts.leg_smem = 1024 + (size_t)ts.kcmax * 2 * ts.npad * 128 + kChunk + (size_t)kStagesLegI * 2 * kChunk + 64 * 8 +
-                  meta + (size_t)lmax * 8;
+    const int nh_s = ts.npad > 64 ? 64 : ts.npad;
+    ts.leg_smem = 1024 + (size_t)ts.kcmax * 2 * nh_s * 128 + (size_t)kStagingLegI * kChunk +
+                  (size_t)kStagesLegI * 2 * kChunk + 64 * 8 + meta + (size_t)B * 8 + (size_t)lmax * 8;
     ts.rad_smem = 1024 + (size_t)kStagesRadI * 4 * kChunk + 64 * 8 + meta + (size_t)rmax * 8;
     if (ts.leg_smem > 227 * 1024 || ts.rad_smem > 227 * 1024) e = cudaErrorInvalidValue;
   }
