@@ -280,6 +280,41 @@ def e2e_path(plan, c_np, steps, warmup):
     return dt, nbytes
 
 
+def source_hash():
+    """Hash of the CUDA library sources (names and contents)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1604_05140_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cpp", ".h", ".cuh")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(prec, kernel, batch):
+    """DRAM bytes of one launch of `kernel` from the committed ncu capture
+    (per function x batch), or None when the capture is for other sources."""
+    if prec != "tf32x3":
+        return None
+    path = os.path.join(ROOT, "profiles", "tf32x3_kernels_b128x4_dram.md")
+    if not os.path.exists(path):
+        return None
+    recorded, per_fn = None, {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("source-hash:"):
+                recorded = line.split(":", 1)[1].strip()
+            if line.startswith("dram-bytes-per-function:"):
+                for kv in line.split(":", 1)[1].split():
+                    k, v = kv.split("=")
+                    per_fn[k] = int(v)
+    if recorded != source_hash() or kernel not in per_fn:
+        return None
+    return per_fn[kernel] * batch
+
+
 def roofline(stage, cbytes, prec):
     hbm, src = peaks()
     model = stage_model(B_BENCH, BATCH, cbytes)
@@ -287,7 +322,7 @@ def roofline(stage, cbytes, prec):
     ms, nl = stage[dom]
     nbytes, flops = model[dom]
     out = {"kernel": dom, "bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-           "traffic": None, "peak_source": src, "launch_ms": ms,
+           "traffic": measured_traffic(prec, dom, BATCH), "peak_source": src, "launch_ms": ms,
            "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
            "stage_ms": {k: v[0] for k, v in stage.items()}}
     out["frac"] = out["achieved"] / out["peak"]
