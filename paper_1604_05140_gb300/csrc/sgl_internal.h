@@ -91,6 +91,32 @@ inline int64_t si_rows_before(int B, int m_idx, int p) {
   return rows;
 }
 
+// Contiguous slices of an ordered tile list for `grid` persistent CTAs with
+// about equal estimated cost each: tile t goes to the CTA in whose share of
+// the total cost the tile's midpoint falls.  Returns grid + 1 offsets (CTA k
+// runs tiles first[k] .. first[k+1]-1; a slice may be empty) and the largest
+// slice in *max_slice.
+inline std::vector<int> balance_slices(const std::vector<double>& cost, int grid, int* max_slice) {
+  const int n = (int)cost.size();
+  std::vector<int> first(grid + 1, n);
+  double total = 0.0;
+  for (double c : cost) total += c;
+  int k = 0;
+  double p = 0.0;
+  for (int t = 0; t < n; ++t) {
+    const double mid = p + 0.5 * cost[t];
+    int c = total > 0.0 ? (int)(mid / total * grid) : 0;
+    if (c > grid - 1) c = grid - 1;
+    while (k <= c) first[k++] = t;
+    p += cost[t];
+  }
+  while (k <= grid) first[k++] = n;
+  int mx = 0;
+  for (int j = 0; j < grid; ++j) mx = first[j + 1] - first[j] > mx ? first[j + 1] - first[j] : mx;
+  *max_slice = mx;
+  return first;
+}
+
 // ---------------------------------------------------------------------------
 // Segments: functions of one bandlimit processed together
 // ---------------------------------------------------------------------------

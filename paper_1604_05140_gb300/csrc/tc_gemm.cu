@@ -80,6 +80,7 @@ using namespace tcx;
 
 struct TcArgs {
   const int2* tiles;            // (group, row0) in group order
+  const int* cta_first;         // tile slice of each CTA (gridDim.x + 1 offsets)
   int ntiles;
   const unsigned char* tabimg;  // pre-swizzled hi/lo tables
   const int64_t* grp_off;       // byte offset of each group's image (weighted set, then plain set)
@@ -149,8 +150,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   }
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
   // contiguous tile range of this CTA (re-based to 0 in shared memory)
-  const int g_begin = (int)((int64_t)a.ntiles * blockIdx.x / gridDim.x);
-  const int g_end = (int)((int64_t)a.ntiles * (blockIdx.x + 1) / gridDim.x);
+  const int g_begin = a.cta_first[blockIdx.x];
+  const int g_end = a.cta_first[blockIdx.x + 1];
   const int t_begin = 0, t_end = g_end - g_begin;
   const int64_t wsel = a.weighted ? 0 : a.ngroups;
   for (int k = threadIdx.x; k < t_end; k += blockDim.x) s_tiles[k] = a.tiles[g_begin + k];
@@ -295,13 +296,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int64_t rbase = a.w2_off + (int64_t)cc * B + i;
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
-          tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
-          if (NMAIN == 2) {
-            float w[16];
-            tmem_ld16(tmain1 + (uint32_t)c0, w);
-#pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] += w[k];
-          }
+          if (NMAIN == 2) tmem_ld16_sum3(taddr + (uint32_t)c0, tmain1 + (uint32_t)c0, tcorr + (uint32_t)c0, v);
+          else tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
           if (valid) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -326,13 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int64_t cbase = valid ? a.fn_coef[b] : 0;
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
-          tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
-          if (NMAIN == 2) {
-            float w[16];
-            tmem_ld16(tmain1 + (uint32_t)c0, w);
-#pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] += w[k];
-          }
+          if (NMAIN == 2) tmem_ld16_sum3(taddr + (uint32_t)c0, tmain1 + (uint32_t)c0, tcorr + (uint32_t)c0, v);
+          else tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
           if (valid) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -367,6 +358,7 @@ namespace {
 struct TcStage {
   CUtensorMap xmap;
   int2* d_tiles = nullptr;
+  int* d_first = nullptr;
   int ntiles = 0;
   int64_t* d_off = nullptr;
   int* d_npad = nullptr;
@@ -438,6 +430,7 @@ cudaError_t tc_prepare(Plan& P) {
     std::vector<int64_t> off;
     std::vector<int> npad;
     std::vector<int2> tiles;
+    std::vector<double> cost;  // estimated bytes moved per tile (slice balancing)
   };
   std::vector<Pending> pend;
   for (size_t s = 0; s < P.segs.size(); ++s) {
@@ -485,8 +478,13 @@ cudaError_t tc_prepare(Plan& P) {
       const int m = mi - (B - 1);
       const int am = m < 0 ? -m : m;
       for (int p = 0; p < 2; ++p) {
-        if (n_par(B, am, p) == 0) continue;
-        for (int r0 = 0; r0 < NB * 2 * B; r0 += 128) pl.tiles.push_back(make_int2(mi * 2 + p, r0));
+        const int N = n_par(B, am, p);
+        if (N == 0) continue;
+        for (int r0 = 0; r0 < NB * 2 * B; r0 += 128) {
+          pl.tiles.push_back(make_int2(mi * 2 + p, r0));
+          // X chunks in, S columns out, the group's table on its first tile
+          pl.cost.push_back(KC * 16384.0 + 512.0 * N + (r0 == 0 ? 256.0 * KC * pad16(N) : 0.0));
+        }
       }
     }
     ts.leg.ngroups = 2 * (2 * B - 1);
@@ -514,7 +512,10 @@ cudaError_t tc_prepare(Plan& P) {
         append_image(img, N, B, np, KC, A);
       }
     for (int l = 0; l < B; ++l)
-      for (int r0 = 0; r0 < NB * (2 * l + 1) * 2; r0 += 128) pr.tiles.push_back(make_int2(l, r0));
+      for (int r0 = 0; r0 < NB * (2 * l + 1) * 2; r0 += 128) {
+        pr.tiles.push_back(make_int2(l, r0));
+        pr.cost.push_back(KC * 16384.0 + 512.0 * (B - l) + (r0 == 0 ? 256.0 * KC * pad16(B - l) : 0.0));
+      }
     ts.rad.ngroups = B;
     ts.rad.npmax = npmax_r;
     ts.rad.KC = KC;
@@ -553,7 +554,13 @@ cudaError_t tc_prepare(Plan& P) {
       if (e != cudaSuccess) { delete st; return e; }
       const int stages = k == 0 ? kStagesLeg : kStagesRad;
       S.grid = S.ntiles < nsm ? S.ntiles : nsm;
-      const int max_tiles = (S.ntiles + S.grid - 1) / S.grid + 1;
+      int max_tiles = 0;
+      const std::vector<int> first = balance_slices(pd.cost, S.grid > 0 ? S.grid : 1, &max_tiles);
+      if (e == cudaSuccess) e = cudaMalloc(&S.d_first, first.size() * sizeof(int));
+      if (e == cudaSuccess) e = cudaMemcpy(S.d_first, first.data(), first.size() * sizeof(int),
+                                           cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) { delete st; return e; }
+      max_tiles += 1;
       // tables, X ring, 64 barrier/flag slots, group metadata, tile slice
       S.smem = 1024 + (size_t)2 * S.KC * S.npmax * 128 + (size_t)stages * 2 * kChunkBytes + 64 * 8 +
                (size_t)S.ngroups * 12 + 8 + (size_t)max_tiles * 8;
@@ -571,6 +578,7 @@ void tc_release(Plan& P) {
   for (TcSeg& s : st->segs)
     for (TcStage* S : {&s.leg, &s.rad}) {
       if (S->d_tiles) cudaFree(S->d_tiles);
+      if (S->d_first) cudaFree(S->d_first);
       if (S->d_off) cudaFree(S->d_off);
       if (S->d_npad) cudaFree(S->d_npad);
     }
@@ -597,6 +605,7 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
     const SegDesc& sg = P.segs[k];
     TcArgs a;
     a.tiles = S.d_tiles;
+    a.cta_first = S.d_first;
     a.ntiles = S.ntiles;
     a.tabimg = st->d_img;
     a.grp_off = S.d_off;

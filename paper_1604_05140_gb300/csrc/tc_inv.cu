@@ -72,6 +72,7 @@ __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo
 // read once per half.
 struct LegIArgs {
   const int2* tiles;          // (m_idx, row0 | j'-half), ordered by (m_idx, half, row0)
+  const int* cta_first;       // tile slice of each CTA (gridDim.x + 1 offsets)
   int ntiles;
   const unsigned char* tabimg;
   const int64_t* am_off;      // image offset per (|m|, half)
@@ -134,9 +135,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
-  const int g_begin = (int)((int64_t)a.ntiles * blockIdx.x / gridDim.x);
-  const int g_end = (int)((int64_t)a.ntiles * (blockIdx.x + 1) / gridDim.x);
-  const int nt = g_end - g_begin;
+  const int g_begin = a.cta_first[blockIdx.x];
+  const int nt = a.cta_first[blockIdx.x + 1] - g_begin;
   for (int k = threadIdx.x; k < nt; k += blockDim.x) s_tiles[k] = a.tiles[g_begin + k];
   tc_before();
   __syncthreads();
@@ -316,8 +316,14 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
 // ===========================================================================
 // inverse radial
 // ===========================================================================
+// Tiles of degrees with more than 64 terms (B - l > 64) are 64 columns wide
+// and keep two main accumulators (even and odd K steps) besides the
+// correction, so that no accumulator takes more than 8 truncating additions
+// of hi*hi products; the other tiles are 128 columns wide with one main
+// accumulator.  Either way a tile uses 256 TMEM columns, two tiles in flight.
 struct RadIArgs {
-  const int2* tiles;          // (l, col0), grouped by l
+  const int2* tiles;          // (l, col0 | narrow), grouped by l
+  const int* cta_first;       // tile slice of each CTA (gridDim.x + 1 offsets)
   int ntiles;
   const unsigned char* tabimg;
   const int64_t* l_off;       // image offset per l (KC_l chunk pairs of 32 KB)
@@ -329,6 +335,34 @@ struct RadIArgs {
   int B, NB;
 };
 
+// Coefficients of one K chunk (32 degrees n) of one tile column, gathered by
+// split thread tid: 16 (wide tile) or 8 (narrow tile) consecutive degrees.
+__device__ __forceinline__ void rad_gather(const RadIArgs& a, int2 tl, int kc, int tid, float* v) {
+  const int B = a.B, l = tl.x;
+  const bool nar = tl.y & 1;
+  const int col_in = nar ? (tid & 63) : (tid & 127);
+  const int h = nar ? (tid >> 6) : (tid >> 7);
+  const int nv = nar ? 8 : 16;
+  const int per_b = (2 * l + 1) * 2;
+  const int col = (tl.y & ~1) + col_in;
+  const bool valid = col < a.NB * per_b;
+  const int b = valid ? col / per_b : 0;
+  const int rem = col - b * per_b;
+  const int m = (rem >> 1) - l, cc = rem & 1;
+  const float* cf = a.coef + 2 * a.fn_coef[b] + cc;
+  const int np0 = kc * 32 + h * nv;        // degree n = l + 1 + n'
+  int n = l + 1 + np0;
+  int64_t off = omega_of(n, l, m);          // omega(n + 1) - omega(n) = n^2
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    if (k < nv) {
+      v[k] = (valid && np0 + k < B - l) ? cf[2 * off] : 0.f;
+      off += (int64_t)n * n;
+      ++n;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -337,10 +371,10 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   unsigned char* st = base;
   uint64_t* bars = (uint64_t*)(st + kStagesRadI * 4 * kChunk);
   uint64_t* tfull = bars;                   // [S] table chunk landed
-  uint64_t* split = tfull + kStagesRadI;    // [S] data ready (128)
+  uint64_t* split = tfull + kStagesRadI;    // [S] data ready (split threads)
   uint64_t* empty = split + kStagesRadI;    // [S] MMAs done
   uint64_t* accf = empty + kStagesRadI;     // [2]
-  uint64_t* acce = accf + 2;                // [2] (128)
+  uint64_t* acce = accf + 2;                // [2] (epilogue threads)
   uint32_t* tmem_slot = (uint32_t*)(acce + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   int64_t* s_si = (int64_t*)(bars + 64);          // [(2B-1)*2] S row offsets
@@ -350,7 +384,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   for (int k = threadIdx.x; k < B; k += blockDim.x) s_loff[k] = a.l_off[k];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t tmem_cols = 512;  // 2 buffers x {main, corr} x 128 columns
+  const uint32_t tmem_cols = 512;  // 2 buffers x 256 columns
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesRadI; ++s) {
       mbar_init(tfull + s, 1);
@@ -365,9 +399,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
-  const int g_begin = (int)((int64_t)a.ntiles * blockIdx.x / gridDim.x);
-  const int g_end = (int)((int64_t)a.ntiles * (blockIdx.x + 1) / gridDim.x);
-  const int nt = g_end - g_begin;
+  const int g_begin = a.cta_first[blockIdx.x];
+  const int nt = a.cta_first[blockIdx.x + 1] - g_begin;
   for (int k = threadIdx.x; k < nt; k += blockDim.x) s_tiles[k] = a.tiles[g_begin + k];
   tc_before();
   __syncthreads();
@@ -393,15 +426,18 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   } else if (warp == 1) {
     if (lane == 0) {
       uint32_t c = 0, tcount = 0;
-      const uint32_t idesc = idesc_tf32(128);
       for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
-        const int l = s_tiles[t].x;
+        const int2 tl = s_tiles[t];
+        const int l = tl.x;
+        const bool nar = tl.y & 1;
+        const uint32_t idesc = idesc_tf32(nar ? 64 : 128);
         const int kcn = (B - l + 31) / 32;
         const int acc = tcount & 1;
         if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
         tc_after();
-        const uint32_t d = tmem + (uint32_t)(acc * 256);  // main
-        const uint32_t dc = d + 128u;                     // correction
+        // buffer: wide [main 128][corr 128], narrow [main 64][main 64][corr 64]
+        const uint32_t d = tmem + (uint32_t)(acc * 256);
+        const uint32_t dc = d + 128u;
         bool ok = true;
         for (int kc = 0; kc < kcn; ++kc, ++c) {
           const int s = c % kStagesRadI;
@@ -419,7 +455,9 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t ko = (uint32_t)(kk * 32);
             const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
-            mma_tf32(d, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, first);
+            const uint32_t dm = nar ? d + (uint32_t)((kk & 1) * 64) : d;
+            const uint32_t first_m = nar ? ((kc > 0 || kk >= 2) ? 1u : 0u) : first;
+            mma_tf32(dm, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, first_m);
             mma_tf32(dc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, first);
             mma_tf32(dc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
           }
@@ -430,41 +468,33 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       }
     }
   } else if (warp < kFirstEpiWarp) {
-    // gather: column (b, m, c) of the tile; thread (col, h) loads the degrees
-    // n' = 32 kc + 16h .. +15 of the chunk
+    // gather: thread (column, h) loads 16 (wide) or 8 (narrow) consecutive
+    // degrees of its column per chunk; the next chunk's loads are issued
+    // before the current chunk is split and stored
     const int tid = threadIdx.x - 32 * kFirstSplitWarp;
-    const int col_in = tid & 127, h = tid >> 7;
-    uint32_t c = 0;
-    for (int t = 0; t < nt; ++t) {
+    float v[16], vn[16];
+    int t = 0, kc = 0;
+    if (nt > 0) rad_gather(a, s_tiles[0], 0, tid, v);
+    for (uint32_t c = 0; t < nt; ++c) {
       const int2 tl = s_tiles[t];
-      const int l = tl.x;
-      const int kcn = (B - l + 31) / 32;
-      const int per_b = (2 * l + 1) * 2;
-      const int col = tl.y + col_in;
-      const bool valid = col < NB * per_b;
-      const int b = valid ? col / per_b : 0;
-      const int rem = col - b * per_b;
-      const int m = (rem >> 1) - l, cc = rem & 1;
-      const float* cf = a.coef + 2 * a.fn_coef[b] + cc;
-      bool ok = true;
-      for (int kc = 0; kc < kcn; ++kc, ++c) {
-        const int s = c % kStagesRadI;
-        if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) { ok = false; break; }
-        float v[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int np = kc * 32 + 16 * h + k;   // n = l + 1 + np
-          const int n = l + 1 + np;
-          v[k] = (valid && np < B - l)
-                     ? cf[2 * ((int64_t)n * (n - 1) * (2 * n - 1) / 6 + (int64_t)l * (l + 1) + m)]
-                     : 0.f;
-        }
-        unsigned char* sb = st + s * 4 * kChunk + 2 * kChunk;
-        split_store<4>(sb, sb + kChunk, col_in, v, 4 * h);
-        fence_proxy_async();
-        mbar_arrive(split + s);
+      const bool nar = tl.y & 1;
+      int tn = t, kcn_next = kc + 1;
+      if (kcn_next == (B - tl.x + 31) / 32) {
+        tn = t + 1;
+        kcn_next = 0;
       }
-      if (!ok) break;
+      if (tn < nt) rad_gather(a, s_tiles[tn], kcn_next, tid, vn);
+      const int s = c % kStagesRadI;
+      if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) break;
+      unsigned char* sb = st + s * 4 * kChunk + 2 * kChunk;
+      if (nar) split_store<2>(sb, sb + kChunk, tid & 63, v, 2 * (tid >> 6));
+      else split_store<4>(sb, sb + kChunk, tid & 127, v, 4 * (tid >> 7));
+      fence_proxy_async();
+      mbar_arrive(split + s);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = vn[k];
+      t = tn;
+      kc = kcn_next;
     }
   } else {
     const int quarter = warp & 3;
@@ -477,20 +507,24 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
       tc_after();
       const int l = tl.x;
+      const bool nar = tl.y & 1;
+      const int col0 = tl.y & ~1;
+      const int width = nar ? 64 : 128;
       const int per_b = (2 * l + 1) * 2;
       const int ncol = NB * per_b;
       const int64_t L = (int64_t)NB * 2 * B;
       const uint32_t dq = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quarter * 32) << 16);
       // column (b, rem = 2(m+l) + c) decoded at the start of each 16-column
       // block, then stepped
-      for (int c0 = 16 * ehalf; c0 < 128; c0 += 32) {
+      for (int c0 = 16 * ehalf; c0 < width; c0 += 32) {
         float v[16];
-        tmem_ld16_sum(dq + (uint32_t)c0, dq + (uint32_t)(128 + c0), v);
-        int b = (tl.y + c0) / per_b;
-        int rem = tl.y + c0 - b * per_b;
+        if (nar) tmem_ld16_sum3(dq + (uint32_t)c0, dq + (uint32_t)(64 + c0), dq + (uint32_t)(128 + c0), v);
+        else tmem_ld16_sum(dq + (uint32_t)c0, dq + (uint32_t)(128 + c0), v);
+        int b = (col0 + c0) / per_b;
+        int rem = col0 + c0 - b * per_b;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-          if (i < B && tl.y + c0 + k < ncol) {
+          if (i < B && col0 + c0 + k < ncol) {
             const int m = (rem >> 1) - l, cc = rem & 1;
             const int am = m < 0 ? -m : m;
             const int p = (l - am) & 1;
@@ -560,6 +594,7 @@ struct TcInvSeg {
   // Legendre
   CUtensorMap smap;
   int2* leg_tiles = nullptr;
+  int* leg_first = nullptr;
   int leg_ntiles = 0, leg_grid = 0;
   size_t leg_smem = 0;
   int64_t* am_off = nullptr;
@@ -567,6 +602,7 @@ struct TcInvSeg {
   int npad = 0, kcmax = 0;
   // radial
   int2* rad_tiles = nullptr;
+  int* rad_first = nullptr;
   int rad_ntiles = 0, rad_grid = 0;
   size_t rad_smem = 0;
   int64_t* l_off = nullptr;
@@ -597,6 +633,7 @@ cudaError_t tc_inv_prepare(Plan& P) {
   std::vector<std::vector<int64_t>> am_offs, l_offs;
   std::vector<std::vector<int>> am_kcs;
   std::vector<std::vector<int2>> lt, rt;
+  std::vector<std::vector<double>> lcost, rcost;  // estimated bytes moved per tile
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
     const HostTables& H = P.tables[s];
@@ -631,9 +668,18 @@ cudaError_t tc_inv_prepare(Plan& P) {
     }
     ts.kcmax = kcmax;
     std::vector<int2> ltiles;
-    for (int mi = 0; mi < 2 * B - 1; ++mi)
+    std::vector<double> lc;
+    for (int mi = 0; mi < 2 * B - 1; ++mi) {
+      const int am = mi < B - 1 ? B - 1 - mi : mi - (B - 1);
+      const int kcs = (akc[am] & 0xff) + (akc[am] >> 8);
       for (int jh = 0; jh < halves; ++jh)
-        for (int r0 = 0; r0 < NB * 2 * B; r0 += 128) ltiles.push_back(make_int2(mi, r0 | jh));
+        for (int r0 = 0; r0 < NB * 2 * B; r0 += 128) {
+          ltiles.push_back(make_int2(mi, r0 | jh));
+          // S chunks in, both G halves out, the table on its first tile
+          const int ncols = jh ? ts.npad - 64 : nh;
+          lc.push_back(kcs * 16384.0 + 1024.0 * ncols + (r0 == 0 ? 2.0 * kcs * nh * 128 : 0.0));
+        }
+    }
     // radial inverse tables, per l: KC_l x [hi chunk][lo chunk], rows i (128), K = n'
     std::vector<int64_t> loff(B, 0);
     for (int l = 0; l < B; ++l) {
@@ -647,9 +693,19 @@ cudaError_t tc_inv_prepare(Plan& P) {
           return H.T[((size_t)l * B + (l + np)) * B + i];
         });
     }
+    // tiles: 64 columns with two main accumulators where B - l > 64, else 128
     std::vector<int2> rtiles;
-    for (int l = 0; l < B; ++l)
-      for (int c0 = 0; c0 < NB * (2 * l + 1) * 2; c0 += 128) rtiles.push_back(make_int2(l, c0));
+    std::vector<double> rc;
+    for (int l = 0; l < B; ++l) {
+      const int nar = B - l > 64 ? 1 : 0;
+      const int width = nar ? 64 : 128;
+      const int kcn = (B - l + 31) / 32;
+      for (int c0 = 0; c0 < NB * (2 * l + 1) * 2; c0 += width) {
+        rtiles.push_back(make_int2(l, c0 | nar));
+        // gathered coefficients, table chunks (from L2, half weight), S out
+        rc.push_back(kcn * (width * 128.0 + 16384.0) + 512.0 * width);
+      }
+    }
     // tensor map over S: [B^2 rows of l'][NB*2*B]
     float* w2 = (float*)P.d_w2 + sg.w2_off;
     if (!make_map_2d(&ts.smap, w2, (uint64_t)NB * 2 * B, (uint64_t)B * B, 128, 32, CU_TENSOR_MAP_SWIZZLE_NONE)) {
@@ -662,6 +718,8 @@ cudaError_t tc_inv_prepare(Plan& P) {
     l_offs.push_back(loff);
     lt.push_back(ltiles);
     rt.push_back(rtiles);
+    lcost.push_back(lc);
+    rcost.push_back(rc);
   }
   int64_t bytes = 0;
   cudaError_t e = upload(&st->d_img, img, bytes);
@@ -677,8 +735,13 @@ cudaError_t tc_inv_prepare(Plan& P) {
     ts.rad_ntiles = (int)rt[s].size();
     ts.leg_grid = std::min(ts.leg_ntiles, nsm);
     ts.rad_grid = std::min(ts.rad_ntiles, nsm);
-    const int lmax = (ts.leg_ntiles + ts.leg_grid - 1) / std::max(ts.leg_grid, 1) + 1;
-    const int rmax = (ts.rad_ntiles + ts.rad_grid - 1) / std::max(ts.rad_grid, 1) + 1;
+    int lmax = 0, rmax = 0;
+    const std::vector<int> lf = balance_slices(lcost[s], std::max(ts.leg_grid, 1), &lmax);
+    const std::vector<int> rf = balance_slices(rcost[s], std::max(ts.rad_grid, 1), &rmax);
+    if (e == cudaSuccess) e = upload(&ts.leg_first, lf, bytes);
+    if (e == cudaSuccess) e = upload(&ts.rad_first, rf, bytes);
+    lmax += 1;
+    rmax += 1;
     // tables, staging, operand ring, barrier slots, metadata (S row offsets,
     // image offsets, chunk counts), tile slice
     const size_t meta = (size_t)2 * (2 * B - 1) * 8 + (size_t)B * 12 + 8;
@@ -701,7 +764,7 @@ void tc_inv_release(Plan& P) {
   TcInvState* st = (TcInvState*)P.tc_inv_state;
   if (!st) return;
   for (TcInvSeg& s : st->segs) {
-    void* ptrs[] = {s.leg_tiles, s.am_off, s.am_kc, s.rad_tiles, s.l_off};
+    void* ptrs[] = {s.leg_tiles, s.leg_first, s.am_off, s.am_kc, s.rad_tiles, s.rad_first, s.l_off};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -722,6 +785,7 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
     if (prob == 2) {
       RadIArgs a;
       a.tiles = ts.rad_tiles;
+      a.cta_first = ts.rad_first;
       a.ntiles = ts.rad_ntiles;
       a.tabimg = st->d_img;
       a.l_off = ts.l_off;
@@ -738,6 +802,7 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
     } else {
       LegIArgs a;
       a.tiles = ts.leg_tiles;
+      a.cta_first = ts.leg_first;
       a.ntiles = ts.leg_ntiles;
       a.tabimg = st->d_img;
       a.am_off = ts.am_off;

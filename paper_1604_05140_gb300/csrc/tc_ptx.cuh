@@ -125,13 +125,44 @@ static __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// Two 16-column loads issued together, one wait.
+static __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float* va, float* vb) {
+  uint32_t r[32];
+  asm volatile(
+      "{\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%33];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      "}\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    va[k] = __uint_as_float(r[k]);
+    vb[k] = __uint_as_float(r[16 + k]);
+  }
+}
+
 // main + correction accumulators, 16 columns each, summed with round-to-nearest
 static __device__ __forceinline__ void tmem_ld16_sum(uint32_t tmain, uint32_t tcorr, float* v) {
   float c[16];
-  tmem_ld16(tmain, v);
-  tmem_ld16(tcorr, c);
+  tmem_ld16x2(tmain, tcorr, v, c);
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] += c[k];
+}
+
+// two main accumulators and a correction: (main0 + main1) + corr
+static __device__ __forceinline__ void tmem_ld16_sum3(uint32_t tm0, uint32_t tm1, uint32_t tcorr, float* v) {
+  float w[16], c[16];
+  tmem_ld16x2(tm0, tm1, v, w);
+  tmem_ld16(tcorr, c);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = (v[k] + w[k]) + c[k];
 }
 
 static __device__ __forceinline__ float tf32_rna(float x) {
