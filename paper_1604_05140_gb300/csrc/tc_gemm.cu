@@ -299,15 +299,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (NMAIN == 2) tmem_ld16_sum3(taddr + (uint32_t)c0, tmain1 + (uint32_t)c0, tcorr + (uint32_t)c0, v);
           else tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
           if (valid) {
+            // S_f[l][b][m+l][c][i] = 2B (NB l^2 + b(2l+1) + m + l) + c B + i, stepped in l += 2
+            int l = am + p + 2 * c0;
+            int64_t t = (int64_t)NB * l * l + (int64_t)(2 * b + 1) * l + b + m;
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-              const int col = c0 + k;
-              if (col < ncol) {
-                // S_f[l][b][m+l][c][i] = 2B (NB l^2 + b(2l+1) + m + l) + c B + i
-                const int l = am + p + 2 * col;
-                const int64_t t = (int64_t)NB * l * l + (int64_t)(2 * b + 1) * l + b + m;
-                Y[rbase + 2 * (int64_t)B * t] = sgn * v[k];
-              }
+              if (c0 + k < ncol) Y[rbase + 2 * (int64_t)B * t] = sgn * v[k];
+              t += (int64_t)NB * (4 * l + 4) + 2 * (2 * b + 1);
+              l += 2;
             }
           }
         }
@@ -325,10 +324,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (NMAIN == 2) tmem_ld16_sum3(taddr + (uint32_t)c0, tmain1 + (uint32_t)c0, tcorr + (uint32_t)c0, v);
           else tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
           if (valid) {
+            // omega(n + 1, l, m) - omega(n, l, m) = n^2
+            int n = l + 1 + c0;
+            int64_t off = cbase + omega_of(n, l, mm - l);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-              const int col = c0 + k;
-              if (col < ncol) Y[2 * (cbase + omega_of(l + 1 + col, l, mm - l)) + cc] = v[k];
+              if (c0 + k < ncol) Y[2 * off + cc] = v[k];
+              off += (int64_t)n * n;
+              ++n;
             }
           }
         }

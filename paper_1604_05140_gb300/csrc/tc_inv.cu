@@ -511,30 +511,29 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       const int col0 = tl.y & ~1;
       const int width = nar ? 64 : 128;
       const int per_b = (2 * l + 1) * 2;
-      const int ncol = NB * per_b;
-      const int64_t L = (int64_t)NB * 2 * B;
       const uint32_t dq = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quarter * 32) << 16);
-      // column (b, rem = 2(m+l) + c) decoded at the start of each 16-column
-      // block, then stepped
       for (int c0 = 16 * ehalf; c0 < width; c0 += 32) {
-        float v[16];
-        if (nar) tmem_ld16_sum3(dq + (uint32_t)c0, dq + (uint32_t)(64 + c0), dq + (uint32_t)(128 + c0), v);
-        else tmem_ld16_sum(dq + (uint32_t)c0, dq + (uint32_t)(128 + c0), v);
-        int b = (col0 + c0) / per_b;
-        int rem = col0 + c0 - b * per_b;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          if (i < B && col0 + c0 + k < ncol) {
+        // lane k < 16 finds the S offset of column c0 + k (b, m, c); the
+        // stores take it by shuffle
+        int64_t o = -1;
+        {
+          const int col = col0 + c0 + (lane & 15);
+          if (col < NB * per_b) {
+            const int b = col / per_b, rem = col - b * per_b;
             const int m = (rem >> 1) - l, cc = rem & 1;
             const int am = m < 0 ? -m : m;
             const int p = (l - am) & 1;
             const int64_t srow = s_si[2 * (m + B - 1) + p] + ((l - am - p) >> 1);
-            a.s[srow * L + ((int64_t)b * 2 + cc) * B + i] = v[k];
+            o = srow * ((int64_t)NB * 2 * B) + ((int64_t)b * 2 + cc) * B;
           }
-          if (++rem == per_b) {
-            rem = 0;
-            ++b;
-          }
+        }
+        float v[16];
+        if (nar) tmem_ld16_sum3(dq + (uint32_t)c0, dq + (uint32_t)(64 + c0), dq + (uint32_t)(128 + c0), v);
+        else tmem_ld16_sum(dq + (uint32_t)c0, dq + (uint32_t)(128 + c0), v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int64_t ok = __shfl_sync(0xffffffffu, o, k);
+          if (i < B && ok >= 0) a.s[ok + i] = v[k];
         }
       }
       tc_before();

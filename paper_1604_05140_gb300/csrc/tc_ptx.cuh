@@ -55,13 +55,26 @@ static __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) 
   return ok != 0;
 }
 
+// As mbar_try, but the thread may sleep in the instruction until the phase
+// completes or about `ns` nanoseconds have passed, so that waiting warps take
+// no issue slots from the working ones.
+static __device__ __forceinline__ bool mbar_try_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait for the phase of the given parity.  On timeout, or when another
 // role already aborted, returns false.
 static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try_sleep(bar, parity, 100000u)) return true;
     if (*abort_flag) return false;
     if (gtimer() - t0 > kWaitNs) {
       *abort_flag = 1;
