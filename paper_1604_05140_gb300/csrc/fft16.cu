@@ -141,7 +141,7 @@ template <typename real, int N2>
 __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   constexpr int N = 16 * N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);      // W_N^k, k < N
+  c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);      // [k1 < 16][c < N2]: W_N^{c k1}
   c2<real>* buf = tw + N;                                    // 2*JP rings of N
   const int4 cta = a.ctas[blockIdx.x];
   const SegDesc sg = a.segs[cta.x];
@@ -152,7 +152,12 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   const int JP = min(JPmax, B - j0);
   const int R = 2 * JP;
   const real* misc = reinterpret_cast<const real*>(a.tab) + sg.tab_misc;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = {misc[5 * B + 2 * k], misc[5 * B + 2 * k + 1]};
+  // twiddles indexed [k1][c], so that the threads of a warp (consecutive c)
+  // read consecutive words
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const int e = (k % N2) * (k / N2);  // < N
+    tw[k] = {misc[5 * B + 2 * e], misc[5 * B + 2 * e + 1]};
+  }
   real scale = 1;
   if (a.mode == 1) scale = misc[B + i];
   if (a.mode == 2) scale = misc[2 * B + i];
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
       for (int n1 = 0; n1 < 16; ++n1) v[u][n1] = {v[u][n1].x * scale, v[u][n1].y * scale};
       fft_n<real, 16, false>(v[u]);
 #pragma unroll
-      for (int k1 = 1; k1 < 16; ++k1) v[u][k1] = cmul(v[u][k1], tw[cc[u] * k1]);
+      for (int k1 = 1; k1 < 16; ++k1) v[u][k1] = cmul(v[u][k1], tw[k1 * N2 + cc[u]]);
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) buf[spos<N2>(rr[u], k1, cc[u])] = v[u][k1];
     }

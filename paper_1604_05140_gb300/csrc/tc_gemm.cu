@@ -6,15 +6,19 @@
 // X: the stage's FP32 input rows (E/O spectra, or per-degree spectra), K-major;
 // A: the FP64 table rounded to a hi + lo pair of TF32 values.  Three TF32
 // products per K step, X_hi A_hi + X_hi A_lo + X_lo A_hi, accumulate in FP32 in
-// tensor memory (the lo*lo term is below FP32 round-off).
+// tensor memory (the lo*lo term is below FP32 round-off).  The table image
+// stacks the hi rows over the lo rows of each K chunk, so that one MMA of
+// width 2N gives X_hi A_hi and X_hi A_lo side by side and a second of width N
+// adds X_lo A_hi to the latter: two MMAs per K step.
 //
-// One persistent CTA per SM, warp-specialized (320 threads):
+// One persistent CTA per SM, warp-specialized (608 threads):
 //   warp 0      TMA producer: 128-row x 32-float X chunks (SWIZZLE_128B) into a
-//               4-stage ring; the group's pre-swizzled hi/lo table by bulk copy
-//   warp 1      TMEM owner and MMA issuer (one thread): 3 x 4 tcgen05.mma per chunk
-//   warps 2-5   split: X -> hi (in place, cvt.rna.tf32) and lo = X - hi
-//   warps 6-9   epilogue: tcgen05.ld of the double-buffered accumulator, sign,
+//               staged ring; the group's pre-swizzled hi/lo table by bulk copy
+//   warp 1      TMEM owner and MMA issuer of the even K steps (one thread)
+//   warps 2-9   split: X -> hi (in place, cvt.rna.tf32) and lo = X - hi
+//   warps 10-17 epilogue: tcgen05.ld of the double-buffered accumulators, sign,
 //               scatter to the next stage's layout
+//   warp 18     MMA issuer of the odd K steps (one thread)
 // Every wait on an mbarrier is bounded: after ~2 s the CTA sets the plan's
 // error flag, stops, and frees its tensor memory.
 #include <cuda.h>
@@ -23,6 +27,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "sgl_internal.h"
@@ -68,10 +73,11 @@ namespace {
 
 enum { TC_LEG_F = 0, TC_RAD_F = 1 };
 
-// pipeline depth: the Legendre table (<= 64 rows) leaves room for 4 stages,
-// the radial table (<= 128 rows) for 2
+// pipeline depth: both tables are at most 64 rows (radial degrees with more
+// than 64 terms are cut into two groups), which leaves room for 4 stages
 constexpr int kStagesLeg = 4;
-constexpr int kStagesRad = 2;
+constexpr int kStagesRad = 4;
+constexpr int kRadRows = 64;  // largest radial group (rows n' of the table)
 constexpr int kChunkBytes = 128 * 128;  // 128 rows x 32 floats
 constexpr int kThreads = tcx::kRoleThreads;
 
@@ -84,7 +90,7 @@ struct TcArgs {
   int ntiles;
   const unsigned char* tabimg;  // pre-swizzled hi/lo tables
   const int64_t* grp_off;       // byte offset of each group's image (weighted set, then plain set)
-  const int* grp_npad;          // padded N of each group
+  const int* grp_npad;          // padded N of each group | l << 8 | n0 << 16 (radial)
   int ngroups;
   void* y;
   const int64_t* fn_coef;
@@ -116,35 +122,34 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   // per-CTA copies of the tile slice and of the group metadata, so that no
   // role waits on a global load per tile
   int64_t* s_off = (int64_t*)(bars + 64);                 // [ngroups] table image offsets
-  int* s_npad = (int*)(s_off + a.ngroups);                 // [ngroups] padded N
+  int* s_npad = (int*)(s_off + a.ngroups);                 // [ngroups] padded N (| l, n0 for radial)
   int2* s_tiles = (int2*)(((uintptr_t)(s_npad + a.ngroups) + 7) & ~(uintptr_t)7);  // [max_tiles]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // per tile: a main accumulator (hi*hi) and a correction accumulator
-  // (hi*lo + lo*hi), double-buffered.  The tensor cores round partial sums
-  // toward zero; keeping the small corrections apart cuts the number of
-  // truncating additions into the large accumulator by three, and the two are
-  // added with round-to-nearest in the epilogue.
-  // With NMAIN = 2 the hi*hi products of even and odd K steps go to two main
-  // accumulators, halving the truncating additions again (Legendre stage,
-  // whose accumulators are at most 64 columns wide).
-  constexpr int NMAIN = (PROB == TC_LEG_F) ? 2 : 1;
-  constexpr int NACC = NMAIN + 1;
+  // Per tile two pairs of a main accumulator (hi*hi) and a correction
+  // accumulator (hi*lo + lo*hi), [main0 | corr0 | main1 | corr1], npmax
+  // columns each, double-buffered: pair k takes the K steps of parity k and is
+  // fed by MMA issuer k.  The tensor cores round partial sums toward zero;
+  // keeping the small corrections apart, and the K steps in two chains, cuts
+  // the truncating additions into each main accumulator by six, and the four
+  // are added with round-to-nearest in the epilogue.  Groups have at most 64
+  // rows, so a buffer is at most 256 columns.
+  const uint32_t bufcols = (uint32_t)(4 * a.npmax);
   uint32_t tmem_cols = 32;
-  while (tmem_cols < (uint32_t)(2 * NACC * a.npmax)) tmem_cols <<= 1;  // power of two >= 32
+  while (tmem_cols < 2 * bufcols) tmem_cols <<= 1;  // power of two >= 32
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full + s, 1);
       mbar_init(split + s, kSplitThreads);
-      mbar_init(empty + s, 1);
+      mbar_init(empty + s, 2);  // both MMA issuers
     }
     for (int k = 0; k < 2; ++k) {
-      mbar_init(accf + k, 1);
+      mbar_init(accf + k, 2);
       mbar_init(acce + k, kEpiThreads);
     }
     mbar_init(tabf, 1);
-    mbar_init(tabe, 1);
+    mbar_init(tabe, 2);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int2 tl = s_tiles[t];
         if (tl.x != cur) {
           if (ngrp > 0 && !mbar_wait(tabe, (ngrp - 1) & 1, abort_flag)) break;
-          const uint32_t bytes = (uint32_t)(2 * KC * s_npad[tl.x] * 128);
+          const uint32_t bytes = (uint32_t)(2 * KC * (s_npad[tl.x] & 0xff) * 128);
           mbar_arrive_tx(tabf, bytes);
           bulk_load(tab, a.tabimg + s_off[tl.x], bytes, tabf);
           cur = tl.x;
@@ -182,8 +187,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
         // tensor rows of this tile
         int64_t row;
-        if (PROB == TC_LEG_F) row = (int64_t)tl.x * NB * 2 * B + tl.y;
-        else row = (int64_t)NB * 2 * tl.x * tl.x + tl.y;
+        if (PROB == TC_LEG_F) {
+          row = (int64_t)tl.x * NB * 2 * B + tl.y;
+        } else {
+          const int l = (s_npad[tl.x] >> 8) & 0xff;
+          row = (int64_t)NB * 2 * l * l + tl.y;
+        }
         for (int kc = 0; kc < KC; ++kc, ++c) {
           const int s = c % STAGES;
           if (!mbar_wait(empty + s, ((c / STAGES) & 1) ^ 1, abort_flag)) break;
@@ -192,11 +201,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
       }
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
+  } else if (warp == 1 || warp == kMma2Warp) {
+    // ---------------- MMA issuers: K steps of parity `me` ----------------
     if (lane == 0) {
+      const int me = warp == 1 ? 0 : 1;
       int cur = -1, ngrp = 0;
       uint32_t c = 0, tcount = 0;
+      const uint64_t xdesc0 = sw128_desc(smem_u32(xs));
+      const uint64_t tdesc0 = sw128_desc(smem_u32(tab));
       for (int t = t_begin; t < t_end && !*abort_flag; ++t, ++tcount) {
         const int2 tl = s_tiles[t];
         if (tl.x != cur) {
@@ -204,35 +216,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           cur = tl.x;
           ++ngrp;
         }
-        const int npad = s_npad[tl.x];
-        const uint32_t idesc = idesc_tf32(npad);
+        const int npad = s_npad[tl.x] & 0xff;
+        const uint32_t idesc2 = idesc_tf32(2 * npad), idesc1 = idesc_tf32(npad);
         const int acc = tcount & 1;
         if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
         tc_after();
-        // buffer acc: [main 0][main 1 (NMAIN = 2)][correction], npmax columns each
-        const uint32_t d = tmem + (uint32_t)(NACC * acc * a.npmax);
-        const uint32_t dc = d + (uint32_t)(NMAIN * a.npmax);
-        const uint32_t tab_hi = smem_u32(tab);
-        const uint32_t tab_lo = tab_hi + (uint32_t)(KC * npad * 128);
+        // [main_me | corr_me]: one MMA of width 2 npad gives X_hi A_hi and
+        // X_hi A_lo side by side, a second of width npad adds X_lo A_hi
+        const uint32_t dm = tmem + (uint32_t)acc * bufcols + (uint32_t)(me * 2 * npad);
+        const uint32_t dc = dm + (uint32_t)npad;
         bool ok = true;
         for (int kc = 0; kc < KC; ++kc, ++c) {
           const int s = c % STAGES;
           if (!mbar_wait(split + s, (c / STAGES) & 1, abort_flag)) { ok = false; break; }
           tc_after();
-          const uint32_t xh = smem_u32(xs + s * 2 * kChunkBytes);
-          const uint32_t xl = xh + kChunkBytes;
-          const uint32_t th = tab_hi + (uint32_t)(kc * npad * 128);
-          const uint32_t tlo = tab_lo + (uint32_t)(kc * npad * 128);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t koff = (uint32_t)(kk * 32);
-            const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
-            const uint32_t dm = d + (uint32_t)((kk % NMAIN) * a.npmax);
-            const uint32_t first_m = (kc > 0 || kk >= NMAIN) ? 1u : 0u;
-            mma_tf32(dm, sw128_desc(xh + koff), sw128_desc(th + koff), idesc, first_m);
-            mma_tf32(dc, sw128_desc(xh + koff), sw128_desc(tlo + koff), idesc, first);
-            mma_tf32(dc, sw128_desc(xl + koff), sw128_desc(th + koff), idesc, 1u);
-          }
+          const uint64_t xh = xdesc0 + (uint64_t)((s * 2 * kChunkBytes) >> 4) + 2 * me;
+          const uint64_t xl = xh + (uint64_t)(kChunkBytes >> 4);
+          const uint64_t tb = tdesc0 + (uint64_t)((kc * 2 * npad * 128) >> 4) + 2 * me;
+          const uint32_t first = kc > 0 ? 1u : 0u;
+          mma_tf32(dm, xh, tb, idesc2, first);
+          mma_tf32(dc, xl, tb, idesc1, 1u);
+          mma_tf32(dm, xh + 4, tb + 4, idesc2, 1u);
+          mma_tf32(dc, xl + 4, tb + 4, idesc1, 1u);
           mma_commit(empty + s);
         }
         if (!ok) break;
@@ -279,10 +284,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const int acc = tcount & 1;
       if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
       tc_after();
-      const int npad = s_npad[tl.x];
-      const uint32_t taddr = tmem + (uint32_t)(NACC * acc * a.npmax) + ((uint32_t)(quarter * 32) << 16);
-      const uint32_t tcorr = taddr + (uint32_t)(NMAIN * a.npmax);
-      const uint32_t tmain1 = taddr + (uint32_t)a.npmax;  // second main (NMAIN = 2)
+      const int npad = s_npad[tl.x] & 0xff;
+      const uint32_t taddr = tmem + (uint32_t)acc * bufcols + ((uint32_t)(quarter * 32) << 16);
+      const uint32_t np = (uint32_t)npad;
       const int grow = tl.y + r_in;
       if (PROB == TC_LEG_F) {
         const int g = tl.x;
@@ -296,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int64_t rbase = a.w2_off + (int64_t)cc * B + i;
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
-          if (NMAIN == 2) tmem_ld16_sum3(taddr + (uint32_t)c0, tmain1 + (uint32_t)c0, tcorr + (uint32_t)c0, v);
-          else tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
+          const uint32_t tc = taddr + (uint32_t)c0;
+          tmem_ld16_sum4(tc, tc + 2 * np, tc + np, tc + 3 * np, v);
           if (valid) {
             // S_f[l][b][m+l][c][i] = 2B (NB l^2 + b(2l+1) + m + l) + c B + i, stepped in l += 2
             int l = am + p + 2 * c0;
@@ -311,21 +315,21 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           }
         }
       } else {
-        const int l = tl.x;
+        const int l = (s_npad[tl.x] >> 8) & 0xff, n0 = s_npad[tl.x] >> 16;
         const int per_b = (2 * l + 1) * 2;
         const bool valid = grow < NB * per_b;
         const int b = grow / per_b;
         const int rem = grow - b * per_b;
         const int mm = rem >> 1, cc = rem & 1;
-        const int ncol = B - l;
+        const int ncol = min(B - l - n0, kRadRows);
         const int64_t cbase = valid ? a.fn_coef[b] : 0;
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
-          if (NMAIN == 2) tmem_ld16_sum3(taddr + (uint32_t)c0, tmain1 + (uint32_t)c0, tcorr + (uint32_t)c0, v);
-          else tmem_ld16_sum(taddr + (uint32_t)c0, tcorr + (uint32_t)c0, v);
+          const uint32_t tc = taddr + (uint32_t)c0;
+          tmem_ld16_sum4(tc, tc + 2 * np, tc + np, tc + 3 * np, v);
           if (valid) {
             // omega(n + 1, l, m) - omega(n, l, m) = n^2
-            int n = l + 1 + c0;
+            int n = l + 1 + n0 + c0;
             int64_t off = cbase + omega_of(n, l, mm - l);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -394,12 +398,13 @@ uint32_t rna_tf32_bits(float x) {
 }
 
 // Append the swizzled hi/lo image of a table A[n][k] (n < N, k < K; zero
-// padded to npad rows and KC*32 columns).
+// padded to npad rows and KC*32 columns): per K chunk the npad hi rows, then
+// the npad lo rows.
 void append_image(std::vector<unsigned char>& img, int N, int K, int npad, int KC,
                   const std::vector<double>& A /* N x K */) {
   const size_t off = img.size();
-  const size_t plane = (size_t)KC * npad * 128;
-  img.resize(off + 2 * plane, 0);
+  const size_t plane = (size_t)npad * 128;
+  img.resize(off + 2 * (size_t)KC * plane, 0);
   for (int n = 0; n < N; ++n)
     for (int k = 0; k < K; ++k) {
       const double v = A[(size_t)n * K + k];
@@ -412,7 +417,7 @@ void append_image(std::vector<unsigned char>& img, int N, int K, int npad, int K
       memcpy(&lo, &lb, 4);
       const int kc = k / 32, kin = k % 32;
       const int chunk = kin / 4, w = kin % 4;
-      const size_t pos = (size_t)kc * npad * 128 + (size_t)n * 128 + (size_t)((chunk ^ (n & 7)) * 16) + w * 4;
+      const size_t pos = (size_t)kc * 2 * plane + (size_t)n * 128 + (size_t)((chunk ^ (n & 7)) * 16) + w * 4;
       memcpy(&img[off + pos], &hi, 4);
       memcpy(&img[off + plane + pos], &lo, 4);
     }
@@ -493,33 +498,42 @@ cudaError_t tc_prepare(Plan& P) {
     ts.leg.ngroups = 2 * (2 * B - 1);
     ts.leg.npmax = npmax;
     ts.leg.KC = KC;
-    // radial: groups l
+    // radial: groups (l, n0); degrees with more than kRadRows terms n' are cut
+    // into the rows n' < kRadRows and the rest
     Pending pr;
-    pr.off.assign(2 * B, 0);
-    pr.npad.assign(B, 16);
+    std::vector<int2> rgrp;  // (l, n0)
+    for (int l = 0; l < B; ++l)
+      for (int n0 = 0; n0 < B - l; n0 += kRadRows) rgrp.push_back(make_int2(l, n0));
+    const int ngr = (int)rgrp.size();
+    pr.off.assign(2 * ngr, 0);
+    pr.npad.assign(ngr, 16);
     int npmax_r = 16;
     for (int w = 0; w < 2; ++w)
-      for (int l = 0; l < B; ++l) {
-        const int N = B - l;
+      for (int g = 0; g < ngr; ++g) {
+        const int l = rgrp[g].x, n0 = rgrp[g].y;
+        const int N = std::min(B - l - n0, kRadRows);
         const int np = pad16(N);
         npmax_r = np > npmax_r ? np : npmax_r;
         std::vector<double> A((size_t)N * B);
         for (int q = 0; q < N; ++q)
           for (int i = 0; i < B; ++i) {
-            const double v = H.T[((size_t)l * B + (l + q)) * B + i];
+            const double v = H.T[((size_t)l * B + (l + n0 + q)) * B + i];
             A[(size_t)q * B + i] = w == 0 ? H.what[i] * v : v;
           }
         img.resize((img.size() + 1023) / 1024 * 1024);
-        pr.off[w * B + l] = (int64_t)img.size();
-        pr.npad[l] = np;
+        pr.off[w * ngr + g] = (int64_t)img.size();
+        pr.npad[g] = np | (l << 8) | (n0 << 16);
         append_image(img, N, B, np, KC, A);
       }
-    for (int l = 0; l < B; ++l)
+    for (int g = 0; g < ngr; ++g) {
+      const int l = rgrp[g].x, n0 = rgrp[g].y;
+      const int N = std::min(B - l - n0, kRadRows);
       for (int r0 = 0; r0 < NB * (2 * l + 1) * 2; r0 += 128) {
-        pr.tiles.push_back(make_int2(l, r0));
-        pr.cost.push_back(KC * 16384.0 + 512.0 * (B - l) + (r0 == 0 ? 256.0 * KC * pad16(B - l) : 0.0));
+        pr.tiles.push_back(make_int2(g, r0));
+        pr.cost.push_back(KC * 16384.0 + 512.0 * N + (r0 == 0 ? 256.0 * KC * pad16(N) : 0.0));
       }
-    ts.rad.ngroups = B;
+    }
+    ts.rad.ngroups = ngr;
     ts.rad.npmax = npmax_r;
     ts.rad.KC = KC;
     // tensor maps over the segment's workspaces

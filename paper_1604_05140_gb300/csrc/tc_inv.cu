@@ -126,11 +126,11 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
       mbar_init(empty + s, 1);
     }
     for (int k = 0; k < 2; ++k) {
-      mbar_init(accf + k, 1);
+      mbar_init(accf + k, 2);  // both MMA issuers
       mbar_init(acce + k, kEpiThreads);
     }
     mbar_init(tabf, 1);
-    mbar_init(tabe, 1);
+    mbar_init(tabe, 2);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -177,14 +177,20 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
         if (!ok) break;
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == kMma2Warp) {
+    // MMA issuer `me` takes the chunks of parity p = me (P or Q accumulators)
     if (lane == 0) {
+      const int p = warp == 1 ? 0 : 1;
       int cur = -1, ngrp = 0;
       uint32_t c = 0, tcount = 0;
+      // the table image stacks nh hi rows over nh lo rows per K chunk: one
+      // MMA of width 2 nh gives [X_hi T_hi | X_hi T_lo], a second of width nh
+      // adds X_lo T_hi to the correction
+      const uint32_t idesc2 = idesc_tf32(2 * nh), idesc1 = idesc_tf32(nh);
+      const uint64_t xdesc0 = sw128_desc(smem_u32(xs));
+      const uint64_t tdesc0 = sw128_desc(smem_u32(tab));
       for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
         const int2 tl = s_tiles[t];
-        const int jh = tl.y & 1;
-        const uint32_t idesc = idesc_tf32(jh ? npad - 64 : nh);
         const int am = abs_m(tl.x);
         const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
         if (table_key(tl) != cur) {
@@ -196,31 +202,27 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
         if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
         tc_after();
         bool ok = true;
-        for (int p = 0; p < 2 && ok; ++p) {
-          const int kcn = p ? kcq : kcp;
-          // accumulators of this buffer: [P main][P corr][Q main][Q corr], nh columns each
-          const uint32_t d = tmem + (uint32_t)((4 * acc + 2 * p) * nh);
-          const uint32_t dc = d + (uint32_t)nh;
-          const uint32_t th0 = smem_u32(tab) + (uint32_t)((p ? 2 * kcp : 0) * chunk_tab);
-          const uint32_t tl0 = th0 + (uint32_t)(kcn * chunk_tab);
-          for (int kc = 0; kc < kcn; ++kc, ++c) {
-            const int s = c % kStagesLegI;
-            if (!mbar_wait(split + s, (c / kStagesLegI) & 1, abort_flag)) { ok = false; break; }
-            tc_after();
-            const uint32_t xh = smem_u32(xs + s * 2 * kChunk);
-            const uint32_t xl = xh + kChunk;
-            const uint32_t th = th0 + (uint32_t)(kc * chunk_tab);
-            const uint32_t tlo = tl0 + (uint32_t)(kc * chunk_tab);
+        // accumulators of this buffer: [P main][P corr][Q main][Q corr], nh columns each
+        const uint32_t d = tmem + (uint32_t)((4 * acc + 2 * p) * nh);
+        const uint64_t tp = tdesc0 + (uint64_t)(((p ? kcp : 0) * 2 * chunk_tab) >> 4);
+        // every chunk of the tile is waited for, so that the ring's phases are
+        // followed in order; only the chunks of parity p are issued here
+        for (int ch = 0; ch < kcp + kcq; ++ch, ++c) {
+          const int s = c % kStagesLegI;
+          if (!mbar_wait(split + s, (c / kStagesLegI) & 1, abort_flag)) { ok = false; break; }
+          if ((ch >= kcp) != (p == 1)) continue;
+          const int kc = p ? ch - kcp : ch;
+          tc_after();
+          const uint64_t xh = xdesc0 + (uint64_t)((s * 2 * kChunk) >> 4);
+          const uint64_t xl = xh + (uint64_t)(kChunk >> 4);
+          const uint64_t th = tp + (uint64_t)((kc * 2 * chunk_tab) >> 4);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t ko = (uint32_t)(kk * 32);
-              const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
-              mma_tf32(d, sw128_desc(xh + ko), sw128_desc(th + ko), idesc, first);
-              mma_tf32(dc, sw128_desc(xh + ko), sw128_desc(tlo + ko), idesc, first);
-              mma_tf32(dc, sw128_desc(xl + ko), sw128_desc(th + ko), idesc, 1u);
-            }
-            mma_commit(empty + s);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
+            mma_tf32(d, xh + 2 * kk, th + 2 * kk, idesc2, first);
+            mma_tf32(d + (uint32_t)nh, xl + 2 * kk, th + 2 * kk, idesc1, 1u);
           }
+          mma_commit(empty + s);
         }
         if (!ok) break;
         mma_commit(accf + acc);
@@ -317,10 +319,11 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
 // inverse radial
 // ===========================================================================
 // Tiles of degrees with more than 64 terms (B - l > 64) are 64 columns wide
-// and keep two main accumulators (even and odd K steps) besides the
-// correction, so that no accumulator takes more than 8 truncating additions
-// of hi*hi products; the other tiles are 128 columns wide with one main
-// accumulator.  Either way a tile uses 256 TMEM columns, two tiles in flight.
+// and keep two main/correction pairs (even and odd K steps, one per MMA
+// issuer), so that no accumulator takes more than 8 truncating additions of
+// hi*hi products; the other tiles are 128 columns wide, one pair per half of
+// 64 columns and issuer.  Either way a tile uses 256 TMEM columns, two tiles
+// in flight.
 struct RadIArgs {
   const int2* tiles;          // (l, col0 | narrow), grouped by l
   const int* cta_first;       // tile slice of each CTA (gridDim.x + 1 offsets)
@@ -389,10 +392,10 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     for (int s = 0; s < kStagesRadI; ++s) {
       mbar_init(tfull + s, 1);
       mbar_init(split + s, kSplitThreads);
-      mbar_init(empty + s, 1);
+      mbar_init(empty + s, 2);  // both MMA issuers
     }
     for (int k = 0; k < 2; ++k) {
-      mbar_init(accf + k, 1);
+      mbar_init(accf + k, 2);
       mbar_init(acce + k, kEpiThreads);
     }
     *abort_flag = 0;
@@ -423,21 +426,27 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
         if (!ok) break;
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == kMma2Warp) {
+    // MMA issuer `me`: narrow tiles, the K steps of parity me into
+    // [main_me | corr_me]; wide tiles, the columns 64 me .. 64 me + 63
     if (lane == 0) {
+      const int me = warp == 1 ? 0 : 1;
       uint32_t c = 0, tcount = 0;
+      const uint64_t sdesc0 = sw128_desc(smem_u32(st));
+      // B operand of each half: 64 hi rows over 64 lo rows.  One MMA of width
+      // 128 gives [T_hi X_hi | T_hi X_lo], a second of width 64 adds T_lo X_hi.
+      const uint32_t idesc2 = idesc_tf32(128), idesc1 = idesc_tf32(64);
       for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
         const int2 tl = s_tiles[t];
         const int l = tl.x;
         const bool nar = tl.y & 1;
-        const uint32_t idesc = idesc_tf32(nar ? 64 : 128);
         const int kcn = (B - l + 31) / 32;
         const int acc = tcount & 1;
         if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
         tc_after();
-        // buffer: wide [main 128][corr 128], narrow [main 64][main 64][corr 64]
-        const uint32_t d = tmem + (uint32_t)(acc * 256);
-        const uint32_t dc = d + 128u;
+        // buffer: [main0 | corr0 | main1 | corr1], 64 columns each
+        const uint32_t dm = tmem + (uint32_t)(acc * 256 + me * 128);
+        const uint32_t dc = dm + 64u;
         bool ok = true;
         for (int kc = 0; kc < kcn; ++kc, ++c) {
           const int s = c % kStagesRadI;
@@ -447,19 +456,22 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
             break;
           }
           tc_after();
-          const uint32_t ah = smem_u32(st + s * 4 * kChunk);
-          const uint32_t al = ah + kChunk;
-          const uint32_t bh = al + kChunk;
-          const uint32_t bl = bh + kChunk;
+          const uint64_t ah = sdesc0 + (uint64_t)((s * 4 * kChunk) >> 4);
+          const uint64_t al = ah + (uint64_t)(kChunk >> 4);
+          const uint64_t bh = al + (uint64_t)(kChunk >> 4) + (nar ? 0u : (uint64_t)(me * (128 * 128 >> 4)));
+          if (nar) {
+            const uint32_t first = kc > 0 ? 1u : 0u;
+            mma_tf32(dm, ah + 2 * me, bh + 2 * me, idesc2, first);
+            mma_tf32(dc, al + 2 * me, bh + 2 * me, idesc1, 1u);
+            mma_tf32(dm, ah + 2 * me + 4, bh + 2 * me + 4, idesc2, 1u);
+            mma_tf32(dc, al + 2 * me + 4, bh + 2 * me + 4, idesc1, 1u);
+          } else {
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t ko = (uint32_t)(kk * 32);
-            const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
-            const uint32_t dm = nar ? d + (uint32_t)((kk & 1) * 64) : d;
-            const uint32_t first_m = nar ? ((kc > 0 || kk >= 2) ? 1u : 0u) : first;
-            mma_tf32(dm, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, first_m);
-            mma_tf32(dc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, first);
-            mma_tf32(dc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
+              mma_tf32(dm, ah + 2 * kk, bh + 2 * kk, idesc2, first);
+              mma_tf32(dc, al + 2 * kk, bh + 2 * kk, idesc1, 1u);
+            }
           }
           mma_commit(empty + s);
         }
@@ -486,9 +498,14 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       if (tn < nt) rad_gather(a, s_tiles[tn], kcn_next, tid, vn);
       const int s = c % kStagesRadI;
       if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) break;
+      // B operand: per half of 64 columns, 64 hi rows then 64 lo rows
       unsigned char* sb = st + s * 4 * kChunk + 2 * kChunk;
-      if (nar) split_store<2>(sb, sb + kChunk, tid & 63, v, 2 * (tid >> 6));
-      else split_store<4>(sb, sb + kChunk, tid & 127, v, 4 * (tid >> 7));
+      if (nar) {
+        split_store<2>(sb, sb + 64 * 128, tid & 63, v, 2 * (tid >> 6));
+      } else {
+        unsigned char* hb = sb + ((tid >> 6) & 1) * (128 * 128);
+        split_store<4>(hb, hb + 64 * 128, tid & 63, v, 4 * (tid >> 7));
+      }
       fence_proxy_async();
       mbar_arrive(split + s);
 #pragma unroll
@@ -528,8 +545,13 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
           }
         }
         float v[16];
-        if (nar) tmem_ld16_sum3(dq + (uint32_t)c0, dq + (uint32_t)(64 + c0), dq + (uint32_t)(128 + c0), v);
-        else tmem_ld16_sum(dq + (uint32_t)c0, dq + (uint32_t)(128 + c0), v);
+        if (nar) {
+          const uint32_t tc = dq + (uint32_t)c0;
+          tmem_ld16_sum4(tc, tc + 128u, tc + 64u, tc + 192u, v);
+        } else {  // columns 64h + c: [main_h | corr_h] at 128 h
+          const uint32_t tc = dq + (uint32_t)((c0 >> 6) * 128 + (c0 & 63));
+          tmem_ld16_sum(tc, tc + 64u, v);
+        }
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int64_t ok = __shfl_sync(0xffffffffu, o, k);
@@ -562,13 +584,13 @@ uint32_t rna_bits(float x) {
   return (u + 0x1000u) & 0xFFFFE000u;
 }
 
-// Append a hi and a lo plane of KC chunks, each `rows` x 32 floats, 128-byte
-// swizzled: value(row, k) for k < K.
+// Append KC chunks of `rows` x 32 floats, 128-byte swizzled, each as its hi
+// rows followed by its lo rows: value(row, k) for k < K.
 template <typename F>
 void append_planes(std::vector<unsigned char>& img, int rows, int K, int KC, F value) {
   const size_t off = img.size();
-  const size_t plane = (size_t)KC * rows * 128;
-  img.resize(off + 2 * plane, 0);
+  const size_t plane = (size_t)rows * 128;
+  img.resize(off + 2 * (size_t)KC * plane, 0);
   for (int r = 0; r < rows; ++r)
     for (int k = 0; k < K; ++k) {
       const double v = value(r, k);
@@ -579,7 +601,7 @@ void append_planes(std::vector<unsigned char>& img, int rows, int K, int KC, F v
       memcpy(&hi, &hb, 4);
       const uint32_t lb = rna_bits((float)(v - (double)hi));
       const int kc = k / 32, kin = k % 32;
-      const size_t pos = (size_t)kc * rows * 128 + (size_t)r * 128 + (size_t)((((kin >> 2) ^ (r & 7)) << 4) + (kin & 3) * 4);
+      const size_t pos = (size_t)kc * 2 * plane + (size_t)r * 128 + (size_t)((((kin >> 2) ^ (r & 7)) << 4) + (kin & 3) * 4);
       memcpy(&img[off + pos], &hb, 4);
       memcpy(&img[off + plane + pos], &lb, 4);
     }

@@ -11,16 +11,20 @@ namespace tcx {
 constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every mbarrier wait
 
 // Warp roles of the tensor-core kernels: warp 0 producer, warp 1 TMEM owner
-// and MMA issuer, then kSplitWarps operand-split warps and kEpiWarps epilogue
-// warps.  Epilogue warp w reads TMEM lanes 32*(w%4) .. +31; the two warps of
-// one lane quarter take alternate 16-column blocks.
+// and first MMA issuer, then kSplitWarps operand-split warps, kEpiWarps
+// epilogue warps and the second MMA issuer.  Epilogue warp w reads TMEM lanes
+// 32*(w%4) .. +31; the two warps of one lane quarter take alternate 16-column
+// blocks.  Each issuer owns its own accumulators (one thread issues an MMA
+// only every ~60 cycles, less than the tensor core takes for the small tiles
+// here, so two threads on two schedulers keep it busier).
 constexpr int kSplitWarps = 8;
 constexpr int kEpiWarps = 8;
 constexpr int kFirstSplitWarp = 2;
 constexpr int kFirstEpiWarp = kFirstSplitWarp + kSplitWarps;
+constexpr int kMma2Warp = kFirstEpiWarp + kEpiWarps;
 constexpr int kSplitThreads = 32 * kSplitWarps;
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kRoleThreads = 32 * (kFirstEpiWarp + kEpiWarps);
+constexpr int kRoleThreads = 32 * (kMma2Warp + 1);
 
 static __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -169,13 +173,14 @@ static __device__ __forceinline__ void tmem_ld16_sum(uint32_t tmain, uint32_t tc
   for (int k = 0; k < 16; ++k) v[k] += c[k];
 }
 
-// two main accumulators and a correction: (main0 + main1) + corr
-static __device__ __forceinline__ void tmem_ld16_sum3(uint32_t tm0, uint32_t tm1, uint32_t tcorr, float* v) {
-  float w[16], c[16];
+// two main and two correction accumulators: (main0 + main1) + (corr0 + corr1)
+static __device__ __forceinline__ void tmem_ld16_sum4(uint32_t tm0, uint32_t tm1, uint32_t tc0, uint32_t tc1,
+                                                      float* v) {
+  float w[16], c[16], d[16];
   tmem_ld16x2(tm0, tm1, v, w);
-  tmem_ld16(tcorr, c);
+  tmem_ld16x2(tc0, tc1, c, d);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = (v[k] + w[k]) + c[k];
+  for (int k = 0; k < 16; ++k) v[k] = (v[k] + w[k]) + (c[k] + d[k]);
 }
 
 static __device__ __forceinline__ float tf32_rna(float x) {
@@ -184,7 +189,9 @@ static __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-// K-major, 128-byte swizzled operand: 8-row groups 1024 B apart.
+// K-major, 128-byte swizzled operand: 8-row groups 1024 B apart.  The start
+// address is the low field (address / 16), so a descriptor moves by `bytes`
+// (a multiple of 16, staying inside shared memory) with desc + bytes / 16.
 static __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFF) >> 4);       // start address
