@@ -15,7 +15,7 @@
 //   warp 0      TMA producer: 128-row x 32-float X chunks (SWIZZLE_128B) into a
 //               staged ring; the group's pre-swizzled hi/lo table by bulk copy
 //   warp 1      TMEM owner and MMA issuer of the even K steps (one thread)
-//   warps 2-9   split: X -> hi (in place, cvt.rna.tf32) and lo = X - hi
+//   warps 2-9   split: X -> hi (in place, TF32 round to nearest) and lo = X - hi
 //   warps 10-17 epilogue: tcgen05.ld of the double-buffered accumulators, sign,
 //               scatter to the next stage's layout
 //   warp 18     MMA issuer of the odd K steps (one thread)
@@ -303,14 +303,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const uint32_t tc = taddr + (uint32_t)c0;
           tmem_ld16_sum4(tc, tc + 2 * np, tc + np, tc + 3 * np, v);
           if (valid) {
-            // S_f[l][b][m+l][c][i] = 2B (NB l^2 + b(2l+1) + m + l) + c B + i, stepped in l += 2
-            int l = am + p + 2 * c0;
-            int64_t t = (int64_t)NB * l * l + (int64_t)(2 * b + 1) * l + b + m;
+            // S_f[l][b][m+l][c][i] = 2B (NB l^2 + b(2l+1) + m + l) + c B + i, stepped in
+            // l += 2 by first and second differences
+            const int l = am + p + 2 * c0;
+            const int64_t t = (int64_t)NB * l * l + (int64_t)(2 * b + 1) * l + b + m;
+            float* yp = Y + rbase + 2 * (int64_t)B * t;
+            int64_t d = 2 * (int64_t)B * ((int64_t)NB * (4 * l + 4) + 2 * (2 * b + 1));
+            const int64_t dd = 16 * (int64_t)B * NB;
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-              if (c0 + k < ncol) Y[rbase + 2 * (int64_t)B * t] = sgn * v[k];
-              t += (int64_t)NB * (4 * l + 4) + 2 * (2 * b + 1);
-              l += 2;
+              if (c0 + k < ncol) *yp = sgn * v[k];
+              yp += d;
+              d += dd;
             }
           }
         }

@@ -183,10 +183,12 @@ static __device__ __forceinline__ void tmem_ld16_sum4(uint32_t tm0, uint32_t tm1
   for (int k = 0; k < 16; ++k) v[k] = (v[k] + w[k]) + (c[k] + d[k]);
 }
 
+// Round to TF32 (10 fraction bits), to nearest with ties away from zero: add
+// half a unit of the 11th significant bit to the magnitude bits and clear the
+// 13 bits below it (a carry into the exponent gives the correctly rounded
+// power of two).  Finite inputs only.
 static __device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // K-major, 128-byte swizzled operand: 8-row groups 1024 B apart.  The start
