@@ -178,6 +178,31 @@ sgl_status  sgl_set_profiling(sgl_plan_t plan, int enable);
 sgl_status  sgl_stage_times(sgl_plan_t plan, double* ms, int64_t* launches);
 const char* sgl_stage_name(int stage);
 
+/*
+ * sgl_autotune - choose the plan's launch configuration by timing it on this
+ * GPU (an implementation aid; the paper has no counterpart).  Tuned: the ring
+ * pairs per CTA of the forward and of the inverse phi-FFT, and for
+ * SGL_TF32X3 plans the tile width policy of the inverse radial stage.  Each
+ * candidate is timed with CUDA events over whole forward or inverse calls
+ * (one warm-up, best of three) on `stream`; the fastest is kept.  The
+ * transforms computed are the same for every candidate (the FFT choices give
+ * identical results; the radial tile policy changes only the summation order
+ * of the TF32x3 accumulation).
+ *   samples, coeffs  device buffers of sgl_sample_count / sgl_coeff_count
+ *                    complex elements, used as scratch: both are overwritten.
+ *   cache_path       NULL, or a text file of earlier results: a line for this
+ *                    GPU model, precision and bandlimit list is applied without
+ *                    timing; otherwise the result is appended to the file.
+ * Synchronizes `stream`; replaces device schedules, so call it before capturing
+ * the plan's calls in a CUDA graph.  Host buffers give SGL_ERR_ARG.
+ */
+sgl_status sgl_autotune(sgl_plan_t plan, void* samples, void* coeffs, const char* cache_path,
+                        sgl_stream_t stream);
+
+/* The plan's launch configuration as text, e.g. "fft_fwd_jp=8 fft_inv_jp=16
+ * rad_inv_narrow=65 source=timed"; valid until the next call on the plan. */
+const char* sgl_tuning(sgl_plan_t plan);
+
 /* Message for the last failure on `plan` (or of plan creation when NULL).
  * The string stays valid until the next call on the same plan. */
 const char* sgl_last_error(sgl_plan_t plan);

@@ -12,7 +12,6 @@
 
 namespace sgl {
 size_t fft_smem_for(int prec, int n1, int n2, int B);
-int fft_pairs_per_cta(int prec, int B);
 void gemm_tile_dims(int& tm, int& tn, int& tk);
 cudaError_t tc_prepare(Plan& P);   // tensor-core tables and schedules (tc_gemm.cu)
 void tc_release(Plan& P);
@@ -122,6 +121,48 @@ void sgl::pack_tables(const Plan& P, std::vector<real>& tab) {
 
 template void sgl::pack_tables<double>(const Plan& P, std::vector<double>& tab);
 template void sgl::pack_tables<float>(const Plan& P, std::vector<float>& tab);
+
+// FFT CTA lists of both directions (segment order) for the plan's current
+// ring pairs per CTA; replaces the previous lists.
+static cudaError_t build_fft_lists(Plan& P) {
+  std::vector<int4> ff;
+  for (size_t s = 0; s < P.segs.size(); ++s) {
+    const SegDesc& sg = P.segs[s];
+    const int JP = fft_jp(P, sg.B, false);
+    for (int sh = 0; sh < sg.NB * sg.B; ++sh)
+      for (int j0 = 0; j0 < sg.B; j0 += JP) ff.push_back(make_int4((int)s, sh, j0, 0));
+  }
+  if (P.d_fft_fwd) {
+    cudaFree(P.d_fft_fwd);
+    P.d_fft_fwd = nullptr;
+    P.bytes -= (int64_t)P.n_fft_fwd * sizeof(int4);
+  }
+  P.n_fft_fwd = (int)ff.size();
+  cudaError_t e = dev_upload(P, &P.d_fft_fwd, ff);
+  if (e != cudaSuccess) return e;
+  ff.clear();
+  for (size_t s = 0; s < P.segs.size(); ++s) {
+    const SegDesc& sg = P.segs[s];
+    const int JP = fft_jp(P, sg.B, true);
+    if (P.prec == SGL_TF32X3) {
+      // the tensor-core Legendre synthesis stores spectra [m][b][c][j][i]: each
+      // inverse-FFT CTA takes JP consecutive shells of one ring pair (layout 1)
+      for (int b = 0; b < sg.NB; ++b)
+        for (int i0 = 0; i0 < sg.B; i0 += JP)
+          for (int jp = 0; jp < sg.B; ++jp) ff.push_back(make_int4((int)s, b * sg.B + i0, jp, 1));
+    } else {
+      for (int sh = 0; sh < sg.NB * sg.B; ++sh)
+        for (int j0 = 0; j0 < sg.B; j0 += JP) ff.push_back(make_int4((int)s, sh, j0, 0));
+    }
+  }
+  if (P.d_fft_inv) {
+    cudaFree(P.d_fft_inv);
+    P.d_fft_inv = nullptr;
+    P.bytes -= (int64_t)P.n_fft_inv * sizeof(int4);
+  }
+  P.n_fft_inv = (int)ff.size();
+  return dev_upload(P, &P.d_fft_inv, ff);
+}
 
 static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) {
   cudaGetDevice(&P->device);
@@ -253,30 +294,7 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
     e = dev_upload(*P, &x.s->d_tiles, *x.v);
     if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
   }
-  // FFT CTA lists (segment order)
-  std::vector<int4> ff;
-  for (size_t s = 0; s < P->segs.size(); ++s) {
-    const SegDesc& sg = P->segs[s];
-    const int JP = fft_pairs_per_cta(P->prec, sg.B);
-    for (int sh = 0; sh < sg.NB * sg.B; ++sh)
-      for (int j0 = 0; j0 < sg.B; j0 += JP) ff.push_back(make_int4((int)s, sh, j0, 0));
-  }
-  P->n_fft_fwd = P->n_fft_inv = (int)ff.size();
-  e = dev_upload(*P, &P->d_fft_fwd, ff);
-  if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
-  if (P->prec == SGL_TF32X3) {
-    // the tensor-core Legendre synthesis stores spectra [m][b][c][j][i]: each
-    // inverse-FFT CTA takes JP consecutive shells of one ring pair (layout 1)
-    ff.clear();
-    for (size_t s = 0; s < P->segs.size(); ++s) {
-      const SegDesc& sg = P->segs[s];
-      const int JP = fft_pairs_per_cta(P->prec, sg.B);
-      for (int b = 0; b < sg.NB; ++b)
-        for (int i0 = 0; i0 < sg.B; i0 += JP)
-          for (int jp = 0; jp < sg.B; ++jp) ff.push_back(make_int4((int)s, b * sg.B + i0, jp, 1));
-    }
-  }
-  e = dev_upload(*P, &P->d_fft_inv, ff);
+  e = build_fft_lists(*P);
   if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
   for (const SegDesc& sg : P->segs) {
     size_t smem = fft_smem_for(P->prec, sg.n1, sg.n2, sg.B);
@@ -358,6 +376,129 @@ static sgl_status execute(Plan* P, bool is_fwd, bool weights, const void* in, vo
 done:
   if (cur != P->device) cudaSetDevice(cur);
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// autotuning (sgl_autotune)
+// ---------------------------------------------------------------------------
+static std::string tuning_text(const Plan& P, const char* source) {
+  char buf[192];
+  snprintf(buf, sizeof buf, "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d source=%s", fft_jp(P, P.maxB, false),
+           fft_jp(P, P.maxB, true), P.radi_narrow, source);
+  return buf;
+}
+
+// cache key: GPU model, precision, segments (bandlimit x functions)
+static std::string tuning_key(const Plan& P) {
+  cudaDeviceProp prop;
+  std::string name = "unknown";
+  if (cudaGetDeviceProperties(&prop, P.device) == cudaSuccess) name = prop.name;
+  std::string k = name + " prec=" + std::to_string(P.prec) + " segs=";
+  for (const SegDesc& sg : P.segs) k += std::to_string(sg.B) + "x" + std::to_string(sg.NB) + ",";
+  return k;
+}
+
+// Best of three timed calls after one warm-up (milliseconds), or a negative
+// value if a launch failed.
+static double time_calls(Plan& P, bool fwd, void* samples, void* coeffs, cudaStream_t s) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1.0;
+  double best = 1e30;
+  for (int rep = 0; rep < 4 && best >= 0.0; ++rep) {
+    cudaEventRecord(a, s);
+    const cudaError_t e = fwd ? run_forward(P, samples, coeffs, s, true) : run_inverse(P, coeffs, samples, s, true);
+    cudaEventRecord(b, s);
+    if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+      best = -1.0;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cache_path, cudaStream_t s) {
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(P, e, "stream synchronize");
+  const std::string key = tuning_key(*P);
+  bool cached = false;
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "r");
+    if (f) {
+      char line[1024];
+      while (fgets(line, sizeof line, f)) {
+        const std::string ln(line);
+        if (ln.compare(0, key.size() + 3, key + " | ") != 0) continue;
+        int jf = 0, ji = 0, rn = 0;
+        if (sscanf(ln.c_str() + key.size() + 3, "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d", &jf, &ji, &rn) == 3 &&
+            jf >= 1 && jf <= 16 && ji >= 1 && ji <= 16 && rn >= 1) {
+          P->jp_fwd = jf;
+          P->jp_inv = ji;
+          P->radi_narrow = rn;
+          cached = true;
+        }
+      }
+      fclose(f);
+    }
+  }
+  if (!cached) {
+    const size_t cb = complex_bytes(*P);
+    cudaMemsetAsync(samples, 0, (size_t)P->n_samples * cb, s);
+    cudaMemsetAsync(coeffs, 0, (size_t)P->n_coeffs * cb, s);
+    std::vector<int> jps = {4, 8};
+    if (P->prec != SGL_FP64) jps.push_back(16);
+    for (int dir = 0; dir < 2; ++dir) {
+      int& knob = dir == 0 ? P->jp_fwd : P->jp_inv;
+      int best = 0;
+      double tbest = 1e30;
+      for (int jp : jps) {
+        knob = jp;
+        e = build_fft_lists(*P);
+        if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+        const double t = time_calls(*P, dir == 0, samples, coeffs, s);
+        if (t < 0.0) return cuda_fail(P, cudaGetLastError(), "autotune launch");
+        if (t < tbest) {
+          tbest = t;
+          best = jp;
+        }
+      }
+      knob = best;
+    }
+    e = build_fft_lists(*P);
+    if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+    if (P->prec == SGL_TF32X3) {
+      int best = 65;
+      double tbest = 1e30;
+      for (int rn : {65, 1}) {
+        P->radi_narrow = rn;
+        e = tc_radi_retile(*P);
+        if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+        const double t = time_calls(*P, false, samples, coeffs, s);
+        if (t < 0.0) return cuda_fail(P, cudaGetLastError(), "autotune launch");
+        if (t < tbest) {
+          tbest = t;
+          best = rn;
+        }
+      }
+      P->radi_narrow = best;
+    }
+  }
+  e = build_fft_lists(*P);
+  if (e == cudaSuccess && P->prec == SGL_TF32X3) e = tc_radi_retile(*P);
+  if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+  P->tuning = tuning_text(*P, cached ? "cache" : "timed");
+  if (!cached && cache_path) {
+    FILE* f = fopen(cache_path, "a");
+    if (!f) return fail(P, SGL_ERR_ARG, std::string("cannot append to tuning cache ") + cache_path);
+    fprintf(f, "%s | fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d\n", key.c_str(), P->jp_fwd, P->jp_inv,
+            P->radi_narrow);
+    fclose(f);
+  }
+  return SGL_OK;
 }
 
 extern "C" {
@@ -520,6 +661,28 @@ const char* sgl_stage_name(int stage) {
                                               "radial_inverse", "legendre_inverse", "fft_inverse"};
   if (stage < 0 || stage >= SGL_NUM_STAGES) return "";
   return names[stage];
+}
+
+sgl_status sgl_autotune(sgl_plan_t plan, void* samples, void* coeffs, const char* cache_path,
+                        sgl_stream_t stream) {
+  Plan* P = (Plan*)plan;
+  if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
+  if (!samples || !coeffs || !is_device_ptr(samples) || !is_device_ptr(coeffs))
+    return fail(P, SGL_ERR_ARG, "sgl_autotune needs device buffers for samples and coefficients");
+  if (P->latched != SGL_OK) return (sgl_status)P->latched;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != P->device) cudaSetDevice(P->device);
+  const sgl_status st = autotune(P, samples, coeffs, cache_path, (cudaStream_t)stream);
+  if (cur != P->device) cudaSetDevice(cur);
+  return st;
+}
+
+const char* sgl_tuning(sgl_plan_t plan) {
+  Plan* P = (Plan*)plan;
+  if (!P) return "";
+  if (P->tuning.empty()) P->tuning = tuning_text(*P, "default");
+  return P->tuning.c_str();
 }
 
 const char* sgl_last_error(sgl_plan_t plan) {

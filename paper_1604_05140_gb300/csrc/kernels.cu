@@ -579,13 +579,12 @@ static void fft_slices(const Plan& P, std::vector<FftSlice>& out, bool inv) {
   int first = 0;
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
-    const int JP = fft_pairs_per_cta(P.prec, sg.B);
+    const int JP = fft_jp(P, sg.B, inv);
     const int per_shell = (sg.B + JP - 1) / JP;
     const int count = sg.NB * sg.B * per_shell;
     out.push_back({first, count, sg.n1, sg.n2, sg.B});
     first += count;
   }
-  (void)inv;
 }
 
 template <typename real>
@@ -602,7 +601,7 @@ static cudaError_t run_fft(Plan& P, bool inv, const void* in, void* out, int mod
     a.in = in;
     a.out = out;
     a.w1 = P.d_w1;
-    a.JP = fft_pairs_per_cta(P.prec, f.B);
+    a.JP = fft_jp(P, f.B, inv);
     a.mode = mode;
     {
       Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode};

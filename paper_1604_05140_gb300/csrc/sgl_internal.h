@@ -178,6 +178,14 @@ struct Plan {
   void* tc_state = nullptr;      // tensor-core forward stage state (tc_gemm.cu)
   void* tc_inv_state = nullptr;  // tensor-core inverse stage state (tc_inv.cu)
 
+  // launch configuration chosen by sgl_autotune: ring pairs per CTA of the
+  // forward and inverse phi-FFT (0: default), and the number of radial terms
+  // B - l from which the TF32x3 inverse radial stage cuts 64-column tiles
+  // with two K chains (smaller counts get 128-column tiles)
+  int jp_fwd = 0, jp_inv = 0;
+  int radi_narrow = 65;
+  std::string tuning;
+
   // stage timing (sgl_set_profiling): event pairs per stage, and a free pool
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[SGL_NUM_STAGES];
@@ -249,5 +257,17 @@ void pack_tables(const Plan& P, std::vector<real>& tab);
 // Stage launchers (kernels.cu)
 cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights);
 cudaError_t run_inverse(Plan& P, const void* coeffs, void* samples, cudaStream_t s, bool weights);
+
+// Default ring pairs per phi-FFT CTA (kernels.cu), and the plan's choice for
+// one direction (the tuned value where set), at most B.
+int fft_pairs_per_cta(int prec, int B);
+inline int fft_jp(const Plan& P, int B, bool inv) {
+  int jp = inv ? P.jp_inv : P.jp_fwd;
+  if (jp <= 0) jp = fft_pairs_per_cta(P.prec, B);
+  return jp < B ? jp : B;
+}
+
+// Rebuilds the TF32x3 inverse radial tiles for P.radi_narrow (tc_inv.cu).
+cudaError_t tc_radi_retile(Plan& P);
 
 }  // namespace sgl

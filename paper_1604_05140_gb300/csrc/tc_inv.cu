@@ -645,6 +645,63 @@ static cudaError_t upload(T** dst, const std::vector<T>& v, int64_t& bytes) {
   return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+// Inverse radial tiles of segment s: 64 columns with two K chains where
+// B - l >= P.radi_narrow, else 128 columns; the CTA slices and shared memory.
+static cudaError_t radi_tiles(const Plan& P, size_t s, TcInvSeg& ts, int nsm, int64_t& bytes) {
+  const int B = P.segs[s].B, NB = P.segs[s].NB;
+  std::vector<int2> rtiles;
+  std::vector<double> rc;
+  for (int l = 0; l < B; ++l) {
+    const int nar = B - l >= P.radi_narrow ? 1 : 0;
+    const int width = nar ? 64 : 128;
+    const int kcn = (B - l + 31) / 32;
+    for (int c0 = 0; c0 < NB * (2 * l + 1) * 2; c0 += width) {
+      rtiles.push_back(make_int2(l, c0 | nar));
+      // gathered coefficients, table chunks (from L2, half weight), S out
+      rc.push_back(kcn * (width * 128.0 + 16384.0) + 512.0 * width);
+    }
+  }
+  cudaError_t e = upload(&ts.rad_tiles, rtiles, bytes);
+  ts.rad_ntiles = (int)rtiles.size();
+  ts.rad_grid = std::min(ts.rad_ntiles, nsm);
+  int rmax = 0;
+  const std::vector<int> rf = balance_slices(rc, std::max(ts.rad_grid, 1), &rmax);
+  if (e == cudaSuccess) e = upload(&ts.rad_first, rf, bytes);
+  const size_t meta = (size_t)2 * (2 * B - 1) * 8 + (size_t)B * 12 + 8;
+  ts.rad_smem = 1024 + (size_t)kStagesRadI * 4 * kChunk + 64 * 8 + meta + (size_t)(rmax + 1) * 8;
+  if (e == cudaSuccess && ts.rad_smem > 227 * 1024) e = cudaErrorInvalidValue;
+  return e;
+}
+
+cudaError_t tc_radi_retile(Plan& P) {
+  TcInvState* st = (TcInvState*)P.tc_inv_state;
+  if (!st) return cudaSuccess;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int64_t bytes = 0;
+  for (size_t s = 0; s < st->segs.size(); ++s) {
+    TcInvSeg& ts = st->segs[s];
+    if (ts.rad_tiles) {
+      cudaFree(ts.rad_tiles);
+      P.bytes -= (int64_t)ts.rad_ntiles * sizeof(int2);
+    }
+    if (ts.rad_first) {
+      cudaFree(ts.rad_first);
+      P.bytes -= (int64_t)(ts.rad_grid > 0 ? ts.rad_grid + 1 : 2) * sizeof(int);
+    }
+    ts.rad_tiles = nullptr;
+    ts.rad_first = nullptr;
+    cudaError_t e = radi_tiles(P, s, ts, nsm, bytes);
+    if (e != cudaSuccess) {
+      P.bytes += bytes;
+      return e;
+    }
+  }
+  P.bytes += bytes;
+  return cudaSuccess;
+}
+
 cudaError_t tc_inv_prepare(Plan& P) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -653,8 +710,8 @@ cudaError_t tc_inv_prepare(Plan& P) {
   std::vector<unsigned char> img;
   std::vector<std::vector<int64_t>> am_offs, l_offs;
   std::vector<std::vector<int>> am_kcs;
-  std::vector<std::vector<int2>> lt, rt;
-  std::vector<std::vector<double>> lcost, rcost;  // estimated bytes moved per tile
+  std::vector<std::vector<int2>> lt;
+  std::vector<std::vector<double>> lcost;  // estimated bytes moved per tile
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
     const HostTables& H = P.tables[s];
@@ -714,19 +771,6 @@ cudaError_t tc_inv_prepare(Plan& P) {
           return H.T[((size_t)l * B + (l + np)) * B + i];
         });
     }
-    // tiles: 64 columns with two main accumulators where B - l > 64, else 128
-    std::vector<int2> rtiles;
-    std::vector<double> rc;
-    for (int l = 0; l < B; ++l) {
-      const int nar = B - l > 64 ? 1 : 0;
-      const int width = nar ? 64 : 128;
-      const int kcn = (B - l + 31) / 32;
-      for (int c0 = 0; c0 < NB * (2 * l + 1) * 2; c0 += width) {
-        rtiles.push_back(make_int2(l, c0 | nar));
-        // gathered coefficients, table chunks (from L2, half weight), S out
-        rc.push_back(kcn * (width * 128.0 + 16384.0) + 512.0 * width);
-      }
-    }
     // tensor map over S: [B^2 rows of l'][NB*2*B]
     float* w2 = (float*)P.d_w2 + sg.w2_off;
     if (!make_map_2d(&ts.smap, w2, (uint64_t)NB * 2 * B, (uint64_t)B * B, 128, 32, CU_TENSOR_MAP_SWIZZLE_NONE)) {
@@ -738,9 +782,7 @@ cudaError_t tc_inv_prepare(Plan& P) {
     am_kcs.push_back(akc);
     l_offs.push_back(loff);
     lt.push_back(ltiles);
-    rt.push_back(rtiles);
     lcost.push_back(lc);
-    rcost.push_back(rc);
   }
   int64_t bytes = 0;
   cudaError_t e = upload(&st->d_img, img, bytes);
@@ -751,26 +793,20 @@ cudaError_t tc_inv_prepare(Plan& P) {
     if (e == cudaSuccess) e = upload(&ts.am_kc, am_kcs[s], bytes);
     if (e == cudaSuccess) e = upload(&ts.l_off, l_offs[s], bytes);
     if (e == cudaSuccess) e = upload(&ts.leg_tiles, lt[s], bytes);
-    if (e == cudaSuccess) e = upload(&ts.rad_tiles, rt[s], bytes);
     ts.leg_ntiles = (int)lt[s].size();
-    ts.rad_ntiles = (int)rt[s].size();
     ts.leg_grid = std::min(ts.leg_ntiles, nsm);
-    ts.rad_grid = std::min(ts.rad_ntiles, nsm);
-    int lmax = 0, rmax = 0;
+    int lmax = 0;
     const std::vector<int> lf = balance_slices(lcost[s], std::max(ts.leg_grid, 1), &lmax);
-    const std::vector<int> rf = balance_slices(rcost[s], std::max(ts.rad_grid, 1), &rmax);
     if (e == cudaSuccess) e = upload(&ts.leg_first, lf, bytes);
-    if (e == cudaSuccess) e = upload(&ts.rad_first, rf, bytes);
     lmax += 1;
-    rmax += 1;
+    if (e == cudaSuccess) e = radi_tiles(P, s, ts, nsm, bytes);
     // tables, staging, operand ring, barrier slots, metadata (S row offsets,
     // image offsets, chunk counts), tile slice
     const size_t meta = (size_t)2 * (2 * B - 1) * 8 + (size_t)B * 12 + 8;
     const int nh_s = ts.npad > 64 ? 64 : ts.npad;
     ts.leg_smem = 1024 + (size_t)ts.kcmax * 2 * nh_s * 128 + (size_t)kStagingLegI * kChunk +
                   (size_t)kStagesLegI * 2 * kChunk + 64 * 8 + meta + (size_t)B * 8 + (size_t)lmax * 8;
-    ts.rad_smem = 1024 + (size_t)kStagesRadI * 4 * kChunk + 64 * 8 + meta + (size_t)rmax * 8;
-    if (ts.leg_smem > 227 * 1024 || ts.rad_smem > 227 * 1024) e = cudaErrorInvalidValue;
+    if (ts.leg_smem > 227 * 1024) e = cudaErrorInvalidValue;
   }
   P.bytes += bytes;
   if (e != cudaSuccess) {

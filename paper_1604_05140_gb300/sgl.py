@@ -76,6 +76,8 @@ def load_library():
         "sgl_stage_times": (i32, [vp, vp, vp]),
         "sgl_stage_name": (ctypes.c_char_p, [i32]),
         "sgl_forward_noalloc": (i32, [i32, i32, vp, vp, vp]),
+        "sgl_autotune": (i32, [vp, vp, vp, ctypes.c_char_p, vp]),
+        "sgl_tuning": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -143,6 +145,15 @@ def sgl_grid(plan, fn: int = 0):
 
 def sgl_destroy(plan):
     load_library().sgl_destroy(plan)
+
+
+def sgl_autotune(plan, samples_ptr: int, coeffs_ptr: int, cache_path: Optional[str] = None, stream: int = 0):
+    path = cache_path.encode() if cache_path else None
+    _check(load_library().sgl_autotune(plan, samples_ptr, coeffs_ptr, path, stream), plan)
+
+
+def sgl_tuning(plan) -> str:
+    return load_library().sgl_tuning(plan).decode()
 
 
 def sgl_check(plan, stream: int = 0):
@@ -280,6 +291,26 @@ class Plan:
             self._prep(out, self.n_samples, "out")
         sgl_adjoint(self.handle, int(bool(of_inverse)), x.data_ptr(), out.data_ptr(), self._stream(x, out))
         return out
+
+    def autotune(self, cache: Optional[str] = None, samples=None, coeffs=None) -> str:
+        """Choose the plan's launch configuration by timing it (sgl_autotune).
+        samples / coeffs are device scratch tensors of the plan's shapes
+        (allocated here when None; their contents are overwritten).  Returns
+        the configuration text (sgl_tuning)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if samples is None:
+            samples = torch.empty(self.sample_shape, dtype=self.dtype, device=dev)
+        if coeffs is None:
+            coeffs = torch.empty(self.coeff_shape, dtype=self.dtype, device=dev)
+        self._prep(samples, self.n_samples, "samples")
+        self._prep(coeffs, self.n_coeffs, "coeffs")
+        sgl_autotune(self.handle, samples.data_ptr(), coeffs.data_ptr(), cache, self._stream(samples, coeffs))
+        return self.tuning
+
+    @property
+    def tuning(self) -> str:
+        return sgl_tuning(self.handle)
 
     def check(self):
         import torch
