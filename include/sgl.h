@@ -75,9 +75,12 @@ typedef enum {
 typedef enum {
   SGL_FP64 = 0,    /* every stage in double precision on the CUDA cores */
   SGL_FP32 = 1,    /* every stage in single precision on the CUDA cores */
-  SGL_TF32X3 = 2   /* FP32 FFT; Legendre and radial stages on tcgen05 tensor
+  SGL_TF32X3 = 2,  /* FP32 FFT; Legendre and radial stages on tcgen05 tensor
                       cores as three TF32 products (hi*hi + hi*lo + lo*hi)
                       with FP32 accumulation; bandlimits divisible by 4 */
+  SGL_TF32 = 3     /* as SGL_TF32X3 with the hi*hi product only (inputs and
+                      tables rounded to TF32, 11 significant bits): the fast,
+                      low-accuracy variant (normwise error of order 1e-3) */
 } sgl_precision;
 
 typedef enum {

@@ -144,7 +144,7 @@ static cudaError_t build_fft_lists(Plan& P) {
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
     const int JP = fft_jp(P, sg.B, true);
-    if (P.prec == SGL_TF32X3) {
+    if (tc_precision(P.prec)) {
       // the tensor-core Legendre synthesis stores spectra [m][b][c][j][i]: each
       // inverse-FFT CTA takes JP consecutive shells of one ring pair (layout 1)
       for (int b = 0; b < sg.NB; ++b)
@@ -300,12 +300,12 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
     size_t smem = fft_smem_for(P->prec, sg.n1, sg.n2, sg.B);
     if (smem > 227 * 1024) return fail(P, SGL_ERR_UNSUPPORTED, "FFT tile exceeds shared memory");
   }
-  if (P->prec == SGL_TF32X3) {
+  if (tc_precision(P->prec)) {
     e = tc_prepare(*P);
     if (e != cudaSuccess) return cuda_fail(P, e, "tensor-core preparation");
   }
   P->launches_per_call = (int)P->segs.size() + 2;
-  if (P->prec == SGL_TF32X3) P->launches_per_call = (int)P->segs.size() + tc_launches(*P);
+  if (tc_precision(P->prec)) P->launches_per_call = (int)P->segs.size() + tc_launches(*P);
   return SGL_OK;
 }
 
@@ -470,7 +470,7 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
     }
     e = build_fft_lists(*P);
     if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
-    if (P->prec == SGL_TF32X3) {
+    if (tc_precision(P->prec)) {
       int best = 65;
       double tbest = 1e30;
       for (int rn : {65, 1}) {
@@ -488,7 +488,7 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
     }
   }
   e = build_fft_lists(*P);
-  if (e == cudaSuccess && P->prec == SGL_TF32X3) e = tc_radi_retile(*P);
+  if (e == cudaSuccess && tc_precision(P->prec)) e = tc_radi_retile(*P);
   if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
   P->tuning = tuning_text(*P, cached ? "cache" : "timed");
   if (!cached && cache_path) {
@@ -508,14 +508,14 @@ sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples) {
   *out = nullptr;
   if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
   if (batch < 1) return fail(nullptr, SGL_ERR_ARG, "batch must be >= 1");
-  if (prec < SGL_FP64 || prec > SGL_TF32X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
+  if (prec < SGL_FP64 || prec > SGL_TF32) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
   if (samples != SGL_SAMPLES_WEIGHTED && samples != SGL_SAMPLES_PHYSICAL)
     return fail(nullptr, SGL_ERR_ARG, "unknown sample convention");
   if (samples == SGL_SAMPLES_PHYSICAL && prec != SGL_FP64)
     return fail(nullptr, SGL_ERR_ARG, "physical samples need an FP64 plan");
   if (!bandlimit_supported(B)) return fail(nullptr, SGL_ERR_UNSUPPORTED, "unsupported bandlimit");
-  if (prec == SGL_TF32X3 && B % 4 != 0)
-    return fail(nullptr, SGL_ERR_UNSUPPORTED, "SGL_TF32X3 plans need a bandlimit divisible by 4");
+  if (tc_precision(prec) && B % 4 != 0)
+    return fail(nullptr, SGL_ERR_UNSUPPORTED, "tensor-core plans need a bandlimit divisible by 4");
   Plan* P = new Plan();
   P->prec = prec;
   P->samples = samples;
@@ -534,13 +534,13 @@ sgl_status sgl_plan_many(sgl_plan_t* out, const int* B_per_fn, int nfn, int prec
   if (!out) return fail(nullptr, SGL_ERR_ARG, "null output pointer");
   *out = nullptr;
   if (!B_per_fn || nfn < 1) return fail(nullptr, SGL_ERR_ARG, "need at least one function");
-  if (prec < SGL_FP64 || prec > SGL_TF32X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
+  if (prec < SGL_FP64 || prec > SGL_TF32) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
   std::vector<int> Bs(B_per_fn, B_per_fn + nfn);
   for (int B : Bs) {
     if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
     if (!bandlimit_supported(B)) return fail(nullptr, SGL_ERR_UNSUPPORTED, "unsupported bandlimit");
-    if (prec == SGL_TF32X3 && B % 4 != 0)
-      return fail(nullptr, SGL_ERR_UNSUPPORTED, "SGL_TF32X3 plans need bandlimits divisible by 4");
+    if (tc_precision(prec) && B % 4 != 0)
+      return fail(nullptr, SGL_ERR_UNSUPPORTED, "tensor-core plans need bandlimits divisible by 4");
   }
   Plan* P = new Plan();
   P->prec = prec;

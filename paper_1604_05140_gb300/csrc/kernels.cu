@@ -648,7 +648,7 @@ static cudaError_t forward_t(Plan& P, const void* samples, void* coeffs, cudaStr
   if (P.samples == SGL_SAMPLES_PHYSICAL) mode = weights ? 1 : 2;
   cudaError_t e = run_fft<real>(P, false, samples, nullptr, mode, s);
   if (e != cudaSuccess) return e;
-  if (P.prec == SGL_TF32X3) {
+  if (tc_precision(P.prec)) {
     e = run_tc_stage(P, LEG_F, P.d_w1, P.d_w2, weights, s);
     if (e != cudaSuccess) return e;
     return run_tc_stage(P, RAD_F, P.d_w2, coeffs, weights, s);
@@ -661,7 +661,7 @@ static cudaError_t forward_t(Plan& P, const void* samples, void* coeffs, cudaStr
 template <typename real>
 static cudaError_t inverse_t(Plan& P, const void* coeffs, void* samples, cudaStream_t s, bool weights) {
   cudaError_t e;
-  if (P.prec == SGL_TF32X3) {
+  if (tc_precision(P.prec)) {
     e = run_tc_stage(P, RAD_I, coeffs, P.d_w2, 0, s);
     if (e != cudaSuccess) return e;
     e = run_tc_stage(P, LEG_I, P.d_w2, P.d_w1, 0, s);

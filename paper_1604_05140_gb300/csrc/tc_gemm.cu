@@ -99,6 +99,7 @@ struct TcArgs {
   int weighted;
   int64_t w2_off;
   int npmax;
+  int nprod;                    // TF32 products per K step: 3 (hi*hi + hi*lo + lo*hi) or 1 (hi*hi)
 };
 
 template <int PROB, int STAGES>
@@ -234,10 +235,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const uint64_t xl = xh + (uint64_t)(kChunkBytes >> 4);
           const uint64_t tb = tdesc0 + (uint64_t)((kc * 2 * npad * 128) >> 4) + 2 * me;
           const uint32_t first = kc > 0 ? 1u : 0u;
-          mma_tf32(dm, xh, tb, idesc2, first);
-          mma_tf32(dc, xl, tb, idesc1, 1u);
-          mma_tf32(dm, xh + 4, tb + 4, idesc2, 1u);
-          mma_tf32(dc, xl + 4, tb + 4, idesc1, 1u);
+          if (a.nprod == 3) {
+            mma_tf32(dm, xh, tb, idesc2, first);
+            mma_tf32(dc, xl, tb, idesc1, 1u);
+            mma_tf32(dm, xh + 4, tb + 4, idesc2, 1u);
+            mma_tf32(dc, xl + 4, tb + 4, idesc1, 1u);
+          } else {  // hi*hi only: the table's hi rows, main accumulator
+            mma_tf32(dm, xh, tb, idesc1, first);
+            mma_tf32(dm, xh + 4, tb + 4, idesc1, 1u);
+          }
           mma_commit(empty + s);
         }
         if (!ok) break;
@@ -262,10 +268,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const int idx = v * kSplitThreads + tid;
           float4 x = hi[idx];
           float4 h = {tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w)};
-          // lo rounded to TF32 too, so that the tensor core uses it unchanged
-          float4 l = {tf32_rna(x.x - h.x), tf32_rna(x.y - h.y), tf32_rna(x.z - h.z), tf32_rna(x.w - h.w)};
           hi[idx] = h;
-          lo[idx] = l;
+          if (a.nprod == 3) {
+            // lo rounded to TF32 too, so that the tensor core uses it unchanged
+            float4 l = {tf32_rna(x.x - h.x), tf32_rna(x.y - h.y), tf32_rna(x.z - h.z), tf32_rna(x.w - h.w)};
+            lo[idx] = l;
+          }
         }
         fence_proxy_async();
         mbar_arrive(split + s);
@@ -301,7 +309,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
           const uint32_t tc = taddr + (uint32_t)c0;
-          tmem_ld16_sum4(tc, tc + 2 * np, tc + np, tc + 3 * np, v);
+          if (a.nprod == 3) {
+            tmem_ld16_sum4(tc, tc + 2 * np, tc + np, tc + 3 * np, v);
+          } else {
+            float w[16];
+            tmem_ld16x2(tc, tc + 2 * np, v, w);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] += w[k];
+          }
           if (valid) {
             // S_f[l][b][m+l][c][i] = 2B (NB l^2 + b(2l+1) + m + l) + c B + i, stepped in
             // l += 2 by first and second differences
@@ -330,7 +345,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
           const uint32_t tc = taddr + (uint32_t)c0;
-          tmem_ld16_sum4(tc, tc + 2 * np, tc + np, tc + 3 * np, v);
+          if (a.nprod == 3) {
+            tmem_ld16_sum4(tc, tc + 2 * np, tc + np, tc + 3 * np, v);
+          } else {
+            float w[16];
+            tmem_ld16x2(tc, tc + 2 * np, v, w);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] += w[k];
+          }
           if (valid) {
             // omega(n + 1, l, m) - omega(n, l, m) = n^2
             int n = l + 1 + n0 + c0;
@@ -641,6 +663,7 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
     a.weighted = weighted;
     a.w2_off = sg.w2_off;
     a.npmax = S.npmax;
+    a.nprod = tc_products(P.prec);
     (void)x;
     void (*fn)(const CUtensorMap, TcArgs) =
         prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg> : tc_gemm_kernel<TC_RAD_F, kStagesRad>;

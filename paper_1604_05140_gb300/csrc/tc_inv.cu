@@ -38,9 +38,10 @@ constexpr int kStagesRadI = 3;
 __device__ __forceinline__ int sw_pos(int row, int q) { return row * 128 + ((q ^ (row & 7)) << 4); }
 
 // Split 4*NQ consecutive K values v of one row into TF32 hi/lo and store them
-// at 16-byte chunks q0 .. q0+NQ-1 of the row.
+// at 16-byte chunks q0 .. q0+NQ-1 of the row (hi only when !with_lo).
 template <int NQ>
-__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, int row, const float* v, int q0) {
+__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, int row, const float* v, int q0,
+                                            bool with_lo = true) {
 #pragma unroll
   for (int qq = 0; qq < NQ; ++qq) {
     const int q = q0 + qq;
@@ -54,7 +55,7 @@ __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo
     l.z = tf32_rna(v[4 * qq +2] - h.z);
     l.w = tf32_rna(v[4 * qq +3] - h.w);
     *(float4*)(hi + sw_pos(row, q)) = h;
-    *(float4*)(lo + sw_pos(row, q)) = l;
+    if (with_lo) *(float4*)(lo + sw_pos(row, q)) = l;
   }
 }
 }  // namespace
@@ -81,6 +82,7 @@ struct LegIArgs {
   float* g;                   // output, layout [m_idx][b][c][j < 2B][i]
   int* err;
   int B, NB, npad, kcmax;
+  int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
 };
 
 __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid_constant__ CUtensorMap smap,
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
     }
     for (int s = 0; s < kStagesLegI; ++s) {
       mbar_init(split + s, kSplitThreads);
-      mbar_init(empty + s, 1);
+      mbar_init(empty + s, 2);  // the issuing warp's MMAs done, and the other issuer past the stage
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(accf + k, 2);  // both MMA issuers
@@ -205,12 +207,18 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
         // accumulators of this buffer: [P main][P corr][Q main][Q corr], nh columns each
         const uint32_t d = tmem + (uint32_t)((4 * acc + 2 * p) * nh);
         const uint64_t tp = tdesc0 + (uint64_t)(((p ? kcp : 0) * 2 * chunk_tab) >> 4);
-        // every chunk of the tile is waited for, so that the ring's phases are
-        // followed in order; only the chunks of parity p are issued here
+        // Every chunk of the tile is waited for, so that the ring's phases are
+        // followed in order; only the chunks of parity p are issued here.  A
+        // stage is refilled only after both issuers are past it (the other
+        // issuer's plain arrival on `empty`), so neither can fall a whole ring
+        // behind and mistake an older phase of the same parity for the next.
         for (int ch = 0; ch < kcp + kcq; ++ch, ++c) {
           const int s = c % kStagesLegI;
           if (!mbar_wait(split + s, (c / kStagesLegI) & 1, abort_flag)) { ok = false; break; }
-          if ((ch >= kcp) != (p == 1)) continue;
+          if ((ch >= kcp) != (p == 1)) {
+            mbar_arrive(empty + s);
+            continue;
+          }
           const int kc = p ? ch - kcp : ch;
           tc_after();
           const uint64_t xh = xdesc0 + (uint64_t)((s * 2 * kChunk) >> 4);
@@ -219,8 +227,12 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
-            mma_tf32(d, xh + 2 * kk, th + 2 * kk, idesc2, first);
-            mma_tf32(d + (uint32_t)nh, xl + 2 * kk, th + 2 * kk, idesc1, 1u);
+            if (a.nprod == 3) {
+              mma_tf32(d, xh + 2 * kk, th + 2 * kk, idesc2, first);
+              mma_tf32(d + (uint32_t)nh, xl + 2 * kk, th + 2 * kk, idesc1, 1u);
+            } else {
+              mma_tf32(d, xh + 2 * kk, th + 2 * kk, idesc1, first);
+            }
           }
           mma_commit(empty + s);
         }
@@ -249,7 +261,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
         mbar_arrive(stge + st);
         const int s = c % kStagesLegI;
         if (!mbar_wait(empty + s, ((c / kStagesLegI) & 1) ^ 1, abort_flag)) { ok = false; break; }
-        split_store<4>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h);
+        split_store<4>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h, a.nprod == 3);
         fence_proxy_async();
         mbar_arrive(split + s);
       }
@@ -281,12 +293,16 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
       const uint32_t dQ = dP + (uint32_t)(2 * nh);
       for (int c0 = 16 * ehalf; c0 < ncols; c0 += 32) {
         float P[16], Q[16];
-        if (kcp) tmem_ld16_sum(dP + (uint32_t)c0, dP + (uint32_t)(nh + c0), P);
-        else
+        if (a.nprod == 1) {
+          tmem_ld16x2(dP + (uint32_t)c0, dQ + (uint32_t)c0, P, Q);
+        } else {
+          if (kcp) tmem_ld16_sum(dP + (uint32_t)c0, dP + (uint32_t)(nh + c0), P);
+          if (kcq) tmem_ld16_sum(dQ + (uint32_t)c0, dQ + (uint32_t)(nh + c0), Q);
+        }
+        if (!kcp)
 #pragma unroll
           for (int k = 0; k < 16; ++k) P[k] = 0.f;
-        if (kcq) tmem_ld16_sum(dQ + (uint32_t)c0, dQ + (uint32_t)(nh + c0), Q);
-        else
+        if (!kcq)
 #pragma unroll
           for (int k = 0; k < 16; ++k) Q[k] = 0.f;
         if (valid) {
@@ -336,6 +352,7 @@ struct RadIArgs {
   float* s;                   // output S, layout [m_idx][p][l'][b][c][i]
   int* err;
   int B, NB;
+  int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
 };
 
 // Coefficients of one K chunk (32 degrees n) of one tile column, gathered by
@@ -459,7 +476,16 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
           const uint64_t ah = sdesc0 + (uint64_t)((s * 4 * kChunk) >> 4);
           const uint64_t al = ah + (uint64_t)(kChunk >> 4);
           const uint64_t bh = al + (uint64_t)(kChunk >> 4) + (nar ? 0u : (uint64_t)(me * (128 * 128 >> 4)));
-          if (nar) {
+          if (a.nprod == 1) {  // hi*hi only: the B operand's hi rows, main accumulator
+            if (nar) {
+              mma_tf32(dm, ah + 2 * me, bh + 2 * me, idesc1, kc > 0 ? 1u : 0u);
+              mma_tf32(dm, ah + 2 * me + 4, bh + 2 * me + 4, idesc1, 1u);
+            } else {
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                mma_tf32(dm, ah + 2 * kk, bh + 2 * kk, idesc1, (kc > 0 || kk > 0) ? 1u : 0u);
+            }
+          } else if (nar) {
             const uint32_t first = kc > 0 ? 1u : 0u;
             mma_tf32(dm, ah + 2 * me, bh + 2 * me, idesc2, first);
             mma_tf32(dc, al + 2 * me, bh + 2 * me, idesc1, 1u);
@@ -501,10 +527,10 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       // B operand: per half of 64 columns, 64 hi rows then 64 lo rows
       unsigned char* sb = st + s * 4 * kChunk + 2 * kChunk;
       if (nar) {
-        split_store<2>(sb, sb + 64 * 128, tid & 63, v, 2 * (tid >> 6));
+        split_store<2>(sb, sb + 64 * 128, tid & 63, v, 2 * (tid >> 6), a.nprod == 3);
       } else {
         unsigned char* hb = sb + ((tid >> 6) & 1) * (128 * 128);
-        split_store<4>(hb, hb + 64 * 128, tid & 63, v, 4 * (tid >> 7));
+        split_store<4>(hb, hb + 64 * 128, tid & 63, v, 4 * (tid >> 7), a.nprod == 3);
       }
       fence_proxy_async();
       mbar_arrive(split + s);
@@ -547,10 +573,15 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
         float v[16];
         if (nar) {
           const uint32_t tc = dq + (uint32_t)c0;
-          tmem_ld16_sum4(tc, tc + 128u, tc + 64u, tc + 192u, v);
+          if (a.nprod == 3) {
+            tmem_ld16_sum4(tc, tc + 128u, tc + 64u, tc + 192u, v);
+          } else {
+            tmem_ld16_sum(tc, tc + 128u, v);  // main0 + main1
+          }
         } else {  // columns 64h + c: [main_h | corr_h] at 128 h
           const uint32_t tc = dq + (uint32_t)((c0 >> 6) * 128 + (c0 & 63));
-          tmem_ld16_sum(tc, tc + 64u, v);
+          if (a.nprod == 3) tmem_ld16_sum(tc, tc + 64u, v);
+          else tmem_ld16(tc, v);
         }
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -853,6 +884,7 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
       a.err = P.d_err;
       a.B = sg.B;
       a.NB = sg.NB;
+      a.nprod = tc_products(P.prec);
       e = cudaFuncSetAttribute(tc_rad_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.rad_smem);
       if (e != cudaSuccess) return e;
       tc_rad_inv_kernel<<<ts.rad_grid, kThreadsInv, ts.rad_smem, s>>>(a);
@@ -871,6 +903,7 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
       a.NB = sg.NB;
       a.npad = ts.npad;
       a.kcmax = ts.kcmax;
+      a.nprod = tc_products(P.prec);
       e = cudaFuncSetAttribute(tc_leg_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.leg_smem);
       if (e != cudaSuccess) return e;
       tc_leg_inv_kernel<<<ts.leg_grid, kThreadsInv, ts.leg_smem, s>>>(ts.smap, a);
