@@ -382,7 +382,8 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3+f32acc", "tf32": "tf32+f32acc"}[args.precision],
+        "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3+f32acc", "tf32": "tf32+f32acc",
+                  "bf16x3": "bf16x3+f32acc"}[args.precision],
         "data": "synthetic: seeded complex-normal SGL coefficients with 1/n decay, synthesized to samples by the inverse",
         "config": {"workload": f"SGL inverse+forward, B={B_BENCH}, batch {BATCH} functions per GPU",
                    "B": B_BENCH, "batch": BATCH, "precision": args.precision,
@@ -399,12 +400,14 @@ def run_ours(args):
     }
     if not args.no_variants and args.precision == "tf32x3":
         # reduced-precision variant of the tensor-core stages, same workload
-        v_plan, v_ms, v_stage, v_clocks, v_err, _, _ = time_path("tf32", args.steps, args.warmup, ws, rank)
-        v_value, v_ms = whole_job(ws, BATCH, v_ms)
-        line["variants"] = {"tf32": {"value": v_value, "unit": "transforms/s", "ms_per_step": v_ms,
-                                     "round_trip_max_rel_err": v_err,
-                                     "stage_ms": {k: v[0] for k, v in v_stage.items()}}}
-        del v_plan
+        line["variants"] = {}
+        for vp in ("tf32", "bf16x3"):
+            v_plan, v_ms, v_stage, v_clocks, v_err, _, _ = time_path(vp, args.steps, args.warmup, ws, rank)
+            v_value, v_ms = whole_job(ws, BATCH, v_ms)
+            line["variants"][vp] = {"value": v_value, "unit": "transforms/s", "ms_per_step": v_ms,
+                                    "round_trip_max_rel_err": v_err,
+                                    "stage_ms": {k: v[0] for k, v in v_stage.items()}}
+            del v_plan
     if "fp64" in results and args.precision != "fp64":
         r = results["fp64"]
         line["fp64_path"] = {"value": r["value"], "unit": "transforms/s", "ms_per_step": r["ms"],
@@ -462,7 +465,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "tf32", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "tf32", "bf16x3", "fp32", "fp64"])
     ap.add_argument("--no-variants", action="store_true", help="skip the reduced-precision variant lines")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")

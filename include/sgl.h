@@ -78,9 +78,12 @@ typedef enum {
   SGL_TF32X3 = 2,  /* FP32 FFT; Legendre and radial stages on tcgen05 tensor
                       cores as three TF32 products (hi*hi + hi*lo + lo*hi)
                       with FP32 accumulation; bandlimits divisible by 4 */
-  SGL_TF32 = 3     /* as SGL_TF32X3 with the hi*hi product only (inputs and
+  SGL_TF32 = 3,    /* as SGL_TF32X3 with the hi*hi product only (inputs and
                       tables rounded to TF32, 11 significant bits): the fast,
                       low-accuracy variant (normwise error of order 1e-3) */
+  SGL_BF16X3 = 4   /* as SGL_TF32X3 with BF16 hi/lo pairs (8 + 8 significant
+                      bits) on the kind::f16 tensor-core path: normwise error
+                      of order 1e-5 */
 } sgl_precision;
 
 typedef enum {

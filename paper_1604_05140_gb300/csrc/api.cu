@@ -508,7 +508,7 @@ sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples) {
   *out = nullptr;
   if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
   if (batch < 1) return fail(nullptr, SGL_ERR_ARG, "batch must be >= 1");
-  if (prec < SGL_FP64 || prec > SGL_TF32) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
+  if (prec < SGL_FP64 || prec > SGL_BF16X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
   if (samples != SGL_SAMPLES_WEIGHTED && samples != SGL_SAMPLES_PHYSICAL)
     return fail(nullptr, SGL_ERR_ARG, "unknown sample convention");
   if (samples == SGL_SAMPLES_PHYSICAL && prec != SGL_FP64)
@@ -534,7 +534,7 @@ sgl_status sgl_plan_many(sgl_plan_t* out, const int* B_per_fn, int nfn, int prec
   if (!out) return fail(nullptr, SGL_ERR_ARG, "null output pointer");
   *out = nullptr;
   if (!B_per_fn || nfn < 1) return fail(nullptr, SGL_ERR_ARG, "need at least one function");
-  if (prec < SGL_FP64 || prec > SGL_TF32) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
+  if (prec < SGL_FP64 || prec > SGL_BF16X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
   std::vector<int> Bs(B_per_fn, B_per_fn + nfn);
   for (int B : Bs) {
     if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");

@@ -47,8 +47,9 @@ inline bool bandlimit_supported(int B) {
 
 // Plans whose Legendre and radial stages run on the tensor cores, and the
 // number of TF32 products per K step they use (hi*hi [+ hi*lo + lo*hi]).
-inline bool tc_precision(int prec) { return prec == SGL_TF32X3 || prec == SGL_TF32; }
+inline bool tc_precision(int prec) { return prec == SGL_TF32X3 || prec == SGL_TF32 || prec == SGL_BF16X3; }
 inline int tc_products(int prec) { return prec == SGL_TF32 ? 1 : 3; }
+inline bool tc_bf16(int prec) { return prec == SGL_BF16X3; }
 
 inline int64_t coeff_count(int B) { return (int64_t)B * (B + 1) * (2 * B + 1) / 6; }
 inline int64_t sample_count(int B) { return 4LL * B * B * B; }

@@ -102,12 +102,15 @@ struct TcArgs {
   int nprod;                    // TF32 products per K step: 3 (hi*hi + hi*lo + lo*hi) or 1 (hi*hi)
 };
 
-template <int PROB, int STAGES>
+// BF: BF16 hi/lo operands (kind::f16, 64-byte rows, K = 16 per MMA) instead
+// of TF32 (kind::tf32, 128-byte rows, K = 8 per MMA).
+template <int PROB, int STAGES, bool BF>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap xmap, TcArgs a) {
+  constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int KC = a.KC;
-  const int tab_bytes = 2 * KC * a.npmax * 128;            // hi + lo for the largest group
+  const int tab_bytes = 2 * KC * a.npmax * ROWB;           // hi + lo for the largest group
   unsigned char* tab = base;                                 // [hi: KC][npad][128 B] [lo: same]
   unsigned char* xs = base + tab_bytes;                      // STAGES x (hi 16 KB, lo 16 KB)
   uint64_t* bars = (uint64_t*)(xs + STAGES * 2 * kChunkBytes);
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int2 tl = s_tiles[t];
         if (tl.x != cur) {
           if (ngrp > 0 && !mbar_wait(tabe, (ngrp - 1) & 1, abort_flag)) break;
-          const uint32_t bytes = (uint32_t)(2 * KC * (s_npad[tl.x] & 0xff) * 128);
+          const uint32_t bytes = (uint32_t)(2 * KC * (s_npad[tl.x] & 0xff) * ROWB);
           mbar_arrive_tx(tabf, bytes);
           bulk_load(tab, a.tabimg + s_off[tl.x], bytes, tabf);
           cur = tl.x;
@@ -208,8 +211,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const int me = warp == 1 ? 0 : 1;
       int cur = -1, ngrp = 0;
       uint32_t c = 0, tcount = 0;
-      const uint64_t xdesc0 = sw128_desc(smem_u32(xs));
-      const uint64_t tdesc0 = sw128_desc(smem_u32(tab));
+      // TF32: X_hi in place of the raw chunk, X_lo in the second half of the
+      // stage; BF16: X_hi and X_lo (8 KB each) in the second half
+      const uint64_t xdesc0 = BF ? sw64_desc(smem_u32(xs + kChunkBytes)) : sw128_desc(smem_u32(xs));
+      const uint64_t tdesc0 = BF ? sw64_desc(smem_u32(tab)) : sw128_desc(smem_u32(tab));
       for (int t = t_begin; t < t_end && !*abort_flag; ++t, ++tcount) {
         const int2 tl = s_tiles[t];
         if (tl.x != cur) {
@@ -218,7 +223,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           ++ngrp;
         }
         const int npad = s_npad[tl.x] & 0xff;
-        const uint32_t idesc2 = idesc_tf32(2 * npad), idesc1 = idesc_tf32(npad);
+        const uint32_t idesc2 = BF ? idesc_bf16(2 * npad) : idesc_tf32(2 * npad);
+        const uint32_t idesc1 = BF ? idesc_bf16(npad) : idesc_tf32(npad);
         const int acc = tcount & 1;
         if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
         tc_after();
@@ -232,10 +238,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (!mbar_wait(split + s, (c / STAGES) & 1, abort_flag)) { ok = false; break; }
           tc_after();
           const uint64_t xh = xdesc0 + (uint64_t)((s * 2 * kChunkBytes) >> 4) + 2 * me;
-          const uint64_t xl = xh + (uint64_t)(kChunkBytes >> 4);
-          const uint64_t tb = tdesc0 + (uint64_t)((kc * 2 * npad * 128) >> 4) + 2 * me;
+          const uint64_t xl = xh + (uint64_t)((BF ? kChunkBytes / 2 : kChunkBytes) >> 4);
+          const uint64_t tb = tdesc0 + (uint64_t)((kc * 2 * npad * ROWB) >> 4) + 2 * me;
           const uint32_t first = kc > 0 ? 1u : 0u;
-          if (a.nprod == 3) {
+          if (BF) {  // K = 16 per MMA: one K step of the chunk per issuer
+            mma_bf16(dm, xh, tb, idesc2, first);
+            mma_bf16(dc, xl, tb, idesc1, 1u);
+          } else if (a.nprod == 3) {
             mma_tf32(dm, xh, tb, idesc2, first);
             mma_tf32(dc, xl, tb, idesc1, 1u);
             mma_tf32(dm, xh + 4, tb + 4, idesc2, 1u);
@@ -263,6 +272,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         if (!mbar_wait(full + s, (c / STAGES) & 1, abort_flag)) { ok = false; break; }
         float4* hi = (float4*)(xs + s * 2 * kChunkBytes);
         float4* lo = (float4*)(xs + s * 2 * kChunkBytes + kChunkBytes);
+        if (BF) {
+          // raw chunk (128-byte rows, 32 floats) -> BF16 hi/lo rows of 64 bytes
+          unsigned char* ob = xs + s * 2 * kChunkBytes + kChunkBytes;
+#pragma unroll
+          for (int v = 0; v < kChunkBytes / 16 / kSplitThreads; ++v) {
+            const int idx = v * kSplitThreads + tid;
+            const int r = idx >> 3, q = (idx & 7) ^ (r & 7);  // values 4q .. 4q+3 of row r
+            const float4 x = hi[idx];
+            const uint32_t s0 = bf16_split(x.x), s1 = bf16_split(x.y), s2 = bf16_split(x.z), s3 = bf16_split(x.w);
+            const uint2 h2 = {(s0 & 0xFFFFu) | (s1 << 16), (s2 & 0xFFFFu) | (s3 << 16)};
+            const uint2 l2 = {(s0 >> 16) | (s1 & 0xFFFF0000u), (s2 >> 16) | (s3 & 0xFFFF0000u)};
+            const int off = sw64_off(r, q >> 1) + (q & 1) * 8;
+            *(uint2*)(ob + off) = h2;
+            *(uint2*)(ob + kChunkBytes / 2 + off) = l2;
+          }
+          fence_proxy_async();
+          mbar_arrive(split + s);
+          continue;
+        }
 #pragma unroll
         for (int v = 0; v < kChunkBytes / 16 / kSplitThreads; ++v) {
           const int idx = v * kSplitThreads + tid;
@@ -449,6 +477,36 @@ void append_image(std::vector<unsigned char>& img, int N, int K, int npad, int K
     }
 }
 
+// BF16 round to nearest even of a float (finite values)
+uint16_t bf16_bits(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+
+// BF16 image of the same table: per K chunk the npad hi rows, then the npad
+// lo rows, each row 32 values in 64 bytes with the 64-byte swizzle.
+void append_image_bf16(std::vector<unsigned char>& img, int N, int K, int npad, int KC,
+                       const std::vector<double>& A /* N x K */) {
+  const size_t off = img.size();
+  const size_t plane = (size_t)npad * 64;
+  img.resize(off + 2 * (size_t)KC * plane, 0);
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k) {
+      const double v = A[(size_t)n * K + k];
+      const uint16_t hb = bf16_bits((float)v);
+      uint32_t hu = (uint32_t)hb << 16;
+      float hi;
+      memcpy(&hi, &hu, 4);
+      const uint16_t lb = bf16_bits((float)(v - (double)hi));
+      const int kc = k / 32, kin = k % 32;
+      const int q = kin / 8, w = kin % 8;  // 16-byte chunk of the 64-byte row, element in it
+      const size_t pos = (size_t)kc * 2 * plane + (size_t)n * 64 + (size_t)((q ^ ((n >> 1) & 3)) * 16) + w * 2;
+      memcpy(&img[off + pos], &hb, 2);
+      memcpy(&img[off + plane + pos], &lb, 2);
+    }
+}
+
 int pad16(int n) { return n <= 16 ? 16 : (n + 15) / 16 * 16; }
 
 }  // namespace
@@ -459,6 +517,7 @@ cudaError_t tc_prepare(Plan& P) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   TcState* st = new TcState();
+  const bool bf = tc_bf16(P.prec);
   std::vector<unsigned char> img;
   struct Pending {
     std::vector<int64_t> off;
@@ -496,7 +555,7 @@ cudaError_t tc_prepare(Plan& P) {
           }
           img.resize((img.size() + 1023) / 1024 * 1024);
           am_off[am * 2 + p] = (int64_t)img.size();
-          append_image(img, N, B, np, KC, A);
+          (bf ? append_image_bf16 : append_image)(img, N, B, np, KC, A);
         }
       for (int mi = 0; mi < 2 * B - 1; ++mi) {
         const int m = mi - (B - 1);
@@ -549,7 +608,7 @@ cudaError_t tc_prepare(Plan& P) {
         img.resize((img.size() + 1023) / 1024 * 1024);
         pr.off[w * ngr + g] = (int64_t)img.size();
         pr.npad[g] = np | (l << 8) | (n0 << 16);
-        append_image(img, N, B, np, KC, A);
+        (bf ? append_image_bf16 : append_image)(img, N, B, np, KC, A);
       }
     for (int g = 0; g < ngr; ++g) {
       const int l = rgrp[g].x, n0 = rgrp[g].y;
@@ -605,7 +664,7 @@ cudaError_t tc_prepare(Plan& P) {
       if (e != cudaSuccess) { delete st; return e; }
       max_tiles += 1;
       // tables, X ring, 64 barrier/flag slots, group metadata, tile slice
-      S.smem = 1024 + (size_t)2 * S.KC * S.npmax * 128 + (size_t)stages * 2 * kChunkBytes + 64 * 8 +
+      S.smem = 1024 + (size_t)2 * S.KC * S.npmax * (bf ? 64 : 128) + (size_t)stages * 2 * kChunkBytes + 64 * 8 +
                (size_t)S.ngroups * 12 + 8 + (size_t)max_tiles * 8;
       if (S.smem > 227 * 1024) { delete st; return cudaErrorInvalidValue; }
     }
@@ -665,8 +724,11 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
     a.npmax = S.npmax;
     a.nprod = tc_products(P.prec);
     (void)x;
-    void (*fn)(const CUtensorMap, TcArgs) =
-        prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg> : tc_gemm_kernel<TC_RAD_F, kStagesRad>;
+    void (*fn)(const CUtensorMap, TcArgs);
+    if (tc_bf16(P.prec))
+      fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, true> : tc_gemm_kernel<TC_RAD_F, kStagesRad, true>;
+    else
+      fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, false> : tc_gemm_kernel<TC_RAD_F, kStagesRad, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem);
     if (e != cudaSuccess) return e;
     fn<<<S.grid, kThreads, S.smem, s>>>(S.xmap, a);

@@ -58,6 +58,26 @@ __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo
     if (with_lo) *(float4*)(lo + sw_pos(row, q)) = l;
   }
 }
+
+// BF16 form: 4*NQ consecutive K values of one row (NQ even) as BF16 hi/lo
+// pairs, at 16-byte chunks q0/2 .. q0/2 + NQ/2 - 1 of 64-byte rows.
+template <int NQ>
+__device__ __forceinline__ void split_store_bf(unsigned char* hi, unsigned char* lo, int row, const float* v,
+                                               int q0) {
+#pragma unroll
+  for (int j = 0; j < NQ / 2; ++j) {
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint32_t a = bf16_split(v[8 * j + 2 * e]), b = bf16_split(v[8 * j + 2 * e + 1]);
+      hw[e] = (a & 0xFFFFu) | (b << 16);
+      lw[e] = (a >> 16) | (b & 0xFFFF0000u);
+    }
+    const int off = sw64_off(row, q0 / 2 + j);
+    *(uint4*)(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *(uint4*)(lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
 }  // namespace
 
 // ===========================================================================
@@ -85,13 +105,16 @@ struct LegIArgs {
   int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
 };
 
+// BF: BF16 hi/lo operands (kind::f16, 64-byte rows, K = 16 per MMA).
+template <bool BF>
 __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid_constant__ CUtensorMap smap,
                                                                     LegIArgs a) {
+  constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int B = a.B, NB = a.NB, npad = a.npad;
   const int nh = npad > 64 ? 64 : npad;                    // rows (j') of one table half
-  const int chunk_tab = nh * 128;                          // one table chunk (hi or lo)
+  const int chunk_tab = nh * ROWB;                         // one table chunk (hi or lo)
   unsigned char* tab = base;                               // [P hi][P lo][Q hi][Q lo] of one half
   unsigned char* stg = tab + (size_t)a.kcmax * 2 * chunk_tab;   // staging ring: 32 l' x 128 rows each
   unsigned char* xs = stg + kStagingLegI * kChunk;         // operand ring: (hi, lo)
@@ -188,9 +211,10 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
       // the table image stacks nh hi rows over nh lo rows per K chunk: one
       // MMA of width 2 nh gives [X_hi T_hi | X_hi T_lo], a second of width nh
       // adds X_lo T_hi to the correction
-      const uint32_t idesc2 = idesc_tf32(2 * nh), idesc1 = idesc_tf32(nh);
-      const uint64_t xdesc0 = sw128_desc(smem_u32(xs));
-      const uint64_t tdesc0 = sw128_desc(smem_u32(tab));
+      const uint32_t idesc2 = BF ? idesc_bf16(2 * nh) : idesc_tf32(2 * nh);
+      const uint32_t idesc1 = BF ? idesc_bf16(nh) : idesc_tf32(nh);
+      const uint64_t xdesc0 = BF ? sw64_desc(smem_u32(xs)) : sw128_desc(smem_u32(xs));
+      const uint64_t tdesc0 = BF ? sw64_desc(smem_u32(tab)) : sw128_desc(smem_u32(tab));
       for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
         const int2 tl = s_tiles[t];
         const int am = abs_m(tl.x);
@@ -224,14 +248,23 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
           const uint64_t xh = xdesc0 + (uint64_t)((s * 2 * kChunk) >> 4);
           const uint64_t xl = xh + (uint64_t)(kChunk >> 4);
           const uint64_t th = tp + (uint64_t)((kc * 2 * chunk_tab) >> 4);
+          if (BF) {  // two K steps of 16
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
-            if (a.nprod == 3) {
-              mma_tf32(d, xh + 2 * kk, th + 2 * kk, idesc2, first);
-              mma_tf32(d + (uint32_t)nh, xl + 2 * kk, th + 2 * kk, idesc1, 1u);
-            } else {
-              mma_tf32(d, xh + 2 * kk, th + 2 * kk, idesc1, first);
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
+              mma_bf16(d, xh + 2 * kk, th + 2 * kk, idesc2, first);
+              mma_bf16(d + (uint32_t)nh, xl + 2 * kk, th + 2 * kk, idesc1, 1u);
+            }
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t first = (kc > 0 || kk > 0) ? 1u : 0u;
+              if (a.nprod == 3) {
+                mma_tf32(d, xh + 2 * kk, th + 2 * kk, idesc2, first);
+                mma_tf32(d + (uint32_t)nh, xl + 2 * kk, th + 2 * kk, idesc1, 1u);
+              } else {
+                mma_tf32(d, xh + 2 * kk, th + 2 * kk, idesc1, first);
+              }
             }
           }
           mma_commit(empty + s);
@@ -261,7 +294,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
         mbar_arrive(stge + st);
         const int s = c % kStagesLegI;
         if (!mbar_wait(empty + s, ((c / kStagesLegI) & 1) ^ 1, abort_flag)) { ok = false; break; }
-        split_store<4>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h, a.nprod == 3);
+        if (BF) split_store_bf<4>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h);
+        else split_store<4>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h, a.nprod == 3);
         fence_proxy_async();
         mbar_arrive(split + s);
       }
@@ -383,11 +417,16 @@ __device__ __forceinline__ void rad_gather(const RadIArgs& a, int2 tl, int kc, i
   }
 }
 
+template <bool BF>
 __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) {
+  constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
+  constexpr int TCH = 128 * ROWB;      // one table chunk (hi or lo): 128 rows i
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int B = a.B, NB = a.NB;
-  // stage s: [table hi][table lo][data hi][data lo], 16 KB each
+  // stage s: [table hi][table lo][data], 16 KB each part (BF16: the table
+  // parts use their first 8 KB; data halves of 64 columns are 64 hi rows over
+  // 64 lo rows, 16 KB (TF32) or 8 KB (BF16) each)
   unsigned char* st = base;
   uint64_t* bars = (uint64_t*)(st + kStagesRadI * 4 * kChunk);
   uint64_t* tfull = bars;                   // [S] table chunk landed
@@ -437,8 +476,10 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
         for (int kc = 0; kc < kcn; ++kc, ++c) {
           const int s = c % kStagesRadI;
           if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) { ok = false; break; }
-          mbar_arrive_tx(tfull + s, 2 * kChunk);
-          bulk_load(st + s * 4 * kChunk, a.tabimg + s_loff[l] + (int64_t)kc * 2 * kChunk, 2 * kChunk, tfull + s);
+          // hi and lo chunk of the image, contiguous; the lo part lands at +kChunk
+          mbar_arrive_tx(tfull + s, 2 * TCH);
+          bulk_load(st + s * 4 * kChunk, a.tabimg + s_loff[l] + (int64_t)kc * 2 * TCH, TCH, tfull + s);
+          bulk_load(st + s * 4 * kChunk + kChunk, a.tabimg + s_loff[l] + (int64_t)kc * 2 * TCH + TCH, TCH, tfull + s);
         }
         if (!ok) break;
       }
@@ -449,10 +490,11 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     if (lane == 0) {
       const int me = warp == 1 ? 0 : 1;
       uint32_t c = 0, tcount = 0;
-      const uint64_t sdesc0 = sw128_desc(smem_u32(st));
+      const uint64_t sdesc0 = BF ? sw64_desc(smem_u32(st)) : sw128_desc(smem_u32(st));
       // B operand of each half: 64 hi rows over 64 lo rows.  One MMA of width
       // 128 gives [T_hi X_hi | T_hi X_lo], a second of width 64 adds T_lo X_hi.
-      const uint32_t idesc2 = idesc_tf32(128), idesc1 = idesc_tf32(64);
+      const uint32_t idesc2 = BF ? idesc_bf16(128) : idesc_tf32(128);
+      const uint32_t idesc1 = BF ? idesc_bf16(64) : idesc_tf32(64);
       for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
         const int2 tl = s_tiles[t];
         const int l = tl.x;
@@ -475,8 +517,19 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
           tc_after();
           const uint64_t ah = sdesc0 + (uint64_t)((s * 4 * kChunk) >> 4);
           const uint64_t al = ah + (uint64_t)(kChunk >> 4);
-          const uint64_t bh = al + (uint64_t)(kChunk >> 4) + (nar ? 0u : (uint64_t)(me * (128 * 128 >> 4)));
-          if (a.nprod == 1) {  // hi*hi only: the B operand's hi rows, main accumulator
+          const uint64_t bh = al + (uint64_t)(kChunk >> 4) + (nar ? 0u : (uint64_t)(me * (128 * ROWB >> 4)));
+          if (BF) {  // two K steps of 16: narrow, one per issuer; wide, both
+            if (nar) {
+              mma_bf16(dm, ah + 2 * me, bh + 2 * me, idesc2, kc > 0 ? 1u : 0u);
+              mma_bf16(dc, al + 2 * me, bh + 2 * me, idesc1, 1u);
+            } else {
+#pragma unroll
+              for (int kk = 0; kk < 2; ++kk) {
+                mma_bf16(dm, ah + 2 * kk, bh + 2 * kk, idesc2, (kc > 0 || kk > 0) ? 1u : 0u);
+                mma_bf16(dc, al + 2 * kk, bh + 2 * kk, idesc1, 1u);
+              }
+            }
+          } else if (a.nprod == 1) {  // hi*hi only: the B operand's hi rows, main accumulator
             if (nar) {
               mma_tf32(dm, ah + 2 * me, bh + 2 * me, idesc1, kc > 0 ? 1u : 0u);
               mma_tf32(dm, ah + 2 * me + 4, bh + 2 * me + 4, idesc1, 1u);
@@ -526,11 +579,18 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) break;
       // B operand: per half of 64 columns, 64 hi rows then 64 lo rows
       unsigned char* sb = st + s * 4 * kChunk + 2 * kChunk;
-      if (nar) {
-        split_store<2>(sb, sb + 64 * 128, tid & 63, v, 2 * (tid >> 6), a.nprod == 3);
+      if (BF) {
+        if (nar) {
+          split_store_bf<2>(sb, sb + 64 * ROWB, tid & 63, v, 2 * (tid >> 6));
+        } else {
+          unsigned char* hb = sb + ((tid >> 6) & 1) * (128 * ROWB);
+          split_store_bf<4>(hb, hb + 64 * ROWB, tid & 63, v, 4 * (tid >> 7));
+        }
+      } else if (nar) {
+        split_store<2>(sb, sb + 64 * ROWB, tid & 63, v, 2 * (tid >> 6), a.nprod == 3);
       } else {
-        unsigned char* hb = sb + ((tid >> 6) & 1) * (128 * 128);
-        split_store<4>(hb, hb + 64 * 128, tid & 63, v, 4 * (tid >> 7), a.nprod == 3);
+        unsigned char* hb = sb + ((tid >> 6) & 1) * (128 * ROWB);
+        split_store<4>(hb, hb + 64 * ROWB, tid & 63, v, 4 * (tid >> 7), a.nprod == 3);
       }
       fence_proxy_async();
       mbar_arrive(split + s);
@@ -638,6 +698,35 @@ void append_planes(std::vector<unsigned char>& img, int rows, int K, int KC, F v
     }
 }
 
+uint16_t bf16_rn_bits(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+
+// BF16 form of append_planes: per chunk the hi rows, then the lo rows, each
+// row 32 values in 64 bytes with the 64-byte swizzle.
+template <typename F>
+void append_planes_bf16(std::vector<unsigned char>& img, int rows, int K, int KC, F value) {
+  const size_t off = img.size();
+  const size_t plane = (size_t)rows * 64;
+  img.resize(off + 2 * (size_t)KC * plane, 0);
+  for (int r = 0; r < rows; ++r)
+    for (int k = 0; k < K; ++k) {
+      const double v = value(r, k);
+      if (v == 0.0) continue;
+      const uint16_t hb = bf16_rn_bits((float)v);
+      const uint32_t hu = (uint32_t)hb << 16;
+      float hi;
+      memcpy(&hi, &hu, 4);
+      const uint16_t lb = bf16_rn_bits((float)(v - (double)hi));
+      const int kc = k / 32, kin = k % 32;
+      const size_t pos = (size_t)kc * 2 * plane + (size_t)r * 64 + (size_t)((((kin >> 3) ^ ((r >> 1) & 3)) << 4) + (kin & 7) * 2);
+      memcpy(&img[off + pos], &hb, 2);
+      memcpy(&img[off + plane + pos], &lb, 2);
+    }
+}
+
 int pad16i(int n) { return n <= 16 ? 16 : (n + 15) / 16 * 16; }
 
 }  // namespace
@@ -738,6 +827,7 @@ cudaError_t tc_inv_prepare(Plan& P) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   TcInvState* st = new TcInvState();
+  const bool bf = tc_bf16(P.prec);
   std::vector<unsigned char> img;
   std::vector<std::vector<int64_t>> am_offs, l_offs;
   std::vector<std::vector<int>> am_kcs;
@@ -764,12 +854,14 @@ cudaError_t tc_inv_prepare(Plan& P) {
         aoff[2 * am + jh] = (int64_t)img.size();
         for (int p = 0; p < 2; ++p) {
           if (kcs[p] == 0) continue;
-          append_planes(img, nh, n_par(B, am, p), kcs[p], [&](int jr, int q) -> double {
+          auto lam = [&](int jr, int q) -> double {
             const int j = 64 * jh + jr;
             if (j >= B) return 0.0;
             const int l = am + p + 2 * q;
             return H.lam[((size_t)am * B + l) * B + j];
-          });
+          };
+          if (bf) append_planes_bf16(img, nh, n_par(B, am, p), kcs[p], lam);
+          else append_planes(img, nh, n_par(B, am, p), kcs[p], lam);
         }
       }
       akc[am] = kcs[0] | (kcs[1] << 8);
@@ -795,12 +887,15 @@ cudaError_t tc_inv_prepare(Plan& P) {
       img.resize((img.size() + 1023) / 1024 * 1024);
       loff[l] = (int64_t)img.size();
       const int K = B - l, KC = (K + 31) / 32;
-      for (int kc = 0; kc < KC; ++kc)
-        append_planes(img, 128, 32, 1, [&](int i, int k) -> double {
+      for (int kc = 0; kc < KC; ++kc) {
+        auto tv = [&](int i, int k) -> double {
           const int np = kc * 32 + k;
           if (i >= B || np >= K) return 0.0;
           return H.T[((size_t)l * B + (l + np)) * B + i];
-        });
+        };
+        if (bf) append_planes_bf16(img, 128, 32, 1, tv);
+        else append_planes(img, 128, 32, 1, tv);
+      }
     }
     // tensor map over S: [B^2 rows of l'][NB*2*B]
     float* w2 = (float*)P.d_w2 + sg.w2_off;
@@ -835,7 +930,7 @@ cudaError_t tc_inv_prepare(Plan& P) {
     // image offsets, chunk counts), tile slice
     const size_t meta = (size_t)2 * (2 * B - 1) * 8 + (size_t)B * 12 + 8;
     const int nh_s = ts.npad > 64 ? 64 : ts.npad;
-    ts.leg_smem = 1024 + (size_t)ts.kcmax * 2 * nh_s * 128 + (size_t)kStagingLegI * kChunk +
+    ts.leg_smem = 1024 + (size_t)ts.kcmax * 2 * nh_s * (bf ? 64 : 128) + (size_t)kStagingLegI * kChunk +
                   (size_t)kStagesLegI * 2 * kChunk + 64 * 8 + meta + (size_t)B * 8 + (size_t)lmax * 8;
     if (ts.leg_smem > 227 * 1024) e = cudaErrorInvalidValue;
   }
@@ -885,9 +980,10 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
       a.B = sg.B;
       a.NB = sg.NB;
       a.nprod = tc_products(P.prec);
-      e = cudaFuncSetAttribute(tc_rad_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.rad_smem);
+      void (*fn)(RadIArgs) = tc_bf16(P.prec) ? tc_rad_inv_kernel<true> : tc_rad_inv_kernel<false>;
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.rad_smem);
       if (e != cudaSuccess) return e;
-      tc_rad_inv_kernel<<<ts.rad_grid, kThreadsInv, ts.rad_smem, s>>>(a);
+      fn<<<ts.rad_grid, kThreadsInv, ts.rad_smem, s>>>(a);
     } else {
       LegIArgs a;
       a.tiles = ts.leg_tiles;
@@ -904,9 +1000,10 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
       a.npad = ts.npad;
       a.kcmax = ts.kcmax;
       a.nprod = tc_products(P.prec);
-      e = cudaFuncSetAttribute(tc_leg_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.leg_smem);
+      void (*fn)(const CUtensorMap, LegIArgs) = tc_bf16(P.prec) ? tc_leg_inv_kernel<true> : tc_leg_inv_kernel<false>;
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.leg_smem);
       if (e != cudaSuccess) return e;
-      tc_leg_inv_kernel<<<ts.leg_grid, kThreadsInv, ts.leg_smem, s>>>(ts.smap, a);
+      fn<<<ts.leg_grid, kThreadsInv, ts.leg_smem, s>>>(ts.smap, a);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -204,6 +204,47 @@ static __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// K-major, 64-byte swizzled operand (rows of 64 bytes, the BF16 operands):
+// 8-row groups 512 B apart.
+static __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);       // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;               // stride byte offset
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)4 << 61;                        // 64-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, M = 128.
+static __device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+static __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Split x into BF16 hi = RN(x) and lo = RN(x - hi) (round to nearest even);
+// returns hi in the low and lo in the high half-word.
+static __device__ __forceinline__ uint32_t bf16_split(float x) {
+  uint32_t u = __float_as_uint(x);
+  const uint32_t hb = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+  const float r = x - __uint_as_float(hb << 16);
+  u = __float_as_uint(r);
+  const uint32_t lb = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+  return hb | (lb << 16);
+}
+
+// 128-byte swizzled (TF32 rows) and 64-byte swizzled (BF16 rows) byte
+// offsets of 16-byte chunk q of row r in a K-major tile.
+static __device__ __forceinline__ int sw128_off(int r, int q) { return r * 128 + ((q ^ (r & 7)) << 4); }
+static __device__ __forceinline__ int sw64_off(int r, int q) { return r * 64 + ((q ^ ((r >> 1) & 3)) << 4); }
+
 // kind::tf32 instruction descriptor: D f32, A and B tf32, both K-major, M = 128.
 static __device__ __forceinline__ uint32_t idesc_tf32(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);

@@ -23,11 +23,11 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsgl.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "sgl.h")
 
 SGL_OK, SGL_ERR_ARG, SGL_ERR_ALLOC, SGL_ERR_CUDA, SGL_ERR_TIMEOUT, SGL_ERR_UNSUPPORTED = range(6)
-SGL_FP64, SGL_FP32, SGL_TF32X3, SGL_TF32 = 0, 1, 2, 3
+SGL_FP64, SGL_FP32, SGL_TF32X3, SGL_TF32, SGL_BF16X3 = 0, 1, 2, 3, 4
 SGL_SAMPLES_WEIGHTED, SGL_SAMPLES_PHYSICAL = 0, 1
 SGL_MAX_B = 128
 
-PRECISIONS = {"fp64": SGL_FP64, "fp32": SGL_FP32, "tf32x3": SGL_TF32X3, "tf32": SGL_TF32}
+PRECISIONS = {"fp64": SGL_FP64, "fp32": SGL_FP32, "tf32x3": SGL_TF32X3, "tf32": SGL_TF32, "bf16x3": SGL_BF16X3}
 STATUS_NAMES = {0: "SGL_OK", 1: "SGL_ERR_ARG", 2: "SGL_ERR_ALLOC", 3: "SGL_ERR_CUDA",
                 4: "SGL_ERR_TIMEOUT", 5: "SGL_ERR_UNSUPPORTED"}
 

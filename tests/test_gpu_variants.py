@@ -1,4 +1,5 @@
-"""Reduced-precision variant of the tensor-core path: SGL_TF32 (hi*hi only).
+"""Reduced-precision variants of the tensor-core path: SGL_TF32 (hi*hi only)
+and SGL_BF16X3 (BF16 hi/lo pairs, three products).
 
 Every input and table entry is rounded to TF32 (unit round-off u = 2^-11) and
 multiplied once, so each stage carries a relative error of up to 2u ~ 1e-3 of
@@ -6,6 +7,11 @@ its terms; four chained stages (inverse then forward) give the bound
 TF32_TOL = 4 * 2u = 3.9e-3 on the normwise error, doubled for the forward of
 arbitrary samples, whose sums cancel more.  The test also checks that the
 variant is indeed coarser than SGL_TF32X3 (the products really are dropped).
+
+SGL_BF16X3 represents every input and table entry as hi + lo with 8 + 8
+significant bits (representation error <= 2^-17 relative, the dropped lo*lo
+product <= 2^-18), so each stage carries up to ~2^-16 of its terms; four
+stages and a factor 2 for cancellation give BF16X3_TOL = 8 * 2^-16 = 1.2e-4.
 """
 import numpy as np
 import pytest
@@ -18,6 +24,7 @@ pytestmark = pytest.mark.gpu
 
 U = 2.0 ** -11
 TF32_TOL = 4 * 2 * U
+BF16X3_TOL = 8 * 2.0 ** -16
 
 
 def _err(gpu, ref):
@@ -60,4 +67,48 @@ def test_tf32_full_size_round_trip():
     assert _err(f, c) < TF32_TOL
     sk = s[0].cpu().numpy()
     assert _err(sk[None], O.inverse(c[0], B)) < TF32_TOL
+    p.check()
+
+
+@pytest.mark.parametrize("B", [8, 32, 64])
+def test_bf16x3_vs_oracle(B):
+    from paper_1604_05140_gb300 import Plan
+    p = Plan(B, 2, "bf16x3")
+    c = inputs.random_coeffs(B, 2, seed=7500 + B)
+    s_gpu = p.inverse(_dev(c)).cpu().numpy()
+    assert _err(s_gpu, O.inverse(c, B)) < BF16X3_TOL
+    g = inputs.random_samples(B, 2, seed=7600 + B)
+    assert _err(p.forward(_dev(g)).cpu().numpy(), O.forward(g.astype(np.complex64), B)) < 2 * BF16X3_TOL
+    e_rt = _err(p.forward(_dev(O.inverse(c, B))).cpu().numpy(), c)
+    assert e_rt < BF16X3_TOL
+    p.check()
+
+
+def test_bf16x3_adjoint_and_uneven():
+    from paper_1604_05140_gb300 import Plan
+    B = 16
+    p = Plan(B, 2, "bf16x3")
+    y = inputs.random_coeffs(B, 2, seed=9300)
+    a1 = p.adjoint(_dev(y), of_inverse=False).cpu().numpy()
+    assert _err(a1, O.adjoint_forward(y, B)) < BF16X3_TOL
+    Bs = [16, 40, 8, 64]
+    q = Plan.many(Bs, precision="bf16x3")
+    cs = [inputs.random_coeffs(b, 1, seed=960 + k)[0] for k, b in enumerate(Bs)]
+    f = q.forward(q.inverse(_dev(np.concatenate(cs)))).cpu().numpy()
+    for k, b in enumerate(Bs):
+        co = q.coeff_offset(k)
+        assert _err(f[co:co + O.coeff_count(b)][None], cs[k][None]) < BF16X3_TOL, (k, b)
+    q.check()
+
+
+def test_bf16x3_full_size_round_trip():
+    from paper_1604_05140_gb300 import Plan
+    B, NB = 128, 64
+    p = Plan(B, NB, "bf16x3")
+    c = inputs.random_coeffs(B, NB, seed=inputs.BASE_SEED + 3, decay=True)
+    s = p.inverse(_dev(c))
+    f = p.forward(s).cpu().numpy()
+    assert _err(f, c) < BF16X3_TOL
+    sk = s[NB - 1].cpu().numpy()
+    assert _err(sk[None], O.inverse(c[NB - 1], B)) < BF16X3_TOL
     p.check()
