@@ -32,11 +32,14 @@
  *
  * Buffers: every data pointer may point to device memory or to host memory
  * (pinned or pageable); the library asks the CUDA driver which it is.  Host
- * buffers are staged through plan-owned device memory with copies on the
- * call's stream, and the call then synchronizes that stream before it
- * returns.  Device buffers are used in place and the call is asynchronous
- * (stream-ordered).  Inputs are never modified.  The caller owns all data
- * buffers; the plan owns its tables and workspace.
+ * buffers are staged through plan-owned device memory, and the call then
+ * synchronizes its stream before it returns; on single-bandlimit plans of
+ * 8 or more functions such a call runs in 4 chunks of functions, the copies
+ * of one chunk (on a stream of the plan) overlapping the kernels of the
+ * previous one (the first such call builds the chunk plans).  Device buffers
+ * are used in place and the call is asynchronous (stream-ordered).  Inputs
+ * are never modified.  The caller owns all data buffers; the plan owns its
+ * tables and workspace.
  *
  * Errors: argument errors are found before any work is queued and returned
  * as SGL_ERR_ARG.  CUDA launch errors are returned as SGL_ERR_CUDA.  A

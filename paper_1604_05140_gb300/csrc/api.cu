@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -56,14 +57,18 @@ static void clear_profile(Plan& P) {
   }
 }
 
+static void release_pipeline(Plan* P);
+
 static void release(Plan* P) {
   if (!P) return;
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(P->device);
+  release_pipeline(P);
   clear_profile(*P);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
   tc_release(*P);
+  if (!P->owns_err) P->d_err = nullptr;
   void* ptrs[] = {P->d_tab, P->d_tab_lo, P->d_w1, P->d_w2, P->d_stage_in, P->d_stage_out, P->d_segs,
                   P->d_fn_samp, P->d_fn_coef, P->d_si_rows, P->d_err, P->leg_fwd.d_tiles, P->rad_fwd.d_tiles,
                   P->rad_inv.d_tiles, P->leg_inv.d_tiles, P->d_fft_fwd, P->d_fft_inv};
@@ -71,6 +76,31 @@ static void release(Plan* P) {
     if (p) cudaFree(p);
   cudaSetDevice(cur);
   delete P;
+}
+
+static void release_pipeline(Plan* P) {
+  if (P->sub) release(P->sub);
+  if (P->sub_tail) release(P->sub_tail);
+  P->sub = P->sub_tail = nullptr;
+  for (cudaEvent_t e : P->pipe_ev) cudaEventDestroy(e);
+  P->pipe_ev.clear();
+  if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
+  P->copy_stream = nullptr;
+}
+
+// Host tables depend on the bandlimit only; built once per process.
+static bool cached_tables(int B, HostTables& out, std::string& msg) {
+  static std::mutex mu;
+  static std::map<int, HostTables> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(B);
+  if (it == cache.end()) {
+    HostTables H;
+    if (!build_tables(B, H, msg)) return false;
+    it = cache.emplace(B, std::move(H)).first;
+  }
+  out = it->second;
+  return true;
 }
 
 template <typename real>
@@ -218,7 +248,7 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
       for (int p = 0; p < 2; ++p) si_rows.push_back(si_rows_before(sg.B, mi, p));
     HostTables H;
     std::string msg;
-    if (!build_tables(sg.B, H, msg)) return fail(P, SGL_ERR_ARG, "table generation: " + msg);
+    if (!cached_tables(sg.B, H, msg)) return fail(P, SGL_ERR_ARG, "table generation: " + msg);
     P->tables.push_back(std::move(H));
     P->segs.push_back(sg);
   }
@@ -334,6 +364,107 @@ static sgl_status ensure_stage(Plan& P, void** buf, size_t* have, size_t need) {
   return SGL_OK;
 }
 
+// ---------------------------------------------------------------------------
+// host-buffer calls in sub-batches: the copies of one chunk of functions
+// overlap the kernels of the previous chunk
+// ---------------------------------------------------------------------------
+constexpr int kPipeChunks = 4;   // chunks of one call
+constexpr int kPipeMinFunctions = 8;
+
+static sgl_status ensure_pipeline(Plan* P) {
+  if (P->sub) return SGL_OK;
+  const int NB = P->nfn, B = P->fn_B[0];
+  const int q = (NB + kPipeChunks - 1) / kPipeChunks;
+  const int nchunks = (NB + q - 1) / q;
+  const int r = NB - (nchunks - 1) * q;
+  auto make = [&](int n, Plan** out) -> sgl_status {
+    Plan* S = new Plan();
+    S->prec = P->prec;
+    S->samples = P->samples;
+    S->jp_fwd = P->jp_fwd;
+    S->jp_inv = P->jp_inv;
+    S->radi_narrow = P->radi_narrow;
+    const sgl_status st = build_plan(S, std::vector<int>(n, B), true);
+    if (st != SGL_OK) {
+      const std::string m = S->err;
+      release(S);
+      return fail(P, st, "sub-batch plan: " + m);
+    }
+    cudaFree(S->d_err);  // the parent's flag collects device-side errors
+    S->d_err = P->d_err;
+    S->owns_err = false;
+    *out = S;
+    return SGL_OK;
+  };
+  sgl_status st = make(q, &P->sub);
+  if (st == SGL_OK && r != q) st = make(r, &P->sub_tail);
+  if (st == SGL_OK && cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    st = fail(P, SGL_ERR_CUDA, "copy stream creation failed");
+  for (int k = 0; st == SGL_OK && k < 2 * nchunks + 2; ++k) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      st = fail(P, SGL_ERR_CUDA, "event creation failed");
+    else
+      P->pipe_ev.push_back(ev);
+  }
+  if (st != SGL_OK) {
+    release_pipeline(P);
+    return st;
+  }
+  P->sub_q = q;
+  return SGL_OK;
+}
+
+static sgl_status execute_pipelined(Plan* P, bool is_fwd, bool weights, const void* in, void* out, bool in_dev,
+                                    bool out_dev, cudaStream_t s) {
+  sgl_status st = ensure_pipeline(P);
+  if (st != SGL_OK) return st;
+  const size_t cb = complex_bytes(*P);
+  const int B = P->fn_B[0];
+  const size_t in_per = (size_t)(is_fwd ? sample_count(B) : coeff_count(B)) * cb;   // bytes per function
+  const size_t out_per = (size_t)(is_fwd ? coeff_count(B) : sample_count(B)) * cb;
+  const char* din = (const char*)in;
+  char* dout = (char*)out;
+  if (!in_dev) {
+    st = ensure_stage(*P, &P->d_stage_in, &P->stage_in_bytes, P->nfn * in_per);
+    if (st != SGL_OK) return st;
+    din = (const char*)P->d_stage_in;
+  }
+  if (!out_dev) {
+    st = ensure_stage(*P, &P->d_stage_out, &P->stage_out_bytes, P->nfn * out_per);
+    if (st != SGL_OK) return st;
+    dout = (char*)P->d_stage_out;
+  }
+  const int q = P->sub_q, n = (P->nfn + q - 1) / q;
+  cudaEvent_t* ev = P->pipe_ev.data();  // [0] start, [1] end, then in/out per chunk
+  cudaError_t e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_stream, ev[0], 0);
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    const int f0 = k * q, nk = std::min(q, P->nfn - f0);
+    Plan* S = nk == q ? P->sub : P->sub_tail;
+    const size_t io = (size_t)f0 * in_per, oo = (size_t)f0 * out_per;
+    if (!in_dev) {
+      e = cudaMemcpyAsync((void*)(din + io), (const char*)in + io, (size_t)nk * in_per, cudaMemcpyHostToDevice,
+                          P->copy_stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[2 + 2 * k], P->copy_stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[2 + 2 * k], 0);
+    }
+    if (e == cudaSuccess)
+      e = is_fwd ? run_forward(*S, din + io, dout + oo, s, weights) : run_inverse(*S, din + io, dout + oo, s, weights);
+    if (e == cudaSuccess && !out_dev) {
+      e = cudaEventRecord(ev[3 + 2 * k], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_stream, ev[3 + 2 * k], 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char*)out + oo, dout + oo, (size_t)nk * out_per, cudaMemcpyDeviceToHost, P->copy_stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], P->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(P, e, "sub-batch execution");
+  return SGL_OK;
+}
+
 // Runs fwd (is_fwd) or inv with in/out that may be host or device memory.
 static sgl_status execute(Plan* P, bool is_fwd, bool weights, const void* in, void* out, sgl_stream_t stream) {
   if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
@@ -351,6 +482,10 @@ static sgl_status execute(Plan* P, bool is_fwd, bool weights, const void* in, vo
   void* dout = out;
   sgl_status st = SGL_OK;
   cudaError_t e = cudaSuccess;
+  if ((!in_dev || !out_dev) && P->uniform && P->nfn >= kPipeMinFunctions) {
+    st = execute_pipelined(P, is_fwd, weights, in, out, in_dev, out_dev, s);
+    goto done;
+  }
   if (!in_dev) {
     st = ensure_stage(*P, &P->d_stage_in, &P->stage_in_bytes, in_bytes);
     if (st != SGL_OK) goto done;
@@ -491,6 +626,7 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
   if (e == cudaSuccess && tc_precision(P->prec)) e = tc_radi_retile(*P);
   if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
   P->tuning = tuning_text(*P, cached ? "cache" : "timed");
+  release_pipeline(P);  // sub-batch plans are rebuilt with the new configuration on next use
   if (!cached && cache_path) {
     FILE* f = fopen(cache_path, "a");
     if (!f) return fail(P, SGL_ERR_ARG, std::string("cannot append to tuning cache ") + cache_path);
@@ -612,7 +748,11 @@ int sgl_bandlimit(sgl_plan_t plan, int fn) {
   return P->fn_B[fn];
 }
 
-int64_t sgl_workspace_bytes(sgl_plan_t plan) { return plan ? ((Plan*)plan)->bytes : -1; }
+int64_t sgl_workspace_bytes(sgl_plan_t plan) {
+  if (!plan) return -1;
+  const Plan* P = (const Plan*)plan;
+  return P->bytes + (P->sub ? P->sub->bytes : 0) + (P->sub_tail ? P->sub_tail->bytes : 0);
+}
 
 int sgl_launches_per_call(sgl_plan_t plan) { return plan ? ((Plan*)plan)->launches_per_call : -1; }
 

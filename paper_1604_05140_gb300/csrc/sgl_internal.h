@@ -192,6 +192,17 @@ struct Plan {
   int radi_narrow = 65;
   std::string tuning;
 
+  // calls with host buffers on single-bandlimit plans run in sub-batches so
+  // that the copies overlap the kernels (api.cu): a plan of sub_q functions
+  // used for every chunk, one for a shorter last chunk, a copy stream and
+  // its events.  Sub-plans share the parent's error flag.
+  Plan* sub = nullptr;
+  Plan* sub_tail = nullptr;
+  int sub_q = 0;
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> pipe_ev;
+  bool owns_err = true;
+
   // stage timing (sgl_set_profiling): event pairs per stage, and a free pool
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[SGL_NUM_STAGES];

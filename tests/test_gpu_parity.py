@@ -161,6 +161,28 @@ def test_host_buffers_match_device_buffers():
     assert torch.equal(f_host, f_dev)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_host_buffers_in_sub_batches_match_device_buffers(prec):
+    # 10 functions: host-buffer calls run in chunks of 3, 3, 3 and 1 function
+    # with the copies of one chunk overlapping the kernels of the previous one;
+    # every function's arithmetic is the same as in the whole-batch launch
+    B, NB = 16, 10
+    p = _plan(B, NB, prec)
+    dt = p.dtype
+    c = inputs.random_coeffs(B, NB, seed=78)
+    s_dev = p.inverse(_dev(c, dt))
+    s_pin = p.inverse(torch.from_numpy(c).to(dt).pin_memory())
+    assert not s_pin.is_cuda and torch.equal(s_pin, s_dev.cpu())
+    f_dev = p.forward(s_dev)
+    f_host = p.forward(s_pin)                       # host in, host out
+    f_mixed = p.forward(s_dev, out=torch.empty(p.coeff_shape, dtype=dt).pin_memory())  # device in, host out
+    assert torch.equal(f_host, f_dev.cpu()) and torch.equal(f_mixed, f_dev.cpu())
+    a_dev = p.adjoint(f_dev, of_inverse=False)
+    a_host = p.adjoint(f_dev.cpu().pin_memory(), of_inverse=False)
+    assert torch.equal(a_host, a_dev.cpu())
+    p.check()
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
 def test_uneven_bandlimits_plan(prec, tol):
     from paper_1604_05140_gb300 import Plan
