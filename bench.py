@@ -282,6 +282,54 @@ def time_path(precision, steps, warmup, ws, rank, profile=True):
     return plan, ms, stage, clocks, err, launches, (c_np, c, s, c2)
 
 
+def uneven_path(steps, warmup):
+    """The batching workload: 256 functions with bandlimits uniform in
+    {16, 24, ..., 128} in one TF32x3 plan, round trip captured in one CUDA
+    graph and replayed; per-function error against the input coefficients."""
+    import torch
+    from paper_1604_05140_gb300 import Plan, inputs
+    Bs = [int(b) for b in inputs.uneven_bandlimits(256)]
+    plan = Plan.many(Bs, precision="tf32x3")
+    if TUNE:
+        plan.autotune()
+    cs = [inputs.random_coeffs(B, 1, seed=inputs.BASE_SEED + 4 + 10 * k)[0] for k, B in enumerate(Bs)]
+    c = torch.from_numpy(np.concatenate(cs)).to(torch.complex64).cuda()
+    s = torch.empty(plan.sample_shape, dtype=plan.dtype, device="cuda")
+    out = torch.empty(plan.coeff_shape, dtype=plan.dtype, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(max(1, warmup)):
+            plan.inverse(c, out=s)
+            plan.forward(s, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.inverse(c, out=s)
+        plan.forward(s, out=out)
+    g.replay()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        g.replay()
+    ev1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    ms = ev0.elapsed_time(ev1) / steps
+    f = out.cpu().numpy()
+    err = 0.0
+    for k, B in enumerate(Bs):
+        co = plan.coeff_offset(k)
+        fk = f[co:co + len(cs[k])]
+        err = max(err, float(np.abs(fk - cs[k]).max() / np.abs(cs[k]).max()))
+    return {"workload": "256 functions, B uniform in {16, 24, ..., 128}, TF32x3, one CUDA graph per round trip",
+            "value": len(Bs) / (ms * 1e-3), "unit": "transforms/s", "ms_per_step": ms, "steps": steps,
+            "segments": len(set(Bs)), "launches_per_round_trip": 2 * plan.launches_per_call,
+            "max_rel_err": err, "launch_config": plan.tuning}
+
+
 def e2e_path(plan, c_np, steps, warmup):
     """Same step through the C ABI with host buffers: pinned host coefficients
     in, pinned host coefficients out; the library stages the copies."""
@@ -369,7 +417,7 @@ def run_ours(args):
     cbytes = 16 if args.precision == "fp64" else 8
     value = head["value"]
     rl = roofline(head["stage"], cbytes, args.precision)
-    e2e_dt, nbytes = e2e_path(plan, head["bufs"][0], max(2, min(args.steps, 5)), 1)
+    e2e_dt, nbytes = e2e_path(plan, head["bufs"][0], max(3, min(args.steps, 10)), 2)
     e2e_value, _ = whole_job(ws, BATCH, e2e_dt * 1e3)
     line = {
         "metric": METRIC,
@@ -408,6 +456,8 @@ def run_ours(args):
                                     "round_trip_max_rel_err": v_err,
                                     "stage_ms": {k: v[0] for k, v in v_stage.items()}}
             del v_plan
+    if not args.no_variants and args.precision == "tf32x3" and ws == 1:
+        line["uneven_batch"] = uneven_path(max(3, min(args.steps, 20)), args.warmup)
     if "fp64" in results and args.precision != "fp64":
         r = results["fp64"]
         line["fp64_path"] = {"value": r["value"], "unit": "transforms/s", "ms_per_step": r["ms"],

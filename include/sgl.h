@@ -34,7 +34,7 @@
  * (pinned or pageable); the library asks the CUDA driver which it is.  Host
  * buffers are staged through plan-owned device memory, and the call then
  * synchronizes its stream before it returns; on single-bandlimit plans of
- * 8 or more functions such a call runs in 4 chunks of functions, the copies
+ * 16 or more functions such a call runs in 8 chunks of functions, the copies
  * of one chunk (on a stream of the plan) overlapping the kernels of the
  * previous one (the first such call builds the chunk plans).  Device buffers
  * are used in place and the call is asynchronous (stream-ordered).  Inputs

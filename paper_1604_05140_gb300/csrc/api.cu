@@ -368,8 +368,8 @@ static sgl_status ensure_stage(Plan& P, void** buf, size_t* have, size_t need) {
 // host-buffer calls in sub-batches: the copies of one chunk of functions
 // overlap the kernels of the previous chunk
 // ---------------------------------------------------------------------------
-constexpr int kPipeChunks = 4;   // chunks of one call
-constexpr int kPipeMinFunctions = 8;
+constexpr int kPipeChunks = 8;   // chunks of one call
+constexpr int kPipeMinFunctions = 16;
 
 static sgl_status ensure_pipeline(Plan* P) {
   if (P->sub) return SGL_OK;

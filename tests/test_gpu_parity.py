@@ -163,10 +163,11 @@ def test_host_buffers_match_device_buffers():
 
 @pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
 def test_host_buffers_in_sub_batches_match_device_buffers(prec):
-    # 10 functions: host-buffer calls run in chunks of 3, 3, 3 and 1 function
-    # with the copies of one chunk overlapping the kernels of the previous one;
-    # every function's arithmetic is the same as in the whole-batch launch
-    B, NB = 16, 10
+    # 17 functions: host-buffer calls run in chunks of 3 functions and a last
+    # chunk of 2, the copies of one chunk overlapping the kernels of the
+    # previous one; every function's arithmetic is the same as in the
+    # whole-batch launch
+    B, NB = 16, 17
     p = _plan(B, NB, prec)
     dt = p.dtype
     c = inputs.random_coeffs(B, NB, seed=78)
