@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "sgl_internal.h"
@@ -84,20 +85,37 @@ constexpr int kThreads = tcx::kRoleThreads;
 using namespace tcx;
 }  // namespace
 
+// One bandlimit segment of a launch; a launch covers every segment of the
+// plan (the tiles carry their segment).  Aligned as its tensor map.
+struct TcSegInfo {
+  CUtensorMap xmap;             // the segment's stage input, [rows][B] floats
+  int B, NB, KC, fn0;           // bandlimit, functions, K chunks, first function in fn_coef
+  int64_t w2_off;               // the segment's S_f block (forward Legendre output)
+  int g0;                       // the segment's first group in the launch's group list
+};
+
+// per-segment values the roles read per tile, staged in shared memory
+struct SegSmall {
+  int B, NB, KC, fn0;
+  int64_t w2_off;
+  int g0, pad;
+};
+
 struct TcArgs {
-  const int2* tiles;            // (group, row0) in group order
+  const int2* tiles;            // (group | segment << 20, row0), groups in order
   const int* cta_first;         // tile slice of each CTA (gridDim.x + 1 offsets)
   int ntiles;
   const unsigned char* tabimg;  // pre-swizzled hi/lo tables
   const int64_t* grp_off;       // byte offset of each group's image (weighted set, then plain set)
   const int* grp_npad;          // padded N of each group | l << 8 | n0 << 16 (radial)
   int ngroups;
+  const TcSegInfo* segs;        // [nseg]
+  int nseg;
   void* y;
   const int64_t* fn_coef;
   int* err;
-  int B, NB, KC;
+  int KCmax;                    // largest K chunk count over the segments
   int weighted;
-  int64_t w2_off;
   int npmax;
   int nprod;                    // TF32 products per K step: 3 (hi*hi + hi*lo + lo*hi) or 1 (hi*hi)
 };
@@ -105,12 +123,11 @@ struct TcArgs {
 // BF: BF16 hi/lo operands (kind::f16, 64-byte rows, K = 16 per MMA) instead
 // of TF32 (kind::tf32, 128-byte rows, K = 8 per MMA).
 template <int PROB, int STAGES, bool BF>
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap xmap, TcArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int KC = a.KC;
-  const int tab_bytes = 2 * KC * a.npmax * ROWB;           // hi + lo for the largest group
+  const int tab_bytes = 2 * a.KCmax * a.npmax * ROWB;      // hi + lo for the largest group
   unsigned char* tab = base;                                 // [hi: KC][npad][128 B] [lo: same]
   unsigned char* xs = base + tab_bytes;                      // STAGES x (hi 16 KB, lo 16 KB)
   uint64_t* bars = (uint64_t*)(xs + STAGES * 2 * kChunkBytes);
@@ -123,11 +140,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   uint64_t* tabe = tabf + 1;             // table no longer read
   uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  // per-CTA copies of the tile slice and of the group metadata, so that no
-  // role waits on a global load per tile
-  int64_t* s_off = (int64_t*)(bars + 64);                 // [ngroups] table image offsets
-  int* s_npad = (int*)(s_off + a.ngroups);                 // [ngroups] padded N (| l, n0 for radial)
-  int2* s_tiles = (int2*)(((uintptr_t)(s_npad + a.ngroups) + 7) & ~(uintptr_t)7);  // [max_tiles]
+  // per-CTA copies of the tile slice, of the segments and of the metadata of
+  // the groups the slice touches, so that no role waits on a global load per
+  // tile
+  const int g_begin = a.cta_first[blockIdx.x];
+  const int g_end = a.cta_first[blockIdx.x + 1];
+  const int t_begin = 0, t_end = g_end - g_begin;
+  const int g_lo = t_end > 0 ? (a.tiles[g_begin].x & 0xFFFFF) : 0;
+  const int ngr = t_end > 0 ? (a.tiles[g_end - 1].x & 0xFFFFF) - g_lo + 1 : 0;
+  SegSmall* s_seg = (SegSmall*)(bars + 64);                // [nseg]
+  int64_t* s_off = (int64_t*)(s_seg + a.nseg);              // [ngr] table image offsets
+  int* s_npad = (int*)(s_off + ngr);                        // [ngr] padded N (| l, n0 for radial)
+  int4* s_tiles = (int4*)(((uintptr_t)(s_npad + ngr) + 15) & ~(uintptr_t)15);  // [slice] (group, row0, segment)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Per tile two pairs of a main accumulator (hi*hi) and a correction
@@ -158,32 +182,42 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
-  // contiguous tile range of this CTA (re-based to 0 in shared memory)
-  const int g_begin = a.cta_first[blockIdx.x];
-  const int g_end = a.cta_first[blockIdx.x + 1];
-  const int t_begin = 0, t_end = g_end - g_begin;
+  // contiguous tile range of this CTA (re-based to 0 in shared memory), group
+  // indices re-based to g_lo
   const int64_t wsel = a.weighted ? 0 : a.ngroups;
-  for (int k = threadIdx.x; k < t_end; k += blockDim.x) s_tiles[k] = a.tiles[g_begin + k];
-  for (int k = threadIdx.x; k < a.ngroups; k += blockDim.x) {
-    s_off[k] = a.grp_off[wsel + k];
-    s_npad[k] = a.grp_npad[k];
+  for (int k = threadIdx.x; k < t_end; k += blockDim.x) {
+    const int2 tl = a.tiles[g_begin + k];
+    s_tiles[k] = make_int4((tl.x & 0xFFFFF) - g_lo, tl.y, tl.x >> 20, 0);
+  }
+  for (int k = threadIdx.x; k < ngr; k += blockDim.x) {
+    s_off[k] = a.grp_off[wsel + g_lo + k];
+    s_npad[k] = a.grp_npad[g_lo + k];
+  }
+  for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) {
+    const TcSegInfo& g = a.segs[k];
+    s_seg[k] = SegSmall{g.B, g.NB, g.KC, g.fn0, g.w2_off, g.g0, 0};
   }
   tc_before();
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
-  const int B = a.B, NB = a.NB;
 
   if (warp == 0) {
     // ---------------- producer ----------------
     if (lane == 0) {
-      int cur = -1, ngrp = 0;
+      int cur = -1, ngrp = 0, cur_seg = -1;
       uint32_t c = 0;
       for (int t = t_begin; t < t_end && !*abort_flag; ++t) {
-        const int2 tl = s_tiles[t];
+        const int4 tl = s_tiles[t];
+        const SegSmall sg = s_seg[tl.z];
+        const CUtensorMap* xmap = &a.segs[tl.z].xmap;
+        if (tl.z != cur_seg) {  // the tensor map lives in global memory
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(xmap) : "memory");
+          cur_seg = tl.z;
+        }
         if (tl.x != cur) {
           if (ngrp > 0 && !mbar_wait(tabe, (ngrp - 1) & 1, abort_flag)) break;
-          const uint32_t bytes = (uint32_t)(2 * KC * (s_npad[tl.x] & 0xff) * ROWB);
+          const uint32_t bytes = (uint32_t)(2 * sg.KC * (s_npad[tl.x] & 0xff) * ROWB);
           mbar_arrive_tx(tabf, bytes);
           bulk_load(tab, a.tabimg + s_off[tl.x], bytes, tabf);
           cur = tl.x;
@@ -192,16 +226,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         // tensor rows of this tile
         int64_t row;
         if (PROB == TC_LEG_F) {
-          row = (int64_t)tl.x * NB * 2 * B + tl.y;
+          row = (int64_t)(tl.x + g_lo - sg.g0) * sg.NB * 2 * sg.B + tl.y;
         } else {
           const int l = (s_npad[tl.x] >> 8) & 0xff;
-          row = (int64_t)NB * 2 * l * l + tl.y;
+          row = (int64_t)sg.NB * 2 * l * l + tl.y;
         }
-        for (int kc = 0; kc < KC; ++kc, ++c) {
+        for (int kc = 0; kc < sg.KC; ++kc, ++c) {
           const int s = c % STAGES;
           if (!mbar_wait(empty + s, ((c / STAGES) & 1) ^ 1, abort_flag)) break;
           mbar_arrive_tx(full + s, kChunkBytes);
-          tma_load_2d(xs + s * 2 * kChunkBytes, &xmap, full + s, kc * 32, (int)row);
+          tma_load_2d(xs + s * 2 * kChunkBytes, xmap, full + s, kc * 32, (int)row);
         }
       }
     }
@@ -216,7 +250,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const uint64_t xdesc0 = BF ? sw64_desc(smem_u32(xs + kChunkBytes)) : sw128_desc(smem_u32(xs));
       const uint64_t tdesc0 = BF ? sw64_desc(smem_u32(tab)) : sw128_desc(smem_u32(tab));
       for (int t = t_begin; t < t_end && !*abort_flag; ++t, ++tcount) {
-        const int2 tl = s_tiles[t];
+        const int4 tl = s_tiles[t];
+        const int KC = s_seg[tl.z].KC;
         if (tl.x != cur) {
           if (!mbar_wait(tabf, ngrp & 1, abort_flag)) break;
           cur = tl.x;
@@ -267,6 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     uint32_t c = 0;
     for (int t = t_begin; t < t_end; ++t) {
       bool ok = true;
+      const int KC = s_seg[s_tiles[t].z].KC;
       for (int kc = 0; kc < KC; ++kc, ++c) {
         const int s = c % STAGES;
         if (!mbar_wait(full + s, (c / STAGES) & 1, abort_flag)) { ok = false; break; }
@@ -316,7 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     uint32_t tcount = 0;
     float* Y = reinterpret_cast<float*>(a.y);
     for (int t = t_begin; t < t_end; ++t, ++tcount) {
-      const int2 tl = s_tiles[t];
+      const int4 tl = s_tiles[t];
+      const SegSmall sg = s_seg[tl.z];
+      const int B = sg.B, NB = sg.NB;
       const int acc = tcount & 1;
       if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
       tc_after();
@@ -325,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const uint32_t np = (uint32_t)npad;
       const int grow = tl.y + r_in;
       if (PROB == TC_LEG_F) {
-        const int g = tl.x;
+        const int g = tl.x + g_lo - sg.g0;  // group within the segment
         const int m_idx = g >> 1, p = g & 1;
         const int m = m_idx - (B - 1);
         const int am = m < 0 ? -m : m;
@@ -333,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const float sgn = (m < 0 && (am & 1)) ? -1.f : 1.f;
         const bool valid = grow < NB * 2 * B;
         const int b = grow / (2 * B), cc = (grow / B) & 1, i = grow % B;
-        const int64_t rbase = a.w2_off + (int64_t)cc * B + i;
+        const int64_t rbase = sg.w2_off + (int64_t)cc * B + i;
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
           const uint32_t tc = taddr + (uint32_t)c0;
@@ -369,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int rem = grow - b * per_b;
         const int mm = rem >> 1, cc = rem & 1;
         const int ncol = min(B - l - n0, kRadRows);
-        const int64_t cbase = valid ? a.fn_coef[b] : 0;
+        const int64_t cbase = valid ? a.fn_coef[sg.fn0 + b] : 0;
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
           const uint32_t tc = taddr + (uint32_t)c0;
@@ -416,26 +454,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 // ---------------------------------------------------------------------------
 namespace {
 
+// One stage (forward Legendre or forward radial) of every segment of the
+// plan, run as one launch.
 struct TcStage {
-  CUtensorMap xmap;
   int2* d_tiles = nullptr;
   int* d_first = nullptr;
   int ntiles = 0;
   int64_t* d_off = nullptr;
   int* d_npad = nullptr;
   int ngroups = 0;
-  int npmax = 0;
-  int KC = 0;
+  TcSegInfo* d_segs = nullptr;
+  int nseg = 0;
+  int npmax = 16;
+  int KCmax = 1;
   size_t smem = 0;
   int grid = 0;
 };
 
-struct TcSeg {
-  TcStage leg, rad;
-};
-
 struct TcState {
-  std::vector<TcSeg> segs;
+  TcStage leg, rad;
   unsigned char* d_img = nullptr;
 };
 
@@ -519,32 +556,37 @@ cudaError_t tc_prepare(Plan& P) {
   TcState* st = new TcState();
   const bool bf = tc_bf16(P.prec);
   std::vector<unsigned char> img;
+  // group lists of both stages over all segments: image offsets (weighted
+  // set, plain set), padded widths, tiles and their estimated cost
   struct Pending {
-    std::vector<int64_t> off;
+    std::vector<int64_t> off[2];
     std::vector<int> npad;
-    std::vector<int2> tiles;
+    std::vector<int2> tiles;   // (group | segment << 20, row0)
     std::vector<double> cost;  // estimated bytes moved per tile (slice balancing)
-  };
-  std::vector<Pending> pend;
+    std::vector<TcSegInfo> segs;
+  } pl, pr;
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
     const HostTables& H = P.tables[s];
     const int B = sg.B, NB = sg.NB;
     const int KC = (B + 31) / 32;
-    TcSeg ts;
+    float* w1 = (float*)P.d_w1 + sg.w1_off;
+    float* w2 = (float*)P.d_w2 + sg.w2_off;
     // Legendre: groups g = m_idx*2 + p; images per (|m|, p), shared by +-m
-    Pending pl;
-    pl.off.assign(2 * 2 * (2 * B - 1), 0);
-    pl.npad.assign(2 * (2 * B - 1), 16);
-    int npmax = 16;
+    TcSegInfo li;
+    memset(&li, 0, sizeof(li));
+    li.B = B, li.NB = NB, li.KC = KC, li.fn0 = sg.fn0, li.w2_off = sg.w2_off, li.g0 = (int)pl.npad.size();
+    if (!make_xmap(&li.xmap, w1, B, (int64_t)(2 * B - 1) * 2 * NB * 2 * B)) {
+      delete st;
+      return cudaErrorInvalidValue;
+    }
     for (int w = 0; w < 2; ++w) {
-      std::vector<int64_t> am_off(2 * B, -1);
+      std::vector<int64_t> am_off(2 * B, 0);
       for (int am = 0; am < B; ++am)
         for (int p = 0; p < 2; ++p) {
           const int N = n_par(B, am, p);
           if (N == 0) continue;
           const int np = pad16(N);
-          npmax = np > npmax ? np : npmax;
           std::vector<double> A((size_t)N * B);
           for (int q = 0; q < N; ++q) {
             const int l = am + p + 2 * q;
@@ -558,47 +600,42 @@ cudaError_t tc_prepare(Plan& P) {
           (bf ? append_image_bf16 : append_image)(img, N, B, np, KC, A);
         }
       for (int mi = 0; mi < 2 * B - 1; ++mi) {
-        const int m = mi - (B - 1);
-        const int am = m < 0 ? -m : m;
-        for (int p = 0; p < 2; ++p) {
-          const int g = mi * 2 + p;
-          pl.off[w * 2 * (2 * B - 1) + g] = am_off[am * 2 + p] < 0 ? 0 : am_off[am * 2 + p];
-          pl.npad[g] = pad16(n_par(B, am, p));
-        }
+        const int am = mi < B - 1 ? B - 1 - mi : mi - (B - 1);
+        for (int p = 0; p < 2; ++p) pl.off[w].push_back(am_off[am * 2 + p]);
       }
     }
     for (int mi = 0; mi < 2 * B - 1; ++mi) {
-      const int m = mi - (B - 1);
-      const int am = m < 0 ? -m : m;
+      const int am = mi < B - 1 ? B - 1 - mi : mi - (B - 1);
       for (int p = 0; p < 2; ++p) {
         const int N = n_par(B, am, p);
+        const int g = li.g0 + mi * 2 + p;
+        pl.npad.push_back(pad16(N));
+        st->leg.npmax = std::max(st->leg.npmax, pad16(N));
         if (N == 0) continue;
         for (int r0 = 0; r0 < NB * 2 * B; r0 += 128) {
-          pl.tiles.push_back(make_int2(mi * 2 + p, r0));
+          pl.tiles.push_back(make_int2(g | ((int)s << 20), r0));
           // X chunks in, S columns out, the group's table on its first tile
           pl.cost.push_back(KC * 16384.0 + 512.0 * N + (r0 == 0 ? 256.0 * KC * pad16(N) : 0.0));
         }
       }
     }
-    ts.leg.ngroups = 2 * (2 * B - 1);
-    ts.leg.npmax = npmax;
-    ts.leg.KC = KC;
+    pl.segs.push_back(li);
     // radial: groups (l, n0); degrees with more than kRadRows terms n' are cut
     // into the rows n' < kRadRows and the rest
-    Pending pr;
+    TcSegInfo ri = li;
+    ri.g0 = (int)pr.npad.size();
+    if (!make_xmap(&ri.xmap, w2, B, (int64_t)2 * NB * B * B)) {
+      delete st;
+      return cudaErrorInvalidValue;
+    }
     std::vector<int2> rgrp;  // (l, n0)
     for (int l = 0; l < B; ++l)
       for (int n0 = 0; n0 < B - l; n0 += kRadRows) rgrp.push_back(make_int2(l, n0));
-    const int ngr = (int)rgrp.size();
-    pr.off.assign(2 * ngr, 0);
-    pr.npad.assign(ngr, 16);
-    int npmax_r = 16;
     for (int w = 0; w < 2; ++w)
-      for (int g = 0; g < ngr; ++g) {
+      for (size_t g = 0; g < rgrp.size(); ++g) {
         const int l = rgrp[g].x, n0 = rgrp[g].y;
         const int N = std::min(B - l - n0, kRadRows);
         const int np = pad16(N);
-        npmax_r = np > npmax_r ? np : npmax_r;
         std::vector<double> A((size_t)N * B);
         for (int q = 0; q < N; ++q)
           for (int i = 0; i < B; ++i) {
@@ -606,70 +643,71 @@ cudaError_t tc_prepare(Plan& P) {
             A[(size_t)q * B + i] = w == 0 ? H.what[i] * v : v;
           }
         img.resize((img.size() + 1023) / 1024 * 1024);
-        pr.off[w * ngr + g] = (int64_t)img.size();
-        pr.npad[g] = np | (l << 8) | (n0 << 16);
+        pr.off[w].push_back((int64_t)img.size());
+        if (w == 0) {
+          pr.npad.push_back(np | (l << 8) | (n0 << 16));
+          st->rad.npmax = std::max(st->rad.npmax, np);
+        }
         (bf ? append_image_bf16 : append_image)(img, N, B, np, KC, A);
       }
-    for (int g = 0; g < ngr; ++g) {
+    for (size_t g = 0; g < rgrp.size(); ++g) {
       const int l = rgrp[g].x, n0 = rgrp[g].y;
       const int N = std::min(B - l - n0, kRadRows);
       for (int r0 = 0; r0 < NB * (2 * l + 1) * 2; r0 += 128) {
-        pr.tiles.push_back(make_int2(g, r0));
+        pr.tiles.push_back(make_int2((ri.g0 + (int)g) | ((int)s << 20), r0));
         pr.cost.push_back(KC * 16384.0 + 512.0 * N + (r0 == 0 ? 256.0 * KC * pad16(N) : 0.0));
       }
     }
-    ts.rad.ngroups = ngr;
-    ts.rad.npmax = npmax_r;
-    ts.rad.KC = KC;
-    // tensor maps over the segment's workspaces
-    float* w1 = (float*)P.d_w1 + sg.w1_off;
-    float* w2 = (float*)P.d_w2 + sg.w2_off;
-    if (!make_xmap(&ts.leg.xmap, w1, B, (int64_t)(2 * B - 1) * 2 * NB * 2 * B) ||
-        !make_xmap(&ts.rad.xmap, w2, B, (int64_t)2 * NB * B * B)) {
-      delete st;
-      return cudaErrorInvalidValue;
-    }
-    st->segs.push_back(ts);
-    pend.push_back(pl);
-    pend.push_back(pr);
+    pr.segs.push_back(ri);
+    st->leg.KCmax = std::max(st->leg.KCmax, KC);
+    st->rad.KCmax = std::max(st->rad.KCmax, KC);
   }
   cudaError_t e = cudaMalloc(&st->d_img, img.size());
   if (e != cudaSuccess) { delete st; return e; }
   P.bytes += img.size();
   e = cudaMemcpy(st->d_img, img.data(), img.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { delete st; return e; }
-  for (size_t s = 0; s < st->segs.size(); ++s) {
-    TcStage* stg[2] = {&st->segs[s].leg, &st->segs[s].rad};
-    for (int k = 0; k < 2; ++k) {
-      Pending& pd = pend[2 * s + k];
-      TcStage& S = *stg[k];
-      S.ntiles = (int)pd.tiles.size();
-      e = cudaMalloc(&S.d_tiles, pd.tiles.size() * sizeof(int2));
-      if (e == cudaSuccess) e = cudaMemcpy(S.d_tiles, pd.tiles.data(), pd.tiles.size() * sizeof(int2),
-                                           cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMalloc(&S.d_off, pd.off.size() * sizeof(int64_t));
-      if (e == cudaSuccess) e = cudaMemcpy(S.d_off, pd.off.data(), pd.off.size() * sizeof(int64_t),
-                                           cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMalloc(&S.d_npad, pd.npad.size() * sizeof(int));
-      if (e == cudaSuccess) e = cudaMemcpy(S.d_npad, pd.npad.data(), pd.npad.size() * sizeof(int),
-                                           cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) { delete st; return e; }
-      const int stages = k == 0 ? kStagesLeg : kStagesRad;
-      S.grid = S.ntiles < nsm ? S.ntiles : nsm;
-      int max_tiles = 0;
-      const std::vector<int> first = balance_slices(pd.cost, S.grid > 0 ? S.grid : 1, &max_tiles);
-      if (e == cudaSuccess) e = cudaMalloc(&S.d_first, first.size() * sizeof(int));
-      if (e == cudaSuccess) e = cudaMemcpy(S.d_first, first.data(), first.size() * sizeof(int),
-                                           cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) { delete st; return e; }
-      max_tiles += 1;
-      // tables, X ring, 64 barrier/flag slots, group metadata, tile slice
-      S.smem = 1024 + (size_t)2 * S.KC * S.npmax * (bf ? 64 : 128) + (size_t)stages * 2 * kChunkBytes + 64 * 8 +
-               (size_t)S.ngroups * 12 + 8 + (size_t)max_tiles * 8;
-      if (S.smem > 227 * 1024) { delete st; return cudaErrorInvalidValue; }
+  auto upload = [&](auto** dst, const auto& v) -> cudaError_t {
+    using T = typename std::decay<decltype(v[0])>::type;
+    cudaError_t r = cudaMalloc((void**)dst, std::max<size_t>(v.size(), 1) * sizeof(T));
+    if (r == cudaSuccess && !v.empty()) r = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    P.bytes += v.size() * sizeof(T);
+    return r;
+  };
+  Pending* pend[2] = {&pl, &pr};
+  TcStage* stg[2] = {&st->leg, &st->rad};
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    Pending& pd = *pend[k];
+    TcStage& S = *stg[k];
+    S.ntiles = (int)pd.tiles.size();
+    S.ngroups = (int)pd.npad.size();
+    S.nseg = (int)pd.segs.size();
+    std::vector<int64_t> off = pd.off[0];
+    off.insert(off.end(), pd.off[1].begin(), pd.off[1].end());
+    e = upload(&S.d_tiles, pd.tiles);
+    if (e == cudaSuccess) e = upload(&S.d_off, off);
+    if (e == cudaSuccess) e = upload(&S.d_npad, pd.npad);
+    if (e == cudaSuccess) e = upload(&S.d_segs, pd.segs);
+    // tables, X ring, 64 barrier/flag slots, segments, group metadata of the
+    // slice (at most one group per tile), tile slice; more CTAs (further
+    // waves) when the slices of one wave would not fit
+    const int stages = k == 0 ? kStagesLeg : kStagesRad;
+    const size_t fixed = 1024 + (size_t)2 * S.KCmax * S.npmax * (bf ? 64 : 128) + (size_t)stages * 2 * kChunkBytes +
+                         64 * 8 + (size_t)S.nseg * sizeof(SegSmall) + 16 + 12 + 16;
+    const size_t per_tile = 12 + 16;
+    S.grid = S.ntiles < nsm ? S.ntiles : nsm;
+    int max_tiles = 0;
+    std::vector<int> first = balance_slices(pd.cost, S.grid > 0 ? S.grid : 1, &max_tiles);
+    while (fixed + (size_t)max_tiles * per_tile > 227 * 1024 && S.grid < S.ntiles) {
+      S.grid = std::min(S.ntiles, S.grid + nsm);
+      first = balance_slices(pd.cost, S.grid, &max_tiles);
     }
+    S.smem = fixed + (size_t)max_tiles * per_tile;
+    if (e == cudaSuccess) e = upload(&S.d_first, first);
+    if (e == cudaSuccess && S.smem > 227 * 1024) e = cudaErrorInvalidValue;
   }
   P.tc_state = st;
+  if (e != cudaSuccess) return e;
   return tc_inv_prepare(P);
 }
 
@@ -677,22 +715,21 @@ void tc_release(Plan& P) {
   tc_inv_release(P);
   TcState* st = (TcState*)P.tc_state;
   if (!st) return;
-  for (TcSeg& s : st->segs)
-    for (TcStage* S : {&s.leg, &s.rad}) {
-      if (S->d_tiles) cudaFree(S->d_tiles);
-      if (S->d_first) cudaFree(S->d_first);
-      if (S->d_off) cudaFree(S->d_off);
-      if (S->d_npad) cudaFree(S->d_npad);
-    }
+  for (TcStage* S : {&st->leg, &st->rad}) {
+    void* ptrs[] = {S->d_tiles, S->d_first, S->d_off, S->d_npad, S->d_segs};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+  }
   if (st->d_img) cudaFree(st->d_img);
   delete st;
   P.tc_state = nullptr;
 }
 
 int tc_launches(const Plan& P) {
-  // GEMM launches per call (forward or inverse): two stages, one launch per
-  // segment each; FFT launches are counted by the caller
-  return 2 * (int)P.segs.size();
+  // GEMM launches per call (forward or inverse): two stages, one launch each
+  // over every segment; FFT launches are counted by the caller
+  (void)P;
+  return 2;
 }
 
 cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted, cudaStream_t s) {
@@ -701,10 +738,8 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
   if (!st) return cudaErrorNotSupported;
   static const int stage_of[2] = {ST_LEG_F, ST_RAD_F};
   StageTimer timer(P, stage_of[prob], s);
-  for (size_t k = 0; k < st->segs.size(); ++k) {
-    TcStage& S = prob == 0 ? st->segs[k].leg : st->segs[k].rad;
-    if (S.ntiles == 0) continue;
-    const SegDesc& sg = P.segs[k];
+  TcStage& S = prob == 0 ? st->leg : st->rad;
+  if (S.ntiles > 0) {
     TcArgs a;
     a.tiles = S.d_tiles;
     a.cta_first = S.d_first;
@@ -713,25 +748,24 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
     a.grp_off = S.d_off;
     a.grp_npad = S.d_npad;
     a.ngroups = S.ngroups;
+    a.segs = S.d_segs;
+    a.nseg = S.nseg;
     a.y = y;
-    a.fn_coef = P.d_fn_coef + sg.fn0;
+    a.fn_coef = P.d_fn_coef;
     a.err = P.d_err;
-    a.B = sg.B;
-    a.NB = sg.NB;
-    a.KC = S.KC;
+    a.KCmax = S.KCmax;
     a.weighted = weighted;
-    a.w2_off = sg.w2_off;
     a.npmax = S.npmax;
     a.nprod = tc_products(P.prec);
     (void)x;
-    void (*fn)(const CUtensorMap, TcArgs);
+    void (*fn)(TcArgs);
     if (tc_bf16(P.prec))
       fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, true> : tc_gemm_kernel<TC_RAD_F, kStagesRad, true>;
     else
       fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, false> : tc_gemm_kernel<TC_RAD_F, kStagesRad, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem);
     if (e != cudaSuccess) return e;
-    fn<<<S.grid, kThreads, S.smem, s>>>(S.xmap, a);
+    fn<<<S.grid, kThreads, S.smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
