@@ -91,32 +91,44 @@ __device__ __forceinline__ void split_store_bf(unsigned char* hi, unsigned char*
 // order (m, j'-half, rows): only the current half of the table is resident,
 // which leaves shared memory for a 4-deep staging ring; each row block is
 // read once per half.
+// One bandlimit segment of a launch; a launch covers every segment of the
+// plan.  Aligned as its tensor map.
+struct LegISeg {
+  CUtensorMap smap;           // the segment's S: [B^2 rows of l'][NB*2*B]
+  int B, NB, npad, pad;
+  int64_t w1_off;             // the segment's G block
+};
+struct LegISegSmall {
+  int B, NB, npad, pad;
+  int64_t w1_off;
+};
+
 struct LegIArgs {
-  const int2* tiles;          // (m_idx, row0 | j'-half), ordered by (m_idx, half, row0)
+  // per tile, two int4: (m_idx, row0, j'-half | segment << 8, KC_P | KC_Q << 8)
+  // and (table image offset, S row of the P block, S row of the Q block, 0);
+  // ordered by (segment, m_idx, half, row0)
+  const int4* tiles;
   const int* cta_first;       // tile slice of each CTA (gridDim.x + 1 offsets)
   int ntiles;
   const unsigned char* tabimg;
-  const int64_t* am_off;      // image offset per (|m|, half)
-  const int* am_kc;           // KC_P | KC_Q << 8 per |m|
-  const int64_t* si_rows;     // S row offset per (m_idx, p)
-  float* g;                   // output, layout [m_idx][b][c][j < 2B][i]
+  const LegISeg* segs;
+  int nseg;
+  float* g;                   // output, per segment layout [m_idx][b][c][j < 2B][i]
   int* err;
-  int B, NB, npad, kcmax;
+  int npad_max, kcmax;        // over the segments
   int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
 };
 
 // BF: BF16 hi/lo operands (kind::f16, 64-byte rows, K = 16 per MMA).
 template <bool BF>
-__global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid_constant__ CUtensorMap smap,
-                                                                    LegIArgs a) {
+__global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) {
   constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int B = a.B, NB = a.NB, npad = a.npad;
-  const int nh = npad > 64 ? 64 : npad;                    // rows (j') of one table half
-  const int chunk_tab = nh * ROWB;                         // one table chunk (hi or lo)
+  // rows (j') of one table half: per segment min(npad, 64); buffers sized for the largest
+  const int nhm = a.npad_max > 64 ? 64 : a.npad_max;
   unsigned char* tab = base;                               // [P hi][P lo][Q hi][Q lo] of one half
-  unsigned char* stg = tab + (size_t)a.kcmax * 2 * chunk_tab;   // staging ring: 32 l' x 128 rows each
+  unsigned char* stg = tab + (size_t)a.kcmax * 2 * nhm * ROWB;   // staging ring: 32 l' x 128 rows each
   unsigned char* xs = stg + kStagingLegI * kChunk;         // operand ring: (hi, lo)
   uint64_t* bars = (uint64_t*)(xs + kStagesLegI * 2 * kChunk);
   uint64_t* stgf = bars;                        // [T] staging landed
@@ -129,18 +141,18 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
   uint64_t* tabe = tabf + 1;
   uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  // per-group metadata and the tile slice, copied once to shared memory
-  int64_t* s_si = (int64_t*)(bars + 64);          // [(2B-1)*2] S row offsets
-  int64_t* s_off = s_si + 2 * (2 * B - 1);         // [2B] table image offsets per (|m|, half)
-  int* s_kc = (int*)(s_off + 2 * B);               // [B] KC_P | KC_Q << 8
-  int2* s_tiles = (int2*)(((uintptr_t)(s_kc + B) + 7) & ~(uintptr_t)7);
-  for (int k = threadIdx.x; k < 2 * (2 * B - 1); k += blockDim.x) s_si[k] = a.si_rows[k];
-  for (int k = threadIdx.x; k < 2 * B; k += blockDim.x) s_off[k] = a.am_off[k];
-  for (int k = threadIdx.x; k < B; k += blockDim.x) s_kc[k] = a.am_kc[k];
+  // the segments and the tile slice (two records per tile), copied once to
+  // shared memory
+  LegISegSmall* s_seg = (LegISegSmall*)(bars + 64);
+  int4* s_tiles = (int4*)(((uintptr_t)(s_seg + a.nseg) + 15) & ~(uintptr_t)15);
+  for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) {
+    const LegISeg& g = a.segs[k];
+    s_seg[k] = LegISegSmall{g.B, g.NB, g.npad, 0, g.w1_off};
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t tmem_cols = 32;
-  while (tmem_cols < (uint32_t)(8 * nh)) tmem_cols <<= 1;  // 2 buffers x {P, Q} x {main, corr}
+  while (tmem_cols < (uint32_t)(8 * nhm)) tmem_cols <<= 1;  // 2 buffers x {P, Q} x {main, corr}
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagingLegI; ++s) {
       mbar_init(stgf + s, 1);
@@ -162,41 +174,46 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
   const int g_begin = a.cta_first[blockIdx.x];
   const int nt = a.cta_first[blockIdx.x + 1] - g_begin;
-  for (int k = threadIdx.x; k < nt; k += blockDim.x) s_tiles[k] = a.tiles[g_begin + k];
+  for (int k = threadIdx.x; k < 2 * nt; k += blockDim.x) s_tiles[k] = a.tiles[2 * g_begin + k];
   tc_before();
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
-  // the resident table changes with (m_idx, half)
-  auto table_key = [&](int2 tl) { return 2 * tl.x + (tl.y & 1); };
-  auto abs_m = [&](int m_idx) { return m_idx >= B - 1 ? m_idx - (B - 1) : (B - 1) - m_idx; };
+  // tile t: s_tiles[2t] = (m_idx, row0, half | seg << 8, KC_P | KC_Q << 8),
+  //         s_tiles[2t+1] = (table image offset, S row of P, S row of Q, 0);
+  // the resident table changes with its image offset
 
   if (warp == 0) {
     if (lane == 0) {
-      int cur = -1, ngrp = 0;
+      int cur = -1, ngrp = 0, cur_seg = -1;
       uint32_t c = 0;
       for (int t = 0; t < nt && !*abort_flag; ++t) {
-        const int2 tl = s_tiles[t];
-        const int m_idx = tl.x, jh = tl.y & 1;
-        const int am = abs_m(m_idx);
-        const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
-        if (table_key(tl) != cur) {
+        const int4 ta = s_tiles[2 * t], tb = s_tiles[2 * t + 1];
+        const int seg = ta.z >> 8;
+        const int nh = min(s_seg[seg].npad, 64);
+        const int kcp = ta.w & 0xff, kcq = ta.w >> 8;
+        const CUtensorMap* smap = &a.segs[seg].smap;
+        if (seg != cur_seg) {  // the tensor map lives in global memory
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(smap) : "memory");
+          cur_seg = seg;
+        }
+        if (tb.x != cur) {
           if (ngrp > 0 && !mbar_wait(tabe, (ngrp - 1) & 1, abort_flag)) break;
-          const uint32_t bytes = (uint32_t)((kcp + kcq) * 2 * chunk_tab);
+          const uint32_t bytes = (uint32_t)((kcp + kcq) * 2 * nh * ROWB);
           mbar_arrive_tx(tabf, bytes);
-          bulk_load(tab, a.tabimg + s_off[2 * am + jh], bytes, tabf);
-          cur = table_key(tl);
+          bulk_load(tab, a.tabimg + (uint32_t)tb.x, bytes, tabf);
+          cur = tb.x;
           ++ngrp;
         }
         bool ok = true;
         for (int p = 0; p < 2 && ok; ++p) {
           const int kcn = p ? kcq : kcp;
-          const int64_t r0 = s_si[2 * m_idx + p];
+          const int r0 = p ? tb.z : tb.y;
           for (int kc = 0; kc < kcn; ++kc, ++c) {
             const int s = c % kStagingLegI;
             if (!mbar_wait(stge + s, ((c / kStagingLegI) & 1) ^ 1, abort_flag)) { ok = false; break; }
             mbar_arrive_tx(stgf + s, kChunk);
-            tma_load_2d(stg + s * kChunk, &smap, stgf + s, tl.y & ~1, (int)(r0 + kc * 32));
+            tma_load_2d(stg + s * kChunk, smap, stgf + s, ta.y, r0 + kc * 32);
           }
         }
         if (!ok) break;
@@ -211,25 +228,26 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
       // the table image stacks nh hi rows over nh lo rows per K chunk: one
       // MMA of width 2 nh gives [X_hi T_hi | X_hi T_lo], a second of width nh
       // adds X_lo T_hi to the correction
-      const uint32_t idesc2 = BF ? idesc_bf16(2 * nh) : idesc_tf32(2 * nh);
-      const uint32_t idesc1 = BF ? idesc_bf16(nh) : idesc_tf32(nh);
       const uint64_t xdesc0 = BF ? sw64_desc(smem_u32(xs)) : sw128_desc(smem_u32(xs));
       const uint64_t tdesc0 = BF ? sw64_desc(smem_u32(tab)) : sw128_desc(smem_u32(tab));
       for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
-        const int2 tl = s_tiles[t];
-        const int am = abs_m(tl.x);
-        const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
-        if (table_key(tl) != cur) {
+        const int4 ta = s_tiles[2 * t], tb = s_tiles[2 * t + 1];
+        const int nh = min(s_seg[ta.z >> 8].npad, 64);
+        const int chunk_tab = nh * ROWB;
+        const uint32_t idesc2 = BF ? idesc_bf16(2 * nh) : idesc_tf32(2 * nh);
+        const uint32_t idesc1 = BF ? idesc_bf16(nh) : idesc_tf32(nh);
+        const int kcp = ta.w & 0xff, kcq = ta.w >> 8;
+        if (tb.x != cur) {
           if (!mbar_wait(tabf, ngrp & 1, abort_flag)) break;
-          cur = table_key(tl);
+          cur = tb.x;
           ++ngrp;
         }
         const int acc = tcount & 1;
         if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
         tc_after();
         bool ok = true;
-        // accumulators of this buffer: [P main][P corr][Q main][Q corr], nh columns each
-        const uint32_t d = tmem + (uint32_t)((4 * acc + 2 * p) * nh);
+        // accumulators of this buffer (4 nhm columns apart): [P main][P corr][Q main][Q corr], nh columns each
+        const uint32_t d = tmem + (uint32_t)(4 * acc * nhm + 2 * p * nh);
         const uint64_t tp = tdesc0 + (uint64_t)(((p ? kcp : 0) * 2 * chunk_tab) >> 4);
         // Every chunk of the tile is waited for, so that the ring's phases are
         // followed in order; only the chunks of parity p are issued here.  A
@@ -271,7 +289,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
         }
         if (!ok) break;
         mma_commit(accf + acc);
-        if (t + 1 >= nt || table_key(s_tiles[t + 1]) != cur) mma_commit(tabe);
+        if (t + 1 >= nt || s_tiles[2 * t + 3].x != cur) mma_commit(tabe);
       }
     }
   } else if (warp < kFirstEpiWarp) {
@@ -281,8 +299,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
     const int r = tid & 127, h = tid >> 7;
     uint32_t c = 0;
     for (int t = 0; t < nt; ++t) {
-      const int am = abs_m(s_tiles[t].x);
-      const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
+      const int kcw = s_tiles[2 * t].w;
+      const int kcp = kcw & 0xff, kcq = kcw >> 8;
       bool ok = true;
       for (int ch = 0; ch < kcp + kcq; ++ch, ++c) {
         const int st = c % kStagingLegI;
@@ -307,23 +325,26 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
     const int r_in = quarter * 32 + lane;
     uint32_t tcount = 0;
     for (int t = 0; t < nt; ++t, ++tcount) {
-      const int2 tl = s_tiles[t];
+      const int4 ta = s_tiles[2 * t];
       const int acc = tcount & 1;
       if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
       tc_after();
-      const int m_idx = tl.x;
+      const LegISegSmall sg = s_seg[ta.z >> 8];
+      const int B = sg.B, NB = sg.NB, npad = sg.npad;
+      const int nh = min(npad, 64);
+      const int m_idx = ta.x;
       const int m = m_idx - (B - 1);
       const int am = m < 0 ? -m : m;
-      const int kcp = s_kc[am] & 0xff, kcq = s_kc[am] >> 8;
+      const int kcp = ta.w & 0xff, kcq = ta.w >> 8;
       const float sgn = (m < 0 && (am & 1)) ? -1.f : 1.f;
-      const int jh = tl.y & 1;
+      const int jh = ta.z & 1;
       const int ncols = jh ? npad - 64 : nh;
-      const int grow = (tl.y & ~1) + r_in;
+      const int grow = ta.y + r_in;
       const bool valid = grow < NB * 2 * B;
       const int b = grow / (2 * B), cc = (grow / B) & 1, i = grow % B;
-      float* out = a.g + (((int64_t)m_idx * NB + b) * 2 + cc) * (2 * B) * B + i;
+      float* out = a.g + sg.w1_off + (((int64_t)m_idx * NB + b) * 2 + cc) * (2 * B) * B + i;
       const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
-      const uint32_t dP = tmem + (uint32_t)(4 * acc * nh) + lanes;
+      const uint32_t dP = tmem + (uint32_t)(4 * acc * nhm) + lanes;
       const uint32_t dQ = dP + (uint32_t)(2 * nh);
       for (int c0 = 16 * ehalf; c0 < ncols; c0 += 32) {
         float P[16], Q[16];
@@ -374,36 +395,45 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(const __grid
 // hi*hi products; the other tiles are 128 columns wide, one pair per half of
 // 64 columns and issuer.  Either way a tile uses 256 TMEM columns, two tiles
 // in flight.
+// One bandlimit segment of an inverse radial launch (a launch covers every
+// segment of the plan).
+struct RadISeg {
+  int B, NB, fn0, si0;        // bandlimit, functions, first function, first S row entry in si_rows
+  int64_t w2_off;             // the segment's S block
+};
+
 struct RadIArgs {
-  const int2* tiles;          // (l, col0 | narrow), grouped by l
+  const int4* tiles;          // (l, col0 | narrow, segment, table image offset of l), by segment and l
   const int* cta_first;       // tile slice of each CTA (gridDim.x + 1 offsets)
   int ntiles;
   const unsigned char* tabimg;
-  const int64_t* l_off;       // image offset per l (KC_l chunk pairs of 32 KB)
-  const int64_t* si_rows;     // S row offset per (m_idx, p)
+  const RadISeg* segs;
+  int nseg;
+  const int64_t* si_rows;     // S row offset per (m_idx, p), per segment from si0
   const float* coef;          // complex interleaved coefficients
-  const int64_t* fn_coef;     // coefficient offset per function of the segment
-  float* s;                   // output S, layout [m_idx][p][l'][b][c][i]
+  const int64_t* fn_coef;     // coefficient offset per function (plan order of segments)
+  float* s;                   // output S, per segment layout [m_idx][p][l'][b][c][i]
   int* err;
-  int B, NB;
+  int si_max;                 // shared-memory entries for the S row offsets of one CTA's segments
   int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
 };
 
 // Coefficients of one K chunk (32 degrees n) of one tile column, gathered by
 // split thread tid: 16 (wide tile) or 8 (narrow tile) consecutive degrees.
-__device__ __forceinline__ void rad_gather(const RadIArgs& a, int2 tl, int kc, int tid, float* v) {
-  const int B = a.B, l = tl.x;
+__device__ __forceinline__ void rad_gather(const RadIArgs& a, const RadISeg& sg, int4 tl, int kc, int tid,
+                                           float* v) {
+  const int B = sg.B, l = tl.x;
   const bool nar = tl.y & 1;
   const int col_in = nar ? (tid & 63) : (tid & 127);
   const int h = nar ? (tid >> 6) : (tid >> 7);
   const int nv = nar ? 8 : 16;
   const int per_b = (2 * l + 1) * 2;
   const int col = (tl.y & ~1) + col_in;
-  const bool valid = col < a.NB * per_b;
+  const bool valid = col < sg.NB * per_b;
   const int b = valid ? col / per_b : 0;
   const int rem = col - b * per_b;
   const int m = (rem >> 1) - l, cc = rem & 1;
-  const float* cf = a.coef + 2 * a.fn_coef[b] + cc;
+  const float* cf = a.coef + 2 * a.fn_coef[sg.fn0 + b] + cc;
   const int np0 = kc * 32 + h * nv;        // degree n = l + 1 + n'
   int n = l + 1 + np0;
   int64_t off = omega_of(n, l, m);          // omega(n + 1) - omega(n) = n^2
@@ -423,7 +453,6 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   constexpr int TCH = 128 * ROWB;      // one table chunk (hi or lo): 128 rows i
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int B = a.B, NB = a.NB;
   // stage s: [table hi][table lo][data], 16 KB each part (BF16: the table
   // parts use their first 8 KB; data halves of 64 columns are 64 hi rows over
   // 64 lo rows, 16 KB (TF32) or 8 KB (BF16) each)
@@ -436,11 +465,29 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   uint64_t* acce = accf + 2;                // [2] (epilogue threads)
   uint32_t* tmem_slot = (uint32_t*)(acce + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  int64_t* s_si = (int64_t*)(bars + 64);          // [(2B-1)*2] S row offsets
-  int64_t* s_loff = s_si + 2 * (2 * B - 1);        // [B] table image offsets
-  int2* s_tiles = (int2*)(s_loff + B);
-  for (int k = threadIdx.x; k < 2 * (2 * B - 1); k += blockDim.x) s_si[k] = a.si_rows[k];
-  for (int k = threadIdx.x; k < B; k += blockDim.x) s_loff[k] = a.l_off[k];
+  // the tile slice, the segments it touches (seg_lo ..) and their S row
+  // offsets, copied once to shared memory
+  const int g_begin = a.cta_first[blockIdx.x];
+  const int nt = a.cta_first[blockIdx.x + 1] - g_begin;
+  const int seg_lo = nt > 0 ? a.tiles[g_begin].z : 0;
+  const int nseg_cta = nt > 0 ? a.tiles[g_begin + nt - 1].z - seg_lo + 1 : 0;
+  RadISeg* s_seg = (RadISeg*)(bars + 64);                  // [nseg_cta]
+  int* s_sib = (int*)(s_seg + (nseg_cta > 0 ? nseg_cta : 1));  // [nseg_cta] first entry in s_si
+  int64_t* s_si = (int64_t*)(((uintptr_t)(s_sib + (nseg_cta > 0 ? nseg_cta : 1)) + 7) & ~(uintptr_t)7);  // [si_max]
+  int4* s_tiles = (int4*)(((uintptr_t)(s_si + a.si_max) + 15) & ~(uintptr_t)15);
+  if (threadIdx.x == 0) {
+    int e = 0;
+    for (int k = 0; k < nseg_cta; ++k) {
+      s_seg[k] = a.segs[seg_lo + k];
+      s_sib[k] = e;
+      e += 2 * (2 * s_seg[k].B - 1);
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < nseg_cta; ++k) {
+    const int n = 2 * (2 * s_seg[k].B - 1);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) s_si[s_sib[k] + q] = a.si_rows[s_seg[k].si0 + q];
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tmem_cols = 512;  // 2 buffers x 256 columns
@@ -458,9 +505,11 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
-  const int g_begin = a.cta_first[blockIdx.x];
-  const int nt = a.cta_first[blockIdx.x + 1] - g_begin;
-  for (int k = threadIdx.x; k < nt; k += blockDim.x) s_tiles[k] = a.tiles[g_begin + k];
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    int4 tl = a.tiles[g_begin + k];
+    tl.z -= seg_lo;  // segment within this CTA's copy
+    s_tiles[k] = tl;
+  }
   tc_before();
   __syncthreads();
   tc_after();
@@ -470,16 +519,18 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     if (lane == 0) {
       uint32_t c = 0;
       for (int t = 0; t < nt && !*abort_flag; ++t) {
-        const int l = s_tiles[t].x;
-        const int kcn = (B - l + 31) / 32;
+        const int4 tl = s_tiles[t];
+        const int l = tl.x;
+        const int kcn = (s_seg[tl.z].B - l + 31) / 32;
+        const unsigned char* img = a.tabimg + (uint32_t)tl.w;
         bool ok = true;
         for (int kc = 0; kc < kcn; ++kc, ++c) {
           const int s = c % kStagesRadI;
           if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) { ok = false; break; }
           // hi and lo chunk of the image, contiguous; the lo part lands at +kChunk
           mbar_arrive_tx(tfull + s, 2 * TCH);
-          bulk_load(st + s * 4 * kChunk, a.tabimg + s_loff[l] + (int64_t)kc * 2 * TCH, TCH, tfull + s);
-          bulk_load(st + s * 4 * kChunk + kChunk, a.tabimg + s_loff[l] + (int64_t)kc * 2 * TCH + TCH, TCH, tfull + s);
+          bulk_load(st + s * 4 * kChunk, img + (int64_t)kc * 2 * TCH, TCH, tfull + s);
+          bulk_load(st + s * 4 * kChunk + kChunk, img + (int64_t)kc * 2 * TCH + TCH, TCH, tfull + s);
         }
         if (!ok) break;
       }
@@ -496,10 +547,10 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       const uint32_t idesc2 = BF ? idesc_bf16(128) : idesc_tf32(128);
       const uint32_t idesc1 = BF ? idesc_bf16(64) : idesc_tf32(64);
       for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
-        const int2 tl = s_tiles[t];
+        const int4 tl = s_tiles[t];
         const int l = tl.x;
         const bool nar = tl.y & 1;
-        const int kcn = (B - l + 31) / 32;
+        const int kcn = (s_seg[tl.z].B - l + 31) / 32;
         const int acc = tcount & 1;
         if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
         tc_after();
@@ -565,16 +616,16 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     const int tid = threadIdx.x - 32 * kFirstSplitWarp;
     float v[16], vn[16];
     int t = 0, kc = 0;
-    if (nt > 0) rad_gather(a, s_tiles[0], 0, tid, v);
+    if (nt > 0) rad_gather(a, s_seg[s_tiles[0].z], s_tiles[0], 0, tid, v);
     for (uint32_t c = 0; t < nt; ++c) {
-      const int2 tl = s_tiles[t];
+      const int4 tl = s_tiles[t];
       const bool nar = tl.y & 1;
       int tn = t, kcn_next = kc + 1;
-      if (kcn_next == (B - tl.x + 31) / 32) {
+      if (kcn_next == (s_seg[tl.z].B - tl.x + 31) / 32) {
         tn = t + 1;
         kcn_next = 0;
       }
-      if (tn < nt) rad_gather(a, s_tiles[tn], kcn_next, tid, vn);
+      if (tn < nt) rad_gather(a, s_seg[s_tiles[tn].z], s_tiles[tn], kcn_next, tid, vn);
       const int s = c % kStagesRadI;
       if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) break;
       // B operand: per half of 64 columns, 64 hi rows then 64 lo rows
@@ -605,10 +656,14 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     const int i = quarter * 32 + lane;   // TMEM lane = radius index
     uint32_t tcount = 0;
     for (int t = 0; t < nt; ++t, ++tcount) {
-      const int2 tl = s_tiles[t];
+      const int4 tl = s_tiles[t];
       const int acc = tcount & 1;
       if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
       tc_after();
+      const RadISeg sg = s_seg[tl.z];
+      const int B = sg.B, NB = sg.NB;
+      const int64_t* si = s_si + s_sib[tl.z];
+      float* sout = a.s + sg.w2_off;
       const int l = tl.x;
       const bool nar = tl.y & 1;
       const int col0 = tl.y & ~1;
@@ -626,7 +681,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
             const int m = (rem >> 1) - l, cc = rem & 1;
             const int am = m < 0 ? -m : m;
             const int p = (l - am) & 1;
-            const int64_t srow = s_si[2 * (m + B - 1) + p] + ((l - am - p) >> 1);
+            const int64_t srow = si[2 * (m + B - 1) + p] + ((l - am - p) >> 1);
             o = srow * ((int64_t)NB * 2 * B) + ((int64_t)b * 2 + cc) * B;
           }
         }
@@ -646,7 +701,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int64_t ok = __shfl_sync(0xffffffffu, o, k);
-          if (i < B && ok >= 0) a.s[ok + i] = v[k];
+          if (i < B && ok >= 0) sout[ok + i] = v[k];
         }
       }
       tc_before();
@@ -731,27 +786,23 @@ int pad16i(int n) { return n <= 16 ? 16 : (n + 15) / 16 * 16; }
 
 }  // namespace
 
-struct TcInvSeg {
-  // Legendre
-  CUtensorMap smap;
-  int2* leg_tiles = nullptr;
-  int* leg_first = nullptr;
-  int leg_ntiles = 0, leg_grid = 0;
-  size_t leg_smem = 0;
-  int64_t* am_off = nullptr;
-  int* am_kc = nullptr;
-  int npad = 0, kcmax = 0;
-  // radial
-  int2* rad_tiles = nullptr;
-  int* rad_first = nullptr;
-  int rad_ntiles = 0, rad_grid = 0;
-  size_t rad_smem = 0;
-  int64_t* l_off = nullptr;
-};
-
+// The two inverse stages over every segment of the plan, one launch each.
 struct TcInvState {
-  std::vector<TcInvSeg> segs;
   unsigned char* d_img = nullptr;
+  // Legendre synthesis
+  int4* leg_tiles = nullptr;      // two records per tile
+  int* leg_first = nullptr;
+  LegISeg* leg_segs = nullptr;
+  int leg_ntiles = 0, leg_grid = 0, npad_max = 16, kcmax = 1;
+  size_t leg_smem = 0;
+  // radial
+  int4* rad_tiles = nullptr;
+  int* rad_first = nullptr;
+  RadISeg* rad_segs = nullptr;
+  int rad_ntiles = 0, rad_grid = 0, si_max = 0;
+  size_t rad_smem = 0;
+  std::vector<int64_t> l_off;     // image offset of the radial table of (segment, l)
+  std::vector<int> l_base;        // first entry of each segment in l_off
 };
 
 bool make_map_2d(CUtensorMap* map, void* base, uint64_t inner, uint64_t rows, uint32_t box_inner, uint32_t box_rows,
@@ -765,31 +816,66 @@ static cudaError_t upload(T** dst, const std::vector<T>& v, int64_t& bytes) {
   return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-// Inverse radial tiles of segment s: 64 columns with two K chains where
+// Grid for a tile list: cost-balanced slices of one wave of CTAs, more waves
+// while the largest slice's share of shared memory does not fit.
+static std::vector<int> slices_for(const std::vector<double>& cost, int nsm, size_t fixed, size_t per_tile,
+                                   int* grid, int* max_tiles) {
+  const int n = (int)cost.size();
+  *grid = std::max(1, std::min(n, nsm));
+  std::vector<int> first = balance_slices(cost, *grid, max_tiles);
+  while (fixed + (size_t)*max_tiles * per_tile > 227 * 1024 && *grid < n) {
+    *grid = std::min(n, *grid + nsm);
+    first = balance_slices(cost, *grid, max_tiles);
+  }
+  return first;
+}
+
+// Inverse radial tiles of every segment: 64 columns with two K chains where
 // B - l >= P.radi_narrow, else 128 columns; the CTA slices and shared memory.
-static cudaError_t radi_tiles(const Plan& P, size_t s, TcInvSeg& ts, int nsm, int64_t& bytes) {
-  const int B = P.segs[s].B, NB = P.segs[s].NB;
-  std::vector<int2> rtiles;
+static cudaError_t radi_tiles(const Plan& P, TcInvState& st, int nsm, int64_t& bytes) {
+  std::vector<int4> rtiles;
   std::vector<double> rc;
-  for (int l = 0; l < B; ++l) {
-    const int nar = B - l >= P.radi_narrow ? 1 : 0;
-    const int width = nar ? 64 : 128;
-    const int kcn = (B - l + 31) / 32;
-    for (int c0 = 0; c0 < NB * (2 * l + 1) * 2; c0 += width) {
-      rtiles.push_back(make_int2(l, c0 | nar));
-      // gathered coefficients, table chunks (from L2, half weight), S out
-      rc.push_back(kcn * (width * 128.0 + 16384.0) + 512.0 * width);
+  for (size_t s = 0; s < P.segs.size(); ++s) {
+    const int B = P.segs[s].B, NB = P.segs[s].NB;
+    for (int l = 0; l < B; ++l) {
+      const int nar = B - l >= P.radi_narrow ? 1 : 0;
+      const int width = nar ? 64 : 128;
+      const int kcn = (B - l + 31) / 32;
+      const int img = (int)st.l_off[st.l_base[s] + l];
+      for (int c0 = 0; c0 < NB * (2 * l + 1) * 2; c0 += width) {
+        rtiles.push_back(make_int4(l, c0 | nar, (int)s, img));
+        // gathered coefficients, table chunks (from L2, half weight), S out
+        rc.push_back(kcn * (width * 128.0 + 16384.0) + 512.0 * width);
+      }
     }
   }
-  cudaError_t e = upload(&ts.rad_tiles, rtiles, bytes);
-  ts.rad_ntiles = (int)rtiles.size();
-  ts.rad_grid = std::min(ts.rad_ntiles, nsm);
-  int rmax = 0;
-  const std::vector<int> rf = balance_slices(rc, std::max(ts.rad_grid, 1), &rmax);
-  if (e == cudaSuccess) e = upload(&ts.rad_first, rf, bytes);
-  const size_t meta = (size_t)2 * (2 * B - 1) * 8 + (size_t)B * 12 + 8;
-  ts.rad_smem = 1024 + (size_t)kStagesRadI * 4 * kChunk + 64 * 8 + meta + (size_t)(rmax + 1) * 8;
-  if (e == cudaSuccess && ts.rad_smem > 227 * 1024) e = cudaErrorInvalidValue;
+  cudaError_t e = upload(&st.rad_tiles, rtiles, bytes);
+  st.rad_ntiles = (int)rtiles.size();
+  // shared memory: stages, barrier slots, the segments of the slice, their S
+  // row offsets (si_max entries: the most any CTA's segments need), the tile
+  // slice; more waves of CTAs while that does not fit
+  const size_t fixed = 1024 + (size_t)kStagesRadI * 4 * kChunk + 64 * 8 + (P.segs.size() + 1) * (sizeof(RadISeg) + 4) +
+                       8 + 16;
+  const int n = (int)rc.size();
+  st.rad_grid = std::max(1, std::min(n, nsm));
+  std::vector<int> rf;
+  for (;;) {
+    int rmax = 0;
+    rf = balance_slices(rc, st.rad_grid, &rmax);
+    int si_max = 0;
+    for (int k = 0; k < st.rad_grid; ++k) {
+      if (rf[k + 1] <= rf[k]) continue;
+      int need = 0;
+      for (int sg = rtiles[rf[k]].z; sg <= rtiles[rf[k + 1] - 1].z; ++sg) need += 2 * (2 * P.segs[sg].B - 1);
+      si_max = std::max(si_max, need);
+    }
+    st.si_max = si_max;
+    st.rad_smem = fixed + (size_t)si_max * 8 + (size_t)(rmax + 1) * 16;
+    if (st.rad_smem <= 227 * 1024 || st.rad_grid >= n) break;
+    st.rad_grid = std::min(n, st.rad_grid + nsm);
+  }
+  if (e == cudaSuccess) e = upload(&st.rad_first, rf, bytes);
+  if (e == cudaSuccess && st.rad_smem > 227 * 1024) e = cudaErrorInvalidValue;
   return e;
 }
 
@@ -799,27 +885,20 @@ cudaError_t tc_radi_retile(Plan& P) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int64_t bytes = 0;
-  for (size_t s = 0; s < st->segs.size(); ++s) {
-    TcInvSeg& ts = st->segs[s];
-    if (ts.rad_tiles) {
-      cudaFree(ts.rad_tiles);
-      P.bytes -= (int64_t)ts.rad_ntiles * sizeof(int2);
-    }
-    if (ts.rad_first) {
-      cudaFree(ts.rad_first);
-      P.bytes -= (int64_t)(ts.rad_grid > 0 ? ts.rad_grid + 1 : 2) * sizeof(int);
-    }
-    ts.rad_tiles = nullptr;
-    ts.rad_first = nullptr;
-    cudaError_t e = radi_tiles(P, s, ts, nsm, bytes);
-    if (e != cudaSuccess) {
-      P.bytes += bytes;
-      return e;
-    }
+  if (st->rad_tiles) {
+    cudaFree(st->rad_tiles);
+    P.bytes -= (int64_t)st->rad_ntiles * sizeof(int4);
   }
+  if (st->rad_first) {
+    cudaFree(st->rad_first);
+    P.bytes -= (int64_t)(st->rad_grid + 1) * sizeof(int);
+  }
+  st->rad_tiles = nullptr;
+  st->rad_first = nullptr;
+  int64_t bytes = 0;
+  const cudaError_t e = radi_tiles(P, *st, nsm, bytes);
   P.bytes += bytes;
-  return cudaSuccess;
+  return e;
 }
 
 cudaError_t tc_inv_prepare(Plan& P) {
@@ -827,25 +906,27 @@ cudaError_t tc_inv_prepare(Plan& P) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   TcInvState* st = new TcInvState();
+  P.tc_inv_state = st;
   const bool bf = tc_bf16(P.prec);
   std::vector<unsigned char> img;
-  std::vector<std::vector<int64_t>> am_offs, l_offs;
-  std::vector<std::vector<int>> am_kcs;
-  std::vector<std::vector<int2>> lt;
-  std::vector<std::vector<double>> lcost;  // estimated bytes moved per tile
+  std::vector<int4> lt;
+  std::vector<double> lcost;  // estimated bytes moved per tile
+  std::vector<LegISeg> lsegs;
+  std::vector<RadISeg> rsegs;
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
     const HostTables& H = P.tables[s];
     const int B = sg.B, NB = sg.NB;
-    TcInvSeg ts;
-    ts.npad = pad16i(B);
+    LegISeg ls;
+    memset(&ls, 0, sizeof(ls));
+    ls.B = B, ls.NB = NB, ls.npad = pad16i(B), ls.w1_off = sg.w1_off;
+    st->npad_max = std::max(st->npad_max, ls.npad);
     // Legendre synthesis tables, per (|m|, j'-half of 64 rows):
     // [P hi][P lo][Q hi][Q lo], rows j', K = l'
-    const int nh = ts.npad > 64 ? 64 : ts.npad;
-    const int halves = (ts.npad + 63) / 64;
+    const int nh = ls.npad > 64 ? 64 : ls.npad;
+    const int halves = (ls.npad + 63) / 64;
     std::vector<int64_t> aoff(2 * B, 0);
     std::vector<int> akc(B, 0);
-    int kcmax = 1;
     for (int am = 0; am < B; ++am) {
       int kcs[2];
       for (int p = 0; p < 2; ++p) kcs[p] = (n_par(B, am, p) + 31) / 32;
@@ -865,27 +946,26 @@ cudaError_t tc_inv_prepare(Plan& P) {
         }
       }
       akc[am] = kcs[0] | (kcs[1] << 8);
-      kcmax = std::max(kcmax, kcs[0] + kcs[1]);
+      st->kcmax = std::max(st->kcmax, kcs[0] + kcs[1]);
     }
-    ts.kcmax = kcmax;
-    std::vector<int2> ltiles;
-    std::vector<double> lc;
     for (int mi = 0; mi < 2 * B - 1; ++mi) {
       const int am = mi < B - 1 ? B - 1 - mi : mi - (B - 1);
       const int kcs = (akc[am] & 0xff) + (akc[am] >> 8);
+      const int siP = (int)si_rows_before(B, mi, 0), siQ = (int)si_rows_before(B, mi, 1);
       for (int jh = 0; jh < halves; ++jh)
         for (int r0 = 0; r0 < NB * 2 * B; r0 += 128) {
-          ltiles.push_back(make_int2(mi, r0 | jh));
+          lt.push_back(make_int4(mi, r0, jh | ((int)s << 8), akc[am]));
+          lt.push_back(make_int4((int)aoff[2 * am + jh], siP, siQ, 0));
           // S chunks in, both G halves out, the table on its first tile
-          const int ncols = jh ? ts.npad - 64 : nh;
-          lc.push_back(kcs * 16384.0 + 1024.0 * ncols + (r0 == 0 ? 2.0 * kcs * nh * 128 : 0.0));
+          const int ncols = jh ? ls.npad - 64 : nh;
+          lcost.push_back(kcs * 16384.0 + 1024.0 * ncols + (r0 == 0 ? 2.0 * kcs * nh * 128 : 0.0));
         }
     }
     // radial inverse tables, per l: KC_l x [hi chunk][lo chunk], rows i (128), K = n'
-    std::vector<int64_t> loff(B, 0);
+    st->l_base.push_back((int)st->l_off.size());
     for (int l = 0; l < B; ++l) {
       img.resize((img.size() + 1023) / 1024 * 1024);
-      loff[l] = (int64_t)img.size();
+      st->l_off.push_back((int64_t)img.size());
       const int K = B - l, KC = (K + 31) / 32;
       for (int kc = 0; kc < KC; ++kc) {
         auto tv = [&](int i, int k) -> double {
@@ -899,59 +979,38 @@ cudaError_t tc_inv_prepare(Plan& P) {
     }
     // tensor map over S: [B^2 rows of l'][NB*2*B]
     float* w2 = (float*)P.d_w2 + sg.w2_off;
-    if (!make_map_2d(&ts.smap, w2, (uint64_t)NB * 2 * B, (uint64_t)B * B, 128, 32, CU_TENSOR_MAP_SWIZZLE_NONE)) {
-      delete st;
+    if (!make_map_2d(&ls.smap, w2, (uint64_t)NB * 2 * B, (uint64_t)B * B, 128, 32, CU_TENSOR_MAP_SWIZZLE_NONE))
       return cudaErrorInvalidValue;
-    }
-    st->segs.push_back(ts);
-    am_offs.push_back(aoff);
-    am_kcs.push_back(akc);
-    l_offs.push_back(loff);
-    lt.push_back(ltiles);
-    lcost.push_back(lc);
+    lsegs.push_back(ls);
+    rsegs.push_back(RadISeg{B, NB, sg.fn0, (int)sg.si_rows, sg.w2_off});
   }
+  if (img.size() >= (size_t)1 << 31) return cudaErrorInvalidValue;  // image offsets are 32-bit
   int64_t bytes = 0;
   cudaError_t e = upload(&st->d_img, img, bytes);
-  for (size_t s = 0; s < st->segs.size() && e == cudaSuccess; ++s) {
-    TcInvSeg& ts = st->segs[s];
-    const int B = P.segs[s].B;
-    e = upload(&ts.am_off, am_offs[s], bytes);
-    if (e == cudaSuccess) e = upload(&ts.am_kc, am_kcs[s], bytes);
-    if (e == cudaSuccess) e = upload(&ts.l_off, l_offs[s], bytes);
-    if (e == cudaSuccess) e = upload(&ts.leg_tiles, lt[s], bytes);
-    ts.leg_ntiles = (int)lt[s].size();
-    ts.leg_grid = std::min(ts.leg_ntiles, nsm);
-    int lmax = 0;
-    const std::vector<int> lf = balance_slices(lcost[s], std::max(ts.leg_grid, 1), &lmax);
-    if (e == cudaSuccess) e = upload(&ts.leg_first, lf, bytes);
-    lmax += 1;
-    if (e == cudaSuccess) e = radi_tiles(P, s, ts, nsm, bytes);
-    // tables, staging, operand ring, barrier slots, metadata (S row offsets,
-    // image offsets, chunk counts), tile slice
-    const size_t meta = (size_t)2 * (2 * B - 1) * 8 + (size_t)B * 12 + 8;
-    const int nh_s = ts.npad > 64 ? 64 : ts.npad;
-    ts.leg_smem = 1024 + (size_t)ts.kcmax * 2 * nh_s * (bf ? 64 : 128) + (size_t)kStagingLegI * kChunk +
-                  (size_t)kStagesLegI * 2 * kChunk + 64 * 8 + meta + (size_t)B * 8 + (size_t)lmax * 8;
-    if (ts.leg_smem > 227 * 1024) e = cudaErrorInvalidValue;
-  }
+  if (e == cudaSuccess) e = upload(&st->leg_tiles, lt, bytes);
+  if (e == cudaSuccess) e = upload(&st->leg_segs, lsegs, bytes);
+  if (e == cudaSuccess) e = upload(&st->rad_segs, rsegs, bytes);
+  st->leg_ntiles = (int)lcost.size();
+  // tables, staging, operand ring, barrier slots, segments, tile slice (32 bytes a tile)
+  const int nhm = st->npad_max > 64 ? 64 : st->npad_max;
+  const size_t lfixed = 1024 + (size_t)st->kcmax * 2 * nhm * (bf ? 64 : 128) + (size_t)kStagingLegI * kChunk +
+                        (size_t)kStagesLegI * 2 * kChunk + 64 * 8 + lsegs.size() * sizeof(LegISegSmall) + 16;
+  int lmax = 0;
+  const std::vector<int> lf = slices_for(lcost, nsm, lfixed, 32, &st->leg_grid, &lmax);
+  if (e == cudaSuccess) e = upload(&st->leg_first, lf, bytes);
+  st->leg_smem = lfixed + (size_t)(lmax + 1) * 32;
+  if (e == cudaSuccess && st->leg_smem > 227 * 1024) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess) e = radi_tiles(P, *st, nsm, bytes);
   P.bytes += bytes;
-  if (e != cudaSuccess) {
-    P.tc_inv_state = st;
-    return e;
-  }
-  P.tc_inv_state = st;
-  return cudaSuccess;
+  return e;
 }
 
 void tc_inv_release(Plan& P) {
   TcInvState* st = (TcInvState*)P.tc_inv_state;
   if (!st) return;
-  for (TcInvSeg& s : st->segs) {
-    void* ptrs[] = {s.leg_tiles, s.leg_first, s.am_off, s.am_kc, s.rad_tiles, s.rad_first, s.l_off};
-    for (void* p : ptrs)
-      if (p) cudaFree(p);
-  }
-  if (st->d_img) cudaFree(st->d_img);
+  void* ptrs[] = {st->d_img, st->leg_tiles, st->leg_first, st->leg_segs, st->rad_tiles, st->rad_first, st->rad_segs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
   delete st;
   P.tc_inv_state = nullptr;
 }
@@ -961,53 +1020,46 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
   TcInvState* st = (TcInvState*)P.tc_inv_state;
   if (!st) return cudaErrorNotSupported;
   StageTimer timer(P, prob == 2 ? ST_RAD_I : ST_LEG_I, s);
-  for (size_t k = 0; k < st->segs.size(); ++k) {
-    TcInvSeg& ts = st->segs[k];
-    const SegDesc& sg = P.segs[k];
-    cudaError_t e;
-    if (prob == 2) {
-      RadIArgs a;
-      a.tiles = ts.rad_tiles;
-      a.cta_first = ts.rad_first;
-      a.ntiles = ts.rad_ntiles;
-      a.tabimg = st->d_img;
-      a.l_off = ts.l_off;
-      a.si_rows = P.d_si_rows + sg.si_rows;
-      a.coef = (const float*)x;
-      a.fn_coef = P.d_fn_coef + sg.fn0;
-      a.s = (float*)y + sg.w2_off;
-      a.err = P.d_err;
-      a.B = sg.B;
-      a.NB = sg.NB;
-      a.nprod = tc_products(P.prec);
-      void (*fn)(RadIArgs) = tc_bf16(P.prec) ? tc_rad_inv_kernel<true> : tc_rad_inv_kernel<false>;
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.rad_smem);
-      if (e != cudaSuccess) return e;
-      fn<<<ts.rad_grid, kThreadsInv, ts.rad_smem, s>>>(a);
-    } else {
-      LegIArgs a;
-      a.tiles = ts.leg_tiles;
-      a.cta_first = ts.leg_first;
-      a.ntiles = ts.leg_ntiles;
-      a.tabimg = st->d_img;
-      a.am_off = ts.am_off;
-      a.am_kc = ts.am_kc;
-      a.si_rows = P.d_si_rows + sg.si_rows;
-      a.g = (float*)y + sg.w1_off;
-      a.err = P.d_err;
-      a.B = sg.B;
-      a.NB = sg.NB;
-      a.npad = ts.npad;
-      a.kcmax = ts.kcmax;
-      a.nprod = tc_products(P.prec);
-      void (*fn)(const CUtensorMap, LegIArgs) = tc_bf16(P.prec) ? tc_leg_inv_kernel<true> : tc_leg_inv_kernel<false>;
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts.leg_smem);
-      if (e != cudaSuccess) return e;
-      fn<<<ts.leg_grid, kThreadsInv, ts.leg_smem, s>>>(ts.smap, a);
-    }
-    e = cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (prob == 2 && st->rad_ntiles > 0) {
+    RadIArgs a;
+    a.tiles = st->rad_tiles;
+    a.cta_first = st->rad_first;
+    a.ntiles = st->rad_ntiles;
+    a.tabimg = st->d_img;
+    a.segs = st->rad_segs;
+    a.nseg = (int)P.segs.size();
+    a.si_rows = P.d_si_rows;
+    a.coef = (const float*)x;
+    a.fn_coef = P.d_fn_coef;
+    a.s = (float*)y;
+    a.err = P.d_err;
+    a.si_max = st->si_max;
+    a.nprod = tc_products(P.prec);
+    void (*fn)(RadIArgs) = tc_bf16(P.prec) ? tc_rad_inv_kernel<true> : tc_rad_inv_kernel<false>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->rad_smem);
     if (e != cudaSuccess) return e;
+    fn<<<st->rad_grid, kThreadsInv, st->rad_smem, s>>>(a);
+  } else if (prob == 3 && st->leg_ntiles > 0) {
+    LegIArgs a;
+    a.tiles = st->leg_tiles;
+    a.cta_first = st->leg_first;
+    a.ntiles = st->leg_ntiles;
+    a.tabimg = st->d_img;
+    a.segs = st->leg_segs;
+    a.nseg = (int)P.segs.size();
+    a.g = (float*)y;
+    a.err = P.d_err;
+    a.npad_max = st->npad_max;
+    a.kcmax = st->kcmax;
+    a.nprod = tc_products(P.prec);
+    void (*fn)(LegIArgs) = tc_bf16(P.prec) ? tc_leg_inv_kernel<true> : tc_leg_inv_kernel<false>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->leg_smem);
+    if (e != cudaSuccess) return e;
+    fn<<<st->leg_grid, kThreadsInv, st->leg_smem, s>>>(a);
   }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   timer.finish();
   return cudaSuccess;
 }
