@@ -16,7 +16,6 @@ size_t fft_smem_for(int prec, int n1, int n2, int B);
 void gemm_tile_dims(int& tm, int& tn, int& tk);
 cudaError_t tc_prepare(Plan& P);   // tensor-core tables and schedules (tc_gemm.cu)
 void tc_release(Plan& P);
-int tc_launches(const Plan& P);
 }  // namespace sgl
 
 using namespace sgl;
@@ -151,6 +150,12 @@ void sgl::pack_tables(const Plan& P, std::vector<real>& tab) {
 
 template void sgl::pack_tables<double>(const Plan& P, std::vector<double>& tab);
 template void sgl::pack_tables<float>(const Plan& P, std::vector<float>& tab);
+
+// Kernel launches of one forward (or inverse) call: the phi-FFT launches (the
+// larger of the two directions) and two stage launches.
+static void set_launch_count(Plan& P) {
+  P.launches_per_call = std::max(fft_launches(P, false), fft_launches(P, true)) + 2;
+}
 
 // FFT CTA lists of both directions (segment order) for the plan's current
 // ring pairs per CTA; replaces the previous lists.
@@ -334,8 +339,7 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
     e = tc_prepare(*P);
     if (e != cudaSuccess) return cuda_fail(P, e, "tensor-core preparation");
   }
-  P->launches_per_call = (int)P->segs.size() + 2;
-  if (tc_precision(P->prec)) P->launches_per_call = (int)P->segs.size() + tc_launches(*P);
+  set_launch_count(*P);
   return SGL_OK;
 }
 
@@ -625,6 +629,7 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
   e = build_fft_lists(*P);
   if (e == cudaSuccess && tc_precision(P->prec)) e = tc_radi_retile(*P);
   if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+  set_launch_count(*P);
   P->tuning = tuning_text(*P, cached ? "cache" : "timed");
   release_pipeline(P);  // sub-batch plans are rebuilt with the new configuration on next use
   if (!cached && cache_path) {

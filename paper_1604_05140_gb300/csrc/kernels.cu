@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sgl_internal.h"
 
 namespace sgl {
@@ -574,17 +576,37 @@ struct FftSlice {
   int first, count, n1, n2, B;
 };
 
+// Consecutive segments that run the same kernel instantiation with the same
+// ring pairs per CTA share one launch (each CTA reads its segment); B of a
+// slice is its largest bandlimit, which sizes the shared memory.
 static void fft_slices(const Plan& P, std::vector<FftSlice>& out, bool inv) {
   out.clear();
-  int first = 0;
+  int first = 0, last_cls = -1, last_jp = -1;
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
     const int JP = fft_jp(P, sg.B, inv);
     const int per_shell = (sg.B + JP - 1) / JP;
     const int count = sg.NB * sg.B * per_shell;
-    out.push_back({first, count, sg.n1, sg.n2, sg.B});
+    // kernel class: the register FFT for 2B = 16 * {8, 16}, else the general
+    // kernel of factor n1 with a run-time n2
+    const int cls = (sg.n1 == 16 && (sg.n2 == 8 || sg.n2 == 16)) ? 100 + sg.n2 : sg.n1;
+    if (!out.empty() && cls == last_cls && JP == last_jp) {
+      FftSlice& f = out.back();
+      f.count += count;
+      f.B = std::max(f.B, sg.B);
+    } else {
+      out.push_back({first, count, sg.n1, sg.n2, sg.B});
+    }
     first += count;
+    last_cls = cls;
+    last_jp = JP;
   }
+}
+
+int fft_launches(const Plan& P, bool inv) {
+  std::vector<FftSlice> sl;
+  fft_slices(P, sl, inv);
+  return (int)sl.size();
 }
 
 template <typename real>

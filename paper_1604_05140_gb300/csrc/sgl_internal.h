@@ -286,6 +286,9 @@ inline int fft_jp(const Plan& P, int B, bool inv) {
   return jp < B ? jp : B;
 }
 
+// phi-FFT launches of one call in direction inv (kernels.cu).
+int fft_launches(const Plan& P, bool inv);
+
 // Rebuilds the TF32x3 inverse radial tiles for P.radi_narrow (tc_inv.cu).
 cudaError_t tc_radi_retile(Plan& P);
 

@@ -725,13 +725,6 @@ void tc_release(Plan& P) {
   P.tc_state = nullptr;
 }
 
-int tc_launches(const Plan& P) {
-  // GEMM launches per call (forward or inverse): two stages, one launch each
-  // over every segment; FFT launches are counted by the caller
-  (void)P;
-  return 2;
-}
-
 cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted, cudaStream_t s) {
   if (prob != 0 && prob != 1) return run_tc_inverse(P, prob, x, y, s);
   TcState* st = (TcState*)P.tc_state;
