@@ -626,7 +626,7 @@ static cudaError_t run_fft(Plan& P, bool inv, const void* in, void* out, int mod
     a.JP = fft_jp(P, f.B, inv);
     a.mode = mode;
     {
-      Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode, f.count, P.d_err};
+      Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode};
       cudaError_t e16 = cudaSuccess;
       if (fft16_launch<real>(inv, a16, f.n1, f.n2, f.count, s, &e16)) {
         if (e16 != cudaSuccess) return e16;

@@ -260,8 +260,6 @@ struct Fft16Args {
   void* w1;
   int JP;                // ring pairs per CTA; blockDim = 16 * JP
   int mode;
-  int nitems;            // entries of ctas (persistent kernels loop over them)
-  int* err;              // plan error flag (bounded waits)
 };
 // Launches the specialized kernel when (n1, n2) = (16, 8) or (16, 16) and
 // returns true (launch status in *err); returns false otherwise.

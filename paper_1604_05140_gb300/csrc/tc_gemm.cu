@@ -1,4 +1,6 @@
-// TF32x3 tensor-core stages (tcgen05, TMEM, TMA) of the SGL transform.
+// Tensor-core forward stages (tcgen05, TMEM, TMA) of the SGL transform:
+// TF32x3 (and its hi*hi-only and BF16 hi/lo variants).  Each launch covers
+// every bandlimit segment of the plan: tiles carry their segment.
 //
 // Forward Legendre stage (Eq. DLT, one GEMM per order m and theta-parity p)
 // and forward radial stage (Eq. DRT_matrix, one GEMM per degree l):

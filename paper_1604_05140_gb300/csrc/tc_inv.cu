@@ -1,4 +1,5 @@
-// TF32x3 tensor-core inverse stages (tcgen05, TMEM, TMA) of the SGL transform.
+// Tensor-core inverse stages (tcgen05, TMEM, TMA) of the SGL transform:
+// TF32x3 (and its hi*hi-only and BF16 hi/lo variants).
 //
 // Inverse radial stage (iDRT, R_l^T of Sect. 3.3.2), one GEMM per degree l:
 //   S[i][col] = sum_{n'} T_{l+1+n',l}(i) fhat[col][n'],  col = (b, m, c)
@@ -11,8 +12,10 @@
 //   G_j' = P + Q,  G_{2B-1-j'} = P - Q   (Lambda(pi - theta) = (-1)^{l+m} Lambda(theta)).
 //   A operand: S rows, loaded l'-major by TMA into a staging ring and
 //   transposed to K-major hi/lo by the split warps; B operand: the table.
-// Same role layout as the forward kernels (tc_ptx.cuh): producer warp, TMEM
-// owner and MMA issuer warp, split warps, epilogue warps; bounded waits.
+// Same role layout as the forward kernels (tc_ptx.cuh): producer warp, two
+// MMA-issuing warps (the first owns tensor memory), split warps, epilogue
+// warps; bounded waits.  Each launch covers every bandlimit segment of the
+// plan: tiles carry their segment.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -90,7 +93,9 @@ __device__ __forceinline__ void split_store_bf(unsigned char* hi, unsigned char*
 // columns to let two tiles' accumulators fit tensor memory.  Tiles run in the
 // order (m, j'-half, rows): only the current half of the table is resident,
 // which leaves shared memory for a 4-deep staging ring; each row block is
-// read once per half.
+// read once per half.  The first MMA issuer takes the P chunks, the second
+// the Q chunks.
+
 // One bandlimit segment of a launch; a launch covers every segment of the
 // plan.  Aligned as its tensor map.
 struct LegISeg {
