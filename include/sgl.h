@@ -212,6 +212,18 @@ sgl_status sgl_autotune(sgl_plan_t plan, void* samples, void* coeffs, const char
  * rad_inv_narrow=65 source=timed"; valid until the next call on the plan. */
 const char* sgl_tuning(sgl_plan_t plan);
 
+/*
+ * sgl_selftest_wait - check the failure detection of the tensor-core kernels
+ * on the current device (an implementation aid; the paper has no
+ * counterpart).  Those kernels bound every wait on an mbarrier and, when a
+ * wait gives up, set the plan's error flag and end (sgl_check then returns
+ * SGL_ERR_TIMEOUT).  This call runs one small kernel whose wait can never be
+ * satisfied, with the bound limit_ns (1 .. 2e9 ns), and stores 1 in
+ * *gave_up when the wait gave up and the kernel ended as designed.
+ * Synchronous; SGL_ERR_ARG for a bad bound or a NULL pointer.
+ */
+sgl_status sgl_selftest_wait(int64_t limit_ns, int* gave_up);
+
 /* Message for the last failure on `plan` (or of plan creation when NULL).
  * The string stays valid until the next call on the same plan. */
 const char* sgl_last_error(sgl_plan_t plan);

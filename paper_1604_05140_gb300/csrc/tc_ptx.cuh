@@ -72,15 +72,17 @@ static __device__ __forceinline__ bool mbar_try_sleep(uint64_t* bar, uint32_t pa
   return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity.  On timeout, or when another
-// role already aborted, returns false.
-static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait for the phase of the given parity.  On timeout (limit_ns,
+// 2 s by default), or when another role already aborted, sets the abort flag
+// and returns false.
+static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                 uint64_t limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
     if (mbar_try_sleep(bar, parity, 100000u)) return true;
     if (*abort_flag) return false;
-    if (gtimer() - t0 > kWaitNs) {
+    if (gtimer() - t0 > limit_ns) {
       *abort_flag = 1;
       return false;
     }

@@ -78,6 +78,7 @@ def load_library():
         "sgl_forward_noalloc": (i32, [i32, i32, vp, vp, vp]),
         "sgl_autotune": (i32, [vp, vp, vp, ctypes.c_char_p, vp]),
         "sgl_tuning": (ctypes.c_char_p, [vp]),
+        "sgl_selftest_wait": (i32, [i64, ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -154,6 +155,14 @@ def sgl_autotune(plan, samples_ptr: int, coeffs_ptr: int, cache_path: Optional[s
 
 def sgl_tuning(plan) -> str:
     return load_library().sgl_tuning(plan).decode()
+
+
+def sgl_selftest_wait(limit_ns: int = 50_000_000) -> bool:
+    """True when a bounded device-side wait that can never be satisfied gave
+    up after limit_ns and its kernel ended (sgl_selftest_wait)."""
+    flag = ctypes.c_int(0)
+    _check(load_library().sgl_selftest_wait(int(limit_ns), ctypes.byref(flag)))
+    return bool(flag.value)
 
 
 def sgl_check(plan, stream: int = 0):

@@ -42,6 +42,8 @@ def test_version(lib):
     ((0, 1, 0, 0), sgl.SGL_ERR_ARG),        # B < 1
     ((8, 0, 0, 0), sgl.SGL_ERR_ARG),        # batch < 1
     ((8, 1, 9, 0), sgl.SGL_ERR_ARG),        # unknown precision
+    ((6, 1, 2, 0), sgl.SGL_ERR_UNSUPPORTED),    # tensor-core plans need 4 | B
+    ((6, 1, 4, 0), sgl.SGL_ERR_UNSUPPORTED),
     ((8, 1, 0, 5), sgl.SGL_ERR_ARG),        # unknown sample convention
     ((8, 1, 1, 1), sgl.SGL_ERR_ARG),        # physical samples need FP64
     ((17, 1, 0, 0), sgl.SGL_ERR_UNSUPPORTED),   # 2B = 2 * 17: odd factor > 16
@@ -67,7 +69,17 @@ def test_null_plan_queries(lib):
     assert lib.sgl_sample_count(None) == -1
     assert lib.sgl_coeff_offset(None, 0) == -1
     assert lib.sgl_forward(None, None, None, None) == sgl.SGL_ERR_ARG
+    assert lib.sgl_autotune(None, None, None, None, None) == sgl.SGL_ERR_ARG
+    assert lib.sgl_tuning(None) == b""
     lib.sgl_destroy(None)
+
+
+def test_selftest_wait_argument_errors(lib):
+    import ctypes
+    flag = ctypes.c_int(7)
+    assert lib.sgl_selftest_wait(0, ctypes.byref(flag)) == sgl.SGL_ERR_ARG            # no bound
+    assert lib.sgl_selftest_wait(3_000_000_000, ctypes.byref(flag)) == sgl.SGL_ERR_ARG  # above 2 s
+    assert lib.sgl_selftest_wait(1000, None) == sgl.SGL_ERR_ARG
 
 
 def test_supported_bandlimits_match_header_rule():
