@@ -37,8 +37,10 @@
  * 16 or more functions such a call runs in 8 chunks of functions, the copies
  * of one chunk (on a stream of the plan) overlapping the kernels of the
  * previous one (the first such call builds the chunk plans).  Device buffers
- * are used in place and the call is asynchronous (stream-ordered).  Inputs
- * are never modified.  The caller owns all data buffers; the plan owns its
+ * are used in place and the call is asynchronous (stream-ordered); they
+ * must be aligned to the complex element (16 bytes for SGL_FP64 plans, 8
+ * otherwise: the kernels move whole complex values), else the call returns
+ * SGL_ERR_ARG.  Inputs are never modified.  The caller owns all data buffers; the plan owns its
  * tables and workspace.
  *
  * Errors: argument errors are found before any work is queued and returned
@@ -255,7 +257,7 @@ void sgl_destroy(sgl_plan_t plan);
  *   samples  device pointer, batch x 4B^3 complex doubles (weighted samples).
  *   coeffs   device pointer, batch x Omega complex doubles; overwritten.
  *            Host pointers are rejected (SGL_ERR_ARG): staging them would
- *            need device memory.
+ *            need device memory; so are pointers not 16-byte aligned.
  *   stream   stream the kernels are launched on.
  *
  * Set-up: the first call on a device looks up the device addresses of the

@@ -180,7 +180,7 @@ static cudaError_t build_fft_lists(Plan& P) {
     const SegDesc& sg = P.segs[s];
     const int JP = fft_jp(P, sg.B, true);
     if (tc_precision(P.prec)) {
-      // the tensor-core Legendre synthesis stores spectra [m][b][c][j][i]: each
+      // the tensor-core Legendre synthesis stores spectra [m][b][j][i][c]: each
       // inverse-FFT CTA takes JP consecutive shells of one ring pair (layout 1)
       for (int b = 0; b < sg.NB; ++b)
         for (int i0 = 0; i0 < sg.B; i0 += JP)
@@ -482,6 +482,10 @@ static sgl_status execute(Plan* P, bool is_fwd, bool weights, const void* in, vo
   const size_t in_bytes = (is_fwd ? P->n_samples : P->n_coeffs) * cb;
   const size_t out_bytes = (is_fwd ? P->n_coeffs : P->n_samples) * cb;
   const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
+  if ((in_dev && (uintptr_t)in % cb) || (out_dev && (uintptr_t)out % cb)) {
+    if (cur != P->device) cudaSetDevice(cur);
+    return fail(P, SGL_ERR_ARG, "device data pointers must be aligned to the complex element size");
+  }
   const void* din = in;
   void* dout = out;
   sgl_status st = SGL_OK;
@@ -814,6 +818,8 @@ sgl_status sgl_autotune(sgl_plan_t plan, void* samples, void* coeffs, const char
   if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
   if (!samples || !coeffs || !is_device_ptr(samples) || !is_device_ptr(coeffs))
     return fail(P, SGL_ERR_ARG, "sgl_autotune needs device buffers for samples and coefficients");
+  if ((uintptr_t)samples % complex_bytes(*P) || (uintptr_t)coeffs % complex_bytes(*P))
+    return fail(P, SGL_ERR_ARG, "device data pointers must be aligned to the complex element size");
   if (P->latched != SGL_OK) return (sgl_status)P->latched;
   int cur = 0;
   cudaGetDevice(&cur);

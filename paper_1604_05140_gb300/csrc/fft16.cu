@@ -19,7 +19,8 @@ namespace sgl {
 namespace {
 
 template <typename real>
-struct c2 {
+// aligned as a whole value, so that loads and stores move (re, im) at once
+struct alignas(2 * sizeof(real)) c2 {
   real x, y;
 };
 
@@ -241,8 +242,8 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
   const int B = sg.B, NB = sg.NB;
   // cta.w = 0: spectra stored [m][b][c][i][j]; the CTA owns shell i and ring
   //            pairs j0 .. j0+JP-1 (cta.y = b*B + i, cta.z = j0);
-  // cta.w = 1: spectra stored [m][b][c][j][i]; the CTA owns shells
-  //            i0 .. i0+JP-1 and the single ring pair jp (cta.y = b*B + i0, cta.z = jp)
+  // cta.w = 1: spectra stored [m][b][j][i][c] (complex pairs); the CTA owns
+  //            shells i0 .. i0+JP-1 and the single ring pair jp (cta.y = b*B + i0, cta.z = jp)
   const int lay = cta.w;
   const int b = cta.y / B, i_or_i0 = cta.y - b * B, j_or_jp = cta.z;
   const int JPmax = a.JP;
@@ -261,24 +262,44 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
     const int iq = lay ? i_or_i0 + q : i_or_i0;
     const int jA = lay ? j_or_jp : j_or_jp + q;
     const int jB = N - 1 - jA;
-    // element (m_idx, c, j) of ring (b, iq): m_idx*sm + c*sc + base + j*sj
-    const int64_t sm = (int64_t)NB * 2 * B * N;
-    const int64_t sc = (int64_t)B * N;
-    const int64_t sj = lay ? B : 1;
-    const int64_t base = lay ? ((int64_t)b * 2 * B * N + iq) : ((((int64_t)b * 2) * B + iq) * N);
-    const int64_t oA = base + jA * sj, oB = base + jB * sj;
     c2<real> x0[N2], x1[N2];
+    if (lay) {
+      // complex element (m_idx, j, i) of function b: m_idx*sm + b*N*B + j*B + i
+      const c2<real>* gc = reinterpret_cast<const c2<real>*>(g);
+      const int64_t sm = (int64_t)NB * N * B;
+      const int64_t base = (int64_t)b * N * B + iq;
+      const int64_t oA = base + (int64_t)jA * B, oB = base + (int64_t)jB * B;
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) {
-      const int k = k1 + 16 * k2;
-      if (k == B) {
-        x0[k2] = {0, 0};
-        x1[k2] = {0, 0};
-      } else {
-        const int m = k < B ? k : k - N;
-        const int64_t o = (int64_t)(m + B - 1) * sm;
-        x0[k2] = {g[o + oA], g[o + sc + oA]};
-        x1[k2] = {g[o + oB], g[o + sc + oB]};
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int k = k1 + 16 * k2;
+        if (k == B) {
+          x0[k2] = {0, 0};
+          x1[k2] = {0, 0};
+        } else {
+          const int m = k < B ? k : k - N;
+          const int64_t o = (int64_t)(m + B - 1) * sm;
+          x0[k2] = gc[o + oA];
+          x1[k2] = gc[o + oB];
+        }
+      }
+    } else {
+      // element (m_idx, c, j) of ring (b, iq): m_idx*sm + c*sc + base + j
+      const int64_t sm = (int64_t)NB * 2 * B * N;
+      const int64_t sc = (int64_t)B * N;
+      const int64_t base = (((int64_t)b * 2) * B + iq) * N;
+      const int64_t oA = base + jA, oB = base + jB;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int k = k1 + 16 * k2;
+        if (k == B) {
+          x0[k2] = {0, 0};
+          x1[k2] = {0, 0};
+        } else {
+          const int m = k < B ? k : k - N;
+          const int64_t o = (int64_t)(m + B - 1) * sm;
+          x0[k2] = {g[o + oA], g[o + sc + oA]};
+          x1[k2] = {g[o + oB], g[o + sc + oB]};
+        }
       }
     }
     fft_n<real, N2, true>(x0);

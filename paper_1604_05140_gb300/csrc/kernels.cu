@@ -22,7 +22,8 @@ namespace sgl {
 // complex helpers
 // ---------------------------------------------------------------------------
 template <typename real>
-struct cx {
+// aligned as a whole value, so that loads and stores move (re, im) at once
+struct alignas(2 * sizeof(real)) cx {
   real x, y;
 };
 
@@ -232,7 +233,8 @@ __global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
   }
 }
 
-// Inverse: G[m][b][c][i][j] of rings j0..j0+JP-1 and their mirrors -> samples.
+// Inverse: G[m][b][c][i][j] (layout 0) or G[m][b][j][i][c] (layout 1) of
+// the CTA's rings -> samples.
 template <typename real, int N1, int N2C>
 __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -276,8 +278,9 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
     const int m = m_idx - (B - 1);
     const int k = m >= 0 ? m : N + m;
     const int i = ring_i(r), j = ring_j(r);
-    const int64_t fc = (((int64_t)m_idx * NB + b) * 2 + c) * B * N;  // start of (m_idx, b, c)
-    const real v = g[fc + (lay ? (int64_t)j * B + i : (int64_t)i * N + j)];
+    // layout 0: [m_idx][b][c][i][j]; layout 1: [m_idx][b][j][i][c]
+    const real v = lay ? g[(((int64_t)m_idx * NB + b) * N + j) * (2 * B) + 2 * i + c]
+                       : g[(((int64_t)m_idx * NB + b) * 2 + c) * B * N + (int64_t)i * N + j];
     const int c1 = k / n2, c2 = k - c1 * n2;
     (c ? sim : sre)[r * pitch + c1 * (n2 + 1) + c2] = v;
   }

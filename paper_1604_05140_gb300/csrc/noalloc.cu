@@ -187,6 +187,8 @@ extern "C" sgl_status sgl_forward_noalloc(int B, int batch, const void* samples,
                                          std::to_string(kScratchDoubles));
   if (!device_pointer(samples) || !device_pointer(coeffs))
     return fail(SGL_ERR_ARG, "sgl_forward_noalloc takes device pointers only");
+  if ((uintptr_t)samples % 16 || (uintptr_t)coeffs % 16)
+    return fail(SGL_ERR_ARG, "data pointers must be aligned to the complex element size (16 bytes)");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(SGL_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));

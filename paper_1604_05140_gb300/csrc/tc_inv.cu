@@ -5,9 +5,10 @@
 //   S[i][col] = sum_{n'} T_{l+1+n',l}(i) fhat[col][n'],  col = (b, m, c)
 //   A operand: the table, M = 128 rows i, streamed per K chunk by bulk copy;
 //   B operand: coefficients gathered by the split warps (N = 128 columns).
-//   Output rows i are contiguous in the Legendre stage's input layout.
+//   S is stored [l'][b][i][c]: the (re, im) columns of one (b, m) go out as
+//   one 8-byte pair per radius.
 // Inverse Legendre stage (the inner sum of Eq. iSFFT_rearranged), one tile
-// per (m, 128 rows (b, c, i)) with both theta-parities:
+// per (m, 128 rows (b, i, c)) with both theta-parities:
 //   P[row][j'] = sum_{l' even} S[row][l'] Lambda(theta_j'),  Q likewise for odd,
 //   G_j' = P + Q,  G_{2B-1-j'} = P - Q   (Lambda(pi - theta) = (-1)^{l+m} Lambda(theta)).
 //   A operand: S rows, loaded l'-major by TMA into a staging ring and
@@ -118,7 +119,7 @@ struct LegIArgs {
   const unsigned char* tabimg;
   const LegISeg* segs;
   int nseg;
-  float* g;                   // output, per segment layout [m_idx][b][c][j < 2B][i]
+  float* g;                   // output, per segment layout [m_idx][b][j < 2B][i][c]
   int* err;
   int npad_max, kcmax;        // over the segments
   int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
@@ -344,10 +345,11 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
       const float sgn = (m < 0 && (am & 1)) ? -1.f : 1.f;
       const int jh = ta.z & 1;
       const int ncols = jh ? npad - 64 : nh;
+      // row (b, i, c): G element (m_idx, b, j, i, c) at stride 2B in j
       const int grow = ta.y + r_in;
       const bool valid = grow < NB * 2 * B;
-      const int b = grow / (2 * B), cc = (grow / B) & 1, i = grow % B;
-      float* out = a.g + sg.w1_off + (((int64_t)m_idx * NB + b) * 2 + cc) * (2 * B) * B + i;
+      const int b = grow / (2 * B), ic = grow - b * (2 * B);
+      float* out = a.g + sg.w1_off + ((int64_t)m_idx * NB + b) * (2 * B) * (2 * B) + ic;
       const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
       const uint32_t dP = tmem + (uint32_t)(4 * acc * nhm) + lanes;
       const uint32_t dQ = dP + (uint32_t)(2 * nh);
@@ -370,8 +372,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
           for (int k = 0; k < 16; ++k) {
             const int j = jh * 64 + c0 + k;
             if (j < B) {
-              out[(int64_t)j * B] = sgn * (P[k] + Q[k]);
-              out[(int64_t)(2 * B - 1 - j) * B] = sgn * (P[k] - Q[k]);
+              out[(int64_t)j * (2 * B)] = sgn * (P[k] + Q[k]);
+              out[(int64_t)(2 * B - 1 - j) * (2 * B)] = sgn * (P[k] - Q[k]);
             }
           }
         }
@@ -417,7 +419,7 @@ struct RadIArgs {
   const int64_t* si_rows;     // S row offset per (m_idx, p), per segment from si0
   const float* coef;          // complex interleaved coefficients
   const int64_t* fn_coef;     // coefficient offset per function (plan order of segments)
-  float* s;                   // output S, per segment layout [m_idx][p][l'][b][c][i]
+  float* s;                   // output S, per segment layout [m_idx][p][l'][b][i][c]
   int* err;
   int si_max;                 // shared-memory entries for the S row offsets of one CTA's segments
   int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
@@ -676,18 +678,19 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       const int per_b = (2 * l + 1) * 2;
       const uint32_t dq = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quarter * 32) << 16);
       for (int c0 = 16 * ehalf; c0 < width; c0 += 32) {
-        // lane k < 16 finds the S offset of column c0 + k (b, m, c); the
-        // stores take it by shuffle
+        // lane k < 8 finds the S offset of the column pair c0 + 2k, c0 + 2k + 1
+        // ((b, m), re and im: column pairs never straddle (b, m), as tiles
+        // start at even columns); the stores take it by shuffle
         int64_t o = -1;
         {
-          const int col = col0 + c0 + (lane & 15);
+          const int col = col0 + c0 + 2 * (lane & 7);
           if (col < NB * per_b) {
             const int b = col / per_b, rem = col - b * per_b;
-            const int m = (rem >> 1) - l, cc = rem & 1;
+            const int m = (rem >> 1) - l;
             const int am = m < 0 ? -m : m;
             const int p = (l - am) & 1;
             const int64_t srow = si[2 * (m + B - 1) + p] + ((l - am - p) >> 1);
-            o = srow * ((int64_t)NB * 2 * B) + ((int64_t)b * 2 + cc) * B;
+            o = srow * ((int64_t)NB * 2 * B) + (int64_t)b * 2 * B;
           }
         }
         float v[16];
@@ -704,9 +707,9 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
           else tmem_ld16(tc, v);
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
           const int64_t ok = __shfl_sync(0xffffffffu, o, k);
-          if (i < B && ok >= 0) sout[ok + i] = v[k];
+          if (i < B && ok >= 0) *(float2*)(sout + ok + 2 * i) = make_float2(v[2 * k], v[2 * k + 1]);
         }
       }
       tc_before();

@@ -228,6 +228,28 @@ def test_inputs_not_modified():
     assert torch.equal(c, c0) and torch.equal(s, s0)
 
 
+@pytest.mark.parametrize("prec,ctype", [("fp64", torch.complex128), ("tf32x3", torch.complex64)])
+def test_misaligned_device_pointers_are_rejected(prec, ctype):
+    # the kernels move whole complex values: a device pointer off the complex
+    # element's alignment is an argument error, found before any launch, and
+    # the plan keeps working
+    from paper_1604_05140_gb300 import sgl
+    B = 8
+    p = _plan(B, 1, prec)
+    c = _dev(inputs.random_coeffs(B, 1, seed=6), ctype)
+    s = p.inverse(c)
+    raw = torch.empty(2 * s.numel() + 8, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+    shift = raw.element_size()  # one real past the complex alignment
+    st = p.lib.sgl_forward(p.handle, raw.data_ptr() + shift, c.data_ptr(), None)
+    assert st == sgl.SGL_ERR_ARG
+    st = p.lib.sgl_inverse(p.handle, c.data_ptr(), raw.data_ptr() + shift, None)
+    assert st == sgl.SGL_ERR_ARG
+    torch.cuda.synchronize()
+    back = p.forward(s)
+    tol = FP64_TOL if prec == "fp64" else 2e-6
+    assert _err(back.cpu().numpy(), c.cpu().numpy()) < tol
+
+
 # ---------------------------------------------------------------------------
 # split precision: TF32x3 tensor-core stages
 # ---------------------------------------------------------------------------
