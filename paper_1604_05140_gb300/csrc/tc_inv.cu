@@ -36,7 +36,12 @@ constexpr int kThreadsInv = kRoleThreads;
 constexpr int kChunk = 128 * 128;   // 128 rows x 32 floats
 constexpr int kStagesLegI = 2;    // operand ring of the Legendre synthesis
 constexpr int kStagingLegI = 4;   // TMA staging ring of the Legendre synthesis
-constexpr int kStagesRadI = 3;
+constexpr int kStagesRadI = 2;
+// coefficient gather of the inverse radial stage: chunks in flight per split
+// thread (asynchronous copies), and staging slots ([16 values][256 threads])
+constexpr int kGatherDepth = 2;
+constexpr int kGatherSlots = kGatherDepth + 1;
+constexpr int kGatherSlotBytes = 16 * 256 * 4;
 
 // 128-byte swizzled K-major position of (row, 16-byte chunk q) in a tile
 __device__ __forceinline__ int sw_pos(int row, int q) { return row * 128 + ((q ^ (row & 7)) << 4); }
@@ -425,10 +430,23 @@ struct RadIArgs {
   int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
 };
 
+// Function of split thread tid's column (b, m, c) in tile tl (fn0 + b), or
+// -1 past the segment's columns.
+__device__ __forceinline__ int rad_fn_of(const RadISeg& sg, int4 tl, int tid) {
+  const int l = tl.x;
+  const bool nar = tl.y & 1;
+  const int per_b = (2 * l + 1) * 2;
+  const int col = (tl.y & ~1) + (nar ? (tid & 63) : (tid & 127));
+  return col < sg.NB * per_b ? sg.fn0 + col / per_b : -1;
+}
+
 // Coefficients of one K chunk (32 degrees n) of one tile column, gathered by
-// split thread tid: 16 (wide tile) or 8 (narrow tile) consecutive degrees.
-__device__ __forceinline__ void rad_gather(const RadIArgs& a, const RadISeg& sg, int4 tl, int kc, int tid,
-                                           float* v) {
+// split thread tid: 16 (wide tile) or 8 (narrow tile) consecutive degrees,
+// copied asynchronously to slot[k * 256 + tid] (zeros past the degree range
+// or the segment's columns).  fco is the coefficient offset of the column's
+// function (fn_coef, fetched a tile ahead by the caller).
+__device__ __forceinline__ void rad_gather_async(const RadIArgs& a, const RadISeg& sg, int4 tl, int kc, int tid,
+                                                 int64_t fco, float* slot) {
   const int B = sg.B, l = tl.x;
   const bool nar = tl.y & 1;
   const int col_in = nar ? (tid & 63) : (tid & 127);
@@ -440,14 +458,15 @@ __device__ __forceinline__ void rad_gather(const RadIArgs& a, const RadISeg& sg,
   const int b = valid ? col / per_b : 0;
   const int rem = col - b * per_b;
   const int m = (rem >> 1) - l, cc = rem & 1;
-  const float* cf = a.coef + 2 * a.fn_coef[sg.fn0 + b] + cc;
+  const float* cf = a.coef + 2 * fco + cc;
   const int np0 = kc * 32 + h * nv;        // degree n = l + 1 + n'
   int n = l + 1 + np0;
   int64_t off = omega_of(n, l, m);          // omega(n + 1) - omega(n) = n^2
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     if (k < nv) {
-      v[k] = (valid && np0 + k < B - l) ? cf[2 * off] : 0.f;
+      const bool in = valid && np0 + k < B - l;
+      cp_async4(slot + k * 256 + tid, in ? cf + 2 * off : a.coef, in);
       off += (int64_t)n * n;
       ++n;
     }
@@ -464,7 +483,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   // parts use their first 8 KB; data halves of 64 columns are 64 hi rows over
   // 64 lo rows, 16 KB (TF32) or 8 KB (BF16) each)
   unsigned char* st = base;
-  uint64_t* bars = (uint64_t*)(st + kStagesRadI * 4 * kChunk);
+  float* gslots = (float*)(st + kStagesRadI * 4 * kChunk);  // gather staging slots
+  uint64_t* bars = (uint64_t*)((unsigned char*)gslots + kGatherSlots * kGatherSlotBytes);
   uint64_t* tfull = bars;                   // [S] table chunk landed
   uint64_t* split = tfull + kStagesRadI;    // [S] data ready (split threads)
   uint64_t* empty = split + kStagesRadI;    // [S] MMAs done
@@ -617,13 +637,43 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       }
     }
   } else if (warp < kFirstEpiWarp) {
-    // gather: thread (column, h) loads 16 (wide) or 8 (narrow) consecutive
-    // degrees of its column per chunk; the next chunk's loads are issued
-    // before the current chunk is split and stored
+    // gather: thread (column, h) copies 16 (wide) or 8 (narrow) consecutive
+    // degrees of its column per chunk into a staging slot, kGatherDepth
+    // chunks ahead of the chunk it splits and stores (asynchronous copies: no
+    // registers held while they are in flight).  The coefficient offset of
+    // the column's function is fetched a tile ahead of the copies.
     const int tid = threadIdx.x - 32 * kFirstSplitWarp;
-    float v[16], vn[16];
+    auto fetch_fco = [&](int tt) -> int64_t {
+      if (tt >= nt) return 0;
+      const int f = rad_fn_of(s_seg[s_tiles[tt].z], s_tiles[tt], tid);
+      return f >= 0 ? a.fn_coef[f] : 0;
+    };
+    // copy cursor: tile ti, chunk kci, chunks issued ci
+    int ti = 0, kci = 0;
+    uint32_t ci = 0;
+    int64_t fco_i = 0, fco_n = 0;  // tiles ti and ti + 1
+    if (nt > 0) {
+      fco_i = fetch_fco(0);
+      fco_n = fetch_fco(1);
+    }
+    auto issue_next = [&]() {
+      if (ti < nt) {
+        const int4 tl = s_tiles[ti];
+        const RadISeg& sg = s_seg[tl.z];
+        rad_gather_async(a, sg, tl, kci, tid, fco_i, gslots + (ci % kGatherSlots) * (kGatherSlotBytes / 4));
+        if (++kci == (sg.B - tl.x + 31) / 32) {
+          kci = 0;
+          ++ti;
+          fco_i = fco_n;
+          fco_n = fetch_fco(ti + 1);
+        }
+      }
+      cp_async_commit();  // one group per chunk, empty past the end
+      ++ci;
+    };
+#pragma unroll
+    for (int d = 0; d < kGatherDepth; ++d) issue_next();
     int t = 0, kc = 0;
-    if (nt > 0) rad_gather(a, s_seg[s_tiles[0].z], s_tiles[0], 0, tid, v);
     for (uint32_t c = 0; t < nt; ++c) {
       const int4 tl = s_tiles[t];
       const bool nar = tl.y & 1;
@@ -632,7 +682,15 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
         tn = t + 1;
         kcn_next = 0;
       }
-      if (tn < nt) rad_gather(a, s_seg[s_tiles[tn].z], s_tiles[tn], kcn_next, tid, vn);
+      // chunk c landed (the kGatherDepth - 1 later groups may still be in
+      // flight); its values to registers, then the slot read one chunk ago
+      // is refilled with chunk c + kGatherDepth
+      cp_async_wait<kGatherDepth - 1>();
+      float v[16];
+      const float* gv = gslots + (c % kGatherSlots) * (kGatherSlotBytes / 4) + tid;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = gv[k * 256];
+      issue_next();
       const int s = c % kStagesRadI;
       if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) break;
       // B operand: per half of 64 columns, 64 hi rows then 64 lo rows
@@ -652,11 +710,10 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       }
       fence_proxy_async();
       mbar_arrive(split + s);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = vn[k];
       t = tn;
       kc = kcn_next;
     }
+    cp_async_wait_all();  // no copy may land after the CTA has left
   } else {
     const int quarter = warp & 3;
     const int ehalf = (warp - kFirstEpiWarp) >> 2;  // alternate 16-column blocks
@@ -862,8 +919,8 @@ static cudaError_t radi_tiles(const Plan& P, TcInvState& st, int nsm, int64_t& b
   // shared memory: stages, barrier slots, the segments of the slice, their S
   // row offsets (si_max entries: the most any CTA's segments need), the tile
   // slice; more waves of CTAs while that does not fit
-  const size_t fixed = 1024 + (size_t)kStagesRadI * 4 * kChunk + 64 * 8 + (P.segs.size() + 1) * (sizeof(RadISeg) + 4) +
-                       8 + 16;
+  const size_t fixed = 1024 + (size_t)kStagesRadI * 4 * kChunk + (size_t)kGatherSlots * kGatherSlotBytes + 64 * 8 +
+                       (P.segs.size() + 1) * (sizeof(RadISeg) + 4) + 8 + 16;
   const int n = (int)rc.size();
   st.rad_grid = std::max(1, std::min(n, nsm));
   std::vector<int> rf;
