@@ -282,6 +282,45 @@ def time_path(precision, steps, warmup, ws, rank, profile=True):
     return plan, ms, stage, clocks, err, launches, (c_np, c, s, c2)
 
 
+def real_path(steps, warmup):
+    """Real functions: 64 real functions of B=128 in one TF32x3 plan of real
+    functions (two per complex transform, separated by the coefficient
+    symmetry of real functions).  Round trip on coefficients of real
+    functions (the symmetric part of random decaying coefficients, obtained
+    by one round trip), timed with CUDA events like the main workload."""
+    import torch
+    from paper_1604_05140_gb300 import Plan, inputs
+    plan = Plan(B_BENCH, BATCH, "tf32x3", samples="real")
+    if TUNE:
+        plan.autotune()
+    c0 = torch.from_numpy(inputs.random_coeffs(B_BENCH, BATCH, seed=inputs.BASE_SEED + 5, decay=True)).to(
+        torch.complex64).cuda()
+    s = torch.empty(plan.sample_shape, dtype=plan.sample_dtype, device="cuda")
+    c = torch.empty(plan.coeff_shape, dtype=plan.dtype, device="cuda")
+    c2 = torch.empty_like(c)
+    plan.inverse(c0, out=s)
+    plan.forward(s, out=c)  # coefficients of real functions
+    for _ in range(max(1, warmup)):
+        plan.inverse(c, out=s)
+        plan.forward(s, out=c2)
+    torch.cuda.synchronize()
+    err = float((c2 - c).abs().max().item() / c.abs().max().item())
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        plan.inverse(c, out=s)
+        plan.forward(s, out=c2)
+    ev1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    ms = ev0.elapsed_time(ev1) / steps
+    return {"workload": f"{BATCH} real functions, B={B_BENCH}, TF32x3, two per complex transform",
+            "value": BATCH / (ms * 1e-3), "unit": "transforms/s", "ms_per_step": ms, "steps": steps,
+            "round_trip_max_rel_err": err, "launches_per_round_trip": 2 * plan.launches_per_call,
+            "sample_bytes_per_function": 4 * B_BENCH ** 3 * 4}
+
+
 def uneven_path(steps, warmup):
     """The batching workload: 256 functions with bandlimits uniform in
     {16, 24, ..., 128} in one TF32x3 plan, round trip captured in one CUDA
@@ -458,6 +497,7 @@ def run_ours(args):
             del v_plan
     if not args.no_variants and args.precision == "tf32x3" and ws == 1:
         line["uneven_batch"] = uneven_path(max(3, min(args.steps, 20)), args.warmup)
+        line["real_functions"] = real_path(max(3, min(args.steps, 20)), args.warmup)
     if "fp64" in results and args.precision != "fp64":
         r = results["fp64"]
         line["fp64_path"] = {"value": r["value"], "unit": "transforms/s", "ms_per_step": r["ms"],

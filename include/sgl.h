@@ -93,8 +93,33 @@ typedef enum {
 
 typedef enum {
   SGL_SAMPLES_WEIGHTED = 0, /* samples are exp(-r^2/2) f(x) */
-  SGL_SAMPLES_PHYSICAL = 1  /* samples are f(x); SGL_FP64 plans only */
+  SGL_SAMPLES_PHYSICAL = 1, /* samples are f(x); SGL_FP64 plans only */
+  SGL_SAMPLES_REAL = 2      /* real f: samples exp(-r^2/2) f(x) as reals (see below) */
 } sgl_samples;
+
+/*
+ * Real functions (SGL_SAMPLES_REAL, sgl_plan only, every precision).  For a
+ * real f the coefficients obey fhat_{n,l,-m} = (-1)^m conj(fhat_{n,l,m})
+ * (Def 2.1: Y_l^{-m} = (-1)^m conj(Y_l^m), real radial part), so a real
+ * function carries half the information of a complex one.  Such a plan
+ * transforms the functions two at a time as the real and imaginary parts of
+ * one complex function and separates the two coefficient sets with that
+ * symmetry: about half the work and half the sample bytes per function.
+ *   samples      [batch][i][j][k] reals (double for SGL_FP64, else float),
+ *                weighted as SGL_SAMPLES_WEIGHTED; sgl_sample_count counts
+ *                reals, and sample pointers need the real type's alignment;
+ *   coefficients the full complex layout above (both signs of m).
+ *   sgl_forward  the coefficients of the real functions (obeying the
+ *                symmetry up to rounding);
+ *   sgl_inverse  the real part of the inverse transform of the given
+ *                coefficients (the inverse of their symmetric part), so any
+ *                coefficient array is accepted;
+ *   sgl_adjoint  the adjoints of these two maps for the real inner product
+ *                on samples and Re <u, v> on coefficients: of_inverse == 0
+ *                gives the real part of the complex adjoint, of_inverse != 0
+ *                the complex adjoint of real samples.
+ * Host buffers are staged in one piece (no chunked overlap).
+ */
 
 /* Largest supported bandlimit.  2B must factor as 2^a * q with 2^a <= 16
  * (the power of two capped at 16) and q <= 16; every B <= 16 and every
@@ -107,7 +132,8 @@ typedef enum {
  *   B        bandlimit, 1 <= B <= SGL_MAX_B (see above for the factor rule).
  *   batch    number of functions per call, >= 1.
  *   prec     an sgl_precision.
- *   samples  an sgl_samples; SGL_SAMPLES_PHYSICAL requires SGL_FP64.
+ *   samples  an sgl_samples; SGL_SAMPLES_PHYSICAL requires SGL_FP64;
+ *            SGL_SAMPLES_REAL makes a plan for `batch` real functions.
  * Builds the FP64 tables on the host (nodes and weights of Thm 3.1 and of the
  * radial Gauss-Laguerre rule; Legendre functions, Def 2.1 and Eq.
  * legendre_recurrence; radial functions, Lemma 3.7), uploads them and

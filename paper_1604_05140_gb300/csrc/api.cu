@@ -70,7 +70,7 @@ static void release(Plan* P) {
   if (!P->owns_err) P->d_err = nullptr;
   void* ptrs[] = {P->d_tab, P->d_tab_lo, P->d_w1, P->d_w2, P->d_stage_in, P->d_stage_out, P->d_segs,
                   P->d_fn_samp, P->d_fn_coef, P->d_si_rows, P->d_err, P->leg_fwd.d_tiles, P->rad_fwd.d_tiles,
-                  P->rad_inv.d_tiles, P->leg_inv.d_tiles, P->d_fft_fwd, P->d_fft_inv};
+                  P->rad_inv.d_tiles, P->leg_inv.d_tiles, P->d_fft_fwd, P->d_fft_inv, P->d_ccoef};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);
@@ -154,7 +154,7 @@ template void sgl::pack_tables<float>(const Plan& P, std::vector<float>& tab);
 // Kernel launches of one forward (or inverse) call: the phi-FFT launches (the
 // larger of the two directions) and two stage launches.
 static void set_launch_count(Plan& P) {
-  P.launches_per_call = std::max(fft_launches(P, false), fft_launches(P, true)) + 2;
+  P.launches_per_call = std::max(fft_launches(P, false), fft_launches(P, true)) + 2 + (P.real_pairs ? 1 : 0);
 }
 
 // FFT CTA lists of both directions (segment order) for the plan's current
@@ -353,6 +353,10 @@ static bool is_device_ptr(const void* p) {
 }
 
 static size_t complex_bytes(const Plan& P) { return P.prec == SGL_FP64 ? 16 : 8; }
+// bytes of one element of the user's sample array (a real for real-function plans)
+static size_t sample_bytes(const Plan& P) { return P.real_pairs ? complex_bytes(P) / 2 : complex_bytes(P); }
+// functions as the user counts them
+static int user_fns(const Plan& P) { return P.real_pairs ? P.nreal : P.nfn; }
 
 static sgl_status ensure_stage(Plan& P, void** buf, size_t* have, size_t need) {
   if (*have >= need) return SGL_OK;
@@ -478,19 +482,20 @@ static sgl_status execute(Plan* P, bool is_fwd, bool weights, const void* in, vo
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != P->device) cudaSetDevice(P->device);
-  const size_t cb = complex_bytes(*P);
-  const size_t in_bytes = (is_fwd ? P->n_samples : P->n_coeffs) * cb;
-  const size_t out_bytes = (is_fwd ? P->n_coeffs : P->n_samples) * cb;
+  const size_t cb = complex_bytes(*P), sb = sample_bytes(*P);
+  const size_t in_bytes = is_fwd ? P->n_samples * sb : P->n_coeffs * cb;
+  const size_t out_bytes = is_fwd ? P->n_coeffs * cb : P->n_samples * sb;
+  const size_t in_align = is_fwd ? sb : cb, out_align = is_fwd ? cb : sb;
   const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
-  if ((in_dev && (uintptr_t)in % cb) || (out_dev && (uintptr_t)out % cb)) {
+  if ((in_dev && (uintptr_t)in % in_align) || (out_dev && (uintptr_t)out % out_align)) {
     if (cur != P->device) cudaSetDevice(cur);
-    return fail(P, SGL_ERR_ARG, "device data pointers must be aligned to the complex element size");
+    return fail(P, SGL_ERR_ARG, "device data pointers must be aligned to their element size");
   }
   const void* din = in;
   void* dout = out;
   sgl_status st = SGL_OK;
   cudaError_t e = cudaSuccess;
-  if ((!in_dev || !out_dev) && P->uniform && P->nfn >= kPipeMinFunctions) {
+  if ((!in_dev || !out_dev) && P->uniform && !P->real_pairs && P->nfn >= kPipeMinFunctions) {
     st = execute_pipelined(P, is_fwd, weights, in, out, in_dev, out_dev, s);
     goto done;
   }
@@ -589,9 +594,8 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
     }
   }
   if (!cached) {
-    const size_t cb = complex_bytes(*P);
-    cudaMemsetAsync(samples, 0, (size_t)P->n_samples * cb, s);
-    cudaMemsetAsync(coeffs, 0, (size_t)P->n_coeffs * cb, s);
+    cudaMemsetAsync(samples, 0, (size_t)P->n_samples * sample_bytes(*P), s);
+    cudaMemsetAsync(coeffs, 0, (size_t)P->n_coeffs * complex_bytes(*P), s);
     std::vector<int> jps = {4, 8};
     if (P->prec != SGL_FP64) jps.push_back(16);
     for (int dir = 0; dir < 2; ++dir) {
@@ -654,7 +658,7 @@ sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples) {
   if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
   if (batch < 1) return fail(nullptr, SGL_ERR_ARG, "batch must be >= 1");
   if (prec < SGL_FP64 || prec > SGL_BF16X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
-  if (samples != SGL_SAMPLES_WEIGHTED && samples != SGL_SAMPLES_PHYSICAL)
+  if (samples != SGL_SAMPLES_WEIGHTED && samples != SGL_SAMPLES_PHYSICAL && samples != SGL_SAMPLES_REAL)
     return fail(nullptr, SGL_ERR_ARG, "unknown sample convention");
   if (samples == SGL_SAMPLES_PHYSICAL && prec != SGL_FP64)
     return fail(nullptr, SGL_ERR_ARG, "physical samples need an FP64 plan");
@@ -664,8 +668,22 @@ sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples) {
   Plan* P = new Plan();
   P->prec = prec;
   P->samples = samples;
-  std::vector<int> Bs(batch, B);
+  const bool real = samples == SGL_SAMPLES_REAL;
+  if (real) {  // the real functions in pairs, one complex function per pair
+    P->real_pairs = true;
+    P->nreal = batch;
+  }
+  std::vector<int> Bs(real ? (batch + 1) / 2 : batch, B);
   sgl_status st = build_plan(P, Bs, true);
+  if (st == SGL_OK && real) {
+    P->n_samples = (int64_t)batch * sample_count(B);  // reals
+    P->n_coeffs = (int64_t)batch * coeff_count(B);
+    const int64_t cbytes = (int64_t)P->nfn * coeff_count(B) * (int64_t)complex_bytes(*P);
+    if (cudaMalloc(&P->d_ccoef, cbytes) != cudaSuccess)
+      st = fail(P, SGL_ERR_ALLOC, "workspace allocation failed");
+    else
+      P->bytes += cbytes;
+  }
   if (st != SGL_OK) {
     g_create_error = P->err;
     release(P);
@@ -721,8 +739,8 @@ sgl_status sgl_grid(sgl_plan_t plan, int fn, double* r, double* theta, double* p
                     double* w_theta) {
   Plan* P = (Plan*)plan;
   if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
-  if (fn < 0 || fn >= P->nfn) return fail(P, SGL_ERR_ARG, "function index out of range");
-  const int B = P->fn_B[fn];
+  if (fn < 0 || fn >= user_fns(*P)) return fail(P, SGL_ERR_ARG, "function index out of range");
+  const int B = P->fn_B[P->real_pairs ? 0 : fn];
   size_t seg = 0;
   while (P->segs[seg].B != B) ++seg;
   const HostTables& H = P->tables[seg];
@@ -739,22 +757,24 @@ int64_t sgl_coeff_count(sgl_plan_t plan) { return plan ? ((Plan*)plan)->n_coeffs
 
 int64_t sgl_sample_offset(sgl_plan_t plan, int fn) {
   Plan* P = (Plan*)plan;
-  if (!P || fn < 0 || fn >= P->nfn) return -1;
+  if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
+  if (P->real_pairs) return (int64_t)fn * sample_count(P->fn_B[0]);
   return P->fn_samp_off[fn];
 }
 
 int64_t sgl_coeff_offset(sgl_plan_t plan, int fn) {
   Plan* P = (Plan*)plan;
-  if (!P || fn < 0 || fn >= P->nfn) return -1;
+  if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
+  if (P->real_pairs) return (int64_t)fn * coeff_count(P->fn_B[0]);
   return P->fn_coef_off[fn];
 }
 
-int sgl_num_functions(sgl_plan_t plan) { return plan ? ((Plan*)plan)->nfn : -1; }
+int sgl_num_functions(sgl_plan_t plan) { return plan ? user_fns(*(Plan*)plan) : -1; }
 
 int sgl_bandlimit(sgl_plan_t plan, int fn) {
   Plan* P = (Plan*)plan;
-  if (!P || fn < 0 || fn >= P->nfn) return -1;
-  return P->fn_B[fn];
+  if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
+  return P->fn_B[P->real_pairs ? 0 : fn];
 }
 
 int64_t sgl_workspace_bytes(sgl_plan_t plan) {
@@ -818,8 +838,8 @@ sgl_status sgl_autotune(sgl_plan_t plan, void* samples, void* coeffs, const char
   if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
   if (!samples || !coeffs || !is_device_ptr(samples) || !is_device_ptr(coeffs))
     return fail(P, SGL_ERR_ARG, "sgl_autotune needs device buffers for samples and coefficients");
-  if ((uintptr_t)samples % complex_bytes(*P) || (uintptr_t)coeffs % complex_bytes(*P))
-    return fail(P, SGL_ERR_ARG, "device data pointers must be aligned to the complex element size");
+  if ((uintptr_t)samples % sample_bytes(*P) || (uintptr_t)coeffs % complex_bytes(*P))
+    return fail(P, SGL_ERR_ARG, "device data pointers must be aligned to their element size");
   if (P->latched != SGL_OK) return (sgl_status)P->latched;
   int cur = 0;
   cudaGetDevice(&cur);

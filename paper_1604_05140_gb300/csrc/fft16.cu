@@ -137,8 +137,10 @@ __device__ __forceinline__ int spos(int r, int row, int col) {
 
 }  // namespace
 
-// Forward: samples -> E/O spectra.  blockDim = 16 * JP.
-template <typename real, int N2>
+// Forward: samples -> E/O spectra.  blockDim = 16 * JP.  PAIRS: real
+// functions in pairs, the first at twice the complex offset (in reals) as the
+// real part, the next one as the imaginary part (zero past pair_limit).
+template <typename real, int N2, bool PAIRS>
 __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   constexpr int N = 16 * N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -163,6 +165,9 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   if (a.mode == 1) scale = misc[B + i];
   if (a.mode == 2) scale = misc[2 * B + i];
   const c2<real>* in = reinterpret_cast<const c2<real>*>(a.in) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
+  const int64_t fn_reals = (int64_t)B * N * N;
+  const real* inA = reinterpret_cast<const real*>(a.in) + 2 * a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
+  const bool hasB = PAIRS && 2 * a.fn_samp[sg.fn0 + b] + fn_reals < a.pair_limit;
   __syncthreads();
 
   // step A: items (r, n2), n2 fastest; 16-point DFT over n1, twiddle, store
@@ -177,9 +182,15 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
     if (rr[u] < R) {
       const int q = rr[u] >> 1;
       const int j = (rr[u] & 1) ? (N - 1 - (j0 + q)) : (j0 + q);
-      const c2<real>* ring = in + (int64_t)j * N + cc[u];
+      if constexpr (PAIRS) {
+        const real* ringA = inA + (int64_t)j * N + cc[u];
 #pragma unroll
-      for (int n1 = 0; n1 < 16; ++n1) v[u][n1] = ring[n1 * N2];
+        for (int n1 = 0; n1 < 16; ++n1) v[u][n1] = {ringA[n1 * N2], hasB ? ringA[fn_reals + n1 * N2] : (real)0};
+      } else {
+        const c2<real>* ring = in + (int64_t)j * N + cc[u];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) v[u][n1] = ring[n1 * N2];
+      }
     }
   }
 #pragma unroll
@@ -230,8 +241,9 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   }
 }
 
-// Inverse: G spectra -> samples.  blockDim = 16 * JP.
-template <typename real, int N2>
+// Inverse: G spectra -> samples.  blockDim = 16 * JP.  PAIRS: real and
+// imaginary parts to the pair's two real functions (as in the forward kernel).
+template <typename real, int N2, bool PAIRS>
 __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
   constexpr int N = 16 * N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -331,9 +343,21 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
     if (a.mode == 2) s = misc[i];
     if (a.mode == 3) s = misc[i] * misc[B + i];
     if (a.mode >= 2) s *= misc[3 * B + j];
-    c2<real>* ring = out + ((int64_t)i * N + j) * N + n2;
+    if constexpr (PAIRS) {
+      const int64_t fn_reals = (int64_t)B * N * N;
+      const int64_t f0 = 2 * a.fn_samp[sg.fn0 + b];
+      real* ringA = reinterpret_cast<real*>(a.out) + f0 + ((int64_t)i * N + j) * N + n2;
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) ring[n1 * N2] = {v[n1].x * s, v[n1].y * s};
+      for (int n1 = 0; n1 < 16; ++n1) ringA[n1 * N2] = v[n1].x * s;
+      if (f0 + fn_reals < a.pair_limit) {
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) ringA[fn_reals + n1 * N2] = v[n1].y * s;
+      }
+    } else {
+      c2<real>* ring = out + ((int64_t)i * N + j) * N + n2;
+#pragma unroll
+      for (int n1 = 0; n1 < 16; ++n1) ring[n1 * N2] = {v[n1].x * s, v[n1].y * s};
+    }
   }
 }
 
@@ -344,8 +368,13 @@ bool fft16_launch(bool inv, const Fft16Args& a, int n1, int n2, int nctas, cudaS
   const int N = 16 * n2;
   const size_t smem = sizeof(c2<real>) * ((size_t)N + (size_t)2 * a.JP * N);
   void (*fn)(Fft16Args) = nullptr;
-  if (n2 == 16) fn = inv ? fft16_inv_kernel<real, 16> : fft16_fwd_kernel<real, 16>;
-  else fn = inv ? fft16_inv_kernel<real, 8> : fft16_fwd_kernel<real, 8>;
+  if (a.pair_limit) {
+    if (n2 == 16) fn = inv ? fft16_inv_kernel<real, 16, true> : fft16_fwd_kernel<real, 16, true>;
+    else fn = inv ? fft16_inv_kernel<real, 8, true> : fft16_fwd_kernel<real, 8, true>;
+  } else {
+    if (n2 == 16) fn = inv ? fft16_inv_kernel<real, 16, false> : fft16_fwd_kernel<real, 16, false>;
+    else fn = inv ? fft16_inv_kernel<real, 8, false> : fft16_fwd_kernel<real, 8, false>;
+  }
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     fn<<<nctas, 16 * a.JP, smem, s>>>(a);

@@ -116,6 +116,7 @@ struct FftArgs {
   int JP;                // ring pairs per CTA
   int mode;              // fwd: 0 none, 1 *exp(-t/2), 2 *exp(+t/2);
                          // inv: 0 none, 1 *exp(+t/2), 2 *what*beta, 3 *what*beta*exp(-t/2)
+  int64_t pair_limit;    // real functions in pairs: reals in the sample array; 0 complex samples
 };
 
 __host__ __device__ inline int ring_pitch(int n1, int n2) {
@@ -204,11 +205,22 @@ __global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
   if (a.mode == 1) scale = misc[B + i];
   if (a.mode == 2) scale = misc[2 * B + i];
   const cx<real>* in = reinterpret_cast<const cx<real>*>(a.in) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
+  // real functions in pairs: the pair's first function starts at twice the
+  // complex offset (in reals), the second one function later
+  const int64_t fn_reals = (int64_t)B * N * N;
+  const real* inA = reinterpret_cast<const real*>(a.in) + 2 * a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
+  const bool hasB = 2 * a.fn_samp[sg.fn0 + b] + fn_reals < a.pair_limit;
   for (int e = threadIdx.x; e < R * N; e += blockDim.x) {
     const int r = e / N, k = e - r * N;
     const int q = r >> 1;
     const int j = (r & 1) ? (N - 1 - (j0 + q)) : (j0 + q);
-    cx<real> v = in[(int64_t)j * N + k];
+    cx<real> v;
+    if (a.pair_limit) {
+      const int64_t o = (int64_t)j * N + k;
+      v = {inA[o], hasB ? inA[fn_reals + o] : (real)0};
+    } else {
+      v = in[(int64_t)j * N + k];
+    }
     const int c1 = k / n2, c2 = k - c1 * n2;
     sre[r * pitch + c1 * (n2 + 1) + c2] = v.x * scale;
     sim[r * pitch + c1 * (n2 + 1) + c2] = v.y * scale;
@@ -297,7 +309,14 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
     if (a.mode == 3) s = misc[i] * misc[B + i];
     if (a.mode >= 2) s *= misc[3 * B + j];
     cx<real> v = {sre[r * pitch + slot] * s, sim[r * pitch + slot] * s};
-    out[((int64_t)i * N + j) * N + k] = v;
+    const int64_t o = ((int64_t)i * N + j) * N + k;
+    if (a.pair_limit) {  // real and imaginary parts to the pair's two functions
+      real* outA = reinterpret_cast<real*>(a.out) + 2 * a.fn_samp[sg.fn0 + b];
+      outA[o] = v.x;
+      if (2 * a.fn_samp[sg.fn0 + b] + (int64_t)B * N * N < a.pair_limit) outA[(int64_t)B * N * N + o] = v.y;
+    } else {
+      out[o] = v;
+    }
   }
 }
 
@@ -628,8 +647,9 @@ static cudaError_t run_fft(Plan& P, bool inv, const void* in, void* out, int mod
     a.w1 = P.d_w1;
     a.JP = fft_jp(P, f.B, inv);
     a.mode = mode;
+    a.pair_limit = P.real_pairs ? P.n_samples : 0;
     {
-      Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode};
+      Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode, a.pair_limit};
       cudaError_t e16 = cudaSuccess;
       if (fft16_launch<real>(inv, a16, f.n1, f.n2, f.count, s, &e16)) {
         if (e16 != cudaSuccess) return e16;
@@ -702,12 +722,116 @@ static cudaError_t inverse_t(Plan& P, const void* coeffs, void* samples, cudaStr
   return run_fft<real>(P, true, nullptr, samples, mode, s);
 }
 
+// ---------------------------------------------------------------------------
+// real functions in pairs
+// ---------------------------------------------------------------------------
+// A real f has fhat_{n,l,-m} = (-1)^m conj(fhat_{n,l,m}) (Def 2.1:
+// Y_l^{-m} = (-1)^m conj(Y_l^m), and the radial part is real).  Write
+// S(F)_m = (-1)^m conj(F_{-m}); S is conjugate-linear and fixes the
+// coefficients of every real function.  Pair q carries real functions 2q and
+// 2q + 1 as one complex function g = f_2q + i f_2q+1, whose coefficients are
+// C = F_2q + i F_2q+1, so S(C) = F_2q - i F_2q+1 and
+//   F_2q = (C + S(C)) / 2,   F_2q+1 = (C - S(C)) / (2i).
+// Shell n of pair q (its n^2 coefficients are contiguous from
+// omega(n, 0, 0), element e = l(l+1) + m) per block; each thread computes its
+// elements from themselves and their mirrors m -> -m.
+
+// l and m of element e = l(l+1) + m of a shell
+__device__ __forceinline__ void lm_of(int e, int& l, int& m) {
+  l = (int)sqrtf((float)e);
+  while (l * l > e) --l;
+  while ((l + 1) * (l + 1) <= e) ++l;
+  m = e - l * (l + 1);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) real_split_kernel(const cx<real>* C, cx<real>* out, int64_t Om, int npairs,
+                                                         int nreal) {
+  const int n = blockIdx.x + 1;
+  const int64_t s0 = (int64_t)n * (n - 1) * (2 * n - 1) / 6;
+  for (int q = blockIdx.y; q < npairs; q += gridDim.y) {
+    const cx<real>* c = C + (int64_t)q * Om + s0;
+    cx<real>* o1 = out + (int64_t)(2 * q) * Om + s0;
+    const bool has2 = 2 * q + 1 < nreal;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int l, m;
+      lm_of(e, l, m);
+      const real sg = (m & 1) ? (real)-1 : (real)1;
+      const cx<real> cp = c[e], cm = c[l * (l + 1) - m];
+      const cx<real> d = {sg * cm.x, -sg * cm.y};  // S(C)_m
+      o1[e] = {(cp.x + d.x) * (real)0.5, (cp.y + d.y) * (real)0.5};
+      if (has2) o1[Om + e] = {(cp.y - d.y) * (real)0.5, -(cp.x - d.x) * (real)0.5};  // (C - S(C)) / 2i
+    }
+  }
+}
+
+// Inverse direction: pair q's complex coefficients from the user's
+// coefficients a_2q, a_2q+1, each replaced by its symmetric part
+// (a + S(a)) / 2 (the coefficients of the real part of its inverse), so that
+// the real and imaginary parts of the complex inverse are Re inverse(a_2q)
+// and Re inverse(a_2q+1).
+template <typename real>
+__global__ void __launch_bounds__(256) real_combine_kernel(const cx<real>* in, cx<real>* C, int64_t Om, int npairs,
+                                                           int nreal) {
+  const int n = blockIdx.x + 1;
+  const int64_t s0 = (int64_t)n * (n - 1) * (2 * n - 1) / 6;
+  for (int q = blockIdx.y; q < npairs; q += gridDim.y) {
+    const cx<real>* a1 = in + (int64_t)(2 * q) * Om + s0;
+    const bool has2 = 2 * q + 1 < nreal;
+    cx<real>* c = C + (int64_t)q * Om + s0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int l, m;
+      lm_of(e, l, m);
+      const int em = l * (l + 1) - m;
+      const real sg = (m & 1) ? (real)-1 : (real)1;
+      cx<real> g1 = a1[e], g2 = {0, 0};
+      {
+        const cx<real> t = a1[em];
+        g1 = {(g1.x + sg * t.x) * (real)0.5, (g1.y - sg * t.y) * (real)0.5};
+      }
+      if (has2) {
+        const cx<real> u = a1[Om + e], t = a1[Om + em];
+        g2 = {(u.x + sg * t.x) * (real)0.5, (u.y - sg * t.y) * (real)0.5};
+      }
+      c[e] = {g1.x - g2.y, g1.y + g2.x};  // g1 + i g2
+    }
+  }
+}
+
+template <typename real>
+static cudaError_t run_real_pairs(Plan& P, bool split, const void* src, void* dst, cudaStream_t s) {
+  const int B = P.fn_B[0];
+  const dim3 grid((unsigned)B, (unsigned)std::min(P.nfn, 65535));
+  if (split)
+    real_split_kernel<real><<<grid, 256, 0, s>>>((const cx<real>*)src, (cx<real>*)dst, coeff_count(B), P.nfn, P.nreal);
+  else
+    real_combine_kernel<real><<<grid, 256, 0, s>>>((const cx<real>*)src, (cx<real>*)dst, coeff_count(B), P.nfn,
+                                                   P.nreal);
+  return cudaGetLastError();
+}
+
 cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights) {
+  if (P.real_pairs) {
+    const bool d = P.prec == SGL_FP64;
+    cudaError_t e = d ? forward_t<double>(P, samples, P.d_ccoef, s, weights)
+                      : forward_t<float>(P, samples, P.d_ccoef, s, weights);
+    if (e != cudaSuccess) return e;
+    return d ? run_real_pairs<double>(P, true, P.d_ccoef, coeffs, s)
+             : run_real_pairs<float>(P, true, P.d_ccoef, coeffs, s);
+  }
   if (P.prec == SGL_FP64) return forward_t<double>(P, samples, coeffs, s, weights);
   return forward_t<float>(P, samples, coeffs, s, weights);
 }
 
 cudaError_t run_inverse(Plan& P, const void* coeffs, void* samples, cudaStream_t s, bool weights) {
+  if (P.real_pairs) {
+    const bool d = P.prec == SGL_FP64;
+    cudaError_t e = d ? run_real_pairs<double>(P, false, coeffs, P.d_ccoef, s)
+                      : run_real_pairs<float>(P, false, coeffs, P.d_ccoef, s);
+    if (e != cudaSuccess) return e;
+    return d ? inverse_t<double>(P, P.d_ccoef, samples, s, weights)
+             : inverse_t<float>(P, P.d_ccoef, samples, s, weights);
+  }
   if (P.prec == SGL_FP64) return inverse_t<double>(P, coeffs, samples, s, weights);
   return inverse_t<float>(P, coeffs, samples, s, weights);
 }

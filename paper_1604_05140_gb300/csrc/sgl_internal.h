@@ -208,6 +208,15 @@ struct Plan {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[SGL_NUM_STAGES];
   std::vector<cudaEvent_t> ev_pool;
 
+  // real functions (SGL_SAMPLES_REAL): the plan's nfn complex functions
+  // carry the nreal user functions in pairs (function 2q as the real part of
+  // complex function q, 2q + 1 as its imaginary part); n_samples counts the
+  // user's reals, n_coeffs the user's complex coefficients, and the complex
+  // coefficients of the pairs live in d_ccoef
+  bool real_pairs = false;
+  int nreal = 0;
+  void* d_ccoef = nullptr;
+
   std::string err;
   int latched = SGL_OK;
 };
@@ -260,6 +269,10 @@ struct Fft16Args {
   void* w1;
   int JP;                // ring pairs per CTA; blockDim = 16 * JP
   int mode;
+  // real functions in pairs: 0 for complex samples, else the number of
+  // reals in the sample array (the second function of the last pair exists
+  // only below this limit)
+  int64_t pair_limit;
 };
 // Launches the specialized kernel when (n1, n2) = (16, 8) or (16, 16) and
 // returns true (launch status in *err); returns false otherwise.

@@ -24,7 +24,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "sgl.h")
 
 SGL_OK, SGL_ERR_ARG, SGL_ERR_ALLOC, SGL_ERR_CUDA, SGL_ERR_TIMEOUT, SGL_ERR_UNSUPPORTED = range(6)
 SGL_FP64, SGL_FP32, SGL_TF32X3, SGL_TF32, SGL_BF16X3 = 0, 1, 2, 3, 4
-SGL_SAMPLES_WEIGHTED, SGL_SAMPLES_PHYSICAL = 0, 1
+SGL_SAMPLES_WEIGHTED, SGL_SAMPLES_PHYSICAL, SGL_SAMPLES_REAL = 0, 1, 2
 SGL_MAX_B = 128
 
 PRECISIONS = {"fp64": SGL_FP64, "fp32": SGL_FP32, "tf32x3": SGL_TF32X3, "tf32": SGL_TF32, "bf16x3": SGL_BF16X3}
@@ -181,6 +181,9 @@ class Plan:
     (``Plan.many``) take flat 1-D tensors packed at ``sample_offset(f)`` /
     ``coeff_offset(f)``.  Tensors may live on the GPU (used in place, launch
     on the current torch stream) or in host memory (staged by the library).
+    ``samples="real"`` makes a plan of real functions: real sample tensors
+    (``sample_dtype``), complex coefficients, and the inverse returns the real
+    part (SGL_SAMPLES_REAL in sgl.h).
     """
 
     def __init__(self, B: Optional[int] = None, batch: int = 1, precision: str = "fp64",
@@ -189,13 +192,15 @@ class Plan:
         self.lib = load_library()
         self.prec = PRECISIONS[precision]
         self.precision = precision
+        self.real = samples == "real"
         if _handle is not None:
             self.handle = _handle
             self.Bs = list(_Bs)
             self.B = None
             self.batch = len(self.Bs)
         else:
-            conv = {"weighted": SGL_SAMPLES_WEIGHTED, "physical": SGL_SAMPLES_PHYSICAL}[samples]
+            conv = {"weighted": SGL_SAMPLES_WEIGHTED, "physical": SGL_SAMPLES_PHYSICAL,
+                    "real": SGL_SAMPLES_REAL}[samples]
             self.handle = sgl_plan(B, batch, self.prec, conv)
             self.B = int(B)
             self.batch = int(batch)
@@ -213,6 +218,15 @@ class Plan:
     def dtype(self):
         import torch
         return torch.complex128 if self.prec == SGL_FP64 else torch.complex64
+
+    @property
+    def sample_dtype(self):
+        """Element type of the sample tensors: the coefficient type, or its
+        real counterpart for plans of real functions (samples="real")."""
+        import torch
+        if self.real:
+            return torch.float64 if self.prec == SGL_FP64 else torch.float32
+        return self.dtype
 
     @property
     def sample_shape(self):
@@ -244,12 +258,13 @@ class Plan:
         return sgl_grid(self.handle, fn)
 
     # execution ------------------------------------------------------------
-    def _prep(self, t, numel: int, name: str):
+    def _prep(self, t, numel: int, name: str, dtype=None):
         import torch
+        dtype = self.dtype if dtype is None else dtype
         if not isinstance(t, torch.Tensor):
             raise TypeError(f"{name} must be a torch tensor")
-        if t.dtype != self.dtype:
-            raise TypeError(f"{name} must be {self.dtype}, got {t.dtype}")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
         if t.numel() != numel:
             raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
         if not t.is_contiguous():
@@ -263,16 +278,16 @@ class Plan:
                 return torch.cuda.current_stream(t.device).cuda_stream
         return 0
 
-    def _out(self, like, shape, out):
+    def _out(self, like, shape, out, dtype=None):
         import torch
         if out is None:
-            out = torch.empty(shape, dtype=self.dtype, device=like.device,
+            out = torch.empty(shape, dtype=self.dtype if dtype is None else dtype, device=like.device,
                               pin_memory=(not like.is_cuda and torch.cuda.is_available()))
         return out
 
     def forward(self, samples, out=None):
         """Coefficients of the samples (sgl_forward)."""
-        self._prep(samples, self.n_samples, "samples")
+        self._prep(samples, self.n_samples, "samples", self.sample_dtype)
         out = self._out(samples, self.coeff_shape, out)
         self._prep(out, self.n_coeffs, "out")
         sgl_forward(self.handle, samples.data_ptr(), out.data_ptr(), self._stream(samples, out))
@@ -281,8 +296,8 @@ class Plan:
     def inverse(self, coeffs, out=None):
         """Samples of the function with these coefficients (sgl_inverse)."""
         self._prep(coeffs, self.n_coeffs, "coeffs")
-        out = self._out(coeffs, self.sample_shape, out)
-        self._prep(out, self.n_samples, "out")
+        out = self._out(coeffs, self.sample_shape, out, self.sample_dtype)
+        self._prep(out, self.n_samples, "out", self.sample_dtype)
         sgl_inverse(self.handle, coeffs.data_ptr(), out.data_ptr(), self._stream(coeffs, out))
         return out
 
@@ -291,13 +306,13 @@ class Plan:
         -> samples) or of the inverse map (of_inverse=True, samples ->
         coefficients), sgl_adjoint."""
         if of_inverse:
-            self._prep(x, self.n_samples, "x")
+            self._prep(x, self.n_samples, "x", self.sample_dtype)
             out = self._out(x, self.coeff_shape, out)
             self._prep(out, self.n_coeffs, "out")
         else:
             self._prep(x, self.n_coeffs, "x")
-            out = self._out(x, self.sample_shape, out)
-            self._prep(out, self.n_samples, "out")
+            out = self._out(x, self.sample_shape, out, self.sample_dtype)
+            self._prep(out, self.n_samples, "out", self.sample_dtype)
         sgl_adjoint(self.handle, int(bool(of_inverse)), x.data_ptr(), out.data_ptr(), self._stream(x, out))
         return out
 
@@ -309,10 +324,10 @@ class Plan:
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         if samples is None:
-            samples = torch.empty(self.sample_shape, dtype=self.dtype, device=dev)
+            samples = torch.empty(self.sample_shape, dtype=self.sample_dtype, device=dev)
         if coeffs is None:
             coeffs = torch.empty(self.coeff_shape, dtype=self.dtype, device=dev)
-        self._prep(samples, self.n_samples, "samples")
+        self._prep(samples, self.n_samples, "samples", self.sample_dtype)
         self._prep(coeffs, self.n_coeffs, "coeffs")
         sgl_autotune(self.handle, samples.data_ptr(), coeffs.data_ptr(), cache, self._stream(samples, coeffs))
         return self.tuning

@@ -252,6 +252,31 @@ def test_adjoint_identities(B):
     del rng
 
 
+@pytest.mark.parametrize("B", [3, 6])
+def test_real_function_symmetry(B):
+    # Def 2.1: Y_l^{-m} = (-1)^m conj(Y_l^m) and the radial part is real, so
+    # H_{n,l,-m} = (-1)^m conj(H_{n,l,m}) (closed forms, arbitrary points) ...
+    rng = np.random.default_rng(60 + B)
+    r, th, ph = rng.uniform(0.1, 3.0, 7), rng.uniform(0.0, pi, 7), rng.uniform(0.0, 2 * pi, 7)
+    for n, l, m in [(2, 1, 1), (3, 2, 1), (3, 2, 2), (B, B - 1, B - 1)]:
+        np.testing.assert_allclose(OM.basis_explicit(n, l, -m, r, th, ph),
+                                   (-1) ** m * np.conj(OM.basis_explicit(n, l, m, r, th, ph)), atol=1e-13)
+    # ... hence the coefficients of a real function obey
+    # fhat_{n,l,-m} = (-1)^m conj(fhat_{n,l,m}), which the real-function plans use
+    g = inputs.random_real((2, B, 2 * B, 2 * B), seed=70 + B)
+    c = O.forward(g, B)
+    trip = [(n, l, m) for n in range(1, B + 1) for l in range(n) for m in range(1, l + 1)]
+    ip = [O.omega(n, l, m) for n, l, m in trip]
+    im = [O.omega(n, l, -m) for n, l, m in trip]
+    sign = np.array([(-1.0) ** m for _, _, m in trip])
+    np.testing.assert_allclose(c[:, im], sign * np.conj(c[:, ip]), atol=1e-13 * np.abs(c).max())
+    m0 = [O.omega(n, l, 0) for n in range(1, B + 1) for l in range(n)]
+    assert np.abs(c[:, m0].imag).max() < 1e-13 * np.abs(c).max()
+    # and the inverse of such coefficients is real
+    s = O.inverse(c, B)
+    assert np.abs(s.imag).max() < 1e-13 * np.abs(s).max()
+
+
 def test_forward_then_inverse_is_projector():
     # R10: on arbitrary (non-bandlimited) samples inverse(forward(.)) is an
     # orthogonal projector in the w-weighted inner product
