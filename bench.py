@@ -199,6 +199,19 @@ def whole_job(ws, batch, ms_local):
 # CPU baseline: the oracle
 # ---------------------------------------------------------------------------
 
+def oracle_threads():
+    """Host threads the oracle's NumPy/BLAS calls use."""
+    cores = os.cpu_count()
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        if info:
+            cores = max(i.get("num_threads", 1) for i in info)
+    except Exception:
+        pass
+    return cores
+
+
 def cpu_oracle_sample(B=B_BENCH, budget_s=12.0, seed=1604051403):
     """Times the FP64 oracle (inverse then forward) on whole functions of the
     benchmark workload until about budget_s seconds have passed."""
@@ -214,15 +227,7 @@ def cpu_oracle_sample(B=B_BENCH, budget_s=12.0, seed=1604051403):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    cores = os.cpu_count()
-    try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        if info:
-            cores = max(i.get("num_threads", 1) for i in info)
-    except Exception:
-        pass
-    return {"value": n / dt, "unit": "transforms/s", "cores": cores, "kind": "oracle",
+    return {"value": n / dt, "unit": "transforms/s", "cores": oracle_threads(), "kind": "oracle",
             "sample": f"{n} whole functions of B={B} (inverse + forward each) out of the batch of {BATCH}, "
                       f"{dt:.1f} s, FP64 NumPy separated form"}
 
@@ -533,9 +538,10 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(times)
     value = 1.0 / (ms * 1e-3)
-    cores = os.cpu_count()
+    cores = oracle_threads()
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": args.gpus,
+        "devices": "host cores only: the oracle runs on rank 0's CPU and uses no GPU",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"SGL inverse+forward, B={B_BENCH}, batch {BATCH} functions per GPU",
