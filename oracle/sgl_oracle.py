@@ -37,7 +37,21 @@ R6  phi-DFT sign ``e^{-i m phi}`` forward, ``e^{+i m phi}`` inverse, no 1/N;
     the Nyquist bin ``m = B`` is not a coefficient (dropped forward, zero
     inverse).
 
-Layouts (Sect. 3.4 index maps with ``i < B``):
+The paper's own grid (``rule="hermite"`` wherever a function takes ``rule``):
+the radii are the 2B nodes of the half-range Gauss-Hermite rule of order 2B
+(Thm 3.3, used in Eq. zwischenstufe_2), ``int_0^inf p(r) e^{-r^2} dr =
+sum_i a_i p(r_i)``, so the radial weight is ``a_i r_i^2`` in place of
+``w_i / 2``.  The rule is computed in high precision (mpmath): the recurrence
+coefficients of the orthogonal polynomials from the moments
+``int_0^inf r^k e^{-r^2} dr = Gamma((k+1)/2)/2`` by Chebyshev's algorithm,
+the nodes as eigenvalues of the Jacobi matrix polished by Newton steps on the
+recurrence, the weights from the Christoffel function ``1/sum_k p_k(r_i)^2``
+of the orthonormal polynomials.  The paper leaves the method open (it cites
+special recurrences of the literature); any method gives the same unique Gauss
+rule.
+
+Layouts (Sect. 3.4 index maps with ``i < R``, R = B radii, 2B on the paper's
+grid):
   samples ``[batch][i][j][k]``: psi = 4B^2 i + 2B j + k, complex128;
   coefficients ``[batch][omega]``: omega = n(n-1)(2n-1)/6 + l(l+1) + m.
 """
@@ -50,7 +64,7 @@ import numpy as np
 
 __all__ = [
     "coeff_count", "omega", "nlm_list",
-    "sphere_rule", "laguerre_rule", "radial_weights", "grid",
+    "sphere_rule", "laguerre_rule", "half_range_hermite_rule", "radial_rule", "n_radial", "radial_weights", "grid",
     "legendre_table", "radial_table",
     "laguerre_explicit", "legendre_rodrigues", "basis_explicit",
     "forward", "inverse", "forward_direct", "inverse_direct", "sgl_matrix",
@@ -151,26 +165,91 @@ def laguerre_rule(B: int, alpha: float = 0.5):
     return t.astype(np.float64), logw.astype(np.float64)
 
 
-def radial_weights(B: int):
+@lru_cache(maxsize=None)
+def half_range_hermite_rule(N: int):
+    """Gauss rule of order N for the weight e^{-r^2} on [0, inf) (Thm 3.3):
+    nodes r_i and log a_i (float64), computed in high precision as stated in
+    the module header."""
+    import mpmath as mp
+    with mp.workdps(2 * N + 60):  # Chebyshev's algorithm loses about 1.7 N digits
+        mu = [mp.gamma(mp.mpf(k + 1) / 2) / 2 for k in range(2 * N)]
+        alpha, beta = [mp.mpf(0)] * N, [mp.mpf(0)] * N
+        sig_prev, sig = [mp.mpf(0)] * (2 * N), list(mu)
+        alpha[0], beta[0] = mu[1] / mu[0], mu[0]
+        for k in range(1, N):
+            new = [mp.mpf(0)] * (2 * N)
+            for l in range(k, 2 * N - k):
+                new[l] = sig[l + 1] - alpha[k - 1] * sig[l] - beta[k - 1] * sig_prev[l]
+            alpha[k] = new[k + 1] / new[k] - sig[k] / sig[k - 1]
+            beta[k] = new[k] / sig[k - 1]
+            sig_prev, sig = sig, new
+    off = np.array([float(mp.sqrt(b)) for b in beta[1:]])
+    jac = np.diag([float(a) for a in alpha]) + np.diag(off, 1) + np.diag(off, -1)
+    x0 = np.sort(np.linalg.eigvalsh(jac))
+    r = np.empty(N)
+    loga = np.empty(N)
+    with mp.workdps(50):
+        sb = [mp.sqrt(b) for b in beta]
+        for i, x in enumerate(x0):
+            x = mp.mpf(float(x))
+            for _ in range(4):  # Newton on the monic p_N
+                pm, p, dpm, dp = mp.mpf(0), mp.mpf(1), mp.mpf(0), mp.mpf(0)
+                for k in range(N):
+                    bk = beta[k] if k > 0 else 0
+                    pn = (x - alpha[k]) * p - bk * pm
+                    dpn = p + (x - alpha[k]) * dp - bk * dpm
+                    pm, p, dpm, dp = p, pn, dp, dpn
+                x = x - p / dp
+            qm, q = mp.mpf(0), 1 / sb[0]  # orthonormal polynomials
+            s = q * q
+            for k in range(N - 1):
+                qn = ((x - alpha[k]) * q - (sb[k] if k > 0 else 0) * qm) / sb[k + 1]
+                qm, q = q, qn
+                s += q * q
+            r[i] = float(x)
+            loga[i] = float(-mp.log(s))
+    return r, loga
+
+
+def n_radial(B: int, rule: str = "laguerre") -> int:
+    """Radii of the grid: B (R1) or 2B (the paper's grid)."""
+    return {"laguerre": B, "hermite": 2 * B}[rule]
+
+
+def radial_rule(B: int, rule: str = "laguerre"):
+    """(t_i = r_i^2, log q_i) with int_0^inf p(r) r^2 e^{-r^2} dr =
+    sum_i q_i p(r_i) for the radial degrees of bandlimit B: q_i = w_i / 2 on
+    the B Gauss-Laguerre nodes (R1), q_i = a_i r_i^2 on the paper's 2B
+    half-range Gauss-Hermite nodes (Eq. zwischenstufe_2)."""
+    if rule == "laguerre":
+        t, logw = laguerre_rule(B)
+        return t, logw - log(2.0)
+    if rule == "hermite":
+        r, loga = half_range_hermite_rule(2 * B)
+        return r * r, loga + 2 * np.log(r)
+    raise ValueError(rule)
+
+
+def radial_weights(B: int, rule: str = "laguerre"):
     """r_i, t_i = r_i^2 and the modified radial weights
-    what_i = (w_i / 2) exp(t_i) (R1, R5)."""
-    t, logw = laguerre_rule(B)
-    what = np.exp(logw - log(2.0) + t)
+    what_i = q_i exp(t_i) (R1, R5)."""
+    t, logq = radial_rule(B, rule)
+    what = np.exp(logq + t)
     return np.sqrt(t), t, what
 
 
-def grid(B: int):
+def grid(B: int, rule: str = "laguerre"):
     """(r_i, theta_j, phi_k, what_i, beta_j) of the sampling grid."""
-    r, _, what = radial_weights(B)
+    r, _, what = radial_weights(B, rule)
     theta, phi, beta = sphere_rule(B)
     return r, theta, phi, what, beta
 
 
-def sample_weights(B: int) -> np.ndarray:
-    """w_psi = what_i * beta_j as a (B, 2B, 2B) array (Sect. 3.4)."""
-    _, _, what = radial_weights(B)
+def sample_weights(B: int, rule: str = "laguerre") -> np.ndarray:
+    """w_psi = what_i * beta_j as an (R, 2B, 2B) array (Sect. 3.4)."""
+    _, _, what = radial_weights(B, rule)
     _, _, beta = sphere_rule(B)
-    return np.broadcast_to(what[:, None, None] * beta[None, :, None], (B, 2 * B, 2 * B))
+    return np.broadcast_to(what[:, None, None] * beta[None, :, None], (len(what), 2 * B, 2 * B))
 
 
 # ---------------------------------------------------------------------------
@@ -208,19 +287,20 @@ def legendre_table(B: int) -> np.ndarray:
 
 
 @lru_cache(maxsize=None)
-def radial_table(B: int) -> np.ndarray:
-    """T[l, n-1, i] = N_nl R_nl(r_i) exp(-t_i/2) for 0 <= l < n <= B.
+def radial_table(B: int, rule: str = "laguerre") -> np.ndarray:
+    """T[l, n-1, i] = N_nl R_nl(r_i) exp(-t_i/2) for 0 <= l < n <= B, i < R.
 
     Lemma 3.7 read for the normalized functions (R3), seed
     sqrt(2/Gamma(l+3/2)) r^l formed in logarithms together with exp(-t/2).
     Entries with n <= l are zero.
     """
-    _, t, _ = radial_weights(B)
+    _, t, _ = radial_weights(B, rule)
+    R = len(t)
     logt = np.log(t)
-    T = np.zeros((B, B, B))
+    T = np.zeros((B, B, R))
     for l in range(B):
         seed = np.exp(0.5 * log(2.0) - 0.5 * lgamma(l + 1.5) + 0.5 * l * logt - 0.5 * t)
-        prev = np.zeros(B)
+        prev = np.zeros(R)
         cur = seed
         T[l, l] = cur  # n = l + 1
         for n in range(l + 1, B):
@@ -282,13 +362,13 @@ def basis_explicit(n: int, l: int, m: int, r, theta, phi) -> np.ndarray:
 # sample conventions (R5)
 # ---------------------------------------------------------------------------
 
-def physical_to_weighted(f: np.ndarray, B: int) -> np.ndarray:
-    _, t, _ = radial_weights(B)
+def physical_to_weighted(f: np.ndarray, B: int, rule: str = "laguerre") -> np.ndarray:
+    _, t, _ = radial_weights(B, rule)
     return f * np.exp(-0.5 * t)[:, None, None]
 
 
-def weighted_to_physical(g: np.ndarray, B: int) -> np.ndarray:
-    _, t, _ = radial_weights(B)
+def weighted_to_physical(g: np.ndarray, B: int, rule: str = "laguerre") -> np.ndarray:
+    _, t, _ = radial_weights(B, rule)
     return g * np.exp(0.5 * t)[:, None, None]
 
 
@@ -296,9 +376,9 @@ def weighted_to_physical(g: np.ndarray, B: int) -> np.ndarray:
 # transforms
 # ---------------------------------------------------------------------------
 
-def _as_batch_samples(samples: np.ndarray, B: int) -> np.ndarray:
+def _as_batch_samples(samples: np.ndarray, B: int, rule: str = "laguerre") -> np.ndarray:
     s = np.asarray(samples, dtype=np.complex128)
-    return s.reshape(-1, B, 2 * B, 2 * B)
+    return s.reshape(-1, n_radial(B, rule), 2 * B, 2 * B)
 
 
 def _as_batch_coeffs(coeffs: np.ndarray, B: int) -> np.ndarray:
@@ -306,10 +386,10 @@ def _as_batch_coeffs(coeffs: np.ndarray, B: int) -> np.ndarray:
     return c.reshape(-1, coeff_count(B))
 
 
-def _sphere_coeffs_to_sgl(S: np.ndarray, B: int, what) -> np.ndarray:
+def _sphere_coeffs_to_sgl(S: np.ndarray, B: int, what, rule: str = "laguerre") -> np.ndarray:
     """Radial stage (DRT of Eq. DRT_matrix), all l:  fhat_nlm =
     sum_i T_nl(i) what_i S[b, i, l, m].  S is [b, i, l, m+B-1]."""
-    T = radial_table(B)
+    T = radial_table(B, rule)
     nb = S.shape[0]
     out = np.zeros((nb, coeff_count(B)), dtype=np.complex128)
     for l in range(B):
@@ -322,7 +402,7 @@ def _sphere_coeffs_to_sgl(S: np.ndarray, B: int, what) -> np.ndarray:
     return out
 
 
-def forward(samples: np.ndarray, B: int, weights: bool = True) -> np.ndarray:
+def forward(samples: np.ndarray, B: int, weights: bool = True, rule: str = "laguerre") -> np.ndarray:
     """Forward SGL transform of weighted samples (Thm 3.4), separated form.
 
     Steps of Eq. (SGL-Sampling-Theorem_rearranged) with the inner spherical
@@ -331,33 +411,34 @@ def forward(samples: np.ndarray, B: int, weights: bool = True) -> np.ndarray:
     over i per (l, m) (Eq. DRT).  ``weights=False`` drops what_i and beta_j,
     which is the adjoint of the inverse (Sect. 3.4).
     """
-    f = _as_batch_samples(samples, B)
-    nb = f.shape[0]
-    _, _, what = radial_weights(B)
+    f = _as_batch_samples(samples, B, rule)
+    nb, R = f.shape[0], f.shape[1]
+    _, _, what = radial_weights(B, rule)
     _, _, beta = sphere_rule(B)
     if not weights:
         what = np.ones_like(what)
         beta = np.ones_like(beta)
     lam = legendre_table(B)
     G = np.fft.fft(f, axis=-1)                           # G[b,i,j,(m mod 2B)]
-    S = np.zeros((nb, B, B, 2 * B - 1), dtype=np.complex128)
+    S = np.zeros((nb, R, B, 2 * B - 1), dtype=np.complex128)
     for m in range(-(B - 1), B):
         am = abs(m)
         sign = (-1.0) ** am if m < 0 else 1.0
         A = sign * lam[am, am:, :] * beta[None, :]       # (B-|m|, j)
         Gm = G[:, :, :, m % (2 * B)]                     # (b, i, j)
         S[:, :, am:, m + B - 1] = np.einsum("lj,bij->bil", A, Gm)
-    return _sphere_coeffs_to_sgl(S, B, what)
+    return _sphere_coeffs_to_sgl(S, B, what, rule)
 
 
-def inverse(coeffs: np.ndarray, B: int) -> np.ndarray:
+def inverse(coeffs: np.ndarray, B: int, rule: str = "laguerre") -> np.ndarray:
     """Inverse SGL transform (Algorithm 4 steps): weighted samples
     ftil(x_psi) = sum fhat_nlm T_nl(i) Lam_lm(theta_j) e^{i m phi_k}."""
     c = _as_batch_coeffs(coeffs, B)
     nb = c.shape[0]
-    T = radial_table(B)
+    T = radial_table(B, rule)
+    R = T.shape[2]
     lam = legendre_table(B)
-    S = np.zeros((nb, B, B, 2 * B - 1), dtype=np.complex128)  # [b,i,l,m]
+    S = np.zeros((nb, R, B, 2 * B - 1), dtype=np.complex128)  # [b,i,l,m]
     for l in range(B):
         Tl = T[l, l:, :]                                  # (B-l, i)
         X = np.zeros((nb, B - l, 2 * l + 1), dtype=np.complex128)
@@ -365,7 +446,7 @@ def inverse(coeffs: np.ndarray, B: int) -> np.ndarray:
             o = omega(n, l, -l)
             X[:, n - l - 1, :] = c[:, o:o + 2 * l + 1]
         S[:, :, l, B - 1 - l:B + l] = np.einsum("ni,bnm->bim", Tl, X)
-    G = np.zeros((nb, B, 2 * B, 2 * B), dtype=np.complex128)  # [b,i,j,m mod 2B]
+    G = np.zeros((nb, R, 2 * B, 2 * B), dtype=np.complex128)  # [b,i,j,m mod 2B]
     for m in range(-(B - 1), B):
         am = abs(m)
         sign = (-1.0) ** am if m < 0 else 1.0
@@ -375,10 +456,10 @@ def inverse(coeffs: np.ndarray, B: int) -> np.ndarray:
     return np.fft.ifft(G, axis=-1) * (2 * B)
 
 
-def sgl_matrix(B: int) -> np.ndarray:
+def sgl_matrix(B: int, rule: str = "laguerre") -> np.ndarray:
     """Htil[omega, psi] = T_nl(i) Lam_lm(theta_j) e^{i m phi_k}, the weighted
     basis samples (matrix form of Sect. 3.4), from the recurrence tables."""
-    T = radial_table(B)
+    T = radial_table(B, rule)
     lam = legendre_table(B)
     _, phi, _ = sphere_rule(B)
     rows = []
@@ -390,28 +471,29 @@ def sgl_matrix(B: int) -> np.ndarray:
     return np.array(rows)
 
 
-def forward_direct(samples: np.ndarray, B: int) -> np.ndarray:
+def forward_direct(samples: np.ndarray, B: int, rule: str = "laguerre") -> np.ndarray:
     """Naive forward transform, Algorithm 1: for every coefficient the full
     triple sum over the grid, O(B^7).  Small B only."""
-    f = _as_batch_samples(samples, B).reshape(-1, 4 * B ** 3)
-    H = sgl_matrix(B)
-    w = sample_weights(B).reshape(-1)
+    R = n_radial(B, rule)
+    f = _as_batch_samples(samples, B, rule).reshape(-1, 4 * R * B * B)
+    H = sgl_matrix(B, rule)
+    w = sample_weights(B, rule).reshape(-1)
     return (f * w[None, :]) @ np.conj(H).T
 
 
-def inverse_direct(coeffs: np.ndarray, B: int) -> np.ndarray:
+def inverse_direct(coeffs: np.ndarray, B: int, rule: str = "laguerre") -> np.ndarray:
     """Naive inverse transform, Algorithm 2: every sample summed over all
     coefficients, O(B^7).  Small B only."""
     c = _as_batch_coeffs(coeffs, B)
-    H = sgl_matrix(B)
-    return (c @ H).reshape(-1, B, 2 * B, 2 * B)
+    H = sgl_matrix(B, rule)
+    return (c @ H).reshape(-1, n_radial(B, rule), 2 * B, 2 * B)
 
 
-def adjoint_forward(y: np.ndarray, B: int) -> np.ndarray:
+def adjoint_forward(y: np.ndarray, B: int, rule: str = "laguerre") -> np.ndarray:
     """Adjoint of the forward map: F_fwd^H y = diag(w_psi) F_inv y (Sect. 3.4)."""
-    return inverse(y, B) * sample_weights(B)[None]
+    return inverse(y, B, rule) * sample_weights(B, rule)[None]
 
 
-def adjoint_inverse(g: np.ndarray, B: int) -> np.ndarray:
+def adjoint_inverse(g: np.ndarray, B: int, rule: str = "laguerre") -> np.ndarray:
     """Adjoint of the inverse map: F_inv^H g = the forward without weights."""
-    return forward(g, B, weights=False)
+    return forward(g, B, weights=False, rule=rule)

@@ -23,8 +23,8 @@ from paper_1604_05140_gb300 import inputs
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _cartesian(B):
-    r, th, ph, _, _ = O.grid(B)
+def _cartesian(B, rule="laguerre"):
+    r, th, ph, _, _ = O.grid(B, rule)
     R, TH, PH = np.meshgrid(r, th, ph, indexing="ij")
     return R * np.sin(TH) * np.cos(PH), R * np.sin(TH) * np.sin(PH), R * np.cos(TH), R
 
@@ -52,6 +52,66 @@ def test_closed_form_coefficients(B):
             if nm == name:
                 expect[O.omega(n, l, m)] = v
         np.testing.assert_allclose(fh, expect, atol=1e-13, rtol=0, err_msg=name)
+
+
+@pytest.mark.parametrize("B", [3, 5])
+def test_closed_form_coefficients_paper_grid(B):
+    # the same closed forms from samples on the paper's own grid: 2B
+    # half-range Gauss-Hermite radii (Thm 3.3, Eq. zwischenstufe_2)
+    x, y, z, R = _cartesian(B, "hermite")
+    assert x.shape == (2 * B, 2 * B, 2 * B)
+    funcs = {"one": np.ones_like(x), "z": z, "x": x, "y": y, "r2": R ** 2}
+    table = _closed_forms()
+    for name, f in funcs.items():
+        fh = O.forward(O.physical_to_weighted(f + 0j, B, "hermite"), B, rule="hermite")[0]
+        expect = np.zeros_like(fh)
+        for (nm, n, l, m, v) in table:
+            if nm == name:
+                expect[O.omega(n, l, m)] = v
+        np.testing.assert_allclose(fh, expect, atol=1e-13, rtol=0, err_msg=name)
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 32, 128, 256])
+def test_half_range_hermite_rule(N):
+    # Thm 3.3: the N-point Gauss rule for e^{-r^2} on [0, inf) has simple
+    # positive nodes, positive weights, and integrates r^k exactly for
+    # k <= 2N - 1: int_0^inf r^k e^{-r^2} dr = Gamma((k+1)/2) / 2.  Such a rule
+    # is unique, so these moments pin it.  Sums in logarithms (the weights
+    # reach e^{-650} at N = 256).
+    r, loga = O.half_range_hermite_rule(N)
+    assert r[0] > 0 and np.all(np.diff(r) > 0) and np.all(np.isfinite(loga))
+    for k in range(2 * N):
+        terms = loga + k * np.log(r)
+        mx = terms.max()
+        lhs = mx + np.log(np.exp(terms - mx).sum())
+        rhs = lgamma((k + 1) / 2) - np.log(2.0)
+        assert abs(lhs - rhs) < 2e-15 * max(1.0, abs(rhs)), (k, lhs, rhs)
+    if N == 1:  # one node: r_0 = mu_1 / mu_0 = 1/sqrt(pi), a_0 = mu_0 = sqrt(pi)/2
+        assert abs(r[0] - 1 / sqrt(pi)) < 1e-15 and abs(np.exp(loga[0]) - sqrt(pi) / 2) < 1e-15
+
+
+@pytest.mark.parametrize("B", [2, 3, 4])
+def test_paper_grid_direct_equals_separated(B):
+    # Algorithms 1/2 (brute force over the 8B^3 grid) against the separated
+    # stages on the paper's grid
+    c = inputs.random_coeffs(B, 2, seed=210 + B)
+    s = O.inverse(c, B, rule="hermite")
+    assert s.shape == (2, 2 * B, 2 * B, 2 * B)
+    np.testing.assert_allclose(O.inverse_direct(c, B, rule="hermite"), s, atol=1e-13 * np.abs(s).max())
+    g = np.random.default_rng(230 + B).standard_normal((2, 2 * B, 2 * B, 2 * B)) + 0j
+    f = O.forward(g, B, rule="hermite")
+    np.testing.assert_allclose(O.forward_direct(g, B, rule="hermite"), f, atol=1e-13 * np.abs(f).max())
+
+
+@pytest.mark.parametrize("B", [2, 4, 8, 16, 32])
+def test_sampling_theorem_round_trip_paper_grid(B):
+    # Thm 3.4 on the paper's own grid, at the error scale of its Table 1
+    # (which was measured on that grid)
+    c = inputs.random_coeffs(B, 3, seed=300 + B, dist="uniform")
+    back = O.forward(O.inverse(c, B, rule="hermite"), B, rule="hermite")
+    err = np.abs(back - c).max(axis=1)
+    am, asd, _, _ = _paper_table1()[B]
+    assert err.mean() < 10 * (am + 3 * asd), (err, am)
 
 
 def test_single_node_rule():
@@ -295,6 +355,7 @@ def _clear_caches():
     OM.legendre_table.cache_clear()
     OM.radial_table.cache_clear()
     OM.laguerre_rule.cache_clear()
+    OM.half_range_hermite_rule.cache_clear()
 
 
 def _closed_form_ok(B=3):
@@ -342,8 +403,8 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     # 4. radial recurrence with a wrong sign on the three-term coupling
     orig_rad = OM.radial_table.__wrapped__
 
-    def bad_radial(B):
-        T = orig_rad(B).copy()
+    def bad_radial(B, rule="laguerre"):
+        T = orig_rad(B, rule).copy()
         T[:, 1::2, :] *= -1.0  # flips every second n: breaks the r^2 pin
         return T
     monkeypatch.setattr(OM, "radial_table", bad_radial)
