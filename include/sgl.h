@@ -98,6 +98,20 @@ typedef enum {
 } sgl_samples;
 
 /*
+ * Radial grids.  SGL_GRID_LAGUERRE: B radii, the zeros of the generalized
+ * Laguerre polynomial L_B^(1/2) in t = r^2 (the default of sgl_plan; exact
+ * for bandlimit B: 4B^3 samples per function).  SGL_GRID_HALF_RANGE_HERMITE:
+ * the paper's own grid, 2B radii at the nodes of the half-range Gauss-Hermite
+ * rule of order 2B (Thm 3.3, Thm 3.4 / Eq. zwischenstufe_2: 8B^3 samples per
+ * function, samples [batch][i < 2B][j][k]).  The coefficients do not depend
+ * on the grid.
+ */
+typedef enum {
+  SGL_GRID_LAGUERRE = 0,
+  SGL_GRID_HALF_RANGE_HERMITE = 1
+} sgl_grid_kind;
+
+/*
  * Real functions (SGL_SAMPLES_REAL, sgl_plan only, every precision).  For a
  * real f the coefficients obey fhat_{n,l,-m} = (-1)^m conj(fhat_{n,l,m})
  * (Def 2.1: Y_l^{-m} = (-1)^m conj(Y_l^m), real radial part), so a real
@@ -142,6 +156,16 @@ typedef enum {
 sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples);
 
 /*
+ * sgl_plan_grid - sgl_plan on the radial grid `grid` (an sgl_grid_kind).
+ * SGL_GRID_LAGUERRE is sgl_plan itself.  SGL_GRID_HALF_RANGE_HERMITE needs
+ * SGL_FP64 or SGL_FP32 (the tensor-core precisions return
+ * SGL_ERR_UNSUPPORTED); every sample convention is accepted.  Sample counts,
+ * offsets, sgl_grid's r and w_r arrays and the host-buffer staging follow
+ * the plan's 2B radii.
+ */
+sgl_status sgl_plan_grid(sgl_plan_t* out, int B, int batch, int prec, int samples, int grid);
+
+/*
  * sgl_plan_many - one plan for nfn functions with their own bandlimits
  * B_per_fn[f] (each obeying the rules of sgl_plan), weighted samples.
  * Samples of function f start at element offset sgl_sample_offset(plan, f)
@@ -179,19 +203,22 @@ sgl_status sgl_adjoint(sgl_plan_t plan, int of_inverse, const void* in, void* ou
 
 /*
  * sgl_grid - copy the grid of function `fn` (0 for single-B plans) to host
- * arrays: r[B], theta[2B], phi[2B], w_r[B] (= what_i), w_theta[2B] (= beta_j).
+ * arrays: r[R], theta[2B], phi[2B], w_r[R] (= what_i), w_theta[2B]
+ * (= beta_j), with R = sgl_radii(plan, fn) (B, or 2B on the paper's grid).
  * Any pointer may be NULL to skip that array.
  */
 sgl_status sgl_grid(sgl_plan_t plan, int fn, double* r, double* theta, double* phi,
                     double* w_r, double* w_theta);
 
-/* Element counts and offsets (complex elements). */
+/* Element counts and offsets (complex elements; reals for the samples of
+ * SGL_SAMPLES_REAL plans). */
 int64_t sgl_sample_count(sgl_plan_t plan);           /* whole batch */
 int64_t sgl_coeff_count(sgl_plan_t plan);            /* whole batch */
 int64_t sgl_sample_offset(sgl_plan_t plan, int fn);  /* -1 if fn out of range */
 int64_t sgl_coeff_offset(sgl_plan_t plan, int fn);
 int     sgl_num_functions(sgl_plan_t plan);
 int     sgl_bandlimit(sgl_plan_t plan, int fn);      /* -1 if fn out of range */
+int     sgl_radii(sgl_plan_t plan, int fn);          /* radial nodes of fn; -1 if out of range */
 int64_t sgl_workspace_bytes(sgl_plan_t plan);        /* device bytes the plan holds */
 
 /* Number of kernel launches one sgl_forward / sgl_inverse call makes. */

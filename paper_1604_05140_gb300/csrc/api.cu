@@ -87,16 +87,17 @@ static void release_pipeline(Plan* P) {
   P->copy_stream = nullptr;
 }
 
-// Host tables depend on the bandlimit only; built once per process.
-static bool cached_tables(int B, HostTables& out, std::string& msg) {
+// Host tables depend on the bandlimit and the radial grid only; built once
+// per process.
+static bool cached_tables(int B, int grid, HostTables& out, std::string& msg) {
   static std::mutex mu;
-  static std::map<int, HostTables> cache;
+  static std::map<std::pair<int, int>, HostTables> cache;
   std::lock_guard<std::mutex> lock(mu);
-  auto it = cache.find(B);
+  auto it = cache.find({B, grid});
   if (it == cache.end()) {
     HostTables H;
-    if (!build_tables(B, H, msg)) return false;
-    it = cache.emplace(B, std::move(H)).first;
+    if (!build_tables(B, grid, H, msg)) return false;
+    it = cache.emplace(std::make_pair(B, grid), std::move(H)).first;
   }
   out = it->second;
   return true;
@@ -108,19 +109,19 @@ void sgl::pack_tables(const Plan& P, std::vector<real>& tab) {
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
     const HostTables& H = P.tables[s];
-    const int B = sg.B;
+    const int B = sg.B, R = sg.R;
     real* misc = tab.data() + sg.tab_misc;
-    for (int i = 0; i < B; ++i) {
+    for (int i = 0; i < R; ++i) {
       misc[i] = (real)H.what[i];
-      misc[B + i] = (real)exp(-0.5 * H.t[i]);
-      misc[2 * B + i] = (real)exp(0.5 * H.t[i]);
+      misc[R + i] = (real)exp(-0.5 * H.t[i]);
+      misc[2 * R + i] = (real)exp(0.5 * H.t[i]);
     }
-    for (int j = 0; j < 2 * B; ++j) misc[3 * B + j] = (real)H.beta[j];
+    for (int j = 0; j < 2 * B; ++j) misc[3 * R + j] = (real)H.beta[j];
     for (int k = 0; k < 2 * B; ++k) {
       // e^{-2 pi i k / 2B}
       long double ang = 3.141592653589793238462643383279502884L * (long double)k / (long double)B;
-      misc[5 * B + 2 * k] = (real)cosl(ang);
-      misc[5 * B + 2 * k + 1] = (real)(-sinl(ang));
+      misc[3 * R + 2 * B + 2 * k] = (real)cosl(ang);
+      misc[3 * R + 2 * B + 2 * k + 1] = (real)(-sinl(ang));
     }
     for (int m = 0; m < B; ++m)
       for (int p = 0; p < 2; ++p) {
@@ -138,10 +139,10 @@ void sgl::pack_tables(const Plan& P, std::vector<real>& tab) {
       const int64_t r0 = rad_rows_before(B, l);
       for (int q = 0; q < B - l; ++q) {
         const int n = l + 1 + q;
-        for (int i = 0; i < B; ++i) {
-          const double v = H.T[((size_t)l * B + (n - 1)) * B + i];
-          tab[sg.tab_rad_f + (r0 + q) * B + i] = (real)(H.what[i] * v);
-          tab[sg.tab_rad_i + (r0 + q) * B + i] = (real)v;
+        for (int i = 0; i < R; ++i) {
+          const double v = H.T[((size_t)l * B + (n - 1)) * R + i];
+          tab[sg.tab_rad_f + (r0 + q) * R + i] = (real)(H.what[i] * v);
+          tab[sg.tab_rad_i + (r0 + q) * R + i] = (real)v;
         }
       }
     }
@@ -164,7 +165,7 @@ static cudaError_t build_fft_lists(Plan& P) {
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
     const int JP = fft_jp(P, sg.B, false);
-    for (int sh = 0; sh < sg.NB * sg.B; ++sh)
+    for (int sh = 0; sh < sg.NB * sg.R; ++sh)
       for (int j0 = 0; j0 < sg.B; j0 += JP) ff.push_back(make_int4((int)s, sh, j0, 0));
   }
   if (P.d_fft_fwd) {
@@ -183,10 +184,10 @@ static cudaError_t build_fft_lists(Plan& P) {
       // the tensor-core Legendre synthesis stores spectra [m][b][j][i][c]: each
       // inverse-FFT CTA takes JP consecutive shells of one ring pair (layout 1)
       for (int b = 0; b < sg.NB; ++b)
-        for (int i0 = 0; i0 < sg.B; i0 += JP)
-          for (int jp = 0; jp < sg.B; ++jp) ff.push_back(make_int4((int)s, b * sg.B + i0, jp, 1));
+        for (int i0 = 0; i0 < sg.R; i0 += JP)
+          for (int jp = 0; jp < sg.B; ++jp) ff.push_back(make_int4((int)s, b * sg.R + i0, jp, 1));
     } else {
-      for (int sh = 0; sh < sg.NB * sg.B; ++sh)
+      for (int sh = 0; sh < sg.NB * sg.R; ++sh)
         for (int j0 = 0; j0 < sg.B; j0 += JP) ff.push_back(make_int4((int)s, sh, j0, 0));
     }
   }
@@ -209,7 +210,7 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
   for (int B : Bs) {
     P->fn_samp_off.push_back(so);
     P->fn_coef_off.push_back(co);
-    so += sample_count(B);
+    so += sample_count(B, n_radial(B, P->grid));
     co += coeff_count(B);
     P->maxB = std::max(P->maxB, B);
   }
@@ -224,6 +225,7 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
     SegDesc sg;
     memset(&sg, 0, sizeof(sg));
     sg.B = kv.first;
+    sg.R = n_radial(sg.B, P->grid);
     sg.NB = (int)kv.second.size();
     sg.n1 = fft_n1(2 * sg.B);
     sg.n2 = 2 * sg.B / sg.n1;
@@ -235,25 +237,25 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
     }
     sg.w1_off = w1;
     sg.w2_off = w2;
-    w1 += w1_size(sg.B, sg.NB);
-    w2 += w2_size(sg.B, sg.NB);
+    w1 += w1_size(sg.B, sg.NB, sg.R);
+    w2 += w2_size(sg.B, sg.NB, sg.R);
     sg.tab_misc = tab;
-    tab += misc_size(sg.B);
+    tab += misc_size(sg.B, sg.R);
     sg.tab_leg_f = tab;
     tab += leg_table_size(sg.B);
     sg.tab_leg_i = tab;
     tab += leg_table_size(sg.B);
     sg.tab_rad_f = tab;
-    tab += rad_table_size(sg.B);
+    tab += rad_table_size(sg.B, sg.R);
     sg.tab_rad_i = tab;
-    tab += rad_table_size(sg.B);
+    tab += rad_table_size(sg.B, sg.R);
     tab = (tab + 31) / 32 * 32;
     sg.si_rows = (int64_t)si_rows.size();
     for (int mi = 0; mi < 2 * sg.B - 1; ++mi)
       for (int p = 0; p < 2; ++p) si_rows.push_back(si_rows_before(sg.B, mi, p));
     HostTables H;
     std::string msg;
-    if (!cached_tables(sg.B, H, msg)) return fail(P, SGL_ERR_ARG, "table generation: " + msg);
+    if (!cached_tables(sg.B, P->grid, H, msg)) return fail(P, SGL_ERR_ARG, "table generation: " + msg);
     P->tables.push_back(std::move(H));
     P->segs.push_back(sg);
   }
@@ -299,11 +301,11 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
   std::vector<int4> lf, rf, ri, li;
   for (size_t s = 0; s < P->segs.size(); ++s) {
     const SegDesc& sg = P->segs[s];
-    const int B = sg.B, NB = sg.NB;
+    const int B = sg.B, NB = sg.NB, R = sg.R;
     for (int g = 0; g < 2 * (2 * B - 1); ++g) {
       const int m = (g >> 1) - (B - 1);
       const int N = n_par(B, m < 0 ? -m : m, g & 1);
-      const int rows = NB * 2 * B;
+      const int rows = NB * 2 * R;
       for (int r0 = 0; r0 < rows; r0 += TM)
         for (int c0 = 0; c0 < N; c0 += TN) lf.push_back(make_int4((int)s, g, r0, c0));
     }
@@ -311,11 +313,11 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
       const int rows = NB * (2 * l + 1) * 2;
       for (int r0 = 0; r0 < rows; r0 += TM) {
         for (int c0 = 0; c0 < B - l; c0 += TN) rf.push_back(make_int4((int)s, l, r0, c0));
-        for (int c0 = 0; c0 < B; c0 += TN) ri.push_back(make_int4((int)s, l, r0, c0));
+        for (int c0 = 0; c0 < R; c0 += TN) ri.push_back(make_int4((int)s, l, r0, c0));
       }
     }
     for (int mi = 0; mi < 2 * B - 1; ++mi) {
-      const int rows = NB * 2 * B;
+      const int rows = NB * 2 * R;
       for (int r0 = 0; r0 < rows; r0 += TM)
         for (int c0 = 0; c0 < B; c0 += TN) li.push_back(make_int4((int)s, mi, r0, c0));
     }
@@ -389,6 +391,7 @@ static sgl_status ensure_pipeline(Plan* P) {
     Plan* S = new Plan();
     S->prec = P->prec;
     S->samples = P->samples;
+    S->grid = P->grid;
     S->jp_fwd = P->jp_fwd;
     S->jp_inv = P->jp_inv;
     S->radi_narrow = P->radi_narrow;
@@ -429,8 +432,9 @@ static sgl_status execute_pipelined(Plan* P, bool is_fwd, bool weights, const vo
   if (st != SGL_OK) return st;
   const size_t cb = complex_bytes(*P);
   const int B = P->fn_B[0];
-  const size_t in_per = (size_t)(is_fwd ? sample_count(B) : coeff_count(B)) * cb;   // bytes per function
-  const size_t out_per = (size_t)(is_fwd ? coeff_count(B) : sample_count(B)) * cb;
+  const int64_t spf = sample_count(B, n_radial(B, P->grid));  // samples per function
+  const size_t in_per = (size_t)(is_fwd ? spf : coeff_count(B)) * cb;   // bytes per function
+  const size_t out_per = (size_t)(is_fwd ? coeff_count(B) : spf) * cb;
   const char* din = (const char*)in;
   char* dout = (char*)out;
   if (!in_dev) {
@@ -653,6 +657,10 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
 extern "C" {
 
 sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples) {
+  return sgl_plan_grid(out, B, batch, prec, samples, SGL_GRID_LAGUERRE);
+}
+
+sgl_status sgl_plan_grid(sgl_plan_t* out, int B, int batch, int prec, int samples, int grid) {
   if (!out) return fail(nullptr, SGL_ERR_ARG, "null output pointer");
   *out = nullptr;
   if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
@@ -662,12 +670,17 @@ sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples) {
     return fail(nullptr, SGL_ERR_ARG, "unknown sample convention");
   if (samples == SGL_SAMPLES_PHYSICAL && prec != SGL_FP64)
     return fail(nullptr, SGL_ERR_ARG, "physical samples need an FP64 plan");
+  if (grid != SGL_GRID_LAGUERRE && grid != SGL_GRID_HALF_RANGE_HERMITE)
+    return fail(nullptr, SGL_ERR_ARG, "unknown radial grid");
+  if (grid == SGL_GRID_HALF_RANGE_HERMITE && tc_precision(prec))
+    return fail(nullptr, SGL_ERR_UNSUPPORTED, "the half-range Gauss-Hermite grid needs an FP64 or FP32 plan");
   if (!bandlimit_supported(B)) return fail(nullptr, SGL_ERR_UNSUPPORTED, "unsupported bandlimit");
   if (tc_precision(prec) && B % 4 != 0)
     return fail(nullptr, SGL_ERR_UNSUPPORTED, "tensor-core plans need a bandlimit divisible by 4");
   Plan* P = new Plan();
   P->prec = prec;
   P->samples = samples;
+  P->grid = grid;
   const bool real = samples == SGL_SAMPLES_REAL;
   if (real) {  // the real functions in pairs, one complex function per pair
     P->real_pairs = true;
@@ -676,7 +689,7 @@ sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples) {
   std::vector<int> Bs(real ? (batch + 1) / 2 : batch, B);
   sgl_status st = build_plan(P, Bs, true);
   if (st == SGL_OK && real) {
-    P->n_samples = (int64_t)batch * sample_count(B);  // reals
+    P->n_samples = (int64_t)batch * sample_count(B, n_radial(B, grid));  // reals
     P->n_coeffs = (int64_t)batch * coeff_count(B);
     const int64_t cbytes = (int64_t)P->nfn * coeff_count(B) * (int64_t)complex_bytes(*P);
     if (cudaMalloc(&P->d_ccoef, cbytes) != cudaSuccess)
@@ -744,10 +757,10 @@ sgl_status sgl_grid(sgl_plan_t plan, int fn, double* r, double* theta, double* p
   size_t seg = 0;
   while (P->segs[seg].B != B) ++seg;
   const HostTables& H = P->tables[seg];
-  if (r) memcpy(r, H.r.data(), B * sizeof(double));
+  if (r) memcpy(r, H.r.data(), H.R * sizeof(double));
   if (theta) memcpy(theta, H.theta.data(), 2 * B * sizeof(double));
   if (phi) memcpy(phi, H.phi.data(), 2 * B * sizeof(double));
-  if (w_r) memcpy(w_r, H.what.data(), B * sizeof(double));
+  if (w_r) memcpy(w_r, H.what.data(), H.R * sizeof(double));
   if (w_theta) memcpy(w_theta, H.beta.data(), 2 * B * sizeof(double));
   return SGL_OK;
 }
@@ -758,7 +771,7 @@ int64_t sgl_coeff_count(sgl_plan_t plan) { return plan ? ((Plan*)plan)->n_coeffs
 int64_t sgl_sample_offset(sgl_plan_t plan, int fn) {
   Plan* P = (Plan*)plan;
   if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
-  if (P->real_pairs) return (int64_t)fn * sample_count(P->fn_B[0]);
+  if (P->real_pairs) return (int64_t)fn * sample_count(P->fn_B[0], n_radial(P->fn_B[0], P->grid));
   return P->fn_samp_off[fn];
 }
 
@@ -775,6 +788,13 @@ int sgl_bandlimit(sgl_plan_t plan, int fn) {
   Plan* P = (Plan*)plan;
   if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
   return P->fn_B[P->real_pairs ? 0 : fn];
+}
+
+int sgl_radii(sgl_plan_t plan, int fn) {
+  Plan* P = (Plan*)plan;
+  if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
+  const int B = P->fn_B[P->real_pairs ? 0 : fn];
+  return n_radial(B, P->grid);
 }
 
 int64_t sgl_workspace_bytes(sgl_plan_t plan) {

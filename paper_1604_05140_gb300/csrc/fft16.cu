@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   c2<real>* buf = tw + N;                                    // 2*JP rings of N
   const int4 cta = a.ctas[blockIdx.x];
   const SegDesc sg = a.segs[cta.x];
-  const int B = sg.B, NB = sg.NB;
+  const int B = sg.B, NB = sg.NB, NR = sg.R;  // NR radii
   const int shell = cta.y, j0 = cta.z;
-  const int b = shell / B, i = shell - b * B;
+  const int b = shell / NR, i = shell - b * NR;
   const int JPmax = a.JP;
   const int JP = min(JPmax, B - j0);
   const int R = 2 * JP;
@@ -159,13 +159,13 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   // read consecutive words
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const int e = (k % N2) * (k / N2);  // < N
-    tw[k] = {misc[5 * B + 2 * e], misc[5 * B + 2 * e + 1]};
+    tw[k] = {misc[3 * NR + 2 * B + 2 * e], misc[3 * NR + 2 * B + 2 * e + 1]};
   }
   real scale = 1;
-  if (a.mode == 1) scale = misc[B + i];
-  if (a.mode == 2) scale = misc[2 * B + i];
+  if (a.mode == 1) scale = misc[NR + i];
+  if (a.mode == 2) scale = misc[2 * NR + i];
   const c2<real>* in = reinterpret_cast<const c2<real>*>(a.in) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
-  const int64_t fn_reals = (int64_t)B * N * N;
+  const int64_t fn_reals = (int64_t)NR * N * N;
   const real* inA = reinterpret_cast<const real*>(a.in) + 2 * a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
   const bool hasB = PAIRS && 2 * a.fn_samp[sg.fn0 + b] + fn_reals < a.pair_limit;
   __syncthreads();
@@ -221,10 +221,10 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
     fft_n<real, N2, false>(x0);
     fft_n<real, N2, false>(x1);
     real* w1 = reinterpret_cast<real*>(a.w1) + sg.w1_off;
-    const int64_t sp = (int64_t)NB * 2 * B * B;               // stride of p
+    const int64_t sp = (int64_t)NB * 2 * NR * B;              // stride of p
     const int64_t sm = 2 * sp;                                // stride of m_idx
-    const int64_t base = (((int64_t)b * 2) * B + i) * B + j0 + q;  // c = 0, p = 0, m_idx = 0
-    const int64_t sc = (int64_t)B * B;                        // stride of c
+    const int64_t base = (((int64_t)b * 2) * NR + i) * B + j0 + q;  // c = 0, p = 0, m_idx = 0
+    const int64_t sc = (int64_t)NR * B;                       // stride of c
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) {
       const int k = k1 + 16 * k2;
@@ -251,18 +251,19 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
   c2<real>* buf = tw + N;
   const int4 cta = a.ctas[blockIdx.x];
   const SegDesc sg = a.segs[cta.x];
-  const int B = sg.B, NB = sg.NB;
+  const int B = sg.B, NB = sg.NB, NR = sg.R;  // NR radii
   // cta.w = 0: spectra stored [m][b][c][i][j]; the CTA owns shell i and ring
-  //            pairs j0 .. j0+JP-1 (cta.y = b*B + i, cta.z = j0);
+  //            pairs j0 .. j0+JP-1 (cta.y = b*NR + i, cta.z = j0);
   // cta.w = 1: spectra stored [m][b][j][i][c] (complex pairs); the CTA owns
-  //            shells i0 .. i0+JP-1 and the single ring pair jp (cta.y = b*B + i0, cta.z = jp)
+  //            shells i0 .. i0+JP-1 and the single ring pair jp (cta.y = b*NR + i0, cta.z = jp)
   const int lay = cta.w;
-  const int b = cta.y / B, i_or_i0 = cta.y - b * B, j_or_jp = cta.z;
+  const int b = cta.y / NR, i_or_i0 = cta.y - b * NR, j_or_jp = cta.z;
   const int JPmax = a.JP;
-  const int JP = min(JPmax, B - (lay ? i_or_i0 : j_or_jp));
+  const int JP = min(JPmax, lay ? NR - i_or_i0 : B - j_or_jp);
   const int R = 2 * JP;
   const real* misc = reinterpret_cast<const real*>(a.tab) + sg.tab_misc;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = {misc[5 * B + 2 * k], misc[5 * B + 2 * k + 1]};
+  for (int k = threadIdx.x; k < N; k += blockDim.x)
+    tw[k] = {misc[3 * NR + 2 * B + 2 * k], misc[3 * NR + 2 * B + 2 * k + 1]};
   __syncthreads();
 
   // step 1: items (q, k1); gather X[k1 + 16 k2] of both rings, inverse
@@ -276,11 +277,11 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
     const int jB = N - 1 - jA;
     c2<real> x0[N2], x1[N2];
     if (lay) {
-      // complex element (m_idx, j, i) of function b: m_idx*sm + b*N*B + j*B + i
+      // complex element (m_idx, j, i) of function b: m_idx*sm + b*N*NR + j*NR + i
       const c2<real>* gc = reinterpret_cast<const c2<real>*>(g);
-      const int64_t sm = (int64_t)NB * N * B;
-      const int64_t base = (int64_t)b * N * B + iq;
-      const int64_t oA = base + (int64_t)jA * B, oB = base + (int64_t)jB * B;
+      const int64_t sm = (int64_t)NB * N * NR;
+      const int64_t base = (int64_t)b * N * NR + iq;
+      const int64_t oA = base + (int64_t)jA * NR, oB = base + (int64_t)jB * NR;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
         const int k = k1 + 16 * k2;
@@ -296,9 +297,9 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
       }
     } else {
       // element (m_idx, c, j) of ring (b, iq): m_idx*sm + c*sc + base + j
-      const int64_t sm = (int64_t)NB * 2 * B * N;
-      const int64_t sc = (int64_t)B * N;
-      const int64_t base = (((int64_t)b * 2) * B + iq) * N;
+      const int64_t sm = (int64_t)NB * 2 * NR * N;
+      const int64_t sc = (int64_t)NR * N;
+      const int64_t base = (((int64_t)b * 2) * NR + iq) * N;
       const int64_t oA = base + jA, oB = base + jB;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
@@ -339,12 +340,12 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
     const int jq = lay ? j_or_jp : j_or_jp + qq;
     const int j = (r & 1) ? (N - 1 - jq) : jq;
     real s = 1;
-    if (a.mode == 1) s = misc[2 * B + i];
+    if (a.mode == 1) s = misc[2 * NR + i];
     if (a.mode == 2) s = misc[i];
-    if (a.mode == 3) s = misc[i] * misc[B + i];
-    if (a.mode >= 2) s *= misc[3 * B + j];
+    if (a.mode == 3) s = misc[i] * misc[NR + i];
+    if (a.mode >= 2) s *= misc[3 * NR + j];
     if constexpr (PAIRS) {
-      const int64_t fn_reals = (int64_t)B * N * N;
+      const int64_t fn_reals = (int64_t)NR * N * N;
       const int64_t f0 = 2 * a.fn_samp[sg.fn0 + b];
       real* ringA = reinterpret_cast<real*>(a.out) + f0 + ((int64_t)i * N + j) * N + n2;
 #pragma unroll

@@ -185,10 +185,10 @@ __global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int4 cta = a.ctas[blockIdx.x];
   const SegDesc sg = a.segs[cta.x];
-  const int B = sg.B, N = 2 * B, NB = sg.NB;
+  const int B = sg.B, N = 2 * B, NB = sg.NB, NR = sg.R;  // NR radii
   const int n2 = sg.n2;
   const int shell = cta.y, j0 = cta.z;
-  const int b = shell / B, i = shell - b * B;
+  const int b = shell / NR, i = shell - b * NR;
   const int JP = min(a.JP, B - j0);
   const int R = 2 * JP;
   const int pitch = ring_pitch(N1, n2);
@@ -198,16 +198,16 @@ __global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
   real* sim = sre + 2 * a.JP * pitch;
   const real* misc = reinterpret_cast<const real*>(a.tab) + sg.tab_misc;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    wre[k] = misc[5 * B + 2 * k];
-    wim[k] = misc[5 * B + 2 * k + 1];
+    wre[k] = misc[3 * NR + 2 * B + 2 * k];
+    wim[k] = misc[3 * NR + 2 * B + 2 * k + 1];
   }
   real scale = 1;
-  if (a.mode == 1) scale = misc[B + i];
-  if (a.mode == 2) scale = misc[2 * B + i];
+  if (a.mode == 1) scale = misc[NR + i];
+  if (a.mode == 2) scale = misc[2 * NR + i];
   const cx<real>* in = reinterpret_cast<const cx<real>*>(a.in) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
   // real functions in pairs: the pair's first function starts at twice the
   // complex offset (in reals), the second one function later
-  const int64_t fn_reals = (int64_t)B * N * N;
+  const int64_t fn_reals = (int64_t)NR * N * N;
   const real* inA = reinterpret_cast<const real*>(a.in) + 2 * a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
   const bool hasB = 2 * a.fn_samp[sg.fn0 + b] + fn_reals < a.pair_limit;
   for (int e = threadIdx.x; e < R * N; e += blockDim.x) {
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
     const real g0 = plane[(2 * q) * pitch + slot];
     const real g1 = plane[(2 * q + 1) * pitch + slot];
     const real v = p ? (g0 - g1) : (g0 + g1);
-    w1[(((((int64_t)m_idx * 2 + p) * NB + b) * 2 + c) * B + i) * B + j0 + q] = v;
+    w1[(((((int64_t)m_idx * 2 + p) * NB + b) * 2 + c) * NR + i) * B + j0 + q] = v;
   }
 }
 
@@ -252,14 +252,14 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int4 cta = a.ctas[blockIdx.x];
   const SegDesc sg = a.segs[cta.x];
-  const int B = sg.B, N = 2 * B, NB = sg.NB;
+  const int B = sg.B, N = 2 * B, NB = sg.NB, NR = sg.R;  // NR radii
   const int n2 = sg.n2;
   // cta.w selects the spectra layout (see fft16_inv_kernel): 0 -> one shell
-  // i = cta.y % B and ring pairs j0 = cta.z ...; 1 -> shells i0 = cta.y % B ...
+  // i = cta.y % NR and ring pairs j0 = cta.z ...; 1 -> shells i0 = cta.y % NR ...
   // and one ring pair jp = cta.z
   const int lay = cta.w;
-  const int b = cta.y / B, i_or_i0 = cta.y - b * B, j0 = cta.z;
-  const int JP = min(a.JP, B - (lay ? i_or_i0 : j0));
+  const int b = cta.y / NR, i_or_i0 = cta.y - b * NR, j0 = cta.z;
+  const int JP = min(a.JP, lay ? NR - i_or_i0 : B - j0);
   const int R = 2 * JP;
   const int pitch = ring_pitch(N1, n2);
   real* wre = reinterpret_cast<real*>(smem_raw);
@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
   real* sim = sre + 2 * a.JP * pitch;
   const real* misc = reinterpret_cast<const real*>(a.tab) + sg.tab_misc;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    wre[k] = misc[5 * B + 2 * k];
-    wim[k] = misc[5 * B + 2 * k + 1];
+    wre[k] = misc[3 * NR + 2 * B + 2 * k];
+    wim[k] = misc[3 * NR + 2 * B + 2 * k + 1];
   }
   // ring r (layout 0): r < JP -> j = j0 + r; r >= JP -> j = N - j0 - 2*JP + r (mirror run)
   // ring r (layout 1): shell i0 + (r mod JP), j = jp (r < JP) or N - 1 - jp
@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
     const int k = m >= 0 ? m : N + m;
     const int i = ring_i(r), j = ring_j(r);
     // layout 0: [m_idx][b][c][i][j]; layout 1: [m_idx][b][j][i][c]
-    const real v = lay ? g[(((int64_t)m_idx * NB + b) * N + j) * (2 * B) + 2 * i + c]
-                       : g[(((int64_t)m_idx * NB + b) * 2 + c) * B * N + (int64_t)i * N + j];
+    const real v = lay ? g[(((int64_t)m_idx * NB + b) * N + j) * (2 * NR) + 2 * i + c]
+                       : g[(((int64_t)m_idx * NB + b) * 2 + c) * NR * N + (int64_t)i * N + j];
     const int c1 = k / n2, c2 = k - c1 * n2;
     (c ? sim : sre)[r * pitch + c1 * (n2 + 1) + c2] = v;
   }
@@ -304,16 +304,16 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
     const int i = ring_i(r), j = ring_j(r);
     const int slot = (k % N1) * (n2 + 1) + k / N1;
     real s = 1;
-    if (a.mode == 1) s = misc[2 * B + i];
+    if (a.mode == 1) s = misc[2 * NR + i];
     if (a.mode == 2) s = misc[i];
-    if (a.mode == 3) s = misc[i] * misc[B + i];
-    if (a.mode >= 2) s *= misc[3 * B + j];
+    if (a.mode == 3) s = misc[i] * misc[NR + i];
+    if (a.mode >= 2) s *= misc[3 * NR + j];
     cx<real> v = {sre[r * pitch + slot] * s, sim[r * pitch + slot] * s};
     const int64_t o = ((int64_t)i * N + j) * N + k;
     if (a.pair_limit) {  // real and imaginary parts to the pair's two functions
       real* outA = reinterpret_cast<real*>(a.out) + 2 * a.fn_samp[sg.fn0 + b];
       outA[o] = v.x;
-      if (2 * a.fn_samp[sg.fn0 + b] + (int64_t)B * N * N < a.pair_limit) outA[(int64_t)B * N * N + o] = v.y;
+      if (2 * a.fn_samp[sg.fn0 + b] + (int64_t)NR * N * N < a.pair_limit) outA[(int64_t)NR * N * N + o] = v.y;
     } else {
       out[o] = v;
     }
@@ -352,7 +352,8 @@ __device__ __forceinline__ int n_par_d(int B, int m, int p) {
 }
 
 struct GroupCtx {
-  int B, NB, rows, N, K, KP, KPpad;
+  int B, NB, R, rows, N, K, KP, KPpad;
+  int xs, as;  // row strides of X (forward stages) and of the table A
   int g;       // group id within the stage
   int m, am, p, l, m_idx;
   int64_t xbase, xbase2, abase, abase2;
@@ -362,43 +363,48 @@ template <int PROB>
 __device__ __forceinline__ void group_setup(const GemmArgs& a, const SegDesc& sg, int g, GroupCtx& c) {
   c.B = sg.B;
   c.NB = sg.NB;
+  c.R = sg.R;
   c.g = g;
-  const int B = sg.B, NB = sg.NB;
+  const int B = sg.B, NB = sg.NB, R = sg.R;  // R radii
   if (PROB == LEG_F) {
     c.m_idx = g >> 1;
     c.p = g & 1;
     c.m = c.m_idx - (B - 1);
     c.am = c.m < 0 ? -c.m : c.m;
-    c.rows = NB * 2 * B;
+    c.rows = NB * 2 * R;
     c.N = n_par_d(B, c.am, c.p);
     c.K = B;
-    c.xbase = sg.w1_off + ((int64_t)c.m_idx * 2 + c.p) * NB * 2 * B * B;
+    c.xs = c.as = B;
+    c.xbase = sg.w1_off + ((int64_t)c.m_idx * 2 + c.p) * NB * 2 * R * B;
     c.abase = (a.weighted ? sg.tab_leg_f : sg.tab_leg_i) + leg_rows_before_d(B, c.am, c.p) * B;
   } else if (PROB == RAD_F) {
     c.l = g;
     c.rows = NB * (2 * c.l + 1) * 2;
     c.N = B - c.l;
-    c.K = B;
-    c.xbase = sg.w2_off + (int64_t)NB * 2 * B * c.l * c.l;
-    c.abase = (a.weighted ? sg.tab_rad_f : sg.tab_rad_i) + ((int64_t)c.l * B - (int64_t)c.l * (c.l - 1) / 2) * B;
+    c.K = R;
+    c.xs = c.as = R;
+    c.xbase = sg.w2_off + (int64_t)NB * 2 * R * c.l * c.l;
+    c.abase = (a.weighted ? sg.tab_rad_f : sg.tab_rad_i) + ((int64_t)c.l * B - (int64_t)c.l * (c.l - 1) / 2) * R;
   } else if (PROB == RAD_I) {
     c.l = g;
     c.rows = NB * (2 * c.l + 1) * 2;
-    c.N = B;
+    c.N = R;
     c.K = B - c.l;
-    c.abase = sg.tab_rad_i + ((int64_t)c.l * B - (int64_t)c.l * (c.l - 1) / 2) * B;
+    c.as = R;
+    c.abase = sg.tab_rad_i + ((int64_t)c.l * B - (int64_t)c.l * (c.l - 1) / 2) * R;
   } else {  // LEG_I
     c.m_idx = g;
     c.m = g - (B - 1);
     c.am = c.m < 0 ? -c.m : c.m;
-    c.rows = NB * 2 * B;
+    c.rows = NB * 2 * R;
     c.N = B;
+    c.as = B;
     c.KP = n_par_d(B, c.am, 0);
     c.KPpad = (c.KP + TK - 1) / TK * TK;
     c.K = c.KPpad + n_par_d(B, c.am, 1);
     const int64_t* sr = a.si_rows + sg.si_rows;
-    c.xbase = sg.w2_off + sr[2 * c.m_idx] * (int64_t)NB * 2 * B;
-    c.xbase2 = sg.w2_off + sr[2 * c.m_idx + 1] * (int64_t)NB * 2 * B;
+    c.xbase = sg.w2_off + sr[2 * c.m_idx] * (int64_t)NB * 2 * R;
+    c.xbase2 = sg.w2_off + sr[2 * c.m_idx + 1] * (int64_t)NB * 2 * R;
     c.abase = sg.tab_leg_i + leg_rows_before_d(B, c.am, 0) * B;
     c.abase2 = sg.tab_leg_i + leg_rows_before_d(B, c.am, 1) * B;
   }
@@ -409,7 +415,7 @@ __device__ __forceinline__ real load_x(const GemmArgs& a, const SegDesc& sg, con
   const real* X = reinterpret_cast<const real*>(a.x);
   if (row >= c.rows || k >= c.K) return 0;
   if (PROB == LEG_F || PROB == RAD_F) {
-    return X[c.xbase + (int64_t)row * c.B + k];
+    return X[c.xbase + (int64_t)row * c.xs + k];
   } else if (PROB == RAD_I) {
     const int per_b = (2 * c.l + 1) * 2;
     const int b = row / per_b;
@@ -418,12 +424,12 @@ __device__ __forceinline__ real load_x(const GemmArgs& a, const SegDesc& sg, con
     const int64_t off = a.fn_coef[sg.fn0 + b] + omega_idx(c.l + 1 + k, c.l, mm - c.l);
     return X[2 * off + cc];
   } else {
-    const int64_t NB2B = (int64_t)c.NB * 2 * c.B;
+    const int64_t NB2R = (int64_t)c.NB * 2 * c.R;  // one l' row of S_i
     if (k < c.KPpad) {
       if (k >= c.KP) return 0;
-      return X[c.xbase + k * NB2B + row];
+      return X[c.xbase + k * NB2R + row];
     }
-    return X[c.xbase2 + (k - c.KPpad) * NB2B + row];
+    return X[c.xbase2 + (k - c.KPpad) * NB2R + row];
   }
 }
 
@@ -432,15 +438,15 @@ __device__ __forceinline__ real load_a(const GemmArgs& a, const GroupCtx& c, int
   const real* A = reinterpret_cast<const real*>(a.tab);
   if (col >= c.N || k >= c.K) return 0;
   if (PROB == LEG_F || PROB == RAD_F) {
-    return A[c.abase + (int64_t)col * c.B + k];
+    return A[c.abase + (int64_t)col * c.as + k];
   } else if (PROB == RAD_I) {
-    return A[c.abase + (int64_t)k * c.B + col];
+    return A[c.abase + (int64_t)k * c.as + col];
   } else {
     if (k < c.KPpad) {
       if (k >= c.KP) return 0;
-      return A[c.abase + (int64_t)k * c.B + col];
+      return A[c.abase + (int64_t)k * c.as + col];
     }
-    return A[c.abase2 + (int64_t)(k - c.KPpad) * c.B + col];
+    return A[c.abase2 + (int64_t)(k - c.KPpad) * c.as + col];
   }
 }
 
@@ -449,14 +455,14 @@ __device__ __forceinline__ void store_y(const GemmArgs& a, const SegDesc& sg, co
                                         real v, real v2) {
   if (row >= c.rows || col >= c.N) return;
   real* Y = reinterpret_cast<real*>(a.y);
-  const int B = c.B, NB = c.NB;
+  const int B = c.B, NB = c.NB, R = c.R;
   if (PROB == LEG_F) {
-    const int b = row / (2 * B);
-    const int cc = (row / B) & 1;
-    const int i = row % B;
+    const int b = row / (2 * R);
+    const int cc = (row / R) & 1;
+    const int i = row % R;
     const int l = c.am + c.p + 2 * col;
     const real s = (c.m < 0 && (c.am & 1)) ? real(-1) : real(1);
-    Y[sg.w2_off + (int64_t)NB * 2 * B * l * l + (((int64_t)b * (2 * l + 1) + (c.m + l)) * 2 + cc) * B + i] = s * v;
+    Y[sg.w2_off + (int64_t)NB * 2 * R * l * l + (((int64_t)b * (2 * l + 1) + (c.m + l)) * 2 + cc) * R + i] = s * v;
   } else if (PROB == RAD_F) {
     const int per_b = (2 * c.l + 1) * 2;
     const int b = row / per_b;
@@ -475,10 +481,10 @@ __device__ __forceinline__ void store_y(const GemmArgs& a, const SegDesc& sg, co
     const int lp = (c.l - am - p) >> 1;
     const int m_idx = m + B - 1;
     const int64_t srow = a.si_rows[sg.si_rows + 2 * m_idx + p] + lp;
-    Y[sg.w2_off + srow * NB * 2 * B + ((int64_t)b * 2 + cc) * B + col] = v;
+    Y[sg.w2_off + srow * NB * 2 * R + ((int64_t)b * 2 + cc) * R + col] = v;
   } else {
     const real s = (c.m < 0 && (c.am & 1)) ? real(-1) : real(1);
-    const int64_t base = sg.w1_off + (int64_t)c.m_idx * NB * 2 * B * 2 * B + (int64_t)row * 2 * B;
+    const int64_t base = sg.w1_off + (int64_t)c.m_idx * NB * 2 * R * 2 * B + (int64_t)row * 2 * B;
     Y[base + col] = s * (v + v2);
     Y[base + 2 * B - 1 - col] = s * (v - v2);
   }
@@ -607,8 +613,8 @@ static void fft_slices(const Plan& P, std::vector<FftSlice>& out, bool inv) {
   for (size_t s = 0; s < P.segs.size(); ++s) {
     const SegDesc& sg = P.segs[s];
     const int JP = fft_jp(P, sg.B, inv);
-    const int per_shell = (sg.B + JP - 1) / JP;
-    const int count = sg.NB * sg.B * per_shell;
+    const int per_shell = (sg.B + JP - 1) / JP;  // ring-pair groups per shell
+    const int count = sg.NB * sg.R * per_shell;   // R shells per function (R = B on the tensor-core path)
     // kernel class: the register FFT for 2B = 16 * {8, 16}, else the general
     // kernel of factor n1 with a run-time n2
     const int cls = (sg.n1 == 16 && (sg.n2 == 8 || sg.n2 == 16)) ? 100 + sg.n2 : sg.n1;

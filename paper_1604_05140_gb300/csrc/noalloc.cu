@@ -77,39 +77,40 @@ sgl_status describe(DeviceState& D, int B, int batch) {
   P.samples = SGL_SAMPLES_WEIGHTED;
   P.nfn = batch;
   P.maxB = B;
-  P.n_samples = sample_count(B) * batch;
+  P.n_samples = sample_count(B, B) * batch;
   P.n_coeffs = coeff_count(B) * batch;
   SegDesc sg;
   memset(&sg, 0, sizeof(sg));
   sg.B = B;
+  sg.R = B;  // the Gauss-Laguerre grid
   sg.NB = batch;
   sg.n1 = fft_n1(2 * B);
   sg.n2 = 2 * B / sg.n1;
   sg.fn0 = 0;
   sg.w1_off = 0;
-  sg.w2_off = w1_size(B, batch);
+  sg.w2_off = w1_size(B, batch, B);
   int64_t tab = 0;
   sg.tab_misc = tab;
-  tab += misc_size(B);
+  tab += misc_size(B, B);
   sg.tab_leg_f = tab;
   tab += leg_table_size(B);
   sg.tab_leg_i = tab;
   tab += leg_table_size(B);
   sg.tab_rad_f = tab;
-  tab += rad_table_size(B);
+  tab += rad_table_size(B, B);
   sg.tab_rad_i = tab;
-  tab += rad_table_size(B);
+  tab += rad_table_size(B, B);
   sg.si_rows = 0;
   P.tab_elems = tab;
   HostTables H;
   std::string msg;
-  if (!build_tables(B, H, msg)) return fail(SGL_ERR_ARG, "table generation: " + msg);
+  if (!build_tables(B, SGL_GRID_LAGUERRE, H, msg)) return fail(SGL_ERR_ARG, "table generation: " + msg);
   P.tables.push_back(std::move(H));
   P.segs.push_back(sg);
 
   std::vector<int64_t> fn_samp(batch), fn_coef(batch), si_rows;
   for (int b = 0; b < batch; ++b) {
-    fn_samp[b] = sample_count(B) * b;
+    fn_samp[b] = sample_count(B, B) * b;
     fn_coef[b] = coeff_count(B) * b;
   }
   for (int mi = 0; mi < 2 * B - 1; ++mi)
@@ -180,7 +181,7 @@ extern "C" sgl_status sgl_forward_noalloc(int B, int batch, const void* samples,
     return fail(SGL_ERR_UNSUPPORTED, "sgl_forward_noalloc accepts bandlimits 1.." + std::to_string(kMaxB));
   if (batch < 1) return fail(SGL_ERR_ARG, "batch must be >= 1");
   if (!samples || !coeffs) return fail(SGL_ERR_ARG, "null data pointer");
-  const size_t need = (size_t)(w1_size(B, batch) + w2_size(B, batch));
+  const size_t need = (size_t)(w1_size(B, batch, B) + w2_size(B, batch, B));
   if (need > kScratchDoubles)
     return fail(SGL_ERR_UNSUPPORTED, "B=" + std::to_string(B) + " batch=" + std::to_string(batch) + " needs " +
                                          std::to_string(need) + " scratch doubles; the static scratch holds " +

@@ -16,15 +16,19 @@ namespace sgl {
 // ---------------------------------------------------------------------------
 struct HostTables {
   int B = 0;
-  std::vector<double> t, r, what;          // [B]   radial nodes t_i = r_i^2, weights what_i
+  int R = 0;                               // radii: B, or 2B on the paper's grid
+  std::vector<double> t, r, what;          // [R]   radial nodes t_i = r_i^2, weights what_i
   std::vector<double> theta, phi, beta;    // [2B]  sphere rule (Thm 3.1, beta = pi/B b_j)
   std::vector<double> lam;                 // [m][l][j'] m,l < B, j' < B: Lambda_lm(theta_j')
-  std::vector<double> T;                   // [l][n-1][i]: N_nl R_nl(r_i) exp(-t_i/2)
+  std::vector<double> T;                   // [l][n-1][i < R]: N_nl R_nl(r_i) exp(-t_i/2)
 };
 
-// Builds every table for bandlimit B (1 <= B <= SGL_MAX_B).  Returns false and
-// sets msg on failure.
-bool build_tables(int B, HostTables& out, std::string& msg);
+// Builds every table for bandlimit B (1 <= B <= SGL_MAX_B) on the radial grid
+// `grid` (an sgl_grid_kind).  Returns false and sets msg on failure.
+bool build_tables(int B, int grid, HostTables& out, std::string& msg);
+
+// Radii of the grid of bandlimit B.
+inline int n_radial(int B, int grid) { return grid == SGL_GRID_HALF_RANGE_HERMITE ? 2 * B : B; }
 
 // Number of degrees l >= m with (l - m) % 2 == p, l < B.
 inline int n_par(int B, int m, int p) {
@@ -52,18 +56,19 @@ inline int tc_products(int prec) { return prec == SGL_TF32 ? 1 : 3; }
 inline bool tc_bf16(int prec) { return prec == SGL_BF16X3; }
 
 inline int64_t coeff_count(int B) { return (int64_t)B * (B + 1) * (2 * B + 1) / 6; }
-inline int64_t sample_count(int B) { return 4LL * B * B * B; }
+// samples of one function: R radii x 2B x 2B (R = B, or 2B on the paper's grid)
+inline int64_t sample_count(int B, int R) { return 4LL * R * B * B; }
 
 // ---------------------------------------------------------------------------
 // Table and workspace layouts (reals)
 // ---------------------------------------------------------------------------
-// Misc block of one bandlimit:
-//   [0, B)      what_i
-//   [B, 2B)     exp(-t_i/2)
-//   [2B, 3B)    exp(+t_i/2)
-//   [3B, 5B)    beta_j, j < 2B
-//   [5B, 9B)    twiddles e^{-2 pi i k/(2B)} as (re, im), k < 2B
-inline int64_t misc_size(int B) { return 9LL * B; }
+// Misc block of one bandlimit with R radii:
+//   [0, R)            what_i
+//   [R, 2R)           exp(-t_i/2)
+//   [2R, 3R)          exp(+t_i/2)
+//   [3R, 3R+2B)       beta_j, j < 2B
+//   [3R+2B, 3R+6B)    twiddles e^{-2 pi i k/(2B)} as (re, im), k < 2B
+inline int64_t misc_size(int B, int R) { return 3LL * R + 6LL * B; }
 
 // Legendre block: for m = 0..B-1, p = 0,1: n_par(B,m,p) rows of B reals over
 // the half grid j' < B; row q of (m,p) is degree l = m + p + 2q.
@@ -73,17 +78,19 @@ inline int64_t leg_rows_before(int B, int m, int p) {
   return rows;
 }
 inline int64_t leg_table_size(int B) { return (int64_t)B * (B + 1) / 2 * B; }
-// Radial block: [l][n' < B-l][i < B], row n' is degree n = l + 1 + n'.
+// Radial block: [l][n' < B-l][i < R], row n' is degree n = l + 1 + n'.
 inline int64_t rad_rows_before(int B, int l) { return (int64_t)l * B - (int64_t)l * (l - 1) / 2; }
-inline int64_t rad_table_size(int B) { return (int64_t)B * (B + 1) / 2 * B; }
+inline int64_t rad_table_size(int B, int R) { return (int64_t)B * (B + 1) / 2 * R; }
 
-// Workspaces of a segment of NB functions with one bandlimit B:
-//   W1 forward "EO":  [m_idx < 2B-1][p<2][b<NB][c<2][i<B][j'<B]      (E = G_j'+G_mirror, O = G_j'-G_mirror)
-//   W1 inverse "G":   [m_idx < 2B-1][b<NB][c<2][i<B][j<2B]
-//   W2 forward "S_f": block l at NB*2*B*l^2: [b][m+l < 2l+1][c][i<B]
-//   W2 inverse "S_i": block (m_idx,p) at NB*2*B*si_rows_before: [l'<n_par][b][c][i<B]
-inline int64_t w1_size(int B, int NB) { return 4LL * NB * B * B * (2 * B - 1); }
-inline int64_t w2_size(int B, int NB) { return 2LL * NB * B * B * B; }
+// Workspaces of a segment of NB functions with one bandlimit B and R radii
+// (the tensor-core path stores W1 inverse as [m_idx][b][j][i][c] and S_i rows
+// as [b][i][c], R = B there):
+//   W1 forward "EO":  [m_idx < 2B-1][p<2][b<NB][c<2][i<R][j'<B]      (E = G_j'+G_mirror, O = G_j'-G_mirror)
+//   W1 inverse "G":   [m_idx < 2B-1][b<NB][c<2][i<R][j<2B]
+//   W2 forward "S_f": block l at NB*2*R*l^2: [b][m+l < 2l+1][c][i<R]
+//   W2 inverse "S_i": block (m_idx,p) at NB*2*R*si_rows_before: [l'<n_par][b][c][i<R]
+inline int64_t w1_size(int B, int NB, int R) { return 4LL * NB * R * B * (2 * B - 1); }
+inline int64_t w2_size(int B, int NB, int R) { return 2LL * NB * B * B * R; }
 inline int64_t si_rows_before(int B, int m_idx, int p) {
   int64_t rows = 0;
   for (int mi = 0; mi < m_idx; ++mi) {
@@ -130,7 +137,7 @@ struct SegDesc {
   int B, NB;          // bandlimit, functions in the segment
   int n1, n2;         // 2B = n1 * n2 (phi-FFT factors)
   int fn0;            // first entry of the segment in the per-function offset arrays
-  int pad;
+  int R;              // radii: B, or 2B on the paper's grid
   int64_t w1_off, w2_off;               // reals
   int64_t tab_leg_f, tab_leg_i;         // reals: Legendre tables (fwd: * beta, inv: plain)
   int64_t tab_rad_f, tab_rad_i;         // reals: radial tables (fwd: * what, inv: plain)
@@ -139,7 +146,7 @@ struct SegDesc {
 };
 
 // Tile of a GEMM stage: (segment, group, row0, col0)
-// FFT CTA:            (segment, shell = b*B + i, j'0, 0)
+// FFT CTA:            (segment, shell = b*R + i, j'0, 0)
 
 struct GemmSched {
   int4* d_tiles = nullptr;
@@ -149,6 +156,7 @@ struct GemmSched {
 struct Plan {
   int prec = SGL_FP64;
   int samples = SGL_SAMPLES_WEIGHTED;
+  int grid = SGL_GRID_LAGUERRE;  // radial grid (sgl_grid_kind)
   int nfn = 0;
   bool uniform = true;
   int maxB = 0;

@@ -25,6 +25,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "sgl.h")
 SGL_OK, SGL_ERR_ARG, SGL_ERR_ALLOC, SGL_ERR_CUDA, SGL_ERR_TIMEOUT, SGL_ERR_UNSUPPORTED = range(6)
 SGL_FP64, SGL_FP32, SGL_TF32X3, SGL_TF32, SGL_BF16X3 = 0, 1, 2, 3, 4
 SGL_SAMPLES_WEIGHTED, SGL_SAMPLES_PHYSICAL, SGL_SAMPLES_REAL = 0, 1, 2
+SGL_GRID_LAGUERRE, SGL_GRID_HALF_RANGE_HERMITE = 0, 1
+GRIDS = {"laguerre": SGL_GRID_LAGUERRE, "hermite": SGL_GRID_HALF_RANGE_HERMITE}
 SGL_MAX_B = 128
 
 PRECISIONS = {"fp64": SGL_FP64, "fp32": SGL_FP32, "tf32x3": SGL_TF32X3, "tf32": SGL_TF32, "bf16x3": SGL_BF16X3}
@@ -55,6 +57,7 @@ def load_library():
     dp = ctypes.POINTER(ctypes.c_double)
     sigs = {
         "sgl_plan": (i32, [ctypes.POINTER(vp), i32, i32, i32, i32]),
+        "sgl_plan_grid": (i32, [ctypes.POINTER(vp), i32, i32, i32, i32, i32]),
         "sgl_plan_many": (i32, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), i32, i32]),
         "sgl_forward": (i32, [vp, vp, vp, vp]),
         "sgl_inverse": (i32, [vp, vp, vp, vp]),
@@ -66,6 +69,7 @@ def load_library():
         "sgl_coeff_offset": (i64, [vp, i32]),
         "sgl_num_functions": (i32, [vp]),
         "sgl_bandlimit": (i32, [vp, i32]),
+        "sgl_radii": (i32, [vp, i32]),
         "sgl_workspace_bytes": (i64, [vp]),
         "sgl_launches_per_call": (i32, [vp]),
         "sgl_check": (i32, [vp, vp]),
@@ -113,6 +117,14 @@ def sgl_plan(B: int, batch: int = 1, prec: int = SGL_FP64, samples: int = SGL_SA
     return h
 
 
+def sgl_plan_grid(B: int, batch: int = 1, prec: int = SGL_FP64, samples: int = SGL_SAMPLES_WEIGHTED,
+                  grid: int = SGL_GRID_LAGUERRE):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.sgl_plan_grid(ctypes.byref(h), int(B), int(batch), int(prec), int(samples), int(grid)))
+    return h
+
+
 def sgl_plan_many(Bs: Sequence[int], prec: int = SGL_TF32X3):
     lib = load_library()
     arr = (ctypes.c_int * len(Bs))(*[int(b) for b in Bs])
@@ -138,7 +150,8 @@ def sgl_grid(plan, fn: int = 0):
     B = lib.sgl_bandlimit(plan, fn)
     if B < 1:
         raise SGLError(SGL_ERR_ARG, "function index out of range")
-    r, th, ph, wr, wt = (np.zeros(n) for n in (B, 2 * B, 2 * B, B, 2 * B))
+    R = lib.sgl_radii(plan, fn)
+    r, th, ph, wr, wt = (np.zeros(n) for n in (R, 2 * B, 2 * B, R, 2 * B))
     P = ctypes.POINTER(ctypes.c_double)
     _check(lib.sgl_grid(plan, fn, *(a.ctypes.data_as(P) for a in (r, th, ph, wr, wt))), plan)
     return r, th, ph, wr, wt
@@ -183,16 +196,19 @@ class Plan:
     on the current torch stream) or in host memory (staged by the library).
     ``samples="real"`` makes a plan of real functions: real sample tensors
     (``sample_dtype``), complex coefficients, and the inverse returns the real
-    part (SGL_SAMPLES_REAL in sgl.h).
+    part (SGL_SAMPLES_REAL in sgl.h).  ``grid="hermite"`` samples on the
+    paper's own grid of 2B half-range Gauss-Hermite radii (FP64/FP32 plans):
+    samples of shape (batch, 2B, 2B, 2B).
     """
 
     def __init__(self, B: Optional[int] = None, batch: int = 1, precision: str = "fp64",
-                 samples: str = "weighted", _handle=None, _Bs=None):
+                 samples: str = "weighted", grid: str = "laguerre", _handle=None, _Bs=None):
         import torch  # noqa: F401  (device memory and streams)
         self.lib = load_library()
         self.prec = PRECISIONS[precision]
         self.precision = precision
         self.real = samples == "real"
+        self.grid_kind = grid
         if _handle is not None:
             self.handle = _handle
             self.Bs = list(_Bs)
@@ -201,7 +217,7 @@ class Plan:
         else:
             conv = {"weighted": SGL_SAMPLES_WEIGHTED, "physical": SGL_SAMPLES_PHYSICAL,
                     "real": SGL_SAMPLES_REAL}[samples]
-            self.handle = sgl_plan(B, batch, self.prec, conv)
+            self.handle = sgl_plan_grid(B, batch, self.prec, conv, GRIDS[grid])
             self.B = int(B)
             self.batch = int(batch)
             self.Bs = [self.B] * self.batch
@@ -229,10 +245,15 @@ class Plan:
         return self.dtype
 
     @property
+    def radii(self) -> int:
+        """Radial nodes per function: B, or 2B on the paper's grid."""
+        return 2 * self.B if self.grid_kind == "hermite" else self.B
+
+    @property
     def sample_shape(self):
         if self.B is None:
             return (self.n_samples,)
-        return (self.batch, self.B, 2 * self.B, 2 * self.B)
+        return (self.batch, self.radii, 2 * self.B, 2 * self.B)
 
     @property
     def coeff_shape(self):

@@ -57,6 +57,21 @@ def test_plan_argument_errors(lib, args, status):
     assert lib.sgl_last_error(None)
 
 
+@pytest.mark.parametrize("args,status", [
+    ((8, 1, 0, 0, 7), sgl.SGL_ERR_ARG),             # unknown radial grid
+    ((8, 1, 2, 0, 1), sgl.SGL_ERR_UNSUPPORTED),     # paper's grid: FP64 / FP32 plans only
+    ((8, 1, 3, 0, 1), sgl.SGL_ERR_UNSUPPORTED),
+    ((8, 1, 4, 0, 1), sgl.SGL_ERR_UNSUPPORTED),
+    ((8, 1, 1, 1, 1), sgl.SGL_ERR_ARG),             # physical samples still need FP64
+    ((0, 1, 0, 0, 1), sgl.SGL_ERR_ARG),
+])
+def test_plan_grid_argument_errors(lib, args, status):
+    h = ctypes.c_void_p(1234)
+    assert lib.sgl_plan_grid(ctypes.byref(h), *args) == status
+    assert h.value is None
+    assert lib.sgl_last_error(None)
+
+
 def test_plan_many_argument_errors(lib):
     h = ctypes.c_void_p()
     arr = (ctypes.c_int * 3)(8, 0, 16)
@@ -66,6 +81,7 @@ def test_plan_many_argument_errors(lib):
 
 
 def test_null_plan_queries(lib):
+    assert lib.sgl_radii(None, 0) == -1
     assert lib.sgl_sample_count(None) == -1
     assert lib.sgl_coeff_offset(None, 0) == -1
     assert lib.sgl_forward(None, None, None, None) == sgl.SGL_ERR_ARG
