@@ -326,6 +326,42 @@ def real_path(steps, warmup):
             "sample_bytes_per_function": 4 * B_BENCH ** 3 * 4}
 
 
+def paper_grid_path(steps, warmup):
+    """The paper's own grid (2B half-range Gauss-Hermite radii, FP64/FP32
+    plans): the paper's timing configuration (B=64, one function, round trip
+    in FP64, as in its Table 2) and B=128 x 16 functions in FP64 and FP32.
+    Round trip on seeded decaying coefficients, CUDA events."""
+    import torch
+    from paper_1604_05140_gb300 import Plan, inputs
+    out = {}
+    for label, B, nb, prec in (("b64x1_fp64", 64, 1, "fp64"), ("b128x16_fp64", 128, 16, "fp64"),
+                               ("b128x16_fp32", 128, 16, "fp32")):
+        plan = Plan(B, nb, prec, grid="hermite")
+        c = torch.from_numpy(inputs.random_coeffs(B, nb, seed=inputs.BASE_SEED + 6, decay=True)).to(plan.dtype).cuda()
+        s = torch.empty(plan.sample_shape, dtype=plan.dtype, device="cuda")
+        c2 = torch.empty_like(c)
+        for _ in range(max(1, warmup)):
+            plan.inverse(c, out=s)
+            plan.forward(s, out=c2)
+        torch.cuda.synchronize()
+        err = float((c2 - c).abs().max().item() / c.abs().max().item())
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(steps):
+            plan.inverse(c, out=s)
+            plan.forward(s, out=c2)
+        ev1.record()
+        torch.cuda.synchronize()
+        plan.check()
+        ms = ev0.elapsed_time(ev1) / steps
+        out[label] = {"B": B, "batch": nb, "precision": prec, "radii": 2 * B, "ms_per_step": ms,
+                      "value": nb / (ms * 1e-3), "unit": "transforms/s", "steps": steps,
+                      "round_trip_max_rel_err": err}
+        del plan, s, c, c2
+    return out
+
+
 def uneven_path(steps, warmup):
     """The batching workload: 256 functions with bandlimits uniform in
     {16, 24, ..., 128} in one TF32x3 plan, round trip captured in one CUDA
@@ -503,6 +539,7 @@ def run_ours(args):
     if not args.no_variants and args.precision == "tf32x3" and ws == 1:
         line["uneven_batch"] = uneven_path(max(3, min(args.steps, 20)), args.warmup)
         line["real_functions"] = real_path(max(3, min(args.steps, 20)), args.warmup)
+        line["paper_grid"] = paper_grid_path(3, 1)
     if "fp64" in results and args.precision != "fp64":
         r = results["fp64"]
         line["fp64_path"] = {"value": r["value"], "unit": "transforms/s", "ms_per_step": r["ms"],
