@@ -362,6 +362,60 @@ def paper_grid_path(steps, warmup):
     return out
 
 
+def midpoint_path(reps=3):
+    """Accuracy and cost of the Cartesian midpoint rule (sgl_midpoint, the
+    practice of the paper's Discussion) against the SGL transform, FP64, on 16
+    random complex polynomials of degree <= 3 (band-limited: the SGL sampling
+    theorem makes the transform exact, so its coefficients are the reference).
+    B = 16, cube [-6, 6]^3, M = 24 .. 64 cells per axis."""
+    import torch
+    from paper_1604_05140_gb300 import Plan, midpoint
+    B, nf, L = 16, 16, 6.0
+    rng = np.random.default_rng(1604051407)
+    mons = [(i, j, k) for i in range(4) for j in range(4) for k in range(4) if i + j + k <= 3]
+    cf = rng.standard_normal((nf, len(mons))) + 1j * rng.standard_normal((nf, len(mons)))
+
+    def sample(x, y, z):
+        return np.stack([sum(c * x ** i * y ** j * z ** k for c, (i, j, k) in zip(cf[q], mons)) for q in range(nf)])
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / reps
+
+    plan = Plan(B, nf, "fp64", samples="physical")
+    r, th, ph, _, _ = plan.grid()
+    R, TH, PH = np.meshgrid(r, th, ph, indexing="ij")
+    fs = torch.from_numpy(sample(R * np.sin(TH) * np.cos(PH), R * np.sin(TH) * np.sin(PH), R * np.cos(TH))).cuda()
+    ref, ms = timed(lambda: plan.forward(fs))
+    ref = ref.cpu().numpy()
+    res = {"B": B, "functions": nf, "cube_half_width": L, "reference": "the SGL transform (exact for these functions)",
+           "sgl": {"ms": ms, "samples_per_function": 4 * B ** 3}, "midpoint": {}}
+    for M in (24, 32, 48, 64):
+        x, y, z, _ = cartesian_midpoints(M, L)
+        fm = torch.from_numpy(sample(x, y, z)).cuda()
+        got, ms = timed(lambda: midpoint(fm, B, L))
+        err = float(np.abs(got.cpu().numpy() - ref).max() / np.abs(ref).max())
+        res["midpoint"][str(M)] = {"ms": ms, "samples_per_function": M ** 3, "max_rel_err": err}
+        del fm
+    return res
+
+
+def cartesian_midpoints(M, L):
+    """Cell midpoints of [-L, L]^3 (the grid sgl_midpoint samples on)."""
+    h = 2.0 * L / M
+    c = -L + (np.arange(M) + 0.5) * h
+    x, y, z = np.meshgrid(c, c, c, indexing="ij")
+    return x, y, z, h ** 3
+
+
 def uneven_path(steps, warmup):
     """The batching workload: 256 functions with bandlimits uniform in
     {16, 24, ..., 128} in one TF32x3 plan, round trip captured in one CUDA
@@ -540,6 +594,7 @@ def run_ours(args):
         line["uneven_batch"] = uneven_path(max(3, min(args.steps, 20)), args.warmup)
         line["real_functions"] = real_path(max(3, min(args.steps, 20)), args.warmup)
         line["paper_grid"] = paper_grid_path(3, 1)
+        line["midpoint_comparison"] = midpoint_path()
     if "fp64" in results and args.precision != "fp64":
         r = results["fp64"]
         line["fp64_path"] = {"value": r["value"], "unit": "transforms/s", "ms_per_step": r["ms"],

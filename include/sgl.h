@@ -328,6 +328,32 @@ void sgl_destroy(sgl_plan_t plan);
  */
 sgl_status sgl_forward_noalloc(int B, int batch, const void* samples, void* coeffs, sgl_stream_t stream);
 
+/*
+ * sgl_midpoint - SGL coefficients by the midpoint rule on a Cartesian grid,
+ * the current practice the paper's Discussion describes (built to compare
+ * accuracy and cost with the SGL transform; no sampling theorem makes it
+ * exact):
+ *   fhat_nlm ~= sum_k f(x_k) conj(H_nlm(x_k)) exp(-|x_k|^2) dV,
+ * the midpoint rule for the inner product of Eq. (inner_product); x_k are the
+ * midpoints of the M^3 cells of the cube [-L, L]^3 and dV = (2L/M)^3.
+ *   B       bandlimit, 1..32.
+ *   M, L    cells per axis (1..1024) and half-width of the cube (> 0).
+ *   batch   functions, 1..65535.
+ *   prec    SGL_FP64 (complex double) or SGL_FP32 (complex float).
+ *   f       device pointer: batch x M^3 complex PHYSICAL samples f(x_k),
+ *           index (ix * M + iy) * M + iz, x = -L + (ix + 1/2) 2L/M (same for
+ *           y, z).
+ *   coeffs  device pointer: batch x Omega complex in the coefficient layout;
+ *           overwritten (cleared, then accumulated with atomic adds, so the
+ *           summation order and the last bits vary from run to run).
+ *   stream  stream the memset and the kernel are queued on (asynchronous).
+ * Errors: SGL_ERR_ARG / SGL_ERR_UNSUPPORTED for arguments (host or misaligned
+ * pointers included), SGL_ERR_CUDA for launch errors; sgl_last_error(NULL)
+ * has the message.
+ */
+sgl_status sgl_midpoint(int B, int M, double L, int batch, int prec, const void* f, void* coeffs,
+                        sgl_stream_t stream);
+
 /* Library version string. */
 const char* sgl_version(void);
 

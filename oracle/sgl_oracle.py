@@ -69,7 +69,7 @@ __all__ = [
     "laguerre_explicit", "legendre_rodrigues", "basis_explicit",
     "forward", "inverse", "forward_direct", "inverse_direct", "sgl_matrix",
     "adjoint_forward", "adjoint_inverse", "sample_weights",
-    "physical_to_weighted", "weighted_to_physical",
+    "physical_to_weighted", "weighted_to_physical", "cartesian_midpoints", "midpoint",
 ]
 
 
@@ -487,6 +487,37 @@ def inverse_direct(coeffs: np.ndarray, B: int, rule: str = "laguerre") -> np.nda
     c = _as_batch_coeffs(coeffs, B)
     H = sgl_matrix(B, rule)
     return (c @ H).reshape(-1, n_radial(B, rule), 2 * B, 2 * B)
+
+
+# ---------------------------------------------------------------------------
+# the midpoint rule on a Cartesian grid (the practice of the Discussion)
+# ---------------------------------------------------------------------------
+
+def cartesian_midpoints(M: int, L: float):
+    """x, y, z (each (M, M, M), index [ix, iy, iz]) of the cell midpoints of
+    [-L, L]^3 with M cells per axis, and the cell volume."""
+    h = 2.0 * L / M
+    c = -L + (np.arange(M) + 0.5) * h
+    x, y, z = np.meshgrid(c, c, c, indexing="ij")
+    return x, y, z, h ** 3
+
+
+def midpoint(f: np.ndarray, B: int, M: int, L: float) -> np.ndarray:
+    """fhat_nlm ~= sum_k f(x_k) conj(H_nlm(x_k)) exp(-|x_k|^2) dV: the midpoint
+    rule for the inner product Eq. (inner_product) on the cells of [-L, L]^3,
+    H_nlm from the closed forms (small B only).  f: (batch, M, M, M) physical
+    samples."""
+    f = np.asarray(f, dtype=np.complex128).reshape(-1, M, M, M)
+    x, y, z, dV = cartesian_midpoints(M, L)
+    r = np.sqrt(x * x + y * y + z * z)
+    theta = np.arccos(np.where(r > 0, z / np.where(r > 0, r, 1.0), 1.0))
+    phi = np.arctan2(y, x)
+    w = np.exp(-r * r) * dV
+    out = np.zeros((f.shape[0], coeff_count(B)), dtype=np.complex128)
+    for (n, l, m) in nlm_list(B):
+        h = basis_explicit(n, l, m, r, theta, phi)
+        out[:, omega(n, l, m)] = np.einsum("bxyz,xyz->b", f, np.conj(h) * w)
+    return out
 
 
 def adjoint_forward(y: np.ndarray, B: int, rule: str = "laguerre") -> np.ndarray:

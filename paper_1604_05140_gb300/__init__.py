@@ -11,6 +11,7 @@ from .sgl import (  # noqa: F401
     sgl_destroy, sgl_check, sgl_autotune, sgl_tuning, sgl_selftest_wait, sgl_forward_autograd, sgl_inverse_autograd,
     SGL_FP64, SGL_FP32, SGL_TF32X3, SGL_TF32, SGL_BF16X3, SGL_SAMPLES_WEIGHTED, SGL_SAMPLES_PHYSICAL,
     SGL_SAMPLES_REAL, SGL_GRID_LAGUERRE, SGL_GRID_HALF_RANGE_HERMITE, sgl_plan_grid,
+    sgl_midpoint, midpoint,
 )
 
 __version__ = "0.1"

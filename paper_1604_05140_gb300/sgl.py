@@ -83,6 +83,7 @@ def load_library():
         "sgl_autotune": (i32, [vp, vp, vp, ctypes.c_char_p, vp]),
         "sgl_tuning": (ctypes.c_char_p, [vp]),
         "sgl_selftest_wait": (i32, [i64, ctypes.POINTER(ctypes.c_int)]),
+        "sgl_midpoint": (i32, [i32, i32, ctypes.c_double, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -176,6 +177,30 @@ def sgl_selftest_wait(limit_ns: int = 50_000_000) -> bool:
     flag = ctypes.c_int(0)
     _check(load_library().sgl_selftest_wait(int(limit_ns), ctypes.byref(flag)))
     return bool(flag.value)
+
+
+def sgl_midpoint(B: int, M: int, L: float, batch: int, prec: int, f_ptr: int, coeffs_ptr: int, stream: int = 0):
+    _check(load_library().sgl_midpoint(int(B), int(M), float(L), int(batch), int(prec), f_ptr, coeffs_ptr, stream))
+
+
+def midpoint(f, B: int, L: float, out=None):
+    """Midpoint-rule coefficients (sgl_midpoint) of physical samples f of
+    shape (batch, M, M, M) on the cell midpoints of [-L, L]^3: a CUDA
+    complex128 (FP64) or complex64 (FP32) tensor."""
+    import torch
+    if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dim() == 4 and f.is_contiguous()):
+        raise TypeError("f must be a contiguous CUDA tensor of shape (batch, M, M, M)")
+    if f.dtype not in (torch.complex128, torch.complex64):
+        raise TypeError("f must be complex128 or complex64")
+    batch, M = f.shape[0], f.shape[1]
+    if f.shape[2] != M or f.shape[3] != M:
+        raise ValueError("f must have M cells on every axis")
+    n = B * (B + 1) * (2 * B + 1) // 6
+    if out is None:
+        out = torch.empty((batch, n), dtype=f.dtype, device=f.device)
+    prec = SGL_FP64 if f.dtype == torch.complex128 else SGL_FP32
+    sgl_midpoint(B, M, L, batch, prec, f.data_ptr(), out.data_ptr(), torch.cuda.current_stream(f.device).cuda_stream)
+    return out
 
 
 def sgl_check(plan, stream: int = 0):

@@ -72,6 +72,18 @@ def test_plan_grid_argument_errors(lib, args, status):
     assert lib.sgl_last_error(None)
 
 
+def test_midpoint_argument_errors(lib):
+    # found before any device call: bandlimit, sizes, precision, null pointers
+    assert lib.sgl_midpoint(0, 8, 5.0, 1, 0, None, None, None) == sgl.SGL_ERR_UNSUPPORTED
+    assert lib.sgl_midpoint(33, 8, 5.0, 1, 0, None, None, None) == sgl.SGL_ERR_UNSUPPORTED
+    assert lib.sgl_midpoint(4, 0, 5.0, 1, 0, None, None, None) == sgl.SGL_ERR_ARG
+    assert lib.sgl_midpoint(4, 8, 0.0, 1, 0, None, None, None) == sgl.SGL_ERR_ARG
+    assert lib.sgl_midpoint(4, 8, 5.0, 0, 0, None, None, None) == sgl.SGL_ERR_ARG
+    assert lib.sgl_midpoint(4, 8, 5.0, 1, 2, None, None, None) == sgl.SGL_ERR_ARG
+    assert lib.sgl_midpoint(4, 8, 5.0, 1, 0, None, None, None) == sgl.SGL_ERR_ARG
+    assert lib.sgl_last_error(None)
+
+
 def test_plan_many_argument_errors(lib):
     h = ctypes.c_void_p()
     arr = (ctypes.c_int * 3)(8, 0, 16)

@@ -114,6 +114,26 @@ def test_sampling_theorem_round_trip_paper_grid(B):
     assert err.mean() < 10 * (am + 3 * asd), (err, am)
 
 
+@pytest.mark.parametrize("name", ["one", "x", "y", "z", "r2"])
+def test_midpoint_rule_converges_to_closed_forms(name):
+    # the midpoint rule of the Discussion, applied to the inner product Eq.
+    # (inner_product) on [-6, 6]^3: for these Gaussian-weighted polynomials it
+    # converges (fast) to the closed-form coefficients; a wrong weight, volume
+    # element or conjugation would not
+    B = 3
+    table = [r for r in _closed_forms() if r[0] == name]
+    errs = []
+    for M in (12, 40):
+        x, y, z, _ = O.cartesian_midpoints(M, 6.0)
+        f = {"one": np.ones_like(x), "x": x, "y": y, "z": z, "r2": x * x + y * y + z * z}[name]
+        c = O.midpoint(f[None] + 0j, B, M, 6.0)[0]
+        expect = np.zeros_like(c)
+        for (_, n, l, m, v) in table:
+            expect[O.omega(n, l, m)] = v
+        errs.append(np.abs(c - expect).max())
+    assert errs[1] < 1e-11 and errs[0] > 1e3 * errs[1], errs
+
+
 def test_single_node_rule():
     t, logw = O.laguerre_rule(1)
     assert abs(t[0] - 1.5) < 1e-15
