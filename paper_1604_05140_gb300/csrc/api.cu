@@ -69,10 +69,12 @@ static void release(Plan* P) {
   tc_release(*P);
   if (!P->owns_err) P->d_err = nullptr;
   void* ptrs[] = {P->d_tab, P->d_tab_lo, P->d_w1, P->d_w2, P->d_stage_in, P->d_stage_out, P->d_segs,
-                  P->d_fn_samp, P->d_fn_coef, P->d_si_rows, P->d_err, P->leg_fwd.d_tiles, P->rad_fwd.d_tiles,
-                  P->rad_inv.d_tiles, P->leg_inv.d_tiles, P->d_fft_fwd, P->d_fft_inv, P->d_ccoef};
+                  P->d_fn_samp, P->d_fn_coef, P->d_si_rows, P->d_err, P->d_fft_fwd, P->d_fft_inv, P->d_ccoef};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (GemmSched* g : {&P->leg_fwd, &P->rad_fwd, &P->rad_inv, &P->leg_inv})
+    for (int w = 0; w < kGemmShapes; ++w)
+      if (g->d_tiles[w]) cudaFree(g->d_tiles[w]);
   cudaSetDevice(cur);
   delete P;
 }
@@ -152,10 +154,19 @@ void sgl::pack_tables(const Plan& P, std::vector<real>& tab) {
 template void sgl::pack_tables<double>(const Plan& P, std::vector<double>& tab);
 template void sgl::pack_tables<float>(const Plan& P, std::vector<float>& tab);
 
-// Kernel launches of one forward (or inverse) call: the phi-FFT launches (the
-// larger of the two directions) and two stage launches.
+// Kernel launches of one forward (or inverse) call, the larger of the two
+// directions: the phi-FFT launches and the stage launches (one per
+// tensor-core stage, one per tile shape of a SIMT stage).
 static void set_launch_count(Plan& P) {
-  P.launches_per_call = std::max(fft_launches(P, false), fft_launches(P, true)) + 2 + (P.real_pairs ? 1 : 0);
+  int fwd = fft_launches(P, false), inv = fft_launches(P, true);
+  if (tc_precision(P.prec)) {
+    fwd += 2;
+    inv += 2;
+  } else {
+    fwd += P.leg_fwd.launches() + P.rad_fwd.launches();
+    inv += P.rad_inv.launches() + P.leg_inv.launches();
+  }
+  P.launches_per_call = std::max(fwd, inv) + (P.real_pairs ? 1 : 0);
 }
 
 // FFT CTA lists of both directions (segment order) for the plan's current
@@ -298,39 +309,35 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
   // SIMT GEMM schedules
   int TM, TN, TK;
   gemm_tile_dims(TM, TN, TK);
-  std::vector<int4> lf, rf, ri, li;
+  // tiles of every stage (0 LEG_F, 1 RAD_F, 2 RAD_I, 3 LEG_I) in the narrowest
+  // shape that holds the group's columns
+  std::vector<int4> lists[4][kGemmShapes];
+  auto add = [&](int stage, int s, int g, int rows, int ncols) {
+    const int w = gemm_shape_of(ncols), tm = gemm_shape_rows(w), tn = gemm_shape_cols(w);
+    for (int r0 = 0; r0 < rows; r0 += tm)
+      for (int c0 = 0; c0 < ncols; c0 += tn) lists[stage][w].push_back(make_int4(s, g, r0, c0));
+  };
   for (size_t s = 0; s < P->segs.size(); ++s) {
     const SegDesc& sg = P->segs[s];
     const int B = sg.B, NB = sg.NB, R = sg.R;
     for (int g = 0; g < 2 * (2 * B - 1); ++g) {
       const int m = (g >> 1) - (B - 1);
-      const int N = n_par(B, m < 0 ? -m : m, g & 1);
-      const int rows = NB * 2 * R;
-      for (int r0 = 0; r0 < rows; r0 += TM)
-        for (int c0 = 0; c0 < N; c0 += TN) lf.push_back(make_int4((int)s, g, r0, c0));
+      add(0, (int)s, g, NB * 2 * R, n_par(B, m < 0 ? -m : m, g & 1));
     }
     for (int l = 0; l < B; ++l) {
       const int rows = NB * (2 * l + 1) * 2;
-      for (int r0 = 0; r0 < rows; r0 += TM) {
-        for (int c0 = 0; c0 < B - l; c0 += TN) rf.push_back(make_int4((int)s, l, r0, c0));
-        for (int c0 = 0; c0 < R; c0 += TN) ri.push_back(make_int4((int)s, l, r0, c0));
-      }
+      add(1, (int)s, l, rows, B - l);
+      add(2, (int)s, l, rows, R);
     }
-    for (int mi = 0; mi < 2 * B - 1; ++mi) {
-      const int rows = NB * 2 * R;
-      for (int r0 = 0; r0 < rows; r0 += TM)
-        for (int c0 = 0; c0 < B; c0 += TN) li.push_back(make_int4((int)s, mi, r0, c0));
+    for (int mi = 0; mi < 2 * B - 1; ++mi) add(3, (int)s, mi, NB * 2 * R, B);
+  }
+  GemmSched* scheds[4] = {&P->leg_fwd, &P->rad_fwd, &P->rad_inv, &P->leg_inv};
+  for (int st = 0; st < 4; ++st)
+    for (int w = 0; w < kGemmShapes; ++w) {
+      scheds[st]->ntiles[w] = (int)lists[st][w].size();
+      e = dev_upload(*P, &scheds[st]->d_tiles[w], lists[st][w]);
+      if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
     }
-  }
-  struct {
-    GemmSched* s;
-    std::vector<int4>* v;
-  } scheds[] = {{&P->leg_fwd, &lf}, {&P->rad_fwd, &rf}, {&P->rad_inv, &ri}, {&P->leg_inv, &li}};
-  for (auto& x : scheds) {
-    x.s->ntiles = (int)x.v->size();
-    e = dev_upload(*P, &x.s->d_tiles, *x.v);
-    if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
-  }
   e = build_fft_lists(*P);
   if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
   for (const SegDesc& sg : P->segs) {

@@ -490,16 +490,22 @@ __device__ __forceinline__ void store_y(const GemmArgs& a, const SegDesc& sg, co
   }
 }
 
-template <int PROB, typename real>
+// Tiles of TMv x TNv outputs (TMv * TNv = 4096: 64 x 64, 128 x 32 or 256 x 16),
+// each of the 256 threads 4 x 4 of them; a stage's groups with few columns
+// (N <= 32 or <= 16) use the narrow shapes, so that padding columns do not
+// cost multiply-adds.
+template <int PROB, typename real, int TMv, int TNv>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
-  __shared__ real Xs[TK][TM + 1];
-  __shared__ real As[TK][TN + 1];
+  static_assert(TMv * TNv == 16 * 256, "256 threads of 4 x 4 outputs");
+  constexpr int CX = TNv / 4, RX = TMv / 4;  // threads along columns and rows
+  __shared__ real Xs[TK][TMv + 1];
+  __shared__ real As[TK][TNv + 1];
   const int4 t = a.tiles[blockIdx.x];
   const SegDesc sg = a.segs[t.x];
   GroupCtx c;
   group_setup<PROB>(a, sg, t.y, c);
   const int row0 = t.z, col0 = t.w;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x % CX, ty = threadIdx.x / CX;
   real acc[4][4], acc2[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -507,15 +513,15 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
     for (int q = 0; q < 4; ++q) acc[r][q] = acc2[r][q] = 0;
   for (int k0 = 0; k0 < c.K; k0 += TK) {
     // X tile: TM rows x TK (k fastest across threads for coalesced row reads)
-    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+    for (int e = threadIdx.x; e < TMv * TK; e += 256) {
       const int rr = e / TK, kk = e % TK;
       Xs[kk][rr] = load_x<PROB, real>(a, sg, c, row0 + rr, k0 + kk);
     }
-    for (int e = threadIdx.x; e < TN * TK; e += 256) {
+    for (int e = threadIdx.x; e < TNv * TK; e += 256) {
       int cc, kk;
       if (PROB == RAD_I || PROB == LEG_I) {  // tables stored [k][col]: col fastest
-        kk = e / TN;
-        cc = e % TN;
+        kk = e / TNv;
+        cc = e % TNv;
       } else {
         cc = e / TK;
         kk = e % TK;
@@ -528,9 +534,9 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
     for (int kk = 0; kk < TK; ++kk) {
       real xv[4], av[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) xv[r] = Xs[kk][ty + 16 * r];
+      for (int r = 0; r < 4; ++r) xv[r] = Xs[kk][ty + RX * r];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) av[q] = As[kk][tx + 16 * q];
+      for (int q = 0; q < 4; ++q) av[q] = As[kk][tx + CX * q];
       if (second) {
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -549,7 +555,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      store_y<PROB, real>(a, sg, c, row0 + ty + 16 * r, col0 + tx + 16 * q, acc[r][q], acc2[r][q]);
+      store_y<PROB, real>(a, sg, c, row0 + ty + RX * r, col0 + tx + CX * q, acc[r][q], acc2[r][q]);
 }
 
 // ---------------------------------------------------------------------------
@@ -585,15 +591,23 @@ static cudaError_t launch_fft_t(const Plan& P, const FftArgs& a, int n1, int n2,
   return cudaGetLastError();
 }
 
-template <typename real>
-static cudaError_t launch_gemm_t(int prob, const GemmArgs& a, int ntiles, cudaStream_t s) {
-  if (ntiles == 0) return cudaSuccess;
+template <typename real, int TMv, int TNv>
+static void launch_gemm_shape(int prob, const GemmArgs& a, int ntiles, cudaStream_t s) {
   switch (prob) {
-    case LEG_F: gemm_simt_kernel<LEG_F, real><<<ntiles, 256, 0, s>>>(a); break;
-    case RAD_F: gemm_simt_kernel<RAD_F, real><<<ntiles, 256, 0, s>>>(a); break;
-    case RAD_I: gemm_simt_kernel<RAD_I, real><<<ntiles, 256, 0, s>>>(a); break;
-    default: gemm_simt_kernel<LEG_I, real><<<ntiles, 256, 0, s>>>(a); break;
+    case LEG_F: gemm_simt_kernel<LEG_F, real, TMv, TNv><<<ntiles, 256, 0, s>>>(a); break;
+    case RAD_F: gemm_simt_kernel<RAD_F, real, TMv, TNv><<<ntiles, 256, 0, s>>>(a); break;
+    case RAD_I: gemm_simt_kernel<RAD_I, real, TMv, TNv><<<ntiles, 256, 0, s>>>(a); break;
+    default: gemm_simt_kernel<LEG_I, real, TMv, TNv><<<ntiles, 256, 0, s>>>(a); break;
   }
+}
+
+// shape w of GemmSched: 0 -> 64 x 64, 1 -> 128 x 32, 2 -> 256 x 16
+template <typename real>
+static cudaError_t launch_gemm_t(int prob, const GemmArgs& a, int w, int ntiles, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  if (w == 0) launch_gemm_shape<real, 64, 64>(prob, a, ntiles, s);
+  else if (w == 1) launch_gemm_shape<real, 128, 32>(prob, a, ntiles, s);
+  else launch_gemm_shape<real, 256, 16>(prob, a, ntiles, s);
   return cudaGetLastError();
 }
 
@@ -681,14 +695,17 @@ static cudaError_t run_gemm(Plan& P, int prob, const GemmSched& sch, const void*
   a.segs = P.d_segs;
   a.fn_coef = P.d_fn_coef;
   a.si_rows = P.d_si_rows;
-  a.tiles = sch.d_tiles;
   a.tab = P.d_tab;
   a.x = x;
   a.y = y;
   a.weighted = weighted;
   static const int stage_of[4] = {ST_LEG_F, ST_RAD_F, ST_RAD_I, ST_LEG_I};
   StageTimer timer(P, stage_of[prob], s);
-  cudaError_t e = launch_gemm_t<real>(prob, a, sch.ntiles, s);
+  cudaError_t e = cudaSuccess;
+  for (int w = 0; w < kGemmShapes && e == cudaSuccess; ++w) {
+    a.tiles = sch.d_tiles[w];
+    e = launch_gemm_t<real>(prob, a, w, sch.ntiles[w], s);
+  }
   timer.finish();
   return e;
 }

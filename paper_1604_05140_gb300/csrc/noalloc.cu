@@ -152,10 +152,10 @@ sgl_status describe(DeviceState& D, int B, int batch) {
   P.d_fn_samp = (int64_t*)(c + o_samp);
   P.d_fn_coef = (int64_t*)(c + o_coef);
   P.d_si_rows = (int64_t*)(c + o_si);
-  P.leg_fwd.d_tiles = (int4*)(c + o_lf);
-  P.leg_fwd.ntiles = (int)lf.size();
-  P.rad_fwd.d_tiles = (int4*)(c + o_rf);
-  P.rad_fwd.ntiles = (int)rf.size();
+  P.leg_fwd.d_tiles[0] = (int4*)(c + o_lf);  // 64 x 64 tiles only
+  P.leg_fwd.ntiles[0] = (int)lf.size();
+  P.rad_fwd.d_tiles[0] = (int4*)(c + o_rf);
+  P.rad_fwd.ntiles[0] = (int)rf.size();
   P.d_fft_fwd = (int4*)(c + o_ff);
   P.n_fft_fwd = (int)ff.size();
   P.d_w1 = D.scratch;

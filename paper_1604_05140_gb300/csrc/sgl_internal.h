@@ -148,9 +148,17 @@ struct SegDesc {
 // Tile of a GEMM stage: (segment, group, row0, col0)
 // FFT CTA:            (segment, shell = b*R + i, j'0, 0)
 
+// Tile lists of one SIMT GEMM stage, one per tile shape: 64 x 64, 128 x 32
+// and 256 x 16 outputs (rows x columns); a group's tiles take the narrowest
+// shape that holds its column count (kernels.cu).
+constexpr int kGemmShapes = 3;
+inline int gemm_shape_of(int ncols) { return ncols <= 16 ? 2 : ncols <= 32 ? 1 : 0; }
+inline int gemm_shape_cols(int w) { return 64 >> w; }
+inline int gemm_shape_rows(int w) { return 64 << w; }
 struct GemmSched {
-  int4* d_tiles = nullptr;
-  int ntiles = 0;
+  int4* d_tiles[kGemmShapes] = {nullptr, nullptr, nullptr};
+  int ntiles[kGemmShapes] = {0, 0, 0};
+  int launches() const { return (ntiles[0] > 0) + (ntiles[1] > 0) + (ntiles[2] > 0); }
 };
 
 struct Plan {
