@@ -59,6 +59,37 @@ __global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
   real* rad = lam + kPts * nlm;                       // [kPts][l][n-1 >= l]: index l*B - l(l-1)/2 + (n-1-l)
   real* eph = rad + kPts * nlm;                       // [kPts][m < B][2]: e^{-i m phi}
   real* fw = eph + kPts * 2 * B;                      // [kPts][2]: f(x_k) exp(-|x_k|^2 / 2) dV
+  // recurrence coefficients, once per block (no square roots or divisions in
+  // the per-point loops): Legendre a, c at [m][l]; radial 1/s, (2n-l-1/2)/s
+  // and c at [l][n-1]; sectoral and radial seed factors per m and per l
+  real* la = fw + 2 * kPts;
+  real* lc = la + nlm;
+  real* rs = lc + nlm;
+  real* r0 = rs + nlm;
+  real* rc = r0 + nlm;
+  real* sf = rc + nlm;    // [m]: -sqrt((2m+1)/(2m)), m >= 1
+  real* rf = sf + B;      // [l]: 1/sqrt(l + 1/2), l >= 1
+  for (int w = threadIdx.x; w < nlm; w += blockDim.x) {
+    int m = 0;
+    while ((m + 1) * B - (m + 1) * m / 2 <= w) ++m;  // row m of the [m][l >= m] triangle
+    const int l = m + (w - (m * B - m * (m - 1) / 2));
+    la[w] = l > m ? sqrt((4 * (real)l * l - 1) / ((real)(l - m) * (l + m))) : 0;
+    lc[w] = l > m + 1 ? sqrt(((l - 1) * (real)(l - 1) - (real)m * m) / (4 * (real)(l - 1) * (l - 1) - 1)) : 0;
+    // the same triangle read as [l][n-1 >= l]: row l = m, n - 1 = l_index
+    const int ll = m, n = l;  // degree n + 1 of T, recurrence from n
+    if (n > ll) {
+      const real inv = 1 / sqrt((n + (real)0.5) * (n - ll));
+      rs[w] = inv;
+      r0[w] = (2 * (real)n - ll - (real)0.5) * inv;
+      rc[w] = sqrt((n - (real)0.5) / (n + (real)0.5) * (real)(n - ll - 1) / (real)(n - ll));
+    } else {
+      rs[w] = r0[w] = rc[w] = 0;
+    }
+  }
+  for (int w = threadIdx.x; w < B; w += blockDim.x) {
+    sf[w] = w > 0 ? -sqrt((2 * w + 1) / (real)(2 * w)) : 0;
+    rf[w] = w > 0 ? 1 / sqrt(w + (real)0.5) : 0;
+  }
   const int b = blockIdx.y;
   const int64_t M3 = (int64_t)a.M * a.M * a.M;
   const int64_t p0 = (int64_t)blockIdx.x * a.pts_per_block;
@@ -104,22 +135,20 @@ __global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
       const int ix = (int)(p / ((int64_t)a.M * a.M)), iy = (int)((p / a.M) % a.M), iz = (int)(p % a.M);
       const real x = (real)(-a.L + (ix + 0.5) * h), y = (real)(-a.L + (iy + 0.5) * h), z = (real)(-a.L + (iz + 0.5) * h);
       const real rho2 = x * x + y * y, t = rho2 + z * z, r = sqrt(t);
-      const real ct = r > 0 ? z / r : (real)1, st = r > 0 ? sqrt(rho2) / r : (real)0;
-      const real phi = atan2(y, x);
-      real s, c;
-      if (sizeof(real) == 8) {
-        double sd, cd;
-        sincos((double)m * (double)phi, &sd, &cd);
-        s = (real)sd;
-        c = (real)cd;
-      } else {
-        float sf, cf;
-        sincosf((float)m * (float)phi, &sf, &cf);
-        s = (real)sf;
-        c = (real)cf;
+      const real rho = sqrt(rho2);
+      const real ct = r > 0 ? z / r : (real)1, st = r > 0 ? rho / r : (real)0;
+      // e^{-i m phi} as the m-th power of (x - i y) / rho (phi = 0 on the z axis)
+      {
+        const real c1 = rho > 0 ? x / rho : (real)1, s1 = rho > 0 ? -y / rho : (real)0;
+        real c = 1, sn = 0;
+        for (int mm = 0; mm < m; ++mm) {
+          const real cn = c * c1 - sn * s1;
+          sn = c * s1 + sn * c1;
+          c = cn;
+        }
+        eph[(k * B + m) * 2] = c;
+        eph[(k * B + m) * 2 + 1] = sn;
       }
-      eph[(k * B + m) * 2] = c;
-      eph[(k * B + m) * 2 + 1] = -s;
       if (m == 0) {
         // weight exp(-|x|^2) dV, of which T_nl carries exp(-|x|^2 / 2)
         const int64_t fo = ((int64_t)b * M3 + p) * 2;
@@ -127,16 +156,15 @@ __global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
         fw[k * 2] = a.f[fo] * g;
         fw[k * 2 + 1] = a.f[fo + 1] * g;
       }
+      const int tri = m * B - m * (m - 1) / 2;  // row m (or l = m) of a triangle
       // Lambda_lm(theta), l = m .. B-1: sectoral seed, then the recurrence in l
       real sect = (real)(1.0 / sqrt(4.0 * 3.14159265358979323846));
-      for (int mm = 1; mm <= m; ++mm) sect *= -sqrt((2 * mm + 1) / (real)(2 * mm)) * st;
-      real* lm = lam + k * nlm + (m * B - m * (m - 1) / 2);
+      for (int mm = 1; mm <= m; ++mm) sect *= sf[mm] * st;
+      real* lm = lam + k * nlm + tri;
       real pm2 = 0, pm1 = sect;
       lm[0] = sect;
       for (int l = m + 1; l < B; ++l) {
-        const real ca = sqrt((4 * (real)l * l - 1) / ((real)(l - m) * (l + m)));
-        const real cc = sqrt(((l - 1) * (real)(l - 1) - (real)m * m) / (4 * (real)(l - 1) * (l - 1) - 1));
-        const real v = ca * (ct * pm1 - cc * pm2);
+        const real v = la[tri + l - m] * (ct * pm1 - lc[tri + l - m] * pm2);
         pm2 = pm1;
         pm1 = v;
         lm[l - m] = v;
@@ -145,14 +173,13 @@ __global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
       {
         const int l = m;
         real seed = sqrt((real)2 / (sqrt(kPi) / 2)) * exp(-t / 2);
-        for (int ll = 1; ll <= l; ++ll) seed *= r / sqrt(ll + (real)0.5);
-        real* rl = rad + k * nlm + (l * B - l * (l - 1) / 2);
+        for (int ll = 1; ll <= l; ++ll) seed *= r * rf[ll];
+        real* rl = rad + k * nlm + tri;
         real prev = 0, cur = seed;
         rl[0] = cur;
         for (int n = l + 1; n < B; ++n) {
-          const real ca = (2 * (real)n - l - (real)0.5 - t) / sqrt((n + (real)0.5) * (n - l));
-          const real cc = sqrt((n - (real)0.5) / (n + (real)0.5) * (real)(n - l - 1) / (real)(n - l));
-          const real nxt = ca * cur - cc * prev;
+          const int w = tri + n - l;
+          const real nxt = (r0[w] - t * rs[w]) * cur - rc[w] * prev;
           prev = cur;
           cur = nxt;
           rl[n - l] = cur;
@@ -208,7 +235,7 @@ cudaError_t launch_midpoint(int B, int M, double L, int batch, const void* f, vo
   if (a.pts_per_block < kPts) a.pts_per_block = kPts;
   const int64_t nbx = (M3 + a.pts_per_block - 1) / a.pts_per_block;
   const size_t nlm = (size_t)B * (B + 1) / 2;
-  const size_t smem = sizeof(real) * (2 * kPts * nlm + (size_t)kPts * 2 * B + 2 * kPts);
+  const size_t smem = sizeof(real) * (2 * kPts * nlm + (size_t)kPts * 2 * B + 2 * kPts + 5 * nlm + 2 * (size_t)B);
   cudaError_t e = cudaMemsetAsync(coeffs, 0, (size_t)batch * a.omega * 2 * sizeof(real), s);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(midpoint_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
