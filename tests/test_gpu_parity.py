@@ -311,3 +311,25 @@ def test_tf32x3_full_size_b128_sampled_functions():
         assert _err(sk[None], O.inverse(c[k], B)) < TF32X3_TOL
         assert _err(f[k][None], O.forward(sk, B)) < TF32X3_TOL
     p.check()
+
+
+def test_tf32x3_b128_batch256_offsets_beyond_2_31():
+    # B=128, 256 functions: the phi-FFT spectra alone hold 4.3e9 floats
+    # (beyond 2^31), so every offset of the path must be 64-bit.  Round trip
+    # of all 256 functions; the first and the last also against a plan of one
+    # function on the same coefficients (same arithmetic per function).
+    B, NB = 128, 256
+    p = _plan(B, NB, "tf32x3")
+    c = inputs.random_coeffs(B, NB, seed=inputs.BASE_SEED + 11, decay=True).astype(np.complex64)
+    cd = torch.from_numpy(c).cuda()
+    s = p.inverse(cd)
+    f = p.forward(s)
+    p.check()
+    assert _err(f.cpu().numpy(), c) < TF32X3_TOL
+    one = _plan(B, 1, "tf32x3")
+    for k in (0, NB - 1):
+        s1 = one.inverse(cd[k:k + 1])
+        assert _err(s[k:k + 1].cpu().numpy(), s1.cpu().numpy()) < 1e-6, k
+    del s, f, cd
+    torch.cuda.empty_cache()
+
