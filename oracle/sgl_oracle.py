@@ -70,6 +70,7 @@ __all__ = [
     "forward", "inverse", "forward_direct", "inverse_direct", "sgl_matrix",
     "adjoint_forward", "adjoint_inverse", "sample_weights",
     "physical_to_weighted", "weighted_to_physical", "cartesian_midpoints", "midpoint",
+    "dct_matrix", "legendre_cosine_coeffs", "forward_seminaive",
 ]
 
 
@@ -487,6 +488,61 @@ def inverse_direct(coeffs: np.ndarray, B: int, rule: str = "laguerre") -> np.nda
     c = _as_batch_coeffs(coeffs, B)
     H = sgl_matrix(B, rule)
     return (c @ H).reshape(-1, n_radial(B, rule), 2 * B, 2 * B)
+
+
+# ---------------------------------------------------------------------------
+# the seminaive Legendre transform (Eq. DCT, Eq. dct_trick)
+# ---------------------------------------------------------------------------
+
+def dct_matrix(N: int) -> np.ndarray:
+    """C_N of Eq. (DCT): row k = sqrt(1/N) or sqrt(2/N) times cos(k theta_j),
+    theta_j = (2j+1) pi / 2N."""
+    j = np.arange(N)
+    C = np.cos(np.outer(np.arange(N), (2 * j + 1) * pi / (2 * N)))
+    C[0] *= sqrt(1.0 / N)
+    C[1:] *= sqrt(2.0 / N)
+    return C
+
+
+def legendre_cosine_coeffs(B: int) -> np.ndarray:
+    """Q[m, l, k] = [C_2B q_lm]_k, q_lm = Lambda_lm(theta_j) / w_m(theta_j) on the
+    2B rings, w_m = 1 for even m and sin(theta) for odd m: q_lm is then a
+    cosine polynomial of degree l (even m) or l - 1 (odd m) in theta, so by
+    the property stated after Eq. (DCT) its entries vanish beyond that degree
+    (reading for odd m: the factor sin(theta) goes with the data)."""
+    theta, _, _ = sphere_rule(B)
+    lam = legendre_table(B)                         # [m, l, j]
+    w = np.where(np.arange(B)[:, None] % 2 == 1, np.sin(theta)[None, :], 1.0)  # [m, j]
+    C = dct_matrix(2 * B)
+    return np.einsum("kj,mlj->mlk", C, lam / w[:, None, :])
+
+
+def forward_seminaive(samples: np.ndarray, B: int, weights: bool = True, rule: str = "laguerre") -> np.ndarray:
+    """The forward transform with the Legendre sums of Eq. (DLT) taken by the
+    seminaive algorithm: per order m, the DCT C_2B of the data t_j = beta_j
+    w_m(theta_j) G_j over all 2B rings (a library DCT as the step), then for
+    every l the inner product of Eq. (dct_trick) over the first deg + 1 DCT
+    coefficients only.  The phi-FFT and the radial sum as in forward()."""
+    f = _as_batch_samples(samples, B, rule)
+    nb, R = f.shape[0], f.shape[1]
+    _, _, what = radial_weights(B, rule)
+    theta, _, beta = sphere_rule(B)
+    if not weights:
+        what = np.ones_like(what)
+        beta = np.ones_like(beta)
+    Q = legendre_cosine_coeffs(B)
+    C = dct_matrix(2 * B)
+    G = np.fft.fft(f, axis=-1)                            # G[b,i,j,(m mod 2B)]
+    S = np.zeros((nb, R, B, 2 * B - 1), dtype=np.complex128)
+    for m in range(-(B - 1), B):
+        am = abs(m)
+        sign = (-1.0) ** am if m < 0 else 1.0
+        w = np.sin(theta) if am % 2 else np.ones_like(theta)
+        T = np.einsum("kj,bij->bik", C, G[:, :, :, m % (2 * B)] * (beta * w)[None, None, :])
+        for l in range(am, B):
+            deg = l if am % 2 == 0 else l - 1
+            S[:, :, l, m + B - 1] = sign * T[:, :, :deg + 1] @ Q[am, l, :deg + 1]
+    return _sphere_coeffs_to_sgl(S, B, what, rule)
 
 
 # ---------------------------------------------------------------------------

@@ -134,6 +134,34 @@ def test_midpoint_rule_converges_to_closed_forms(name):
     assert errs[1] < 1e-11 and errs[0] > 1e3 * errs[1], errs
 
 
+@pytest.mark.parametrize("B", [3, 6, 16])
+def test_dct_truncation_property(B):
+    # Eq. (DCT): C_2B is orthogonal, and the DCT of a cosine polynomial of
+    # degree d on the 2B rings vanishes beyond index d.  Lambda_lm / w_m is one
+    # of degree l (even m) or l - 1 (odd m, w_m = sin theta): this pins the
+    # Legendre table's theta dependence and the odd-m reading of the
+    # seminaive algorithm.
+    C = O.dct_matrix(2 * B)
+    np.testing.assert_allclose(C @ C.T, np.eye(2 * B), atol=1e-14)
+    Q = O.legendre_cosine_coeffs(B)
+    for m in range(B):
+        for l in range(m, B):
+            deg = l if m % 2 == 0 else l - 1
+            assert np.abs(Q[m, l, deg + 1:]).max(initial=0.0) < 1e-13 * np.abs(Q[m, l]).max(), (m, l)
+            assert abs(Q[m, l, deg]) > 1e-3 * np.abs(Q[m, l]).max(), (m, l)  # the degree is reached
+
+
+@pytest.mark.parametrize("B", [2, 5, 12])
+def test_seminaive_equals_direct(B):
+    # the seminaive Legendre sums (Eq. dct_trick) give the forward transform of
+    # the direct sums (Eq. DLT), with and without the quadrature weights
+    g = inputs.random_samples(B, 2, seed=400 + B)
+    for w in (True, False):
+        a = O.forward(g, B, weights=w)
+        b = O.forward_seminaive(g, B, weights=w)
+        assert np.abs(a - b).max() < 1e-13 * np.abs(a).max(), w
+
+
 def test_single_node_rule():
     t, logw = O.laguerre_rule(1)
     assert abs(t[0] - 1.5) < 1e-15
