@@ -416,6 +416,43 @@ def cartesian_midpoints(M, L):
     return x, y, z, h ** 3
 
 
+def seminaive_path(steps=3, warmup=1):
+    """The forward transform with direct and with seminaive Legendre sums
+    (sgl_set_dlt), FP64, B = 128 x 64: forward time and Legendre stage time
+    (per-stage CUDA events)."""
+    import ctypes
+    import torch
+    from paper_1604_05140_gb300 import Plan, inputs, sgl
+    lib = sgl.load_library()
+    plan = Plan(B_BENCH, BATCH, "fp64")
+    c = torch.from_numpy(inputs.random_coeffs(B_BENCH, BATCH, seed=inputs.BASE_SEED + 3, decay=True)).cuda()
+    s = plan.inverse(c)
+    out = {"B": B_BENCH, "batch": BATCH, "precision": "fp64"}
+    for label, on in (("direct", False), ("seminaive", True)):
+        plan.set_dlt(on)
+        f = torch.empty_like(c)
+        for _ in range(max(1, warmup)):
+            plan.forward(s, out=f)
+        torch.cuda.synchronize()
+        err = float((f - c).abs().max().item() / c.abs().max().item())
+        lib.sgl_set_profiling(plan.handle, 1)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(steps):
+            plan.forward(s, out=f)
+        ev1.record()
+        torch.cuda.synchronize()
+        tms = (ctypes.c_double * 6)()
+        tl = (ctypes.c_int64 * 6)()
+        lib.sgl_stage_times(plan.handle, tms, tl)
+        lib.sgl_set_profiling(plan.handle, 0)
+        out[label] = {"forward_ms": ev0.elapsed_time(ev1) / steps, "legendre_forward_ms": tms[1] / max(tl[1], 1),
+                      "max_rel_err": err}
+    plan.check()
+    return out
+
+
 def uneven_path(steps, warmup):
     """The batching workload: 256 functions with bandlimits uniform in
     {16, 24, ..., 128} in one TF32x3 plan, round trip captured in one CUDA
@@ -595,6 +632,7 @@ def run_ours(args):
         line["real_functions"] = real_path(max(3, min(args.steps, 20)), args.warmup)
         line["paper_grid"] = paper_grid_path(3, 1)
         line["midpoint_comparison"] = midpoint_path()
+        line["seminaive_dlt"] = seminaive_path()
     if "fp64" in results and args.precision != "fp64":
         r = results["fp64"]
         line["fp64_path"] = {"value": r["value"], "unit": "transforms/s", "ms_per_step": r["ms"],

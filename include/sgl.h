@@ -329,6 +329,21 @@ void sgl_destroy(sgl_plan_t plan);
 sgl_status sgl_forward_noalloc(int B, int batch, const void* samples, void* coeffs, sgl_stream_t stream);
 
 /*
+ * sgl_set_dlt - choose how the forward Legendre sums (Eq. DLT) of an
+ * SGL_FP64 or SGL_FP32 plan are taken: seminaive == 0, directly (the
+ * default); seminaive != 0, by the paper's seminaive algorithm (Eq. DCT,
+ * Eq. dct_trick): a DCT of every order's data over the rings (with the
+ * theta-parity fold: a DCT-II of the symmetric and a DCT-IV of the
+ * antisymmetric part, each of length B, through an FFT of length 2B), then
+ * for each degree l an inner product over the first deg/2 + 1 DCT
+ * coefficients with the stored cosine coefficients of Lambda_lm (of
+ * Lambda_lm / sin theta for odd m).  Same results up to rounding; applies to
+ * sgl_forward and to sgl_adjoint(of_inverse != 0).  Tensor-core plans return
+ * SGL_ERR_UNSUPPORTED.  Not safe while calls on the plan are in flight.
+ */
+sgl_status sgl_set_dlt(sgl_plan_t plan, int seminaive);
+
+/*
  * sgl_midpoint - SGL coefficients by the midpoint rule on a Cartesian grid,
  * the current practice the paper's Discussion describes (built to compare
  * accuracy and cost with the SGL transform; no sampling theorem makes it

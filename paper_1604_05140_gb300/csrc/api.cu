@@ -69,7 +69,8 @@ static void release(Plan* P) {
   tc_release(*P);
   if (!P->owns_err) P->d_err = nullptr;
   void* ptrs[] = {P->d_tab, P->d_tab_lo, P->d_w1, P->d_w2, P->d_stage_in, P->d_stage_out, P->d_segs,
-                  P->d_fn_samp, P->d_fn_coef, P->d_si_rows, P->d_err, P->d_fft_fwd, P->d_fft_inv, P->d_ccoef};
+                  P->d_fn_samp, P->d_fn_coef, P->d_si_rows, P->d_err, P->d_fft_fwd, P->d_fft_inv, P->d_ccoef,
+                  P->d_dct_ctas};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (GemmSched* g : {&P->leg_fwd, &P->rad_fwd, &P->rad_inv, &P->leg_inv})
@@ -137,6 +138,22 @@ void sgl::pack_tables(const Plan& P, std::vector<real>& tab) {
           }
         }
       }
+    for (int m = 0; m < B; ++m)
+      for (int p = 0; p < 2; ++p) {
+        const int64_t r0 = leg_rows_before(B, m, p);
+        for (int q = 0; q < n_par(B, m, p); ++q) {
+          const int l = m + p + 2 * q;
+          for (int k = 0; k < B; ++k) tab[sg.tab_leg_s + (r0 + q) * B + k] = (real)H.lcos[((size_t)m * B + l) * B + k];
+        }
+      }
+    for (int k = 0; k < B; ++k) {
+      const long double pi = 3.141592653589793238462643383279502884L;
+      tab[sg.tab_dct + k] = (real)cosl(pi * k / (2.0L * B));
+      tab[sg.tab_dct + B + k] = (real)sinl(pi * k / (2.0L * B));
+      tab[sg.tab_dct + 2 * B + k] = (real)cosl(pi * (2.0L * k + 1.0L) / (4.0L * B));
+      tab[sg.tab_dct + 3 * B + k] = (real)sinl(pi * (2.0L * k + 1.0L) / (4.0L * B));
+      tab[sg.tab_dct + 4 * B + k] = (real)sinl(pi * (2.0L * k + 1.0L) / (4.0L * B));  // sin theta_k
+    }
     for (int l = 0; l < B; ++l) {
       const int64_t r0 = rad_rows_before(B, l);
       for (int q = 0; q < B - l; ++q) {
@@ -163,7 +180,7 @@ static void set_launch_count(Plan& P) {
     fwd += 2;
     inv += 2;
   } else {
-    fwd += P.leg_fwd.launches() + P.rad_fwd.launches();
+    fwd += P.leg_fwd.launches() + P.rad_fwd.launches() + (P.seminaive ? (int)P.segs.size() : 0);
     inv += P.rad_inv.launches() + P.leg_inv.launches();
   }
   P.launches_per_call = std::max(fwd, inv) + (P.real_pairs ? 1 : 0);
@@ -260,6 +277,10 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
     tab += rad_table_size(sg.B, sg.R);
     sg.tab_rad_i = tab;
     tab += rad_table_size(sg.B, sg.R);
+    sg.tab_leg_s = tab;
+    tab += leg_table_size(sg.B);
+    sg.tab_dct = tab;
+    tab += 5 * sg.B;
     tab = (tab + 31) / 32 * 32;
     sg.si_rows = (int64_t)si_rows.size();
     for (int mi = 0; mi < 2 * sg.B - 1; ++mi)
@@ -367,6 +388,27 @@ static size_t sample_bytes(const Plan& P) { return P.real_pairs ? complex_bytes(
 // functions as the user counts them
 static int user_fns(const Plan& P) { return P.real_pairs ? P.nreal : P.nfn; }
 
+// Forward Legendre stage by the seminaive algorithm (or back to the direct
+// sums); builds the DCT CTA list on first use.
+static sgl_status set_dlt(Plan* P, bool on) {
+  if (on && !P->d_dct_ctas) {
+    std::vector<int4> v;
+    for (size_t s = 0; s < P->segs.size(); ++s) {
+      const SegDesc& sg = P->segs[s];
+      const int64_t nvec = (int64_t)(2 * sg.B - 1) * 2 * sg.NB * 2 * sg.R;
+      if (nvec >= ((int64_t)1 << 31)) return fail(P, SGL_ERR_UNSUPPORTED, "too many spectra for the DCT schedule");
+      for (int64_t v0 = 0; v0 < nvec; v0 += kDctVec)
+        v.push_back(make_int4((int)s, (int)v0, (int)std::min<int64_t>(kDctVec, nvec - v0), 0));
+    }
+    const cudaError_t e = dev_upload(*P, &P->d_dct_ctas, v);
+    if (e != cudaSuccess) return cuda_fail(P, e, "DCT schedule upload");
+    P->n_dct = (int)v.size();
+  }
+  P->seminaive = on;
+  set_launch_count(*P);
+  return SGL_OK;
+}
+
 static sgl_status ensure_stage(Plan& P, void** buf, size_t* have, size_t need) {
   if (*have >= need) return SGL_OK;
   if (*buf) {
@@ -402,7 +444,8 @@ static sgl_status ensure_pipeline(Plan* P) {
     S->jp_fwd = P->jp_fwd;
     S->jp_inv = P->jp_inv;
     S->radi_narrow = P->radi_narrow;
-    const sgl_status st = build_plan(S, std::vector<int>(n, B), true);
+    sgl_status st = build_plan(S, std::vector<int>(n, B), true);
+    if (st == SGL_OK && P->seminaive) st = set_dlt(S, true);
     if (st != SGL_OK) {
       const std::string m = S->err;
       release(S);
@@ -857,6 +900,20 @@ const char* sgl_stage_name(int stage) {
                                               "radial_inverse", "legendre_inverse", "fft_inverse"};
   if (stage < 0 || stage >= SGL_NUM_STAGES) return "";
   return names[stage];
+}
+
+sgl_status sgl_set_dlt(sgl_plan_t plan, int seminaive) {
+  Plan* P = (Plan*)plan;
+  if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
+  if (tc_precision(P->prec))
+    return fail(P, SGL_ERR_UNSUPPORTED, "the seminaive Legendre transform is built for FP64 and FP32 plans");
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != P->device) cudaSetDevice(P->device);
+  release_pipeline(P);  // sub-batch plans are rebuilt with the setting on next use
+  const sgl_status st = set_dlt(P, seminaive != 0);
+  if (cur != P->device) cudaSetDevice(cur);
+  return st;
 }
 
 sgl_status sgl_autotune(sgl_plan_t plan, void* samples, void* coeffs, const char* cache_path,

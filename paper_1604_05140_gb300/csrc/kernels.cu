@@ -334,6 +334,7 @@ struct GemmArgs {
   const void* x;     // stage input (W1, W2 or coefficients)
   void* y;           // stage output
   int weighted;      // forward stages: use the weighted tables
+  int seminaive;     // forward Legendre stage: x holds DCTs, table of cosine coefficients
 };
 
 constexpr int TM = 64, TN = 64, TK = 16;
@@ -376,7 +377,8 @@ __device__ __forceinline__ void group_setup(const GemmArgs& a, const SegDesc& sg
     c.K = B;
     c.xs = c.as = B;
     c.xbase = sg.w1_off + ((int64_t)c.m_idx * 2 + c.p) * NB * 2 * R * B;
-    c.abase = (a.weighted ? sg.tab_leg_f : sg.tab_leg_i) + leg_rows_before_d(B, c.am, c.p) * B;
+    c.abase = (a.seminaive ? sg.tab_leg_s : a.weighted ? sg.tab_leg_f : sg.tab_leg_i) +
+              leg_rows_before_d(B, c.am, c.p) * B;
   } else if (PROB == RAD_F) {
     c.l = g;
     c.rows = NB * (2 * c.l + 1) * 2;
@@ -511,7 +513,16 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[r][q] = acc2[r][q] = 0;
-  for (int k0 = 0; k0 < c.K; k0 += TK) {
+  // seminaive forward Legendre: the tile's highest degree l bounds the DCT
+  // indices k' it needs (k' <= deg / 2, the table is zero beyond)
+  int kend = c.K;
+  if (PROB == LEG_F && a.seminaive) {
+    const int cmax = min(col0 + TNv, c.N) - 1;
+    const int l = c.am + c.p + 2 * cmax;
+    const int deg = (c.am & 1) ? l - 1 : l;
+    kend = min(c.K, (c.p ? (deg - 1) / 2 : deg / 2) + 1);
+  }
+  for (int k0 = 0; k0 < kend; k0 += TK) {
     // X tile: TM rows x TK (k fastest across threads for coalesced row reads)
     for (int e = threadIdx.x; e < TMv * TK; e += 256) {
       const int rr = e / TK, kk = e % TK;
@@ -556,6 +567,108 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       store_y<PROB, real>(a, sg, c, row0 + ty + RX * r, col0 + tx + CX * q, acc[r][q], acc2[r][q]);
+}
+
+// ---------------------------------------------------------------------------
+// seminaive Legendre transform: DCTs of the forward spectra
+// ---------------------------------------------------------------------------
+// Eq. (dct_trick) with the theta-parity fold: an E vector (symmetric part)
+// pairs with cos(2k' theta), an O vector with cos((2k'+1) theta), so the DCT
+// of the weighted data u_j' = beta_j' w_m(theta_j') x_j' over the half grid
+// is a DCT-II (E) or a DCT-IV (O) of length B:
+//   E: D_k' = sum_j' u_j' cos(k'(2j'+1) pi / 2B) = Re(e^{-i pi k'/2B} Y_k') / 2,
+//      Y the FFT of length 2B of (u_0 .. u_{B-1}, u_{B-1} .. u_0);
+//   O: D_k' = sum_j' u_j' cos((2k'+1)(2j'+1) pi / 4B) = Re(e^{-i pi (2k'+1)/4B} Z_k'),
+//      Z the FFT of length 2B of (u_j' e^{-i pi j'/2B}, then B zeros).
+// w_m = sin(theta) for odd |m| (the cosine-coefficient table holds
+// Lambda_lm / w_m), 1 otherwise; beta only for weighted transforms.  In place
+// on the spectra, vectors [m_idx][p][b][c][i] of B reals each; the FFT is the
+// phi-FFT's shared-memory one.
+
+struct DctArgs {
+  const SegDesc* segs;
+  const int4* ctas;  // (segment, first vector, vectors, 0)
+  const void* tab;
+  void* w1;
+  int weighted;
+};
+
+template <typename real, int N1, int N2C>
+__global__ void __launch_bounds__(256) dct_kernel(DctArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int4 cta = a.ctas[blockIdx.x];
+  const SegDesc sg = a.segs[cta.x];
+  const int B = sg.B, N = 2 * B, NB = sg.NB, NR = sg.R;
+  const int n2 = sg.n2;
+  const int NV = cta.z;
+  const int pitch = ring_pitch(N1, n2);
+  real* wre = reinterpret_cast<real*>(smem_raw);
+  real* wim = wre + N;
+  real* sre = wim + N;
+  real* sim = sre + kDctVec * pitch;
+  const real* tab = reinterpret_cast<const real*>(a.tab);
+  const real* misc = tab + sg.tab_misc;
+  const real* dc = tab + sg.tab_dct;  // [cos pi k/2B | sin | cos pi(2k+1)/4B | sin | sin theta]
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    wre[k] = misc[3 * NR + 2 * B + 2 * k];
+    wim[k] = misc[3 * NR + 2 * B + 2 * k + 1];
+  }
+  real* w1 = reinterpret_cast<real*>(a.w1) + sg.w1_off;
+  const int64_t per_m = (int64_t)2 * NB * 2 * NR;  // vectors per m_idx
+  for (int e = threadIdx.x; e < NV * B; e += blockDim.x) {
+    const int r = e / B, j = e - r * B;
+    const int64_t vec = cta.y + r;
+    const int m_idx = (int)(vec / per_m);
+    const int p = (int)((vec / (per_m / 2)) & 1);
+    const int am = m_idx - (B - 1) < 0 ? (B - 1) - m_idx : m_idx - (B - 1);
+    real u = w1[vec * B + j];
+    if (a.weighted) u *= misc[3 * NR + j];
+    if (am & 1) u *= dc[4 * B + j];
+    real* pr = sre + r * pitch;
+    real* pi = sim + r * pitch;
+    auto slot = [&](int k) { const int c1 = k / n2; return c1 * (n2 + 1) + (k - c1 * n2); };
+    if (p == 0) {
+      pr[slot(j)] = u;
+      pi[slot(j)] = 0;
+      pr[slot(N - 1 - j)] = u;
+      pi[slot(N - 1 - j)] = 0;
+    } else {
+      pr[slot(j)] = u * dc[j];
+      pi[slot(j)] = -u * dc[B + j];
+      pr[slot(B + j)] = 0;
+      pi[slot(B + j)] = 0;
+    }
+  }
+  __syncthreads();
+  fft_rings<real, N1, N2C, false>(sre, sim, wre, wim, NV, n2, N, pitch);
+  for (int e = threadIdx.x; e < NV * B; e += blockDim.x) {
+    const int r = e / B, k = e - r * B;
+    const int64_t vec = cta.y + r;
+    const int p = (int)((vec / (per_m / 2)) & 1);
+    const int sl = (k % N1) * (n2 + 1) + k / N1;
+    const real yr = sre[r * pitch + sl], yi = sim[r * pitch + sl];
+    w1[vec * B + k] = p == 0 ? (real)0.5 * (dc[k] * yr + dc[B + k] * yi) : dc[2 * B + k] * yr + dc[3 * B + k] * yi;
+  }
+}
+
+template <typename real>
+static cudaError_t launch_dct_t(const DctArgs& a, int n1, int n2, int first, int nctas, size_t smem, cudaStream_t s) {
+  void (*fn)(DctArgs) = nullptr;
+#define SGL_PICK(N1, N2C) fn = dct_kernel<real, N1, N2C>;
+  if (n1 == 16 && n2 == 16) { SGL_PICK(16, 16) }
+  else if (n1 == 16 && n2 == 8) { SGL_PICK(16, 8) }
+  else if (n1 == 16) { SGL_PICK(16, 0) }
+  else if (n1 == 8) { SGL_PICK(8, 0) }
+  else if (n1 == 4) { SGL_PICK(4, 0) }
+  else if (n1 == 2) { SGL_PICK(2, 0) }
+  else { SGL_PICK(1, 0) }
+#undef SGL_PICK
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  DctArgs b = a;
+  b.ctas = a.ctas + first;
+  fn<<<nctas, 256, smem, s>>>(b);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -690,8 +803,9 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
 
 template <typename real>
 static cudaError_t run_gemm(Plan& P, int prob, const GemmSched& sch, const void* x, void* y, int weighted,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool seminaive = false) {
   GemmArgs a;
+  a.seminaive = seminaive ? 1 : 0;
   a.segs = P.d_segs;
   a.fn_coef = P.d_fn_coef;
   a.si_rows = P.d_si_rows;
@@ -699,15 +813,34 @@ static cudaError_t run_gemm(Plan& P, int prob, const GemmSched& sch, const void*
   a.x = x;
   a.y = y;
   a.weighted = weighted;
-  static const int stage_of[4] = {ST_LEG_F, ST_RAD_F, ST_RAD_I, ST_LEG_I};
-  StageTimer timer(P, stage_of[prob], s);
   cudaError_t e = cudaSuccess;
   for (int w = 0; w < kGemmShapes && e == cudaSuccess; ++w) {
     a.tiles = sch.d_tiles[w];
     e = launch_gemm_t<real>(prob, a, w, sch.ntiles[w], s);
   }
-  timer.finish();
   return e;
+}
+
+// DCT launches of the seminaive forward Legendre stage, one per segment
+template <typename real>
+static cudaError_t run_dct(Plan& P, bool weights, cudaStream_t s) {
+  DctArgs a;
+  a.segs = P.d_segs;
+  a.ctas = P.d_dct_ctas;
+  a.tab = P.d_tab;
+  a.w1 = P.d_w1;
+  a.weighted = weights ? 1 : 0;
+  int first = 0;
+  for (size_t k = 0; k < P.segs.size(); ++k) {
+    const SegDesc& sg = P.segs[k];
+    const int64_t nvec = (int64_t)(2 * sg.B - 1) * 2 * sg.NB * 2 * sg.R;
+    const int nctas = (int)((nvec + kDctVec - 1) / kDctVec);
+    const size_t smem = sizeof(real) * (4 * (size_t)sg.B + 2 * (size_t)kDctVec * ring_pitch(sg.n1, sg.n2));
+    const cudaError_t e = launch_dct_t<real>(a, sg.n1, sg.n2, first, nctas, smem, s);
+    if (e != cudaSuccess) return e;
+    first += nctas;
+  }
+  return cudaSuccess;
 }
 
 template <typename real>
@@ -721,9 +854,17 @@ static cudaError_t forward_t(Plan& P, const void* samples, void* coeffs, cudaStr
     if (e != cudaSuccess) return e;
     return run_tc_stage(P, RAD_F, P.d_w2, coeffs, weights, s);
   }
-  e = run_gemm<real>(P, LEG_F, P.leg_fwd, P.d_w1, P.d_w2, weights, s);
+  {
+    StageTimer timer(P, ST_LEG_F, s);
+    if (P.seminaive) e = run_dct<real>(P, weights, s);
+    if (e == cudaSuccess) e = run_gemm<real>(P, LEG_F, P.leg_fwd, P.d_w1, P.d_w2, weights, s, P.seminaive);
+    timer.finish();
+  }
   if (e != cudaSuccess) return e;
-  return run_gemm<real>(P, RAD_F, P.rad_fwd, P.d_w2, coeffs, weights, s);
+  StageTimer timer(P, ST_RAD_F, s);
+  e = run_gemm<real>(P, RAD_F, P.rad_fwd, P.d_w2, coeffs, weights, s);
+  timer.finish();
+  return e;
 }
 
 template <typename real>
@@ -734,9 +875,15 @@ static cudaError_t inverse_t(Plan& P, const void* coeffs, void* samples, cudaStr
     if (e != cudaSuccess) return e;
     e = run_tc_stage(P, LEG_I, P.d_w2, P.d_w1, 0, s);
   } else {
-    e = run_gemm<real>(P, RAD_I, P.rad_inv, coeffs, P.d_w2, 0, s);
+    {
+      StageTimer timer(P, ST_RAD_I, s);
+      e = run_gemm<real>(P, RAD_I, P.rad_inv, coeffs, P.d_w2, 0, s);
+      timer.finish();
+    }
     if (e != cudaSuccess) return e;
+    StageTimer timer(P, ST_LEG_I, s);
     e = run_gemm<real>(P, LEG_I, P.leg_inv, P.d_w2, P.d_w1, 0, s);
+    timer.finish();
   }
   if (e != cudaSuccess) return e;
   int mode = 0;

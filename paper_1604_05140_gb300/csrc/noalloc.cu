@@ -100,6 +100,10 @@ sgl_status describe(DeviceState& D, int B, int batch) {
   tab += rad_table_size(B, B);
   sg.tab_rad_i = tab;
   tab += rad_table_size(B, B);
+  sg.tab_leg_s = tab;  // packed with the others, unused here
+  tab += leg_table_size(B);
+  sg.tab_dct = tab;
+  tab += 5 * B;
   sg.si_rows = 0;
   P.tab_elems = tab;
   HostTables H;

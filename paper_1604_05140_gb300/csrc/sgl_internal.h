@@ -21,6 +21,10 @@ struct HostTables {
   std::vector<double> theta, phi, beta;    // [2B]  sphere rule (Thm 3.1, beta = pi/B b_j)
   std::vector<double> lam;                 // [m][l][j'] m,l < B, j' < B: Lambda_lm(theta_j')
   std::vector<double> T;                   // [l][n-1][i < R]: N_nl R_nl(r_i) exp(-t_i/2)
+  // seminaive Legendre transform: cosine coefficients of Lambda_lm / w_m
+  // (w_m = sin theta for odd m) in the frequencies 2k' (l - m even) or 2k'+1
+  // (l - m odd), k' < B, zero beyond the degree: [m][l][k']
+  std::vector<double> lcos;
 };
 
 // Builds every table for bandlimit B (1 <= B <= SGL_MAX_B) on the radial grid
@@ -143,6 +147,10 @@ struct SegDesc {
   int64_t tab_rad_f, tab_rad_i;         // reals: radial tables (fwd: * what, inv: plain)
   int64_t tab_misc;                     // reals
   int64_t si_rows;                      // offset of the segment's S_i row table in d_si_rows
+  // seminaive Legendre transform (SIMT plans): cosine coefficients of
+  // Lambda_lm / w_m in the Legendre block layout, then 5B reals of DCT
+  // twiddles: cos, sin of pi k / 2B; cos, sin of pi (2k+1) / 4B; sin theta_j'
+  int64_t tab_leg_s, tab_dct;
 };
 
 // Tile of a GEMM stage: (segment, group, row0, col0)
@@ -152,6 +160,7 @@ struct SegDesc {
 // and 256 x 16 outputs (rows x columns); a group's tiles take the narrowest
 // shape that holds its column count (kernels.cu).
 constexpr int kGemmShapes = 3;
+constexpr int kDctVec = 16;  // vectors per CTA of the seminaive DCT kernel
 inline int gemm_shape_of(int ncols) { return ncols <= 16 ? 2 : ncols <= 32 ? 1 : 0; }
 inline int gemm_shape_cols(int w) { return 64 >> w; }
 inline int gemm_shape_rows(int w) { return 64 << w; }
@@ -232,6 +241,12 @@ struct Plan {
   bool real_pairs = false;
   int nreal = 0;
   void* d_ccoef = nullptr;
+
+  // forward Legendre stage by the seminaive algorithm (sgl_set_dlt, SIMT
+  // plans): DCT CTA list (segment, first vector, vectors, 0)
+  bool seminaive = false;
+  int4* d_dct_ctas = nullptr;
+  int n_dct = 0;
 
   std::string err;
   int latched = SGL_OK;

@@ -326,6 +326,35 @@ bool build_tables(int B, int grid, HostTables& out, std::string& msg) {
       }
     }
   }
+
+  // cosine coefficients for the seminaive Legendre transform (Eq. dct_trick):
+  // on the half grid j' < B, Q = Lambda_lm / w_m expands in cos(2k' theta)
+  // (even l - m, a DCT-II of length B inverts it) or cos((2k'+1) theta) (odd
+  // l - m, a DCT-IV); only k' up to half the degree (l, or l - 1 for odd m)
+  // can be non-zero, and the rest is set to zero
+  out.lcos.assign((size_t)B * B * B, 0.0);
+  std::vector<double> q(B), cs2((size_t)B * B), cs4((size_t)B * B), snt(B);
+  for (int j = 0; j < B; ++j) snt[j] = (double)sinl((2.0L * j + 1.0L) * kPiL / (4.0L * B));
+  for (int k = 0; k < B; ++k)
+    for (int j = 0; j < B; ++j) {
+      cs2[(size_t)k * B + j] = (double)cosl((long double)k * (2.0L * j + 1.0L) * kPiL / (2.0L * B));
+      cs4[(size_t)k * B + j] = (double)cosl((2.0L * k + 1.0L) * (2.0L * j + 1.0L) * kPiL / (4.0L * B));
+    }
+  for (int m = 0; m < B; ++m)
+    for (int l = m; l < B; ++l) {
+      const bool odd_p = (l - m) & 1;
+      const int deg = (m & 1) ? l - 1 : l;
+      const int kmax = odd_p ? (deg - 1) / 2 : deg / 2;
+      for (int j = 0; j < B; ++j) q[j] = out.lam[((size_t)m * B + l) * B + j] / ((m & 1) ? snt[j] : 1.0);
+      for (int k = 0; k <= kmax && k < B; ++k) {
+        const double* cs = (odd_p ? cs4.data() : cs2.data()) + (size_t)k * B;
+        long double acc = 0.0L;
+        for (int j = 0; j < B; ++j) acc += (long double)q[j] * cs[j];
+        double v = (double)(acc * 2.0L / B);
+        if (!odd_p && k == 0) v *= 0.5;
+        out.lcos[((size_t)m * B + l) * B + k] = v;
+      }
+    }
   return true;
 }
 

@@ -84,6 +84,7 @@ def load_library():
         "sgl_tuning": (ctypes.c_char_p, [vp]),
         "sgl_selftest_wait": (i32, [i64, ctypes.POINTER(ctypes.c_int)]),
         "sgl_midpoint": (i32, [i32, i32, ctypes.c_double, i32, i32, vp, vp, vp]),
+        "sgl_set_dlt": (i32, [vp, i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -377,6 +378,11 @@ class Plan:
         self._prep(coeffs, self.n_coeffs, "coeffs")
         sgl_autotune(self.handle, samples.data_ptr(), coeffs.data_ptr(), cache, self._stream(samples, coeffs))
         return self.tuning
+
+    def set_dlt(self, seminaive: bool):
+        """Forward Legendre sums directly (False) or by the seminaive
+        algorithm (True); FP64/FP32 plans (sgl_set_dlt)."""
+        _check(self.lib.sgl_set_dlt(self.handle, int(bool(seminaive))), self.handle)
 
     @property
     def tuning(self) -> str:

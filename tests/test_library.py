@@ -93,6 +93,7 @@ def test_plan_many_argument_errors(lib):
 
 
 def test_null_plan_queries(lib):
+    assert lib.sgl_set_dlt(None, 1) == sgl.SGL_ERR_ARG
     assert lib.sgl_radii(None, 0) == -1
     assert lib.sgl_sample_count(None) == -1
     assert lib.sgl_coeff_offset(None, 0) == -1
