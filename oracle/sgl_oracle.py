@@ -12,7 +12,11 @@ Gauss-Laguerre Basis Functions"):
 * the quadrature of the SGL sampling theorem (Thm 3.4), i.e. the forward
   transform ``fhat_nlm = sum_{i,j,k} w_ijk f(x_ijk) conj(H_nlm(x_ijk))``, and
   the reconstruction (inverse) ``f(x) = sum fhat_nlm H_nlm(x)`` (Algorithm 2);
-* the adjoints of both, from the matrix form of Sect. 3.4.
+* the adjoints of both, from the matrix form of Sect. 3.4;
+* the same forward transform with the Legendre sums taken by the seminaive
+  algorithm (Eq. DCT, Eq. dct_trick; ``forward_seminaive``);
+* the midpoint rule on a Cartesian grid that the Discussion describes as the
+  current practice (``midpoint``), with the closed-form basis.
 
 Readings taken where the paper is silent or differs from the grid used here
 (each is listed in the design notes with its reason):
