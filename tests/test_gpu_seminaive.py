@@ -94,3 +94,17 @@ def test_seminaive_unsupported_on_tensor_cores():
     p = Plan(8, 1, "tf32x3")
     assert p.lib.sgl_set_dlt(p.handle, 1) == sgl.SGL_ERR_UNSUPPORTED
     assert p.lib.sgl_set_dlt(p.handle, 0) == sgl.SGL_ERR_UNSUPPORTED
+
+
+def test_seminaive_uneven_bandlimits():
+    # one DCT launch per bandlimit segment
+    from paper_1604_05140_gb300 import Plan
+    Bs = [8, 5, 16, 8, 12]
+    p = Plan.many(Bs, precision="fp64")
+    p.set_dlt(True)
+    gs = [inputs.random_samples(B, 1, seed=3600 + k)[0] for k, B in enumerate(Bs)]
+    f = p.forward(_dev(np.concatenate([g.reshape(-1) for g in gs]), torch.complex128)).cpu().numpy()
+    for k, B in enumerate(Bs):
+        co = p.coeff_offset(k)
+        assert _err(f[co:co + O.coeff_count(B)][None], O.forward(gs[k], B)) < 1e-12, (k, B)
+    p.check()
