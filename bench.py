@@ -39,6 +39,20 @@ def omega_count(B):
     return B * (B + 1) * (2 * B + 1) // 6
 
 
+# CUDA-core arithmetic peak of GB300: 152 SMs at the 2070 MHz maximum SM
+# clock; FMA lanes per SM per clock: 128 in FP32, 2 in FP64 (152 x 2 x 2 flops
+# x 2.07 GHz = 1.26 TFLOP/s, the nominal FP64 rate).  FP64 and FP32 plans run
+# their Legendre and radial stages as GEMMs on these units.
+SMS = 152
+SM_MAX_MHZ = 2070
+SIMT_FMA_LANES = {"fp32": 128, "fp64": 2}
+GEMM_STAGES = ("legendre_forward", "radial_forward", "radial_inverse", "legendre_inverse")
+
+
+def alu_peak_tflops(prec):
+    return SMS * SIMT_FMA_LANES[prec] * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -535,12 +549,15 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+TRAFFIC_PROFILES = {"tf32x3": "tf32x3_kernels_b128x4_dram.md", "fp64": "fp64_simt_gemm_b128x2.md"}
+
+
 def measured_traffic(prec, kernel, batch):
-    """DRAM bytes of one launch of `kernel` from the committed ncu capture
+    """DRAM bytes of one stage of `kernel` from the committed ncu capture
     (per function x batch), or None when the capture is for other sources."""
-    if prec != "tf32x3":
+    if prec not in TRAFFIC_PROFILES:
         return None
-    path = os.path.join(ROOT, "profiles", "tf32x3_kernels_b128x4_dram.md")
+    path = os.path.join(ROOT, "profiles", TRAFFIC_PROFILES[prec])
     if not os.path.exists(path):
         return None
     recorded, per_fn = None, {}
@@ -567,6 +584,11 @@ def roofline(stage, cbytes, prec):
            "traffic": measured_traffic(prec, dom, BATCH), "peak_source": src, "launch_ms": ms,
            "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
            "stage_ms": {k: v[0] for k, v in stage.items()}}
+    if prec in SIMT_FMA_LANES and dom in GEMM_STAGES:
+        # a GEMM on the CUDA cores: bound by the FMA pipe of its precision
+        out.update(bound="alu", achieved=flops / (ms * 1e-3) / 1e12, peak=alu_peak_tflops(prec), unit="TFLOP/s",
+                   peak_source=f"derived: {SMS} SMs x {SIMT_FMA_LANES[prec]} {prec.upper()} FMA/clk x 2 flops"
+                               f" x {SM_MAX_MHZ} MHz")
     out["frac"] = out["achieved"] / out["peak"]
     return out
 
@@ -637,7 +659,8 @@ def run_ours(args):
         r = results["fp64"]
         line["fp64_path"] = {"value": r["value"], "unit": "transforms/s", "ms_per_step": r["ms"],
                              "steps": r["steps"], "round_trip_max_rel_err": r["err"],
-                             "stage_ms": {k: v[0] for k, v in r["stage"].items()}, "clocks": r["clocks"]}
+                             "stage_ms": {k: v[0] for k, v in r["stage"].items()}, "clocks": r["clocks"],
+                             "roofline": roofline(r["stage"], 16, "fp64")}
         line["split_vs_fp64"] = line["value"] / line["fp64_path"]["value"]
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(budget_s=args.cpu_seconds)

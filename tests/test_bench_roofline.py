@@ -1,0 +1,58 @@
+"""Roofline bookkeeping of bench.py on the host (no GPU): which bound a
+stage is measured against, the derived CUDA-core peaks, and the DRAM traffic
+read from the committed ncu summaries only while the sources match them."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+STAGES = ("fft_forward", "legendre_forward", "radial_forward", "radial_inverse", "legendre_inverse", "fft_inverse")
+
+
+def _stage(dominant, ms=10.0):
+    return {k: ((ms if k == dominant else 1.0), 1) for k in STAGES}
+
+
+def test_derived_alu_peaks():
+    # 152 SMs x FMA lanes x 2 flops x 2.07 GHz; FP64 is GB300's nominal 1.25 TFLOP/s
+    assert bench.alu_peak_tflops("fp64") == pytest.approx(1.25856)
+    assert bench.alu_peak_tflops("fp32") == pytest.approx(80.548, rel=1e-4)
+
+
+@pytest.mark.parametrize("prec,cbytes", [("fp64", 16), ("fp32", 8)])
+def test_cuda_core_gemm_stage_is_alu_bound(prec, cbytes, monkeypatch):
+    monkeypatch.setattr(bench, "BATCH", 4)
+    r = bench.roofline(_stage("legendre_forward"), cbytes, prec)
+    flops = bench.stage_model(bench.B_BENCH, 4, cbytes)["legendre_forward"][1]
+    assert r["kernel"] == "legendre_forward" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(flops / 10e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.alu_peak_tflops(prec))
+
+
+@pytest.mark.parametrize("prec,dominant", [("fp64", "fft_inverse"), ("tf32x3", "legendre_forward"),
+                                           ("tf32x3", "fft_inverse")])
+def test_hbm_bound_otherwise(prec, dominant, monkeypatch):
+    monkeypatch.setattr(bench, "BATCH", 4)
+    cbytes = 16 if prec == "fp64" else 8
+    r = bench.roofline(_stage(dominant), cbytes, prec)
+    nbytes = bench.stage_model(bench.B_BENCH, 4, cbytes)[dominant][0]
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(nbytes / 10e-3 / 1e9)
+
+
+@pytest.mark.parametrize("prec,stage", [("tf32x3", "fft_inverse"), ("tf32x3", "legendre_forward"),
+                                        ("fp64", "legendre_forward"), ("fp64", "radial_inverse")])
+def test_traffic_only_for_matching_sources(prec, stage, monkeypatch):
+    path = os.path.join(ROOT, "profiles", bench.TRAFFIC_PROFILES[prec])
+    with open(path) as fh:
+        recorded = [ln.split(":", 1)[1].strip() for ln in fh if ln.startswith("source-hash:")][0]
+    monkeypatch.setattr(bench, "source_hash", lambda: recorded)
+    per_fn = bench.measured_traffic(prec, stage, 1)
+    assert per_fn > 0 and bench.measured_traffic(prec, stage, 64) == 64 * per_fn
+    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
+    assert bench.measured_traffic(prec, stage, 64) is None
+    assert bench.measured_traffic("bf16x3", stage, 64) is None
