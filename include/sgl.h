@@ -48,8 +48,8 @@
  * device-side error flag (a bounded wait that gave up) is latched in the plan
  * and returned as SGL_ERR_TIMEOUT by the next call that synchronizes or by
  * sgl_check().  No call aborts the process.  sgl_last_error() returns a
- * message for the most recent failure on a plan (or on a failed creation when
- * passed NULL).
+ * message for the most recent failure on a plan (or, when passed NULL, for
+ * the most recent failed creation or plan-free call on the calling thread).
  *
  * Concurrency: a plan's workspace is shared by its calls, so calls on one
  * plan must be ordered (one stream, or synchronized); distinct plans are
@@ -279,8 +279,10 @@ const char* sgl_tuning(sgl_plan_t plan);
  */
 sgl_status sgl_selftest_wait(int64_t limit_ns, int* gave_up);
 
-/* Message for the last failure on `plan` (or of plan creation when NULL).
- * The string stays valid until the next call on the same plan. */
+/* Message for the last failure on `plan`; with NULL, for the last failed
+ * plan creation or plan-free call (sgl_forward_noalloc, sgl_midpoint) on the
+ * calling thread.  The string stays valid until the next call on the same
+ * plan (with NULL: the next such call on the same thread). */
 const char* sgl_last_error(sgl_plan_t plan);
 
 /* Release the plan, its tables and its workspace.  NULL is ignored. */

@@ -20,10 +20,12 @@ void tc_release(Plan& P);
 
 using namespace sgl;
 
-static std::string g_create_error;
+// Failures that have no plan to hold their message (plan creation, plan-free
+// entry points); one per thread, so concurrent creations keep their own.
+static thread_local std::string g_create_error;
 
 namespace sgl {
-// Message returned by sgl_last_error(NULL).
+// Message returned by sgl_last_error(NULL) on the calling thread.
 void set_global_error(const std::string& msg) { g_create_error = msg; }
 }  // namespace sgl
 

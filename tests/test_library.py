@@ -72,6 +72,29 @@ def test_plan_grid_argument_errors(lib, args, status):
     assert lib.sgl_last_error(None)
 
 
+def test_creation_errors_are_per_thread(lib):
+    # two threads fail plan creation in turn; each then reads its own message
+    import threading
+    bar = threading.Barrier(2)
+    seen = {}
+
+    def worker(name, args):
+        h = ctypes.c_void_p()
+        if name == "second":
+            bar.wait()
+        assert lib.sgl_plan(ctypes.byref(h), *args) != sgl.SGL_OK
+        if name == "first":
+            bar.wait()
+        bar.wait()
+        seen[name] = lib.sgl_last_error(None).decode()
+
+    t1 = threading.Thread(target=worker, args=("first", (0, 1, 0, 0)))
+    t2 = threading.Thread(target=worker, args=("second", (8, 1, 9, 0)))
+    t1.start(); t2.start(); t1.join(); t2.join()
+    assert "bandlimit" in seen["first"]
+    assert "precision" in seen["second"]
+
+
 def test_midpoint_argument_errors(lib):
     # found before any device call: bandlimit, sizes, precision, null pointers
     assert lib.sgl_midpoint(0, 8, 5.0, 1, 0, None, None, None) == sgl.SGL_ERR_UNSUPPORTED
