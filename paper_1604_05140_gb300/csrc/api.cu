@@ -332,13 +332,16 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
   // SIMT GEMM schedules
   int TM, TN, TK;
   gemm_tile_dims(TM, TN, TK);
-  // tiles of every stage (0 LEG_F, 1 RAD_F, 2 RAD_I, 3 LEG_I) in the narrowest
-  // shape that holds the group's columns
+  // tiles of every stage (0 LEG_F, 1 RAD_F, 2 RAD_I, 3 LEG_I): whole blocks of
+  // 64 columns, then the group's remaining columns in the narrowest shape that
+  // holds them
   std::vector<int4> lists[4][kGemmShapes];
   auto add = [&](int stage, int s, int g, int rows, int ncols) {
-    const int w = gemm_shape_of(ncols), tm = gemm_shape_rows(w), tn = gemm_shape_cols(w);
-    for (int r0 = 0; r0 < rows; r0 += tm)
-      for (int c0 = 0; c0 < ncols; c0 += tn) lists[stage][w].push_back(make_int4(s, g, r0, c0));
+    for (int c0 = 0; c0 < ncols;) {
+      const int w = gemm_shape_of(ncols - c0), tm = gemm_shape_rows(w), tn = gemm_shape_cols(w);
+      for (int r0 = 0; r0 < rows; r0 += tm) lists[stage][w].push_back(make_int4(s, g, r0, c0));
+      c0 += tn;
+    }
   };
   for (size_t s = 0; s < P->segs.size(); ++s) {
     const SegDesc& sg = P->segs[s];

@@ -493,9 +493,9 @@ __device__ __forceinline__ void store_y(const GemmArgs& a, const SegDesc& sg, co
 }
 
 // Tiles of TMv x TNv outputs (TMv * TNv = 4096: 64 x 64, 128 x 32 or 256 x 16),
-// each of the 256 threads 4 x 4 of them; a stage's groups with few columns
-// (N <= 32 or <= 16) use the narrow shapes, so that padding columns do not
-// cost multiply-adds.
+// each of the 256 threads 4 x 4 of them; the columns of a group left after
+// its whole 64-column blocks (N <= 32 or <= 16 of them) use the narrow shapes,
+// so that padding columns do not cost multiply-adds.
 template <int PROB, typename real, int TMv, int TNv>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
   static_assert(TMv * TNv == 16 * 256, "256 threads of 4 x 4 outputs");
