@@ -492,13 +492,14 @@ __device__ __forceinline__ void store_y(const GemmArgs& a, const SegDesc& sg, co
   }
 }
 
-// Tiles of TMv x TNv outputs (TMv * TNv = 4096: 64 x 64, 128 x 32 or 256 x 16),
-// each of the 256 threads 4 x 4 of them; the columns of a group left after
-// its whole 64-column blocks (N <= 32 or <= 16 of them) use the narrow shapes,
-// so that padding columns do not cost multiply-adds.
+// Tiles of TMv x TNv outputs (64 x 64, 128 x 32, 256 x 16 with 256 threads;
+// 64 x 48 with 192), each thread 4 x 4 of them; the columns of a group left
+// after its whole 64-column blocks (N <= 48, 32 or 16 of them) use the
+// narrower shapes, so that padding columns do not cost multiply-adds.
 template <int PROB, typename real, int TMv, int TNv>
-__global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
-  static_assert(TMv * TNv == 16 * 256, "256 threads of 4 x 4 outputs");
+__global__ void __launch_bounds__(TMv * TNv / 16) gemm_simt_kernel(GemmArgs a) {
+  constexpr int NT = TMv * TNv / 16;  // threads
+  static_assert(TMv % 4 == 0 && TNv % 4 == 0 && NT % 32 == 0 && NT <= 256, "4 x 4 outputs per thread");
   constexpr int CX = TNv / 4, RX = TMv / 4;  // threads along columns and rows
   __shared__ real Xs[TK][TMv + 1];
   __shared__ real As[TK][TNv + 1];
@@ -524,11 +525,11 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs a) {
   }
   for (int k0 = 0; k0 < kend; k0 += TK) {
     // X tile: TM rows x TK (k fastest across threads for coalesced row reads)
-    for (int e = threadIdx.x; e < TMv * TK; e += 256) {
+    for (int e = threadIdx.x; e < TMv * TK; e += NT) {
       const int rr = e / TK, kk = e % TK;
       Xs[kk][rr] = load_x<PROB, real>(a, sg, c, row0 + rr, k0 + kk);
     }
-    for (int e = threadIdx.x; e < TNv * TK; e += 256) {
+    for (int e = threadIdx.x; e < TNv * TK; e += NT) {
       int cc, kk;
       if (PROB == RAD_I || PROB == LEG_I) {  // tables stored [k][col]: col fastest
         kk = e / TNv;
@@ -706,21 +707,23 @@ static cudaError_t launch_fft_t(const Plan& P, const FftArgs& a, int n1, int n2,
 
 template <typename real, int TMv, int TNv>
 static void launch_gemm_shape(int prob, const GemmArgs& a, int ntiles, cudaStream_t s) {
+  constexpr int NT = TMv * TNv / 16;
   switch (prob) {
-    case LEG_F: gemm_simt_kernel<LEG_F, real, TMv, TNv><<<ntiles, 256, 0, s>>>(a); break;
-    case RAD_F: gemm_simt_kernel<RAD_F, real, TMv, TNv><<<ntiles, 256, 0, s>>>(a); break;
-    case RAD_I: gemm_simt_kernel<RAD_I, real, TMv, TNv><<<ntiles, 256, 0, s>>>(a); break;
-    default: gemm_simt_kernel<LEG_I, real, TMv, TNv><<<ntiles, 256, 0, s>>>(a); break;
+    case LEG_F: gemm_simt_kernel<LEG_F, real, TMv, TNv><<<ntiles, NT, 0, s>>>(a); break;
+    case RAD_F: gemm_simt_kernel<RAD_F, real, TMv, TNv><<<ntiles, NT, 0, s>>>(a); break;
+    case RAD_I: gemm_simt_kernel<RAD_I, real, TMv, TNv><<<ntiles, NT, 0, s>>>(a); break;
+    default: gemm_simt_kernel<LEG_I, real, TMv, TNv><<<ntiles, NT, 0, s>>>(a); break;
   }
 }
 
-// shape w of GemmSched: 0 -> 64 x 64, 1 -> 128 x 32, 2 -> 256 x 16
+// shape w of GemmSched: 0 -> 64 x 64, 1 -> 128 x 32, 2 -> 256 x 16, 3 -> 64 x 48
 template <typename real>
 static cudaError_t launch_gemm_t(int prob, const GemmArgs& a, int w, int ntiles, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   if (w == 0) launch_gemm_shape<real, 64, 64>(prob, a, ntiles, s);
   else if (w == 1) launch_gemm_shape<real, 128, 32>(prob, a, ntiles, s);
-  else launch_gemm_shape<real, 256, 16>(prob, a, ntiles, s);
+  else if (w == 2) launch_gemm_shape<real, 256, 16>(prob, a, ntiles, s);
+  else launch_gemm_shape<real, 64, 48>(prob, a, ntiles, s);
   return cudaGetLastError();
 }
 

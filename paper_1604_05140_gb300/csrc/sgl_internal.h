@@ -156,18 +156,23 @@ struct SegDesc {
 // Tile of a GEMM stage: (segment, group, row0, col0)
 // FFT CTA:            (segment, shell = b*R + i, j'0, 0)
 
-// Tile lists of one SIMT GEMM stage, one per tile shape: 64 x 64, 128 x 32
-// and 256 x 16 outputs (rows x columns); a group's tiles take the narrowest
-// shape that holds its column count (kernels.cu).
-constexpr int kGemmShapes = 3;
+// Tile lists of one SIMT GEMM stage, one per tile shape w: 64 x 64 (w = 0),
+// 128 x 32 (1), 256 x 16 (2) and 64 x 48 (3) outputs (rows x columns); a
+// group's columns are covered by whole 64-column blocks, the rest by the
+// narrowest shape that holds it (kernels.cu).
+constexpr int kGemmShapes = 4;
 constexpr int kDctVec = 16;  // vectors per CTA of the seminaive DCT kernel
-inline int gemm_shape_of(int ncols) { return ncols <= 16 ? 2 : ncols <= 32 ? 1 : 0; }
-inline int gemm_shape_cols(int w) { return 64 >> w; }
-inline int gemm_shape_rows(int w) { return 64 << w; }
+inline int gemm_shape_of(int ncols) { return ncols <= 16 ? 2 : ncols <= 32 ? 1 : ncols <= 48 ? 3 : 0; }
+inline int gemm_shape_cols(int w) { return w == 3 ? 48 : 64 >> w; }
+inline int gemm_shape_rows(int w) { return w == 3 ? 64 : 64 << w; }
 struct GemmSched {
-  int4* d_tiles[kGemmShapes] = {nullptr, nullptr, nullptr};
-  int ntiles[kGemmShapes] = {0, 0, 0};
-  int launches() const { return (ntiles[0] > 0) + (ntiles[1] > 0) + (ntiles[2] > 0); }
+  int4* d_tiles[kGemmShapes] = {nullptr, nullptr, nullptr, nullptr};
+  int ntiles[kGemmShapes] = {0, 0, 0, 0};
+  int launches() const {
+    int n = 0;
+    for (int w = 0; w < kGemmShapes; ++w) n += ntiles[w] > 0;
+    return n;
+  }
 };
 
 struct Plan {

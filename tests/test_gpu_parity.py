@@ -217,6 +217,34 @@ def test_full_size_b128_sampled_functions_fp64():
         assert _err(f[k][None], O.forward(sk, B)) < FP64_TOL
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("B", [40, 104])
+def test_simt_tile_shapes_vs_oracle(prec, B):
+    # every SIMT tile shape (64, 48, 32 and 16 columns) in every stage: at
+    # B = 104 the radial stages and the Legendre synthesis cover 104 columns
+    # with a 64-column block and a 48-column tile, the forward Legendre groups
+    # have up to 52 columns; at B = 40 the synthesis and the inverse radial
+    # stage take one 48-column tile.  Coefficients without decay, so that the
+    # high degrees weigh as much as the low ones.
+    NB = 2
+    p = _plan(B, NB, prec)
+    ctype = torch.complex128 if prec == "fp64" else torch.complex64
+    tol = FP64_TOL if prec == "fp64" else FP32_TOL
+    c = inputs.random_coeffs(B, NB, seed=7000 + B)
+    if prec == "fp32":
+        c = c.astype(np.complex64).astype(np.complex128)
+    s = p.inverse(_dev(c, ctype))
+    s_ref = O.inverse(c[0], B)
+    assert _err(s[0].cpu().numpy()[None], s_ref) < tol
+    g = O.inverse(c[1], B)
+    if prec == "fp32":
+        g = g.astype(np.complex64).astype(np.complex128)
+    f = p.forward(_dev(np.concatenate([s_ref, g]), ctype)).cpu().numpy()
+    assert _err(f[1:], O.forward(g, B)) < tol
+    assert _err(f, c) < tol
+    assert _err(p.forward(s).cpu().numpy(), c) < tol
+
+
 def test_inputs_not_modified():
     B = 8
     p = _plan(B, 1, "fp64")
