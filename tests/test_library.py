@@ -144,3 +144,12 @@ def test_supported_bandlimits_match_header_rule():
             p *= 2
         assert n // p <= 16, B
     assert set(uneven_bandlimits()) <= set(range(16, 129, 8))
+    # the complete set: also these bandlimits that are neither <= 16 nor multiples of 8
+    extra = []
+    for B in range(17, 129):
+        n, p = 2 * B, 1
+        while p < 16 and n % (2 * p) == 0:
+            p *= 2
+        if n // p <= 16 and B % 8:
+            extra.append(B)
+    assert extra == [18, 20, 22, 26, 28, 30, 36, 44, 52, 60]
