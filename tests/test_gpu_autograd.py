@@ -7,7 +7,9 @@ with the same 1/n scaling).  The loss is quadratic, so central differences
 with h = 1e-6 are exact up to rounding: for a direction v the derivative
 Re<grad, v> (PyTorch's conjugate-Wirtinger gradient) must match
 (L(f + h v) - L(f - h v)) / 2h to about 1e-8 relative.  The gradient is also
-compared with 2 F^H (F f - c) from the FP64 oracle's adjoint.
+compared with 2 F^H (F f - c) from the FP64 oracle's adjoint.  Real-function
+plans (B=8, FP64) and TF32x3 plans (B=16, 2e-5) are checked against the
+oracle's adjoints the same way.
 """
 import numpy as np
 import pytest
@@ -88,3 +90,50 @@ def test_inverse_autograd_matches_oracle_adjoint(setup):
     ref = O.adjoint_inverse(wn[:1], B)[0]
     err = np.abs(g[0] - ref).max() / np.abs(ref).max()
     assert err < 1e-12, err
+
+
+def test_real_plan_autograd_matches_oracle_adjoints():
+    # real samples: the forward's gradient is the real part of the complex
+    # adjoint, the inverse's (samples = Re of the complex inverse) is the
+    # complex adjoint of the real sample gradient
+    from paper_1604_05140_gb300 import Plan, sgl_forward_autograd, sgl_inverse_autograd
+    Bs, nb = 8, 3
+    p = Plan(Bs, nb, "fp64", samples="real")
+    rng = np.random.default_rng(321)
+    g = rng.standard_normal(p.sample_shape)
+    ct = inputs.random_coeffs(Bs, nb, seed=322)
+    x = torch.from_numpy(g).cuda().requires_grad_(True)
+    loss = ((sgl_forward_autograd(x, p) - torch.from_numpy(ct).cuda()).abs() ** 2).sum()
+    loss.backward()
+    assert x.grad.dtype == torch.float64
+    resid = O.forward(g, Bs) - ct
+    ref = 2 * O.adjoint_forward(resid, Bs).real
+    gx = x.grad.cpu().numpy()
+    assert np.abs(gx - ref).max() / np.abs(ref).max() < 1e-12
+
+    c = torch.from_numpy(inputs.random_coeffs(Bs, nb, seed=323)).cuda().requires_grad_(True)
+    w = rng.standard_normal(p.sample_shape)
+    s = sgl_inverse_autograd(c, p)
+    assert s.dtype == torch.float64
+    (s * torch.from_numpy(w).cuda()).sum().backward()
+    ref = O.adjoint_inverse(w + 0j, Bs)
+    gc = c.grad.cpu().numpy()
+    assert np.abs(gc - ref).max() / np.abs(ref).max() < 1e-12
+
+
+def test_tf32x3_autograd_matches_oracle_adjoint():
+    # the tensor-core adjoint kernels as backward passes, split-precision gate
+    from paper_1604_05140_gb300 import Plan, sgl_forward_autograd
+    Bs, nb = 16, 2
+    p = Plan(Bs, nb, "tf32x3")
+    c0 = inputs.random_coeffs(Bs, nb, seed=324, decay=True)
+    f = O.inverse(c0, Bs).astype(np.complex64)
+    ct = inputs.random_coeffs(Bs, nb, seed=325, decay=True).astype(np.complex64)
+    x = torch.from_numpy(f).cuda().requires_grad_(True)
+    loss = ((sgl_forward_autograd(x, p) - torch.from_numpy(ct).cuda()).abs() ** 2).sum()
+    loss.backward()
+    resid = O.forward(f.astype(np.complex128), Bs) - ct.astype(np.complex128)
+    ref = 2 * O.adjoint_forward(resid, Bs)
+    gx = x.grad.cpu().numpy()
+    for k in range(nb):
+        assert np.abs(gx[k] - ref[k]).max() / np.abs(ref[k]).max() < 2e-5, k
