@@ -53,6 +53,23 @@ def alu_peak_tflops(prec):
     return SMS * SIMT_FMA_LANES[prec] * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
+# tensor-core precisions: MMA products per useful multiply-add and the dense
+# peak of their operand type relative to bf16 (TF32 runs at half the rate)
+TC_PRECS = {"tf32x3": (3, 0.5), "tf32": (1, 0.5), "bf16x3": (3, 1.0)}
+
+
+def bf16_peak():
+    """Measured dense bf16 TF/s (burst: each stage is timed as one launch
+    inside a short step, below the power cap), else the fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        if "bf16_tflops" in d:
+            return d["bf16_tflops"], "measured"
+    return 1900.0, "fallback"
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -590,6 +607,24 @@ def roofline(stage, cbytes, prec):
                    peak_source=f"derived: {SMS} SMs x {SIMT_FMA_LANES[prec]} {prec.upper()} FMA/clk x 2 flops"
                                f" x {SM_MAX_MHZ} MHz")
     out["frac"] = out["achieved"] / out["peak"]
+    if prec in TC_PRECS:
+        # the tcgen05 GEMM stages against the tensor pipe: achieved MMA rate,
+        # and the most that streaming their bytes at the HBM peak would allow
+        nprod, ratio = TC_PRECS[prec]
+        bf16, bsrc = bf16_peak()
+        tpeak = bf16 * ratio
+        out["gemm_stages"] = {"tensor_peak_tflops": tpeak, "tensor_peak_source": f"{bsrc} bf16 x {ratio}"}
+        for k in GEMM_STAGES:
+            if k not in stage:
+                continue
+            nb, fl = model[k]
+            t = stage[k][0] * 1e-3
+            out["gemm_stages"][k] = {
+                "mma_tflops": nprod * fl / t / 1e12,
+                "frac_tensor_peak": nprod * fl / t / 1e12 / tpeak,
+                "tensor_frac_at_hbm_peak": nprod * fl / (nb / (hbm * 1e9)) / 1e12 / tpeak,
+                "frac_hbm": nb / t / 1e9 / hbm,
+            }
     return out
 
 

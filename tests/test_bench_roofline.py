@@ -56,3 +56,22 @@ def test_traffic_only_for_matching_sources(prec, stage, monkeypatch):
     monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
     assert bench.measured_traffic(prec, stage, 64) is None
     assert bench.measured_traffic("bf16x3", stage, 64) is None
+
+
+def test_tensor_core_stages_against_the_tensor_pipe(monkeypatch):
+    # TF32x3: three TF32 products per useful multiply-add; streaming a
+    # Legendre stage's bytes at the HBM peak bounds its tensor-pipe share at
+    # 12 B^4 flops / (83.6 MB / HBM) / TF32 peak, independent of the batch
+    monkeypatch.setattr(bench, "BATCH", 64)
+    st = {k: (1.0, 1) for k in STAGES}
+    r = bench.roofline(st, 8, "tf32x3")
+    g = r["gemm_stages"]
+    hbm, _ = bench.peaks()
+    bf16, _ = bench.bf16_peak()
+    B = bench.B_BENCH
+    per_fn_bytes = 4 * B * B * (2 * B - 1) * 4 + 2 * B ** 3 * 4
+    ceiling = 3 * 4 * B ** 4 / (per_fn_bytes / (hbm * 1e9)) / 1e12 / (bf16 / 2)
+    assert g["legendre_forward"]["tensor_frac_at_hbm_peak"] == pytest.approx(ceiling)
+    assert g["legendre_forward"]["mma_tflops"] == pytest.approx(3 * 4 * B ** 4 * 64 / 1e-3 / 1e12)
+    assert set(g) >= set(bench.GEMM_STAGES)
+    assert "gemm_stages" not in bench.roofline(st, 16, "fp64")
