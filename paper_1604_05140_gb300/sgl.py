@@ -208,6 +208,80 @@ def sgl_check(plan, stream: int = 0):
     _check(load_library().sgl_check(plan, stream), plan)
 
 
+def sgl_sample_count(plan) -> int:
+    return load_library().sgl_sample_count(plan)
+
+
+def sgl_coeff_count(plan) -> int:
+    return load_library().sgl_coeff_count(plan)
+
+
+def sgl_sample_offset(plan, fn: int) -> int:
+    return load_library().sgl_sample_offset(plan, int(fn))
+
+
+def sgl_coeff_offset(plan, fn: int) -> int:
+    return load_library().sgl_coeff_offset(plan, int(fn))
+
+
+def sgl_num_functions(plan) -> int:
+    return load_library().sgl_num_functions(plan)
+
+
+def sgl_bandlimit(plan, fn: int) -> int:
+    return load_library().sgl_bandlimit(plan, int(fn))
+
+
+def sgl_radii(plan, fn: int) -> int:
+    return load_library().sgl_radii(plan, int(fn))
+
+
+def sgl_workspace_bytes(plan) -> int:
+    return load_library().sgl_workspace_bytes(plan)
+
+
+def sgl_launches_per_call(plan) -> int:
+    return load_library().sgl_launches_per_call(plan)
+
+
+def sgl_last_error(plan=None) -> str:
+    msg = load_library().sgl_last_error(plan)
+    return msg.decode() if msg else ""
+
+
+def sgl_version() -> str:
+    return load_library().sgl_version().decode()
+
+
+SGL_NUM_STAGES = 6
+
+
+def sgl_set_profiling(plan, enable: bool):
+    _check(load_library().sgl_set_profiling(plan, int(bool(enable))), plan)
+
+
+def sgl_stage_times(plan):
+    """{stage name: (summed device ms, launches)} since profiling was enabled."""
+    lib = load_library()
+    ms = (ctypes.c_double * SGL_NUM_STAGES)()
+    n = (ctypes.c_int64 * SGL_NUM_STAGES)()
+    _check(lib.sgl_stage_times(plan, ms, n), plan)
+    return {sgl_stage_name(k): (ms[k], int(n[k])) for k in range(SGL_NUM_STAGES)}
+
+
+def sgl_stage_name(stage: int) -> str:
+    name = load_library().sgl_stage_name(int(stage))
+    return name.decode() if name else ""
+
+
+def sgl_forward_noalloc(B: int, batch: int, samples_ptr: int, coeffs_ptr: int, stream: int = 0):
+    _check(load_library().sgl_forward_noalloc(int(B), int(batch), samples_ptr, coeffs_ptr, stream))
+
+
+def sgl_set_dlt(plan, seminaive: bool):
+    _check(load_library().sgl_set_dlt(plan, int(bool(seminaive))), plan)
+
+
 # ---------------------------------------------------------------------------
 # torch-facing plan
 # ---------------------------------------------------------------------------

@@ -126,6 +126,31 @@ def test_null_plan_queries(lib):
     lib.sgl_destroy(None)
 
 
+def test_binding_has_every_function_under_its_own_name(lib):
+    # the Python binding exposes each C function of the header as a module
+    # function of the same name; plan-free and null-plan calls need no GPU
+    missing = [n for n in sgl.header_functions() if not callable(getattr(sgl, n, None))]
+    assert not missing, missing
+    assert sgl.sgl_version().startswith("sgl-gb300")
+    assert [sgl.sgl_stage_name(k) for k in range(sgl.SGL_NUM_STAGES)] == [
+        "fft_forward", "legendre_forward", "radial_forward", "radial_inverse", "legendre_inverse", "fft_inverse"]
+    assert sgl.sgl_stage_name(sgl.SGL_NUM_STAGES) == ""
+    for q in (sgl.sgl_sample_count, sgl.sgl_coeff_count, sgl.sgl_num_functions, sgl.sgl_workspace_bytes,
+              sgl.sgl_launches_per_call):
+        assert q(None) == -1
+    for q in (sgl.sgl_sample_offset, sgl.sgl_coeff_offset, sgl.sgl_bandlimit, sgl.sgl_radii):
+        assert q(None, 0) == -1
+    for call in (lambda: sgl.sgl_set_profiling(None, True), lambda: sgl.sgl_stage_times(None),
+                 lambda: sgl.sgl_set_dlt(None, True), lambda: sgl.sgl_forward_noalloc(8, 0, 1, 1)):
+        with pytest.raises(sgl.SGLError) as e:
+            call()
+        assert e.value.status == sgl.SGL_ERR_ARG
+    with pytest.raises(sgl.SGLError) as e:
+        sgl.sgl_forward_noalloc(0, 1, 1, 1)
+    assert e.value.status == sgl.SGL_ERR_UNSUPPORTED
+    assert "bandlimits" in sgl.sgl_last_error(None)
+
+
 def test_selftest_wait_argument_errors(lib):
     import ctypes
     flag = ctypes.c_int(7)
