@@ -532,6 +532,18 @@ def uneven_path(steps, warmup):
             "max_rel_err": err, "launch_config": plan.tuning}
 
 
+def error_metrics(c, c2):
+    """Round-trip errors of the coefficients c2 = forward(inverse(c)) against c,
+    both (batch, Omega) tensors: the normwise max|d| / max|c| per function (the
+    tests' gate), the per-function l2 ratio ||d|| / ||c||, and the paper's
+    per-coefficient max |d_w| / |c_w| (Sect. 4), each the worst function."""
+    d = (c2 - c).abs().double()
+    a = c.abs().double()
+    return {"normwise_max": float((d.amax(dim=1) / a.amax(dim=1)).max()),
+            "l2": float((d.norm(dim=1) / a.norm(dim=1)).max()),
+            "per_coefficient": float((d / a).max())}
+
+
 def e2e_path(plan, c_np, steps, warmup):
     """Same step through the C ABI with host buffers: pinned host coefficients
     in, pinned host coefficients out; the library stages the copies."""
@@ -668,6 +680,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}", "launch_config": plan.tuning},
         "coeffs_per_s": value * omega_count(B_BENCH),
         "round_trip_max_rel_err": head["err"],
+        "round_trip_errors": error_metrics(head["bufs"][1], head["bufs"][3]),
         "roofline": rl,
         "e2e": {"value": e2e_value, "unit": "transforms/s",
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
@@ -694,6 +707,7 @@ def run_ours(args):
         r = results["fp64"]
         line["fp64_path"] = {"value": r["value"], "unit": "transforms/s", "ms_per_step": r["ms"],
                              "steps": r["steps"], "round_trip_max_rel_err": r["err"],
+                             "round_trip_errors": error_metrics(r["bufs"][1], r["bufs"][3]),
                              "stage_ms": {k: v[0] for k, v in r["stage"].items()}, "clocks": r["clocks"],
                              "roofline": roofline(r["stage"], 16, "fp64")}
         line["split_vs_fp64"] = line["value"] / line["fp64_path"]["value"]

@@ -75,3 +75,17 @@ def test_tensor_core_stages_against_the_tensor_pipe(monkeypatch):
     assert g["legendre_forward"]["mma_tflops"] == pytest.approx(3 * 4 * B ** 4 * 64 / 1e-3 / 1e12)
     assert set(g) >= set(bench.GEMM_STAGES)
     assert "gemm_stages" not in bench.roofline(st, 16, "fp64")
+
+
+def test_round_trip_error_metrics():
+    # the three error measures of the bench line on a hand-made case: two
+    # functions, the second with one coefficient off by 1e-6 of the largest
+    torch = pytest.importorskip("torch")
+    c = torch.tensor([[1.0 + 0j, 0.5j, -0.25], [2.0, 1.0j, 1e-3]], dtype=torch.complex128)
+    c2 = c.clone()
+    c2[1, 2] += 2e-6
+    e = bench.error_metrics(c, c2)
+    assert e["normwise_max"] == pytest.approx(2e-6 / 2.0)
+    assert e["l2"] == pytest.approx(2e-6 / (4 + 1 + 1e-6) ** 0.5)
+    assert e["per_coefficient"] == pytest.approx(2e-6 / 1e-3)
+    assert bench.error_metrics(c, c.clone()) == {"normwise_max": 0.0, "l2": 0.0, "per_coefficient": 0.0}
