@@ -230,17 +230,11 @@ def whole_job(ws, batch, ms_local):
 # CPU baseline: the oracle
 # ---------------------------------------------------------------------------
 
-def oracle_threads():
-    """Host threads the oracle's NumPy/BLAS calls use."""
-    cores = os.cpu_count()
-    try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        if info:
-            cores = max(i.get("num_threads", 1) for i in info)
-    except Exception:
-        pass
-    return cores
+def cores_used(wall_s, cpu_s):
+    """Threads the oracle kept busy on average: process CPU time over wall
+    time (the oracle's NumPy work is mostly single-threaded whatever the size
+    of the BLAS pool)."""
+    return max(1, round(cpu_s / wall_s)) if wall_s > 0 else 1
 
 
 def cpu_oracle_sample(B=B_BENCH, budget_s=12.0, seed=1604051403):
@@ -250,15 +244,16 @@ def cpu_oracle_sample(B=B_BENCH, budget_s=12.0, seed=1604051403):
     from paper_1604_05140_gb300 import inputs
     O.legendre_table(B)
     O.radial_table(B)  # tables are set-up, not part of a transform
-    n, t0 = 0, time.perf_counter()
+    n, t0, p0 = 0, time.perf_counter(), time.process_time()
     while True:
         c = inputs.random_coeffs(B, 1, seed=seed + n, decay=True)
         O.forward(O.inverse(c, B), B)
         n += 1
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "transforms/s", "cores": oracle_threads(), "kind": "oracle",
+    dt, cpu = time.perf_counter() - t0, time.process_time() - p0
+    return {"value": n / dt, "unit": "transforms/s", "cores": cores_used(dt, cpu), "kind": "oracle",
+            "threads_available": os.cpu_count(), "cpu_s": cpu,
             "sample": f"{n} whole functions of B={B} (inverse + forward each) out of the batch of {BATCH}, "
                       f"{dt:.1f} s, FP64 NumPy separated form"}
 
@@ -732,15 +727,16 @@ def run_reference(args):
     for w in range(args.warmup):
         c = inputs.random_coeffs(B_BENCH, 1, seed=7 + w, decay=True)
         O.forward(O.inverse(c, B_BENCH), B_BENCH)
-    times = []
+    times, cpu = [], 0.0
     for k in range(args.steps):
         c = inputs.random_coeffs(B_BENCH, 1, seed=inputs.BASE_SEED + 3 + k, decay=True)
-        t0 = time.perf_counter()
+        t0, p0 = time.perf_counter(), time.process_time()
         O.forward(O.inverse(c, B_BENCH), B_BENCH)
         times.append(time.perf_counter() - t0)
+        cpu += time.process_time() - p0
     ms = 1e3 * statistics.mean(times)
     value = 1.0 / (ms * 1e-3)
-    cores = oracle_threads()
+    cores = cores_used(sum(times), cpu)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": args.gpus,
         "devices": "host cores only: the oracle runs on rank 0's CPU and uses no GPU",
@@ -750,6 +746,7 @@ def run_reference(args):
                    "B": B_BENCH, "batch": BATCH, "precision": "fp64 (oracle)",
                    "step_sample": "one function of the batch per step"},
         "cpu_baseline": {"value": value, "unit": "transforms/s", "cores": cores, "kind": "oracle",
+                         "threads_available": os.cpu_count(), "cpu_s": cpu,
                          "sample": "one whole function of B=128 per step (inverse + forward), FP64 NumPy"},
         "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -89,3 +89,10 @@ def test_round_trip_error_metrics():
     assert e["l2"] == pytest.approx(2e-6 / (4 + 1 + 1e-6) ** 0.5)
     assert e["per_coefficient"] == pytest.approx(2e-6 / 1e-3)
     assert bench.error_metrics(c, c.clone()) == {"normwise_max": 0.0, "l2": 0.0, "per_coefficient": 0.0}
+
+
+def test_cores_used_is_cpu_time_over_wall_time():
+    assert bench.cores_used(10.0, 10.2) == 1
+    assert bench.cores_used(10.0, 0.5) == 1
+    assert bench.cores_used(2.0, 7.9) == 4
+    assert bench.cores_used(0.0, 1.0) == 1

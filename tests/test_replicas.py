@@ -91,5 +91,8 @@ def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
         assert k in line, k
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    # cores: the threads the oracle kept busy (CPU time over wall time), not the pool size
+    cb = line["cpu_baseline"]
+    assert 1 <= cb["cores"] <= cb["threads_available"] and cb["cpu_s"] > 0
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
