@@ -96,3 +96,10 @@ def test_cores_used_is_cpu_time_over_wall_time():
     assert bench.cores_used(10.0, 0.5) == 1
     assert bench.cores_used(2.0, 7.9) == 4
     assert bench.cores_used(0.0, 1.0) == 1
+
+
+def test_cpu_oracle_sample_line():
+    r = bench.cpu_oracle_sample(B=8, budget_s=0.2)
+    assert r["kind"] == "oracle" and r["unit"] == "transforms/s" and r["value"] > 0
+    assert 1 <= r["cores"] <= r["threads_available"] and r["cpu_s"] > 0
+    assert "B=8" in r["sample"]
