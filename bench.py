@@ -9,7 +9,9 @@ GPU path is timed on the same workload and reported alongside.
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank runs an independent replica of the batch (the
 transform of one function never needs another function's data), so the job
-scales weakly with no data-path collective.
+scales weakly with no data-path collective; `--gpus N` outside a launcher
+starts the N ranks itself.  The exit status is 3 when the round trip misses
+its error bound (1e-12 FP64, 1e-6 split precision), after the line is printed.
 """
 from __future__ import annotations
 
@@ -237,25 +239,97 @@ def cores_used(wall_s, cpu_s):
     return max(1, round(cpu_s / wall_s)) if wall_s > 0 else 1
 
 
-def cpu_oracle_sample(B=B_BENCH, budget_s=12.0, seed=1604051403):
-    """Times the FP64 oracle (inverse then forward) on whole functions of the
-    benchmark workload until about budget_s seconds have passed."""
+def _oracle_serve(B, inq, outq):
+    """Worker process of OraclePool: builds the oracle's tables, then runs one
+    whole function (inverse, then forward) per seed it receives and returns
+    the CPU seconds it took; None ends it."""
     import oracle as O
     from paper_1604_05140_gb300 import inputs
     O.legendre_table(B)
     O.radial_table(B)  # tables are set-up, not part of a transform
-    n, t0, p0 = 0, time.perf_counter(), time.process_time()
+    outq.put("ready")
     while True:
-        c = inputs.random_coeffs(B, 1, seed=seed + n, decay=True)
+        seed = inq.get()
+        if seed is None:
+            return
+        p0 = time.process_time()
+        c = inputs.random_coeffs(B, 1, seed=seed, decay=True)
         O.forward(O.inverse(c, B), B)
-        n += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt, cpu = time.perf_counter() - t0, time.process_time() - p0
-    return {"value": n / dt, "unit": "transforms/s", "cores": cores_used(dt, cpu), "kind": "oracle",
+        outq.put(time.process_time() - p0)
+
+
+class OraclePool:
+    """`workers` processes (spawned, so that none inherits a CUDA context; one
+    BLAS thread each) that transform whole functions of the workload with the
+    FP64 oracle in parallel: the oracle as it stands, on the host's cores."""
+
+    BLAS_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+    def __init__(self, workers, B=B_BENCH):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        saved = {k: os.environ.get(k) for k in self.BLAS_ENV}
+        for k in self.BLAS_ENV:
+            os.environ[k] = "1"
+        try:
+            self.inq = [ctx.Queue() for _ in range(workers)]
+            self.outq = ctx.Queue()
+            self.procs = [ctx.Process(target=_oracle_serve, args=(B, q, self.outq), daemon=True) for q in self.inq]
+            for p in self.procs:
+                p.start()
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        for _ in self.procs:
+            self.outq.get()
+        self.workers = workers
+
+    def run(self, seed0):
+        """One function per worker (seeds seed0, seed0 + 1, ...); returns the
+        wall seconds until the last finished and the summed CPU seconds."""
+        t0 = time.perf_counter()
+        for k, q in enumerate(self.inq):
+            q.put(seed0 + k)
+        cpu = sum(self.outq.get() for _ in self.inq)
+        return time.perf_counter() - t0, cpu
+
+    def close(self):
+        for q in self.inq:
+            q.put(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def host_workers():
+    """Oracle worker processes for the all-cores baseline: one per host core."""
+    return os.cpu_count() or 1
+
+
+def cpu_oracle_sample(B=B_BENCH, budget_s=12.0, seed=1604051403, workers=None):
+    """Times the FP64 oracle (inverse then forward) on whole functions of the
+    benchmark workload, on one core and on all host cores (one process per
+    core), each for about budget_s / 2 seconds."""
+    workers = workers or host_workers()
+    out = {}
+    for key, w in (("all", workers), ("one", 1)):
+        pool = OraclePool(w, B)
+        n, wall, cpu = 0, 0.0, 0.0
+        while wall < budget_s / 2:
+            dt, c = pool.run(seed + n)
+            n, wall, cpu = n + w, wall + dt, cpu + c
+        pool.close()
+        out[key] = (n, wall, cpu, w)
+    n, wall, cpu, w = out["all"]
+    n1, wall1, cpu1, _ = out["one"]
+    return {"value": n / wall, "unit": "transforms/s", "cores": w, "kind": "oracle",
             "threads_available": os.cpu_count(), "cpu_s": cpu,
-            "sample": f"{n} whole functions of B={B} (inverse + forward each) out of the batch of {BATCH}, "
-                      f"{dt:.1f} s, FP64 NumPy separated form"}
+            "sample": f"{n} whole functions of B={B} (inverse + forward each, {w} at a time in {w} processes "
+                      f"of one BLAS thread) out of the batch of {BATCH}, {wall:.1f} s, FP64 NumPy separated form",
+            "one_thread": {"value": n1 / wall1, "unit": "transforms/s", "cores": 1, "cpu_s": cpu1,
+                           "sample": f"{n1} whole functions of B={B} in one process, {wall1:.1f} s"}}
 
 
 # ---------------------------------------------------------------------------
@@ -527,6 +601,43 @@ def uneven_path(steps, warmup):
             "max_rel_err": err, "launch_config": plan.tuning}
 
 
+def profile_case(case, precision, steps, warmup):
+    """Round trips of one workload and nothing else, for profiler captures
+    (`--profile-case`): the uneven-bandlimit batch (256 functions, B in
+    {16, ..., 128}) or the uniform one (B = 128, --batch functions), eager
+    launches, default launch configuration.  Prints one JSON line with the
+    mean step time; not a benchmark line."""
+    import torch
+    from paper_1604_05140_gb300 import Plan, inputs
+    if case == "uneven":
+        Bs = [int(b) for b in inputs.uneven_bandlimits(256)]
+        plan = Plan.many(Bs, precision=precision)
+        c = np.concatenate([inputs.random_coeffs(B, 1, seed=inputs.BASE_SEED + 4 + 10 * k)[0]
+                            for k, B in enumerate(Bs)])
+    else:
+        plan = Plan(B_BENCH, BATCH, precision)
+        c = inputs.random_coeffs(B_BENCH, BATCH, seed=inputs.BASE_SEED + 3, decay=True)
+    c = torch.from_numpy(c).to(plan.dtype).cuda()
+    s = torch.empty(plan.sample_shape, dtype=plan.dtype, device="cuda")
+    out = torch.empty(plan.coeff_shape, dtype=plan.dtype, device="cuda")
+    for _ in range(warmup):
+        plan.inverse(c, out=s)
+        plan.forward(s, out=out)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        plan.inverse(c, out=s)
+        plan.forward(s, out=out)
+    ev1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    print(json.dumps({"profile_case": case, "precision": precision, "steps": steps, "warmup": warmup,
+                      "ms_per_step": ev0.elapsed_time(ev1) / steps,
+                      "launches_per_round_trip": 2 * plan.launches_per_call}), flush=True)
+
+
 def error_metrics(c, c2):
     """Round-trip errors of the coefficients c2 = forward(inverse(c)) against c,
     both (batch, Omega) tensors: the normwise max|d| / max|c| per function (the
@@ -637,6 +748,11 @@ def roofline(stage, cbytes, prec):
 
 def run_ours(args):
     import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if not torch.cuda.is_available() or ws > torch.cuda.device_count():
+        print(f"bench.py: {ws} rank(s) need as many visible GPUs; found "
+              f"{torch.cuda.device_count() if torch.cuda.is_available() else 0}", file=sys.stderr)
+        sys.exit(2)
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
     precs = [args.precision] + ([] if args.no_fp64 or args.precision == "fp64" else ["fp64"])
@@ -707,50 +823,91 @@ def run_ours(args):
                              "roofline": roofline(r["stage"], 16, "fp64")}
         line["split_vs_fp64"] = line["value"] / line["fp64_path"]["value"]
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_oracle_sample(budget_s=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_oracle_sample(budget_s=args.cpu_seconds, workers=args.cpu_workers)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    missed = error_gate(line)
+    if missed:
+        print("bench.py: error bound missed: " + "; ".join(missed), file=sys.stderr)
+        sys.exit(3)
 
 
 def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # each step: one whole function of the workload (inverse + forward) in the oracle
-    import oracle as O
-    from paper_1604_05140_gb300 import inputs
-    O.legendre_table(B_BENCH)
-    O.radial_table(B_BENCH)
+    # each step: one whole function of the workload (inverse + forward) per
+    # host core, in parallel worker processes running the oracle
+    workers = args.cpu_workers or host_workers()
+    pool = OraclePool(workers, B_BENCH)
     for w in range(args.warmup):
-        c = inputs.random_coeffs(B_BENCH, 1, seed=7 + w, decay=True)
-        O.forward(O.inverse(c, B_BENCH), B_BENCH)
+        pool.run(7 + w * workers)
     times, cpu = [], 0.0
     for k in range(args.steps):
-        c = inputs.random_coeffs(B_BENCH, 1, seed=inputs.BASE_SEED + 3 + k, decay=True)
-        t0, p0 = time.perf_counter(), time.process_time()
-        O.forward(O.inverse(c, B_BENCH), B_BENCH)
-        times.append(time.perf_counter() - t0)
-        cpu += time.process_time() - p0
+        dt, c = pool.run(inputs_base_seed() + 3 + k * workers)
+        times.append(dt)
+        cpu += c
+    pool.close()
     ms = 1e3 * statistics.mean(times)
-    value = 1.0 / (ms * 1e-3)
+    value = workers / (ms * 1e-3)
     cores = cores_used(sum(times), cpu)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": ws,
         "devices": "host cores only: the oracle runs on rank 0's CPU and uses no GPU",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"SGL inverse+forward, B={B_BENCH}, batch {BATCH} functions per GPU",
                    "B": B_BENCH, "batch": BATCH, "precision": "fp64 (oracle)",
-                   "step_sample": "one function of the batch per step"},
+                   "step_sample": f"{workers} functions of the batch per step, one per worker process"},
         "cpu_baseline": {"value": value, "unit": "transforms/s", "cores": cores, "kind": "oracle",
                          "threads_available": os.cpu_count(), "cpu_s": cpu,
-                         "sample": "one whole function of B=128 per step (inverse + forward), FP64 NumPy"},
+                         "sample": f"{workers} whole functions of B=128 per step (inverse + forward), "
+                                   f"{workers} processes of one BLAS thread, FP64 NumPy"},
         "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def inputs_base_seed():
+    from paper_1604_05140_gb300 import inputs
+    return inputs.BASE_SEED
+
+
+def relaunch(args):
+    """`--gpus N` with N > 1 outside a launcher: run this script again as N
+    ranks under torch.distributed.run (one process per GPU, rendezvous on
+    127.0.0.1) and return its exit status; None when no relaunch is needed."""
+    if args.gpus <= 1 or "WORLD_SIZE" in os.environ:
+        return None
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def error_gate(line):
+    """Names of the round-trip error bounds the line misses: 1e-12 normwise
+    for the FP64 path, 1e-6 for the split-precision (tensor-core, three
+    product) paths; empty when every bound holds."""
+    bounds = {"fp64": 1e-12, "tf32x3": 1e-6, "fp16x3": 1e-6}
+    missed = []
+    prec = line["config"]["precision"]
+    if prec in bounds and line["round_trip_errors"]["normwise_max"] > bounds[prec]:
+        missed.append(f"{prec} round trip {line['round_trip_errors']['normwise_max']:.3g} > {bounds[prec]:g}")
+    fp = line.get("fp64_path")
+    if fp and fp["round_trip_errors"]["normwise_max"] > bounds["fp64"]:
+        missed.append(f"fp64 round trip {fp['round_trip_errors']['normwise_max']:.3g} > 1e-12")
+    for name, v in line.get("variants", {}).items():
+        if name in bounds and v["round_trip_max_rel_err"] > bounds[name]:
+            missed.append(f"{name} round trip {v['round_trip_max_rel_err']:.3g} > {bounds[name]:g}")
+    return missed
 
 
 def main():
@@ -765,13 +922,24 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=16.0,
+                    help="CPU baseline budget, split between one core and all cores")
+    ap.add_argument("--cpu-workers", type=int, default=0,
+                    help="oracle worker processes of the all-cores baseline and the reference arm (0: one per core)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--profile-case", choices=["uneven", "uniform"], default=None,
+                    help="run only this workload's round trips (for profiler captures) and exit")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="functions per GPU (64 is the benchmark workload; smaller only for profiling runs)")
     args = ap.parse_args()
     BATCH = args.batch
     TUNE = not args.no_autotune
+    if args.profile_case:
+        profile_case(args.profile_case, args.precision, args.steps, args.warmup)
+        return
+    rc = relaunch(args)
+    if rc is not None:
+        sys.exit(rc)
     if args.impl == "reference":
         run_reference(args)
     else:

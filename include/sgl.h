@@ -86,9 +86,23 @@ typedef enum {
   SGL_TF32 = 3,    /* as SGL_TF32X3 with the hi*hi product only (inputs and
                       tables rounded to TF32, 11 significant bits): the fast,
                       low-accuracy variant (normwise error of order 1e-3) */
-  SGL_BF16X3 = 4   /* as SGL_TF32X3 with BF16 hi/lo pairs (8 + 8 significant
+  SGL_BF16X3 = 4,  /* as SGL_TF32X3 with BF16 hi/lo pairs (8 + 8 significant
                       bits) on the kind::f16 tensor-core path: normwise error
                       of order 1e-5 */
+  SGL_FP16X3 = 5   /* the Legendre sums (Eq. DLT) and radial sums (Eq.
+                      DRT_matrix) as three products of FP16 hi/lo pairs
+                      (11 + 11 significant bits, as TF32x3) on the kind::f16
+                      tensor-core path, FP32 accumulation and FFT.  FP16's
+                      range is held by power-of-two scales: one per table
+                      block (each order m and parity of the Legendre tables,
+                      each degree of the radial tables), chosen on the host,
+                      and one per function and stage for the data, taken from
+                      the largest magnitude of the function's phi-spectra
+                      (forward) or coefficients (inverse), measured by the
+                      kernels of each call, times a bound on the growth
+                      through the table for the second stage.  Normwise
+                      error as TF32x3 (of order 1e-7 to 1e-6) for inputs of
+                      any magnitude FP32 holds; bandlimits divisible by 4 */
 } sgl_precision;
 
 typedef enum {
@@ -271,10 +285,13 @@ const char* sgl_tuning(sgl_plan_t plan);
  * sgl_selftest_wait - check the failure detection of the tensor-core kernels
  * on the current device (an implementation aid; the paper has no
  * counterpart).  Those kernels bound every wait on an mbarrier and, when a
- * wait gives up, set the plan's error flag and end (sgl_check then returns
- * SGL_ERR_TIMEOUT).  This call runs one small kernel whose wait can never be
- * satisfied, with the bound limit_ns (1 .. 2e9 ns), and stores 1 in
- * *gave_up when the wait gave up and the kernel ended as designed.
+ * wait gives up, set the plan's error flag, wait (bounded) for the copies and
+ * MMAs they had already issued, free their tensor memory and end (sgl_check
+ * then returns SGL_ERR_TIMEOUT).  This call runs one small kernel that holds
+ * tensor memory and has a copy in flight while it waits on a barrier that is
+ * never completed, with the bound limit_ns (1 .. 2e9 ns), and stores 1 in
+ * *gave_up when the wait gave up, the wind-down finished and the kernel
+ * ended as designed (0 otherwise).
  * Synchronous; SGL_ERR_ARG for a bad bound or a NULL pointer.
  */
 sgl_status sgl_selftest_wait(int64_t limit_ns, int* gave_up);
@@ -300,19 +317,31 @@ void sgl_destroy(sgl_plan_t plan);
  * loop where an allocation could block on the device.  Creating a plan
  * allocates tables and workspace; this call does not: its scratch lives in a
  * static device array compiled into the library (16 MiB of doubles), and its
- * tables and launch schedules in a second static array (8 MiB).  Every GPU
- * that loads the library holds both arrays until the process exits.
+ * tables and launch schedules in a second static array (8 MiB).  A GPU holds
+ * both arrays from the moment the part of the library that defines them is
+ * loaded on it until the process exits.  Under CUDA's lazy module loading
+ * (the default) that happens at the first call on the device, which also
+ * loads the forward kernels' code: the driver reserves that memory then, and
+ * the call fails with SGL_ERR_CUDA if the device has no room left.  Make the
+ * first call at start-up, before the caller's allocator takes the device's
+ * memory, or run with CUDA_MODULE_LOADING=EAGER (everything loaded when the
+ * library is).  Later calls reserve nothing.
  *
  *   B        bandlimit, 1 <= B <= 32 (and the factor rule of SGL_MAX_B).
  *   batch    functions, >= 1, with 4 B^2 (2B-1) + 2 B^3 doubles of scratch per
  *            function fitting the 2^21-double scratch: B = 32 allows 6
  *            functions, B = 16 allows 52, B = 8 allows 431.  Larger requests
  *            return SGL_ERR_UNSUPPORTED with a message saying how much
- *            scratch they need.
+ *            scratch they need.  The tables and launch schedules of the
+ *            call must also fit the 8 MiB table array; only at B = 1 does
+ *            that bind first (about 170,000 functions), again with
+ *            SGL_ERR_UNSUPPORTED and a message.
  *   samples  device pointer, batch x 4B^3 complex doubles (weighted samples).
  *   coeffs   device pointer, batch x Omega complex doubles; overwritten.
  *            Host pointers are rejected (SGL_ERR_ARG): staging them would
- *            need device memory; so are pointers not 16-byte aligned.
+ *            need device memory; so are pointers not 16-byte aligned and
+ *            device memory of a GPU other than the current one (managed
+ *            memory is accepted).
  *   stream   stream the kernels are launched on.
  *
  * Set-up: the first call on a device looks up the device addresses of the

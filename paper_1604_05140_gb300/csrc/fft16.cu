@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   // the pair, then E/O straight to global memory
   const int q = threadIdx.x % JPmax;
   const int k1 = threadIdx.x / JPmax;
+  float mx = 0.f;  // largest |E/O| of this thread (FP16x3 data scale)
   if (q < JP && k1 < 16) {
     c2<real> x0[N2], x1[N2];
 #pragma unroll
@@ -237,8 +238,11 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
       w1[o + sc] = e.y;
       w1[o + sp] = d.x;
       w1[o + sp + sc] = d.y;
+      if (a.amax) mx = fmaxf(mx, fmaxf(fmaxf(fabsf((float)e.x), fabsf((float)e.y)),
+                                         fmaxf(fabsf((float)d.x), fabsf((float)d.y))));
     }
   }
+  if (a.amax) cta_amax(mx, a.amax + sg.fn0 + b);
 }
 
 // Inverse: G spectra -> samples.  blockDim = 16 * JP.  PAIRS: real and

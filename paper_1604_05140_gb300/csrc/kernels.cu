@@ -117,6 +117,7 @@ struct FftArgs {
   int mode;              // fwd: 0 none, 1 *exp(-t/2), 2 *exp(+t/2);
                          // inv: 0 none, 1 *exp(+t/2), 2 *what*beta, 3 *what*beta*exp(-t/2)
   int64_t pair_limit;    // real functions in pairs: reals in the sample array; 0 complex samples
+  unsigned* amax;        // forward, FP16x3 plans: per-function largest |E/O| (else null)
 };
 
 __host__ __device__ inline int ring_pitch(int n1, int n2) {
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
   // E/O spectra for m in (-B, B): spectral index k = m mod N at slot (k % n1, k / n1)
   real* w1 = reinterpret_cast<real*>(a.w1) + sg.w1_off;
   const int total = (2 * B - 1) * 4 * JP;
+  float mx = 0.f;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int q = e % JP;
     const int rest = e / JP;
@@ -242,7 +244,9 @@ __global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
     const real g1 = plane[(2 * q + 1) * pitch + slot];
     const real v = p ? (g0 - g1) : (g0 + g1);
     w1[(((((int64_t)m_idx * 2 + p) * NB + b) * 2 + c) * NR + i) * B + j0 + q] = v;
+    mx = fmaxf(mx, fabsf((float)v));
   }
+  if (a.amax) cta_amax(mx, a.amax + sg.fn0 + b);
 }
 
 // Inverse: G[m][b][c][i][j] (layout 0) or G[m][b][j][i][c] (layout 1) of
@@ -784,8 +788,9 @@ static cudaError_t run_fft(Plan& P, bool inv, const void* in, void* out, int mod
     a.JP = fft_jp(P, f.B, inv);
     a.mode = mode;
     a.pair_limit = P.real_pairs ? P.n_samples : 0;
+    a.amax = (!inv && P.d_amax) ? P.d_amax + AMAX_EO * P.nfn : nullptr;
     {
-      Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode, a.pair_limit};
+      Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode, a.pair_limit, a.amax};
       cudaError_t e16 = cudaSuccess;
       if (fft16_launch<real>(inv, a16, f.n1, f.n2, f.count, s, &e16)) {
         if (e16 != cudaSuccess) return e16;

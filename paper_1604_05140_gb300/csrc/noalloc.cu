@@ -8,6 +8,15 @@
 // descriptor, offsets, launch schedules) in a second one.  Host code never
 // dereferences either array: it asks the runtime for their device addresses
 // with cudaGetSymbolAddress, once per device, and passes those addresses on.
+//
+// The library is built without relocatable device code, so this file is its
+// own CUDA module.  Under CUDA's lazy module loading (the default) a module
+// is loaded on a device when host code first needs it there: the first
+// cudaGetSymbolAddress below loads this one and reserves both arrays (24 MiB)
+// on that device, and the first launch of each forward kernel loads that
+// kernel's module.  The first call on a device therefore belongs at start-up,
+// before the caller's allocator takes the device's memory (or the process
+// runs with CUDA_MODULE_LOADING=EAGER, which loads every module up front).
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -87,8 +96,10 @@ sgl_status describe(DeviceState& D, int B, int batch) {
   sg.n1 = fft_n1(2 * B);
   sg.n2 = 2 * B / sg.n1;
   sg.fn0 = 0;
+  // offsets of the (only) segment within workspaces 1 and 2; the workspaces
+  // themselves sit back to back in the scratch (d_w1, d_w2 below)
   sg.w1_off = 0;
-  sg.w2_off = w1_size(B, batch, B);
+  sg.w2_off = 0;
   int64_t tab = 0;
   sg.tab_misc = tab;
   tab += misc_size(B, B);
@@ -163,17 +174,21 @@ sgl_status describe(DeviceState& D, int B, int batch) {
   P.d_fft_fwd = (int4*)(c + o_ff);
   P.n_fft_fwd = (int)ff.size();
   P.d_w1 = D.scratch;
-  P.d_w2 = D.scratch + sg.w2_off;
+  P.d_w2 = D.scratch + w1_size(B, batch, B);
   return SGL_OK;
 }
 
-bool device_pointer(const void* p) {
+// True for managed memory and for device memory of device `dev` (the kernels
+// run there, with that device's static arrays; a buffer of another GPU would
+// be reached across devices, or not at all without peer access).
+bool device_pointer(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -190,14 +205,14 @@ extern "C" sgl_status sgl_forward_noalloc(int B, int batch, const void* samples,
     return fail(SGL_ERR_UNSUPPORTED, "B=" + std::to_string(B) + " batch=" + std::to_string(batch) + " needs " +
                                          std::to_string(need) + " scratch doubles; the static scratch holds " +
                                          std::to_string(kScratchDoubles));
-  if (!device_pointer(samples) || !device_pointer(coeffs))
-    return fail(SGL_ERR_ARG, "sgl_forward_noalloc takes device pointers only");
-  if ((uintptr_t)samples % 16 || (uintptr_t)coeffs % 16)
-    return fail(SGL_ERR_ARG, "data pointers must be aligned to the complex element size (16 bytes)");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(SGL_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(SGL_ERR_UNSUPPORTED, "device index too large");
+  if (!device_pointer(samples, dev) || !device_pointer(coeffs, dev))
+    return fail(SGL_ERR_ARG, "sgl_forward_noalloc takes device pointers of the current device only");
+  if ((uintptr_t)samples % 16 || (uintptr_t)coeffs % 16)
+    return fail(SGL_ERR_ARG, "data pointers must be aligned to the complex element size (16 bytes)");
   DeviceState& D = g_dev[dev];
   if (!D.ready) {
     // once per device, with that device current

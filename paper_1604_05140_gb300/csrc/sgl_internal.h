@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -55,9 +56,32 @@ inline bool bandlimit_supported(int B) {
 
 // Plans whose Legendre and radial stages run on the tensor cores, and the
 // number of TF32 products per K step they use (hi*hi [+ hi*lo + lo*hi]).
-inline bool tc_precision(int prec) { return prec == SGL_TF32X3 || prec == SGL_TF32 || prec == SGL_BF16X3; }
+inline bool tc_precision(int prec) {
+  return prec == SGL_TF32X3 || prec == SGL_TF32 || prec == SGL_BF16X3 || prec == SGL_FP16X3;
+}
 inline int tc_products(int prec) { return prec == SGL_TF32 ? 1 : 3; }
-inline bool tc_bf16(int prec) { return prec == SGL_BF16X3; }
+// operand format of the tensor-core stages: TF32 (kind::tf32), or 16-bit
+// hi/lo pairs on the kind::f16 path, BF16 or scaled FP16
+enum TcOperand { TC_OP_TF32 = 0, TC_OP_BF16 = 1, TC_OP_FP16 = 2 };
+inline int tc_operand(int prec) {
+  return prec == SGL_BF16X3 ? TC_OP_BF16 : prec == SGL_FP16X3 ? TC_OP_FP16 : TC_OP_TF32;
+}
+inline bool tc_bf16(int prec) { return tc_operand(prec) != TC_OP_TF32; }  // a 16-bit operand path
+
+// FP16x3 scales.  Data: per function, the largest magnitude of a stage's input
+// (measured, or a measured magnitude times a bound on the growth through a
+// table) as the bits of a non-negative float; slots of Plan::d_amax:
+enum AmaxSlot { AMAX_EO = 0, AMAX_COEF = 1, AMAX_SLOTS = 2 };
+// Power-of-two exponent e that puts a largest magnitude x into [2^13, 2^14)
+// (x * 2^e), so that FP16 hi parts stay below 65504 and small values keep
+// 28 binades of normal range; 0 for x = 0, clamped to +-100.
+inline int fp16_scale_exp(double x) {
+  if (!(x > 0)) return 0;
+  int E = 0;
+  (void)std::frexp(x, &E);  // x = f 2^E, f in [0.5, 1)
+  int e = 14 - E;
+  return e > 100 ? 100 : e < -100 ? -100 : e;
+}
 
 inline int64_t coeff_count(int B) { return (int64_t)B * (B + 1) * (2 * B + 1) / 6; }
 // samples of one function: R radii x 2B x 2B (R = B, or 2B on the paper's grid)
@@ -222,6 +246,10 @@ struct Plan {
   int radi_narrow = 65;
   std::string tuning;
 
+  // FP16x3 plans: per-function largest magnitudes [AMAX_SLOTS][nfn] (segment
+  // order), cleared and measured by every call (the data scales)
+  unsigned* d_amax = nullptr;
+
   // calls with host buffers on single-bandlimit plans run in sub-batches so
   // that the copies overlap the kernels (api.cu): a plan of sub_q functions
   // used for every chunk, one for a shorter last chunk, a copy stream and
@@ -309,7 +337,24 @@ struct Fft16Args {
   // reals in the sample array (the second function of the last pair exists
   // only below this limit)
   int64_t pair_limit;
+  unsigned* amax;        // forward, FP16x3 plans: per-function largest |E/O| (else null)
 };
+// Largest magnitude of a CTA's values, folded into *amax (bits of a
+// non-negative float, compared as integers) with one atomic per CTA; each
+// thread passes the largest |value| it produced.  Every thread of the CTA
+// calls it, with the same amax.
+#ifdef __CUDACC__
+__device__ __forceinline__ void cta_amax(float v, unsigned* amax) {
+  __shared__ unsigned s_amax;
+  if (threadIdx.x == 0) s_amax = 0u;
+  __syncthreads();
+  const unsigned w = __reduce_max_sync(__activemask(), __float_as_uint(v));
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_amax, w);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_amax != 0u) atomicMax(amax, s_amax);
+}
+#endif
+
 // Launches the specialized kernel when (n1, n2) = (16, 8) or (16, 16) and
 // returns true (launch status in *err); returns false otherwise.
 template <typename real>

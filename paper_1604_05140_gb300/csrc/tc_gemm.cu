@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   uint64_t* tabe = tabf + 1;             // table no longer read
   uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  uint64_t* drain = bars + 62;           // [2] MMA issuers' own barriers, used after an abort
   // per-CTA copies of the tile slice, of the segments and of the metadata of
   // the groups the slice touches, so that no role waits on a global load per
   // tile
@@ -180,6 +181,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
     }
     mbar_init(tabf, 1);
     mbar_init(tabe, 2);
+    mbar_init(drain, 1);
+    mbar_init(drain + 1, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -203,6 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
+  uint32_t issued = 0, tables = 0;  // producer: X chunk copies and table copies issued
 
   if (warp == 0) {
     // ---------------- producer ----------------
@@ -240,6 +244,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
           tma_load_2d(xs + s * 2 * kChunkBytes, xmap, full + s, kc * 32, (int)row);
         }
       }
+      issued = c;
+      tables = (uint32_t)ngrp;
     }
   } else if (warp == 1 || warp == kMma2Warp) {
     // ---------------- MMA issuers: K steps of parity `me` ----------------
@@ -439,13 +445,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
     }
   }
 
+  // Every role has left its loop.  After an abort (whichever role gave up,
+  // and when) the producer waits, bounded, for the copies it issued and each
+  // MMA issuer for its MMAs, before shared and tensor memory are released.
   __syncthreads();
   if (*abort_flag) {
     if (threadIdx.x == 0) atomicExch(a.err, 1);
-    // let copies and MMAs already issued drain before the memory is released
-    const uint64_t t0 = gtimer();
-    while (gtimer() - t0 < 20000000ull) {
+    if (warp == 0 && lane == 0) {
+      drain_ring(full, STAGES, issued);
+      if (tables > 0) mbar_drain(tabf, (tables - 1) & 1);
     }
+    if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(drain + (warp == 1 ? 0 : 1));
+    __syncthreads();
   }
   tc_after();
   if (warp == 1) tmem_dealloc(tmem, tmem_cols);

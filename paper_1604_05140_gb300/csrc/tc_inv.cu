@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
   uint64_t* tabe = tabf + 1;
   uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  uint64_t* drain = bars + 62;                  // [2] MMA issuers' own barriers, used after an abort
   // the segments and the tile slice (two records per tile), copied once to
   // shared memory
   LegISegSmall* s_seg = (LegISegSmall*)(bars + 64);
@@ -179,6 +180,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
     }
     mbar_init(tabf, 1);
     mbar_init(tabe, 2);
+    mbar_init(drain, 1);
+    mbar_init(drain + 1, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
+  uint32_t issued = 0, tables = 0;  // producer: staging copies and table copies issued
   // tile t: s_tiles[2t] = (m_idx, row0, half | seg << 8, KC_P | KC_Q << 8),
   //         s_tiles[2t+1] = (table image offset, S row of P, S row of Q, 0);
   // the resident table changes with its image offset
@@ -229,6 +233,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
         }
         if (!ok) break;
       }
+      issued = c;
+      tables = (uint32_t)ngrp;
     }
   } else if (warp == 1 || warp == kMma2Warp) {
     // MMA issuer `me` takes the chunks of parity p = me (P or Q accumulators)
@@ -387,12 +393,18 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
       mbar_arrive(acce + acc);
     }
   }
+  // Every role has left its loop.  After an abort the producer waits,
+  // bounded, for the copies it issued and each MMA issuer for its MMAs,
+  // before shared and tensor memory are released.
   __syncthreads();
   if (*abort_flag) {
     if (threadIdx.x == 0) atomicExch(a.err, 1);
-    const uint64_t t0 = gtimer();
-    while (gtimer() - t0 < 20000000ull) {
+    if (warp == 0 && lane == 0) {
+      drain_ring(stgf, kStagingLegI, issued);
+      if (tables > 0) mbar_drain(tabf, (tables - 1) & 1);
     }
+    if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(drain + (warp == 1 ? 0 : 1));
+    __syncthreads();
   }
   tc_after();
   if (warp == 1) tmem_dealloc(tmem, tmem_cols);
@@ -492,6 +504,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   uint64_t* acce = accf + 2;                // [2] (epilogue threads)
   uint32_t* tmem_slot = (uint32_t*)(acce + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  uint64_t* drain = bars + 62;              // [2] MMA issuers' own barriers, used after an abort
   // the tile slice, the segments it touches (seg_lo ..) and their S row
   // offsets, copied once to shared memory
   const int g_begin = a.cta_first[blockIdx.x];
@@ -528,6 +541,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       mbar_init(accf + k, 2);
       mbar_init(acce + k, kEpiThreads);
     }
+    mbar_init(drain, 1);
+    mbar_init(drain + 1, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -541,6 +556,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
+  uint32_t issued = 0;  // producer: table chunk copies issued
 
   if (warp == 0) {
     if (lane == 0) {
@@ -561,6 +577,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
         }
         if (!ok) break;
       }
+      issued = c;
     }
   } else if (warp == 1 || warp == kMma2Warp) {
     // MMA issuer `me`: narrow tiles, the K steps of parity me into
@@ -773,12 +790,16 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       mbar_arrive(acce + acc);
     }
   }
+  // Every role has left its loop (the gather threads have waited for their
+  // asynchronous copies).  After an abort the producer waits, bounded, for
+  // the table copies it issued and each MMA issuer for its MMAs, before
+  // shared and tensor memory are released.
   __syncthreads();
   if (*abort_flag) {
     if (threadIdx.x == 0) atomicExch(a.err, 1);
-    const uint64_t t0 = gtimer();
-    while (gtimer() - t0 < 20000000ull) {
-    }
+    if (warp == 0 && lane == 0) drain_ring(tfull, kStagesRadI, issued);
+    if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(drain + (warp == 1 ? 0 : 1));
+    __syncthreads();
   }
   tc_after();
   if (warp == 1) tmem_dealloc(tmem, tmem_cols);

@@ -103,6 +103,32 @@ static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
   }
 }
 
+// Bound of each wait while a CTA winds down after an abort.
+constexpr uint64_t kDrainNs = 200000000ull;
+
+// Wait, bounded by limit_ns, for the phase of the given parity without
+// looking at the abort flag (used after an abort, to let operations that were
+// already issued finish).  Returns whether the phase completed.
+static __device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kDrainNs) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_sleep(bar, parity, 100000u))
+    if (gtimer() - t0 > limit_ns) return false;
+  return true;
+}
+
+// After an abort: wait for the last asynchronous copy that landed, or will
+// land, on each barrier of a ring of `stages` barriers, when `issued` copies
+// were issued in all (copy k completes phase k / stages of bars[k % stages]).
+// Returns whether every one of them finished within the bound.
+static __device__ __forceinline__ bool drain_ring(uint64_t* bars, int stages, uint32_t issued) {
+  bool ok = true;
+  for (int s = 0; s < stages && (uint32_t)s < issued; ++s) {
+    const uint32_t last = (uint32_t)s + (uint32_t)stages * ((issued - 1 - (uint32_t)s) / (uint32_t)stages);
+    ok = mbar_drain(bars + s, (last / (uint32_t)stages) & 1) && ok;
+  }
+  return ok;
+}
+
 static __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
@@ -144,6 +170,14 @@ static __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t
 static __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+// After an abort: an MMA-issuing thread commits every MMA it issued to its
+// own barrier (count 1, not used before) and waits, bounded, until they have
+// finished reading shared memory and writing tensor memory.
+static __device__ __forceinline__ bool drain_mma(uint64_t* bar) {
+  mma_commit(bar);
+  return mbar_drain(bar, 0);
 }
 
 static __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {

@@ -17,7 +17,7 @@ from paper_1604_05140_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TF32X3_TOL = 2e-6
+from tolerances import SPLIT_TOL as TF32X3_TOL
 
 
 def _parse(text):

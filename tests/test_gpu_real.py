@@ -10,18 +10,19 @@ sets with that symmetry.  Checked here through the C ABI:
   adjoints  = the adjoint identities for the real inner product on samples
               and Re <u, v> on coefficients;
 and the same numbers through host buffers.  Tolerances as for complex plans:
-FP64 1e-12, FP32 2e-5, TF32x3 2e-6 (normwise per function).
+FP64 1e-12, FP32 2e-5, TF32x3 1e-6 (normwise per function; tests/tolerances.py).
 """
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_1604_05140_gb300 import inputs
+from tolerances import FP32_TOL, FP64_TOL, SPLIT_TOL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 2e-5, "tf32x3": 2e-6}
+TOL = {"fp64": FP64_TOL, "fp32": FP32_TOL, "tf32x3": SPLIT_TOL}
 RTYPE = {"fp64": torch.float64, "fp32": torch.float32, "tf32x3": torch.float32}
 CTYPE = {"fp64": torch.complex128, "fp32": torch.complex64, "tf32x3": torch.complex64}
 
