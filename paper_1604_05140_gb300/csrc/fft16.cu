@@ -1,10 +1,11 @@
-// phi-FFT kernels for ring lengths 2B = 16 * N2 with N2 in {8, 16}
-// (B = 64 and B = 128), the four-step form of the inner sum of
-// Eq. (SFFT_rearranged):
+// phi-FFT kernels for ring lengths 2B = 16 * N2 with 2 <= N2 <= 16 (every
+// bandlimit B = 8 * N2 from 16 to 128), the four-step form of the inner sum
+// of Eq. (SFFT_rearranged):
 //   X[k1 + 16 k2] = sum_{n2} W_N^{n2 k1} W_{N2}^{n2 k2} sum_{n1} x[N2 n1 + n2] W_16^{n1 k1}.
 //
 // Data path: HBM -> registers (16 independent loads per thread) -> 16-point
-// FFT -> one XOR-swizzled shared-memory transpose -> N2-point FFT -> HBM.
+// FFT -> one swizzled shared-memory transpose -> N2-point DFT (radix 2 for
+// powers of two, mixed radix otherwise) -> HBM.
 // A CTA owns one shell (b, i) and JP ring pairs (theta_j, theta_{2B-1-j});
 // the forward kernel emits E = G_j + G_mirror and O = G_j - G_mirror directly
 // from registers, the inverse kernel gathers its spectra from the Legendre
@@ -127,12 +128,83 @@ __device__ __forceinline__ void fft_n(c2<real>* v) {
   stages<real, N, INV, 2>(v);
 }
 
+constexpr bool is_pow2(int n) { return (n & (n - 1)) == 0; }
+// smallest prime factor of n >= 2
+constexpr int smallest_factor(int n) {
+  for (int p = 2; p * p <= n; ++p)
+    if (n % p == 0) return p;
+  return n;
+}
+
+// N-point DFT (INV: the inverse, unscaled) of v in natural order, in place,
+// 2 <= N <= 16.  Powers of two: the radix-2 FFT above.  Other sizes: mixed
+// radix, decimation in time over the smallest prime factor P (P subsequences
+// of stride P, each transformed recursively, then P-point butterflies with
+// twiddles); prime sizes directly.  w[j] = W_NT^j, j < NT, is the root table
+// of the size NT this transform belongs to (N divides NT); every index into it
+// is a compile-time constant once the loops are unrolled, so w stays in
+// registers.
+template <typename real, int N, int NT, bool INV>
+__device__ __forceinline__ void dft_any(c2<real>* v, const c2<real>* w) {
+  if constexpr (is_pow2(N)) {
+    fft_n<real, N, INV>(v);
+  } else {
+    constexpr int P = smallest_factor(N), Q = N / P, WS = NT / N;
+    c2<real> out[N];
+    if constexpr (Q == 1) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        c2<real> acc = v[0];
+#pragma unroll
+        for (int n = 1; n < N; ++n) {
+          if (k == 0) {
+            acc = acc + v[n];
+          } else {
+            c2<real> t = w[((n * k) % N) * WS];
+            if (INV) t.y = -t.y;
+            acc = acc + cmul(v[n], t);
+          }
+        }
+        out[k] = acc;
+      }
+    } else {
+      c2<real> sub[P][Q];
+#pragma unroll
+      for (int r = 0; r < P; ++r) {
+#pragma unroll
+        for (int n = 0; n < Q; ++n) sub[r][n] = v[n * P + r];
+        dft_any<real, Q, NT, INV>(sub[r], w);
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        c2<real> acc = sub[0][k % Q];
+#pragma unroll
+        for (int r = 1; r < P; ++r) {
+          const int e = (r * k) % N;
+          if (e == 0) {
+            acc = acc + sub[r][k % Q];
+          } else {
+            c2<real> t = w[e * WS];
+            if (INV) t.y = -t.y;
+            acc = acc + cmul(sub[r][k % Q], t);
+          }
+        }
+        out[k] = acc;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = out[k];
+  }
+}
+
 // Shared-memory position (complex units) of row `row` (< 16), column `col`
-// (< N2) of ring r: rows of N2 columns, XOR swizzle by row and ring pair so
-// that both the column-wise writes and the row-wise reads are conflict-free.
+// (< N2) of ring r: rows of N2 columns, swizzled by row and ring pair (XOR
+// for powers of two, a rotation otherwise) so that the column-wise writes and
+// the row-wise reads spread over the banks.
 template <int N2>
 __device__ __forceinline__ int spos(int r, int row, int col) {
-  return r * (16 * N2) + row * N2 + ((col ^ row ^ (r >> 1)) & (N2 - 1));
+  if constexpr (is_pow2(N2)) return r * (16 * N2) + row * N2 + ((col ^ row ^ (r >> 1)) & (N2 - 1));
+  else return r * (16 * N2) + row * N2 + (col + row + (r >> 1)) % N2;
 }
 
 }  // namespace
@@ -146,6 +218,7 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);      // [k1 < 16][c < N2]: W_N^{c k1}
   c2<real>* buf = tw + N;                                    // 2*JP rings of N
+  c2<real>* w2s = buf + 2 * a.JP * N;                        // W_N2^j, j < N2
   const int4 cta = a.ctas[blockIdx.x];
   const SegDesc sg = a.segs[cta.x];
   const int B = sg.B, NB = sg.NB, NR = sg.R;  // NR radii
@@ -161,6 +234,8 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
     const int e = (k % N2) * (k / N2);  // < N
     tw[k] = {misc[3 * NR + 2 * B + 2 * e], misc[3 * NR + 2 * B + 2 * e + 1]};
   }
+  for (int k = threadIdx.x; k < N2; k += blockDim.x)  // W_N2^k = W_N^{16 k}
+    w2s[k] = {misc[3 * NR + 2 * B + 32 * k], misc[3 * NR + 2 * B + 32 * k + 1]};
   real scale = 1;
   if (a.mode == 1) scale = misc[NR + i];
   if (a.mode == 2) scale = misc[2 * NR + i];
@@ -171,7 +246,7 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   __syncthreads();
 
   // step A: items (r, n2), n2 fastest; 16-point DFT over n1, twiddle, store
-  constexpr int PER = N2 / 8;  // (2*JP rings x N2 columns) / (16*JP threads)
+  constexpr int PER = (N2 + 7) / 8;  // (2*JP rings x N2 columns) / (16*JP threads), rounded up
   c2<real> v[PER][16];
   int rr[PER], cc[PER];
 #pragma unroll
@@ -213,14 +288,15 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
   const int k1 = threadIdx.x / JPmax;
   float mx = 0.f;  // largest |E/O| of this thread (FP16x3 data scale)
   if (q < JP && k1 < 16) {
-    c2<real> x0[N2], x1[N2];
+    c2<real> x0[N2], x1[N2], w2[N2];
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) {
       x0[n2] = buf[spos<N2>(2 * q, k1, n2)];
       x1[n2] = buf[spos<N2>(2 * q + 1, k1, n2)];
+      if constexpr (!is_pow2(N2)) w2[n2] = w2s[n2];
     }
-    fft_n<real, N2, false>(x0);
-    fft_n<real, N2, false>(x1);
+    dft_any<real, N2, N2, false>(x0, w2);
+    dft_any<real, N2, N2, false>(x1, w2);
     real* w1 = reinterpret_cast<real*>(a.w1) + sg.w1_off;
     const int64_t sp = (int64_t)NB * 2 * NR * B;              // stride of p
     const int64_t sm = 2 * sp;                                // stride of m_idx
@@ -251,7 +327,7 @@ template <typename real, int N2, bool PAIRS>
 __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
   constexpr int N = 16 * N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);
+  c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);    // W_N^k, k < N
   c2<real>* buf = tw + N;
   const int4 cta = a.ctas[blockIdx.x];
   const SegDesc sg = a.segs[cta.x];
@@ -319,8 +395,13 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
         }
       }
     }
-    fft_n<real, N2, true>(x0);
-    fft_n<real, N2, true>(x1);
+    c2<real> w2[N2];  // W_N2^j = W_N^{16 j}
+    if constexpr (!is_pow2(N2)) {
+#pragma unroll
+      for (int j = 0; j < N2; ++j) w2[j] = tw[16 * j];
+    }
+    dft_any<real, N2, N2, true>(x0, w2);
+    dft_any<real, N2, N2, true>(x1, w2);
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) {
       c2<real> w = tw[n2 * k1];
@@ -366,26 +447,60 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
   }
 }
 
-// Launch helper: returns false when (n1, n2) is not handled here.
+// Launch helper: returns false when (n1, n2) is not handled here.  Every
+// 2B = 16 * N2 with 2 <= N2 <= 16 for FP32 complex samples; N2 in {8, 16} for
+// FP64 and for real functions in pairs.
+template <typename real, int N2>
+static void (*pick_fft16(bool inv, bool pairs))(Fft16Args) {
+  if constexpr (N2 == 8 || N2 == 16) {
+    if (pairs) return inv ? fft16_inv_kernel<real, N2, true> : fft16_fwd_kernel<real, N2, true>;
+  }
+  if (pairs) return nullptr;
+  return inv ? fft16_inv_kernel<real, N2, false> : fft16_fwd_kernel<real, N2, false>;
+}
+
 template <typename real>
 bool fft16_launch(bool inv, const Fft16Args& a, int n1, int n2, int nctas, cudaStream_t s, cudaError_t* err) {
-  if (n1 != 16 || (n2 != 16 && n2 != 8)) return false;
-  const int N = 16 * n2;
-  const size_t smem = sizeof(c2<real>) * ((size_t)N + (size_t)2 * a.JP * N);
+  if (n1 != 16 || n2 < 2 || n2 > 16) return false;
+  const bool pairs = a.pair_limit != 0;
   void (*fn)(Fft16Args) = nullptr;
-  if (a.pair_limit) {
-    if (n2 == 16) fn = inv ? fft16_inv_kernel<real, 16, true> : fft16_fwd_kernel<real, 16, true>;
-    else fn = inv ? fft16_inv_kernel<real, 8, true> : fft16_fwd_kernel<real, 8, true>;
-  } else {
-    if (n2 == 16) fn = inv ? fft16_inv_kernel<real, 16, false> : fft16_fwd_kernel<real, 16, false>;
-    else fn = inv ? fft16_inv_kernel<real, 8, false> : fft16_fwd_kernel<real, 8, false>;
+  if (n2 == 16) fn = pick_fft16<real, 16>(inv, pairs);
+  else if (n2 == 8) fn = pick_fft16<real, 8>(inv, pairs);
+  else if constexpr (sizeof(real) == 4) {
+    switch (n2) {
+      case 2: fn = pick_fft16<real, 2>(inv, pairs); break;
+      case 3: fn = pick_fft16<real, 3>(inv, pairs); break;
+      case 4: fn = pick_fft16<real, 4>(inv, pairs); break;
+      case 5: fn = pick_fft16<real, 5>(inv, pairs); break;
+      case 6: fn = pick_fft16<real, 6>(inv, pairs); break;
+      case 7: fn = pick_fft16<real, 7>(inv, pairs); break;
+      case 9: fn = pick_fft16<real, 9>(inv, pairs); break;
+      case 10: fn = pick_fft16<real, 10>(inv, pairs); break;
+      case 11: fn = pick_fft16<real, 11>(inv, pairs); break;
+      case 12: fn = pick_fft16<real, 12>(inv, pairs); break;
+      case 13: fn = pick_fft16<real, 13>(inv, pairs); break;
+      case 14: fn = pick_fft16<real, 14>(inv, pairs); break;
+      case 15: fn = pick_fft16<real, 15>(inv, pairs); break;
+      default: break;
+    }
   }
+  if (!fn) return false;
+  const int N = 16 * n2;
+  const size_t smem = sizeof(c2<real>) * ((size_t)N + (size_t)2 * a.JP * N + (size_t)n2);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     fn<<<nctas, 16 * a.JP, smem, s>>>(a);
     e = cudaGetLastError();
   }
   *err = e;
+  return true;
+}
+
+// Whether fft16_launch takes rings of 2B = n1 * n2 (the plan groups FFT
+// launches by kernel instantiation).
+bool fft16_handles(bool fp64, bool pairs, int n1, int n2) {
+  if (n1 != 16 || n2 < 2 || n2 > 16) return false;
+  if (fp64 || pairs) return n2 == 8 || n2 == 16;
   return true;
 }
 

@@ -749,9 +749,10 @@ static void fft_slices(const Plan& P, std::vector<FftSlice>& out, bool inv) {
     const int JP = fft_jp(P, sg.B, inv);
     const int per_shell = (sg.B + JP - 1) / JP;  // ring-pair groups per shell
     const int count = sg.NB * sg.R * per_shell;   // R shells per function (R = B on the tensor-core path)
-    // kernel class: the register FFT for 2B = 16 * {8, 16}, else the general
-    // kernel of factor n1 with a run-time n2
-    const int cls = (sg.n1 == 16 && (sg.n2 == 8 || sg.n2 == 16)) ? 100 + sg.n2 : sg.n1;
+    // kernel class: the register FFT of 2B = 16 * n2 where it applies (one
+    // instantiation per n2), else the general kernel of factor n1 with a
+    // run-time n2
+    const int cls = fft16_handles(P.prec == SGL_FP64, P.real_pairs, sg.n1, sg.n2) ? 100 + sg.n2 : sg.n1;
     if (!out.empty() && cls == last_cls && JP == last_jp) {
       FftSlice& f = out.back();
       f.count += count;

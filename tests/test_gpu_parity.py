@@ -99,6 +99,19 @@ def test_fp32_vs_oracle(B):
     assert _err(f_gpu, O.forward(g.astype(np.complex64), B)) < FP32_TOL
 
 
+@pytest.mark.parametrize("B", list(range(16, 129, 8)))
+def test_fp32_register_fft_every_size(B):
+    # 2B = 16 N2 with N2 = 2 .. 16: every size of the register phi-FFT (radix
+    # 2 for powers of two, mixed radix otherwise), both directions, against
+    # the oracle
+    p = _plan(B, 1, "fp32")
+    c = inputs.random_coeffs(B, 1, seed=7700 + B)
+    assert _err(p.inverse(_dev(c, torch.complex64)).cpu().numpy(), O.inverse(c, B)) < FP32_TOL
+    g = inputs.random_samples(B, 1, seed=7800 + B)
+    assert _err(p.forward(_dev(g, torch.complex64)).cpu().numpy(), O.forward(g.astype(np.complex64), B)) < FP32_TOL
+    p.check()
+
+
 @pytest.mark.parametrize("B", [5, 12])
 def test_fp64_adjoints_vs_oracle(B):
     p = _plan(B, 2, "fp64")
