@@ -296,6 +296,26 @@ const char* sgl_tuning(sgl_plan_t plan);
  */
 sgl_status sgl_selftest_wait(int64_t limit_ns, int* gave_up);
 
+/*
+ * sgl_set_graphs - run the plan's calls through CUDA graphs of its own (an
+ * implementation aid; the paper has no counterpart).  While enabled, every
+ * sgl_forward, sgl_inverse and sgl_adjoint call with device buffers replays a
+ * graph of that call's launches on the caller's stream: one launch in place
+ * of the plan's (up to 34 for uneven bandlimits).  The graph of a call kind
+ * (direction, weights) and buffer pair is captured on its first call, on a
+ * stream of the plan (nothing runs during the capture; the replay follows on
+ * the caller's stream), and kept: at most 8 per plan, the least recently used
+ * one dropped first, so callers that reuse their buffers capture once.  Calls
+ * with host buffers, calls while stage profiling is on, and calls on a stream
+ * that is itself being captured launch directly as before.  sgl_autotune and
+ * sgl_set_dlt drop the plan's graphs (their launches change); so does
+ * disabling.  Results are those of the direct launches, bit for bit.
+ */
+sgl_status sgl_set_graphs(sgl_plan_t plan, int enable);
+
+/* Number of graphs the plan holds (0 .. 8); -1 for a NULL plan. */
+int sgl_graph_count(sgl_plan_t plan);
+
 /* Message for the last failure on `plan`; with NULL, for the last failed
  * plan creation or plan-free call (sgl_forward_noalloc, sgl_midpoint) on the
  * calling thread.  The string stays valid until the next call on the same

@@ -60,11 +60,20 @@ static void clear_profile(Plan& P) {
 
 static void release_pipeline(Plan* P);
 
+// Destroys the plan's captured graphs (their launches no longer match the
+// plan's schedules, or graphs were switched off).
+static void drop_graphs(Plan& P) {
+  for (Plan::GraphEntry& g : P.graphs) cudaGraphExecDestroy(g.exec);
+  P.graphs.clear();
+}
+
 static void release(Plan* P) {
   if (!P) return;
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(P->device);
+  drop_graphs(*P);
+  if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
   release_pipeline(P);
   clear_profile(*P);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
@@ -72,7 +81,7 @@ static void release(Plan* P) {
   if (!P->owns_err) P->d_err = nullptr;
   void* ptrs[] = {P->d_tab, P->d_tab_lo, P->d_w1, P->d_w2, P->d_stage_in, P->d_stage_out, P->d_segs,
                   P->d_fn_samp, P->d_fn_coef, P->d_si_rows, P->d_err, P->d_fft_fwd, P->d_fft_inv, P->d_ccoef,
-                  P->d_dct_ctas};
+                  P->d_dct_ctas, P->d_amax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (GemmSched* g : {&P->leg_fwd, &P->rad_fwd, &P->rad_inv, &P->leg_inv})
@@ -180,7 +189,7 @@ static void set_launch_count(Plan& P) {
   int fwd = fft_launches(P, false), inv = fft_launches(P, true);
   if (tc_precision(P.prec)) {
     fwd += 2;
-    inv += 2;
+    inv += 2 + (tc_operand(P.prec) == TC_OP_FP16 ? 1 : 0);  // FP16x3: the coefficients' magnitudes
   } else {
     fwd += P.leg_fwd.launches() + P.rad_fwd.launches() + (P.seminaive ? (int)P.segs.size() : 0);
     inv += P.rad_inv.launches() + P.leg_inv.launches();
@@ -228,6 +237,54 @@ static cudaError_t build_fft_lists(Plan& P) {
   }
   P.n_fft_inv = (int)ff.size();
   return dev_upload(P, &P.d_fft_inv, ff);
+}
+
+// SIMT GEMM tile lists of every stage (0 LEG_F, 1 RAD_F, 2 RAD_I, 3 LEG_I)
+// for the plan's tile-family policy of that stage (Plan::simt_policy):
+//   0  whole blocks of 64 columns, the rest in the narrowest shape that holds
+//      it (the default: least padding);
+//   1  64 x 64 tiles only (fewest tiles);
+//   2  blocks of 32 columns (128 x 32 tiles), a rest of <= 16 in 256 x 16.
+// Replaces the previous lists.
+static cudaError_t build_simt_lists(Plan& P) {
+  std::vector<int4> lists[4][kGemmShapes];
+  auto add = [&](int stage, int s, int g, int rows, int ncols) {
+    const int pol = P.simt_policy[stage];
+    for (int c0 = 0; c0 < ncols;) {
+      const int rest = ncols - c0;
+      const int w = pol == 1 ? 0 : pol == 2 ? (rest <= 16 ? 2 : 1) : gemm_shape_of(rest);
+      const int tm = gemm_shape_rows(w), tn = gemm_shape_cols(w);
+      for (int r0 = 0; r0 < rows; r0 += tm) lists[stage][w].push_back(make_int4(s, g, r0, c0));
+      c0 += tn;
+    }
+  };
+  for (size_t s = 0; s < P.segs.size(); ++s) {
+    const SegDesc& sg = P.segs[s];
+    const int B = sg.B, NB = sg.NB, R = sg.R;
+    for (int g = 0; g < 2 * (2 * B - 1); ++g) {
+      const int m = (g >> 1) - (B - 1);
+      add(0, (int)s, g, NB * 2 * R, n_par(B, m < 0 ? -m : m, g & 1));
+    }
+    for (int l = 0; l < B; ++l) {
+      const int rows = NB * (2 * l + 1) * 2;
+      add(1, (int)s, l, rows, B - l);
+      add(2, (int)s, l, rows, R);
+    }
+    for (int mi = 0; mi < 2 * B - 1; ++mi) add(3, (int)s, mi, NB * 2 * R, B);
+  }
+  GemmSched* scheds[4] = {&P.leg_fwd, &P.rad_fwd, &P.rad_inv, &P.leg_inv};
+  for (int st = 0; st < 4; ++st)
+    for (int w = 0; w < kGemmShapes; ++w) {
+      if (scheds[st]->d_tiles[w]) {
+        cudaFree(scheds[st]->d_tiles[w]);
+        P.bytes -= (int64_t)scheds[st]->ntiles[w] * sizeof(int4);
+        scheds[st]->d_tiles[w] = nullptr;
+      }
+      scheds[st]->ntiles[w] = (int)lists[st][w].size();
+      const cudaError_t e = dev_upload(P, &scheds[st]->d_tiles[w], lists[st][w]);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
 }
 
 static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) {
@@ -328,42 +385,16 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
   e = cudaMalloc((void**)&P->d_err, sizeof(int));
   if (e != cudaSuccess) return fail(P, SGL_ERR_ALLOC, "allocation failed");
   cudaMemset(P->d_err, 0, sizeof(int));
+  if (tc_operand(P->prec) == TC_OP_FP16) {  // per-function largest magnitudes (data scales)
+    const size_t n = (size_t)AMAX_SLOTS * P->nfn * sizeof(unsigned);
+    e = cudaMalloc((void**)&P->d_amax, n);
+    if (e != cudaSuccess) return fail(P, SGL_ERR_ALLOC, "allocation failed");
+    P->bytes += n;
+  }
 
   // SIMT GEMM schedules
-  int TM, TN, TK;
-  gemm_tile_dims(TM, TN, TK);
-  // tiles of every stage (0 LEG_F, 1 RAD_F, 2 RAD_I, 3 LEG_I): whole blocks of
-  // 64 columns, then the group's remaining columns in the narrowest shape that
-  // holds them
-  std::vector<int4> lists[4][kGemmShapes];
-  auto add = [&](int stage, int s, int g, int rows, int ncols) {
-    for (int c0 = 0; c0 < ncols;) {
-      const int w = gemm_shape_of(ncols - c0), tm = gemm_shape_rows(w), tn = gemm_shape_cols(w);
-      for (int r0 = 0; r0 < rows; r0 += tm) lists[stage][w].push_back(make_int4(s, g, r0, c0));
-      c0 += tn;
-    }
-  };
-  for (size_t s = 0; s < P->segs.size(); ++s) {
-    const SegDesc& sg = P->segs[s];
-    const int B = sg.B, NB = sg.NB, R = sg.R;
-    for (int g = 0; g < 2 * (2 * B - 1); ++g) {
-      const int m = (g >> 1) - (B - 1);
-      add(0, (int)s, g, NB * 2 * R, n_par(B, m < 0 ? -m : m, g & 1));
-    }
-    for (int l = 0; l < B; ++l) {
-      const int rows = NB * (2 * l + 1) * 2;
-      add(1, (int)s, l, rows, B - l);
-      add(2, (int)s, l, rows, R);
-    }
-    for (int mi = 0; mi < 2 * B - 1; ++mi) add(3, (int)s, mi, NB * 2 * R, B);
-  }
-  GemmSched* scheds[4] = {&P->leg_fwd, &P->rad_fwd, &P->rad_inv, &P->leg_inv};
-  for (int st = 0; st < 4; ++st)
-    for (int w = 0; w < kGemmShapes; ++w) {
-      scheds[st]->ntiles[w] = (int)lists[st][w].size();
-      e = dev_upload(*P, &scheds[st]->d_tiles[w], lists[st][w]);
-      if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
-    }
+  e = build_simt_lists(*P);
+  if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
   e = build_fft_lists(*P);
   if (e != cudaSuccess) return cuda_fail(P, e, "schedule upload");
   for (const SegDesc& sg : P->segs) {
@@ -532,6 +563,53 @@ static sgl_status execute_pipelined(Plan* P, bool is_fwd, bool weights, const vo
   return SGL_OK;
 }
 
+// Runs the call through the plan's graph for (kind, in, out): replays it on
+// s, or first captures the call's launches on the plan's own stream (nothing
+// runs during the capture) and instantiates it.
+static cudaError_t run_graph(Plan& P, bool is_fwd, bool weights, const void* in, void* out, cudaStream_t s) {
+  const int kind = (is_fwd ? 2 : 0) | (weights ? 1 : 0);
+  for (Plan::GraphEntry& g : P.graphs)
+    if (g.kind == kind && g.in == in && g.out == out) {
+      g.used = ++P.graph_clock;
+      return cudaGraphLaunch(g.exec, s);
+    }
+  cudaError_t e = cudaSuccess;
+  if (!P.graph_stream) e = cudaStreamCreateWithFlags(&P.graph_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCapture(P.graph_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t er = is_fwd ? run_forward(P, in, out, P.graph_stream, weights)
+                                : run_inverse(P, in, out, P.graph_stream, weights);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(P.graph_stream, &graph);  // always ends the capture
+  if (er != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return er != cudaSuccess ? er : e;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return e;
+  if (P.graphs.size() >= Plan::kMaxGraphs) {
+    size_t lru = 0;
+    for (size_t k = 1; k < P.graphs.size(); ++k)
+      if (P.graphs[k].used < P.graphs[lru].used) lru = k;
+    cudaGraphExecDestroy(P.graphs[lru].exec);
+    P.graphs.erase(P.graphs.begin() + (long)lru);
+  }
+  P.graphs.push_back({kind, in, out, exec, ++P.graph_clock});
+  return cudaGraphLaunch(exec, s);
+}
+
+static bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;  // unknown: do not start a capture of our own
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
 // Runs fwd (is_fwd) or inv with in/out that may be host or device memory.
 static sgl_status execute(Plan* P, bool is_fwd, bool weights, const void* in, void* out, sgl_stream_t stream) {
   if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
@@ -554,6 +632,11 @@ static sgl_status execute(Plan* P, bool is_fwd, bool weights, const void* in, vo
   void* dout = out;
   sgl_status st = SGL_OK;
   cudaError_t e = cudaSuccess;
+  if (in_dev && out_dev && P->use_graphs && !P->profiling && !stream_capturing(s)) {
+    e = run_graph(*P, is_fwd, weights, in, out, s);
+    if (e != cudaSuccess) st = cuda_fail(P, e, "graph launch");
+    goto done;
+  }
   if ((!in_dev || !out_dev) && P->uniform && !P->real_pairs && P->nfn >= kPipeMinFunctions) {
     st = execute_pipelined(P, is_fwd, weights, in, out, in_dev, out_dev, s);
     goto done;
@@ -589,9 +672,10 @@ done:
 // autotuning (sgl_autotune)
 // ---------------------------------------------------------------------------
 static std::string tuning_text(const Plan& P, const char* source) {
-  char buf[192];
-  snprintf(buf, sizeof buf, "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d source=%s", fft_jp(P, P.maxB, false),
-           fft_jp(P, P.maxB, true), P.radi_narrow, source);
+  char buf[256];
+  snprintf(buf, sizeof buf, "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d source=%s",
+           fft_jp(P, P.maxB, false), fft_jp(P, P.maxB, true), P.radi_narrow, P.simt_policy[0], P.simt_policy[1],
+           P.simt_policy[2], P.simt_policy[3], P.rad_rows, source);
   return buf;
 }
 
@@ -640,12 +724,19 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
       while (fgets(line, sizeof line, f)) {
         const std::string ln(line);
         if (ln.compare(0, key.size() + 3, key + " | ") != 0) continue;
-        int jf = 0, ji = 0, rn = 0;
-        if (sscanf(ln.c_str() + key.size() + 3, "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d", &jf, &ji, &rn) == 3 &&
-            jf >= 1 && jf <= 16 && ji >= 1 && ji <= 16 && rn >= 1) {
+        int jf = 0, ji = 0, rn = 0, sp[4] = {0, 0, 0, 0}, rr = 64;
+        const int got = sscanf(ln.c_str() + key.size() + 3,
+                               "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d", &jf, &ji,
+                               &rn, &sp[0], &sp[1], &sp[2], &sp[3], &rr);
+        bool valid = (got == 3 || got == 8) && jf >= 1 && jf <= 16 && ji >= 1 && ji <= 16 && rn >= 1;
+        for (int k = 0; k < 4; ++k) valid = valid && sp[k] >= 0 && sp[k] <= 2;
+        valid = valid && (rr == 32 || rr == 48 || rr == 64);
+        if (valid) {
           P->jp_fwd = jf;
           P->jp_inv = ji;
           P->radi_narrow = rn;
+          for (int k = 0; k < 4; ++k) P->simt_policy[k] = sp[k];
+          P->rad_rows = rr;
           cached = true;
         }
       }
@@ -691,19 +782,60 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
         }
       }
       P->radi_narrow = best;
+      // tile width of the forward radial stage: the table group height
+      int best_rr = 64;
+      tbest = 1e30;
+      for (int rr : {64, 48, 32}) {
+        P->rad_rows = rr;
+        tc_release(*P);
+        e = tc_prepare(*P);
+        if (e != cudaSuccess) return cuda_fail(P, e, "autotune tensor-core preparation");
+        const double t = time_calls(*P, true, samples, coeffs, s);
+        if (t < 0.0) return cuda_fail(P, cudaGetLastError(), "autotune launch");
+        if (t < tbest) {
+          tbest = t;
+          best_rr = rr;
+        }
+      }
+      P->rad_rows = best_rr;
+    } else {
+      // SIMT tile family of each GEMM stage, one stage at a time (forward
+      // stages timed on forward calls, inverse stages on inverse calls)
+      for (int st = 0; st < 4; ++st) {
+        int best = 0;
+        double tbest = 1e30;
+        for (int pol = 0; pol < 3; ++pol) {
+          P->simt_policy[st] = pol;
+          e = build_simt_lists(*P);
+          if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+          const double t = time_calls(*P, st < 2, samples, coeffs, s);
+          if (t < 0.0) return cuda_fail(P, cudaGetLastError(), "autotune launch");
+          if (t < tbest) {
+            tbest = t;
+            best = pol;
+          }
+        }
+        P->simt_policy[st] = best;
+      }
     }
   }
   e = build_fft_lists(*P);
-  if (e == cudaSuccess && tc_precision(P->prec)) e = tc_radi_retile(*P);
+  if (e == cudaSuccess) e = build_simt_lists(*P);
+  if (e == cudaSuccess && tc_precision(P->prec)) {
+    tc_release(*P);
+    e = tc_prepare(*P);  // for the chosen radial tile width (and inverse radial policy)
+  }
   if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
   set_launch_count(*P);
   P->tuning = tuning_text(*P, cached ? "cache" : "timed");
   release_pipeline(P);  // sub-batch plans are rebuilt with the new configuration on next use
+  drop_graphs(*P);      // and graphs are captured again
   if (!cached && cache_path) {
     FILE* f = fopen(cache_path, "a");
     if (!f) return fail(P, SGL_ERR_ARG, std::string("cannot append to tuning cache ") + cache_path);
-    fprintf(f, "%s | fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d\n", key.c_str(), P->jp_fwd, P->jp_inv,
-            P->radi_narrow);
+    fprintf(f, "%s | fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d\n", key.c_str(),
+            P->jp_fwd, P->jp_inv, P->radi_narrow, P->simt_policy[0], P->simt_policy[1], P->simt_policy[2],
+            P->simt_policy[3], P->rad_rows);
     fclose(f);
   }
   return SGL_OK;
@@ -720,7 +852,7 @@ sgl_status sgl_plan_grid(sgl_plan_t* out, int B, int batch, int prec, int sample
   *out = nullptr;
   if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
   if (batch < 1) return fail(nullptr, SGL_ERR_ARG, "batch must be >= 1");
-  if (prec < SGL_FP64 || prec > SGL_BF16X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
+  if (prec < SGL_FP64 || prec > SGL_FP16X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
   if (samples != SGL_SAMPLES_WEIGHTED && samples != SGL_SAMPLES_PHYSICAL && samples != SGL_SAMPLES_REAL)
     return fail(nullptr, SGL_ERR_ARG, "unknown sample convention");
   if (samples == SGL_SAMPLES_PHYSICAL && prec != SGL_FP64)
@@ -765,7 +897,7 @@ sgl_status sgl_plan_many(sgl_plan_t* out, const int* B_per_fn, int nfn, int prec
   if (!out) return fail(nullptr, SGL_ERR_ARG, "null output pointer");
   *out = nullptr;
   if (!B_per_fn || nfn < 1) return fail(nullptr, SGL_ERR_ARG, "need at least one function");
-  if (prec < SGL_FP64 || prec > SGL_BF16X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
+  if (prec < SGL_FP64 || prec > SGL_FP16X3) return fail(nullptr, SGL_ERR_ARG, "unknown precision");
   std::vector<int> Bs(B_per_fn, B_per_fn + nfn);
   for (int B : Bs) {
     if (B < 1) return fail(nullptr, SGL_ERR_ARG, "bandlimit must be >= 1");
@@ -874,6 +1006,20 @@ sgl_status sgl_check(sgl_plan_t plan, sgl_stream_t stream) {
   return (sgl_status)P->latched;
 }
 
+sgl_status sgl_set_graphs(sgl_plan_t plan, int enable) {
+  Plan* P = (Plan*)plan;
+  if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != P->device) cudaSetDevice(P->device);
+  P->use_graphs = enable != 0;
+  if (!P->use_graphs) drop_graphs(*P);
+  if (cur != P->device) cudaSetDevice(cur);
+  return SGL_OK;
+}
+
+int sgl_graph_count(sgl_plan_t plan) { return plan ? (int)((Plan*)plan)->graphs.size() : -1; }
+
 sgl_status sgl_set_profiling(sgl_plan_t plan, int enable) {
   Plan* P = (Plan*)plan;
   if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
@@ -916,6 +1062,7 @@ sgl_status sgl_set_dlt(sgl_plan_t plan, int seminaive) {
   cudaGetDevice(&cur);
   if (cur != P->device) cudaSetDevice(P->device);
   release_pipeline(P);  // sub-batch plans are rebuilt with the setting on next use
+  drop_graphs(*P);
   const sgl_status st = set_dlt(P, seminaive != 0);
   if (cur != P->device) cudaSetDevice(cur);
   return st;

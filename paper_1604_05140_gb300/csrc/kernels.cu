@@ -852,11 +852,49 @@ static cudaError_t run_dct(Plan& P, bool weights, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// FP16x3 plans: the largest |coefficient| (real and imaginary parts) of
+// every function, folded into amax[f] (segment order; cleared beforehand).
+// blockIdx.x: slices of one function's coefficients, blockIdx.y: functions
+// (strided beyond gridDim.y).
+__global__ void __launch_bounds__(256) coef_amax_kernel(const cx<float>* coef, const SegDesc* segs, int nseg,
+                                                        const int64_t* fn_coef, int nfn, unsigned* amax) {
+  for (int f = blockIdx.y; f < nfn; f += gridDim.y) {
+    int B = 0;
+    for (int s = 0; s < nseg; ++s)
+      if (f >= segs[s].fn0 && f < segs[s].fn0 + segs[s].NB) B = segs[s].B;
+    const int64_t n = (int64_t)B * (B + 1) * (2 * B + 1) / 6;
+    const cx<float>* c = coef + fn_coef[f];
+    float mx = 0.f;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+      const cx<float> v = c[k];
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    cta_amax(mx, amax + f);
+  }
+}
+
+// FP16x3 data scales of a call: clear the slot, and for the inverse measure
+// the coefficients (the forward phi-FFT measures its own output).
+static cudaError_t fp16_scales(Plan& P, bool inv, const void* coeffs, cudaStream_t s) {
+  if (!P.d_amax) return cudaSuccess;
+  unsigned* slot = P.d_amax + (inv ? AMAX_COEF : AMAX_EO) * P.nfn;
+  cudaError_t e = cudaMemsetAsync(slot, 0, (size_t)P.nfn * sizeof(unsigned), s);
+  if (e != cudaSuccess || !inv) return e;
+  const int64_t om = coeff_count(P.maxB);
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (om + 4095) / 4096)),
+                  (unsigned)std::min(P.nfn, 65535));
+  coef_amax_kernel<<<grid, 256, 0, s>>>((const cx<float>*)coeffs, P.d_segs, (int)P.segs.size(), P.d_fn_coef,
+                                        P.nfn, slot);
+  return cudaGetLastError();
+}
+
 template <typename real>
 static cudaError_t forward_t(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights) {
   int mode = 0;
   if (P.samples == SGL_SAMPLES_PHYSICAL) mode = weights ? 1 : 2;
-  cudaError_t e = run_fft<real>(P, false, samples, nullptr, mode, s);
+  cudaError_t e = fp16_scales(P, false, nullptr, s);
+  if (e != cudaSuccess) return e;
+  e = run_fft<real>(P, false, samples, nullptr, mode, s);
   if (e != cudaSuccess) return e;
   if (tc_precision(P.prec)) {
     e = run_tc_stage(P, LEG_F, P.d_w1, P.d_w2, weights, s);
@@ -880,6 +918,8 @@ template <typename real>
 static cudaError_t inverse_t(Plan& P, const void* coeffs, void* samples, cudaStream_t s, bool weights) {
   cudaError_t e;
   if (tc_precision(P.prec)) {
+    e = fp16_scales(P, true, coeffs, s);
+    if (e != cudaSuccess) return e;
     e = run_tc_stage(P, RAD_I, coeffs, P.d_w2, 0, s);
     if (e != cudaSuccess) return e;
     e = run_tc_stage(P, LEG_I, P.d_w2, P.d_w1, 0, s);

@@ -236,6 +236,7 @@ struct Plan {
   int n_fft_fwd = 0, n_fft_inv = 0;
   int launches_per_call = 0;
   void* tc_state = nullptr;      // tensor-core forward stage state (tc_gemm.cu)
+  int64_t tc_bytes = 0;          // device bytes of the tensor-core state (both directions)
   void* tc_inv_state = nullptr;  // tensor-core inverse stage state (tc_inv.cu)
 
   // launch configuration chosen by sgl_autotune: ring pairs per CTA of the
@@ -244,6 +245,12 @@ struct Plan {
   // with two K chains (smaller counts get 128-column tiles)
   int jp_fwd = 0, jp_inv = 0;
   int radi_narrow = 65;
+  // tile shapes chosen by sgl_autotune: the SIMT tile family of each GEMM
+  // stage (0 LEG_F, 1 RAD_F, 2 RAD_I, 3 LEG_I; see build_simt_lists in
+  // api.cu), and the rows n' of the largest table group of the tensor-core
+  // forward radial stage (its MMA tile width; 32, 48 or 64)
+  int simt_policy[4] = {0, 0, 0, 0};
+  int rad_rows = 64;
   std::string tuning;
 
   // FP16x3 plans: per-function largest magnitudes [AMAX_SLOTS][nfn] (segment
@@ -280,6 +287,23 @@ struct Plan {
   bool seminaive = false;
   int4* d_dct_ctas = nullptr;
   int n_dct = 0;
+
+  // CUDA graphs of the plan's own calls (sgl_set_graphs): one per call kind
+  // (direction, weights) and device buffer pair, captured on first use on a
+  // plan-owned stream and replayed on the caller's stream; the least recently
+  // used one is dropped beyond kMaxGraphs
+  struct GraphEntry {
+    int kind;
+    const void* in;
+    void* out;
+    cudaGraphExec_t exec;
+    uint64_t used;
+  };
+  static constexpr size_t kMaxGraphs = 8;
+  bool use_graphs = false;
+  cudaStream_t graph_stream = nullptr;
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
 
   std::string err;
   int latched = SGL_OK;
@@ -355,10 +379,12 @@ __device__ __forceinline__ void cta_amax(float v, unsigned* amax) {
 }
 #endif
 
-// Launches the specialized kernel when (n1, n2) = (16, 8) or (16, 16) and
+// Launches the register FFT when it takes 2B = n1 * n2 (fft16_handles) and
 // returns true (launch status in *err); returns false otherwise.
 template <typename real>
 bool fft16_launch(bool inv, const Fft16Args& a, int n1, int n2, int nctas, cudaStream_t s, cudaError_t* err);
+// Whether the register FFT takes rings of 2B = n1 * n2 (fft16.cu).
+bool fft16_handles(bool fp64, bool pairs, int n1, int n2);
 
 // Packs the host tables of every segment of P into one array of the plan's
 // real type, at the offsets recorded in the segment descriptors (api.cu).

@@ -30,6 +30,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 #include <vector>
 
@@ -80,7 +81,6 @@ enum { TC_LEG_F = 0, TC_RAD_F = 1 };
 // than 64 terms are cut into two groups), which leaves room for 4 stages
 constexpr int kStagesLeg = 4;
 constexpr int kStagesRad = 4;
-constexpr int kRadRows = 64;  // largest radial group (rows n' of the table)
 constexpr int kChunkBytes = 128 * 128;  // 128 rows x 32 floats
 constexpr int kThreads = tcx::kRoleThreads;
 
@@ -94,13 +94,17 @@ struct TcSegInfo {
   int B, NB, KC, fn0;           // bandlimit, functions, K chunks, first function in fn_coef
   int64_t w2_off;               // the segment's S_f block (forward Legendre output)
   int g0;                       // the segment's first group in the launch's group list
+  float bw, bp;                 // FP16x3, radial stage: bound on |S_f| / largest |E/O|
+                                // (weighted and plain Legendre tables)
 };
 
 // per-segment values the roles read per tile, staged in shared memory
 struct SegSmall {
   int B, NB, KC, fn0;
   int64_t w2_off;
-  int g0, pad;
+  int g0;
+  float bw, bp;
+  int pad;
 };
 
 struct TcArgs {
@@ -120,12 +124,19 @@ struct TcArgs {
   int weighted;
   int npmax;
   int nprod;                    // TF32 products per K step: 3 (hi*hi + hi*lo + lo*hi) or 1 (hi*hi)
+  const int* grp_exp;           // FP16x3: table scale exponent of each group image (as grp_off)
+  const unsigned* amax;         // FP16x3: per-function largest |E/O| (segment order)
+  int rad_rows;                 // radial stage: rows n' of the largest table group (tile width)
 };
 
-// BF: BF16 hi/lo operands (kind::f16, 64-byte rows, K = 16 per MMA) instead
-// of TF32 (kind::tf32, 128-byte rows, K = 8 per MMA).
-template <int PROB, int STAGES, bool BF>
+// OP: the operand format (TcOperand).  TF32: kind::tf32, 128-byte rows, K = 8
+// per MMA.  BF16 and FP16 hi/lo pairs: kind::f16, 64-byte rows, K = 16 per
+// MMA; FP16 values are scaled by powers of two (tables per group image on the
+// host, data per function here) and the epilogue takes the scales out.
+template <int PROB, int STAGES, int OP>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
+  constexpr bool BF = OP != TC_OP_TF32;  // a 16-bit operand path
+  constexpr bool F16 = OP == TC_OP_FP16;
   constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -143,6 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   uint64_t* drain = bars + 62;           // [2] MMA issuers' own barriers, used after an abort
+  uint32_t* issued = (uint32_t*)(bars + 61);  // producer: [copies issued into the ring, table copies]
   // per-CTA copies of the tile slice, of the segments and of the metadata of
   // the groups the slice touches, so that no role waits on a global load per
   // tile
@@ -154,7 +166,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   SegSmall* s_seg = (SegSmall*)(bars + 64);                // [nseg]
   int64_t* s_off = (int64_t*)(s_seg + a.nseg);              // [ngr] table image offsets
   int* s_npad = (int*)(s_off + ngr);                        // [ngr] padded N (| l, n0 for radial)
-  int4* s_tiles = (int4*)(((uintptr_t)(s_npad + ngr) + 15) & ~(uintptr_t)15);  // [slice] (group, row0, segment)
+  int* s_exp = s_npad + ngr;                                 // [ngr] FP16x3 table exponents
+  int4* s_tiles = (int4*)(((uintptr_t)(s_exp + ngr) + 15) & ~(uintptr_t)15);  // [slice] (group, row0, segment)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Per tile two pairs of a main accumulator (hi*hi) and a correction
@@ -183,6 +196,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
     mbar_init(tabe, 2);
     mbar_init(drain, 1);
     mbar_init(drain + 1, 1);
+    issued[0] = issued[1] = 0u;
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -197,16 +211,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   for (int k = threadIdx.x; k < ngr; k += blockDim.x) {
     s_off[k] = a.grp_off[wsel + g_lo + k];
     s_npad[k] = a.grp_npad[g_lo + k];
+    s_exp[k] = F16 ? a.grp_exp[wsel + g_lo + k] : 0;
   }
   for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) {
     const TcSegInfo& g = a.segs[k];
-    s_seg[k] = SegSmall{g.B, g.NB, g.KC, g.fn0, g.w2_off, g.g0, 0};
+    s_seg[k] = SegSmall{g.B, g.NB, g.KC, g.fn0, g.w2_off, g.g0, g.bw, g.bp, 0};
   }
   tc_before();
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t issued = 0, tables = 0;  // producer: X chunk copies and table copies issued
 
   if (warp == 0) {
     // ---------------- producer ----------------
@@ -244,8 +258,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
           tma_load_2d(xs + s * 2 * kChunkBytes, xmap, full + s, kc * 32, (int)row);
         }
       }
-      issued = c;
-      tables = (uint32_t)ngrp;
+      issued[0] = c;
+      issued[1] = (uint32_t)ngrp;
     }
   } else if (warp == 1 || warp == kMma2Warp) {
     // ---------------- MMA issuers: K steps of parity `me` ----------------
@@ -266,8 +280,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
           ++ngrp;
         }
         const int npad = s_npad[tl.x] & 0xff;
-        const uint32_t idesc2 = BF ? idesc_bf16(2 * npad) : idesc_tf32(2 * npad);
-        const uint32_t idesc1 = BF ? idesc_bf16(npad) : idesc_tf32(npad);
+        const uint32_t idesc2 = F16 ? idesc_f16(2 * npad) : BF ? idesc_bf16(2 * npad) : idesc_tf32(2 * npad);
+        const uint32_t idesc1 = F16 ? idesc_f16(npad) : BF ? idesc_bf16(npad) : idesc_tf32(npad);
         const int acc = tcount & 1;
         if (!mbar_wait(acce + acc, ((tcount >> 1) & 1) ^ 1, abort_flag)) break;
         tc_after();
@@ -284,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
           const uint64_t xl = xh + (uint64_t)((BF ? kChunkBytes / 2 : kChunkBytes) >> 4);
           const uint64_t tb = tdesc0 + (uint64_t)((kc * 2 * npad * ROWB) >> 4) + 2 * me;
           const uint32_t first = kc > 0 ? 1u : 0u;
-          if (BF) {  // K = 16 per MMA: one K step of the chunk per issuer
+          if (BF) {  // kind::f16, K = 16 per MMA: one K step of the chunk per issuer
             mma_bf16(dm, xh, tb, idesc2, first);
             mma_bf16(dc, xl, tb, idesc1, 1u);
           } else if (a.nprod == 3) {
@@ -307,44 +321,77 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   } else if (warp < kFirstEpiWarp) {
     // ---------------- split: X -> (hi, lo) ----------------
     const int tid = threadIdx.x - 32 * kFirstSplitWarp;  // 0 .. kSplitThreads-1
+    constexpr int kPer = kChunkBytes / 16 / kSplitThreads;  // 16-byte pieces of a chunk per thread
+    // FP16x3: largest magnitudes of the functions of this thread's rows of
+    // tile tt (~0u past the stage's rows)
+    unsigned amx[kPer];
+    auto split_amax_load = [&](int tt, unsigned* out) {
+      const int4 tl = s_tiles[tt];
+      const SegSmall sg = s_seg[tl.z];
+      const int per_f = PROB == TC_LEG_F ? 2 * sg.B : (2 * ((s_npad[tl.x] >> 8) & 0xff) + 1) * 2;
+#pragma unroll
+      for (int v = 0; v < kPer; ++v) {
+        const int grow = tl.y + ((v * kSplitThreads + tid) >> 3);
+        out[v] = grow < sg.NB * per_f ? a.amax[sg.fn0 + grow / per_f] : ~0u;
+      }
+    };
+    (void)split_amax_load;
     uint32_t c = 0;
     for (int t = t_begin; t < t_end; ++t) {
       bool ok = true;
       const int KC = s_seg[s_tiles[t].z].KC;
+      // FP16x3: the data scale 2^e of each row this thread splits (row r =
+      // piece index / 8), from the largest magnitude of the row's function
+      // (times the growth bound through the Legendre table for the radial
+      // stage); rows past the stage's rows are zeroed.  The magnitudes are
+      // loaded a tile ahead.
+      float xf[kPer];
+      if constexpr (F16) {
+        const SegSmall sg = s_seg[s_tiles[t].z];
+        const float bound = PROB == TC_LEG_F ? 1.f : (a.weighted ? sg.bw : sg.bp);
+        if (t == t_begin) split_amax_load(t, amx);
+#pragma unroll
+        for (int v = 0; v < kPer; ++v) xf[v] = amx[v] == ~0u ? 0.f : pow2f(fp16_data_exp(amx[v], bound));
+        if (t + 1 < t_end) split_amax_load(t + 1, amx);
+      }
       for (int kc = 0; kc < KC; ++kc, ++c) {
         const int s = c % STAGES;
         if (!mbar_wait(full + s, (c / STAGES) & 1, abort_flag)) { ok = false; break; }
         float4* hi = (float4*)(xs + s * 2 * kChunkBytes);
         float4* lo = (float4*)(xs + s * 2 * kChunkBytes + kChunkBytes);
-        if (BF) {
-          // raw chunk (128-byte rows, 32 floats) -> BF16 hi/lo rows of 64 bytes
+        if constexpr (BF) {
+          // raw chunk (128-byte rows, 32 floats) -> 16-bit hi/lo rows of 64 bytes
           unsigned char* ob = xs + s * 2 * kChunkBytes + kChunkBytes;
 #pragma unroll
-          for (int v = 0; v < kChunkBytes / 16 / kSplitThreads; ++v) {
+          for (int v = 0; v < kPer; ++v) {
             const int idx = v * kSplitThreads + tid;
             const int r = idx >> 3, q = (idx & 7) ^ (r & 7);  // values 4q .. 4q+3 of row r
             const float4 x = hi[idx];
-            const uint32_t s0 = bf16_split(x.x), s1 = bf16_split(x.y), s2 = bf16_split(x.z), s3 = bf16_split(x.w);
-            const uint2 h2 = {(s0 & 0xFFFFu) | (s1 << 16), (s2 & 0xFFFFu) | (s3 << 16)};
-            const uint2 l2 = {(s0 >> 16) | (s1 & 0xFFFF0000u), (s2 >> 16) | (s3 & 0xFFFF0000u)};
+            uint2 h2, l2;
+            if constexpr (F16) {
+              fp16_split2(x.x, x.y, xf[v], h2.x, l2.x);
+              fp16_split2(x.z, x.w, xf[v], h2.y, l2.y);
+            } else {
+              const uint32_t s0 = bf16_split(x.x), s1 = bf16_split(x.y), s2 = bf16_split(x.z), s3 = bf16_split(x.w);
+              h2 = {(s0 & 0xFFFFu) | (s1 << 16), (s2 & 0xFFFFu) | (s3 << 16)};
+              l2 = {(s0 >> 16) | (s1 & 0xFFFF0000u), (s2 >> 16) | (s3 & 0xFFFF0000u)};
+            }
             const int off = sw64_off(r, q >> 1) + (q & 1) * 8;
             *(uint2*)(ob + off) = h2;
             *(uint2*)(ob + kChunkBytes / 2 + off) = l2;
           }
-          fence_proxy_async();
-          mbar_arrive(split + s);
-          continue;
-        }
+        } else {
 #pragma unroll
-        for (int v = 0; v < kChunkBytes / 16 / kSplitThreads; ++v) {
-          const int idx = v * kSplitThreads + tid;
-          float4 x = hi[idx];
-          float4 h = {tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w)};
-          hi[idx] = h;
-          if (a.nprod == 3) {
-            // lo rounded to TF32 too, so that the tensor core uses it unchanged
-            float4 l = {tf32_rna(x.x - h.x), tf32_rna(x.y - h.y), tf32_rna(x.z - h.z), tf32_rna(x.w - h.w)};
-            lo[idx] = l;
+          for (int v = 0; v < kPer; ++v) {
+            const int idx = v * kSplitThreads + tid;
+            float4 x = hi[idx];
+            float4 h = {tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w)};
+            hi[idx] = h;
+            if (a.nprod == 3) {
+              // lo rounded to TF32 too, so that the tensor core uses it unchanged
+              float4 l = {tf32_rna(x.x - h.x), tf32_rna(x.y - h.y), tf32_rna(x.z - h.z), tf32_rna(x.w - h.w)};
+              lo[idx] = l;
+            }
           }
         }
         fence_proxy_async();
@@ -364,6 +411,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
       const SegSmall sg = s_seg[tl.z];
       const int B = sg.B, NB = sg.NB;
       const int acc = tcount & 1;
+      // FP16x3: the magnitude of this row's function, loaded before the wait
+      unsigned amx_row = 0u;
+      if constexpr (F16) {
+        const int per_f = PROB == TC_LEG_F ? 2 * B : (2 * ((s_npad[tl.x] >> 8) & 0xff) + 1) * 2;
+        const int gr = tl.y + r_in;
+        if (gr < NB * per_f) amx_row = a.amax[sg.fn0 + gr / per_f];
+      }
       if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
       tc_after();
       const int npad = s_npad[tl.x] & 0xff;
@@ -380,6 +434,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
         const bool valid = grow < NB * 2 * B;
         const int b = grow / (2 * B), cc = (grow / B) & 1, i = grow % B;
         const int64_t rbase = sg.w2_off + (int64_t)cc * B + i;
+        // FP16x3: take out the table's and the row's data scale
+        const float unscale = F16 && valid ? pow2f(-s_exp[tl.x]) * pow2f(-fp16_data_exp(amx_row, 1.f)) : 1.f;
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
           const uint32_t tc = taddr + (uint32_t)c0;
@@ -390,6 +446,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
             tmem_ld16x2(tc, tc + 2 * np, v, w);
 #pragma unroll
             for (int k = 0; k < 16; ++k) v[k] += w[k];
+          }
+          if constexpr (F16) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] *= unscale;
           }
           if (valid) {
             // S_f[l][b][m+l][c][i] = 2B (NB l^2 + b(2l+1) + m + l) + c B + i, stepped in
@@ -414,8 +474,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
         const int b = grow / per_b;
         const int rem = grow - b * per_b;
         const int mm = rem >> 1, cc = rem & 1;
-        const int ncol = min(B - l - n0, kRadRows);
+        const int ncol = min(B - l - n0, a.rad_rows);
         const int64_t cbase = valid ? a.fn_coef[sg.fn0 + b] : 0;
+        const float unscale =
+            F16 && valid ? pow2f(-s_exp[tl.x]) * pow2f(-fp16_data_exp(amx_row, a.weighted ? sg.bw : sg.bp)) : 1.f;
         for (int c0 = 16 * ehalf; c0 < npad; c0 += 32) {
           float v[16];
           const uint32_t tc = taddr + (uint32_t)c0;
@@ -426,6 +488,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
             tmem_ld16x2(tc, tc + 2 * np, v, w);
 #pragma unroll
             for (int k = 0; k < 16; ++k) v[k] += w[k];
+          }
+          if constexpr (F16) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] *= unscale;
           }
           if (valid) {
             // omega(n + 1, l, m) - omega(n, l, m) = n^2
@@ -452,10 +518,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   if (*abort_flag) {
     if (threadIdx.x == 0) atomicExch(a.err, 1);
     if (warp == 0 && lane == 0) {
-      drain_ring(full, STAGES, issued);
-      if (tables > 0) mbar_drain(tabf, (tables - 1) & 1);
+      const uint32_t* cnt = (const uint32_t*)(bars + 61);
+      drain_ring(full, STAGES, cnt[0]);
+      if (cnt[1] > 0) mbar_drain(tabf, (cnt[1] - 1) & 1);
     }
-    if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(drain + (warp == 1 ? 0 : 1));
+    if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(bars + 62 + (warp == 1 ? 0 : 1));
     __syncthreads();
   }
   tc_after();
@@ -475,6 +542,7 @@ struct TcStage {
   int ntiles = 0;
   int64_t* d_off = nullptr;
   int* d_npad = nullptr;
+  int* d_exp = nullptr;
   int ngroups = 0;
   TcSegInfo* d_segs = nullptr;
   int nseg = 0;
@@ -557,22 +625,71 @@ void append_image_bf16(std::vector<unsigned char>& img, int N, int K, int npad, 
     }
 }
 
+// FP16 image of the same table, scaled by 2^e (e = fp16_scale_exp of its
+// largest magnitude, returned): hi = RN(v 2^e), lo = RN(v 2^e - hi), laid out
+// as the BF16 image.
+int append_image_f16(std::vector<unsigned char>& img, int N, int K, int npad, int KC,
+                     const std::vector<double>& A /* N x K */) {
+  double mx = 0.0;
+  for (double v : A) mx = std::max(mx, std::fabs(v));
+  const int e = fp16_scale_exp(mx);
+  const size_t off = img.size();
+  const size_t plane = (size_t)npad * 64;
+  img.resize(off + 2 * (size_t)KC * plane, 0);
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k) {
+      const double v = std::ldexp(A[(size_t)n * K + k], e);
+      const __half h = __float2half_rn((float)v);
+      const __half l = __float2half_rn((float)(v - (double)__half2float(h)));
+      const uint16_t hb = __half_as_ushort(h), lb = __half_as_ushort(l);
+      const int kc = k / 32, kin = k % 32;
+      const int q = kin / 8, w = kin % 8;
+      const size_t pos = (size_t)kc * 2 * plane + (size_t)n * 64 + (size_t)((q ^ ((n >> 1) & 3)) * 16) + w * 2;
+      memcpy(&img[off + pos], &hb, 2);
+      memcpy(&img[off + plane + pos], &lb, 2);
+    }
+  return e;
+}
+
+// Appends table A's image in the plan's operand format; returns the FP16
+// scale exponent (0 for the other formats).
+int append_table(std::vector<unsigned char>& img, int op, int N, int K, int npad, int KC,
+                 const std::vector<double>& A) {
+  if (op == TC_OP_FP16) return append_image_f16(img, N, K, npad, KC, A);
+  if (op == TC_OP_BF16) append_image_bf16(img, N, K, npad, KC, A);
+  else append_image(img, N, K, npad, KC, A);
+  return 0;
+}
+
 int pad16(int n) { return n <= 16 ? 16 : (n + 15) / 16 * 16; }
 
 }  // namespace
 
+static cudaError_t tc_prepare_impl(Plan& P);
+
+// Builds the tensor-core state of both directions and records its device
+// bytes, so that tc_release can take them off the plan's count again.
 cudaError_t tc_prepare(Plan& P) {
+  const int64_t before = P.bytes;
+  const cudaError_t e = tc_prepare_impl(P);
+  P.tc_bytes = P.bytes - before;
+  return e;
+}
+
+static cudaError_t tc_prepare_impl(Plan& P) {
   if (!get_encode()) return cudaErrorNotSupported;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   TcState* st = new TcState();
   const bool bf = tc_bf16(P.prec);
+  const int op = tc_operand(P.prec);
   std::vector<unsigned char> img;
   // group lists of both stages over all segments: image offsets (weighted
   // set, plain set), padded widths, tiles and their estimated cost
   struct Pending {
     std::vector<int64_t> off[2];
+    std::vector<int> exp[2];   // FP16 scale exponents, as off
     std::vector<int> npad;
     std::vector<int2> tiles;   // (group | segment << 20, row0)
     std::vector<double> cost;  // estimated bytes moved per tile (slice balancing)
@@ -593,8 +710,13 @@ cudaError_t tc_prepare(Plan& P) {
       delete st;
       return cudaErrorInvalidValue;
     }
+    // bound on |S_f| / max |E/O| for the FP16x3 radial stage: the largest
+    // absolute row sum of the (weighted, plain) Legendre table over the folded
+    // grid, since S_f[l] = sum_j' A[l][j'] X[j']
+    double rowsum[2] = {0.0, 0.0};
     for (int w = 0; w < 2; ++w) {
       std::vector<int64_t> am_off(2 * B, 0);
+      std::vector<int> am_exp(2 * B, 0);
       for (int am = 0; am < B; ++am)
         for (int p = 0; p < 2; ++p) {
           const int N = n_par(B, am, p);
@@ -603,20 +725,28 @@ cudaError_t tc_prepare(Plan& P) {
           std::vector<double> A((size_t)N * B);
           for (int q = 0; q < N; ++q) {
             const int l = am + p + 2 * q;
+            double rs = 0.0;
             for (int j = 0; j < B; ++j) {
               const double v = H.lam[((size_t)am * B + l) * B + j];
               A[(size_t)q * B + j] = w == 0 ? H.beta[j] * v : v;
+              rs += std::fabs(A[(size_t)q * B + j]);
             }
+            rowsum[w] = std::max(rowsum[w], rs);
           }
           img.resize((img.size() + 1023) / 1024 * 1024);
           am_off[am * 2 + p] = (int64_t)img.size();
-          (bf ? append_image_bf16 : append_image)(img, N, B, np, KC, A);
+          am_exp[am * 2 + p] = append_table(img, op, N, B, np, KC, A);
         }
       for (int mi = 0; mi < 2 * B - 1; ++mi) {
         const int am = mi < B - 1 ? B - 1 - mi : mi - (B - 1);
-        for (int p = 0; p < 2; ++p) pl.off[w].push_back(am_off[am * 2 + p]);
+        for (int p = 0; p < 2; ++p) {
+          pl.off[w].push_back(am_off[am * 2 + p]);
+          pl.exp[w].push_back(am_exp[am * 2 + p]);
+        }
       }
     }
+    li.bw = (float)rowsum[0];
+    li.bp = (float)rowsum[1];
     for (int mi = 0; mi < 2 * B - 1; ++mi) {
       const int am = mi < B - 1 ? B - 1 - mi : mi - (B - 1);
       for (int p = 0; p < 2; ++p) {
@@ -633,8 +763,8 @@ cudaError_t tc_prepare(Plan& P) {
       }
     }
     pl.segs.push_back(li);
-    // radial: groups (l, n0); degrees with more than kRadRows terms n' are cut
-    // into the rows n' < kRadRows and the rest
+    // radial: groups (l, n0); degrees with more than P.rad_rows terms n' are
+    // cut into groups of P.rad_rows rows n' (the tuned tile width) and the rest
     TcSegInfo ri = li;
     ri.g0 = (int)pr.npad.size();
     if (!make_xmap(&ri.xmap, w2, B, (int64_t)2 * NB * B * B)) {
@@ -643,11 +773,11 @@ cudaError_t tc_prepare(Plan& P) {
     }
     std::vector<int2> rgrp;  // (l, n0)
     for (int l = 0; l < B; ++l)
-      for (int n0 = 0; n0 < B - l; n0 += kRadRows) rgrp.push_back(make_int2(l, n0));
+      for (int n0 = 0; n0 < B - l; n0 += P.rad_rows) rgrp.push_back(make_int2(l, n0));
     for (int w = 0; w < 2; ++w)
       for (size_t g = 0; g < rgrp.size(); ++g) {
         const int l = rgrp[g].x, n0 = rgrp[g].y;
-        const int N = std::min(B - l - n0, kRadRows);
+        const int N = std::min(B - l - n0, P.rad_rows);
         const int np = pad16(N);
         std::vector<double> A((size_t)N * B);
         for (int q = 0; q < N; ++q)
@@ -661,11 +791,11 @@ cudaError_t tc_prepare(Plan& P) {
           pr.npad.push_back(np | (l << 8) | (n0 << 16));
           st->rad.npmax = std::max(st->rad.npmax, np);
         }
-        (bf ? append_image_bf16 : append_image)(img, N, B, np, KC, A);
+        pr.exp[w].push_back(append_table(img, op, N, B, np, KC, A));
       }
     for (size_t g = 0; g < rgrp.size(); ++g) {
       const int l = rgrp[g].x, n0 = rgrp[g].y;
-      const int N = std::min(B - l - n0, kRadRows);
+      const int N = std::min(B - l - n0, P.rad_rows);
       for (int r0 = 0; r0 < NB * (2 * l + 1) * 2; r0 += 128) {
         pr.tiles.push_back(make_int2((ri.g0 + (int)g) | ((int)s << 20), r0));
         pr.cost.push_back(KC * 16384.0 + 512.0 * N + (r0 == 0 ? 256.0 * KC * pad16(N) : 0.0));
@@ -697,8 +827,11 @@ cudaError_t tc_prepare(Plan& P) {
     S.nseg = (int)pd.segs.size();
     std::vector<int64_t> off = pd.off[0];
     off.insert(off.end(), pd.off[1].begin(), pd.off[1].end());
+    std::vector<int> ex = pd.exp[0];
+    ex.insert(ex.end(), pd.exp[1].begin(), pd.exp[1].end());
     e = upload(&S.d_tiles, pd.tiles);
     if (e == cudaSuccess) e = upload(&S.d_off, off);
+    if (e == cudaSuccess) e = upload(&S.d_exp, ex);
     if (e == cudaSuccess) e = upload(&S.d_npad, pd.npad);
     if (e == cudaSuccess) e = upload(&S.d_segs, pd.segs);
     // tables, X ring, 64 barrier/flag slots, segments, group metadata of the
@@ -707,7 +840,7 @@ cudaError_t tc_prepare(Plan& P) {
     const int stages = k == 0 ? kStagesLeg : kStagesRad;
     const size_t fixed = 1024 + (size_t)2 * S.KCmax * S.npmax * (bf ? 64 : 128) + (size_t)stages * 2 * kChunkBytes +
                          64 * 8 + (size_t)S.nseg * sizeof(SegSmall) + 16 + 12 + 16;
-    const size_t per_tile = 12 + 16;
+    const size_t per_tile = 16 + 16;
     S.grid = S.ntiles < nsm ? S.ntiles : nsm;
     int max_tiles = 0;
     std::vector<int> first = balance_slices(pd.cost, S.grid > 0 ? S.grid : 1, &max_tiles);
@@ -725,11 +858,13 @@ cudaError_t tc_prepare(Plan& P) {
 }
 
 void tc_release(Plan& P) {
+  P.bytes -= P.tc_bytes;
+  P.tc_bytes = 0;
   tc_inv_release(P);
   TcState* st = (TcState*)P.tc_state;
   if (!st) return;
   for (TcStage* S : {&st->leg, &st->rad}) {
-    void* ptrs[] = {S->d_tiles, S->d_first, S->d_off, S->d_npad, S->d_segs};
+    void* ptrs[] = {S->d_tiles, S->d_first, S->d_off, S->d_npad, S->d_exp, S->d_segs};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
@@ -763,12 +898,24 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
     a.weighted = weighted;
     a.npmax = S.npmax;
     a.nprod = tc_products(P.prec);
+    a.grp_exp = S.d_exp;
+    a.rad_rows = P.rad_rows;
+    a.amax = P.d_amax ? P.d_amax + AMAX_EO * P.nfn : nullptr;
     (void)x;
     void (*fn)(TcArgs);
-    if (tc_bf16(P.prec))
-      fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, true> : tc_gemm_kernel<TC_RAD_F, kStagesRad, true>;
-    else
-      fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, false> : tc_gemm_kernel<TC_RAD_F, kStagesRad, false>;
+    switch (tc_operand(P.prec)) {
+      case TC_OP_FP16:
+        fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, TC_OP_FP16>
+                       : tc_gemm_kernel<TC_RAD_F, kStagesRad, TC_OP_FP16>;
+        break;
+      case TC_OP_BF16:
+        fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, TC_OP_BF16>
+                       : tc_gemm_kernel<TC_RAD_F, kStagesRad, TC_OP_BF16>;
+        break;
+      default:
+        fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, TC_OP_TF32>
+                       : tc_gemm_kernel<TC_RAD_F, kStagesRad, TC_OP_TF32>;
+    }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem);
     if (e != cudaSuccess) return e;
     fn<<<S.grid, kThreads, S.smem, s>>>(a);

@@ -22,6 +22,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "sgl_internal.h"
@@ -68,19 +70,25 @@ __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo
   }
 }
 
-// BF16 form: 4*NQ consecutive K values of one row (NQ even) as BF16 hi/lo
-// pairs, at 16-byte chunks q0/2 .. q0/2 + NQ/2 - 1 of 64-byte rows.
-template <int NQ>
+// 16-bit form: 4*NQ consecutive K values of one row (NQ even) as BF16 hi/lo
+// pairs, or (F16) FP16 pairs of the values times the power of two f, at
+// 16-byte chunks q0/2 .. q0/2 + NQ/2 - 1 of 64-byte rows.
+template <int NQ, bool F16>
 __device__ __forceinline__ void split_store_bf(unsigned char* hi, unsigned char* lo, int row, const float* v,
-                                               int q0) {
+                                               int q0, float f) {
 #pragma unroll
   for (int j = 0; j < NQ / 2; ++j) {
     uint32_t hw[4], lw[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const uint32_t a = bf16_split(v[8 * j + 2 * e]), b = bf16_split(v[8 * j + 2 * e + 1]);
-      hw[e] = (a & 0xFFFFu) | (b << 16);
-      lw[e] = (a >> 16) | (b & 0xFFFF0000u);
+      const float x0 = v[8 * j + 2 * e], x1 = v[8 * j + 2 * e + 1];
+      if constexpr (F16) {
+        fp16_split2(x0, x1, f, hw[e], lw[e]);
+      } else {
+        const uint32_t a = bf16_split(x0), b = bf16_split(x1);
+        hw[e] = (a & 0xFFFFu) | (b << 16);
+        lw[e] = (a >> 16) | (b & 0xFFFF0000u);
+      }
     }
     const int off = sw64_off(row, q0 / 2 + j);
     *(uint4*)(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -106,11 +114,15 @@ __device__ __forceinline__ void split_store_bf(unsigned char* hi, unsigned char*
 // plan.  Aligned as its tensor map.
 struct LegISeg {
   CUtensorMap smap;           // the segment's S: [B^2 rows of l'][NB*2*B]
-  int B, NB, npad, pad;
+  int B, NB, npad, fn0;       // bandlimit, functions, padded j' count, first function
+  float sb;                   // FP16x3: bound on |S| / largest |coefficient| (radial table)
+  int pad;
   int64_t w1_off;             // the segment's G block
 };
 struct LegISegSmall {
-  int B, NB, npad, pad;
+  int B, NB, npad, fn0;
+  float sb;
+  int pad;
   int64_t w1_off;
 };
 
@@ -128,11 +140,17 @@ struct LegIArgs {
   int* err;
   int npad_max, kcmax;        // over the segments
   int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
+  const unsigned* amax;       // FP16x3: per-function largest |coefficient| (segment order)
 };
 
-// BF: BF16 hi/lo operands (kind::f16, 64-byte rows, K = 16 per MMA).
-template <bool BF>
+// OP: the operand format (TcOperand): TF32, or BF16 / scaled FP16 hi/lo pairs
+// (kind::f16, 64-byte rows, K = 16 per MMA).  FP16 tables are scaled per image
+// (exponent in the tile record), S per function (the coefficients' largest
+// magnitude times the radial table's growth bound).
+template <int OP>
 __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) {
+  constexpr bool BF = OP != TC_OP_TF32;
+  constexpr bool F16 = OP == TC_OP_FP16;
   constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -153,13 +171,14 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
   uint32_t* tmem_slot = (uint32_t*)(tabe + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   uint64_t* drain = bars + 62;                  // [2] MMA issuers' own barriers, used after an abort
+  uint32_t* issued = (uint32_t*)(bars + 61);  // producer: [copies issued into the ring, table copies]
   // the segments and the tile slice (two records per tile), copied once to
   // shared memory
   LegISegSmall* s_seg = (LegISegSmall*)(bars + 64);
   int4* s_tiles = (int4*)(((uintptr_t)(s_seg + a.nseg) + 15) & ~(uintptr_t)15);
   for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) {
     const LegISeg& g = a.segs[k];
-    s_seg[k] = LegISegSmall{g.B, g.NB, g.npad, 0, g.w1_off};
+    s_seg[k] = LegISegSmall{g.B, g.NB, g.npad, g.fn0, g.sb, 0, g.w1_off};
   }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -182,6 +201,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
     mbar_init(tabe, 2);
     mbar_init(drain, 1);
     mbar_init(drain + 1, 1);
+    issued[0] = issued[1] = 0u;
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -193,7 +213,6 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t issued = 0, tables = 0;  // producer: staging copies and table copies issued
   // tile t: s_tiles[2t] = (m_idx, row0, half | seg << 8, KC_P | KC_Q << 8),
   //         s_tiles[2t+1] = (table image offset, S row of P, S row of Q, 0);
   // the resident table changes with its image offset
@@ -233,8 +252,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
         }
         if (!ok) break;
       }
-      issued = c;
-      tables = (uint32_t)ngrp;
+      issued[0] = c;
+      issued[1] = (uint32_t)ngrp;
     }
   } else if (warp == 1 || warp == kMma2Warp) {
     // MMA issuer `me` takes the chunks of parity p = me (P or Q accumulators)
@@ -251,8 +270,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
         const int4 ta = s_tiles[2 * t], tb = s_tiles[2 * t + 1];
         const int nh = min(s_seg[ta.z >> 8].npad, 64);
         const int chunk_tab = nh * ROWB;
-        const uint32_t idesc2 = BF ? idesc_bf16(2 * nh) : idesc_tf32(2 * nh);
-        const uint32_t idesc1 = BF ? idesc_bf16(nh) : idesc_tf32(nh);
+        const uint32_t idesc2 = F16 ? idesc_f16(2 * nh) : BF ? idesc_bf16(2 * nh) : idesc_tf32(2 * nh);
+        const uint32_t idesc1 = F16 ? idesc_f16(nh) : BF ? idesc_bf16(nh) : idesc_tf32(nh);
         const int kcp = ta.w & 0xff, kcq = ta.w >> 8;
         if (tb.x != cur) {
           if (!mbar_wait(tabf, ngrp & 1, abort_flag)) break;
@@ -314,11 +333,28 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
     // the 16 values l' = 16h .. 16h+15 of row r
     const int tid = threadIdx.x - 32 * kFirstSplitWarp;
     const int r = tid & 127, h = tid >> 7;
+    // FP16x3: largest magnitude of the function of row r of tile tt (~0u past
+    // the rows), loaded a tile ahead
+    auto row_amax = [&](int tt) -> unsigned {
+      const int4 ta = s_tiles[2 * tt];
+      const LegISegSmall sg = s_seg[ta.z >> 8];
+      const int grow = ta.y + r;
+      return grow < sg.NB * 2 * sg.B ? a.amax[sg.fn0 + grow / (2 * sg.B)] : ~0u;
+    };
+    unsigned amx = 0u;
+    if (F16 && nt > 0) amx = row_amax(0);
     uint32_t c = 0;
     for (int t = 0; t < nt; ++t) {
       const int kcw = s_tiles[2 * t].w;
       const int kcp = kcw & 0xff, kcq = kcw >> 8;
       bool ok = true;
+      // FP16x3: data scale of row r (its function's), zero past the rows
+      float xf = 0.f;
+      if constexpr (F16) {
+        const float sb = s_seg[s_tiles[2 * t].z >> 8].sb;
+        xf = amx == ~0u ? 0.f : pow2f(fp16_data_exp(amx, sb));
+        if (t + 1 < nt) amx = row_amax(t + 1);
+      }
       for (int ch = 0; ch < kcp + kcq; ++ch, ++c) {
         const int st = c % kStagingLegI;
         if (!mbar_wait(stgf + st, (c / kStagingLegI) & 1, abort_flag)) { ok = false; break; }
@@ -329,7 +365,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
         mbar_arrive(stge + st);
         const int s = c % kStagesLegI;
         if (!mbar_wait(empty + s, ((c / kStagesLegI) & 1) ^ 1, abort_flag)) { ok = false; break; }
-        if (BF) split_store_bf<4>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h);
+        if constexpr (BF) split_store_bf<4, F16>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h, xf);
         else split_store<4>(xs + s * 2 * kChunk, xs + s * 2 * kChunk + kChunk, r, v, 4 * h, a.nprod == 3);
         fence_proxy_async();
         mbar_arrive(split + s);
@@ -344,6 +380,13 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
     for (int t = 0; t < nt; ++t, ++tcount) {
       const int4 ta = s_tiles[2 * t];
       const int acc = tcount & 1;
+      // FP16x3: the magnitude of this row's function, loaded before the wait
+      unsigned amx_row = 0u;
+      if constexpr (F16) {
+        const LegISegSmall sq = s_seg[ta.z >> 8];
+        const int gr = ta.y + r_in;
+        if (gr < sq.NB * 2 * sq.B) amx_row = a.amax[sq.fn0 + gr / (2 * sq.B)];
+      }
       if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
       tc_after();
       const LegISegSmall sg = s_seg[ta.z >> 8];
@@ -360,6 +403,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
       const int grow = ta.y + r_in;
       const bool valid = grow < NB * 2 * B;
       const int b = grow / (2 * B), ic = grow - b * (2 * B);
+      // FP16x3: take out the table image's scale (tile record) and the row's data scale
+      const float unscale = F16 && valid ? pow2f(-s_tiles[2 * t + 1].w) * pow2f(-fp16_data_exp(amx_row, sg.sb)) : 1.f;
       float* out = a.g + sg.w1_off + ((int64_t)m_idx * NB + b) * (2 * B) * (2 * B) + ic;
       const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
       const uint32_t dP = tmem + (uint32_t)(4 * acc * nhm) + lanes;
@@ -378,6 +423,13 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
         if (!kcq)
 #pragma unroll
           for (int k = 0; k < 16; ++k) Q[k] = 0.f;
+        if constexpr (F16) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            P[k] *= unscale;
+            Q[k] *= unscale;
+          }
+        }
         if (valid) {
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
@@ -400,10 +452,11 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
   if (*abort_flag) {
     if (threadIdx.x == 0) atomicExch(a.err, 1);
     if (warp == 0 && lane == 0) {
-      drain_ring(stgf, kStagingLegI, issued);
-      if (tables > 0) mbar_drain(tabf, (tables - 1) & 1);
+      const uint32_t* cnt = (const uint32_t*)(bars + 61);
+      drain_ring(stgf, kStagingLegI, cnt[0]);
+      if (cnt[1] > 0) mbar_drain(tabf, (cnt[1] - 1) & 1);
     }
-    if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(drain + (warp == 1 ? 0 : 1));
+    if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(bars + 62 + (warp == 1 ? 0 : 1));
     __syncthreads();
   }
   tc_after();
@@ -424,6 +477,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
 struct RadISeg {
   int B, NB, fn0, si0;        // bandlimit, functions, first function, first S row entry in si_rows
   int64_t w2_off;             // the segment's S block
+  int lb;                     // the segment's first entry in the per-degree table arrays (texp)
+  int pad;
 };
 
 struct RadIArgs {
@@ -440,6 +495,8 @@ struct RadIArgs {
   int* err;
   int si_max;                 // shared-memory entries for the S row offsets of one CTA's segments
   int nprod;                  // TF32 products per K step: 3 or 1 (hi*hi)
+  const int* texp;            // FP16x3: table scale exponent per (segment, l) (RadISeg::lb + l)
+  const unsigned* amax;       // FP16x3: per-function largest |coefficient| (segment order)
 };
 
 // Function of split thread tid's column (b, m, c) in tile tl (fn0 + b), or
@@ -485,8 +542,10 @@ __device__ __forceinline__ void rad_gather_async(const RadIArgs& a, const RadISe
   }
 }
 
-template <bool BF>
+template <int OP>
 __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) {
+  constexpr bool BF = OP != TC_OP_TF32;  // 16-bit hi/lo pairs (kind::f16)
+  constexpr bool F16 = OP == TC_OP_FP16;
   constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
   constexpr int TCH = 128 * ROWB;      // one table chunk (hi or lo): 128 rows i
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -505,6 +564,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   uint32_t* tmem_slot = (uint32_t*)(acce + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   uint64_t* drain = bars + 62;              // [2] MMA issuers' own barriers, used after an abort
+  uint32_t* issued = (uint32_t*)(bars + 61);  // producer: [copies issued into the ring, table copies]
   // the tile slice, the segments it touches (seg_lo ..) and their S row
   // offsets, copied once to shared memory
   const int g_begin = a.cta_first[blockIdx.x];
@@ -543,6 +603,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     }
     mbar_init(drain, 1);
     mbar_init(drain + 1, 1);
+    issued[0] = issued[1] = 0u;
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -556,7 +617,6 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t issued = 0;  // producer: table chunk copies issued
 
   if (warp == 0) {
     if (lane == 0) {
@@ -577,7 +637,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
         }
         if (!ok) break;
       }
-      issued = c;
+      issued[0] = c;
     }
   } else if (warp == 1 || warp == kMma2Warp) {
     // MMA issuer `me`: narrow tiles, the K steps of parity me into
@@ -588,8 +648,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       const uint64_t sdesc0 = BF ? sw64_desc(smem_u32(st)) : sw128_desc(smem_u32(st));
       // B operand of each half: 64 hi rows over 64 lo rows.  One MMA of width
       // 128 gives [T_hi X_hi | T_hi X_lo], a second of width 64 adds T_lo X_hi.
-      const uint32_t idesc2 = BF ? idesc_bf16(128) : idesc_tf32(128);
-      const uint32_t idesc1 = BF ? idesc_bf16(64) : idesc_tf32(64);
+      const uint32_t idesc2 = F16 ? idesc_f16(128) : BF ? idesc_bf16(128) : idesc_tf32(128);
+      const uint32_t idesc1 = F16 ? idesc_f16(64) : BF ? idesc_bf16(64) : idesc_tf32(64);
       for (int t = 0; t < nt && !*abort_flag; ++t, ++tcount) {
         const int4 tl = s_tiles[t];
         const int l = tl.x;
@@ -691,9 +751,24 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
 #pragma unroll
     for (int d = 0; d < kGatherDepth; ++d) issue_next();
     int t = 0, kc = 0;
+    // FP16x3: data scale of this thread's column (its function's), from the
+    // magnitude loaded a tile ahead (~0u past the columns)
+    auto col_amax = [&](int tt) -> unsigned {
+      const int f = rad_fn_of(s_seg[s_tiles[tt].z], s_tiles[tt], tid);
+      return f >= 0 ? a.amax[f] : ~0u;
+    };
+    unsigned amx = 0u;
+    if (F16 && nt > 0) amx = col_amax(0);
+    float xf = 0.f;
     for (uint32_t c = 0; t < nt; ++c) {
       const int4 tl = s_tiles[t];
       const bool nar = tl.y & 1;
+      if constexpr (F16) {
+        if (kc == 0) {
+          xf = amx == ~0u ? 0.f : pow2f(fp16_data_exp(amx, 1.f));
+          if (t + 1 < nt) amx = col_amax(t + 1);
+        }
+      }
       int tn = t, kcn_next = kc + 1;
       if (kcn_next == (s_seg[tl.z].B - tl.x + 31) / 32) {
         tn = t + 1;
@@ -712,12 +787,12 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) break;
       // B operand: per half of 64 columns, 64 hi rows then 64 lo rows
       unsigned char* sb = st + s * 4 * kChunk + 2 * kChunk;
-      if (BF) {
+      if constexpr (BF) {
         if (nar) {
-          split_store_bf<2>(sb, sb + 64 * ROWB, tid & 63, v, 2 * (tid >> 6));
+          split_store_bf<2, F16>(sb, sb + 64 * ROWB, tid & 63, v, 2 * (tid >> 6), xf);
         } else {
           unsigned char* hb = sb + ((tid >> 6) & 1) * (128 * ROWB);
-          split_store_bf<4>(hb, hb + 64 * ROWB, tid & 63, v, 4 * (tid >> 7));
+          split_store_bf<4, F16>(hb, hb + 64 * ROWB, tid & 63, v, 4 * (tid >> 7), xf);
         }
       } else if (nar) {
         split_store<2>(sb, sb + 64 * ROWB, tid & 63, v, 2 * (tid >> 6), a.nprod == 3);
@@ -739,6 +814,18 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     for (int t = 0; t < nt; ++t, ++tcount) {
       const int4 tl = s_tiles[t];
       const int acc = tcount & 1;
+      // FP16x3: magnitudes of the functions of this lane's column pairs (one
+      // per block of 16 columns), loaded before the wait
+      unsigned ramx[4] = {0u, 0u, 0u, 0u};
+      if constexpr (F16) {
+        const RadISeg sq = s_seg[tl.z];
+        const int per_b = (2 * tl.x + 1) * 2;
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+          const int col = (tl.y & ~1) + 16 * ehalf + 32 * it + 2 * (lane & 7);
+          if (col < sq.NB * per_b) ramx[it] = a.amax[sq.fn0 + col / per_b];
+        }
+      }
       if (!mbar_wait(accf + acc, (tcount >> 1) & 1, abort_flag)) break;
       tc_after();
       const RadISeg sg = s_seg[tl.z];
@@ -751,11 +838,17 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       const int width = nar ? 64 : 128;
       const int per_b = (2 * l + 1) * 2;
       const uint32_t dq = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quarter * 32) << 16);
-      for (int c0 = 16 * ehalf; c0 < width; c0 += 32) {
+      const float tscale = F16 ? pow2f(-a.texp[sg.lb + l]) : 1.f;  // FP16x3 table scale out
+#pragma unroll
+      for (int it = 0; it < 4; ++it) {
+        const int c0 = 16 * ehalf + 32 * it;
+        if (c0 >= width) break;
         // lane k < 8 finds the S offset of the column pair c0 + 2k, c0 + 2k + 1
         // ((b, m), re and im: column pairs never straddle (b, m), as tiles
-        // start at even columns); the stores take it by shuffle
+        // start at even columns) and, for FP16x3, the pair's unscale factor;
+        // the stores take both by shuffle
         int64_t o = -1;
+        float un = tscale;
         {
           const int col = col0 + c0 + 2 * (lane & 7);
           if (col < NB * per_b) {
@@ -765,6 +858,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
             const int p = (l - am) & 1;
             const int64_t srow = si[2 * (m + B - 1) + p] + ((l - am - p) >> 1);
             o = srow * ((int64_t)NB * 2 * B) + (int64_t)b * 2 * B;
+            if (F16) un *= pow2f(-fp16_data_exp(ramx[it], 1.f));
           }
         }
         float v[16];
@@ -783,7 +877,12 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int64_t ok = __shfl_sync(0xffffffffu, o, k);
-          if (i < B && ok >= 0) *(float2*)(sout + ok + 2 * i) = make_float2(v[2 * k], v[2 * k + 1]);
+          if constexpr (F16) {
+            const float uk = __shfl_sync(0xffffffffu, un, k);
+            if (i < B && ok >= 0) *(float2*)(sout + ok + 2 * i) = make_float2(v[2 * k] * uk, v[2 * k + 1] * uk);
+          } else {
+            if (i < B && ok >= 0) *(float2*)(sout + ok + 2 * i) = make_float2(v[2 * k], v[2 * k + 1]);
+          }
         }
       }
       tc_before();
@@ -797,8 +896,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   __syncthreads();
   if (*abort_flag) {
     if (threadIdx.x == 0) atomicExch(a.err, 1);
-    if (warp == 0 && lane == 0) drain_ring(tfull, kStagesRadI, issued);
-    if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(drain + (warp == 1 ? 0 : 1));
+    if (warp == 0 && lane == 0) drain_ring(tfull, kStagesRadI, ((const uint32_t*)(bars + 61))[0]);
+    if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(bars + 62 + (warp == 1 ? 0 : 1));
     __syncthreads();
   }
   tc_after();
@@ -868,6 +967,44 @@ void append_planes_bf16(std::vector<unsigned char>& img, int rows, int K, int KC
     }
 }
 
+// FP16 form of append_planes_bf16: the values times 2^e, as FP16 hi/lo pairs
+// (hi = RN(v 2^e), lo = RN(v 2^e - hi)), same layout.
+template <typename F>
+void append_planes_f16(std::vector<unsigned char>& img, int rows, int K, int KC, int e, F value) {
+  const size_t off = img.size();
+  const size_t plane = (size_t)rows * 64;
+  img.resize(off + 2 * (size_t)KC * plane, 0);
+  for (int r = 0; r < rows; ++r)
+    for (int k = 0; k < K; ++k) {
+      const double v = std::ldexp(value(r, k), e);
+      if (v == 0.0) continue;
+      const __half h = __float2half_rn((float)v);
+      const __half l = __float2half_rn((float)(v - (double)__half2float(h)));
+      const uint16_t hb = __half_as_ushort(h), lb = __half_as_ushort(l);
+      const int kc = k / 32, kin = k % 32;
+      const size_t pos = (size_t)kc * 2 * plane + (size_t)r * 64 + (size_t)((((kin >> 3) ^ ((r >> 1) & 3)) << 4) + (kin & 7) * 2);
+      memcpy(&img[off + pos], &hb, 2);
+      memcpy(&img[off + plane + pos], &lb, 2);
+    }
+}
+
+// Largest |value(r, k)| over r < rows, k < K.
+template <typename F>
+double table_max(int rows, int K, F value) {
+  double mx = 0.0;
+  for (int r = 0; r < rows; ++r)
+    for (int k = 0; k < K; ++k) mx = std::max(mx, std::fabs(value(r, k)));
+  return mx;
+}
+
+// Appends a table in the plan's operand format (FP16 scaled by 2^e).
+template <typename F>
+void append_table(std::vector<unsigned char>& img, int op, int rows, int K, int KC, int e, F value) {
+  if (op == TC_OP_FP16) append_planes_f16(img, rows, K, KC, e, value);
+  else if (op == TC_OP_BF16) append_planes_bf16(img, rows, K, KC, value);
+  else append_planes(img, rows, K, KC, value);
+}
+
 int pad16i(int n) { return n <= 16 ? 16 : (n + 15) / 16 * 16; }
 
 }  // namespace
@@ -889,6 +1026,7 @@ struct TcInvState {
   size_t rad_smem = 0;
   std::vector<int64_t> l_off;     // image offset of the radial table of (segment, l)
   std::vector<int> l_base;        // first entry of each segment in l_off
+  int* rad_texp = nullptr;        // FP16x3 scale exponent of the radial table of (segment, l)
 };
 
 bool make_map_2d(CUtensorMap* map, void* base, uint64_t inner, uint64_t rows, uint32_t box_inner, uint32_t box_rows,
@@ -994,7 +1132,9 @@ cudaError_t tc_inv_prepare(Plan& P) {
   TcInvState* st = new TcInvState();
   P.tc_inv_state = st;
   const bool bf = tc_bf16(P.prec);
+  const int op = tc_operand(P.prec);
   std::vector<unsigned char> img;
+  std::vector<int> texp;      // FP16x3 radial table exponents, as l_off
   std::vector<int4> lt;
   std::vector<double> lcost;  // estimated bytes moved per tile
   std::vector<LegISeg> lsegs;
@@ -1005,13 +1145,14 @@ cudaError_t tc_inv_prepare(Plan& P) {
     const int B = sg.B, NB = sg.NB;
     LegISeg ls;
     memset(&ls, 0, sizeof(ls));
-    ls.B = B, ls.NB = NB, ls.npad = pad16i(B), ls.w1_off = sg.w1_off;
+    ls.B = B, ls.NB = NB, ls.npad = pad16i(B), ls.fn0 = sg.fn0, ls.w1_off = sg.w1_off;
     st->npad_max = std::max(st->npad_max, ls.npad);
     // Legendre synthesis tables, per (|m|, j'-half of 64 rows):
     // [P hi][P lo][Q hi][Q lo], rows j', K = l'
     const int nh = ls.npad > 64 ? 64 : ls.npad;
     const int halves = (ls.npad + 63) / 64;
     std::vector<int64_t> aoff(2 * B, 0);
+    std::vector<int> aexp(2 * B, 0);
     std::vector<int> akc(B, 0);
     for (int am = 0; am < B; ++am) {
       int kcs[2];
@@ -1019,16 +1160,21 @@ cudaError_t tc_inv_prepare(Plan& P) {
       for (int jh = 0; jh < halves; ++jh) {
         img.resize((img.size() + 1023) / 1024 * 1024);
         aoff[2 * am + jh] = (int64_t)img.size();
-        for (int p = 0; p < 2; ++p) {
-          if (kcs[p] == 0) continue;
-          auto lam = [&](int jr, int q) -> double {
+        auto lam_p = [&](int p) {
+          return [&, p](int jr, int q) -> double {
             const int j = 64 * jh + jr;
             if (j >= B) return 0.0;
             const int l = am + p + 2 * q;
             return H.lam[((size_t)am * B + l) * B + j];
           };
-          if (bf) append_planes_bf16(img, nh, n_par(B, am, p), kcs[p], lam);
-          else append_planes(img, nh, n_par(B, am, p), kcs[p], lam);
+        };
+        // one FP16 scale for the image (both parities)
+        const double mx = std::max(table_max(nh, n_par(B, am, 0), lam_p(0)), table_max(nh, n_par(B, am, 1), lam_p(1)));
+        const int e = op == TC_OP_FP16 ? fp16_scale_exp(mx) : 0;
+        aexp[2 * am + jh] = e;
+        for (int p = 0; p < 2; ++p) {
+          if (kcs[p] == 0) continue;
+          append_table(img, op, nh, n_par(B, am, p), kcs[p], e, lam_p(p));
         }
       }
       akc[am] = kcs[0] | (kcs[1] << 8);
@@ -1041,7 +1187,7 @@ cudaError_t tc_inv_prepare(Plan& P) {
       for (int jh = 0; jh < halves; ++jh)
         for (int r0 = 0; r0 < NB * 2 * B; r0 += 128) {
           lt.push_back(make_int4(mi, r0, jh | ((int)s << 8), akc[am]));
-          lt.push_back(make_int4((int)aoff[2 * am + jh], siP, siQ, 0));
+          lt.push_back(make_int4((int)aoff[2 * am + jh], siP, siQ, aexp[2 * am + jh]));
           // S chunks in, both G halves out, the table on its first tile
           const int ncols = jh ? ls.npad - 64 : nh;
           lcost.push_back(kcs * 16384.0 + 1024.0 * ncols + (r0 == 0 ? 2.0 * kcs * nh * 128 : 0.0));
@@ -1049,26 +1195,39 @@ cudaError_t tc_inv_prepare(Plan& P) {
     }
     // radial inverse tables, per l: KC_l x [hi chunk][lo chunk], rows i (128), K = n'
     st->l_base.push_back((int)st->l_off.size());
+    double sbound = 0.0;  // bound on |S| / max |coefficient|: largest sum over n of |T_nl(i)|
     for (int l = 0; l < B; ++l) {
       img.resize((img.size() + 1023) / 1024 * 1024);
       st->l_off.push_back((int64_t)img.size());
       const int K = B - l, KC = (K + 31) / 32;
+      double mx = 0.0;
+      for (int i = 0; i < B; ++i) {
+        double rs = 0.0;
+        for (int np = 0; np < K; ++np) {
+          const double t = std::fabs(H.T[((size_t)l * B + (l + np)) * B + i]);
+          rs += t;
+          mx = std::max(mx, t);
+        }
+        sbound = std::max(sbound, rs);
+      }
+      const int e = op == TC_OP_FP16 ? fp16_scale_exp(mx) : 0;
+      texp.push_back(e);
       for (int kc = 0; kc < KC; ++kc) {
         auto tv = [&](int i, int k) -> double {
           const int np = kc * 32 + k;
           if (i >= B || np >= K) return 0.0;
           return H.T[((size_t)l * B + (l + np)) * B + i];
         };
-        if (bf) append_planes_bf16(img, 128, 32, 1, tv);
-        else append_planes(img, 128, 32, 1, tv);
+        append_table(img, op, 128, 32, 1, e, tv);
       }
     }
+    ls.sb = (float)sbound;
     // tensor map over S: [B^2 rows of l'][NB*2*B]
     float* w2 = (float*)P.d_w2 + sg.w2_off;
     if (!make_map_2d(&ls.smap, w2, (uint64_t)NB * 2 * B, (uint64_t)B * B, 128, 32, CU_TENSOR_MAP_SWIZZLE_NONE))
       return cudaErrorInvalidValue;
     lsegs.push_back(ls);
-    rsegs.push_back(RadISeg{B, NB, sg.fn0, (int)sg.si_rows, sg.w2_off});
+    rsegs.push_back(RadISeg{B, NB, sg.fn0, (int)sg.si_rows, sg.w2_off, st->l_base.back(), 0});
   }
   if (img.size() >= (size_t)1 << 31) return cudaErrorInvalidValue;  // image offsets are 32-bit
   int64_t bytes = 0;
@@ -1076,6 +1235,7 @@ cudaError_t tc_inv_prepare(Plan& P) {
   if (e == cudaSuccess) e = upload(&st->leg_tiles, lt, bytes);
   if (e == cudaSuccess) e = upload(&st->leg_segs, lsegs, bytes);
   if (e == cudaSuccess) e = upload(&st->rad_segs, rsegs, bytes);
+  if (e == cudaSuccess) e = upload(&st->rad_texp, texp, bytes);
   st->leg_ntiles = (int)lcost.size();
   // tables, staging, operand ring, barrier slots, segments, tile slice (32 bytes a tile)
   const int nhm = st->npad_max > 64 ? 64 : st->npad_max;
@@ -1094,7 +1254,8 @@ cudaError_t tc_inv_prepare(Plan& P) {
 void tc_inv_release(Plan& P) {
   TcInvState* st = (TcInvState*)P.tc_inv_state;
   if (!st) return;
-  void* ptrs[] = {st->d_img, st->leg_tiles, st->leg_first, st->leg_segs, st->rad_tiles, st->rad_first, st->rad_segs};
+  void* ptrs[] = {st->d_img,     st->leg_tiles, st->leg_first, st->leg_segs,
+                  st->rad_tiles, st->rad_first, st->rad_segs, st->rad_texp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete st;
@@ -1122,7 +1283,12 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
     a.err = P.d_err;
     a.si_max = st->si_max;
     a.nprod = tc_products(P.prec);
-    void (*fn)(RadIArgs) = tc_bf16(P.prec) ? tc_rad_inv_kernel<true> : tc_rad_inv_kernel<false>;
+    a.texp = st->rad_texp;
+    a.amax = P.d_amax ? P.d_amax + AMAX_COEF * P.nfn : nullptr;
+    const int op = tc_operand(P.prec);
+    void (*fn)(RadIArgs) = op == TC_OP_FP16   ? tc_rad_inv_kernel<TC_OP_FP16>
+                           : op == TC_OP_BF16 ? tc_rad_inv_kernel<TC_OP_BF16>
+                                              : tc_rad_inv_kernel<TC_OP_TF32>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->rad_smem);
     if (e != cudaSuccess) return e;
     fn<<<st->rad_grid, kThreadsInv, st->rad_smem, s>>>(a);
@@ -1139,7 +1305,11 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
     a.npad_max = st->npad_max;
     a.kcmax = st->kcmax;
     a.nprod = tc_products(P.prec);
-    void (*fn)(LegIArgs) = tc_bf16(P.prec) ? tc_leg_inv_kernel<true> : tc_leg_inv_kernel<false>;
+    a.amax = P.d_amax ? P.d_amax + AMAX_COEF * P.nfn : nullptr;
+    const int op = tc_operand(P.prec);
+    void (*fn)(LegIArgs) = op == TC_OP_FP16   ? tc_leg_inv_kernel<TC_OP_FP16>
+                           : op == TC_OP_BF16 ? tc_leg_inv_kernel<TC_OP_BF16>
+                                              : tc_leg_inv_kernel<TC_OP_TF32>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->leg_smem);
     if (e != cudaSuccess) return e;
     fn<<<st->leg_grid, kThreadsInv, st->leg_smem, s>>>(a);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -109,7 +110,7 @@ constexpr uint64_t kDrainNs = 200000000ull;
 // Wait, bounded by limit_ns, for the phase of the given parity without
 // looking at the abort flag (used after an abort, to let operations that were
 // already issued finish).  Returns whether the phase completed.
-static __device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kDrainNs) {
+static __device__ __noinline__ bool mbar_drain(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kDrainNs) {
   const uint64_t t0 = gtimer();
   while (!mbar_try_sleep(bar, parity, 100000u))
     if (gtimer() - t0 > limit_ns) return false;
@@ -120,7 +121,7 @@ static __device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity
 // land, on each barrier of a ring of `stages` barriers, when `issued` copies
 // were issued in all (copy k completes phase k / stages of bars[k % stages]).
 // Returns whether every one of them finished within the bound.
-static __device__ __forceinline__ bool drain_ring(uint64_t* bars, int stages, uint32_t issued) {
+static __device__ __noinline__ bool drain_ring(uint64_t* bars, int stages, uint32_t issued) {
   bool ok = true;
   for (int s = 0; s < stages && (uint32_t)s < issued; ++s) {
     const uint32_t last = (uint32_t)s + (uint32_t)stages * ((issued - 1 - (uint32_t)s) / (uint32_t)stages);
@@ -175,7 +176,7 @@ static __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 // After an abort: an MMA-issuing thread commits every MMA it issued to its
 // own barrier (count 1, not used before) and waits, bounded, until they have
 // finished reading shared memory and writing tensor memory.
-static __device__ __forceinline__ bool drain_mma(uint64_t* bar) {
+static __device__ __noinline__ bool drain_mma(uint64_t* bar) {
   mma_commit(bar);
   return mbar_drain(bar, 0);
 }
@@ -288,6 +289,47 @@ static __device__ __forceinline__ uint32_t bf16_split(float x) {
   u = __float_as_uint(r);
   const uint32_t lb = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
   return hb | (lb << 16);
+}
+
+// kind::f16 instruction descriptor with FP16 A and B (format 0): D f32,
+// both K-major, M = 128.
+static __device__ __forceinline__ uint32_t idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// FP16 hi/lo split of x * f (f a power of two, so the product is exact).
+// With the scales used here |x f| < 2^14, so hi never overflows, and lo keeps
+// 11 significant bits down to |x f| ~ 2^-3.
+// Two values at once, packed as the operand rows want them: hi = {hi(x0) in
+// the low half, hi(x1) in the high half}, lo likewise.  hi is x f rounded to
+// 11 significant bits by the integer TF32 rounding (an FP16 value whenever
+// |x f| is in FP16's normal range, which the scales guarantee for all but
+// the negligible values), lo = x f - hi in FP32; one packed conversion
+// (cvt f16x2) each, instead of three scalar conversions per value.
+static __device__ __forceinline__ void fp16_split2(float x0, float x1, float f, uint32_t& hi, uint32_t& lo) {
+  const float a = x0 * f, b = x1 * f;
+  const float ha = tf32_rna(a), hb = tf32_rna(b);
+  const __half2 h = __floats2half2_rn(ha, hb);
+  const __half2 l = __floats2half2_rn(a - ha, b - hb);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// 2^e as a float, -126 <= e <= 127.
+static __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// Exponent e of the FP16x3 data scale: the largest magnitude x (a float's
+// bits; x >= 0), times a growth bound, lands in [2^13, 2^14) after scaling by
+// 2^e; 0 for x = 0; clamped to +-100 (as fp16_scale_exp on the host).
+static __device__ __forceinline__ int fp16_data_exp(unsigned amax_bits, float bound) {
+  const float x = __uint_as_float(amax_bits) * bound;
+  if (!(x > 0.f)) return 0;
+  // x = m 2^E with m in [0.5, 1): E = biased exponent - 126 for normal x, so
+  // e = 14 - E = 140 - biased exponent; subnormal x (biased 0) clamps to
+  // +100, infinite or NaN x (biased 255) to -100
+  const int eb = (int)((__float_as_uint(x) >> 23) & 0xffu);
+  const int e = 140 - eb;
+  return eb == 0 ? 100 : (e > 100 ? 100 : (e < -100 ? -100 : e));
 }
 
 // 128-byte swizzled (TF32 rows) and 64-byte swizzled (BF16 rows) byte

@@ -23,13 +23,14 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsgl.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "sgl.h")
 
 SGL_OK, SGL_ERR_ARG, SGL_ERR_ALLOC, SGL_ERR_CUDA, SGL_ERR_TIMEOUT, SGL_ERR_UNSUPPORTED = range(6)
-SGL_FP64, SGL_FP32, SGL_TF32X3, SGL_TF32, SGL_BF16X3 = 0, 1, 2, 3, 4
+SGL_FP64, SGL_FP32, SGL_TF32X3, SGL_TF32, SGL_BF16X3, SGL_FP16X3 = 0, 1, 2, 3, 4, 5
 SGL_SAMPLES_WEIGHTED, SGL_SAMPLES_PHYSICAL, SGL_SAMPLES_REAL = 0, 1, 2
 SGL_GRID_LAGUERRE, SGL_GRID_HALF_RANGE_HERMITE = 0, 1
 GRIDS = {"laguerre": SGL_GRID_LAGUERRE, "hermite": SGL_GRID_HALF_RANGE_HERMITE}
 SGL_MAX_B = 128
 
-PRECISIONS = {"fp64": SGL_FP64, "fp32": SGL_FP32, "tf32x3": SGL_TF32X3, "tf32": SGL_TF32, "bf16x3": SGL_BF16X3}
+PRECISIONS = {"fp64": SGL_FP64, "fp32": SGL_FP32, "tf32x3": SGL_TF32X3, "tf32": SGL_TF32, "bf16x3": SGL_BF16X3,
+              "fp16x3": SGL_FP16X3}
 STATUS_NAMES = {0: "SGL_OK", 1: "SGL_ERR_ARG", 2: "SGL_ERR_ALLOC", 3: "SGL_ERR_CUDA",
                 4: "SGL_ERR_TIMEOUT", 5: "SGL_ERR_UNSUPPORTED"}
 
@@ -85,6 +86,8 @@ def load_library():
         "sgl_selftest_wait": (i32, [i64, ctypes.POINTER(ctypes.c_int)]),
         "sgl_midpoint": (i32, [i32, i32, ctypes.c_double, i32, i32, vp, vp, vp]),
         "sgl_set_dlt": (i32, [vp, i32]),
+        "sgl_set_graphs": (i32, [vp, i32]),
+        "sgl_graph_count": (i32, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -258,6 +261,14 @@ SGL_NUM_STAGES = 6
 
 def sgl_set_profiling(plan, enable: bool):
     _check(load_library().sgl_set_profiling(plan, int(bool(enable))), plan)
+
+
+def sgl_set_graphs(plan, enable: bool):
+    _check(load_library().sgl_set_graphs(plan, int(bool(enable))), plan)
+
+
+def sgl_graph_count(plan) -> int:
+    return load_library().sgl_graph_count(plan)
 
 
 def sgl_stage_times(plan):
@@ -436,6 +447,16 @@ class Plan:
             self._prep(out, self.n_samples, "out", self.sample_dtype)
         sgl_adjoint(self.handle, int(bool(of_inverse)), x.data_ptr(), out.data_ptr(), self._stream(x, out))
         return out
+
+    def set_graphs(self, enable: bool = True) -> "Plan":
+        """Replay this plan's device-buffer calls through CUDA graphs of its
+        own (sgl_set_graphs); returns the plan."""
+        sgl_set_graphs(self.handle, enable)
+        return self
+
+    @property
+    def graph_count(self) -> int:
+        return int(self.lib.sgl_graph_count(self.handle))
 
     def autotune(self, cache: Optional[str] = None, samples=None, coeffs=None) -> str:
         """Choose the plan's launch configuration by timing it (sgl_autotune).

@@ -103,3 +103,21 @@ def test_cpu_oracle_sample_line():
     assert r["kind"] == "oracle" and r["unit"] == "transforms/s" and r["value"] > 0
     assert 1 <= r["cores"] <= r["threads_available"] and r["cpu_s"] > 0
     assert "B=8" in r["sample"]
+
+
+def test_error_gate_names_every_missed_bound():
+    # the bench exits non-zero when a round trip misses its bound: 1e-12
+    # normwise for FP64, 1e-6 for the split-precision paths; the reduced
+    # precision variants (TF32 hi*hi, BF16x3) have no such bound
+    ok = {"config": {"precision": "tf32x3"}, "round_trip_errors": {"normwise_max": 8e-7},
+          "fp64_path": {"round_trip_errors": {"normwise_max": 5e-15}},
+          "variants": {"fp16x3": {"round_trip_errors": {"normwise_max": 7e-7}, "round_trip_max_rel_err": 6e-7},
+                       "bf16x3": {"round_trip_errors": {"normwise_max": 7e-6}, "round_trip_max_rel_err": 7e-6}}}
+    assert bench.error_gate(ok) == []
+    bad = {"config": {"precision": "tf32x3"}, "round_trip_errors": {"normwise_max": 1.5e-6},
+           "fp64_path": {"round_trip_errors": {"normwise_max": 2e-12}},
+           "variants": {"fp16x3": {"round_trip_errors": {"normwise_max": 3e-6}, "round_trip_max_rel_err": 9e-7}}}
+    missed = bench.error_gate(bad)
+    assert len(missed) == 3
+    assert any(m.startswith("tf32x3") for m in missed) and any(m.startswith("fp64") for m in missed)
+    assert any(m.startswith("fp16x3") for m in missed)

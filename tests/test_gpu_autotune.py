@@ -1,4 +1,5 @@
-"""Autotuner (sgl_autotune): timing-based choice of the launch configuration,
+"""Autotuner (sgl_autotune): timing-based choice of the launch configuration
+(phi-FFT ring pairs per CTA, SIMT tile families, tensor-core tile widths),
 its cache file, and unchanged results.
 
 A TF32x3 plan of B=64 x 4 functions is tuned with a cache file; the chosen
@@ -21,9 +22,19 @@ from tolerances import SPLIT_TOL as TF32X3_TOL
 
 
 def _parse(text):
-    m = re.match(r"fft_fwd_jp=(\d+) fft_inv_jp=(\d+) rad_inv_narrow=(\d+) source=(\w+)", text)
+    """(fft_fwd_jp, fft_inv_jp, rad_inv_narrow, source); the tile shapes are
+    checked by _shapes."""
+    m = re.match(r"fft_fwd_jp=(\d+) fft_inv_jp=(\d+) rad_inv_narrow=(\d+) simt=\d,\d,\d,\d rad_rows=\d+ "
+                 r"source=(\w+)$", text)
     assert m, text
     return int(m.group(1)), int(m.group(2)), int(m.group(3)), m.group(4)
+
+
+def _shapes(text):
+    """(SIMT tile family of each GEMM stage, tensor-core radial tile width)."""
+    m = re.search(r"simt=(\d),(\d),(\d),(\d) rad_rows=(\d+)", text)
+    assert m, text
+    return tuple(int(m.group(k)) for k in range(1, 5)), int(m.group(5))
 
 
 def test_autotune_cache_and_parity(tmp_path):
@@ -32,8 +43,11 @@ def test_autotune_cache_and_parity(tmp_path):
     cache = str(tmp_path / "tuning.txt")
     plan = Plan(B, NB, "tf32x3")
     assert _parse(plan.tuning)[3] == "default"
-    jf, ji, rn, src = _parse(plan.autotune(cache=cache))
+    tuned = plan.autotune(cache=cache)
+    jf, ji, rn, src = _parse(tuned)
     assert src == "timed" and jf in (4, 8, 16) and ji in (4, 8, 16) and rn in (1, 65)
+    simt, rad_rows = _shapes(tuned)
+    assert simt == (0, 0, 0, 0) and rad_rows in (32, 48, 64)  # tensor-core plan: the radial tile width
     lines = open(cache).read().splitlines()
     assert len(lines) == 1 and f"segs={B}x{NB}," in lines[0]
 
@@ -48,7 +62,8 @@ def test_autotune_cache_and_parity(tmp_path):
     plan.check()
 
     plan2 = Plan(B, NB, "tf32x3")
-    assert _parse(plan2.autotune(cache=cache)) == (jf, ji, rn, "cache")
+    cached = plan2.autotune(cache=cache)
+    assert _parse(cached) == (jf, ji, rn, "cache") and _shapes(cached) == (simt, rad_rows)
     assert len(open(cache).read().splitlines()) == 1
     f2 = plan2.forward(plan2.inverse(ct)).cpu().numpy()
     assert np.array_equal(f, f2)  # same configuration, same arithmetic
@@ -61,10 +76,36 @@ def test_autotune_fp64_fft_choice_keeps_results():
     c = inputs.random_coeffs(B, NB, seed=inputs.BASE_SEED + 2)
     ct = torch.from_numpy(c).cuda()
     before = plan.forward(plan.inverse(ct)).cpu().numpy()
-    jf, ji, rn, src = _parse(plan.autotune())
+    tuned = plan.autotune()
+    jf, ji, rn, src = _parse(tuned)
     assert src == "timed" and jf in (4, 8) and ji in (4, 8)
+    simt, _ = _shapes(tuned)
+    assert all(p in (0, 1, 2) for p in simt)
     after = plan.forward(plan.inverse(ct)).cpu().numpy()
-    assert np.array_equal(before, after)  # ring grouping does not change the arithmetic
+    # neither the ring grouping nor the SIMT tile family changes the
+    # arithmetic: each output is one thread's sum over K in the same order
+    assert np.array_equal(before, after)
+
+
+def test_autotune_radial_tile_width_keeps_the_bound(tmp_path):
+    # each tensor-core radial tile width the tuner may pick (forced through
+    # the cache file): the round trip stays within the split-precision gate
+    from paper_1604_05140_gb300 import Plan
+    B, NB = 128, 1
+    c = inputs.random_coeffs(B, NB, seed=inputs.BASE_SEED + 8, decay=True)
+    ct = torch.from_numpy(c).to(torch.complex64).cuda()
+    first = str(tmp_path / "tuned.txt")
+    Plan(B, NB, "tf32x3").autotune(cache=first)
+    line = open(first).read().splitlines()[0]
+    for rr in (32, 48, 64):
+        forced = tmp_path / f"rr{rr}.txt"
+        forced.write_text(re.sub(r"rad_rows=\d+", f"rad_rows={rr}", line) + "\n")
+        plan = Plan(B, NB, "tf32x3")
+        text = plan.autotune(cache=str(forced))
+        assert _parse(text)[3] == "cache" and _shapes(text)[1] == rr, text
+        f = plan.forward(plan.inverse(ct)).cpu().numpy()
+        assert np.abs(f - c).max() / np.abs(c).max() < TF32X3_TOL, rr
+        plan.check()
 
 
 def test_autotune_rejects_host_buffers():

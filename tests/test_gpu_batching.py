@@ -4,7 +4,9 @@ capture of the round trip.
 Workload: 256 functions with bandlimits drawn uniformly from {16, 24, ..., 128}
 (seeded), TF32x3, complex-normal coefficients; every function's round trip,
 and one function of every bandlimit's inverse and forward (of arbitrary,
-not band-limited samples) are checked against the FP64 oracle.  The round trip is captured in a
+not band-limited samples) are checked against the FP64 oracle.  The round
+trip runs through the plan's own CUDA graphs (sgl_set_graphs) and inside a
+caller's graph capture; both must reproduce the direct launches exactly.  The round trip is captured in a
 CUDA graph and replayed; replays must reproduce the eager results exactly.
 """
 import numpy as np
@@ -70,6 +72,52 @@ def test_uneven_batch_forward_of_arbitrary_samples(batch):
         fk = f[co:co + O.coeff_count(B)]
         assert np.abs(fk - ref).max() / np.abs(ref).max() < TF32X3_TOL, (k, B)
     assert len(picked) == 15
+    plan.check()
+
+
+def test_plan_graphs_match_direct_launches(batch):
+    # sgl_set_graphs: the plan captures each call kind and buffer pair once,
+    # replays it afterwards, and gives the direct launches' results bit for
+    # bit; a caller's own capture still records the plan's launches directly
+    plan, Bs, coeffs, flat = batch
+    s = torch.empty(plan.sample_shape, dtype=plan.dtype, device="cuda")
+    out = torch.empty(plan.coeff_shape, dtype=plan.dtype, device="cuda")
+    plan.inverse(flat, out=s)
+    plan.forward(s, out=out)
+    adj = plan.adjoint(s, of_inverse=True)
+    torch.cuda.synchronize()
+    eager_s, eager, eager_adj = s.clone(), out.clone(), adj.clone()
+    plan.set_graphs(True)
+    assert plan.graph_count == 0
+    for _ in range(3):
+        s.zero_()
+        out.zero_()
+        plan.inverse(flat, out=s)
+        plan.forward(s, out=out)
+    torch.cuda.synchronize()
+    assert plan.graph_count == 2
+    assert torch.equal(s, eager_s) and torch.equal(out, eager)
+    out2 = torch.empty_like(out)  # another buffer pair: another graph
+    plan.forward(s, out=out2)
+    adj2 = torch.empty_like(adj)
+    plan.adjoint(s, of_inverse=True, out=adj2)  # another call kind (weights dropped)
+    torch.cuda.synchronize()
+    assert plan.graph_count == 4
+    assert torch.equal(out2, eager) and torch.equal(adj2, eager_adj)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.forward(s, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.forward(s, out=out)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager) and plan.graph_count == 4
+    plan.set_graphs(False)
+    assert plan.graph_count == 0
     plan.check()
 
 

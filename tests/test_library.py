@@ -123,6 +123,7 @@ def test_null_plan_queries(lib):
     assert lib.sgl_forward(None, None, None, None) == sgl.SGL_ERR_ARG
     assert lib.sgl_autotune(None, None, None, None, None) == sgl.SGL_ERR_ARG
     assert lib.sgl_tuning(None) == b""
+    assert lib.sgl_set_graphs(None, 1) == sgl.SGL_ERR_ARG
     lib.sgl_destroy(None)
 
 
@@ -136,7 +137,7 @@ def test_binding_has_every_function_under_its_own_name(lib):
         "fft_forward", "legendre_forward", "radial_forward", "radial_inverse", "legendre_inverse", "fft_inverse"]
     assert sgl.sgl_stage_name(sgl.SGL_NUM_STAGES) == ""
     for q in (sgl.sgl_sample_count, sgl.sgl_coeff_count, sgl.sgl_num_functions, sgl.sgl_workspace_bytes,
-              sgl.sgl_launches_per_call):
+              sgl.sgl_launches_per_call, sgl.sgl_graph_count):
         assert q(None) == -1
     for q in (sgl.sgl_sample_offset, sgl.sgl_coeff_offset, sgl.sgl_bandlimit, sgl.sgl_radii):
         assert q(None, 0) == -1
