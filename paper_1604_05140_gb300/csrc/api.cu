@@ -673,9 +673,11 @@ done:
 // ---------------------------------------------------------------------------
 static std::string tuning_text(const Plan& P, const char* source) {
   char buf[256];
-  snprintf(buf, sizeof buf, "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d source=%s",
+  snprintf(buf, sizeof buf,
+           "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d queue=%d "
+           "source=%s",
            fft_jp(P, P.maxB, false), fft_jp(P, P.maxB, true), P.radi_narrow, P.simt_policy[0], P.simt_policy[1],
-           P.simt_policy[2], P.simt_policy[3], P.rad_rows, source);
+           P.simt_policy[2], P.simt_policy[3], P.rad_rows, P.fft_merge, P.queue_slices, source);
   return buf;
 }
 
@@ -724,19 +726,22 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
       while (fgets(line, sizeof line, f)) {
         const std::string ln(line);
         if (ln.compare(0, key.size() + 3, key + " | ") != 0) continue;
-        int jf = 0, ji = 0, rn = 0, sp[4] = {0, 0, 0, 0}, rr = 64;
+        int jf = 0, ji = 0, rn = 0, sp[4] = {0, 0, 0, 0}, rr = 64, fm = 1, qs = 2;
         const int got = sscanf(ln.c_str() + key.size() + 3,
-                               "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d", &jf, &ji,
-                               &rn, &sp[0], &sp[1], &sp[2], &sp[3], &rr);
-        bool valid = (got == 3 || got == 8) && jf >= 1 && jf <= 16 && ji >= 1 && ji <= 16 && rn >= 1;
+                               "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d "
+                               "queue=%d",
+                               &jf, &ji, &rn, &sp[0], &sp[1], &sp[2], &sp[3], &rr, &fm, &qs);
+        bool valid = (got == 3 || got >= 8) && jf >= 1 && jf <= 16 && ji >= 1 && ji <= 16 && rn >= 1;
         for (int k = 0; k < 4; ++k) valid = valid && sp[k] >= 0 && sp[k] <= 2;
-        valid = valid && (rr == 32 || rr == 48 || rr == 64);
+        valid = valid && (rr == 32 || rr == 48 || rr == 64) && (fm == 0 || fm == 1) && (qs == 1 || qs == 2 || qs == 4);
         if (valid) {
           P->jp_fwd = jf;
           P->jp_inv = ji;
           P->radi_narrow = rn;
           for (int k = 0; k < 4; ++k) P->simt_policy[k] = sp[k];
           P->rad_rows = rr;
+          P->fft_merge = fm;
+          P->queue_slices = qs;
           cached = true;
         }
       }
@@ -767,6 +772,26 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
     }
     e = build_fft_lists(*P);
     if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+    // plans of several register-FFT sizes: one multi-size launch per
+    // direction, or one launch per size (timed over both directions)
+    const int merge0 = P->fft_merge;
+    P->fft_merge = 0;
+    const bool several = fft_launches(*P, false) > 1 || fft_launches(*P, true) > 1;
+    P->fft_merge = merge0;
+    if (several) {
+      int best = P->fft_merge;
+      double tbest = 1e30;
+      for (int fm : {1, 0}) {
+        P->fft_merge = fm;
+        const double t = time_calls(*P, true, samples, coeffs, s) + time_calls(*P, false, samples, coeffs, s);
+        if (t < 0.0) return cuda_fail(P, cudaGetLastError(), "autotune launch");
+        if (t < tbest) {
+          tbest = t;
+          best = fm;
+        }
+      }
+      P->fft_merge = best;
+    }
     if (tc_precision(P->prec)) {
       int best = 65;
       double tbest = 1e30;
@@ -798,6 +823,22 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
         }
       }
       P->rad_rows = best_rr;
+      // work-queue granularity of the tensor-core stages: slices per CTA
+      int best_q = 2;
+      tbest = 1e30;
+      for (int q : {2, 1, 4}) {
+        P->queue_slices = q;
+        tc_release(*P);
+        e = tc_prepare(*P);
+        if (e != cudaSuccess) return cuda_fail(P, e, "autotune tensor-core preparation");
+        const double t = time_calls(*P, true, samples, coeffs, s) + time_calls(*P, false, samples, coeffs, s);
+        if (t < 0.0) return cuda_fail(P, cudaGetLastError(), "autotune launch");
+        if (t < tbest) {
+          tbest = t;
+          best_q = q;
+        }
+      }
+      P->queue_slices = best_q;
     } else {
       // SIMT tile family of each GEMM stage, one stage at a time (forward
       // stages timed on forward calls, inverse stages on inverse calls)
@@ -833,9 +874,10 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
   if (!cached && cache_path) {
     FILE* f = fopen(cache_path, "a");
     if (!f) return fail(P, SGL_ERR_ARG, std::string("cannot append to tuning cache ") + cache_path);
-    fprintf(f, "%s | fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d\n", key.c_str(),
-            P->jp_fwd, P->jp_inv, P->radi_narrow, P->simt_policy[0], P->simt_policy[1], P->simt_policy[2],
-            P->simt_policy[3], P->rad_rows);
+    fprintf(f,
+            "%s | fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d queue=%d\n",
+            key.c_str(), P->jp_fwd, P->jp_inv, P->radi_narrow, P->simt_policy[0], P->simt_policy[1],
+            P->simt_policy[2], P->simt_policy[3], P->rad_rows, P->fft_merge, P->queue_slices);
     fclose(f);
   }
   return SGL_OK;

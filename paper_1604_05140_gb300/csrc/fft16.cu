@@ -213,7 +213,7 @@ __device__ __forceinline__ int spos(int r, int row, int col) {
 // functions in pairs, the first at twice the complex offset (in reals) as the
 // real part, the next one as the imaginary part (zero past pair_limit).
 template <typename real, int N2, bool PAIRS>
-__global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
+__device__ __forceinline__ void fft16_fwd_body(const Fft16Args& a) {
   constexpr int N = 16 * N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);      // [k1 < 16][c < N2]: W_N^{c k1}
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
 // Inverse: G spectra -> samples.  blockDim = 16 * JP.  PAIRS: real and
 // imaginary parts to the pair's two real functions (as in the forward kernel).
 template <typename real, int N2, bool PAIRS>
-__global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
+__device__ __forceinline__ void fft16_inv_body(const Fft16Args& a) {
   constexpr int N = 16 * N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);    // W_N^k, k < N
@@ -445,6 +445,59 @@ __global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
       for (int n1 = 0; n1 < 16; ++n1) ring[n1 * N2] = {v[n1].x * s, v[n1].y * s};
     }
   }
+}
+
+template <typename real, int N2, bool PAIRS>
+__global__ void __launch_bounds__(256) fft16_fwd_kernel(Fft16Args a) {
+  fft16_fwd_body<real, N2, PAIRS>(a);
+}
+
+template <typename real, int N2, bool PAIRS>
+__global__ void __launch_bounds__(256) fft16_inv_kernel(Fft16Args a) {
+  fft16_inv_body<real, N2, PAIRS>(a);
+}
+
+// One launch over segments of several register-FFT sizes (FP32 complex
+// samples): each CTA runs the body of its own segment's N2.  Its register
+// count is the largest of the bodies'.
+#define SGL_FFT16_CASES(BODY)                                                                  \
+  switch (a.segs[a.ctas[blockIdx.x].x].n2) {                                                    \
+    case 2: BODY<float, 2, false>(a); break;                                                    \
+    case 3: BODY<float, 3, false>(a); break;                                                    \
+    case 4: BODY<float, 4, false>(a); break;                                                    \
+    case 5: BODY<float, 5, false>(a); break;                                                    \
+    case 6: BODY<float, 6, false>(a); break;                                                    \
+    case 7: BODY<float, 7, false>(a); break;                                                    \
+    case 8: BODY<float, 8, false>(a); break;                                                    \
+    case 9: BODY<float, 9, false>(a); break;                                                    \
+    case 10: BODY<float, 10, false>(a); break;                                                  \
+    case 11: BODY<float, 11, false>(a); break;                                                  \
+    case 12: BODY<float, 12, false>(a); break;                                                  \
+    case 13: BODY<float, 13, false>(a); break;                                                  \
+    case 14: BODY<float, 14, false>(a); break;                                                  \
+    case 15: BODY<float, 15, false>(a); break;                                                  \
+    case 16: BODY<float, 16, false>(a); break;                                                  \
+    default: break;                                                                             \
+  }
+
+__global__ void __launch_bounds__(256) fft16_fwd_multi_kernel(Fft16Args a) { SGL_FFT16_CASES(fft16_fwd_body) }
+__global__ void __launch_bounds__(256) fft16_inv_multi_kernel(Fft16Args a) { SGL_FFT16_CASES(fft16_inv_body) }
+#undef SGL_FFT16_CASES
+
+// One launch of the multi-size kernel over nctas CTAs whose segments' sizes
+// are at most 16 * max_n2.
+bool fft16_launch_multi(bool inv, const Fft16Args& a, int max_n2, int nctas, cudaStream_t s, cudaError_t* err) {
+  if (max_n2 < 2 || max_n2 > 16 || a.pair_limit) return false;
+  void (*fn)(Fft16Args) = inv ? fft16_inv_multi_kernel : fft16_fwd_multi_kernel;
+  const int N = 16 * max_n2;
+  const size_t smem = sizeof(c2<float>) * ((size_t)N + (size_t)2 * a.JP * N + (size_t)max_n2);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    fn<<<nctas, 16 * a.JP, smem, s>>>(a);
+    e = cudaGetLastError();
+  }
+  *err = e;
+  return true;
 }
 
 // Launch helper: returns false when (n1, n2) is not handled here.  Every

@@ -766,10 +766,21 @@ static void fft_slices(const Plan& P, std::vector<FftSlice>& out, bool inv) {
   }
 }
 
+// Whether the slices of one direction run as one launch of the multi-size
+// register FFT (fft16.cu): the plan's choice (autotuned), several slices,
+// every one a register-FFT size of FP32 complex samples, one ring-pair count.
+static bool fft_merged(const Plan& P, const std::vector<FftSlice>& sl, bool inv) {
+  if (!P.fft_merge || sl.size() < 2 || P.prec == SGL_FP64 || P.real_pairs) return false;
+  const int jp = fft_jp(P, sl[0].B, inv);
+  for (const FftSlice& f : sl)
+    if (!fft16_handles(false, false, f.n1, f.n2) || fft_jp(P, f.B, inv) != jp) return false;
+  return true;
+}
+
 int fft_launches(const Plan& P, bool inv) {
   std::vector<FftSlice> sl;
   fft_slices(P, sl, inv);
-  return (int)sl.size();
+  return fft_merged(P, sl, inv) ? 1 : (int)sl.size();
 }
 
 template <typename real>
@@ -777,6 +788,20 @@ static cudaError_t run_fft(Plan& P, bool inv, const void* in, void* out, int mod
   StageTimer timer(P, inv ? ST_FFT_I : ST_FFT_F, s);
   std::vector<FftSlice> sl;
   fft_slices(P, sl, inv);
+  if (fft_merged(P, sl, inv)) {
+    int count = 0, max_n2 = 0;
+    for (const FftSlice& f : sl) {
+      count += f.count;
+      max_n2 = std::max(max_n2, f.n2);
+    }
+    Fft16Args a16 = {P.d_segs, P.d_fn_samp, inv ? P.d_fft_inv : P.d_fft_fwd, P.d_tab, in, out, P.d_w1,
+                     fft_jp(P, sl[0].B, inv), mode, 0, (!inv && P.d_amax) ? P.d_amax + AMAX_EO * P.nfn : nullptr};
+    cudaError_t e = cudaSuccess;
+    fft16_launch_multi(inv, a16, max_n2, count, s, &e);
+    if (e != cudaSuccess) return e;
+    timer.finish();
+    return cudaSuccess;
+  }
   for (const FftSlice& f : sl) {
     FftArgs a;
     a.segs = P.d_segs;

@@ -251,6 +251,11 @@ struct Plan {
   // forward radial stage (its MMA tile width; 32, 48 or 64)
   int simt_policy[4] = {0, 0, 0, 0};
   int rad_rows = 64;
+  // plans of several register-FFT sizes: one multi-size phi-FFT launch per
+  // direction (1) or one launch per size (0)
+  int fft_merge = 1;
+  // work-queue slices per CTA of the tensor-core forward stages (1, 2 or 4)
+  int queue_slices = 2;
   std::string tuning;
 
   // FP16x3 plans: per-function largest magnitudes [AMAX_SLOTS][nfn] (segment
@@ -385,6 +390,9 @@ template <typename real>
 bool fft16_launch(bool inv, const Fft16Args& a, int n1, int n2, int nctas, cudaStream_t s, cudaError_t* err);
 // Whether the register FFT takes rings of 2B = n1 * n2 (fft16.cu).
 bool fft16_handles(bool fp64, bool pairs, int n1, int n2);
+// One launch of the multi-size register FFT (FP32 complex samples) over
+// nctas CTAs of segments with n2 <= max_n2; false when it does not apply.
+bool fft16_launch_multi(bool inv, const Fft16Args& a, int max_n2, int nctas, cudaStream_t s, cudaError_t* err);
 
 // Packs the host tables of every segment of P into one array of the plan's
 // real type, at the offsets recorded in the segment descriptors (api.cu).

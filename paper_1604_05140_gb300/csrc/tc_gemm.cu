@@ -109,7 +109,13 @@ struct SegSmall {
 
 struct TcArgs {
   const int2* tiles;            // (group | segment << 20, row0), groups in order
-  const int* cta_first;         // tile slice of each CTA (gridDim.x + 1 offsets)
+  const int* slice_first;       // first tile of each slice (nslices + 1 offsets)
+  int nslices;                  // slices of the work queue
+  int slice_cap;                // most tiles of one slice (shared-memory capacity)
+  int group_cap;                // most groups one slice's tiles span (groups without
+                                // tiles in between count: a slice may span more groups
+                                // than it has tiles)
+  int* queue;                   // next slice to take; zero at launch
   int ntiles;
   const unsigned char* tabimg;  // pre-swizzled hi/lo tables
   const int64_t* grp_off;       // byte offset of each group's image (weighted set, then plain set)
@@ -155,19 +161,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   uint64_t* drain = bars + 62;           // [2] MMA issuers' own barriers, used after an abort
   uint32_t* issued = (uint32_t*)(bars + 61);  // producer: [copies issued into the ring, table copies]
-  // per-CTA copies of the tile slice, of the segments and of the metadata of
-  // the groups the slice touches, so that no role waits on a global load per
-  // tile
-  const int g_begin = a.cta_first[blockIdx.x];
-  const int g_end = a.cta_first[blockIdx.x + 1];
-  const int t_begin = 0, t_end = g_end - g_begin;
-  const int g_lo = t_end > 0 ? (a.tiles[g_begin].x & 0xFFFFF) : 0;
-  const int ngr = t_end > 0 ? (a.tiles[g_end - 1].x & 0xFFFFF) - g_lo + 1 : 0;
+  // Work queue: the tile list is cut into a.nslices contiguous slices of
+  // about equal estimated cost; each CTA takes the next slice from a global
+  // counter (cleared before the launch) until none is left.  Per slice the
+  // CTA copies the slice's tiles and the metadata of the groups they touch
+  // to shared memory (fixed capacity a.slice_cap), so that no role waits on
+  // a global load per tile; the segments are copied once.  The roles' barrier
+  // phase counters carry over from slice to slice through s_cnt.
   SegSmall* s_seg = (SegSmall*)(bars + 64);                // [nseg]
-  int64_t* s_off = (int64_t*)(s_seg + a.nseg);              // [ngr] table image offsets
-  int* s_npad = (int*)(s_off + ngr);                        // [ngr] padded N (| l, n0 for radial)
-  int* s_exp = s_npad + ngr;                                 // [ngr] FP16x3 table exponents
-  int4* s_tiles = (int4*)(((uintptr_t)(s_exp + ngr) + 15) & ~(uintptr_t)15);  // [slice] (group, row0, segment)
+  const int cap = a.slice_cap, gcap = a.group_cap;           // most tiles, groups of one slice
+  int64_t* s_off = (int64_t*)(s_seg + a.nseg);              // [gcap] table image offsets
+  int* s_npad = (int*)(s_off + gcap);                       // [gcap] padded N (| l, n0 for radial)
+  int* s_exp = s_npad + gcap;                                // [gcap] FP16x3 table exponents
+  int4* s_tiles = (int4*)(((uintptr_t)(s_exp + gcap) + 15) & ~(uintptr_t)15);  // [cap] (group, row0, segment)
+  // [0, 1] producer chunks and tables; [2 + 3k, 3 + 3k, 4 + 3k] MMA issuer k
+  // chunks, tiles, tables; [8] split chunks; [9] epilogue tiles
+  uint32_t* s_cnt = (uint32_t*)(bars + 48);
+  volatile int* s_slice = (volatile int*)(bars + 53);      // the slice being worked on
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Per tile two pairs of a main accumulator (hi*hi) and a correction
@@ -197,13 +207,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
     mbar_init(drain, 1);
     mbar_init(drain + 1, 1);
     issued[0] = issued[1] = 0u;
+    for (int k = 0; k < 10; ++k) s_cnt[k] = 0u;
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
-  // contiguous tile range of this CTA (re-based to 0 in shared memory), group
-  // indices re-based to g_lo
+  for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) {
+    const TcSegInfo& g = a.segs[k];
+    s_seg[k] = SegSmall{g.B, g.NB, g.KC, g.fn0, g.w2_off, g.g0, g.bw, g.bp, 0};
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tmem_slot;
   const int64_t wsel = a.weighted ? 0 : a.ngroups;
+
+  for (;;) {
+  if (threadIdx.x == 0) *s_slice = atomicAdd(a.queue, 1);
+  __syncthreads();
+  const int sl = *s_slice;
+  if (sl >= a.nslices || *abort_flag) break;
+  // the slice's tile range (re-based to 0 in shared memory), group indices
+  // re-based to g_lo
+  const int g_begin = a.slice_first[sl];
+  const int g_end = a.slice_first[sl + 1];
+  const int t_begin = 0, t_end = g_end - g_begin;
+  const int g_lo = t_end > 0 ? (a.tiles[g_begin].x & 0xFFFFF) : 0;
+  const int ngr = t_end > 0 ? (a.tiles[g_end - 1].x & 0xFFFFF) - g_lo + 1 : 0;
   for (int k = threadIdx.x; k < t_end; k += blockDim.x) {
     const int2 tl = a.tiles[g_begin + k];
     s_tiles[k] = make_int4((tl.x & 0xFFFFF) - g_lo, tl.y, tl.x >> 20, 0);
@@ -213,20 +243,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
     s_npad[k] = a.grp_npad[g_lo + k];
     s_exp[k] = F16 ? a.grp_exp[wsel + g_lo + k] : 0;
   }
-  for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) {
-    const TcSegInfo& g = a.segs[k];
-    s_seg[k] = SegSmall{g.B, g.NB, g.KC, g.fn0, g.w2_off, g.g0, g.bw, g.bp, 0};
-  }
   tc_before();
   __syncthreads();
   tc_after();
-  const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
     // ---------------- producer ----------------
     if (lane == 0) {
-      int cur = -1, ngrp = 0, cur_seg = -1;
-      uint32_t c = 0;
+      int cur = -1, ngrp = (int)s_cnt[1], cur_seg = -1;
+      uint32_t c = s_cnt[0];
       for (int t = t_begin; t < t_end && !*abort_flag; ++t) {
         const int4 tl = s_tiles[t];
         const SegSmall sg = s_seg[tl.z];
@@ -258,15 +283,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
           tma_load_2d(xs + s * 2 * kChunkBytes, xmap, full + s, kc * 32, (int)row);
         }
       }
-      issued[0] = c;
-      issued[1] = (uint32_t)ngrp;
+      issued[0] = s_cnt[0] = c;
+      issued[1] = s_cnt[1] = (uint32_t)ngrp;
     }
   } else if (warp == 1 || warp == kMma2Warp) {
     // ---------------- MMA issuers: K steps of parity `me` ----------------
     if (lane == 0) {
       const int me = warp == 1 ? 0 : 1;
-      int cur = -1, ngrp = 0;
-      uint32_t c = 0, tcount = 0;
+      int cur = -1, ngrp = (int)s_cnt[4 + 3 * me];
+      uint32_t c = s_cnt[2 + 3 * me], tcount = s_cnt[3 + 3 * me];
       // TF32: X_hi in place of the raw chunk, X_lo in the second half of the
       // stage; BF16: X_hi and X_lo (8 KB each) in the second half
       const uint64_t xdesc0 = BF ? sw64_desc(smem_u32(xs + kChunkBytes)) : sw128_desc(smem_u32(xs));
@@ -317,6 +342,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
         const bool last_of_group = (t + 1 >= t_end) || (s_tiles[t + 1].x != cur);
         if (last_of_group) mma_commit(tabe);
       }
+      s_cnt[2 + 3 * me] = c;
+      s_cnt[3 + 3 * me] = tcount;
+      s_cnt[4 + 3 * me] = (uint32_t)ngrp;
     }
   } else if (warp < kFirstEpiWarp) {
     // ---------------- split: X -> (hi, lo) ----------------
@@ -336,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
       }
     };
     (void)split_amax_load;
-    uint32_t c = 0;
+    uint32_t c = s_cnt[8];
     for (int t = t_begin; t < t_end; ++t) {
       bool ok = true;
       const int KC = s_seg[s_tiles[t].z].KC;
@@ -399,12 +427,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
       }
       if (!ok) break;
     }
+    if (tid == 0) s_cnt[8] = c;
   } else {
     // ---------------- epilogue ----------------
     const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
     const int ehalf = (warp - kFirstEpiWarp) >> 2;  // which 16-column blocks
     const int r_in = quarter * 32 + lane;       // tile row of this thread
-    uint32_t tcount = 0;
+    uint32_t tcount = s_cnt[9];
     float* Y = reinterpret_cast<float*>(a.y);
     for (int t = t_begin; t < t_end; ++t, ++tcount) {
       const int4 tl = s_tiles[t];
@@ -509,7 +538,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
       tc_before();
       mbar_arrive(acce + acc);
     }
+    if (threadIdx.x == 32 * kFirstEpiWarp) s_cnt[9] = tcount;
   }
+  // the slice is done in every role: its shared-memory copies may be replaced
+  tc_before();
+  __syncthreads();
+  tc_after();
+  }  // slices
 
   // Every role has left its loop.  After an abort (whichever role gave up,
   // and when) the producer waits, bounded, for the copies it issued and each
@@ -538,7 +573,9 @@ namespace {
 // plan, run as one launch.
 struct TcStage {
   int2* d_tiles = nullptr;
-  int* d_first = nullptr;
+  int* d_first = nullptr;       // slice offsets of the work queue
+  int* d_queue = nullptr;       // the queue's counter
+  int nslices = 0, cap = 0, gcap = 0;
   int ntiles = 0;
   int64_t* d_off = nullptr;
   int* d_npad = nullptr;
@@ -840,16 +877,32 @@ static cudaError_t tc_prepare_impl(Plan& P) {
     const int stages = k == 0 ? kStagesLeg : kStagesRad;
     const size_t fixed = 1024 + (size_t)2 * S.KCmax * S.npmax * (bf ? 64 : 128) + (size_t)stages * 2 * kChunkBytes +
                          64 * 8 + (size_t)S.nseg * sizeof(SegSmall) + 16 + 12 + 16;
-    const size_t per_tile = 16 + 16;
-    S.grid = S.ntiles < nsm ? S.ntiles : nsm;
+    // work queue: P.queue_slices cost-balanced slices per CTA of one wave
+    // (more while one slice's shared-memory copies would not fit)
+    // shared memory per slice: 16 bytes a tile, 16 bytes a group the tiles
+    // span (counted exactly: groups without tiles may lie in between)
+    S.grid = std::max(1, std::min(S.ntiles, nsm));
+    S.nslices = std::max(1, std::min(S.ntiles, S.grid * P.queue_slices));
+    auto group_span = [&](const std::vector<int>& fst) {
+      int g = 1;
+      for (int k = 0; k < (int)fst.size() - 1; ++k)
+        if (fst[k + 1] > fst[k])
+          g = std::max(g, (pd.tiles[fst[k + 1] - 1].x & 0xFFFFF) - (pd.tiles[fst[k]].x & 0xFFFFF) + 1);
+      return g;
+    };
     int max_tiles = 0;
-    std::vector<int> first = balance_slices(pd.cost, S.grid > 0 ? S.grid : 1, &max_tiles);
-    while (fixed + (size_t)max_tiles * per_tile > 227 * 1024 && S.grid < S.ntiles) {
-      S.grid = std::min(S.ntiles, S.grid + nsm);
-      first = balance_slices(pd.cost, S.grid, &max_tiles);
+    std::vector<int> first = balance_slices(pd.cost, S.nslices, &max_tiles);
+    int max_groups = group_span(first);
+    while (fixed + (size_t)max_tiles * 16 + (size_t)max_groups * 16 > 227 * 1024 && S.nslices < S.ntiles) {
+      S.nslices = std::min(S.ntiles, S.nslices + S.grid);
+      first = balance_slices(pd.cost, S.nslices, &max_tiles);
+      max_groups = group_span(first);
     }
-    S.smem = fixed + (size_t)max_tiles * per_tile;
+    S.cap = std::max(1, max_tiles);
+    S.gcap = max_groups;
+    S.smem = fixed + (size_t)S.cap * 16 + (size_t)S.gcap * 16;
     if (e == cudaSuccess) e = upload(&S.d_first, first);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&S.d_queue, sizeof(int));
     if (e == cudaSuccess && S.smem > 227 * 1024) e = cudaErrorInvalidValue;
   }
   P.tc_state = st;
@@ -864,7 +917,7 @@ void tc_release(Plan& P) {
   TcState* st = (TcState*)P.tc_state;
   if (!st) return;
   for (TcStage* S : {&st->leg, &st->rad}) {
-    void* ptrs[] = {S->d_tiles, S->d_first, S->d_off, S->d_npad, S->d_exp, S->d_segs};
+    void* ptrs[] = {S->d_tiles, S->d_first, S->d_queue, S->d_off, S->d_npad, S->d_exp, S->d_segs};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
@@ -883,7 +936,11 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
   if (S.ntiles > 0) {
     TcArgs a;
     a.tiles = S.d_tiles;
-    a.cta_first = S.d_first;
+    a.slice_first = S.d_first;
+    a.nslices = S.nslices;
+    a.slice_cap = S.cap;
+    a.group_cap = S.gcap;
+    a.queue = S.d_queue;
     a.ntiles = S.ntiles;
     a.tabimg = st->d_img;
     a.grp_off = S.d_off;
@@ -917,6 +974,7 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
                        : tc_gemm_kernel<TC_RAD_F, kStagesRad, TC_OP_TF32>;
     }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.d_queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     fn<<<S.grid, kThreads, S.smem, s>>>(a);
     e = cudaGetLastError();

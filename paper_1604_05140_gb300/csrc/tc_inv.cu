@@ -131,7 +131,9 @@ struct LegIArgs {
   // and (table image offset, S row of the P block, S row of the Q block, 0);
   // ordered by (segment, m_idx, half, row0)
   const int4* tiles;
-  const int* cta_first;       // tile slice of each CTA (gridDim.x + 1 offsets)
+  const int* slice_first;     // first tile of each work-queue slice (nslices + 1 offsets)
+  int nslices;
+  int* queue;                 // next slice to take; zero at launch
   int ntiles;
   const unsigned char* tabimg;
   const LegISeg* segs;
@@ -172,10 +174,16 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   uint64_t* drain = bars + 62;                  // [2] MMA issuers' own barriers, used after an abort
   uint32_t* issued = (uint32_t*)(bars + 61);  // producer: [copies issued into the ring, table copies]
-  // the segments and the tile slice (two records per tile), copied once to
-  // shared memory
+  // the segments, copied once, and the tiles of the current slice of the
+  // work queue (two records per tile, capacity a.slice_cap), copied per slice
+  // (see tc_gemm_kernel: slices from a global counter, role counters carried
+  // over through s_cnt)
   LegISegSmall* s_seg = (LegISegSmall*)(bars + 64);
   int4* s_tiles = (int4*)(((uintptr_t)(s_seg + a.nseg) + 15) & ~(uintptr_t)15);
+  // [0, 1] producer copies and tables; [2 + 3p, 3 + 3p, 4 + 3p] MMA issuer p
+  // chunks, tiles, tables; [8] split chunks; [9] epilogue tiles
+  uint32_t* s_cnt = (uint32_t*)(bars + 48);
+  volatile int* s_slice = (volatile int*)(bars + 53);
   for (int k = threadIdx.x; k < a.nseg; k += blockDim.x) {
     const LegISeg& g = a.segs[k];
     s_seg[k] = LegISegSmall{g.B, g.NB, g.npad, g.fn0, g.sb, 0, g.w1_off};
@@ -202,25 +210,35 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
     mbar_init(drain, 1);
     mbar_init(drain + 1, 1);
     issued[0] = issued[1] = 0u;
+    for (int k = 0; k < 10; ++k) s_cnt[k] = 0u;
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
-  const int g_begin = a.cta_first[blockIdx.x];
-  const int nt = a.cta_first[blockIdx.x + 1] - g_begin;
-  for (int k = threadIdx.x; k < 2 * nt; k += blockDim.x) s_tiles[k] = a.tiles[2 * g_begin + k];
   tc_before();
   __syncthreads();
   tc_after();
   const uint32_t tmem = *tmem_slot;
+
+  for (;;) {
+  if (threadIdx.x == 0) *s_slice = atomicAdd(a.queue, 1);
+  __syncthreads();
+  const int sl = *s_slice;
+  if (sl >= a.nslices || *abort_flag) break;
+  const int g_begin = a.slice_first[sl];
+  const int nt = a.slice_first[sl + 1] - g_begin;
+  for (int k = threadIdx.x; k < 2 * nt; k += blockDim.x) s_tiles[k] = a.tiles[2 * g_begin + k];
+  tc_before();
+  __syncthreads();
+  tc_after();
   // tile t: s_tiles[2t] = (m_idx, row0, half | seg << 8, KC_P | KC_Q << 8),
   //         s_tiles[2t+1] = (table image offset, S row of P, S row of Q, 0);
   // the resident table changes with its image offset
 
   if (warp == 0) {
     if (lane == 0) {
-      int cur = -1, ngrp = 0, cur_seg = -1;
-      uint32_t c = 0;
+      int cur = -1, ngrp = (int)s_cnt[1], cur_seg = -1;
+      uint32_t c = s_cnt[0];
       for (int t = 0; t < nt && !*abort_flag; ++t) {
         const int4 ta = s_tiles[2 * t], tb = s_tiles[2 * t + 1];
         const int seg = ta.z >> 8;
@@ -252,15 +270,15 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
         }
         if (!ok) break;
       }
-      issued[0] = c;
-      issued[1] = (uint32_t)ngrp;
+      issued[0] = s_cnt[0] = c;
+      issued[1] = s_cnt[1] = (uint32_t)ngrp;
     }
   } else if (warp == 1 || warp == kMma2Warp) {
     // MMA issuer `me` takes the chunks of parity p = me (P or Q accumulators)
     if (lane == 0) {
       const int p = warp == 1 ? 0 : 1;
-      int cur = -1, ngrp = 0;
-      uint32_t c = 0, tcount = 0;
+      int cur = -1, ngrp = (int)s_cnt[4 + 3 * p];
+      uint32_t c = s_cnt[2 + 3 * p], tcount = s_cnt[3 + 3 * p];
       // the table image stacks nh hi rows over nh lo rows per K chunk: one
       // MMA of width 2 nh gives [X_hi T_hi | X_hi T_lo], a second of width nh
       // adds X_lo T_hi to the correction
@@ -327,6 +345,9 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
         mma_commit(accf + acc);
         if (t + 1 >= nt || s_tiles[2 * t + 3].x != cur) mma_commit(tabe);
       }
+      s_cnt[2 + 3 * p] = c;
+      s_cnt[3 + 3 * p] = tcount;
+      s_cnt[4 + 3 * p] = (uint32_t)ngrp;
     }
   } else if (warp < kFirstEpiWarp) {
     // staging [32 l'][128 rows] -> K-major hi/lo rows; thread (r, h) converts
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
     };
     unsigned amx = 0u;
     if (F16 && nt > 0) amx = row_amax(0);
-    uint32_t c = 0;
+    uint32_t c = s_cnt[8];
     for (int t = 0; t < nt; ++t) {
       const int kcw = s_tiles[2 * t].w;
       const int kcp = kcw & 0xff, kcq = kcw >> 8;
@@ -372,11 +393,12 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
       }
       if (!ok) break;
     }
+    if (tid == 0) s_cnt[8] = c;
   } else {
     const int quarter = warp & 3;
     const int ehalf = (warp - kFirstEpiWarp) >> 2;  // alternate 16-column blocks
     const int r_in = quarter * 32 + lane;
-    uint32_t tcount = 0;
+    uint32_t tcount = s_cnt[9];
     for (int t = 0; t < nt; ++t, ++tcount) {
       const int4 ta = s_tiles[2 * t];
       const int acc = tcount & 1;
@@ -444,7 +466,13 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
       tc_before();
       mbar_arrive(acce + acc);
     }
+    if (threadIdx.x == 32 * kFirstEpiWarp) s_cnt[9] = tcount;
   }
+  // the slice is done in every role: its shared-memory copies may be replaced
+  tc_before();
+  __syncthreads();
+  tc_after();
+  }  // slices
   // Every role has left its loop.  After an abort the producer waits,
   // bounded, for the copies it issued and each MMA issuer for its MMAs,
   // before shared and tensor memory are released.
@@ -483,7 +511,10 @@ struct RadISeg {
 
 struct RadIArgs {
   const int4* tiles;          // (l, col0 | narrow, segment, table image offset of l), by segment and l
-  const int* cta_first;       // tile slice of each CTA (gridDim.x + 1 offsets)
+  const int* slice_first;     // first tile of each work-queue slice (nslices + 1 offsets)
+  int nslices;
+  int slice_cap;              // most tiles of one slice
+  int* queue;                 // next slice to take; zero at launch
   int ntiles;
   const unsigned char* tabimg;
   const RadISeg* segs;
@@ -565,29 +596,18 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   uint64_t* drain = bars + 62;              // [2] MMA issuers' own barriers, used after an abort
   uint32_t* issued = (uint32_t*)(bars + 61);  // producer: [copies issued into the ring, table copies]
-  // the tile slice, the segments it touches (seg_lo ..) and their S row
-  // offsets, copied once to shared memory
-  const int g_begin = a.cta_first[blockIdx.x];
-  const int nt = a.cta_first[blockIdx.x + 1] - g_begin;
-  const int seg_lo = nt > 0 ? a.tiles[g_begin].z : 0;
-  const int nseg_cta = nt > 0 ? a.tiles[g_begin + nt - 1].z - seg_lo + 1 : 0;
-  RadISeg* s_seg = (RadISeg*)(bars + 64);                  // [nseg_cta]
-  int* s_sib = (int*)(s_seg + (nseg_cta > 0 ? nseg_cta : 1));  // [nseg_cta] first entry in s_si
-  int64_t* s_si = (int64_t*)(((uintptr_t)(s_sib + (nseg_cta > 0 ? nseg_cta : 1)) + 7) & ~(uintptr_t)7);  // [si_max]
-  int4* s_tiles = (int4*)(((uintptr_t)(s_si + a.si_max) + 15) & ~(uintptr_t)15);
-  if (threadIdx.x == 0) {
-    int e = 0;
-    for (int k = 0; k < nseg_cta; ++k) {
-      s_seg[k] = a.segs[seg_lo + k];
-      s_sib[k] = e;
-      e += 2 * (2 * s_seg[k].B - 1);
-    }
-  }
-  __syncthreads();
-  for (int k = 0; k < nseg_cta; ++k) {
-    const int n = 2 * (2 * s_seg[k].B - 1);
-    for (int q = threadIdx.x; q < n; q += blockDim.x) s_si[s_sib[k] + q] = a.si_rows[s_seg[k].si0 + q];
-  }
+  // Work queue (see tc_gemm_kernel): per slice the slice's tiles, the
+  // segments they touch (seg_lo ..) and those segments' S row offsets are
+  // copied to shared memory (capacities a.nseg segments, a.si_max offsets,
+  // a.slice_cap tiles); role counters carry over through s_cnt.
+  RadISeg* s_seg = (RadISeg*)(bars + 64);                  // [nseg]
+  int* s_sib = (int*)(s_seg + a.nseg);                      // [nseg] first entry in s_si
+  int64_t* s_si = (int64_t*)(((uintptr_t)(s_sib + a.nseg) + 7) & ~(uintptr_t)7);  // [si_max]
+  int4* s_tiles = (int4*)(((uintptr_t)(s_si + a.si_max) + 15) & ~(uintptr_t)15);  // [slice_cap]
+  // [0] producer table copies; [1 + 2k, 2 + 2k] MMA issuer k chunks, tiles;
+  // [5] gather chunks; [6] epilogue tiles
+  uint32_t* s_cnt = (uint32_t*)(bars + 48);
+  volatile int* s_slice = (volatile int*)(bars + 53);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tmem_cols = 512;  // 2 buffers x 256 columns
@@ -604,10 +624,38 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     mbar_init(drain, 1);
     mbar_init(drain + 1, 1);
     issued[0] = issued[1] = 0u;
+    for (int k = 0; k < 8; ++k) s_cnt[k] = 0u;
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, tmem_cols);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tmem_slot;
+
+  for (;;) {
+  if (threadIdx.x == 0) *s_slice = atomicAdd(a.queue, 1);
+  __syncthreads();
+  const int sl = *s_slice;
+  if (sl >= a.nslices || *abort_flag) break;
+  const int g_begin = a.slice_first[sl];
+  const int nt = a.slice_first[sl + 1] - g_begin;
+  const int seg_lo = nt > 0 ? a.tiles[g_begin].z : 0;
+  const int nseg_cta = nt > 0 ? a.tiles[g_begin + nt - 1].z - seg_lo + 1 : 0;
+  if (threadIdx.x == 0) {
+    int e = 0;
+    for (int k = 0; k < nseg_cta; ++k) {
+      s_seg[k] = a.segs[seg_lo + k];
+      s_sib[k] = e;
+      e += 2 * (2 * s_seg[k].B - 1);
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < nseg_cta; ++k) {
+    const int n = 2 * (2 * s_seg[k].B - 1);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) s_si[s_sib[k] + q] = a.si_rows[s_seg[k].si0 + q];
+  }
   for (int k = threadIdx.x; k < nt; k += blockDim.x) {
     int4 tl = a.tiles[g_begin + k];
     tl.z -= seg_lo;  // segment within this CTA's copy
@@ -616,11 +664,10 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
   tc_before();
   __syncthreads();
   tc_after();
-  const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
     if (lane == 0) {
-      uint32_t c = 0;
+      uint32_t c = s_cnt[0];
       for (int t = 0; t < nt && !*abort_flag; ++t) {
         const int4 tl = s_tiles[t];
         const int l = tl.x;
@@ -637,14 +684,14 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
         }
         if (!ok) break;
       }
-      issued[0] = c;
+      issued[0] = s_cnt[0] = c;
     }
   } else if (warp == 1 || warp == kMma2Warp) {
     // MMA issuer `me`: narrow tiles, the K steps of parity me into
     // [main_me | corr_me]; wide tiles, the columns 64 me .. 64 me + 63
     if (lane == 0) {
       const int me = warp == 1 ? 0 : 1;
-      uint32_t c = 0, tcount = 0;
+      uint32_t c = s_cnt[1 + 2 * me], tcount = s_cnt[2 + 2 * me];
       const uint64_t sdesc0 = BF ? sw64_desc(smem_u32(st)) : sw128_desc(smem_u32(st));
       // B operand of each half: 64 hi rows over 64 lo rows.  One MMA of width
       // 128 gives [T_hi X_hi | T_hi X_lo], a second of width 64 adds T_lo X_hi.
@@ -712,6 +759,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
         if (!ok) break;
         mma_commit(accf + acc);
       }
+      s_cnt[1 + 2 * me] = c;
+      s_cnt[2 + 2 * me] = tcount;
     }
   } else if (warp < kFirstEpiWarp) {
     // gather: thread (column, h) copies 16 (wide) or 8 (narrow) consecutive
@@ -725,9 +774,11 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       const int f = rad_fn_of(s_seg[s_tiles[tt].z], s_tiles[tt], tid);
       return f >= 0 ? a.fn_coef[f] : 0;
     };
-    // copy cursor: tile ti, chunk kci, chunks issued ci
+    // copy cursor: tile ti, chunk kci, chunks issued ci (starting from the
+    // chunks consumed before this slice, so that slots and stages line up)
+    const uint32_t c_begin = s_cnt[5];
     int ti = 0, kci = 0;
-    uint32_t ci = 0;
+    uint32_t ci = c_begin;
     int64_t fco_i = 0, fco_n = 0;  // tiles ti and ti + 1
     if (nt > 0) {
       fco_i = fetch_fco(0);
@@ -760,7 +811,8 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     unsigned amx = 0u;
     if (F16 && nt > 0) amx = col_amax(0);
     float xf = 0.f;
-    for (uint32_t c = 0; t < nt; ++c) {
+    uint32_t c = c_begin;
+    for (; t < nt; ++c) {
       const int4 tl = s_tiles[t];
       const bool nar = tl.y & 1;
       if constexpr (F16) {
@@ -805,12 +857,13 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       t = tn;
       kc = kcn_next;
     }
-    cp_async_wait_all();  // no copy may land after the CTA has left
+    cp_async_wait_all();  // no copy may land after the CTA has left (or the slice is replaced)
+    if (tid == 0) s_cnt[5] = c;
   } else {
     const int quarter = warp & 3;
     const int ehalf = (warp - kFirstEpiWarp) >> 2;  // alternate 16-column blocks
     const int i = quarter * 32 + lane;   // TMEM lane = radius index
-    uint32_t tcount = 0;
+    uint32_t tcount = s_cnt[6];
     for (int t = 0; t < nt; ++t, ++tcount) {
       const int4 tl = s_tiles[t];
       const int acc = tcount & 1;
@@ -888,7 +941,13 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       tc_before();
       mbar_arrive(acce + acc);
     }
+    if (threadIdx.x == 32 * kFirstEpiWarp) s_cnt[6] = tcount;
   }
+  // the slice is done in every role: its shared-memory copies may be replaced
+  tc_before();
+  __syncthreads();
+  tc_after();
+  }  // slices
   // Every role has left its loop (the gather threads have waited for their
   // asynchronous copies).  After an abort the producer waits, bounded, for
   // the table copies it issued and each MMA issuer for its MMAs, before
@@ -1014,15 +1073,17 @@ struct TcInvState {
   unsigned char* d_img = nullptr;
   // Legendre synthesis
   int4* leg_tiles = nullptr;      // two records per tile
-  int* leg_first = nullptr;
+  int* leg_first = nullptr;       // work-queue slice offsets
+  int* leg_queue = nullptr;       // the queue's counter
   LegISeg* leg_segs = nullptr;
-  int leg_ntiles = 0, leg_grid = 0, npad_max = 16, kcmax = 1;
+  int leg_ntiles = 0, leg_grid = 0, leg_nslices = 0, npad_max = 16, kcmax = 1;
   size_t leg_smem = 0;
   // radial
   int4* rad_tiles = nullptr;
   int* rad_first = nullptr;
+  int* rad_queue = nullptr;
   RadISeg* rad_segs = nullptr;
-  int rad_ntiles = 0, rad_grid = 0, si_max = 0;
+  int rad_ntiles = 0, rad_grid = 0, rad_nslices = 0, rad_cap = 0, si_max = 0;
   size_t rad_smem = 0;
   std::vector<int64_t> l_off;     // image offset of the radial table of (segment, l)
   std::vector<int> l_base;        // first entry of each segment in l_off
@@ -1040,16 +1101,18 @@ static cudaError_t upload(T** dst, const std::vector<T>& v, int64_t& bytes) {
   return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-// Grid for a tile list: cost-balanced slices of one wave of CTAs, more waves
-// while the largest slice's share of shared memory does not fit.
-static std::vector<int> slices_for(const std::vector<double>& cost, int nsm, size_t fixed, size_t per_tile,
-                                   int* grid, int* max_tiles) {
+// Work queue of a tile list: one wave of CTAs taking `per_cta` cost-balanced
+// slices each on average, more slices while the largest one's share of shared
+// memory does not fit.
+static std::vector<int> slices_for(const std::vector<double>& cost, int nsm, int per_cta, size_t fixed,
+                                   size_t per_tile, int* grid, int* nslices, int* max_tiles) {
   const int n = (int)cost.size();
   *grid = std::max(1, std::min(n, nsm));
-  std::vector<int> first = balance_slices(cost, *grid, max_tiles);
-  while (fixed + (size_t)*max_tiles * per_tile > 227 * 1024 && *grid < n) {
-    *grid = std::min(n, *grid + nsm);
-    first = balance_slices(cost, *grid, max_tiles);
+  *nslices = std::max(1, std::min(n, *grid * per_cta));
+  std::vector<int> first = balance_slices(cost, *nslices, max_tiles);
+  while (fixed + (size_t)*max_tiles * per_tile > 227 * 1024 && *nslices < n) {
+    *nslices = std::min(n, *nslices + *grid);
+    first = balance_slices(cost, *nslices, max_tiles);
   }
   return first;
 }
@@ -1080,25 +1143,30 @@ static cudaError_t radi_tiles(const Plan& P, TcInvState& st, int nsm, int64_t& b
   // slice; more waves of CTAs while that does not fit
   const size_t fixed = 1024 + (size_t)kStagesRadI * 4 * kChunk + (size_t)kGatherSlots * kGatherSlotBytes + 64 * 8 +
                        (P.segs.size() + 1) * (sizeof(RadISeg) + 4) + 8 + 16;
+  // work queue: P.queue_slices cost-balanced slices per CTA of one wave, more
+  // while a slice's copies do not fit
   const int n = (int)rc.size();
   st.rad_grid = std::max(1, std::min(n, nsm));
+  st.rad_nslices = std::max(1, std::min(n, st.rad_grid * P.queue_slices));
   std::vector<int> rf;
   for (;;) {
     int rmax = 0;
-    rf = balance_slices(rc, st.rad_grid, &rmax);
+    rf = balance_slices(rc, st.rad_nslices, &rmax);
     int si_max = 0;
-    for (int k = 0; k < st.rad_grid; ++k) {
+    for (int k = 0; k < st.rad_nslices; ++k) {
       if (rf[k + 1] <= rf[k]) continue;
       int need = 0;
       for (int sg = rtiles[rf[k]].z; sg <= rtiles[rf[k + 1] - 1].z; ++sg) need += 2 * (2 * P.segs[sg].B - 1);
       si_max = std::max(si_max, need);
     }
     st.si_max = si_max;
-    st.rad_smem = fixed + (size_t)si_max * 8 + (size_t)(rmax + 1) * 16;
-    if (st.rad_smem <= 227 * 1024 || st.rad_grid >= n) break;
-    st.rad_grid = std::min(n, st.rad_grid + nsm);
+    st.rad_cap = std::max(1, rmax);
+    st.rad_smem = fixed + (size_t)si_max * 8 + (size_t)(st.rad_cap + 1) * 16;
+    if (st.rad_smem <= 227 * 1024 || st.rad_nslices >= n) break;
+    st.rad_nslices = std::min(n, st.rad_nslices + st.rad_grid);
   }
   if (e == cudaSuccess) e = upload(&st.rad_first, rf, bytes);
+  if (e == cudaSuccess && !st.rad_queue) e = cudaMalloc((void**)&st.rad_queue, sizeof(int));
   if (e == cudaSuccess && st.rad_smem > 227 * 1024) e = cudaErrorInvalidValue;
   return e;
 }
@@ -1115,7 +1183,7 @@ cudaError_t tc_radi_retile(Plan& P) {
   }
   if (st->rad_first) {
     cudaFree(st->rad_first);
-    P.bytes -= (int64_t)(st->rad_grid + 1) * sizeof(int);
+    P.bytes -= (int64_t)(st->rad_nslices + 1) * sizeof(int);
   }
   st->rad_tiles = nullptr;
   st->rad_first = nullptr;
@@ -1242,8 +1310,10 @@ cudaError_t tc_inv_prepare(Plan& P) {
   const size_t lfixed = 1024 + (size_t)st->kcmax * 2 * nhm * (bf ? 64 : 128) + (size_t)kStagingLegI * kChunk +
                         (size_t)kStagesLegI * 2 * kChunk + 64 * 8 + lsegs.size() * sizeof(LegISegSmall) + 16;
   int lmax = 0;
-  const std::vector<int> lf = slices_for(lcost, nsm, lfixed, 32, &st->leg_grid, &lmax);
+  const std::vector<int> lf =
+      slices_for(lcost, nsm, P.queue_slices, lfixed, 32, &st->leg_grid, &st->leg_nslices, &lmax);
   if (e == cudaSuccess) e = upload(&st->leg_first, lf, bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&st->leg_queue, sizeof(int));
   st->leg_smem = lfixed + (size_t)(lmax + 1) * 32;
   if (e == cudaSuccess && st->leg_smem > 227 * 1024) e = cudaErrorInvalidValue;
   if (e == cudaSuccess) e = radi_tiles(P, *st, nsm, bytes);
@@ -1254,8 +1324,8 @@ cudaError_t tc_inv_prepare(Plan& P) {
 void tc_inv_release(Plan& P) {
   TcInvState* st = (TcInvState*)P.tc_inv_state;
   if (!st) return;
-  void* ptrs[] = {st->d_img,     st->leg_tiles, st->leg_first, st->leg_segs,
-                  st->rad_tiles, st->rad_first, st->rad_segs, st->rad_texp};
+  void* ptrs[] = {st->d_img,     st->leg_tiles, st->leg_first, st->leg_queue, st->leg_segs,
+                  st->rad_tiles, st->rad_first, st->rad_queue, st->rad_segs, st->rad_texp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete st;
@@ -1271,7 +1341,10 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
   if (prob == 2 && st->rad_ntiles > 0) {
     RadIArgs a;
     a.tiles = st->rad_tiles;
-    a.cta_first = st->rad_first;
+    a.slice_first = st->rad_first;
+    a.nslices = st->rad_nslices;
+    a.slice_cap = st->rad_cap;
+    a.queue = st->rad_queue;
     a.ntiles = st->rad_ntiles;
     a.tabimg = st->d_img;
     a.segs = st->rad_segs;
@@ -1290,12 +1363,15 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
                            : op == TC_OP_BF16 ? tc_rad_inv_kernel<TC_OP_BF16>
                                               : tc_rad_inv_kernel<TC_OP_TF32>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->rad_smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st->rad_queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     fn<<<st->rad_grid, kThreadsInv, st->rad_smem, s>>>(a);
   } else if (prob == 3 && st->leg_ntiles > 0) {
     LegIArgs a;
     a.tiles = st->leg_tiles;
-    a.cta_first = st->leg_first;
+    a.slice_first = st->leg_first;
+    a.nslices = st->leg_nslices;
+    a.queue = st->leg_queue;
     a.ntiles = st->leg_ntiles;
     a.tabimg = st->d_img;
     a.segs = st->leg_segs;
@@ -1311,6 +1387,7 @@ cudaError_t run_tc_inverse(Plan& P, int prob, const void* x, void* y, cudaStream
                            : op == TC_OP_BF16 ? tc_leg_inv_kernel<TC_OP_BF16>
                                               : tc_leg_inv_kernel<TC_OP_TF32>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->leg_smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st->leg_queue, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     fn<<<st->leg_grid, kThreadsInv, st->leg_smem, s>>>(a);
   }

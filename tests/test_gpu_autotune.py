@@ -25,7 +25,7 @@ def _parse(text):
     """(fft_fwd_jp, fft_inv_jp, rad_inv_narrow, source); the tile shapes are
     checked by _shapes."""
     m = re.match(r"fft_fwd_jp=(\d+) fft_inv_jp=(\d+) rad_inv_narrow=(\d+) simt=\d,\d,\d,\d rad_rows=\d+ "
-                 r"source=(\w+)$", text)
+                 r"fft_merge=[01] queue=[124] source=(\w+)$", text)
     assert m, text
     return int(m.group(1)), int(m.group(2)), int(m.group(3)), m.group(4)
 
@@ -106,6 +106,66 @@ def test_autotune_radial_tile_width_keeps_the_bound(tmp_path):
         f = plan.forward(plan.inverse(ct)).cpu().numpy()
         assert np.abs(f - c).max() / np.abs(c).max() < TF32X3_TOL, rr
         plan.check()
+
+
+def test_merged_fft_launch_keeps_results(tmp_path):
+    # an uneven plan runs its phi-FFT sizes in one multi-size launch per
+    # direction (default) or one launch per size (forced through the cache):
+    # each CTA runs the same code either way, so the results are identical
+    from paper_1604_05140_gb300 import Plan
+    Bs = [16, 24, 40, 56, 72, 128, 104]
+    cs = [inputs.random_coeffs(b, 1, seed=1200 + k)[0] for k, b in enumerate(Bs)]
+    ct = torch.from_numpy(np.concatenate(cs)).to(torch.complex64).cuda()
+    merged = Plan.many(Bs, precision="tf32x3")
+    f1 = merged.forward(merged.inverse(ct))
+    first = str(tmp_path / "tuned.txt")
+    Plan.many(Bs, precision="tf32x3").autotune(cache=first)
+    line = open(first).read().splitlines()[0]
+    # the default configuration, but for the merge choice
+    line = re.sub(r"fft_fwd_jp=\d+ fft_inv_jp=\d+ rad_inv_narrow=\d+", "fft_fwd_jp=16 fft_inv_jp=16 rad_inv_narrow=65",
+                  line)
+    line = re.sub(r"rad_rows=\d+", "rad_rows=64", line)
+    line = re.sub(r"queue=\d", "queue=2", line)
+    for fm in (0, 1):
+        forced = tmp_path / f"fm{fm}.txt"
+        forced.write_text(re.sub(r"fft_merge=\d", f"fft_merge={fm}", line) + "\n")
+        plan = Plan.many(Bs, precision="tf32x3")
+        text = plan.autotune(cache=str(forced))
+        assert f"fft_merge={fm}" in text
+        # seven FFT sizes: one launch per direction, or seven; two tensor-core stages
+        assert plan.launches_per_call == (1 if fm else 7) + 2
+        f2 = plan.forward(plan.inverse(ct))
+        assert torch.equal(f1, f2), fm
+        for k, b in enumerate(Bs):
+            co = plan.coeff_offset(k)
+            fk = f2[co:co + O.coeff_count(b)].cpu().numpy()
+            assert np.abs(fk - cs[k]).max() / np.abs(cs[k]).max() < TF32X3_TOL, (fm, b)
+        plan.check()
+
+
+def test_work_queue_granularity_keeps_results(tmp_path):
+    # the tensor-core stages take their tiles from a work queue of slices; the
+    # number of slices per CTA (forced through the cache) changes which CTA
+    # runs a tile, never the tile's arithmetic: identical results
+    from paper_1604_05140_gb300 import Plan
+    Bs = [64, 16, 128, 40]
+    cs = [inputs.random_coeffs(b, 1, seed=1300 + k)[0] for k, b in enumerate(Bs)]
+    ct = torch.from_numpy(np.concatenate(cs)).to(torch.complex64).cuda()
+    first = str(tmp_path / "tuned.txt")
+    Plan.many(Bs, precision="tf32x3").autotune(cache=first)
+    line = open(first).read().splitlines()[0]
+    ref = None
+    for q in (1, 2, 4):
+        forced = tmp_path / f"q{q}.txt"
+        forced.write_text(re.sub(r"queue=\d", f"queue={q}", line) + "\n")
+        plan = Plan.many(Bs, precision="tf32x3")
+        assert f"queue={q}" in plan.autotune(cache=str(forced))
+        s = plan.inverse(ct)
+        f = plan.forward(s)
+        plan.check()
+        if ref is None:
+            ref = (s.clone(), f.clone())
+        assert torch.equal(s, ref[0]) and torch.equal(f, ref[1]), q
 
 
 def test_autotune_rejects_host_buffers():
