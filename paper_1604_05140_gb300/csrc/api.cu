@@ -221,10 +221,19 @@ static cudaError_t build_fft_lists(Plan& P) {
     const int JP = fft_jp(P, sg.B, true);
     if (tc_precision(P.prec)) {
       // the tensor-core Legendre synthesis stores spectra [m][b][j][i][c]: each
-      // inverse-FFT CTA takes JP consecutive shells of one ring pair (layout 1)
-      for (int b = 0; b < sg.NB; ++b)
-        for (int i0 = 0; i0 < sg.R; i0 += JP)
-          for (int jp = 0; jp < sg.B; ++jp) ff.push_back(make_int4((int)s, b * sg.R + i0, jp, 1));
+      // inverse-FFT CTA takes JP consecutive shells of one ring pair (layout 1).
+      // CTA order (tuned): shell blocks outer (consecutive CTAs read other
+      // rings), or ring pairs outer (consecutive CTAs read the neighbouring
+      // pieces of the same runs of shells)
+      for (int b = 0; b < sg.NB; ++b) {
+        if (P.fft_inv_order == 0) {
+          for (int i0 = 0; i0 < sg.R; i0 += JP)
+            for (int jp = 0; jp < sg.B; ++jp) ff.push_back(make_int4((int)s, b * sg.R + i0, jp, 1));
+        } else {
+          for (int jp = 0; jp < sg.B; ++jp)
+            for (int i0 = 0; i0 < sg.R; i0 += JP) ff.push_back(make_int4((int)s, b * sg.R + i0, jp, 1));
+        }
+      }
     } else {
       for (int sh = 0; sh < sg.NB * sg.R; ++sh)
         for (int j0 = 0; j0 < sg.B; j0 += JP) ff.push_back(make_int4((int)s, sh, j0, 0));
@@ -675,9 +684,9 @@ static std::string tuning_text(const Plan& P, const char* source) {
   char buf[256];
   snprintf(buf, sizeof buf,
            "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d queue=%d "
-           "source=%s",
+           "inv_order=%d source=%s",
            fft_jp(P, P.maxB, false), fft_jp(P, P.maxB, true), P.radi_narrow, P.simt_policy[0], P.simt_policy[1],
-           P.simt_policy[2], P.simt_policy[3], P.rad_rows, P.fft_merge, P.queue_slices, source);
+           P.simt_policy[2], P.simt_policy[3], P.rad_rows, P.fft_merge, P.queue_slices, P.fft_inv_order, source);
   return buf;
 }
 
@@ -726,14 +735,15 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
       while (fgets(line, sizeof line, f)) {
         const std::string ln(line);
         if (ln.compare(0, key.size() + 3, key + " | ") != 0) continue;
-        int jf = 0, ji = 0, rn = 0, sp[4] = {0, 0, 0, 0}, rr = 64, fm = 1, qs = 2;
+        int jf = 0, ji = 0, rn = 0, sp[4] = {0, 0, 0, 0}, rr = 64, fm = 1, qs = 2, io = 0;
         const int got = sscanf(ln.c_str() + key.size() + 3,
                                "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d "
-                               "queue=%d",
-                               &jf, &ji, &rn, &sp[0], &sp[1], &sp[2], &sp[3], &rr, &fm, &qs);
+                               "queue=%d inv_order=%d",
+                               &jf, &ji, &rn, &sp[0], &sp[1], &sp[2], &sp[3], &rr, &fm, &qs, &io);
         bool valid = (got == 3 || got >= 8) && jf >= 1 && jf <= 16 && ji >= 1 && ji <= 16 && rn >= 1;
         for (int k = 0; k < 4; ++k) valid = valid && sp[k] >= 0 && sp[k] <= 2;
-        valid = valid && (rr == 32 || rr == 48 || rr == 64) && (fm == 0 || fm == 1) && (qs == 1 || qs == 2 || qs == 4);
+        valid = valid && (rr == 32 || rr == 48 || rr == 64) && (fm == 0 || fm == 1) && (qs == 1 || qs == 2 || qs == 4) &&
+                (io == 0 || io == 1);
         if (valid) {
           P->jp_fwd = jf;
           P->jp_inv = ji;
@@ -742,6 +752,7 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
           P->rad_rows = rr;
           P->fft_merge = fm;
           P->queue_slices = qs;
+          P->fft_inv_order = io;
           cached = true;
         }
       }
@@ -772,6 +783,24 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
     }
     e = build_fft_lists(*P);
     if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+    if (tc_precision(P->prec)) {  // CTA order of the inverse phi-FFT (layout 1)
+      int best = 0;
+      double tbest = 1e30;
+      for (int io : {0, 1}) {
+        P->fft_inv_order = io;
+        e = build_fft_lists(*P);
+        if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+        const double t = time_calls(*P, false, samples, coeffs, s);
+        if (t < 0.0) return cuda_fail(P, cudaGetLastError(), "autotune launch");
+        if (t < tbest) {
+          tbest = t;
+          best = io;
+        }
+      }
+      P->fft_inv_order = best;
+      e = build_fft_lists(*P);
+      if (e != cudaSuccess) return cuda_fail(P, e, "autotune schedule upload");
+    }
     // plans of several register-FFT sizes: one multi-size launch per
     // direction, or one launch per size (timed over both directions)
     const int merge0 = P->fft_merge;
@@ -875,9 +904,10 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
     FILE* f = fopen(cache_path, "a");
     if (!f) return fail(P, SGL_ERR_ARG, std::string("cannot append to tuning cache ") + cache_path);
     fprintf(f,
-            "%s | fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d queue=%d\n",
+            "%s | fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d queue=%d "
+            "inv_order=%d\n",
             key.c_str(), P->jp_fwd, P->jp_inv, P->radi_narrow, P->simt_policy[0], P->simt_policy[1],
-            P->simt_policy[2], P->simt_policy[3], P->rad_rows, P->fft_merge, P->queue_slices);
+            P->simt_policy[2], P->simt_policy[3], P->rad_rows, P->fft_merge, P->queue_slices, P->fft_inv_order);
     fclose(f);
   }
   return SGL_OK;

@@ -254,8 +254,11 @@ struct Plan {
   // plans of several register-FFT sizes: one multi-size phi-FFT launch per
   // direction (1) or one launch per size (0)
   int fft_merge = 1;
-  // work-queue slices per CTA of the tensor-core forward stages (1, 2 or 4)
+  // work-queue slices per CTA of the tensor-core stages (1, 2 or 4)
   int queue_slices = 2;
+  // CTA order of the tensor-core plans' inverse phi-FFT: shell blocks outer
+  // (0) or ring pairs outer (1)
+  int fft_inv_order = 0;
   std::string tuning;
 
   // FP16x3 plans: per-function largest magnitudes [AMAX_SLOTS][nfn] (segment

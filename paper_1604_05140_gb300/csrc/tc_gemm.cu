@@ -77,10 +77,14 @@ namespace {
 
 enum { TC_LEG_F = 0, TC_RAD_F = 1 };
 
-// pipeline depth: both tables are at most 64 rows (radial degrees with more
-// than 64 terms are cut into two groups), which leaves room for 4 stages
-constexpr int kStagesLeg = 4;
-constexpr int kStagesRad = 4;
+// Ring depths.  Both tables are at most 64 rows (radial degrees with more
+// than 64 terms are cut into groups), at most 64 KB of hi/lo TF32 (32 KB of
+// 16-bit pairs), which leaves room for 5 raw TMA chunks next to the two
+// operand chunks of TF32 (8 raw chunks for 16-bit pairs, whose operand
+// chunks are half the size).
+constexpr int kRawTf32 = 5;
+constexpr int kRaw16 = 8;
+constexpr int kOps = 2;
 constexpr int kChunkBytes = 128 * 128;  // 128 rows x 32 floats
 constexpr int kThreads = tcx::kRoleThreads;
 
@@ -139,21 +143,30 @@ struct TcArgs {
 // per MMA.  BF16 and FP16 hi/lo pairs: kind::f16, 64-byte rows, K = 16 per
 // MMA; FP16 values are scaled by powers of two (tables per group image on the
 // host, data per function here) and the epilogue takes the scales out.
-template <int PROB, int STAGES, int OP>
+template <int PROB, int RAW, int OP>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   constexpr bool BF = OP != TC_OP_TF32;  // a 16-bit operand path
   constexpr bool F16 = OP == TC_OP_FP16;
   constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
+  // Two rings: RAW chunks of TMA data (16 KB, the input rows as they are in
+  // HBM), each released as soon as the split warps have read it, and OPS
+  // chunks of split hi/lo operands for the MMAs (hi then lo: 16 + 16 KB for
+  // TF32, 8 + 8 KB for 16-bit pairs), so that more input is in flight than
+  // the MMAs hold.
+  constexpr int OPS = kOps;
+  constexpr int OPB = BF ? kChunkBytes : 2 * kChunkBytes;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tab_bytes = 2 * a.KCmax * a.npmax * ROWB;      // hi + lo for the largest group
   unsigned char* tab = base;                                 // [hi: KC][npad][128 B] [lo: same]
-  unsigned char* xs = base + tab_bytes;                      // STAGES x (hi 16 KB, lo 16 KB)
-  uint64_t* bars = (uint64_t*)(xs + STAGES * 2 * kChunkBytes);
-  uint64_t* full = bars;                 // [STAGES] TMA landed
-  uint64_t* split = bars + STAGES;      // [STAGES] hi/lo ready (128 arrivals)
-  uint64_t* empty = bars + 2 * STAGES;  // [STAGES] MMAs done with the stage
-  uint64_t* accf = bars + 3 * STAGES;   // [2] accumulator complete
+  unsigned char* xs = base + tab_bytes;                      // RAW x 16 KB of TMA chunks
+  unsigned char* ops = xs + RAW * kChunkBytes;               // OPS x OPB of split operands
+  uint64_t* bars = (uint64_t*)(ops + OPS * OPB);
+  uint64_t* full = bars;                 // [RAW] TMA landed
+  uint64_t* rfree = bars + RAW;          // [RAW] raw chunk read by the split warps
+  uint64_t* split = bars + 2 * RAW;      // [OPS] hi/lo ready
+  uint64_t* empty = split + OPS;         // [OPS] MMAs done with the operands
+  uint64_t* accf = empty + OPS;          // [2] accumulator complete
   uint64_t* acce = accf + 2;             // [2] accumulator drained (128 arrivals)
   uint64_t* tabf = acce + 2;             // table landed
   uint64_t* tabe = tabf + 1;             // table no longer read
@@ -193,10 +206,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   while (tmem_cols < 2 * bufcols) tmem_cols <<= 1;  // power of two >= 32
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < RAW; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(split + s, kSplitThreads);
-      mbar_init(empty + s, 2);  // both MMA issuers
+      mbar_init(rfree + s, kSplitThreads);
+    }
+    for (int o = 0; o < OPS; ++o) {
+      mbar_init(split + o, kSplitThreads);
+      mbar_init(empty + o, 2);  // both MMA issuers
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(accf + k, 2);
@@ -277,10 +293,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
           row = (int64_t)sg.NB * 2 * l * l + tl.y;
         }
         for (int kc = 0; kc < sg.KC; ++kc, ++c) {
-          const int s = c % STAGES;
-          if (!mbar_wait(empty + s, ((c / STAGES) & 1) ^ 1, abort_flag)) break;
+          const int s = c % RAW;
+          if (!mbar_wait(rfree + s, ((c / RAW) & 1) ^ 1, abort_flag)) break;
           mbar_arrive_tx(full + s, kChunkBytes);
-          tma_load_2d(xs + s * 2 * kChunkBytes, xmap, full + s, kc * 32, (int)row);
+          tma_load_2d(xs + s * kChunkBytes, xmap, full + s, kc * 32, (int)row);
         }
       }
       issued[0] = s_cnt[0] = c;
@@ -292,9 +308,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
       const int me = warp == 1 ? 0 : 1;
       int cur = -1, ngrp = (int)s_cnt[4 + 3 * me];
       uint32_t c = s_cnt[2 + 3 * me], tcount = s_cnt[3 + 3 * me];
-      // TF32: X_hi in place of the raw chunk, X_lo in the second half of the
-      // stage; BF16: X_hi and X_lo (8 KB each) in the second half
-      const uint64_t xdesc0 = BF ? sw64_desc(smem_u32(xs + kChunkBytes)) : sw128_desc(smem_u32(xs));
+      // operand chunk o: X_hi, then X_lo (16 KB each for TF32, 8 KB for 16-bit)
+      const uint64_t xdesc0 = BF ? sw64_desc(smem_u32(ops)) : sw128_desc(smem_u32(ops));
       const uint64_t tdesc0 = BF ? sw64_desc(smem_u32(tab)) : sw128_desc(smem_u32(tab));
       for (int t = t_begin; t < t_end && !*abort_flag; ++t, ++tcount) {
         const int4 tl = s_tiles[t];
@@ -316,10 +331,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
         const uint32_t dc = dm + (uint32_t)npad;
         bool ok = true;
         for (int kc = 0; kc < KC; ++kc, ++c) {
-          const int s = c % STAGES;
-          if (!mbar_wait(split + s, (c / STAGES) & 1, abort_flag)) { ok = false; break; }
+          const int o = c % OPS;
+          if (!mbar_wait(split + o, (c / OPS) & 1, abort_flag)) { ok = false; break; }
           tc_after();
-          const uint64_t xh = xdesc0 + (uint64_t)((s * 2 * kChunkBytes) >> 4) + 2 * me;
+          const uint64_t xh = xdesc0 + (uint64_t)((o * OPB) >> 4) + 2 * me;
           const uint64_t xl = xh + (uint64_t)((BF ? kChunkBytes / 2 : kChunkBytes) >> 4);
           const uint64_t tb = tdesc0 + (uint64_t)((kc * 2 * npad * ROWB) >> 4) + 2 * me;
           const uint32_t first = kc > 0 ? 1u : 0u;
@@ -335,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
             mma_tf32(dm, xh, tb, idesc1, first);
             mma_tf32(dm, xh + 4, tb + 4, idesc1, 1u);
           }
-          mma_commit(empty + s);
+          mma_commit(empty + o);
         }
         if (!ok) break;
         mma_commit(accf + acc);
@@ -383,24 +398,30 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
         if (t + 1 < t_end) split_amax_load(t + 1, amx);
       }
       for (int kc = 0; kc < KC; ++kc, ++c) {
-        const int s = c % STAGES;
-        if (!mbar_wait(full + s, (c / STAGES) & 1, abort_flag)) { ok = false; break; }
-        float4* hi = (float4*)(xs + s * 2 * kChunkBytes);
-        float4* lo = (float4*)(xs + s * 2 * kChunkBytes + kChunkBytes);
+        const int s = c % RAW, o = c % OPS;
+        if (!mbar_wait(full + s, (c / RAW) & 1, abort_flag)) { ok = false; break; }
+        // the raw chunk to registers, and back to the producer
+        float4 x[kPer];
+        const float4* in = (const float4*)(xs + s * kChunkBytes);
+#pragma unroll
+        for (int v = 0; v < kPer; ++v) x[v] = in[v * kSplitThreads + tid];
+        mbar_arrive(rfree + s);
+        // the operand chunk, once the MMAs of chunk c - OPS are done with it
+        if (!mbar_wait(empty + o, ((c / OPS) & 1) ^ 1, abort_flag)) { ok = false; break; }
+        unsigned char* ob = ops + o * OPB;
         if constexpr (BF) {
           // raw chunk (128-byte rows, 32 floats) -> 16-bit hi/lo rows of 64 bytes
-          unsigned char* ob = xs + s * 2 * kChunkBytes + kChunkBytes;
 #pragma unroll
           for (int v = 0; v < kPer; ++v) {
             const int idx = v * kSplitThreads + tid;
             const int r = idx >> 3, q = (idx & 7) ^ (r & 7);  // values 4q .. 4q+3 of row r
-            const float4 x = hi[idx];
             uint2 h2, l2;
             if constexpr (F16) {
-              fp16_split2(x.x, x.y, xf[v], h2.x, l2.x);
-              fp16_split2(x.z, x.w, xf[v], h2.y, l2.y);
+              fp16_split2(x[v].x, x[v].y, xf[v], h2.x, l2.x);
+              fp16_split2(x[v].z, x[v].w, xf[v], h2.y, l2.y);
             } else {
-              const uint32_t s0 = bf16_split(x.x), s1 = bf16_split(x.y), s2 = bf16_split(x.z), s3 = bf16_split(x.w);
+              const uint32_t s0 = bf16_split(x[v].x), s1 = bf16_split(x[v].y), s2 = bf16_split(x[v].z),
+                             s3 = bf16_split(x[v].w);
               h2 = {(s0 & 0xFFFFu) | (s1 << 16), (s2 & 0xFFFFu) | (s3 << 16)};
               l2 = {(s0 >> 16) | (s1 & 0xFFFF0000u), (s2 >> 16) | (s3 & 0xFFFF0000u)};
             }
@@ -409,21 +430,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
             *(uint2*)(ob + kChunkBytes / 2 + off) = l2;
           }
         } else {
+          // same 128-byte swizzled positions as the TMA chunk: hi, then lo
+          float4* hi = (float4*)ob;
+          float4* lo = (float4*)(ob + kChunkBytes);
 #pragma unroll
           for (int v = 0; v < kPer; ++v) {
             const int idx = v * kSplitThreads + tid;
-            float4 x = hi[idx];
-            float4 h = {tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w)};
+            const float4 h = {tf32_rna(x[v].x), tf32_rna(x[v].y), tf32_rna(x[v].z), tf32_rna(x[v].w)};
             hi[idx] = h;
             if (a.nprod == 3) {
               // lo rounded to TF32 too, so that the tensor core uses it unchanged
-              float4 l = {tf32_rna(x.x - h.x), tf32_rna(x.y - h.y), tf32_rna(x.z - h.z), tf32_rna(x.w - h.w)};
+              const float4 l = {tf32_rna(x[v].x - h.x), tf32_rna(x[v].y - h.y), tf32_rna(x[v].z - h.z),
+                                tf32_rna(x[v].w - h.w)};
               lo[idx] = l;
             }
           }
         }
         fence_proxy_async();
-        mbar_arrive(split + s);
+        mbar_arrive(split + o);
       }
       if (!ok) break;
     }
@@ -554,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
     if (threadIdx.x == 0) atomicExch(a.err, 1);
     if (warp == 0 && lane == 0) {
       const uint32_t* cnt = (const uint32_t*)(bars + 61);
-      drain_ring(full, STAGES, cnt[0]);
+      drain_ring(full, RAW, cnt[0]);
       if (cnt[1] > 0) mbar_drain(tabf, (cnt[1] - 1) & 1);
     }
     if ((warp == 1 || warp == kMma2Warp) && lane == 0) drain_mma(bars + 62 + (warp == 1 ? 0 : 1));
@@ -871,12 +895,12 @@ static cudaError_t tc_prepare_impl(Plan& P) {
     if (e == cudaSuccess) e = upload(&S.d_exp, ex);
     if (e == cudaSuccess) e = upload(&S.d_npad, pd.npad);
     if (e == cudaSuccess) e = upload(&S.d_segs, pd.segs);
-    // tables, X ring, 64 barrier/flag slots, segments, group metadata of the
-    // slice (at most one group per tile), tile slice; more CTAs (further
-    // waves) when the slices of one wave would not fit
-    const int stages = k == 0 ? kStagesLeg : kStagesRad;
-    const size_t fixed = 1024 + (size_t)2 * S.KCmax * S.npmax * (bf ? 64 : 128) + (size_t)stages * 2 * kChunkBytes +
-                         64 * 8 + (size_t)S.nseg * sizeof(SegSmall) + 16 + 12 + 16;
+    // tables, raw and operand rings, 64 barrier/flag slots, segments, then
+    // per slice the group metadata and the tiles
+    const size_t rings = bf ? (size_t)kRaw16 * kChunkBytes + (size_t)kOps * kChunkBytes
+                            : (size_t)kRawTf32 * kChunkBytes + (size_t)kOps * 2 * kChunkBytes;
+    const size_t fixed = 1024 + (size_t)2 * S.KCmax * S.npmax * (bf ? 64 : 128) + rings + 64 * 8 +
+                         (size_t)S.nseg * sizeof(SegSmall) + 16 + 12 + 16;
     // work queue: P.queue_slices cost-balanced slices per CTA of one wave
     // (more while one slice's shared-memory copies would not fit)
     // shared memory per slice: 16 bytes a tile, 16 bytes a group the tiles
@@ -962,16 +986,14 @@ cudaError_t run_tc_stage(Plan& P, int prob, const void* x, void* y, int weighted
     void (*fn)(TcArgs);
     switch (tc_operand(P.prec)) {
       case TC_OP_FP16:
-        fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, TC_OP_FP16>
-                       : tc_gemm_kernel<TC_RAD_F, kStagesRad, TC_OP_FP16>;
+        fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kRaw16, TC_OP_FP16> : tc_gemm_kernel<TC_RAD_F, kRaw16, TC_OP_FP16>;
         break;
       case TC_OP_BF16:
-        fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, TC_OP_BF16>
-                       : tc_gemm_kernel<TC_RAD_F, kStagesRad, TC_OP_BF16>;
+        fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kRaw16, TC_OP_BF16> : tc_gemm_kernel<TC_RAD_F, kRaw16, TC_OP_BF16>;
         break;
       default:
-        fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kStagesLeg, TC_OP_TF32>
-                       : tc_gemm_kernel<TC_RAD_F, kStagesRad, TC_OP_TF32>;
+        fn = prob == 0 ? tc_gemm_kernel<TC_LEG_F, kRawTf32, TC_OP_TF32>
+                       : tc_gemm_kernel<TC_RAD_F, kRawTf32, TC_OP_TF32>;
     }
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.d_queue, 0, sizeof(int), s);

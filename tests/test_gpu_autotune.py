@@ -25,7 +25,7 @@ def _parse(text):
     """(fft_fwd_jp, fft_inv_jp, rad_inv_narrow, source); the tile shapes are
     checked by _shapes."""
     m = re.match(r"fft_fwd_jp=(\d+) fft_inv_jp=(\d+) rad_inv_narrow=(\d+) simt=\d,\d,\d,\d rad_rows=\d+ "
-                 r"fft_merge=[01] queue=[124] source=(\w+)$", text)
+                 r"fft_merge=[01] queue=[124] inv_order=[01] source=(\w+)$", text)
     assert m, text
     return int(m.group(1)), int(m.group(2)), int(m.group(3)), m.group(4)
 
@@ -126,6 +126,7 @@ def test_merged_fft_launch_keeps_results(tmp_path):
                   line)
     line = re.sub(r"rad_rows=\d+", "rad_rows=64", line)
     line = re.sub(r"queue=\d", "queue=2", line)
+    line = re.sub(r"inv_order=\d", "inv_order=0", line)
     for fm in (0, 1):
         forced = tmp_path / f"fm{fm}.txt"
         forced.write_text(re.sub(r"fft_merge=\d", f"fft_merge={fm}", line) + "\n")
@@ -145,8 +146,9 @@ def test_merged_fft_launch_keeps_results(tmp_path):
 
 def test_work_queue_granularity_keeps_results(tmp_path):
     # the tensor-core stages take their tiles from a work queue of slices; the
-    # number of slices per CTA (forced through the cache) changes which CTA
-    # runs a tile, never the tile's arithmetic: identical results
+    # number of slices per CTA and the inverse phi-FFT's CTA order (forced
+    # through the cache) change which CTA runs a tile or a ring pair, never
+    # its arithmetic: identical results
     from paper_1604_05140_gb300 import Plan
     Bs = [64, 16, 128, 40]
     cs = [inputs.random_coeffs(b, 1, seed=1300 + k)[0] for k, b in enumerate(Bs)]
@@ -155,11 +157,12 @@ def test_work_queue_granularity_keeps_results(tmp_path):
     Plan.many(Bs, precision="tf32x3").autotune(cache=first)
     line = open(first).read().splitlines()[0]
     ref = None
-    for q in (1, 2, 4):
-        forced = tmp_path / f"q{q}.txt"
-        forced.write_text(re.sub(r"queue=\d", f"queue={q}", line) + "\n")
+    for q, io in ((1, 0), (2, 1), (4, 0), (4, 1)):
+        forced = tmp_path / f"q{q}_{io}.txt"
+        forced.write_text(re.sub(r"inv_order=\d", f"inv_order={io}", re.sub(r"queue=\d", f"queue={q}", line)) + "\n")
         plan = Plan.many(Bs, precision="tf32x3")
-        assert f"queue={q}" in plan.autotune(cache=str(forced))
+        text = plan.autotune(cache=str(forced))
+        assert f"queue={q}" in text and f"inv_order={io}" in text
         s = plan.inverse(ct)
         f = plan.forward(s)
         plan.check()
