@@ -505,7 +505,16 @@ def midpoint_path(reps=3):
         fm = torch.from_numpy(sample(x, y, z)).cuda()
         got, ms = timed(lambda: midpoint(fm, B, L))
         err = float(np.abs(got.cpu().numpy() - ref).max() / np.abs(ref).max())
-        res["midpoint"][str(M)] = {"ms": ms, "samples_per_function": M ** 3, "max_rel_err": err}
+        # roofline: the FP64 pipe; algorithmic work 8 flops (one complex
+        # multiply-add of f by the conjugated basis value) per point,
+        # coefficient and function (the per-point basis tables not counted)
+        fl = 8.0 * M ** 3 * omega_count(B) * nf
+        tf = fl / (ms * 1e-3) / 1e12
+        res["midpoint"][str(M)] = {"ms": ms, "samples_per_function": M ** 3, "max_rel_err": err,
+                                   "roofline": {"bound": "alu", "achieved": tf, "peak": alu_peak_tflops("fp64"),
+                                                "unit": "TFLOP/s", "frac": tf / alu_peak_tflops("fp64"),
+                                                "algorithmic_flops": fl,
+                                                "peak_source": "derived: FP64 FMA lanes x clock"}}
         del fm
     return res
 
@@ -602,16 +611,28 @@ def uneven_path(steps, warmup):
 def profile_case(case, precision, steps, warmup):
     """Round trips of one workload and nothing else, for profiler captures
     (`--profile-case`): the uneven-bandlimit batch (256 functions, B in
-    {16, ..., 128}) or the uniform one (B = 128, --batch functions), eager
-    launches, default launch configuration.  Prints one JSON line with the
-    mean step time; not a benchmark line."""
+    {16, ..., 128}), the uniform one (B = 128, --batch functions), the same on
+    the paper's grid, or the midpoint rule (B = 16, M = 32, 16 functions);
+    eager launches, default launch configuration.  Prints one JSON line with
+    the mean step time; not a benchmark line."""
     import torch
-    from paper_1604_05140_gb300 import Plan, inputs
+    from paper_1604_05140_gb300 import Plan, inputs, midpoint
+    if case == "midpoint":  # the midpoint rule, B = 16, M = 32, 16 functions, FP64
+        fm = torch.from_numpy(inputs.random_samples(1, 16 * 32 ** 3 // 4, seed=inputs.BASE_SEED + 9)
+                              .reshape(16, 32, 32, 32)).cuda()
+        for _ in range(warmup + steps):
+            midpoint(fm, 16, 6.0)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": case, "steps": steps, "warmup": warmup}), flush=True)
+        return
     if case == "uneven":
         Bs = [int(b) for b in inputs.uneven_bandlimits(256)]
         plan = Plan.many(Bs, precision=precision)
         c = np.concatenate([inputs.random_coeffs(B, 1, seed=inputs.BASE_SEED + 4 + 10 * k)[0]
                             for k, B in enumerate(Bs)])
+    elif case == "paper_grid":  # the paper's 2B half-range Gauss-Hermite radii
+        plan = Plan(B_BENCH, BATCH, precision, grid="hermite")
+        c = inputs.random_coeffs(B_BENCH, BATCH, seed=inputs.BASE_SEED + 3, decay=True)
     else:
         plan = Plan(B_BENCH, BATCH, precision)
         c = inputs.random_coeffs(B_BENCH, BATCH, seed=inputs.BASE_SEED + 3, decay=True)
@@ -927,7 +948,7 @@ def main():
     ap.add_argument("--cpu-workers", type=int, default=0,
                     help="oracle worker processes of the all-cores baseline and the reference arm (0: one per core)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
-    ap.add_argument("--profile-case", choices=["uneven", "uniform"], default=None,
+    ap.add_argument("--profile-case", choices=["uneven", "uniform", "paper_grid", "midpoint"], default=None,
                     help="run only this workload's round trips (for profiler captures) and exit")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="functions per GPU (64 is the benchmark workload; smaller only for profiling runs)")
