@@ -9,13 +9,16 @@
 // sampling theorem makes this exact; it is built for the accuracy / cost
 // comparison with the SGL transform.
 //
-// Per block: a slice of the grid points of one function.  Threads first build,
-// for a batch of kPts points, the normalized Legendre functions
-// Lambda_lm(cos theta) (Def 2.1, normalized Eq. legendre_recurrence), the
-// radial functions T_nl(r) = N_nl R_nl(r) exp(-r^2/2) (Lemma 3.7, normalized
-// reading) and e^{-i m phi} in shared memory; then each thread accumulates a
-// fixed set of coefficients over those points, and finally adds its partial
-// sums to the output (one atomic add per coefficient and block).
+// Per block: a slice of the grid points, a group of coefficients and up to
+// kFn functions.  Threads first build, for a batch of kPts points, the
+// normalized Legendre functions Lambda_lm(cos theta) (Def 2.1, normalized
+// Eq. legendre_recurrence), the radial functions T_nl(r) = N_nl R_nl(r)
+// exp(-r^2/2) (Lemma 3.7, normalized reading), e^{-i m phi} and the weighted
+// samples of the block's functions in shared memory; then each thread
+// accumulates a fixed set of coefficients of every one of those functions over
+// the points (the basis value of a (point, coefficient) pair is formed once and
+// used for all kFn functions), and finally adds its partial sums to the output
+// (one atomic add per coefficient, function and block).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -32,7 +35,8 @@ namespace {
 
 constexpr int kPts = 16;          // points per shared-memory batch
 constexpr int kThreads = 256;
-constexpr int kPer = 4;           // coefficients per thread
+constexpr int kPer = 2;           // coefficients per thread
+constexpr int kFn = 8;            // functions per block (grid y: groups of kFn)
 constexpr int kCoefBlock = kPer * kThreads;  // coefficients per block (grid z)
 
 sgl_status midpoint_fail(sgl_status st, const std::string& msg) {
@@ -51,18 +55,18 @@ struct MidArgs {
 };
 
 template <typename real>
-__global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
+__global__ void __launch_bounds__(kThreads, 2) midpoint_kernel(MidArgs<real> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int B = a.B;
   const int nlm = B * (B + 1) / 2;  // entries of one triangular table
   real* lam = reinterpret_cast<real*>(smem_raw);      // [kPts][m][l >= m]: index m*B - m(m-1)/2 + (l - m)
   real* rad = lam + kPts * nlm;                       // [kPts][l][n-1 >= l]: index l*B - l(l-1)/2 + (n-1-l)
   real* eph = rad + kPts * nlm;                       // [kPts][m < B][2]: e^{-i m phi}
-  real* fw = eph + kPts * 2 * B;                      // [kPts][2]: f(x_k) exp(-|x_k|^2 / 2) dV
+  real* fw = eph + kPts * 2 * B;                      // [kPts][kFn][2]: f_j(x_k) exp(-|x_k|^2 / 2) dV
   // recurrence coefficients, once per block (no square roots or divisions in
   // the per-point loops): Legendre a, c at [m][l]; radial 1/s, (2n-l-1/2)/s
   // and c at [l][n-1]; sectoral and radial seed factors per m and per l
-  real* la = fw + 2 * kPts;
+  real* la = fw + 2 * kPts * kFn;
   real* lc = la + nlm;
   real* rs = lc + nlm;
   real* r0 = rs + nlm;
@@ -90,7 +94,8 @@ __global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
     sf[w] = w > 0 ? -sqrt((2 * w + 1) / (real)(2 * w)) : 0;
     rf[w] = w > 0 ? 1 / sqrt(w + (real)0.5) : 0;
   }
-  const int b = blockIdx.y;
+  const int b0 = blockIdx.y * kFn;  // first function of the block
+  const int nfb = a.batch - b0 < kFn ? a.batch - b0 : kFn;
   const int64_t M3 = (int64_t)a.M * a.M * a.M;
   const int64_t p0 = (int64_t)blockIdx.x * a.pts_per_block;
   const int64_t p1 = p0 + a.pts_per_block < M3 ? p0 + a.pts_per_block : M3;
@@ -99,12 +104,13 @@ __global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
   const real kPi = (real)3.14159265358979323846;
   // coefficients of this thread: omega = blockIdx.z * kCoefBlock + threadIdx.x + q * kThreads,
   // with their (n, l, m) decoded once: table offsets, |m|, sign and sign of m
-  real acc_re[kPer], acc_im[kPer];
+  real acc_re[kPer][kFn], acc_im[kPer][kFn];
   int li[kPer], ri[kPer], amq[kPer], neg[kPer];
   real sgnq[kPer];
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
-    acc_re[q] = acc_im[q] = 0;
+#pragma unroll
+    for (int j = 0; j < kFn; ++j) acc_re[q][j] = acc_im[q][j] = 0;
     const int64_t om = (int64_t)blockIdx.z * kCoefBlock + threadIdx.x + (int64_t)q * kThreads;
     li[q] = -1;
     if (om >= a.omega) continue;
@@ -149,12 +155,19 @@ __global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
         eph[(k * B + m) * 2] = c;
         eph[(k * B + m) * 2 + 1] = sn;
       }
-      if (m == 0) {
-        // weight exp(-|x|^2) dV, of which T_nl carries exp(-|x|^2 / 2)
-        const int64_t fo = ((int64_t)b * M3 + p) * 2;
-        const real g = exp(-t / 2) * dV;
-        fw[k * 2] = a.f[fo] * g;
-        fw[k * 2 + 1] = a.f[fo + 1] * g;
+      // weight exp(-|x|^2) dV, of which T_nl carries exp(-|x|^2 / 2): work
+      // item (k, m) weights the samples of functions j = m, m + B, .. (zero
+      // past the batch)
+      const real e2 = exp(-t / 2);
+      for (int j = m; j < kFn; j += B) {
+        real fr = 0, fi = 0;
+        if (j < nfb) {
+          const int64_t fo = ((int64_t)(b0 + j) * M3 + p) * 2;
+          fr = a.f[fo] * e2 * dV;
+          fi = a.f[fo + 1] * e2 * dV;
+        }
+        fw[(k * kFn + j) * 2] = fr;
+        fw[(k * kFn + j) * 2 + 1] = fi;
       }
       const int tri = m * B - m * (m - 1) / 2;  // row m (or l = m) of a triangle
       // Lambda_lm(theta), l = m .. B-1: sectoral seed, then the recurrence in l
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
       // T_nl(r), n = l+1 .. B, for l = m (one column per thread)
       {
         const int l = m;
-        real seed = sqrt((real)2 / (sqrt(kPi) / 2)) * exp(-t / 2);
+        real seed = sqrt((real)2 / (sqrt(kPi) / 2)) * e2;
         for (int ll = 1; ll <= l; ++ll) seed *= r * rf[ll];
         real* rl = rad + k * nlm + tri;
         real prev = 0, cur = seed;
@@ -187,31 +200,42 @@ __global__ void __launch_bounds__(kThreads) midpoint_kernel(MidArgs<real> a) {
       }
     }
     __syncthreads();
-    // accumulate: coefficient omega(n, l, m) += f w conj(T_nl Lambda_l|m| s_m e^{i m phi})
+    // accumulate: coefficient omega(n, l, m) of function j += f_j w
+    // conj(T_nl Lambda_l|m| s_m e^{i m phi}); the sign s_m is applied to the
+    // sums at the end
+    for (int k = 0; k < np; ++k) {
+      real fr[kFn], fi[kFn];
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      if (li[q] < 0) continue;
-      real sr = 0, si = 0;
-      for (int k = 0; k < np; ++k) {
-        const real amp = sgnq[q] * lam[k * nlm + li[q]] * rad[k * nlm + ri[q]];
+      for (int j = 0; j < kFn; ++j) {
+        fr[j] = fw[(k * kFn + j) * 2];
+        fi[j] = fw[(k * kFn + j) * 2 + 1];
+      }
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        if (li[q] < 0) continue;
+        const real amp = lam[k * nlm + li[q]] * rad[k * nlm + ri[q]];
         // e^{-i m phi}: the table for m >= 0, its conjugate for m < 0
         const real ec = eph[(k * B + amq[q]) * 2];
         const real es = neg[q] ? -eph[(k * B + amq[q]) * 2 + 1] : eph[(k * B + amq[q]) * 2 + 1];
         const real hr = amp * ec, hi = amp * es;
-        const real fr = fw[k * 2], fi = fw[k * 2 + 1];
-        sr += fr * hr - fi * hi;
-        si += fr * hi + fi * hr;
+#pragma unroll
+        for (int j = 0; j < kFn; ++j) {
+          acc_re[q][j] += fr[j] * hr - fi[j] * hi;
+          acc_im[q][j] += fr[j] * hi + fi[j] * hr;
+        }
       }
-      acc_re[q] += sr;
-      acc_im[q] += si;
     }
   }
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     if (li[q] < 0) continue;
     const int64_t om = (int64_t)blockIdx.z * kCoefBlock + threadIdx.x + (int64_t)q * kThreads;
-    atomicAdd(&a.out[((int64_t)b * a.omega + om) * 2], acc_re[q]);
-    atomicAdd(&a.out[((int64_t)b * a.omega + om) * 2 + 1], acc_im[q]);
+#pragma unroll
+    for (int j = 0; j < kFn; ++j) {
+      if (j >= nfb) break;
+      atomicAdd(&a.out[((int64_t)(b0 + j) * a.omega + om) * 2], sgnq[q] * acc_re[q][j]);
+      atomicAdd(&a.out[((int64_t)(b0 + j) * a.omega + om) * 2 + 1], sgnq[q] * acc_im[q][j]);
+    }
   }
 }
 
@@ -227,20 +251,21 @@ cudaError_t launch_midpoint(int B, int M, double L, int batch, const void* f, vo
   a.L = L;
   const int64_t M3 = (int64_t)M * M * M;
   const int64_t groups = (a.omega + kCoefBlock - 1) / kCoefBlock;
-  // about four blocks per SM over the batch and coefficient groups, at least
-  // kPts points each
-  int64_t blocks = (4 * 152 + batch * groups - 1) / (batch * groups);
+  // about four blocks per SM over the function and coefficient groups, at
+  // least kPts points each
+  const int64_t fgroups = (batch + kFn - 1) / kFn;
+  int64_t blocks = (4 * 152 + fgroups * groups - 1) / (fgroups * groups);
   if (blocks < 1) blocks = 1;
   a.pts_per_block = (M3 + blocks - 1) / blocks;
   if (a.pts_per_block < kPts) a.pts_per_block = kPts;
   const int64_t nbx = (M3 + a.pts_per_block - 1) / a.pts_per_block;
   const size_t nlm = (size_t)B * (B + 1) / 2;
-  const size_t smem = sizeof(real) * (2 * kPts * nlm + (size_t)kPts * 2 * B + 2 * kPts + 5 * nlm + 2 * (size_t)B);
+  const size_t smem = sizeof(real) * (2 * kPts * nlm + (size_t)kPts * 2 * B + 2 * kPts * kFn + 5 * nlm + 2 * (size_t)B);
   cudaError_t e = cudaMemsetAsync(coeffs, 0, (size_t)batch * a.omega * 2 * sizeof(real), s);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(midpoint_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  midpoint_kernel<real><<<dim3((unsigned)nbx, (unsigned)batch, (unsigned)groups), kThreads, smem, s>>>(a);
+  midpoint_kernel<real><<<dim3((unsigned)nbx, (unsigned)fgroups, (unsigned)groups), kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

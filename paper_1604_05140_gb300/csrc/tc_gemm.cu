@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
   constexpr bool F16 = OP == TC_OP_FP16;
   constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
   // Two rings: RAW chunks of TMA data (16 KB, the input rows as they are in
-  // HBM), each released as soon as the split warps have read it, and OPS
+  // HBM), each released as soon as the split warps have read it (their
+  // shared-memory reads fenced against the next bulk copy), and OPS
   // chunks of split hi/lo operands for the MMAs (hi then lo: 16 + 16 KB for
   // TF32, 8 + 8 KB for 16-bit pairs), so that more input is in flight than
   // the MMAs hold.
@@ -405,6 +406,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(TcArgs a) {
         const float4* in = (const float4*)(xs + s * kChunkBytes);
 #pragma unroll
         for (int v = 0; v < kPer; ++v) x[v] = in[v * kSplitThreads + tid];
+        // the reads (generic proxy) ordered before the producer's next bulk
+        // tensor copy into the slot (async proxy)
+        fence_proxy_async();
         mbar_arrive(rfree + s);
         // the operand chunk, once the MMAs of chunk c - OPS are done with it
         if (!mbar_wait(empty + o, ((c / OPS) & 1) ^ 1, abort_flag)) { ok = false; break; }

@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_leg_inv_kernel(LegIArgs a) 
         const float* sp = (const float*)(stg + st * kChunk) + 16 * h * 128;
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = sp[k * 128 + r];
+        fence_proxy_async();  // reads before the next bulk tensor copy into the slot
         mbar_arrive(stge + st);
         const int s = c % kStagesLegI;
         if (!mbar_wait(empty + s, ((c / kStagesLegI) & 1) ^ 1, abort_flag)) { ok = false; break; }
@@ -531,12 +532,14 @@ struct RadIArgs {
 };
 
 // Function of split thread tid's column (b, m, c) in tile tl (fn0 + b), or
-// -1 past the segment's columns.
+// -1 past the segment's columns.  PAIR: the thread's column pair (b, m, re)
+// and (b, m, im).
+template <bool PAIR>
 __device__ __forceinline__ int rad_fn_of(const RadISeg& sg, int4 tl, int tid) {
   const int l = tl.x;
   const bool nar = tl.y & 1;
   const int per_b = (2 * l + 1) * 2;
-  const int col = (tl.y & ~1) + (nar ? (tid & 63) : (tid & 127));
+  const int col = (tl.y & ~1) + (PAIR ? 2 * (nar ? (tid & 31) : (tid & 63)) : (nar ? (tid & 63) : (tid & 127)));
   return col < sg.NB * per_b ? sg.fn0 + col / per_b : -1;
 }
 
@@ -573,10 +576,45 @@ __device__ __forceinline__ void rad_gather_async(const RadIArgs& a, const RadISe
   }
 }
 
+// TF32 form: the coefficients of one K chunk of one column pair (b, m, re)
+// and (b, m, im) — one complex value, one 8-byte copy per degree — gathered
+// by split thread tid: pair tid & 63 (wide tile) or tid & 31 (narrow tile),
+// 8 or 4 consecutive degrees from kc * 32 + (tid >> 6 or tid >> 5) * nv,
+// copied asynchronously to slot[k * 256 + tid] (zeros past the degree range or
+// the segment's columns).  Half the copies of the one-column form.
+__device__ __forceinline__ void rad_gather_pairs_async(const RadIArgs& a, const RadISeg& sg, int4 tl, int kc,
+                                                       int tid, int64_t fco, float2* slot) {
+  const int B = sg.B, l = tl.x;
+  const bool nar = tl.y & 1;
+  const int pi = nar ? (tid & 31) : (tid & 63);
+  const int h = nar ? (tid >> 5) : (tid >> 6);
+  const int nv = nar ? 4 : 8;
+  const int per_b = (2 * l + 1) * 2;
+  const int col = (tl.y & ~1) + 2 * pi;
+  const bool valid = col < sg.NB * per_b;
+  const int b = valid ? col / per_b : 0;
+  const int rem = col - b * per_b;
+  const int m = (rem >> 1) - l;
+  const float2* cf = (const float2*)a.coef + fco;
+  const int np0 = kc * 32 + h * nv;        // degree n = l + 1 + n'
+  int n = l + 1 + np0;
+  int64_t off = omega_of(n, l, m);          // omega(n + 1) - omega(n) = n^2
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k < nv) {
+      const bool in = valid && np0 + k < B - l;
+      cp_async8(slot + k * 256 + tid, in ? cf + off : (const float2*)a.coef, in);
+      off += (int64_t)n * n;
+      ++n;
+    }
+  }
+}
+
 template <int OP>
 __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) {
   constexpr bool BF = OP != TC_OP_TF32;  // 16-bit hi/lo pairs (kind::f16)
   constexpr bool F16 = OP == TC_OP_FP16;
+  constexpr bool PAIR = !BF;           // coefficient gather by (re, im) pairs
   constexpr int ROWB = BF ? 64 : 128;  // bytes of one operand row of a 32-value K chunk
   constexpr int TCH = 128 * ROWB;      // one table chunk (hi or lo): 128 rows i
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -764,14 +802,16 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     }
   } else if (warp < kFirstEpiWarp) {
     // gather: thread (column, h) copies 16 (wide) or 8 (narrow) consecutive
-    // degrees of its column per chunk into a staging slot, kGatherDepth
-    // chunks ahead of the chunk it splits and stores (asynchronous copies: no
-    // registers held while they are in flight).  The coefficient offset of
-    // the column's function is fetched a tile ahead of the copies.
+    // degrees of its column per chunk into a staging slot (TF32: thread
+    // (column pair, h) copies 8 or 4 degrees of its pair's complex values),
+    // kGatherDepth chunks ahead of the chunk it splits and stores
+    // (asynchronous copies: no registers held while they are in flight).  The
+    // coefficient offset of the column's function is fetched a tile ahead of
+    // the copies.
     const int tid = threadIdx.x - 32 * kFirstSplitWarp;
     auto fetch_fco = [&](int tt) -> int64_t {
       if (tt >= nt) return 0;
-      const int f = rad_fn_of(s_seg[s_tiles[tt].z], s_tiles[tt], tid);
+      const int f = rad_fn_of<PAIR>(s_seg[s_tiles[tt].z], s_tiles[tt], tid);
       return f >= 0 ? a.fn_coef[f] : 0;
     };
     // copy cursor: tile ti, chunk kci, chunks issued ci (starting from the
@@ -788,7 +828,9 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       if (ti < nt) {
         const int4 tl = s_tiles[ti];
         const RadISeg& sg = s_seg[tl.z];
-        rad_gather_async(a, sg, tl, kci, tid, fco_i, gslots + (ci % kGatherSlots) * (kGatherSlotBytes / 4));
+        float* slot = gslots + (ci % kGatherSlots) * (kGatherSlotBytes / 4);
+        if constexpr (PAIR) rad_gather_pairs_async(a, sg, tl, kci, tid, fco_i, (float2*)slot);
+        else rad_gather_async(a, sg, tl, kci, tid, fco_i, slot);
         if (++kci == (sg.B - tl.x + 31) / 32) {
           kci = 0;
           ++ti;
@@ -805,7 +847,7 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
     // FP16x3: data scale of this thread's column (its function's), from the
     // magnitude loaded a tile ahead (~0u past the columns)
     auto col_amax = [&](int tt) -> unsigned {
-      const int f = rad_fn_of(s_seg[s_tiles[tt].z], s_tiles[tt], tid);
+      const int f = rad_fn_of<PAIR>(s_seg[s_tiles[tt].z], s_tiles[tt], tid);
       return f >= 0 ? a.amax[f] : ~0u;
     };
     unsigned amx = 0u;
@@ -831,9 +873,20 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
       // is refilled with chunk c + kGatherDepth
       cp_async_wait<kGatherDepth - 1>();
       float v[16];
-      const float* gv = gslots + (c % kGatherSlots) * (kGatherSlotBytes / 4) + tid;
+      const float* gs = gslots + (c % kGatherSlots) * (kGatherSlotBytes / 4);  // the chunk's slot
+      if constexpr (PAIR) {  // v[2k], v[2k + 1] = re, im of degree k: slot as float2 [k][tid]
+        const float2* gv2 = (const float2*)gs + tid;
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = gv[k * 256];
+        for (int k = 0; k < 8; ++k) {
+          const float2 w = gv2[k * 256];
+          v[2 * k] = w.x;
+          v[2 * k + 1] = w.y;
+        }
+      } else {  // slot as float [k][tid]
+        const float* gv = gs + tid;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = gv[k * 256];
+      }
       issue_next();
       const int s = c % kStagesRadI;
       if (!mbar_wait(empty + s, ((c / kStagesRadI) & 1) ^ 1, abort_flag)) break;
@@ -846,11 +899,28 @@ __global__ void __launch_bounds__(kThreadsInv, 1) tc_rad_inv_kernel(RadIArgs a) 
           unsigned char* hb = sb + ((tid >> 6) & 1) * (128 * ROWB);
           split_store_bf<4, F16>(hb, hb + 64 * ROWB, tid & 63, v, 4 * (tid >> 7), xf);
         }
-      } else if (nar) {
-        split_store<2>(sb, sb + 64 * ROWB, tid & 63, v, 2 * (tid >> 6), a.nprod == 3);
       } else {
-        unsigned char* hb = sb + ((tid >> 6) & 1) * (128 * ROWB);
-        split_store<4>(hb, hb + 64 * ROWB, tid & 63, v, 4 * (tid >> 7), a.nprod == 3);
+        // rows 2 pi (re) and 2 pi + 1 (im) of the pair's half; lanes whose
+        // pair has bit 2 set store the im row first, so that each store
+        // instruction's rows cover all eight 16-byte bank groups of the
+        // 128-byte swizzle (conflict-free)
+        const int pi = nar ? (tid & 31) : (tid & 63);
+        unsigned char* hb = sb + (nar ? 0 : (pi >> 5) * (128 * ROWB));
+        const int r0 = (2 * pi) & 63;
+        const bool sw = (pi >> 2) & 1;
+        float va[8], vb[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          va[k] = sw ? v[2 * k + 1] : v[2 * k];
+          vb[k] = sw ? v[2 * k] : v[2 * k + 1];
+        }
+        if (nar) {
+          split_store<1>(hb, hb + 64 * ROWB, r0 + (sw ? 1 : 0), va, tid >> 5, a.nprod == 3);
+          split_store<1>(hb, hb + 64 * ROWB, r0 + (sw ? 0 : 1), vb, tid >> 5, a.nprod == 3);
+        } else {
+          split_store<2>(hb, hb + 64 * ROWB, r0 + (sw ? 1 : 0), va, 2 * (tid >> 6), a.nprod == 3);
+          split_store<2>(hb, hb + 64 * ROWB, r0 + (sw ? 0 : 1), vb, 2 * (tid >> 6), a.nprod == 3);
+        }
       }
       fence_proxy_async();
       mbar_arrive(split + s);

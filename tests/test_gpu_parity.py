@@ -354,6 +354,27 @@ def test_tf32x3_full_size_b128_sampled_functions():
     p.check()
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
+def test_repeated_calls_are_bit_identical(prec):
+    # B=128, 128 functions: every tile's arithmetic is fixed, whichever CTA
+    # takes it from the work queue and whenever, so repeated calls on the same
+    # input give the same bits; a race between the pipeline roles (a ring
+    # slot refilled before its reader is done with it) shows up here as
+    # differing rows of a few tiles
+    B, NB = 128, 128
+    p = _plan(B, NB, prec)
+    c = inputs.random_coeffs(B, NB, seed=inputs.BASE_SEED + 12, decay=True).astype(np.complex64)
+    cd = torch.from_numpy(c).cuda()
+    s = p.inverse(cd)
+    f = p.forward(s)
+    for _ in range(3):
+        assert torch.equal(p.inverse(cd), s)
+        assert torch.equal(p.forward(s), f)
+    p.check()
+    del s, f, cd
+    torch.cuda.empty_cache()
+
+
 def test_tf32x3_b128_batch256_offsets_beyond_2_31():
     # B=128, 256 functions: the phi-FFT spectra alone hold 4.3e9 floats
     # (beyond 2^31), so every offset of the path must be 64-bit.  Round trip
