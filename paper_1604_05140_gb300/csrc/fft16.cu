@@ -136,37 +136,65 @@ constexpr int smallest_factor(int n) {
   return n;
 }
 
+// P-point DFT of x in natural order, in place, P = 2 or an odd prime, with
+// w[j] = W_NT^j (P divides NT).  Odd P: the sums s_j = x_j + x_{P-j} and
+// differences d_j = x_j - x_{P-j} (j = 1 .. (P-1)/2) give
+//   X_0 = x_0 + sum_j s_j,
+//   X_k, X_{P-k} = A_k -/+ i B_k,  A_k = x_0 + sum_j s_j cos(2 pi jk/P),
+//                                  B_k = sum_j d_j sin(2 pi jk/P)
+// (forward; the inverse swaps the signs), real-by-complex products only:
+// (P-1)^2 real multiply-adds against 4 (P-1)^2 for the plain sum.
+template <typename real, int P, int NT, bool INV>
+__device__ __forceinline__ void dft_prime(c2<real>* x, const c2<real>* w) {
+  if constexpr (P == 2) {
+    const c2<real> a = x[0], b = x[1];
+    x[0] = a + b;
+    x[1] = a - b;
+  } else {
+    constexpr int H = (P - 1) / 2, WSP = NT / P;
+    c2<real> sm[H], df[H];
+    c2<real> x0 = x[0], tot = x[0];
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+      sm[j - 1] = x[j] + x[P - j];
+      df[j - 1] = x[j] - x[P - j];
+      tot = tot + sm[j - 1];
+    }
+    x[0] = tot;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+      c2<real> A = x0, Bv = {(real)0, (real)0};
+#pragma unroll
+      for (int j = 1; j <= H; ++j) {
+        const c2<real> t = w[((j * k) % P) * WSP];  // cos - i sin of 2 pi jk / P
+        A = {A.x + sm[j - 1].x * t.x, A.y + sm[j - 1].y * t.x};
+        Bv = {Bv.x - df[j - 1].x * t.y, Bv.y - df[j - 1].y * t.y};
+      }
+      // -i Bv = (Bv.y, -Bv.x)
+      const c2<real> mib = {Bv.y, -Bv.x};
+      x[k] = INV ? A - mib : A + mib;
+      x[P - k] = INV ? A + mib : A - mib;
+    }
+  }
+}
+
 // N-point DFT (INV: the inverse, unscaled) of v in natural order, in place,
 // 2 <= N <= 16.  Powers of two: the radix-2 FFT above.  Other sizes: mixed
-// radix, decimation in time over the smallest prime factor P (P subsequences
-// of stride P, each transformed recursively, then P-point butterflies with
-// twiddles); prime sizes directly.  w[j] = W_NT^j, j < NT, is the root table
-// of the size NT this transform belongs to (N divides NT); every index into it
-// is a compile-time constant once the loops are unrolled, so w stays in
-// registers.
+// radix, decimation in time over the smallest prime factor P: P subsequences
+// of stride P, each transformed recursively (Q = N / P points), then for each
+// q < Q the twiddled values W_N^{rq} sub_r[q] go through one P-point DFT,
+// which gives the outputs q + Q s; prime sizes by dft_prime.  w[j] = W_NT^j,
+// j < NT, is the root table of the size NT this transform belongs to (N
+// divides NT); every index into it is a compile-time constant once the loops
+// are unrolled, so w stays in registers.
 template <typename real, int N, int NT, bool INV>
 __device__ __forceinline__ void dft_any(c2<real>* v, const c2<real>* w) {
   if constexpr (is_pow2(N)) {
     fft_n<real, N, INV>(v);
   } else {
     constexpr int P = smallest_factor(N), Q = N / P, WS = NT / N;
-    c2<real> out[N];
     if constexpr (Q == 1) {
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        c2<real> acc = v[0];
-#pragma unroll
-        for (int n = 1; n < N; ++n) {
-          if (k == 0) {
-            acc = acc + v[n];
-          } else {
-            c2<real> t = w[((n * k) % N) * WS];
-            if (INV) t.y = -t.y;
-            acc = acc + cmul(v[n], t);
-          }
-        }
-        out[k] = acc;
-      }
+      dft_prime<real, N, NT, INV>(v, w);
     } else {
       c2<real> sub[P][Q];
 #pragma unroll
@@ -176,24 +204,25 @@ __device__ __forceinline__ void dft_any(c2<real>* v, const c2<real>* w) {
         dft_any<real, Q, NT, INV>(sub[r], w);
       }
 #pragma unroll
-      for (int k = 0; k < N; ++k) {
-        c2<real> acc = sub[0][k % Q];
+      for (int q = 0; q < Q; ++q) {
+        c2<real> t[P];
+        t[0] = sub[0][q];
 #pragma unroll
         for (int r = 1; r < P; ++r) {
-          const int e = (r * k) % N;
+          const int e = (r * q) % N;
           if (e == 0) {
-            acc = acc + sub[r][k % Q];
+            t[r] = sub[r][q];
           } else {
-            c2<real> t = w[e * WS];
-            if (INV) t.y = -t.y;
-            acc = acc + cmul(sub[r][k % Q], t);
+            c2<real> tw = w[e * WS];
+            if (INV) tw.y = -tw.y;
+            t[r] = cmul(sub[r][q], tw);
           }
         }
-        out[k] = acc;
+        dft_prime<real, P, NT, INV>(t, w);
+#pragma unroll
+        for (int s = 0; s < P; ++s) v[q + Q * s] = t[s];
       }
     }
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = out[k];
   }
 }
 
