@@ -218,10 +218,14 @@ __global__ void __launch_bounds__(kThreads, 2) midpoint_kernel(MidArgs<real> a) 
         const real ec = eph[(k * B + amq[q]) * 2];
         const real es = neg[q] ? -eph[(k * B + amq[q]) * 2 + 1] : eph[(k * B + amq[q]) * 2 + 1];
         const real hr = amp * ec, hi = amp * es;
+        // four multiply-adds per function (written out: acc += (a - b) would
+        // round a - b first and cost a third instruction)
 #pragma unroll
         for (int j = 0; j < kFn; ++j) {
-          acc_re[q][j] += fr[j] * hr - fi[j] * hi;
-          acc_im[q][j] += fr[j] * hi + fi[j] * hr;
+          acc_re[q][j] = fma(fr[j], hr, acc_re[q][j]);
+          acc_re[q][j] = fma(-fi[j], hi, acc_re[q][j]);
+          acc_im[q][j] = fma(fr[j], hi, acc_im[q][j]);
+          acc_im[q][j] = fma(fi[j], hr, acc_im[q][j]);
         }
       }
     }
