@@ -683,10 +683,11 @@ done:
 static std::string tuning_text(const Plan& P, const char* source) {
   char buf[256];
   snprintf(buf, sizeof buf,
-           "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d queue=%d "
+           "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d queue=%d,%d,%d,%d "
            "inv_order=%d source=%s",
            fft_jp(P, P.maxB, false), fft_jp(P, P.maxB, true), P.radi_narrow, P.simt_policy[0], P.simt_policy[1],
-           P.simt_policy[2], P.simt_policy[3], P.rad_rows, P.fft_merge, P.queue_slices, P.fft_inv_order, source);
+           P.simt_policy[2], P.simt_policy[3], P.rad_rows, P.fft_merge, P.queue_slices[0], P.queue_slices[1],
+           P.queue_slices[2], P.queue_slices[3], P.fft_inv_order, source);
   return buf;
 }
 
@@ -735,15 +736,17 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
       while (fgets(line, sizeof line, f)) {
         const std::string ln(line);
         if (ln.compare(0, key.size() + 3, key + " | ") != 0) continue;
-        int jf = 0, ji = 0, rn = 0, sp[4] = {0, 0, 0, 0}, rr = 64, fm = 1, qs = 2, io = 0;
+        int jf = 0, ji = 0, rn = 0, sp[4] = {0, 0, 0, 0}, rr = 64, fm = 1, qs[4] = {2, 2, 2, 2}, io = 0;
         const int got = sscanf(ln.c_str() + key.size() + 3,
                                "fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d "
-                               "queue=%d inv_order=%d",
-                               &jf, &ji, &rn, &sp[0], &sp[1], &sp[2], &sp[3], &rr, &fm, &qs, &io);
+                               "queue=%d,%d,%d,%d inv_order=%d",
+                               &jf, &ji, &rn, &sp[0], &sp[1], &sp[2], &sp[3], &rr, &fm, &qs[0], &qs[1], &qs[2], &qs[3],
+                               &io);
+        // lines of fewer fields (older formats) keep the defaults of the rest
         bool valid = (got == 3 || got >= 8) && jf >= 1 && jf <= 16 && ji >= 1 && ji <= 16 && rn >= 1;
         for (int k = 0; k < 4; ++k) valid = valid && sp[k] >= 0 && sp[k] <= 2;
-        valid = valid && (rr == 32 || rr == 48 || rr == 64) && (fm == 0 || fm == 1) && (qs == 1 || qs == 2 || qs == 4) &&
-                (io == 0 || io == 1);
+        for (int k = 0; k < 4; ++k) valid = valid && (qs[k] == 1 || qs[k] == 2 || qs[k] == 4 || qs[k] == 8);
+        valid = valid && (rr == 32 || rr == 48 || rr == 64) && (fm == 0 || fm == 1) && (io == 0 || io == 1);
         if (valid) {
           P->jp_fwd = jf;
           P->jp_inv = ji;
@@ -751,7 +754,7 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
           for (int k = 0; k < 4; ++k) P->simt_policy[k] = sp[k];
           P->rad_rows = rr;
           P->fft_merge = fm;
-          P->queue_slices = qs;
+          for (int k = 0; k < 4; ++k) P->queue_slices[k] = qs[k];
           P->fft_inv_order = io;
           cached = true;
         }
@@ -852,22 +855,26 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
         }
       }
       P->rad_rows = best_rr;
-      // work-queue granularity of the tensor-core stages: slices per CTA
-      int best_q = 2;
-      tbest = 1e30;
-      for (int q : {2, 1, 4}) {
-        P->queue_slices = q;
-        tc_release(*P);
-        e = tc_prepare(*P);
-        if (e != cudaSuccess) return cuda_fail(P, e, "autotune tensor-core preparation");
-        const double t = time_calls(*P, true, samples, coeffs, s) + time_calls(*P, false, samples, coeffs, s);
-        if (t < 0.0) return cuda_fail(P, cudaGetLastError(), "autotune launch");
-        if (t < tbest) {
-          tbest = t;
-          best_q = q;
+      // work-queue granularity of each tensor-core stage (slices per CTA),
+      // one stage at a time: the forward stages timed on forward calls, the
+      // inverse stages on inverse calls
+      for (int st = 0; st < 4; ++st) {
+        int best_q = P->queue_slices[st];
+        tbest = 1e30;
+        for (int q : {2, 1, 4, 8}) {
+          P->queue_slices[st] = q;
+          tc_release(*P);
+          e = tc_prepare(*P);
+          if (e != cudaSuccess) return cuda_fail(P, e, "autotune tensor-core preparation");
+          const double t = time_calls(*P, st < 2, samples, coeffs, s);
+          if (t < 0.0) return cuda_fail(P, cudaGetLastError(), "autotune launch");
+          if (t < tbest) {
+            tbest = t;
+            best_q = q;
+          }
         }
+        P->queue_slices[st] = best_q;
       }
-      P->queue_slices = best_q;
     } else {
       // SIMT tile family of each GEMM stage, one stage at a time (forward
       // stages timed on forward calls, inverse stages on inverse calls)
@@ -904,10 +911,11 @@ static sgl_status autotune(Plan* P, void* samples, void* coeffs, const char* cac
     FILE* f = fopen(cache_path, "a");
     if (!f) return fail(P, SGL_ERR_ARG, std::string("cannot append to tuning cache ") + cache_path);
     fprintf(f,
-            "%s | fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d queue=%d "
-            "inv_order=%d\n",
+            "%s | fft_fwd_jp=%d fft_inv_jp=%d rad_inv_narrow=%d simt=%d,%d,%d,%d rad_rows=%d fft_merge=%d "
+            "queue=%d,%d,%d,%d inv_order=%d\n",
             key.c_str(), P->jp_fwd, P->jp_inv, P->radi_narrow, P->simt_policy[0], P->simt_policy[1],
-            P->simt_policy[2], P->simt_policy[3], P->rad_rows, P->fft_merge, P->queue_slices, P->fft_inv_order);
+            P->simt_policy[2], P->simt_policy[3], P->rad_rows, P->fft_merge, P->queue_slices[0], P->queue_slices[1],
+            P->queue_slices[2], P->queue_slices[3], P->fft_inv_order);
     fclose(f);
   }
   return SGL_OK;

@@ -254,8 +254,9 @@ struct Plan {
   // plans of several register-FFT sizes: one multi-size phi-FFT launch per
   // direction (1) or one launch per size (0)
   int fft_merge = 1;
-  // work-queue slices per CTA of the tensor-core stages (1, 2 or 4)
-  int queue_slices = 2;
+  // work-queue slices per CTA of each tensor-core stage (1, 2, 4 or 8):
+  // forward Legendre, forward radial, inverse radial, Legendre synthesis
+  int queue_slices[4] = {2, 2, 2, 2};
   // CTA order of the tensor-core plans' inverse phi-FFT: shell blocks outer
   // (0) or ring pairs outer (1)
   int fft_inv_order = 0;

@@ -905,12 +905,12 @@ static cudaError_t tc_prepare_impl(Plan& P) {
                             : (size_t)kRawTf32 * kChunkBytes + (size_t)kOps * 2 * kChunkBytes;
     const size_t fixed = 1024 + (size_t)2 * S.KCmax * S.npmax * (bf ? 64 : 128) + rings + 64 * 8 +
                          (size_t)S.nseg * sizeof(SegSmall) + 16 + 12 + 16;
-    // work queue: P.queue_slices cost-balanced slices per CTA of one wave
+    // work queue: P.queue_slices[k] cost-balanced slices per CTA of one wave
     // (more while one slice's shared-memory copies would not fit)
     // shared memory per slice: 16 bytes a tile, 16 bytes a group the tiles
     // span (counted exactly: groups without tiles may lie in between)
     S.grid = std::max(1, std::min(S.ntiles, nsm));
-    S.nslices = std::max(1, std::min(S.ntiles, S.grid * P.queue_slices));
+    S.nslices = std::max(1, std::min(S.ntiles, S.grid * P.queue_slices[k]));
     auto group_span = [&](const std::vector<int>& fst) {
       int g = 1;
       for (int k = 0; k < (int)fst.size() - 1; ++k)

@@ -1213,11 +1213,11 @@ static cudaError_t radi_tiles(const Plan& P, TcInvState& st, int nsm, int64_t& b
   // slice; more waves of CTAs while that does not fit
   const size_t fixed = 1024 + (size_t)kStagesRadI * 4 * kChunk + (size_t)kGatherSlots * kGatherSlotBytes + 64 * 8 +
                        (P.segs.size() + 1) * (sizeof(RadISeg) + 4) + 8 + 16;
-  // work queue: P.queue_slices cost-balanced slices per CTA of one wave, more
+  // work queue: P.queue_slices[2] cost-balanced slices per CTA of one wave, more
   // while a slice's copies do not fit
   const int n = (int)rc.size();
   st.rad_grid = std::max(1, std::min(n, nsm));
-  st.rad_nslices = std::max(1, std::min(n, st.rad_grid * P.queue_slices));
+  st.rad_nslices = std::max(1, std::min(n, st.rad_grid * P.queue_slices[2]));
   std::vector<int> rf;
   for (;;) {
     int rmax = 0;
@@ -1381,7 +1381,7 @@ cudaError_t tc_inv_prepare(Plan& P) {
                         (size_t)kStagesLegI * 2 * kChunk + 64 * 8 + lsegs.size() * sizeof(LegISegSmall) + 16;
   int lmax = 0;
   const std::vector<int> lf =
-      slices_for(lcost, nsm, P.queue_slices, lfixed, 32, &st->leg_grid, &st->leg_nslices, &lmax);
+      slices_for(lcost, nsm, P.queue_slices[3], lfixed, 32, &st->leg_grid, &st->leg_nslices, &lmax);
   if (e == cudaSuccess) e = upload(&st->leg_first, lf, bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&st->leg_queue, sizeof(int));
   st->leg_smem = lfixed + (size_t)(lmax + 1) * 32;

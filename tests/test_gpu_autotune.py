@@ -25,7 +25,7 @@ def _parse(text):
     """(fft_fwd_jp, fft_inv_jp, rad_inv_narrow, source); the tile shapes are
     checked by _shapes."""
     m = re.match(r"fft_fwd_jp=(\d+) fft_inv_jp=(\d+) rad_inv_narrow=(\d+) simt=\d,\d,\d,\d rad_rows=\d+ "
-                 r"fft_merge=[01] queue=[124] inv_order=[01] source=(\w+)$", text)
+                 r"fft_merge=[01] queue=[1248],[1248],[1248],[1248] inv_order=[01] source=(\w+)$", text)
     assert m, text
     return int(m.group(1)), int(m.group(2)), int(m.group(3)), m.group(4)
 
@@ -125,7 +125,7 @@ def test_merged_fft_launch_keeps_results(tmp_path):
     line = re.sub(r"fft_fwd_jp=\d+ fft_inv_jp=\d+ rad_inv_narrow=\d+", "fft_fwd_jp=16 fft_inv_jp=16 rad_inv_narrow=65",
                   line)
     line = re.sub(r"rad_rows=\d+", "rad_rows=64", line)
-    line = re.sub(r"queue=\d", "queue=2", line)
+    line = re.sub(r"queue=[\d,]+", "queue=2,2,2,2", line)
     line = re.sub(r"inv_order=\d", "inv_order=0", line)
     for fm in (0, 1):
         forced = tmp_path / f"fm{fm}.txt"
@@ -157,9 +157,9 @@ def test_work_queue_granularity_keeps_results(tmp_path):
     Plan.many(Bs, precision="tf32x3").autotune(cache=first)
     line = open(first).read().splitlines()[0]
     ref = None
-    for q, io in ((1, 0), (2, 1), (4, 0), (4, 1)):
-        forced = tmp_path / f"q{q}_{io}.txt"
-        forced.write_text(re.sub(r"inv_order=\d", f"inv_order={io}", re.sub(r"queue=\d", f"queue={q}", line)) + "\n")
+    for q, io in (("1,1,1,1", 0), ("2,2,2,2", 1), ("4,8,1,2", 0), ("8,4,8,4", 1)):
+        forced = tmp_path / f"q{q.replace(',', '')}_{io}.txt"
+        forced.write_text(re.sub(r"inv_order=\d", f"inv_order={io}", re.sub(r"queue=[\d,]+", f"queue={q}", line)) + "\n")
         plan = Plan.many(Bs, precision="tf32x3")
         text = plan.autotune(cache=str(forced))
         assert f"queue={q}" in text and f"inv_order={io}" in text
