@@ -98,7 +98,8 @@ static void release_pipeline(Plan* P) {
   for (cudaEvent_t e : P->pipe_ev) cudaEventDestroy(e);
   P->pipe_ev.clear();
   if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
-  P->copy_stream = nullptr;
+  if (P->copy_back_stream) cudaStreamDestroy(P->copy_back_stream);
+  P->copy_stream = P->copy_back_stream = nullptr;
 }
 
 // Host tables depend on the bandlimit and the radial grid only; built once
@@ -504,7 +505,8 @@ static sgl_status ensure_pipeline(Plan* P) {
   };
   sgl_status st = make(q, &P->sub);
   if (st == SGL_OK && r != q) st = make(r, &P->sub_tail);
-  if (st == SGL_OK && cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+  if (st == SGL_OK && (cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaStreamCreateWithFlags(&P->copy_back_stream, cudaStreamNonBlocking) != cudaSuccess))
     st = fail(P, SGL_ERR_CUDA, "copy stream creation failed");
   for (int k = 0; st == SGL_OK && k < 2 * nchunks + 2; ++k) {
     cudaEvent_t ev;
@@ -545,7 +547,12 @@ static sgl_status execute_pipelined(Plan* P, bool is_fwd, bool weights, const vo
   const int q = P->sub_q, n = (P->nfn + q - 1) / q;
   cudaEvent_t* ev = P->pipe_ev.data();  // [0] start, [1] end, then in/out per chunk
   cudaError_t e = cudaEventRecord(ev[0], s);
+  // chunk k: its host-to-device copy on copy_stream (not held back by
+  // anything but the start, so it runs while earlier chunks compute), its
+  // transform on s once the copy is in, its device-to-host copy on
+  // copy_back_stream once the transform is done
   if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_stream, ev[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_back_stream, ev[0], 0);
   for (int k = 0; k < n && e == cudaSuccess; ++k) {
     const int f0 = k * q, nk = std::min(q, P->nfn - f0);
     Plan* S = nk == q ? P->sub : P->sub_tail;
@@ -560,12 +567,15 @@ static sgl_status execute_pipelined(Plan* P, bool is_fwd, bool weights, const vo
       e = is_fwd ? run_forward(*S, din + io, dout + oo, s, weights) : run_inverse(*S, din + io, dout + oo, s, weights);
     if (e == cudaSuccess && !out_dev) {
       e = cudaEventRecord(ev[3 + 2 * k], s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_stream, ev[3 + 2 * k], 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_back_stream, ev[3 + 2 * k], 0);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync((char*)out + oo, dout + oo, (size_t)nk * out_per, cudaMemcpyDeviceToHost, P->copy_stream);
+        e = cudaMemcpyAsync((char*)out + oo, dout + oo, (size_t)nk * out_per, cudaMemcpyDeviceToHost,
+                            P->copy_back_stream);
     }
   }
-  if (e == cudaSuccess) e = cudaEventRecord(ev[1], P->copy_stream);
+  // the device-to-host copies follow every transform, which follow every
+  // host-to-device copy: the end of copy_back_stream is the end of the call
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], P->copy_back_stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(P, e, "sub-batch execution");

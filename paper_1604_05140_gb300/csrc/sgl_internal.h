@@ -273,7 +273,8 @@ struct Plan {
   Plan* sub = nullptr;
   Plan* sub_tail = nullptr;
   int sub_q = 0;
-  cudaStream_t copy_stream = nullptr;
+  cudaStream_t copy_stream = nullptr;       // host-to-device copies of the chunks
+  cudaStream_t copy_back_stream = nullptr;  // device-to-host copies (the other direction of the link)
   std::vector<cudaEvent_t> pipe_ev;
   bool owns_err = true;
 
