@@ -227,13 +227,23 @@ __device__ __forceinline__ void dft_any(c2<real>* v, const c2<real>* w) {
 }
 
 // Shared-memory position (complex units) of row `row` (< 16), column `col`
-// (< N2) of ring r: rows of N2 columns, swizzled by row and ring pair (XOR
-// for powers of two, a rotation otherwise) so that the column-wise writes and
-// the row-wise reads spread over the banks.
+// (< N2) of ring r, laid out so that both access patterns of the transpose —
+// consecutive (ring, column) items at one row, and the 16 ring pairs at one
+// (row, column) — spread over the banks.  Powers of two: rows of N2 columns,
+// swizzled by row and ring pair (XOR).  Other N2: columns of 16 rows padded to
+// 17 (ring stride 17 N2), the rows rotated by the ring pair: consecutive items
+// then step by one bank, and ring pair q lands q (2 N2 + 1) banks further, an
+// odd multiple, so the 16 pairs hit 16 different banks (no remainder by N2).
 template <int N2>
 __device__ __forceinline__ int spos(int r, int row, int col) {
   if constexpr (is_pow2(N2)) return r * (16 * N2) + row * N2 + ((col ^ row ^ (r >> 1)) & (N2 - 1));
-  else return r * (16 * N2) + row * N2 + (col + row + (r >> 1)) % N2;
+  else return r * (17 * N2) + col * 17 + ((row + (r >> 1)) & 15);
+}
+
+// Complex elements of one ring in the transpose buffer.
+template <int N2>
+constexpr int ring_elems() {
+  return is_pow2(N2) ? 16 * N2 : 17 * N2;
 }
 
 }  // namespace
@@ -246,8 +256,8 @@ __device__ __forceinline__ void fft16_fwd_body(const Fft16Args& a) {
   constexpr int N = 16 * N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c2<real>* tw = reinterpret_cast<c2<real>*>(smem_raw);      // [k1 < 16][c < N2]: W_N^{c k1}
-  c2<real>* buf = tw + N;                                    // 2*JP rings of N
-  c2<real>* w2s = buf + 2 * a.JP * N;                        // W_N2^j, j < N2
+  c2<real>* buf = tw + N;                                    // 2*JP rings of ring_elems<N2>()
+  c2<real>* w2s = buf + 2 * a.JP * ring_elems<N2>();         // W_N2^j, j < N2
   const int4 cta = a.ctas[blockIdx.x];
   const SegDesc sg = a.segs[cta.x];
   const int B = sg.B, NB = sg.NB, NR = sg.R;  // NR radii
@@ -519,7 +529,8 @@ bool fft16_launch_multi(bool inv, const Fft16Args& a, int max_n2, int nctas, cud
   if (max_n2 < 2 || max_n2 > 16 || a.pair_limit) return false;
   void (*fn)(Fft16Args) = inv ? fft16_inv_multi_kernel : fft16_fwd_multi_kernel;
   const int N = 16 * max_n2;
-  const size_t smem = sizeof(c2<float>) * ((size_t)N + (size_t)2 * a.JP * N + (size_t)max_n2);
+  // transpose rings of at most 17 max_n2 elements (padded layout of the sizes that are not powers of two)
+  const size_t smem = sizeof(c2<float>) * ((size_t)N + (size_t)2 * a.JP * 17 * max_n2 + (size_t)max_n2);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     fn<<<nctas, 16 * a.JP, smem, s>>>(a);
@@ -568,7 +579,8 @@ bool fft16_launch(bool inv, const Fft16Args& a, int n1, int n2, int nctas, cudaS
   }
   if (!fn) return false;
   const int N = 16 * n2;
-  const size_t smem = sizeof(c2<real>) * ((size_t)N + (size_t)2 * a.JP * N + (size_t)n2);
+  const bool p2 = (n2 & (n2 - 1)) == 0;
+  const size_t smem = sizeof(c2<real>) * ((size_t)N + (size_t)2 * a.JP * (p2 ? 16 : 17) * n2 + (size_t)n2);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     fn<<<nctas, 16 * a.JP, smem, s>>>(a);
