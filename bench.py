@@ -429,15 +429,16 @@ def real_path(steps, warmup):
 
 
 def paper_grid_path(steps, warmup):
-    """The paper's own grid (2B half-range Gauss-Hermite radii, FP64/FP32
-    plans): the paper's timing configuration (B=64, one function, round trip
-    in FP64, as in its Table 2) and B=128 x 16 functions in FP64 and FP32.
-    Round trip on seeded decaying coefficients, CUDA events."""
+    """The paper's own grid (2B half-range Gauss-Hermite radii): the paper's
+    timing configuration (B=64, one function, round trip in FP64, as in its
+    Table 2) and B=128 x 16 functions in FP64, FP32 and TF32x3 (the
+    tensor-core stages run each function's radii as two halves).  Round trip
+    on seeded decaying coefficients, CUDA events."""
     import torch
     from paper_1604_05140_gb300 import Plan, inputs
     out = {}
     for label, B, nb, prec in (("b64x1_fp64", 64, 1, "fp64"), ("b128x16_fp64", 128, 16, "fp64"),
-                               ("b128x16_fp32", 128, 16, "fp32")):
+                               ("b128x16_fp32", 128, 16, "fp32"), ("b128x16_tf32x3", 128, 16, "tf32x3")):
         plan = Plan(B, nb, prec, grid="hermite")
         c = torch.from_numpy(inputs.random_coeffs(B, nb, seed=inputs.BASE_SEED + 6, decay=True)).to(plan.dtype).cuda()
         s = torch.empty(plan.sample_shape, dtype=plan.dtype, device="cuda")

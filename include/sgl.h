@@ -171,11 +171,15 @@ sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples);
 
 /*
  * sgl_plan_grid - sgl_plan on the radial grid `grid` (an sgl_grid_kind).
- * SGL_GRID_LAGUERRE is sgl_plan itself.  SGL_GRID_HALF_RANGE_HERMITE needs
- * SGL_FP64 or SGL_FP32 (the tensor-core precisions return
- * SGL_ERR_UNSUPPORTED); every sample convention is accepted.  Sample counts,
- * offsets, sgl_grid's r and w_r arrays and the host-buffer staging follow
- * the plan's 2B radii.
+ * SGL_GRID_LAGUERRE is sgl_plan itself.  SGL_GRID_HALF_RANGE_HERMITE takes
+ * every precision and sample convention, except SGL_SAMPLES_REAL with a
+ * tensor-core precision (SGL_ERR_UNSUPPORTED).  Sample counts, offsets,
+ * sgl_grid's r and w_r arrays and the host-buffer staging follow the plan's
+ * 2B radii.  Tensor-core plans run each function's radial sums (Eq.
+ * DRT_matrix over the 2B nodes) as two partial sums over the first and the
+ * second B nodes, added by one more kernel per forward call (Thm 3.3 and
+ * Thm 3.4 are unchanged: the same rule, summed in two parts); host buffers
+ * are staged whole, without sub-batches.
  */
 sgl_status sgl_plan_grid(sgl_plan_t* out, int B, int batch, int prec, int samples, int grid);
 

@@ -118,6 +118,24 @@ static bool cached_tables(int B, int grid, HostTables& out, std::string& msg) {
   return true;
 }
 
+// Half h of a radial rule of 2B nodes (the paper's grid) as a rule of B
+// nodes: nodes, weights and radial functions at radii h B .. h B + B - 1
+// (the radial sums of Eq. DRT_matrix split into two partial sums); the
+// sphere tables are unchanged.
+static HostTables radial_half(const HostTables& H, int h) {
+  HostTables out = H;
+  const int B = H.B, R = H.R, i0 = h * B;
+  out.R = B;
+  out.t.assign(H.t.begin() + i0, H.t.begin() + i0 + B);
+  out.r.assign(H.r.begin() + i0, H.r.begin() + i0 + B);
+  out.what.assign(H.what.begin() + i0, H.what.begin() + i0 + B);
+  const size_t rows = H.T.size() / (size_t)R;  // (l, n-1) rows of R radii
+  out.T.assign(rows * (size_t)B, 0.0);
+  for (size_t q = 0; q < rows; ++q)
+    std::copy(H.T.begin() + q * R + i0, H.T.begin() + q * R + i0 + B, out.T.begin() + q * B);
+  return out;
+}
+
 template <typename real>
 void sgl::pack_tables(const Plan& P, std::vector<real>& tab) {
   tab.assign(P.tab_elems, real(0));
@@ -195,7 +213,7 @@ static void set_launch_count(Plan& P) {
     fwd += P.leg_fwd.launches() + P.rad_fwd.launches() + (P.seminaive ? (int)P.segs.size() : 0);
     inv += P.rad_inv.launches() + P.leg_inv.launches();
   }
-  P.launches_per_call = std::max(fwd, inv) + (P.real_pairs ? 1 : 0);
+  P.launches_per_call = std::max(fwd, inv) + (P.real_pairs || P.radial_halves ? 1 : 0);
 }
 
 // FFT CTA lists of both directions (segment order) for the plan's current
@@ -302,27 +320,40 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
   P->nfn = (int)Bs.size();
   P->uniform = uniform;
   P->fn_B = Bs;
-  // offsets in user order
+  // offsets in user order (radial halves: the halves in order, B radii each)
+  const int grid_fn = P->radial_halves ? SGL_GRID_LAGUERRE : P->grid;  // radii of one function
   int64_t so = 0, co = 0;
   for (int B : Bs) {
     P->fn_samp_off.push_back(so);
     P->fn_coef_off.push_back(co);
-    so += sample_count(B, n_radial(B, P->grid));
+    so += sample_count(B, n_radial(B, grid_fn));
     co += coeff_count(B);
     P->maxB = std::max(P->maxB, B);
   }
   P->n_samples = so;
   P->n_coeffs = co;
-  // segments: group by bandlimit, largest first
-  std::map<int, std::vector<int>, std::greater<int>> by_B;
-  for (int f = 0; f < P->nfn; ++f) by_B[Bs[f]].push_back(f);
+  // segments: group by bandlimit, largest first; radial halves: one segment
+  // per half (even and odd functions), each with its half of the radial rule
+  std::vector<std::pair<int, std::vector<int>>> by_B;
+  if (P->radial_halves) {
+    for (int h = 0; h < 2; ++h) {
+      std::vector<int> fs;
+      for (int f = h; f < P->nfn; f += 2) fs.push_back(f);
+      by_B.push_back({Bs[0], fs});
+    }
+  } else {
+    std::map<int, std::vector<int>, std::greater<int>> m;
+    for (int f = 0; f < P->nfn; ++f) m[Bs[f]].push_back(f);
+    for (auto& kv : m) by_B.push_back(kv);
+  }
+  int half = 0;
   std::vector<int64_t> fn_samp, fn_coef, si_rows;
   int64_t w1 = 0, w2 = 0, tab = 0;
   for (auto& kv : by_B) {
     SegDesc sg;
     memset(&sg, 0, sizeof(sg));
     sg.B = kv.first;
-    sg.R = n_radial(sg.B, P->grid);
+    sg.R = n_radial(sg.B, grid_fn);
     sg.NB = (int)kv.second.size();
     sg.n1 = fft_n1(2 * sg.B);
     sg.n2 = 2 * sg.B / sg.n1;
@@ -357,6 +388,7 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
     HostTables H;
     std::string msg;
     if (!cached_tables(sg.B, P->grid, H, msg)) return fail(P, SGL_ERR_ARG, "table generation: " + msg);
+    if (P->radial_halves) H = radial_half(H, half++);
     P->tables.push_back(std::move(H));
     P->segs.push_back(sg);
   }
@@ -432,7 +464,7 @@ static size_t complex_bytes(const Plan& P) { return P.prec == SGL_FP64 ? 16 : 8;
 // bytes of one element of the user's sample array (a real for real-function plans)
 static size_t sample_bytes(const Plan& P) { return P.real_pairs ? complex_bytes(P) / 2 : complex_bytes(P); }
 // functions as the user counts them
-static int user_fns(const Plan& P) { return P.real_pairs ? P.nreal : P.nfn; }
+static int user_fns(const Plan& P) { return P.real_pairs ? P.nreal : P.radial_halves ? P.nuser : P.nfn; }
 
 // Forward Legendre stage by the seminaive algorithm (or back to the direct
 // sums); builds the DCT CTA list on first use.
@@ -656,7 +688,7 @@ static sgl_status execute(Plan* P, bool is_fwd, bool weights, const void* in, vo
     if (e != cudaSuccess) st = cuda_fail(P, e, "graph launch");
     goto done;
   }
-  if ((!in_dev || !out_dev) && P->uniform && !P->real_pairs && P->nfn >= kPipeMinFunctions) {
+  if ((!in_dev || !out_dev) && P->uniform && !P->real_pairs && !P->radial_halves && P->nfn >= kPipeMinFunctions) {
     st = execute_pipelined(P, is_fwd, weights, in, out, in_dev, out_dev, s);
     goto done;
   }
@@ -949,8 +981,8 @@ sgl_status sgl_plan_grid(sgl_plan_t* out, int B, int batch, int prec, int sample
     return fail(nullptr, SGL_ERR_ARG, "physical samples need an FP64 plan");
   if (grid != SGL_GRID_LAGUERRE && grid != SGL_GRID_HALF_RANGE_HERMITE)
     return fail(nullptr, SGL_ERR_ARG, "unknown radial grid");
-  if (grid == SGL_GRID_HALF_RANGE_HERMITE && tc_precision(prec))
-    return fail(nullptr, SGL_ERR_UNSUPPORTED, "the half-range Gauss-Hermite grid needs an FP64 or FP32 plan");
+  if (grid == SGL_GRID_HALF_RANGE_HERMITE && tc_precision(prec) && samples == SGL_SAMPLES_REAL)
+    return fail(nullptr, SGL_ERR_UNSUPPORTED, "real functions on the half-range Gauss-Hermite grid need an FP64 or FP32 plan");
   if (!bandlimit_supported(B)) return fail(nullptr, SGL_ERR_UNSUPPORTED, "unsupported bandlimit");
   if (tc_precision(prec) && B % 4 != 0)
     return fail(nullptr, SGL_ERR_UNSUPPORTED, "tensor-core plans need a bandlimit divisible by 4");
@@ -963,8 +995,23 @@ sgl_status sgl_plan_grid(sgl_plan_t* out, int B, int batch, int prec, int sample
     P->real_pairs = true;
     P->nreal = batch;
   }
-  std::vector<int> Bs(real ? (batch + 1) / 2 : batch, B);
+  // tensor-core stages on the paper's grid: the two halves of each
+  // function's 2B radii as two functions of B radii
+  const bool halves = grid == SGL_GRID_HALF_RANGE_HERMITE && tc_precision(prec);
+  if (halves) {
+    P->radial_halves = true;
+    P->nuser = batch;
+  }
+  std::vector<int> Bs(real ? (batch + 1) / 2 : halves ? 2 * batch : batch, B);
   sgl_status st = build_plan(P, Bs, true);
+  if (st == SGL_OK && halves) {
+    P->n_coeffs = (int64_t)batch * coeff_count(B);
+    const int64_t cbytes = (int64_t)P->nfn * coeff_count(B) * (int64_t)complex_bytes(*P);
+    if (cudaMalloc(&P->d_ccoef, cbytes) != cudaSuccess)
+      st = fail(P, SGL_ERR_ALLOC, "workspace allocation failed");
+    else
+      P->bytes += cbytes;
+  }
   if (st == SGL_OK && real) {
     P->n_samples = (int64_t)batch * sample_count(B, n_radial(B, grid));  // reals
     P->n_coeffs = (int64_t)batch * coeff_count(B);
@@ -1030,10 +1077,15 @@ sgl_status sgl_grid(sgl_plan_t plan, int fn, double* r, double* theta, double* p
   Plan* P = (Plan*)plan;
   if (!P) return fail(nullptr, SGL_ERR_ARG, "null plan");
   if (fn < 0 || fn >= user_fns(*P)) return fail(P, SGL_ERR_ARG, "function index out of range");
-  const int B = P->fn_B[P->real_pairs ? 0 : fn];
+  const int B = P->fn_B[P->real_pairs || P->radial_halves ? 0 : fn];
   size_t seg = 0;
   while (P->segs[seg].B != B) ++seg;
-  const HostTables& H = P->tables[seg];
+  HostTables full;  // radial halves: the whole rule, not a segment's half
+  if (P->radial_halves) {
+    std::string msg;
+    if (!cached_tables(B, P->grid, full, msg)) return fail(P, SGL_ERR_ARG, "table generation: " + msg);
+  }
+  const HostTables& H = P->radial_halves ? full : P->tables[seg];
   if (r) memcpy(r, H.r.data(), H.R * sizeof(double));
   if (theta) memcpy(theta, H.theta.data(), 2 * B * sizeof(double));
   if (phi) memcpy(phi, H.phi.data(), 2 * B * sizeof(double));
@@ -1048,14 +1100,14 @@ int64_t sgl_coeff_count(sgl_plan_t plan) { return plan ? ((Plan*)plan)->n_coeffs
 int64_t sgl_sample_offset(sgl_plan_t plan, int fn) {
   Plan* P = (Plan*)plan;
   if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
-  if (P->real_pairs) return (int64_t)fn * sample_count(P->fn_B[0], n_radial(P->fn_B[0], P->grid));
+  if (P->real_pairs || P->radial_halves) return (int64_t)fn * sample_count(P->fn_B[0], n_radial(P->fn_B[0], P->grid));
   return P->fn_samp_off[fn];
 }
 
 int64_t sgl_coeff_offset(sgl_plan_t plan, int fn) {
   Plan* P = (Plan*)plan;
   if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
-  if (P->real_pairs) return (int64_t)fn * coeff_count(P->fn_B[0]);
+  if (P->real_pairs || P->radial_halves) return (int64_t)fn * coeff_count(P->fn_B[0]);
   return P->fn_coef_off[fn];
 }
 
@@ -1064,13 +1116,13 @@ int sgl_num_functions(sgl_plan_t plan) { return plan ? user_fns(*(Plan*)plan) : 
 int sgl_bandlimit(sgl_plan_t plan, int fn) {
   Plan* P = (Plan*)plan;
   if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
-  return P->fn_B[P->real_pairs ? 0 : fn];
+  return P->fn_B[P->real_pairs || P->radial_halves ? 0 : fn];
 }
 
 int sgl_radii(sgl_plan_t plan, int fn) {
   Plan* P = (Plan*)plan;
   if (!P || fn < 0 || fn >= user_fns(*P)) return -1;
-  const int B = P->fn_B[P->real_pairs ? 0 : fn];
+  const int B = P->fn_B[P->real_pairs || P->radial_halves ? 0 : fn];
   return n_radial(B, P->grid);
 }
 

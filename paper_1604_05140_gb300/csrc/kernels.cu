@@ -1054,6 +1054,48 @@ static cudaError_t run_real_pairs(Plan& P, bool split, const void* src, void* ds
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// radial halves (tensor-core plans on the paper's grid)
+// ---------------------------------------------------------------------------
+// Function f runs as the functions 2f and 2f + 1 of B radii each (its first
+// and second half of the 2B-node radial rule).  The radial sums of
+// Eq. DRT_matrix over the 2B nodes are the sums of the two halves' partial
+// sums (forward, and the adjoint of the inverse); both halves synthesize from
+// the same coefficients (inverse, and the adjoint of the forward).
+template <typename real>
+__global__ void halves_sum_kernel(const cx<real>* __restrict__ vc, cx<real>* __restrict__ out, int64_t omega,
+                                  int nuser) {
+  const int64_t n = omega * nuser;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = k / omega, w = k - f * omega;
+    const cx<real> a = vc[2 * f * omega + w], b = vc[(2 * f + 1) * omega + w];
+    out[k] = {a.x + b.x, a.y + b.y};
+  }
+}
+
+template <typename real>
+__global__ void halves_copy_kernel(const cx<real>* __restrict__ in, cx<real>* __restrict__ vc, int64_t omega,
+                                   int nuser) {
+  const int64_t n = omega * nuser;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = k / omega, w = k - f * omega;
+    const cx<real> v = in[k];
+    vc[2 * f * omega + w] = v;
+    vc[(2 * f + 1) * omega + w] = v;
+  }
+}
+
+static cudaError_t run_halves(const Plan& P, bool sum, const void* src, void* dst, cudaStream_t s) {
+  const int64_t omega = coeff_count(P.fn_B[0]);
+  const int64_t n = omega * P.nuser;
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4 * 152);
+  if (sum)  // tensor-core precisions compute in FP32
+    halves_sum_kernel<float><<<blocks, 256, 0, s>>>((const cx<float>*)src, (cx<float>*)dst, omega, P.nuser);
+  else
+    halves_copy_kernel<float><<<blocks, 256, 0, s>>>((const cx<float>*)src, (cx<float>*)dst, omega, P.nuser);
+  return cudaGetLastError();
+}
+
 cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights) {
   if (P.real_pairs) {
     const bool d = P.prec == SGL_FP64;
@@ -1062,6 +1104,10 @@ cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t
     if (e != cudaSuccess) return e;
     return d ? run_real_pairs<double>(P, true, P.d_ccoef, coeffs, s)
              : run_real_pairs<float>(P, true, P.d_ccoef, coeffs, s);
+  }
+  if (P.radial_halves) {
+    const cudaError_t e = forward_t<float>(P, samples, P.d_ccoef, s, weights);
+    return e != cudaSuccess ? e : run_halves(P, true, P.d_ccoef, coeffs, s);
   }
   if (P.prec == SGL_FP64) return forward_t<double>(P, samples, coeffs, s, weights);
   return forward_t<float>(P, samples, coeffs, s, weights);
@@ -1075,6 +1121,10 @@ cudaError_t run_inverse(Plan& P, const void* coeffs, void* samples, cudaStream_t
     if (e != cudaSuccess) return e;
     return d ? inverse_t<double>(P, P.d_ccoef, samples, s, weights)
              : inverse_t<float>(P, P.d_ccoef, samples, s, weights);
+  }
+  if (P.radial_halves) {
+    const cudaError_t e = run_halves(P, false, coeffs, P.d_ccoef, s);
+    return e != cudaSuccess ? e : inverse_t<float>(P, P.d_ccoef, samples, s, weights);
   }
   if (P.prec == SGL_FP64) return inverse_t<double>(P, coeffs, samples, s, weights);
   return inverse_t<float>(P, coeffs, samples, s, weights);

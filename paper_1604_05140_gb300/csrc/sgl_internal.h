@@ -291,6 +291,14 @@ struct Plan {
   bool real_pairs = false;
   int nreal = 0;
   void* d_ccoef = nullptr;
+  // tensor-core plans on the paper's grid: each function's 2B radii run as
+  // two functions of B radii (its first and second half of the radial rule:
+  // two segments with their own radial tables); nfn counts those halves,
+  // nuser the caller's functions.  d_ccoef holds the halves' coefficients:
+  // the forward sums each function's two partial sums, the inverse gives both
+  // halves the function's coefficients.
+  bool radial_halves = false;
+  int nuser = 0;
 
   // forward Legendre stage by the seminaive algorithm (sgl_set_dlt, SIMT
   // plans): DCT CTA list (segment, first vector, vectors, 0)

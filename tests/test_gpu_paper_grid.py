@@ -144,3 +144,66 @@ def test_paper_grid_b128(prec):
     s0 = s[0].cpu().numpy()
     assert _err(s0[None], O.inverse(c[0], B, rule="hermite")) < TOL[prec]
     p.check()
+
+
+# tensor-core precisions on the paper's grid: each function's 2B radii run as
+# two functions of B radii (the first and second half of the radial rule),
+# whose radial partial sums (Eq. DRT_matrix) are added; the split-precision
+# gate of tests/tolerances.py applies
+SPLIT_PRECS = ["tf32x3", "fp16x3"]
+
+
+@pytest.mark.parametrize("prec", SPLIT_PRECS)
+@pytest.mark.parametrize("B,batch", [(8, 3), (32, 2), (64, 2)])
+def test_paper_grid_split_precision_vs_oracle(prec, B, batch):
+    from tolerances import SPLIT_TOL
+    p = _plan(B, batch, prec)
+    assert p.radii == 2 * B and p.sample_shape == (batch, 2 * B, 2 * B, 2 * B)
+    assert p.coeff_shape == (batch, O.coeff_count(B)) and p.lib.sgl_num_functions(p.handle) == batch
+    c = inputs.random_coeffs(B, batch, seed=2600 + B, decay=True)
+    s = p.inverse(_dev(c, torch.complex64)).cpu().numpy()
+    assert _err(s, O.inverse(c, B, rule="hermite")) < SPLIT_TOL
+    rng = np.random.default_rng(2700 + B)
+    shape = (batch, 2 * B, 2 * B, 2 * B)
+    g = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+    f = p.forward(_dev(g, torch.complex64)).cpu().numpy()
+    assert _err(f, O.forward(g.astype(np.complex128), B, rule="hermite")) < SPLIT_TOL
+    back = p.forward(_dev(O.inverse(c, B, rule="hermite"), torch.complex64)).cpu().numpy()
+    assert _err(back, c) < SPLIT_TOL
+    p.check()
+
+
+@pytest.mark.parametrize("prec", SPLIT_PRECS)
+def test_paper_grid_split_precision_adjoints_and_host_buffers(prec):
+    from tolerances import SPLIT_TOL
+    B, batch = 16, 2
+    p = _plan(B, batch, prec)
+    y = inputs.random_coeffs(B, batch, seed=2800)
+    x = (np.random.default_rng(2801).standard_normal((batch, 2 * B, 2 * B, 2 * B)) + 0j).astype(np.complex64)
+    a1 = p.adjoint(_dev(y, torch.complex64), of_inverse=False).cpu().numpy()
+    assert _err(a1, O.adjoint_forward(y, B, rule="hermite")) < SPLIT_TOL
+    a2 = p.adjoint(_dev(x, torch.complex64), of_inverse=True).cpu().numpy()
+    assert _err(a2, O.adjoint_inverse(x.astype(np.complex128), B, rule="hermite")) < SPLIT_TOL
+    # host buffers (whole-batch staging) give the device-buffer result bit for bit
+    c = inputs.random_coeffs(B, batch, seed=2802).astype(np.complex64)
+    dev = p.inverse(_dev(c, torch.complex64)).cpu()
+    assert torch.equal(dev, p.inverse(torch.from_numpy(c)))
+    assert torch.equal(p.forward(dev.cuda()).cpu(), p.forward(dev))
+    p.check()
+
+
+def test_paper_grid_split_precision_b128():
+    # B = 128 on 256 radii, TF32x3: one function against the oracle, the round
+    # trip of four, and bit-identical repeated calls
+    from tolerances import SPLIT_TOL
+    B = 128
+    p = _plan(B, 4, "tf32x3")
+    c = inputs.random_coeffs(B, 4, seed=2900, decay=True).astype(np.complex64)
+    cd = torch.from_numpy(c).cuda()
+    s = p.inverse(cd)
+    f = p.forward(s)
+    assert _err(f.cpu().numpy(), c) < SPLIT_TOL
+    assert torch.equal(p.inverse(cd), s) and torch.equal(p.forward(s), f)
+    s0 = s[0].cpu().numpy()
+    assert _err(s0[None], O.inverse(c[0].astype(np.complex128), B, rule="hermite")) < SPLIT_TOL
+    p.check()
