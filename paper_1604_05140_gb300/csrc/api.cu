@@ -92,9 +92,8 @@ static void release(Plan* P) {
 }
 
 static void release_pipeline(Plan* P) {
-  if (P->sub) release(P->sub);
-  if (P->sub_tail) release(P->sub_tail);
-  P->sub = P->sub_tail = nullptr;
+  for (auto& kv : P->subs) release(kv.second);
+  P->subs.clear();
   for (cudaEvent_t e : P->pipe_ev) cudaEventDestroy(e);
   P->pipe_ev.clear();
   if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
@@ -502,18 +501,44 @@ static sgl_status ensure_stage(Plan& P, void** buf, size_t* have, size_t need) {
 }
 
 // ---------------------------------------------------------------------------
-// host-buffer calls in sub-batches: the copies of one chunk of functions
-// overlap the kernels of the previous chunk
+// host-buffer calls in chunks: the copies of one chunk of functions overlap
+// the kernels of its neighbours
 // ---------------------------------------------------------------------------
-constexpr int kPipeChunks = 8;   // chunks of one call
 constexpr int kPipeMinFunctions = 16;
 
+// Chunk sizes of n functions growing by about 1.6 from n/16: a host-to-device
+// copy of a chunk (≈27 µs a function at B = 128 over a 200 GB/s link) then
+// ends before the transform of the chunk before it (≈49 µs a function), so
+// only the first, small chunk's copy is exposed, and most functions run in
+// large, efficient chunks.  The last chunk takes the remainder.
+static std::vector<int> grow_schedule(int n) {
+  std::vector<int> out;
+  int sum = 0;
+  double x = std::max(1, n / 16);
+  while (sum + (int)x < n) {
+    out.push_back((int)x);
+    sum += (int)x;
+    x = std::ceil(x * 1.6);
+  }
+  out.push_back(n - sum);
+  return out;
+}
+
+// The chunk sizes of a call: growing when the input is on the host (its
+// first copy is the exposed one), shrinking when only the output is (the
+// small chunk last, whose device-to-host copy is the exposed one).  Both
+// directions use the same sizes, so one sub-plan per size serves every call.
+static std::vector<int> pipe_schedule(int n, bool in_host) {
+  std::vector<int> a = grow_schedule(n);
+  if (!in_host) std::reverse(a.begin(), a.end());
+  return a;
+}
+
 static sgl_status ensure_pipeline(Plan* P) {
-  if (P->sub) return SGL_OK;
+  if (!P->subs.empty()) return SGL_OK;
   const int NB = P->nfn, B = P->fn_B[0];
-  const int q = (NB + kPipeChunks - 1) / kPipeChunks;
-  const int nchunks = (NB + q - 1) / q;
-  const int r = NB - (nchunks - 1) * q;
+  const std::vector<int> sizes = grow_schedule(NB);
+  const size_t nchunks = sizes.size();
   auto make = [&](int n, Plan** out) -> sgl_status {
     Plan* S = new Plan();
     S->prec = P->prec;
@@ -535,12 +560,17 @@ static sgl_status ensure_pipeline(Plan* P) {
     *out = S;
     return SGL_OK;
   };
-  sgl_status st = make(q, &P->sub);
-  if (st == SGL_OK && r != q) st = make(r, &P->sub_tail);
+  sgl_status st = SGL_OK;
+  for (int n : sizes) {
+    if (st != SGL_OK || P->subs.count(n)) continue;
+    Plan* S = nullptr;
+    st = make(n, &S);
+    if (st == SGL_OK) P->subs[n] = S;
+  }
   if (st == SGL_OK && (cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
                        cudaStreamCreateWithFlags(&P->copy_back_stream, cudaStreamNonBlocking) != cudaSuccess))
     st = fail(P, SGL_ERR_CUDA, "copy stream creation failed");
-  for (int k = 0; st == SGL_OK && k < 2 * nchunks + 2; ++k) {
+  for (size_t k = 0; st == SGL_OK && k < 2 * nchunks + 2; ++k) {
     cudaEvent_t ev;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
       st = fail(P, SGL_ERR_CUDA, "event creation failed");
@@ -551,7 +581,6 @@ static sgl_status ensure_pipeline(Plan* P) {
     release_pipeline(P);
     return st;
   }
-  P->sub_q = q;
   return SGL_OK;
 }
 
@@ -576,7 +605,8 @@ static sgl_status execute_pipelined(Plan* P, bool is_fwd, bool weights, const vo
     if (st != SGL_OK) return st;
     dout = (char*)P->d_stage_out;
   }
-  const int q = P->sub_q, n = (P->nfn + q - 1) / q;
+  const std::vector<int> sched = pipe_schedule(P->nfn, !in_dev);
+  const int n = (int)sched.size();
   cudaEvent_t* ev = P->pipe_ev.data();  // [0] start, [1] end, then in/out per chunk
   cudaError_t e = cudaEventRecord(ev[0], s);
   // chunk k: its host-to-device copy on copy_stream (not held back by
@@ -585,9 +615,9 @@ static sgl_status execute_pipelined(Plan* P, bool is_fwd, bool weights, const vo
   // copy_back_stream once the transform is done
   if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_stream, ev[0], 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_back_stream, ev[0], 0);
-  for (int k = 0; k < n && e == cudaSuccess; ++k) {
-    const int f0 = k * q, nk = std::min(q, P->nfn - f0);
-    Plan* S = nk == q ? P->sub : P->sub_tail;
+  for (int k = 0, f0 = 0; k < n && e == cudaSuccess; f0 += sched[k], ++k) {
+    const int nk = sched[k];
+    Plan* S = P->subs.at(nk);
     const size_t io = (size_t)f0 * in_per, oo = (size_t)f0 * out_per;
     if (!in_dev) {
       e = cudaMemcpyAsync((void*)(din + io), (const char*)in + io, (size_t)nk * in_per, cudaMemcpyHostToDevice,
@@ -1129,7 +1159,9 @@ int sgl_radii(sgl_plan_t plan, int fn) {
 int64_t sgl_workspace_bytes(sgl_plan_t plan) {
   if (!plan) return -1;
   const Plan* P = (const Plan*)plan;
-  return P->bytes + (P->sub ? P->sub->bytes : 0) + (P->sub_tail ? P->sub_tail->bytes : 0);
+  int64_t b = P->bytes;
+  for (const auto& kv : P->subs) b += kv.second->bytes;
+  return b;
 }
 
 int sgl_launches_per_call(sgl_plan_t plan) { return plan ? ((Plan*)plan)->launches_per_call : -1; }

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/sgl.h"
@@ -266,13 +267,13 @@ struct Plan {
   // order), cleared and measured by every call (the data scales)
   unsigned* d_amax = nullptr;
 
-  // calls with host buffers on single-bandlimit plans run in sub-batches so
-  // that the copies overlap the kernels (api.cu): a plan of sub_q functions
-  // used for every chunk, one for a shorter last chunk, a copy stream and
-  // its events.  Sub-plans share the parent's error flag.
-  Plan* sub = nullptr;
-  Plan* sub_tail = nullptr;
-  int sub_q = 0;
+  // calls with host buffers on single-bandlimit plans run in chunks of
+  // functions so that the copies overlap the kernels (api.cu): one sub-plan
+  // per chunk size of the schedules (sizes growing from a small first chunk
+  // when the input is on the host, shrinking to a small last chunk when the
+  // output is), copy streams and events.  Sub-plans share the parent's error
+  // flag.
+  std::map<int, Plan*> subs;
   cudaStream_t copy_stream = nullptr;       // host-to-device copies of the chunks
   cudaStream_t copy_back_stream = nullptr;  // device-to-host copies (the other direction of the link)
   std::vector<cudaEvent_t> pipe_ev;
