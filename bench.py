@@ -432,17 +432,26 @@ def paper_grid_path(steps, warmup):
     """The paper's own grid (2B half-range Gauss-Hermite radii): the paper's
     timing configuration (B=64, one function, round trip in FP64, as in its
     Table 2) and B=128 x 16 functions in FP64, FP32 and TF32x3 (the
-    tensor-core stages run each function's radii as two halves).  Round trip
-    on seeded decaying coefficients, CUDA events."""
+    tensor-core stages run each function's radii as two halves), and 16 real
+    functions in TF32x3 (paired, then halved).  Round trip on seeded decaying
+    coefficients (real functions: on the coefficients of the real part of
+    their inverse, which the round trip reproduces), CUDA events."""
     import torch
     from paper_1604_05140_gb300 import Plan, inputs
     out = {}
-    for label, B, nb, prec in (("b64x1_fp64", 64, 1, "fp64"), ("b128x16_fp64", 128, 16, "fp64"),
-                               ("b128x16_fp32", 128, 16, "fp32"), ("b128x16_tf32x3", 128, 16, "tf32x3")):
-        plan = Plan(B, nb, prec, grid="hermite")
+    for label, B, nb, prec, samples in (("b64x1_fp64", 64, 1, "fp64", "weighted"),
+                                        ("b128x16_fp64", 128, 16, "fp64", "weighted"),
+                                        ("b128x16_fp32", 128, 16, "fp32", "weighted"),
+                                        ("b128x16_tf32x3", 128, 16, "tf32x3", "weighted"),
+                                        ("b128x16_tf32x3_real", 128, 16, "tf32x3", "real")):
+        plan = Plan(B, nb, prec, samples=samples, grid="hermite")
         c = torch.from_numpy(inputs.random_coeffs(B, nb, seed=inputs.BASE_SEED + 6, decay=True)).to(plan.dtype).cuda()
-        s = torch.empty(plan.sample_shape, dtype=plan.dtype, device="cuda")
+        s = torch.empty(plan.sample_shape, dtype=plan.sample_dtype, device="cuda")
         c2 = torch.empty_like(c)
+        if samples == "real":
+            plan.inverse(c, out=s)
+            plan.forward(s, out=c2)
+            c = c2.clone()
         for _ in range(max(1, warmup)):
             plan.inverse(c, out=s)
             plan.forward(s, out=c2)
@@ -458,7 +467,7 @@ def paper_grid_path(steps, warmup):
         torch.cuda.synchronize()
         plan.check()
         ms = ev0.elapsed_time(ev1) / steps
-        out[label] = {"B": B, "batch": nb, "precision": prec, "radii": 2 * B, "ms_per_step": ms,
+        out[label] = {"B": B, "batch": nb, "precision": prec, "samples": samples, "radii": 2 * B, "ms_per_step": ms,
                       "value": nb / (ms * 1e-3), "unit": "transforms/s", "steps": steps,
                       "round_trip_max_rel_err": err}
         del plan, s, c, c2

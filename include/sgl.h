@@ -172,14 +172,14 @@ sgl_status sgl_plan(sgl_plan_t* out, int B, int batch, int prec, int samples);
 /*
  * sgl_plan_grid - sgl_plan on the radial grid `grid` (an sgl_grid_kind).
  * SGL_GRID_LAGUERRE is sgl_plan itself.  SGL_GRID_HALF_RANGE_HERMITE takes
- * every precision and sample convention, except SGL_SAMPLES_REAL with a
- * tensor-core precision (SGL_ERR_UNSUPPORTED).  Sample counts, offsets,
- * sgl_grid's r and w_r arrays and the host-buffer staging follow the plan's
- * 2B radii.  Tensor-core plans run each function's radial sums (Eq.
- * DRT_matrix over the 2B nodes) as two partial sums over the first and the
- * second B nodes, added by one more kernel per forward call (Thm 3.3 and
- * Thm 3.4 are unchanged: the same rule, summed in two parts); host buffers
- * are staged whole, without sub-batches.
+ * every precision and sample convention.  Sample counts, offsets, sgl_grid's
+ * r and w_r arrays and the host-buffer staging follow the plan's 2B radii.
+ * Tensor-core plans run each function's radial sums (Eq. DRT_matrix over the
+ * 2B nodes) as two partial sums over the first and the second B nodes, added
+ * by one more kernel per forward call (Thm 3.3 and Thm 3.4 are unchanged:
+ * the same rule, summed in two parts); with SGL_SAMPLES_REAL the real
+ * functions are paired first, as for sgl_plan, and each pair is split into
+ * its halves.  Host buffers are staged whole, without sub-batches.
  */
 sgl_status sgl_plan_grid(sgl_plan_t* out, int B, int batch, int prec, int samples, int grid);
 

@@ -81,7 +81,7 @@ static void release(Plan* P) {
   if (!P->owns_err) P->d_err = nullptr;
   void* ptrs[] = {P->d_tab, P->d_tab_lo, P->d_w1, P->d_w2, P->d_stage_in, P->d_stage_out, P->d_segs,
                   P->d_fn_samp, P->d_fn_coef, P->d_si_rows, P->d_err, P->d_fft_fwd, P->d_fft_inv, P->d_ccoef,
-                  P->d_dct_ctas, P->d_amax};
+                  P->d_pcoef, P->d_dct_ctas, P->d_amax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (GemmSched* g : {&P->leg_fwd, &P->rad_fwd, &P->rad_inv, &P->leg_inv})
@@ -212,7 +212,7 @@ static void set_launch_count(Plan& P) {
     fwd += P.leg_fwd.launches() + P.rad_fwd.launches() + (P.seminaive ? (int)P.segs.size() : 0);
     inv += P.rad_inv.launches() + P.leg_inv.launches();
   }
-  P.launches_per_call = std::max(fwd, inv) + (P.real_pairs || P.radial_halves ? 1 : 0);
+  P.launches_per_call = std::max(fwd, inv) + (P.real_pairs ? 1 : 0) + (P.radial_halves ? 1 : 0);
 }
 
 // FFT CTA lists of both directions (segment order) for the plan's current
@@ -329,6 +329,10 @@ static sgl_status build_plan(Plan* P, const std::vector<int>& Bs, bool uniform) 
     co += coeff_count(B);
     P->maxB = std::max(P->maxB, B);
   }
+  // real functions on the paper's grid: half h of pair q (function 2q + h)
+  // starts, in reals, at half h of the pair's first real function
+  if (P->real_pairs && P->radial_halves)
+    for (int f = 0; f < P->nfn; ++f) P->fn_samp_off[f] = (2 * (int64_t)f - (f & 1)) * (so / P->nfn) / 2;
   P->n_samples = so;
   P->n_coeffs = co;
   // segments: group by bandlimit, largest first; radial halves: one segment
@@ -1011,8 +1015,6 @@ sgl_status sgl_plan_grid(sgl_plan_t* out, int B, int batch, int prec, int sample
     return fail(nullptr, SGL_ERR_ARG, "physical samples need an FP64 plan");
   if (grid != SGL_GRID_LAGUERRE && grid != SGL_GRID_HALF_RANGE_HERMITE)
     return fail(nullptr, SGL_ERR_ARG, "unknown radial grid");
-  if (grid == SGL_GRID_HALF_RANGE_HERMITE && tc_precision(prec) && samples == SGL_SAMPLES_REAL)
-    return fail(nullptr, SGL_ERR_UNSUPPORTED, "real functions on the half-range Gauss-Hermite grid need an FP64 or FP32 plan");
   if (!bandlimit_supported(B)) return fail(nullptr, SGL_ERR_UNSUPPORTED, "unsupported bandlimit");
   if (tc_precision(prec) && B % 4 != 0)
     return fail(nullptr, SGL_ERR_UNSUPPORTED, "tensor-core plans need a bandlimit divisible by 4");
@@ -1028,29 +1030,30 @@ sgl_status sgl_plan_grid(sgl_plan_t* out, int B, int batch, int prec, int sample
   // tensor-core stages on the paper's grid: the two halves of each
   // function's 2B radii as two functions of B radii
   const bool halves = grid == SGL_GRID_HALF_RANGE_HERMITE && tc_precision(prec);
+  const int ncomplex = real ? (batch + 1) / 2 : batch;  // complex functions of 2B radii
   if (halves) {
     P->radial_halves = true;
-    P->nuser = batch;
+    P->nuser = ncomplex;
   }
-  std::vector<int> Bs(real ? (batch + 1) / 2 : halves ? 2 * batch : batch, B);
+  std::vector<int> Bs(halves ? 2 * ncomplex : ncomplex, B);
   sgl_status st = build_plan(P, Bs, true);
-  if (st == SGL_OK && halves) {
+  // coefficient workspaces: d_ccoef the plan's nfn functions (halves or
+  // pairs), d_pcoef the pairs when the plan has both
+  const int64_t fbytes = coeff_count(B) * (int64_t)complex_bytes(*P);
+  if (st == SGL_OK && (halves || real)) {
     P->n_coeffs = (int64_t)batch * coeff_count(B);
-    const int64_t cbytes = (int64_t)P->nfn * coeff_count(B) * (int64_t)complex_bytes(*P);
-    if (cudaMalloc(&P->d_ccoef, cbytes) != cudaSuccess)
+    if (cudaMalloc(&P->d_ccoef, P->nfn * fbytes) != cudaSuccess)
       st = fail(P, SGL_ERR_ALLOC, "workspace allocation failed");
     else
-      P->bytes += cbytes;
+      P->bytes += P->nfn * fbytes;
   }
-  if (st == SGL_OK && real) {
-    P->n_samples = (int64_t)batch * sample_count(B, n_radial(B, grid));  // reals
-    P->n_coeffs = (int64_t)batch * coeff_count(B);
-    const int64_t cbytes = (int64_t)P->nfn * coeff_count(B) * (int64_t)complex_bytes(*P);
-    if (cudaMalloc(&P->d_ccoef, cbytes) != cudaSuccess)
+  if (st == SGL_OK && halves && real) {
+    if (cudaMalloc(&P->d_pcoef, ncomplex * fbytes) != cudaSuccess)
       st = fail(P, SGL_ERR_ALLOC, "workspace allocation failed");
     else
-      P->bytes += cbytes;
+      P->bytes += ncomplex * fbytes;
   }
+  if (st == SGL_OK && real) P->n_samples = (int64_t)batch * sample_count(B, n_radial(B, grid));  // reals
   if (st != SGL_OK) {
     g_create_error = P->err;
     release(P);

@@ -250,7 +250,8 @@ constexpr int ring_elems() {
 
 // Forward: samples -> E/O spectra.  blockDim = 16 * JP.  PAIRS: real
 // functions in pairs, the first at twice the complex offset (in reals) as the
-// real part, the next one as the imaginary part (zero past pair_limit).
+// real part, the one pair_gap reals later as the imaginary part (zero past
+// pair_limit).
 template <typename real, int N2, bool PAIRS>
 __device__ __forceinline__ void fft16_fwd_body(const Fft16Args& a) {
   constexpr int N = 16 * N2;
@@ -279,9 +280,8 @@ __device__ __forceinline__ void fft16_fwd_body(const Fft16Args& a) {
   if (a.mode == 1) scale = misc[NR + i];
   if (a.mode == 2) scale = misc[2 * NR + i];
   const c2<real>* in = reinterpret_cast<const c2<real>*>(a.in) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
-  const int64_t fn_reals = (int64_t)NR * N * N;
   const real* inA = reinterpret_cast<const real*>(a.in) + 2 * a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
-  const bool hasB = PAIRS && 2 * a.fn_samp[sg.fn0 + b] + fn_reals < a.pair_limit;
+  const bool hasB = PAIRS && 2 * a.fn_samp[sg.fn0 + b] + a.pair_gap < a.pair_limit;
   __syncthreads();
 
   // step A: items (r, n2), n2 fastest; 16-point DFT over n1, twiddle, store
@@ -299,7 +299,7 @@ __device__ __forceinline__ void fft16_fwd_body(const Fft16Args& a) {
       if constexpr (PAIRS) {
         const real* ringA = inA + (int64_t)j * N + cc[u];
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) v[u][n1] = {ringA[n1 * N2], hasB ? ringA[fn_reals + n1 * N2] : (real)0};
+        for (int n1 = 0; n1 < 16; ++n1) v[u][n1] = {ringA[n1 * N2], hasB ? ringA[a.pair_gap + n1 * N2] : (real)0};
       } else {
         const c2<real>* ring = in + (int64_t)j * N + cc[u];
 #pragma unroll
@@ -469,14 +469,13 @@ __device__ __forceinline__ void fft16_inv_body(const Fft16Args& a) {
     if (a.mode == 3) s = misc[i] * misc[NR + i];
     if (a.mode >= 2) s *= misc[3 * NR + j];
     if constexpr (PAIRS) {
-      const int64_t fn_reals = (int64_t)NR * N * N;
       const int64_t f0 = 2 * a.fn_samp[sg.fn0 + b];
       real* ringA = reinterpret_cast<real*>(a.out) + f0 + ((int64_t)i * N + j) * N + n2;
 #pragma unroll
       for (int n1 = 0; n1 < 16; ++n1) ringA[n1 * N2] = v[n1].x * s;
-      if (f0 + fn_reals < a.pair_limit) {
+      if (f0 + a.pair_gap < a.pair_limit) {
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) ringA[fn_reals + n1 * N2] = v[n1].y * s;
+        for (int n1 = 0; n1 < 16; ++n1) ringA[a.pair_gap + n1 * N2] = v[n1].y * s;
       }
     } else {
       c2<real>* ring = out + ((int64_t)i * N + j) * N + n2;

@@ -118,6 +118,7 @@ struct FftArgs {
                          // inv: 0 none, 1 *exp(+t/2), 2 *what*beta, 3 *what*beta*exp(-t/2)
   int64_t pair_limit;    // real functions in pairs: reals in the sample array; 0 complex samples
   unsigned* amax;        // forward, FP16x3 plans: per-function largest |E/O| (else null)
+  int64_t pair_gap;      // real functions in pairs: reals from the pair's first function to its second
 };
 
 __host__ __device__ inline int ring_pitch(int n1, int n2) {
@@ -207,10 +208,9 @@ __global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
   if (a.mode == 2) scale = misc[2 * NR + i];
   const cx<real>* in = reinterpret_cast<const cx<real>*>(a.in) + a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
   // real functions in pairs: the pair's first function starts at twice the
-  // complex offset (in reals), the second one function later
-  const int64_t fn_reals = (int64_t)NR * N * N;
+  // complex offset (in reals), the second one function (pair_gap reals) later
   const real* inA = reinterpret_cast<const real*>(a.in) + 2 * a.fn_samp[sg.fn0 + b] + (int64_t)i * N * N;
-  const bool hasB = 2 * a.fn_samp[sg.fn0 + b] + fn_reals < a.pair_limit;
+  const bool hasB = 2 * a.fn_samp[sg.fn0 + b] + a.pair_gap < a.pair_limit;
   for (int e = threadIdx.x; e < R * N; e += blockDim.x) {
     const int r = e / N, k = e - r * N;
     const int q = r >> 1;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) fft_fwd_kernel(FftArgs a) {
     cx<real> v;
     if (a.pair_limit) {
       const int64_t o = (int64_t)j * N + k;
-      v = {inA[o], hasB ? inA[fn_reals + o] : (real)0};
+      v = {inA[o], hasB ? inA[a.pair_gap + o] : (real)0};
     } else {
       v = in[(int64_t)j * N + k];
     }
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) fft_inv_kernel(FftArgs a) {
     if (a.pair_limit) {  // real and imaginary parts to the pair's two functions
       real* outA = reinterpret_cast<real*>(a.out) + 2 * a.fn_samp[sg.fn0 + b];
       outA[o] = v.x;
-      if (2 * a.fn_samp[sg.fn0 + b] + (int64_t)NR * N * N < a.pair_limit) outA[(int64_t)NR * N * N + o] = v.y;
+      if (2 * a.fn_samp[sg.fn0 + b] + a.pair_gap < a.pair_limit) outA[a.pair_gap + o] = v.y;
     } else {
       out[o] = v;
     }
@@ -795,7 +795,7 @@ static cudaError_t run_fft(Plan& P, bool inv, const void* in, void* out, int mod
       max_n2 = std::max(max_n2, f.n2);
     }
     Fft16Args a16 = {P.d_segs, P.d_fn_samp, inv ? P.d_fft_inv : P.d_fft_fwd, P.d_tab, in, out, P.d_w1,
-                     fft_jp(P, sl[0].B, inv), mode, 0, (!inv && P.d_amax) ? P.d_amax + AMAX_EO * P.nfn : nullptr};
+                     fft_jp(P, sl[0].B, inv), mode, 0, (!inv && P.d_amax) ? P.d_amax + AMAX_EO * P.nfn : nullptr, 0};
     cudaError_t e = cudaSuccess;
     fft16_launch_multi(inv, a16, max_n2, count, s, &e);
     if (e != cudaSuccess) return e;
@@ -814,9 +814,10 @@ static cudaError_t run_fft(Plan& P, bool inv, const void* in, void* out, int mod
     a.JP = fft_jp(P, f.B, inv);
     a.mode = mode;
     a.pair_limit = P.real_pairs ? P.n_samples : 0;
+    a.pair_gap = P.real_pairs ? sample_count(P.fn_B[0], n_radial(P.fn_B[0], P.grid)) : 0;
     a.amax = (!inv && P.d_amax) ? P.d_amax + AMAX_EO * P.nfn : nullptr;
     {
-      Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode, a.pair_limit, a.amax};
+      Fft16Args a16 = {a.segs, a.fn_samp, a.ctas, a.tab, a.in, a.out, a.w1, a.JP, a.mode, a.pair_limit, a.amax, a.pair_gap};
       cudaError_t e16 = cudaSuccess;
       if (fft16_launch<real>(inv, a16, f.n1, f.n2, f.count, s, &e16)) {
         if (e16 != cudaSuccess) return e16;
@@ -1045,11 +1046,12 @@ __global__ void __launch_bounds__(256) real_combine_kernel(const cx<real>* in, c
 template <typename real>
 static cudaError_t run_real_pairs(Plan& P, bool split, const void* src, void* dst, cudaStream_t s) {
   const int B = P.fn_B[0];
-  const dim3 grid((unsigned)B, (unsigned)std::min(P.nfn, 65535));
+  const int npairs = (P.nreal + 1) / 2;
+  const dim3 grid((unsigned)B, (unsigned)std::min(npairs, 65535));
   if (split)
-    real_split_kernel<real><<<grid, 256, 0, s>>>((const cx<real>*)src, (cx<real>*)dst, coeff_count(B), P.nfn, P.nreal);
+    real_split_kernel<real><<<grid, 256, 0, s>>>((const cx<real>*)src, (cx<real>*)dst, coeff_count(B), npairs, P.nreal);
   else
-    real_combine_kernel<real><<<grid, 256, 0, s>>>((const cx<real>*)src, (cx<real>*)dst, coeff_count(B), P.nfn,
+    real_combine_kernel<real><<<grid, 256, 0, s>>>((const cx<real>*)src, (cx<real>*)dst, coeff_count(B), npairs,
                                                    P.nreal);
   return cudaGetLastError();
 }
@@ -1097,6 +1099,13 @@ static cudaError_t run_halves(const Plan& P, bool sum, const void* src, void* ds
 }
 
 cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t s, bool weights) {
+  if (P.radial_halves) {  // the halves' partial sums, then (real functions) the pairs' split
+    void* pc = P.real_pairs ? P.d_pcoef : coeffs;
+    cudaError_t e = forward_t<float>(P, samples, P.d_ccoef, s, weights);
+    if (e == cudaSuccess) e = run_halves(P, true, P.d_ccoef, pc, s);
+    if (e == cudaSuccess && P.real_pairs) e = run_real_pairs<float>(P, true, pc, coeffs, s);
+    return e;
+  }
   if (P.real_pairs) {
     const bool d = P.prec == SGL_FP64;
     cudaError_t e = d ? forward_t<double>(P, samples, P.d_ccoef, s, weights)
@@ -1105,15 +1114,21 @@ cudaError_t run_forward(Plan& P, const void* samples, void* coeffs, cudaStream_t
     return d ? run_real_pairs<double>(P, true, P.d_ccoef, coeffs, s)
              : run_real_pairs<float>(P, true, P.d_ccoef, coeffs, s);
   }
-  if (P.radial_halves) {
-    const cudaError_t e = forward_t<float>(P, samples, P.d_ccoef, s, weights);
-    return e != cudaSuccess ? e : run_halves(P, true, P.d_ccoef, coeffs, s);
-  }
   if (P.prec == SGL_FP64) return forward_t<double>(P, samples, coeffs, s, weights);
   return forward_t<float>(P, samples, coeffs, s, weights);
 }
 
 cudaError_t run_inverse(Plan& P, const void* coeffs, void* samples, cudaStream_t s, bool weights) {
+  if (P.radial_halves) {  // (real functions) the pairs' coefficients, then both halves of each
+    const void* pc = coeffs;
+    cudaError_t e = cudaSuccess;
+    if (P.real_pairs) {
+      e = run_real_pairs<float>(P, false, coeffs, P.d_pcoef, s);
+      pc = P.d_pcoef;
+    }
+    if (e == cudaSuccess) e = run_halves(P, false, pc, P.d_ccoef, s);
+    return e != cudaSuccess ? e : inverse_t<float>(P, P.d_ccoef, samples, s, weights);
+  }
   if (P.real_pairs) {
     const bool d = P.prec == SGL_FP64;
     cudaError_t e = d ? run_real_pairs<double>(P, false, coeffs, P.d_ccoef, s)
@@ -1121,10 +1136,6 @@ cudaError_t run_inverse(Plan& P, const void* coeffs, void* samples, cudaStream_t
     if (e != cudaSuccess) return e;
     return d ? inverse_t<double>(P, P.d_ccoef, samples, s, weights)
              : inverse_t<float>(P, P.d_ccoef, samples, s, weights);
-  }
-  if (P.radial_halves) {
-    const cudaError_t e = run_halves(P, false, coeffs, P.d_ccoef, s);
-    return e != cudaSuccess ? e : inverse_t<float>(P, P.d_ccoef, samples, s, weights);
   }
   if (P.prec == SGL_FP64) return inverse_t<double>(P, coeffs, samples, s, weights);
   return inverse_t<float>(P, coeffs, samples, s, weights);

@@ -297,9 +297,14 @@ struct Plan {
   // two segments with their own radial tables); nfn counts those halves,
   // nuser the caller's functions.  d_ccoef holds the halves' coefficients:
   // the forward sums each function's two partial sums, the inverse gives both
-  // halves the function's coefficients.
+  // halves the function's coefficients.  Real functions on the paper's grid
+  // take both forms: nuser counts the complex pairs, each pair's two halves
+  // are functions 2q and 2q + 1 (half h of the pair reads half h of both of
+  // its real functions), and d_pcoef holds the pairs' coefficients between
+  // the halves' sum (or copy) and the split into real functions.
   bool radial_halves = false;
   int nuser = 0;
+  void* d_pcoef = nullptr;
 
   // forward Legendre stage by the seminaive algorithm (sgl_set_dlt, SIMT
   // plans): DCT CTA list (segment, first vector, vectors, 0)
@@ -381,6 +386,9 @@ struct Fft16Args {
   // only below this limit)
   int64_t pair_limit;
   unsigned* amax;        // forward, FP16x3 plans: per-function largest |E/O| (else null)
+  // real functions in pairs: reals from a sample of the pair's first function
+  // to the same sample of its second (one function's reals)
+  int64_t pair_gap;
 };
 // Largest magnitude of a CTA's values, folded into *amax (bits of a
 // non-negative float, compared as integers) with one atomic per CTA; each

@@ -308,8 +308,8 @@ class Plan:
     ``samples="real"`` makes a plan of real functions: real sample tensors
     (``sample_dtype``), complex coefficients, and the inverse returns the real
     part (SGL_SAMPLES_REAL in sgl.h).  ``grid="hermite"`` samples on the
-    paper's own grid of 2B half-range Gauss-Hermite radii (every precision;
-    real functions with FP64/FP32 only): samples of shape (batch, 2B, 2B, 2B).
+    paper's own grid of 2B half-range Gauss-Hermite radii (every precision
+    and sample convention): samples of shape (batch, 2B, 2B, 2B).
     """
 
     def __init__(self, B: Optional[int] = None, batch: int = 1, precision: str = "fp64",

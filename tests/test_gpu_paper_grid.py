@@ -192,6 +192,35 @@ def test_paper_grid_split_precision_adjoints_and_host_buffers(prec):
     p.check()
 
 
+@pytest.mark.parametrize("prec", SPLIT_PRECS + ["bf16x3"])
+@pytest.mark.parametrize("B,batch", [(8, 3), (32, 4), (64, 3)])
+def test_paper_grid_split_precision_real_functions(prec, B, batch):
+    # real functions on the paper's grid with a tensor-core precision: paired
+    # into complex functions, each pair run as its two radial halves; odd
+    # batches leave the last pair's second function empty
+    from tolerances import SPLIT_TOL
+    # BF16x3: 8 + 8 significant bits per pair, the gate of test_gpu_variants
+    tol = 8 * 2.0 ** -16 if prec == "bf16x3" else SPLIT_TOL
+    p = _plan(B, batch, prec, samples="real")
+    assert p.sample_shape == (batch, 2 * B, 2 * B, 2 * B) and p.coeff_shape == (batch, O.coeff_count(B))
+    g = np.random.default_rng(3000 + B).standard_normal((batch, 2 * B, 2 * B, 2 * B)).astype(np.float32)
+    f = p.forward(_dev(g, torch.float32)).cpu().numpy()
+    assert _err(f, O.forward(g.astype(np.float64), B, rule="hermite")) < tol
+    c = inputs.random_coeffs(B, batch, seed=3100 + B, decay=True)
+    s = p.inverse(_dev(c, torch.complex64)).cpu().numpy()
+    assert s.dtype == np.float32
+    assert _err(s, O.inverse(c, B, rule="hermite").real) < tol
+    # adjoints: the real part of the complex adjoint of the forward, and the
+    # complex adjoint of the inverse on real samples
+    a1 = p.adjoint(_dev(c, torch.complex64), of_inverse=False).cpu().numpy().astype(np.float64)
+    assert _err(a1, O.adjoint_forward(c, B, rule="hermite").real) < tol
+    a2 = p.adjoint(_dev(g, torch.float32), of_inverse=True).cpu().numpy()
+    assert _err(a2, O.adjoint_inverse(g.astype(np.complex128), B, rule="hermite")) < tol
+    # host buffers give the device-buffer result bit for bit
+    assert torch.equal(p.forward(torch.from_numpy(g)), torch.from_numpy(f))
+    p.check()
+
+
 def test_paper_grid_split_precision_b128():
     # B = 128 on 256 radii, TF32x3: one function against the oracle, the round
     # trip of four, and bit-identical repeated calls

@@ -59,9 +59,6 @@ def test_plan_argument_errors(lib, args, status):
 
 @pytest.mark.parametrize("args,status", [
     ((8, 1, 0, 0, 7), sgl.SGL_ERR_ARG),             # unknown radial grid
-    ((8, 1, 2, 2, 1), sgl.SGL_ERR_UNSUPPORTED),     # paper's grid: real functions on FP64 / FP32 plans only
-    ((8, 1, 3, 2, 1), sgl.SGL_ERR_UNSUPPORTED),
-    ((8, 1, 5, 2, 1), sgl.SGL_ERR_UNSUPPORTED),
     ((6, 1, 2, 0, 1), sgl.SGL_ERR_UNSUPPORTED),     # tensor-core plans: B divisible by 4
     ((8, 1, 1, 1, 1), sgl.SGL_ERR_ARG),             # physical samples still need FP64
     ((0, 1, 0, 0, 1), sgl.SGL_ERR_ARG),
