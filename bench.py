@@ -806,7 +806,10 @@ def run_ours(args):
     cbytes = 16 if args.precision == "fp64" else 8
     value = head["value"]
     rl = roofline(head["stage"], cbytes, args.precision)
-    e2e_dt, e2e_windows, nbytes = e2e_path(plan, head["bufs"][0], max(3, min(args.steps, 10)), 2)
+    # warm-up as for the device-buffer steps, at least 5 round trips: the first
+    # host-buffer calls on freshly pinned buffers run slower (measured 27, 15,
+    # then 7 ms per step in consecutive 5-step windows after 2 warm-up steps)
+    e2e_dt, e2e_windows, nbytes = e2e_path(plan, head["bufs"][0], max(3, min(args.steps, 10)), max(5, args.warmup))
     e2e_value, _ = whole_job(ws, BATCH, e2e_dt * 1e3)
     line = {
         "metric": METRIC,

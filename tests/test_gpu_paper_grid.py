@@ -221,6 +221,22 @@ def test_paper_grid_split_precision_real_functions(prec, B, batch):
     p.check()
 
 
+def test_paper_grid_split_precision_real_b128():
+    # B = 128 on 256 radii, TF32x3, three real functions (the last one
+    # unpaired): its inverse against the oracle's real part, the forward of the
+    # first function's samples against the oracle's forward
+    from tolerances import SPLIT_TOL
+    B = 128
+    p = _plan(B, 3, "tf32x3", samples="real")
+    c = inputs.random_coeffs(B, 3, seed=3200, decay=True).astype(np.complex64)
+    s = p.inverse(torch.from_numpy(c).cuda())
+    f = p.forward(s).cpu().numpy()
+    s = s.cpu().numpy()
+    assert _err(s[2:], O.inverse(c[2].astype(np.complex128), B, rule="hermite").real) < SPLIT_TOL
+    assert _err(f[:1], O.forward(s[0].astype(np.float64), B, rule="hermite")) < SPLIT_TOL
+    p.check()
+
+
 def test_paper_grid_split_precision_b128():
     # B = 128 on 256 radii, TF32x3: one function against the oracle, the round
     # trip of four, and bit-identical repeated calls
