@@ -384,6 +384,14 @@ def test_real_function_symmetry(B):
     # and the inverse of such coefficients is real
     s = O.inverse(c, B)
     assert np.abs(s.imag).max() < 1e-13 * np.abs(s).max()
+    # the same on the paper's grid (2B half-range Gauss-Hermite radii): the
+    # symmetry comes from the angular part alone, whatever the radial rule
+    gh = inputs.random_real((2, 2 * B, 2 * B, 2 * B), seed=80 + B)
+    ch = O.forward(gh, B, rule="hermite")
+    np.testing.assert_allclose(ch[:, im], sign * np.conj(ch[:, ip]), atol=1e-13 * np.abs(ch).max())
+    assert np.abs(ch[:, m0].imag).max() < 1e-13 * np.abs(ch).max()
+    sh = O.inverse(ch, B, rule="hermite")
+    assert np.abs(sh.imag).max() < 1e-13 * np.abs(sh).max()
 
 
 def test_forward_then_inverse_is_projector():
