@@ -34,9 +34,13 @@
  * (pinned or pageable); the library asks the CUDA driver which it is.  Host
  * buffers are staged through plan-owned device memory, and the call then
  * synchronizes its stream before it returns; on single-bandlimit plans of
- * 16 or more functions such a call runs in 8 chunks of functions, the copies
- * of one chunk (on a stream of the plan) overlapping the kernels of the
- * previous one (the first such call builds the chunk plans).  Device buffers
+ * 16 or more functions on complex samples such a call runs in chunks of
+ * functions that grow from n/16 by a factor of about 1.6 (4, 7, 12, 20, 21
+ * for 64 functions; in the reverse order when only the output is on the
+ * host), the host-to-device copies of later chunks and the device-to-host
+ * copies of earlier ones (on two streams of the plan) overlapping the
+ * kernels of the chunk in between (the first such call builds the chunk
+ * plans; the results equal those of one device-buffer call).  Device buffers
  * are used in place and the call is asynchronous (stream-ordered); they
  * must be aligned to the complex element (16 bytes for SGL_FP64 plans, 8
  * otherwise: the kernels move whole complex values), else the call returns
