@@ -60,6 +60,9 @@ def test_plan_argument_errors(lib, args, status):
 @pytest.mark.parametrize("args,status", [
     ((8, 1, 0, 0, 7), sgl.SGL_ERR_ARG),             # unknown radial grid
     ((6, 1, 2, 0, 1), sgl.SGL_ERR_UNSUPPORTED),     # tensor-core plans: B divisible by 4
+    ((6, 3, 3, 2, 1), sgl.SGL_ERR_UNSUPPORTED),     # ... real functions on the paper's grid too
+    ((17, 2, 0, 2, 1), sgl.SGL_ERR_UNSUPPORTED),    # unsupported bandlimit, real functions
+    ((8, 0, 3, 2, 1), sgl.SGL_ERR_ARG),             # empty batch
     ((8, 1, 1, 1, 1), sgl.SGL_ERR_ARG),             # physical samples still need FP64
     ((0, 1, 0, 0, 1), sgl.SGL_ERR_ARG),
 ])
